@@ -1,0 +1,191 @@
+/*
+ * hzs.h - C ABI of a GPU solver for the 2-D Helmholtz equation with two-level
+ * Schwarz preconditioned GMRES and quadratic B-spline (B_2) coarse spaces.
+ *
+ * Method: Sieburgh, Heinlein, Dwarka, Vuik, "Coarse Spaces Based on
+ * Higher-Order Interpolation for Schwarz Preconditioners for Helmholtz
+ * Problems" (arXiv 2408.03571).  Section numbers and equation numbers below
+ * refer to that paper.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Grid functions live on the uniform n x n grid of the unit square, n odd,
+ *   h = 1/(n-1) (Section 2).  A grid function is n*n interleaved complex
+ *   doubles (re, im), row-major, node (i, j) (i = x index, j = y index) at
+ *   flat index j*n + i.  That is the layout of a C-contiguous
+ *   torch.complex128 tensor of shape (n, n).  Several right-hand sides are
+ *   stored back to back (shape (nrhs, n, n)).
+ * - MP-1 (Dirichlet, Eq. 1): the boundary nodes are not unknowns.  Inputs
+ *   are read on interior nodes only; outputs are written as 0 on the boundary.
+ *   MP-2 (Sommerfeld, Eq. 2): all n*n nodes are unknowns.
+ * - All pointers named *_dev are device pointers on the current CUDA device;
+ *   the caller allocates, owns and frees them.  Buffers must be 16-byte
+ *   aligned.  Input and output buffers must not overlap unless stated.
+ * - The library allocates (cudaMalloc) and owns the factors and work space
+ *   of a handle; they are freed by the matching destroy call.  A handle must
+ *   not be used from two host threads at once.
+ * - All work of a handle is issued on the CUDA stream given at grid
+ *   creation.  Calls that return results to host memory (hzs_solve_info)
+ *   synchronise that stream before returning; the others only enqueue.
+ * - Every call returns an hzs_status.  No call aborts or throws.  A
+ *   message for the last failure of a handle is available from
+ *   hzs_last_error().  Asynchronous device errors surface as HZS_ERR_CUDA at
+ *   the next synchronising call.
+ */
+#ifndef HZS_H
+#define HZS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HZS_OK = 0,
+    HZS_NOT_CONVERGED = 1,        /* soft result: u holds the last iterate, info is filled */
+    HZS_ERR_INVALID_ARG = -1,
+    HZS_ERR_CUDA = -2,
+    HZS_ERR_OOM = -3,
+    HZS_ERR_SINGULAR_LOCAL = -4,  /* a zero pivot in a subdomain factorisation */
+    HZS_ERR_SINGULAR_COARSE = -5, /* a zero pivot in the coarse factorisation */
+    HZS_ERR_NONFINITE = -6,       /* NaN/Inf in the right-hand side or the iteration */
+    HZS_ERR_TIMEOUT = -7,
+    HZS_ERR_BREAKDOWN = -8
+} hzs_status;
+
+/* Boundary condition (Section 2). */
+typedef enum { HZS_DIRICHLET = 0 /* MP-1 */, HZS_SOMMERFELD = 1 /* MP-2 */ } hzs_bc;
+
+/* Schwarz preconditioner (Section 3).  Q = R_0^T (R_0 A R_0^T)^{-1} R_0.
+ *   HZS_AS1  : sum_i R_i^T A_i^{-1} R_i                      (one level, Section 3)
+ *   HZS_AS2  : Q + sum_i R_i^T A_i^{-1} R_i                  (Eq. 4)
+ *   HZS_SAS2 : Q + sum_i R_i^T D_i A_i^{-1} R_i              (Eq. 5)
+ *   HZS_SHS2 : Q + (sum_i R_i^T D_i A_i^{-1} R_i)(I - A Q)    (Eq. 6)
+ * with A_i = R_i A R_i^T solved exactly and D_i the 0/1 owner indicator. */
+typedef enum { HZS_AS1 = 0, HZS_AS2 = 1, HZS_SAS2 = 2, HZS_SHS2 = 3 } hzs_precond_kind;
+
+/* Coarse basis (Section 4): linear hats (P_1) or quadratic B-splines of knot
+ * spacing H (B_2; for H = 2h these are the weights of Eq. 7). */
+typedef enum { HZS_COARSE_NONE = 0, HZS_COARSE_P1 = 1, HZS_COARSE_B2 = 2 } hzs_coarse_kind;
+
+/* HZS_FP64: every step in complex128.  HZS_MIXED: flexible GMRES in complex128
+ * (matrix-vector product, orthogonalisation, least squares) around a
+ * preconditioner whose stencil, transfers and subdomain solves run in
+ * complex64; the coarse solve stays complex128. */
+typedef enum { HZS_FP64 = 0, HZS_MIXED = 1 } hzs_precision;
+
+/* Problem and decomposition (Sections 2 and 3).
+ *   n        : grid nodes per axis, odd, >= 5.
+ *   bc       : boundary condition.
+ *   k        : constant wavenumber, used when kappa_dev is NULL (kappa = k^2).
+ *   kappa_dev: optional device array of n*n doubles, the squared wavenumber
+ *              kappa = k(x,y)^2 > 0 at every node; copied at creation.
+ *   nsub     : subdomains per axis; must divide n-1.  Subdomain a owns grid
+ *              nodes [a w, (a+1) w) per axis, w = (n-1)/nsub, the last one
+ *              also node n-1 (MP-1 drops the boundary nodes).
+ *   overlap  : node layers added on each side of an owned block, >= 0. */
+typedef struct {
+    int n;
+    hzs_bc bc;
+    double k;
+    const double* kappa_dev;
+    int nsub;
+    int overlap;
+} hzs_grid_desc;
+
+/* Preconditioner set-up (Sections 3 and 4).
+ *   coarse_ratio: p = H/h, >= 2, must divide n-1 (ignored for HZS_AS1).
+ *   dedup_tiles : nonzero lets subdomains with identical local matrices share
+ *                 one factorisation (only possible for constant k). */
+typedef struct {
+    hzs_precond_kind kind;
+    hzs_coarse_kind coarse;
+    int coarse_ratio;
+    hzs_precision precision;
+    int dedup_tiles;
+} hzs_precond_desc;
+
+/* GMRES controls (Section 5): right preconditioning, zero initial guess, no
+ * restart; stop when ||f - A u||_2 <= tol ||f||_2 (the GMRES estimate) or
+ * after maxit steps. */
+typedef struct {
+    double tol;
+    int maxit;
+    int flags;             /* HZS_SOLVE_PROFILE: time the phases of every step */
+} hzs_solve_desc;
+
+#define HZS_SOLVE_PROFILE 1
+
+/* Per right-hand side results. */
+typedef struct {
+    int iterations;        /* Arnoldi steps taken */
+    int converged;         /* 1 if the estimate met tol */
+    double relres_est;     /* GMRES residual estimate / ||f|| */
+    double relres_true;    /* ||f - A u|| / ||f|| recomputed in FP64 */
+    double t_solve_ms;     /* device time of this solve (CUDA events on the stream) */
+    double t_precond_ms;   /* with HZS_SOLVE_PROFILE: device time in the preconditioner, */
+    double t_matvec_ms;    /*   in the matrix-vector products, */
+    double t_orth_ms;      /*   and in the CGS2 orthogonalisation and Givens update; else 0 */
+    long long launches;    /* kernel launches this solve issued */
+    hzs_status status;
+} hzs_solve_info;
+
+typedef struct hzs_grid hzs_grid;
+typedef struct hzs_precond hzs_precond;
+
+/* Creates the grid, operator and decomposition of Sections 2-3.  cuda_stream
+ * is a cudaStream_t (NULL = legacy default stream).  On success *out is a new
+ * handle; on failure *out is NULL. */
+hzs_status hzs_grid_create(const hzs_grid_desc* desc, void* cuda_stream, hzs_grid** out);
+void hzs_grid_destroy(hzs_grid* g);
+
+/* Factorises the subdomain matrices A_i = R_i A R_i^T (exactly, Section 3) and
+ * the coarse matrix A_0 = R_0 A R_0^T (Eq. 4, Section 4).  The grid must
+ * outlive the preconditioner.  Synchronises the stream. */
+hzs_status hzs_precond_setup(hzs_grid* g, const hzs_precond_desc* desc, hzs_precond** out);
+void hzs_precond_destroy(hzs_precond* p);
+
+/* y = A x for nrhs grid functions (Eq. 3, second-order finite differences;
+ * MP-2 boundary rows are the symmetric ghost-node form).  x_dev and y_dev
+ * must not overlap. */
+hzs_status hzs_apply_operator(hzs_precond* p, const void* x_dev, void* y_dev, int nrhs);
+
+/* z = M^{-1} v for nrhs grid functions (Eqs. 4-6 or one-level AS), in the
+ * preconditioner's precision (complex128 in and out either way). */
+hzs_status hzs_apply_precond(hzs_precond* p, const void* v_dev, void* z_dev, int nrhs);
+
+/* Solves A u = f for nrhs right-hand sides with preconditioned GMRES
+ * (Section 5; flexible GMRES when the preconditioner is HZS_MIXED).
+ * info points to nrhs host structs.  Returns HZS_NOT_CONVERGED if any
+ * right-hand side missed tol within maxit. */
+hzs_status hzs_solve(hzs_precond* p, const hzs_solve_desc* sd, const void* f_dev, void* u_dev,
+                     int nrhs, hzs_solve_info* info);
+
+/* Solves the adjoint system conj(A) lambda = g with the same preconditioned
+ * GMRES (as A mu = conj(g), lambda = conj(mu), since A = A^T, Section 2).
+ * The paper has no adjoint; it serves the kappa gradient below. */
+hzs_status hzs_adjoint_solve(hzs_precond* p, const hzs_solve_desc* sd, const void* g_dev,
+                             void* lam_dev, int nrhs, hzs_solve_info* info);
+
+/* grad[node] = -Re( conj(lam[node]) * dA_PP/dkappa_P * u[node] ) for one
+ * right-hand side: the gradient of a real loss L(u) w.r.t. the squared
+ * wavenumber field, given u = A^{-1} f and lam from hzs_adjoint_solve with
+ * g = dL/d(conj u).  grad_dev is n*n doubles (0 on MP-1 boundary nodes).
+ * The paper has no counterpart. */
+hzs_status hzs_kappa_gradient(hzs_precond* p, const void* u_dev, const void* lam_dev,
+                              double* grad_dev);
+
+/* Human-readable text of a status; never NULL. */
+const char* hzs_status_string(hzs_status s);
+/* Message of the last failure on this grid (or of the last global failure
+ * if g is NULL); never NULL, empty if none. */
+const char* hzs_last_error(const hzs_grid* g);
+
+/* Library version string. */
+const char* hzs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HZS_H */

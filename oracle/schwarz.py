@@ -10,7 +10,8 @@ A_i^{-1} = (R_i A R_i^T)^{-1} done by a sparse direct solver (Section 3):
 * SAS2 (Eq. (5)):                 M^{-1} = Q + sum_i R_i^T D_i A_i^{-1} R_i
 * SHS2 (Eq. (6)):                 M^{-1} = Q + (sum_i R_i^T D_i A_i^{-1} R_i)(I - A Q)
 
-The local problems are factorised once with SuperLU (scipy.sparse.linalg.splu).
+The local problems are factorised once with SuperLU (scipy.sparse.linalg.splu,
+minimum-degree ordering on A_i^T + A_i, partial pivoting).
 """
 from __future__ import annotations
 
@@ -36,7 +37,9 @@ class Schwarz:
         self.lu = []
         for s in self.dec.subs:
             Ai = Ar[s.idx][:, s.idx].tocsc()
-            self.lu.append(spla.splu(Ai))
+            # A_i has a symmetric nonzero pattern (Section 2), so the fill-reducing
+            # ordering is minimum degree on A^T + A
+            self.lu.append(spla.splu(Ai, permc_spec="MMD_AT_PLUS_A"))
         self.coarse = None
         if kind != AS1:
             self.coarse = CoarseSolver(CoarseSpace(prob, coarse, p), Ar)

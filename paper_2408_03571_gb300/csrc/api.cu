@@ -1,0 +1,648 @@
+// C ABI (include/hzs.h): handles, validation, set-up and the GMRES driver.
+//
+// The driver is host-issued: each Arnoldi step enqueues the preconditioner,
+// the matrix-vector product and the CGS2 / Givens kernels on the handle's
+// stream.  The host keeps one step in flight ahead of the convergence flag it
+// reads back (pinned memory, one event per step), and every kernel of a step
+// that is enqueued after convergence returns immediately.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "kernels.cuh"
+
+using namespace hzs;
+
+namespace {
+
+thread_local std::string g_global_err;
+
+struct AxisBlock {
+    int own_lo, own_hi, ext_lo, ext_hi;
+};
+
+}  // namespace
+
+struct hzs_grid {
+    hzs_grid_desc desc{};
+    cudaStream_t stream = nullptr;
+    double* kappa = nullptr;          // owned copy of the field (or null)
+    OpDesc op{};
+    int num_sms = 0;
+    int lo = 0, hi = 0;               // unknown index range per axis
+    std::vector<AxisBlock> blocks;    // per axis (both axes identical)
+    std::vector<Tile> tiles;          // nsub * nsub, tile = by * nsub + bx
+    std::vector<int4> cover;          // per grid index: (block, offset, block, offset)
+    int max_mx = 0, max_my = 0;
+    std::string err;
+};
+
+struct hzs_precond {
+    hzs_grid* g = nullptr;
+    hzs_precond_desc desc{};
+    Ctx cx{};
+    HostCoarseTab hct;
+    int use_coarse = 0;
+    int Nc = 0;
+    // device coarse tables
+    int *c0 = nullptr, *lo = nullptr, *hi = nullptr, *off = nullptr;
+    double *w = nullptr, *wt = nullptr;
+    double2* Ainv = nullptr;
+    double coarse_minpiv = 0.0;
+    // local factors
+    int nfactors = 0;
+    double2* W64 = nullptr;
+    float2* W32 = nullptr;
+    std::vector<FactorStat> fstats;
+    Tile* tiles_d = nullptr;
+    int4* cover_d = nullptr;
+    long long ytiles_elems = 0;
+    // apply work space
+    void* t_buf = nullptr;            // n * nc1 working complex
+    double2* c_buf = nullptr;         // Nc
+    double2* c2_buf = nullptr;        // Nc
+    void* w_buf = nullptr;            // n*n working complex
+    void* ytiles = nullptr;           // sum of tile sizes, working complex
+    float2* zc64 = nullptr;           // n*n (mixed public apply)
+    // solve work space
+    KrylovBufs kb{};
+    int kb_maxit = 0;
+    float2* Z = nullptr;              // maxit x ld (mixed)
+    double2* ztmp = nullptr;          // ld (FP64 z / x)
+    double2* rtmp = nullptr;          // ld
+    double* dres = nullptr;           // 1
+    int* h_done = nullptr;            // pinned, 2 slots
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    std::vector<cudaEvent_t> prof_ev;  // 4 per step when phase timing is on
+};
+
+// ------------------------------------------------------------------ helpers
+static hzs_status fail(hzs_grid* g, hzs_status s, const std::string& msg) {
+    if (g) g->err = msg; else g_global_err = msg;
+    return s;
+}
+
+static hzs_status cuda_fail(hzs_grid* g, cudaError_t e, const char* where) {
+    return fail(g, e == cudaErrorMemoryAllocation ? HZS_ERR_OOM : HZS_ERR_CUDA,
+                std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define HZS_CUDA(g, call)                                             \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return cuda_fail((g), e_, #call);      \
+    } while (0)
+
+template <typename T>
+static cudaError_t dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+static size_t cplx_size(hzs_precision prec) { return prec == HZS_MIXED ? sizeof(float2) : sizeof(double2); }
+
+// ------------------------------------------------------------------ grid
+extern "C" hzs_status hzs_grid_create(const hzs_grid_desc* d, void* cuda_stream, hzs_grid** out) {
+    if (!out) return fail(nullptr, HZS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!d) return fail(nullptr, HZS_ERR_INVALID_ARG, "desc is NULL");
+    if (d->n < 5 || d->n % 2 != 1) return fail(nullptr, HZS_ERR_INVALID_ARG, "n must be odd and >= 5");
+    if (d->bc != HZS_DIRICHLET && d->bc != HZS_SOMMERFELD) return fail(nullptr, HZS_ERR_INVALID_ARG, "bad bc");
+    if (d->nsub < 1 || (d->n - 1) % d->nsub != 0) return fail(nullptr, HZS_ERR_INVALID_ARG, "nsub must divide n-1");
+    const int w = (d->n - 1) / d->nsub;
+    if (d->overlap < 0) return fail(nullptr, HZS_ERR_INVALID_ARG, "overlap must be >= 0");
+    if (2 * d->overlap > w)
+        return fail(nullptr, HZS_ERR_INVALID_ARG, "overlap must be at most half the subdomain width");
+    if (d->bc == HZS_DIRICHLET && w < 2) return fail(nullptr, HZS_ERR_INVALID_ARG, "subdomain width must be >= 2");
+    if (!d->kappa_dev && !(d->k > 0.0 && std::isfinite(d->k)))
+        return fail(nullptr, HZS_ERR_INVALID_ARG, "k must be positive and finite");
+
+    hzs_grid* g = new hzs_grid();
+    g->desc = *d;
+    g->stream = (cudaStream_t)cuda_stream;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        delete g;
+        return fail(nullptr, HZS_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    }
+    const int n = d->n;
+    if (d->kappa_dev) {
+        e = dalloc(&g->kappa, (size_t)n * n);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(g->kappa, d->kappa_dev, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice,
+                                g->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) {
+            cudaFree(g->kappa);
+            delete g;
+            return fail(nullptr, HZS_ERR_CUDA, std::string("kappa copy: ") + cudaGetErrorString(e));
+        }
+    }
+    const double h = 1.0 / (n - 1);
+    g->op.n = n;
+    g->op.bc = d->bc;
+    g->op.inv_h2 = 1.0 / (h * h);
+    g->op.inv_h = 1.0 / h;
+    g->op.kappa0 = d->kappa_dev ? 0.0 : d->k * d->k;
+    g->op.kappa = g->kappa;
+    g->lo = d->bc == HZS_DIRICHLET ? 1 : 0;
+    g->hi = d->bc == HZS_DIRICHLET ? n - 2 : n - 1;
+    // owned blocks [a w, (a+1) w) (last one closed at n-1) within the unknowns, extended by overlap
+    for (int a = 0; a < d->nsub; ++a) {
+        AxisBlock b;
+        b.own_lo = std::max(a * w, g->lo);
+        b.own_hi = std::min(a < d->nsub - 1 ? (a + 1) * w - 1 : n - 1, g->hi);
+        b.ext_lo = std::max(b.own_lo - d->overlap, g->lo);
+        b.ext_hi = std::min(b.own_hi + d->overlap, g->hi);
+        g->blocks.push_back(b);
+    }
+    g->cover.assign(n, make_int4(-1, 0, -1, 0));
+    for (int i = 0; i < n; ++i) {
+        int cnt = 0;
+        int4 c = make_int4(-1, 0, -1, 0);
+        for (int a = 0; a < d->nsub; ++a) {
+            const AxisBlock& b = g->blocks[a];
+            if (i >= b.ext_lo && i <= b.ext_hi) {
+                if (cnt == 0) { c.x = a; c.y = i - b.ext_lo; }
+                else if (cnt == 1) { c.z = a; c.w = i - b.ext_lo; }
+                ++cnt;
+            }
+        }
+        if (cnt > 2) {
+            cudaFree(g->kappa);
+            delete g;
+            return fail(nullptr, HZS_ERR_INVALID_ARG, "a node lies in more than two subdomains per axis");
+        }
+        g->cover[i] = c;
+    }
+    long long yoff = 0;
+    for (int by = 0; by < d->nsub; ++by)
+        for (int bx = 0; bx < d->nsub; ++bx) {
+            const AxisBlock &X = g->blocks[bx], &Y = g->blocks[by];
+            Tile t{};
+            t.x0 = X.ext_lo; t.y0 = Y.ext_lo;
+            t.mx = X.ext_hi - X.ext_lo + 1; t.my = Y.ext_hi - Y.ext_lo + 1;
+            t.ox0 = X.own_lo; t.ox1 = X.own_hi; t.oy0 = Y.own_lo; t.oy1 = Y.own_hi;
+            t.factor = -1; t.woff = 0; t.yoff = yoff;
+            yoff += (long long)t.mx * t.my;
+            g->max_mx = std::max(g->max_mx, t.mx);
+            g->max_my = std::max(g->max_my, t.my);
+            g->tiles.push_back(t);
+        }
+    *out = g;
+    return HZS_OK;
+}
+
+extern "C" void hzs_grid_destroy(hzs_grid* g) {
+    if (!g) return;
+    cudaFree(g->kappa);
+    delete g;
+}
+
+// ------------------------------------------------------------------ preconditioner
+static void free_krylov(hzs_precond* p) {
+    KrylovBufs& kb = p->kb;
+    cudaFree(kb.V); cudaFree(kb.sigma); cudaFree(kb.H); cudaFree(kb.cs); cudaFree(kb.sn); cudaFree(kb.g);
+    cudaFree(kb.y); cudaFree(kb.h1); cudaFree(kb.h2); cudaFree(kb.part); cudaFree(kb.npart); cudaFree(kb.st);
+    cudaFree(p->Z);
+    kb = KrylovBufs{};
+    p->Z = nullptr;
+    p->kb_maxit = 0;
+}
+
+extern "C" void hzs_precond_destroy(hzs_precond* p) {
+    if (!p) return;
+    free_krylov(p);
+    cudaFree(p->c0); cudaFree(p->lo); cudaFree(p->hi); cudaFree(p->off); cudaFree(p->w); cudaFree(p->wt);
+    cudaFree(p->Ainv); cudaFree(p->W64); cudaFree(p->W32); cudaFree(p->tiles_d); cudaFree(p->cover_d);
+    cudaFree(p->t_buf); cudaFree(p->c_buf); cudaFree(p->c2_buf); cudaFree(p->w_buf); cudaFree(p->ytiles);
+    cudaFree(p->zc64); cudaFree(p->ztmp); cudaFree(p->rtmp); cudaFree(p->dres);
+    if (p->h_done) cudaFreeHost(p->h_done);
+    for (auto& e : p->ev) if (e) cudaEventDestroy(e);
+    if (p->t0) cudaEventDestroy(p->t0);
+    if (p->t1) cudaEventDestroy(p->t1);
+    for (auto e : p->prof_ev) cudaEventDestroy(e);
+    delete p;
+}
+
+template <typename T>
+static cudaError_t upload(T** dst, const std::vector<T>& src, cudaStream_t s) {
+    cudaError_t e = dalloc(dst, src.size());
+    if (e != cudaSuccess || src.empty()) return e;
+    return cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+}
+
+static hzs_status setup_impl(hzs_grid* g, const hzs_precond_desc* d, hzs_precond* p) {
+    const int n = g->desc.n;
+    cudaStream_t s = g->stream;
+    p->cx.op = g->op;
+    p->cx.stream = s;
+    p->cx.num_sms = g->num_sms;
+    p->use_coarse = d->kind != HZS_AS1;
+    // ---- coarse level
+    if (p->use_coarse) {
+        if (d->coarse != HZS_COARSE_P1 && d->coarse != HZS_COARSE_B2)
+            return fail(g, HZS_ERR_INVALID_ARG, "two-level preconditioners need coarse = P1 or B2");
+        const int pr = d->coarse_ratio;
+        if (pr < 2 || (n - 1) % pr != 0) return fail(g, HZS_ERR_INVALID_ARG, "coarse_ratio must be >= 2 and divide n-1");
+        build_coarse_tables(n, g->desc.bc, d->coarse, pr, p->hct);
+        if (p->hct.nc1 < 1) return fail(g, HZS_ERR_INVALID_ARG, "coarse mesh has no interior nodes");
+        if (p->hct.bad) return fail(g, HZS_ERR_INVALID_ARG, "coarse basis wider than three coarse cells");
+        p->Nc = p->hct.nc1 * p->hct.nc1;
+        if (p->Nc > 8192) return fail(g, HZS_ERR_INVALID_ARG, "coarse space larger than 8192 (dense coarse solve)");
+        HZS_CUDA(g, upload(&p->c0, p->hct.c0, s));
+        HZS_CUDA(g, upload(&p->w, p->hct.w, s));
+        HZS_CUDA(g, upload(&p->lo, p->hct.lo, s));
+        HZS_CUDA(g, upload(&p->hi, p->hct.hi, s));
+        HZS_CUDA(g, upload(&p->off, p->hct.off, s));
+        HZS_CUDA(g, upload(&p->wt, p->hct.wt, s));
+        p->cx.ct.nc1 = p->hct.nc1;
+        p->cx.ct.c0 = p->c0; p->cx.ct.w = p->w; p->cx.ct.lo = p->lo; p->cx.ct.hi = p->hi;
+        p->cx.ct.off = p->off; p->cx.ct.wt = p->wt;
+        HZS_CUDA(g, dalloc(&p->Ainv, (size_t)p->Nc * p->Nc));
+        launch_galerkin(p->cx, p->Ainv);
+        HZS_CUDA(g, cudaGetLastError());
+        double minpiv = 0.0;
+        const int rc = gj_invert(p->cx, p->Ainv, p->Nc, &minpiv);
+        if (rc < 0) return fail(g, HZS_ERR_CUDA, "coarse factorisation failed");
+        p->coarse_minpiv = minpiv;
+        if (rc > 0) return fail(g, HZS_ERR_SINGULAR_COARSE, "coarse matrix A_0 has a zero pivot");
+        HZS_CUDA(g, dalloc(&p->c_buf, p->Nc));
+        HZS_CUDA(g, dalloc(&p->c2_buf, p->Nc));
+        HZS_CUDA(g, cudaMalloc(&p->t_buf, (size_t)n * p->hct.nc1 * cplx_size(d->precision)));
+    }
+    if (g->max_mx > max_tile_extent() || g->max_my > max_tile_extent())
+        return fail(g, HZS_ERR_INVALID_ARG,
+                    "subdomain tile larger than " + std::to_string(max_tile_extent()) + " nodes per axis");
+    // ---- local factors (dedup identical tiles when kappa is constant)
+    std::vector<Tile> tiles = g->tiles;
+    std::vector<FactorDesc> fds;
+    std::map<std::tuple<int, int, int, int, int, int>, int> keys;
+    long long woff = 0;
+    const bool dedup = d->dedup_tiles && g->kappa == nullptr;
+    for (size_t t = 0; t < tiles.size(); ++t) {
+        Tile& T = tiles[t];
+        const bool sf = g->desc.bc == HZS_SOMMERFELD;
+        auto key = std::make_tuple(T.mx, T.my, sf && T.x0 == 0, sf && T.x0 + T.mx - 1 == n - 1, sf && T.y0 == 0,
+                                   sf && T.y0 + T.my - 1 == n - 1);
+        auto it = dedup ? keys.find(key) : keys.end();
+        if (it != keys.end()) {
+            T.factor = it->second;
+            T.woff = fds[it->second].woff;
+            continue;
+        }
+        FactorDesc fd{T.x0, T.y0, T.mx, T.my, woff};
+        T.factor = (int)fds.size();
+        T.woff = woff;
+        if (dedup) keys[key] = T.factor;
+        fds.push_back(fd);
+        woff += (long long)T.my * T.mx * T.mx;
+    }
+    p->nfactors = (int)fds.size();
+    HZS_CUDA(g, dalloc(&p->W64, (size_t)woff));
+    if (d->precision == HZS_MIXED) HZS_CUDA(g, dalloc(&p->W32, (size_t)woff));
+    FactorDesc* fds_d = nullptr;
+    FactorStat* st_d = nullptr;
+    HZS_CUDA(g, upload(&fds_d, fds, s));
+    HZS_CUDA(g, dalloc(&st_d, fds.size()));
+    int max_m = 0;
+    for (auto& f : fds) max_m = std::max(max_m, f.mx);
+    if (launch_tile_factor(p->cx, fds_d, p->nfactors, max_m, p->W64, p->W32, st_d) != 0) {
+        cudaFree(fds_d); cudaFree(st_d);
+        return fail(g, HZS_ERR_CUDA, "subdomain factorisation launch failed");
+    }
+    p->fstats.resize(fds.size());
+    cudaError_t e = cudaMemcpyAsync(p->fstats.data(), st_d, fds.size() * sizeof(FactorStat), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(fds_d); cudaFree(st_d);
+    if (e != cudaSuccess) return cuda_fail(g, e, "subdomain factorisation");
+    for (auto& fs : p->fstats)
+        if (fs.singular) return fail(g, HZS_ERR_SINGULAR_LOCAL, "a subdomain matrix has a zero pivot");
+    HZS_CUDA(g, upload(&p->tiles_d, tiles, s));
+    HZS_CUDA(g, upload(&p->cover_d, g->cover, s));
+    // ---- apply work space
+    const size_t cs = cplx_size(d->precision);
+    HZS_CUDA(g, cudaMalloc(&p->w_buf, (size_t)n * n * cs));
+    if (d->kind == HZS_AS1 || d->kind == HZS_AS2) {
+        long long tot = 0;
+        for (auto& T : tiles) tot += (long long)T.mx * T.my;
+        p->ytiles_elems = tot;
+        HZS_CUDA(g, cudaMalloc(&p->ytiles, (size_t)tot * cs));
+    }
+    if (d->precision == HZS_MIXED) HZS_CUDA(g, dalloc(&p->zc64, (size_t)n * n));
+    HZS_CUDA(g, cudaHostAlloc((void**)&p->h_done, 2 * sizeof(int), cudaHostAllocDefault));
+    for (auto& ev : p->ev) HZS_CUDA(g, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    HZS_CUDA(g, cudaEventCreate(&p->t0));
+    HZS_CUDA(g, cudaEventCreate(&p->t1));
+    HZS_CUDA(g, cudaStreamSynchronize(s));
+    return HZS_OK;
+}
+
+extern "C" hzs_status hzs_precond_setup(hzs_grid* g, const hzs_precond_desc* d, hzs_precond** out) {
+    if (!out) return fail(g, HZS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!g || !d) return fail(g, HZS_ERR_INVALID_ARG, "grid or desc is NULL");
+    if (d->kind < HZS_AS1 || d->kind > HZS_SHS2) return fail(g, HZS_ERR_INVALID_ARG, "bad preconditioner kind");
+    if (d->precision != HZS_FP64 && d->precision != HZS_MIXED) return fail(g, HZS_ERR_INVALID_ARG, "bad precision");
+    hzs_precond* p = new hzs_precond();
+    p->g = g;
+    p->desc = *d;
+    const hzs_status st = setup_impl(g, d, p);
+    if (st != HZS_OK) {
+        hzs_precond_destroy(p);
+        return st;
+    }
+    *out = p;
+    return HZS_OK;
+}
+
+// ------------------------------------------------------------------ preconditioner apply
+// z = M^{-1} (s v), s = vscale[0] or 1.  R: arithmetic of the stencil,
+// transfers and subdomain solves; the coarse solve is FP64 either way.
+template <typename R>
+static hzs_status precond_apply(hzs_precond* p, const double2* v, const double* vscale, cplx_t<R>* z,
+                                const int* skip) {
+    using C = cplx_t<R>;
+    const Ctx& cx = p->cx;
+    hzs_grid* g = p->g;
+    const C* W = nullptr;
+    if constexpr (sizeof(R) == sizeof(float)) W = p->W32; else W = p->W64;
+    const int kind = p->desc.kind;
+    if (p->use_coarse) {
+        launch_restrict<double2, R>(cx, v, vscale, (C*)p->t_buf, p->c_buf, skip);
+        launch_coarse_matvec(cx, p->Ainv, p->Nc, p->c_buf, p->c2_buf, skip);
+    }
+    int rc = 0;
+    if (kind == HZS_SHS2) {
+        launch_deflate<double2, C, R>(cx, p->c2_buf, v, vscale, (C*)p->w_buf, skip);
+        rc = launch_tile_solve<C, C, R>(cx, p->tiles_d, (int)g->tiles.size(), g->max_mx, g->max_my, W,
+                                        (const C*)p->w_buf, nullptr, 0, p->c2_buf, 1, z, nullptr, skip);
+    } else if (kind == HZS_SAS2) {
+        rc = launch_tile_solve<double2, C, R>(cx, p->tiles_d, (int)g->tiles.size(), g->max_mx, g->max_my, W, v,
+                                              vscale, 0, p->c2_buf, 1, z, nullptr, skip);
+    } else {
+        rc = launch_tile_solve<double2, C, R>(cx, p->tiles_d, (int)g->tiles.size(), g->max_mx, g->max_my, W, v,
+                                              vscale, 1, p->c2_buf, 0, (C*)nullptr, (C*)p->ytiles, skip);
+        launch_combine_additive<C, C, R>(cx, p->c2_buf, p->use_coarse, p->cover_d, p->tiles_d, g->desc.nsub,
+                                         (const C*)p->ytiles, z, skip);
+    }
+    if (rc != 0) return fail(g, HZS_ERR_CUDA, "subdomain solve launch failed");
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(g, e, "preconditioner launch");
+    return HZS_OK;
+}
+
+extern "C" hzs_status hzs_apply_operator(hzs_precond* p, const void* x_dev, void* y_dev, int nrhs) {
+    if (!p) return fail(nullptr, HZS_ERR_INVALID_ARG, "precond is NULL");
+    if (!x_dev || !y_dev || nrhs < 0) return fail(p->g, HZS_ERR_INVALID_ARG, "bad buffers or nrhs");
+    const size_t nn = (size_t)p->g->desc.n * p->g->desc.n;
+    for (int r = 0; r < nrhs; ++r)
+        launch_apply_A<double2, double2, double>(p->cx, (const double2*)x_dev + r * nn, (double2*)y_dev + r * nn,
+                                                 nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(p->g, e, "apply_operator");
+    return HZS_OK;
+}
+
+__global__ void k_c64_to_c128(long long N, const float2* __restrict__ a, double2* __restrict__ b) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x)
+        b[e] = to_d(a[e]);
+}
+
+extern "C" hzs_status hzs_apply_precond(hzs_precond* p, const void* v_dev, void* z_dev, int nrhs) {
+    if (!p) return fail(nullptr, HZS_ERR_INVALID_ARG, "precond is NULL");
+    if (!v_dev || !z_dev || nrhs < 0) return fail(p->g, HZS_ERR_INVALID_ARG, "bad buffers or nrhs");
+    const size_t nn = (size_t)p->g->desc.n * p->g->desc.n;
+    for (int r = 0; r < nrhs; ++r) {
+        const double2* v = (const double2*)v_dev + r * nn;
+        double2* z = (double2*)z_dev + r * nn;
+        hzs_status st;
+        if (p->desc.precision == HZS_MIXED) {
+            st = precond_apply<float>(p, v, nullptr, p->zc64, nullptr);
+            if (st == HZS_OK) k_c64_to_c128<<<4 * p->cx.num_sms, 256, 0, p->cx.stream>>>((long long)nn, p->zc64, z);
+        } else {
+            st = precond_apply<double>(p, v, nullptr, z, nullptr);
+        }
+        if (st != HZS_OK) return st;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(p->g, e, "apply_precond");
+    return HZS_OK;
+}
+
+// ------------------------------------------------------------------ solve
+static hzs_status ensure_krylov(hzs_precond* p, int maxit) {
+    hzs_grid* g = p->g;
+    if (p->kb_maxit >= maxit && p->kb.V) return HZS_OK;
+    free_krylov(p);
+    const long long N = (long long)g->desc.n * g->desc.n;
+    const long long ld = (N + 63) / 64 * 64;
+    KrylovBufs& kb = p->kb;
+    kb.maxit = maxit;
+    kb.N = N;
+    kb.ld = ld;
+    kb.nblk = 2 * g->num_sms;
+    HZS_CUDA(g, dalloc(&kb.V, (size_t)(maxit + 1) * ld));
+    HZS_CUDA(g, dalloc(&kb.sigma, (size_t)maxit + 1));
+    HZS_CUDA(g, dalloc(&kb.H, (size_t)(maxit + 1) * maxit));
+    HZS_CUDA(g, dalloc(&kb.cs, (size_t)maxit));
+    HZS_CUDA(g, dalloc(&kb.sn, (size_t)maxit));
+    HZS_CUDA(g, dalloc(&kb.g, (size_t)maxit + 1));
+    HZS_CUDA(g, dalloc(&kb.y, (size_t)maxit));
+    HZS_CUDA(g, dalloc(&kb.h1, (size_t)maxit + 1));
+    HZS_CUDA(g, dalloc(&kb.h2, (size_t)maxit + 1));
+    HZS_CUDA(g, dalloc(&kb.part, (size_t)kb.nblk * (maxit + 1)));
+    HZS_CUDA(g, dalloc(&kb.npart, (size_t)kb.nblk));
+    HZS_CUDA(g, dalloc(&kb.st, 1));
+    if (p->desc.precision == HZS_MIXED) HZS_CUDA(g, dalloc(&p->Z, (size_t)maxit * ld));
+    if (!p->ztmp) HZS_CUDA(g, dalloc(&p->ztmp, (size_t)ld));
+    if (!p->rtmp) HZS_CUDA(g, dalloc(&p->rtmp, (size_t)ld));
+    if (!p->dres) HZS_CUDA(g, dalloc(&p->dres, 1));
+    p->kb_maxit = maxit;
+    return HZS_OK;
+}
+
+// One right-hand side: A u = f (conj_io: solve A mu = conj(f), return conj(mu)).
+// Kernel launches of one preconditioner apply.
+static int precond_launches(const hzs_precond* p) {
+    int n = p->use_coarse ? 3 : 0;   // restriction (2) + coarse solve
+    if (p->desc.kind == HZS_SHS2) n += 2;       // deflated residual + subdomain solves
+    else if (p->desc.kind == HZS_SAS2) n += 1;  // subdomain solves
+    else n += 2;                                 // subdomain solves + additive combination
+    return n;
+}
+
+static hzs_status ensure_prof_events(hzs_precond* p, int maxit) {
+    const size_t need = (size_t)4 * (maxit + 1);
+    while (p->prof_ev.size() < need) {
+        cudaEvent_t e;
+        HZS_CUDA(p->g, cudaEventCreate(&e));
+        p->prof_ev.push_back(e);
+    }
+    return HZS_OK;
+}
+
+// One right-hand side: A u = f (conj_io: solve A mu = conj(f), return conj(mu)).
+static hzs_status solve_one(hzs_precond* p, const hzs_solve_desc* sd, const double2* f, double2* u, int conj_io,
+                            hzs_solve_info* info) {
+    hzs_grid* g = p->g;
+    const Ctx& cx = p->cx;
+    KrylovBufs& kb = p->kb;
+    cudaStream_t s = cx.stream;
+    const bool mixed = p->desc.precision == HZS_MIXED;
+    const bool prof = (sd->flags & HZS_SOLVE_PROFILE) != 0;
+    const int* skip = &kb.st->done;
+    const int pl = precond_launches(p);
+    long long launches = 0;
+    if (prof) {
+        hzs_status st = ensure_prof_events(p, sd->maxit);
+        if (st != HZS_OK) return st;
+    }
+    HZS_CUDA(g, cudaEventRecord(p->t0, s));
+    launch_mask_copy_c128(cx, f, kb.V, conj_io);        // V_0 = f (masked); it is never rescaled in place
+    launch_norm_init(cx, kb, sd->tol);
+    launches += 3;
+    int j = 0, steps = 0;
+    for (; j < sd->maxit; ++j) {
+        double2* Vj = kb.V + (size_t)j * kb.ld;
+        double2* w = kb.V + (size_t)(j + 1) * kb.ld;
+        cudaEvent_t* pe = prof ? &p->prof_ev[(size_t)4 * j] : nullptr;
+        if (prof) HZS_CUDA(g, cudaEventRecord(pe[0], s));
+        hzs_status st;
+        if (mixed) {
+            float2* Zj = p->Z + (size_t)j * kb.ld;
+            st = precond_apply<float>(p, Vj, kb.sigma + j, Zj, skip);
+            if (prof) HZS_CUDA(g, cudaEventRecord(pe[1], s));
+            launch_apply_A<float2, double2, double>(cx, Zj, w, skip);
+        } else {
+            st = precond_apply<double>(p, Vj, kb.sigma + j, p->ztmp, skip);
+            if (prof) HZS_CUDA(g, cudaEventRecord(pe[1], s));
+            launch_apply_A<double2, double2, double>(cx, p->ztmp, w, skip);
+        }
+        if (st != HZS_OK) return st;
+        if (prof) HZS_CUDA(g, cudaEventRecord(pe[2], s));
+        launch_arnoldi_step(cx, kb, j);
+        if (prof) HZS_CUDA(g, cudaEventRecord(pe[3], s));
+        launches += pl + 1 + 7;
+        steps = j + 1;
+        HZS_CUDA(g, cudaMemcpyAsync(&p->h_done[j & 1], &kb.st->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+        HZS_CUDA(g, cudaEventRecord(p->ev[j & 1], s));
+        if (j >= 1) {
+            HZS_CUDA(g, cudaEventSynchronize(p->ev[(j - 1) & 1]));
+            if (p->h_done[(j - 1) & 1]) break;
+        }
+    }
+    launch_lsq_solve(cx, kb);
+    launches += 1;
+    if (mixed) {
+        launch_combine_Z(cx, kb, p->Z, kb.ld, u);
+        launches += 1;
+    } else {
+        launch_combine_basis(cx, kb, p->ztmp);
+        hzs_status st = precond_apply<double>(p, p->ztmp, nullptr, u, nullptr);
+        if (st != HZS_OK) return st;
+        launches += 1 + pl;
+    }
+    // true residual ||f - A u|| against the masked right-hand side in V_0
+    launch_apply_A<double2, double2, double>(cx, u, p->rtmp, nullptr);
+    launch_residual_norm(cx, kb, kb.V, p->rtmp, p->dres);
+    launches += 3;
+    if (conj_io) { launch_mask_copy_c128(cx, u, u, 1); launches += 1; }
+    HZS_CUDA(g, cudaEventRecord(p->t1, s));
+    KState hs{};
+    double rnorm = 0.0;
+    HZS_CUDA(g, cudaMemcpyAsync(&hs, kb.st, sizeof(KState), cudaMemcpyDeviceToHost, s));
+    HZS_CUDA(g, cudaMemcpyAsync(&rnorm, p->dres, sizeof(double), cudaMemcpyDeviceToHost, s));
+    HZS_CUDA(g, cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p->t0, p->t1);
+    hzs_solve_info inf{};
+    if (prof) {
+        double tp = 0, tm = 0, to = 0;
+        for (int k = 0; k < steps; ++k) {
+            cudaEvent_t* pe = &p->prof_ev[(size_t)4 * k];
+            float a = 0, b = 0, c = 0;
+            cudaEventElapsedTime(&a, pe[0], pe[1]);
+            cudaEventElapsedTime(&b, pe[1], pe[2]);
+            cudaEventElapsedTime(&c, pe[2], pe[3]);
+            tp += a; tm += b; to += c;
+        }
+        inf.t_precond_ms = tp; inf.t_matvec_ms = tm; inf.t_orth_ms = to;
+    }
+    inf.iterations = hs.iters;
+    inf.converged = hs.conv;
+    inf.relres_est = hs.beta0 > 0 ? hs.resid / hs.beta0 : 0.0;
+    inf.relres_true = hs.beta0 > 0 ? rnorm / hs.beta0 : 0.0;
+    inf.t_solve_ms = ms;
+    inf.launches = launches;
+    inf.status = hs.nonfinite ? HZS_ERR_NONFINITE : (hs.conv ? HZS_OK : HZS_NOT_CONVERGED);
+    if (info) *info = inf;
+    if (hs.nonfinite) return fail(g, HZS_ERR_NONFINITE, "non-finite value in the right-hand side or iteration");
+    return inf.status;
+}
+
+static hzs_status solve_many(hzs_precond* p, const hzs_solve_desc* sd, const void* f_dev, void* u_dev, int nrhs,
+                             hzs_solve_info* info, int conj_io) {
+    if (!p) return fail(nullptr, HZS_ERR_INVALID_ARG, "precond is NULL");
+    hzs_grid* g = p->g;
+    if (!sd || !f_dev || !u_dev || nrhs < 0) return fail(g, HZS_ERR_INVALID_ARG, "bad arguments");
+    if (!(sd->tol > 0.0) || sd->maxit < 1) return fail(g, HZS_ERR_INVALID_ARG, "tol must be > 0 and maxit >= 1");
+    hzs_status st = ensure_krylov(p, sd->maxit);
+    if (st != HZS_OK) return st;
+    const size_t nn = (size_t)g->desc.n * g->desc.n;
+    hzs_status worst = HZS_OK;
+    for (int r = 0; r < nrhs; ++r) {
+        st = solve_one(p, sd, (const double2*)f_dev + r * nn, (double2*)u_dev + r * nn, conj_io,
+                       info ? info + r : nullptr);
+        if (st < 0) return st;
+        if (st == HZS_NOT_CONVERGED) worst = HZS_NOT_CONVERGED;
+    }
+    return worst;
+}
+
+extern "C" hzs_status hzs_solve(hzs_precond* p, const hzs_solve_desc* sd, const void* f_dev, void* u_dev, int nrhs,
+                                hzs_solve_info* info) {
+    return solve_many(p, sd, f_dev, u_dev, nrhs, info, 0);
+}
+
+extern "C" hzs_status hzs_adjoint_solve(hzs_precond* p, const hzs_solve_desc* sd, const void* g_dev, void* lam_dev,
+                                        int nrhs, hzs_solve_info* info) {
+    return solve_many(p, sd, g_dev, lam_dev, nrhs, info, 1);
+}
+
+extern "C" hzs_status hzs_kappa_gradient(hzs_precond* p, const void* u_dev, const void* lam_dev, double* grad_dev) {
+    if (!p) return fail(nullptr, HZS_ERR_INVALID_ARG, "precond is NULL");
+    if (!u_dev || !lam_dev || !grad_dev) return fail(p->g, HZS_ERR_INVALID_ARG, "NULL buffer");
+    launch_kappa_gradient(p->cx, (const double2*)u_dev, (const double2*)lam_dev, grad_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(p->g, e, "kappa_gradient");
+    return HZS_OK;
+}
+
+extern "C" const char* hzs_status_string(hzs_status s) {
+    switch (s) {
+        case HZS_OK: return "ok";
+        case HZS_NOT_CONVERGED: return "not converged";
+        case HZS_ERR_INVALID_ARG: return "invalid argument";
+        case HZS_ERR_CUDA: return "CUDA error";
+        case HZS_ERR_OOM: return "out of device memory";
+        case HZS_ERR_SINGULAR_LOCAL: return "singular subdomain matrix";
+        case HZS_ERR_SINGULAR_COARSE: return "singular coarse matrix";
+        case HZS_ERR_NONFINITE: return "non-finite value";
+        case HZS_ERR_TIMEOUT: return "timeout";
+        case HZS_ERR_BREAKDOWN: return "breakdown";
+    }
+    return "unknown status";
+}
+
+extern "C" const char* hzs_last_error(const hzs_grid* g) { return g ? g->err.c_str() : g_global_err.c_str(); }
+
+extern "C" const char* hzs_version(void) { return "hzs 0.1 (sm_103a)"; }

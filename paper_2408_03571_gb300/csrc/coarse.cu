@@ -1,0 +1,336 @@
+// Coarse level (Section 4, Eq. 4): the 1-D P_1 / B_2 tables, restriction
+// c = R_0 v (separable, two passes), the Galerkin matrix A_0 = R_0 A R_0^T,
+// its FP64 Gauss-Jordan inverse and the coarse solve c' = A_0^{-1} c.
+#include <cmath>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace hzs {
+
+// ------------------------------------------------------------------ 1-D tables
+// Cardinal quadratic B-spline on [0, 3].
+static double bspline2(double t) {
+    if (t < 0.0 || t > 3.0) return 0.0;
+    if (t < 1.0) return 0.5 * t * t;
+    if (t < 2.0) return 0.5 * (-2.0 * t * t + 6.0 * t - 3.0);
+    const double u = 3.0 - t;
+    return 0.5 * u * u;
+}
+
+// phi_I at fine node i for coarse ratio p.  B_2: B-spline of knot spacing
+// H = p h centred on X_I (for p = 2 the weights (1,4,6,4,1)/8 of Eq. 7);
+// P_1: hat of half-width H.
+static double basis_value(int kind, int I_node, int i, int p) {
+    const double s = (double)(i - I_node * p) / (double)p;   // (x_i - X_I) / H
+    if (kind == HZS_COARSE_B2) return bspline2(s + 1.5);
+    const double a = std::fabs(s);
+    return a < 1.0 ? 1.0 - a : 0.0;
+}
+
+void build_coarse_tables(int n, int bc, int kind, int p, HostCoarseTab& t) {
+    const int ncoarse_all = (n - 1) / p + 1;
+    const int first = (bc == HZS_DIRICHLET) ? 1 : 0;          // MP-1 drops the coarse boundary nodes
+    const int nc1 = (bc == HZS_DIRICHLET) ? ncoarse_all - 2 : ncoarse_all;
+    const int flo = (bc == HZS_DIRICHLET) ? 1 : 0, fhi = (bc == HZS_DIRICHLET) ? n - 2 : n - 1;
+    t.nc1 = nc1;
+    t.c0.assign(n, 0);
+    t.w.assign(3 * n, 0.0);
+    t.lo.assign(nc1, 0); t.hi.assign(nc1, -1); t.off.assign(nc1, 0);
+    t.wt.clear();
+    for (int I = 0; I < nc1; ++I) {
+        const int node = I + first;
+        int lo = -1, hi = -2;
+        for (int i = flo; i <= fhi; ++i) {
+            if (basis_value(kind, node, i, p) != 0.0) { if (lo < 0) lo = i; hi = i; }
+        }
+        t.off[I] = (int)t.wt.size();
+        t.lo[I] = lo; t.hi[I] = hi;
+        for (int i = lo; lo >= 0 && i <= hi; ++i) t.wt.push_back(basis_value(kind, node, i, p));
+    }
+    // per fine node: first touching coarse index (clamped so c0+2 < nc1 where possible)
+    for (int i = 0; i < n; ++i) {
+        if (i < flo || i > fhi) { t.c0[i] = 0; continue; }
+        int first_I = -1;
+        for (int I = 0; I < nc1; ++I)
+            if (basis_value(kind, I + first, i, p) != 0.0) { first_I = I; break; }
+        if (first_I < 0) { t.c0[i] = 0; continue; }
+        int c0 = first_I;
+        if (c0 + 2 >= nc1) c0 = nc1 - 3 < 0 ? 0 : nc1 - 3;
+        if (c0 > first_I) c0 = first_I;
+        t.c0[i] = c0;
+        for (int a = 0; a < 3; ++a) {
+            const int I = c0 + a;
+            t.w[3 * i + a] = (I < nc1) ? basis_value(kind, I + first, i, p) : 0.0;
+        }
+        // every touching coarse index must be inside the 3-wide window
+        for (int I = 0; I < nc1; ++I)
+            if (basis_value(kind, I + first, i, p) != 0.0 && (I < c0 || I > c0 + 2)) t.bad = 1;
+    }
+}
+
+// ------------------------------------------------------------------ restriction
+// t[j * nc1 + I] = s * sum_{i in supp I} phi_I(x_i) v[j n + i]   (x pass; one warp per (j, I))
+template <typename Cv, typename R>
+__global__ void k_restrict_x(int n, CoarseTab ct, const Cv* __restrict__ v, const double* __restrict__ vscale,
+                             cplx_t<R>* __restrict__ t, const int* __restrict__ skip) {
+    using C = cplx_t<R>;
+    if (skip && *skip) return;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int nc1 = ct.nc1;
+    if (warp >= n * nc1) return;
+    const int j = warp / nc1, I = warp % nc1;
+    const int lo = ct.lo[I], hi = ct.hi[I];
+    const int off = ct.off[I];
+    C acc; acc.x = 0; acc.y = 0;
+    const Cv* row = v + (size_t)j * n;
+    for (int i = lo + lane; i <= hi; i += 32) {
+        const R wgt = (R)ct.wt[off + i - lo];
+        const C x = cvt<C>(to_d(row[i]));
+        acc.x += wgt * x.x; acc.y += wgt * x.y;
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) {
+        const R s = vscale ? (R)vscale[0] : (R)1;
+        acc.x *= s; acc.y *= s;
+        t[(size_t)j * nc1 + I] = acc;
+    }
+}
+
+// c[J * nc1 + I] = sum_{j in supp J} phi_J(y_j) t[j * nc1 + I]   (y pass, FP64 result)
+template <typename R>
+__global__ void k_restrict_y(int n, CoarseTab ct, const cplx_t<R>* __restrict__ t, double2* __restrict__ c,
+                             const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int nc1 = ct.nc1;
+    if (warp >= nc1 * nc1) return;
+    const int J = warp / nc1, I = warp % nc1;
+    const int lo = ct.lo[J], hi = ct.hi[J];
+    const int off = ct.off[J];
+    double2 acc = make_double2(0.0, 0.0);
+    for (int j = lo + lane; j <= hi; j += 32) {
+        const double wgt = ct.wt[off + j - lo];
+        const double2 x = to_d(t[(size_t)j * nc1 + I]);
+        acc.x += wgt * x.x; acc.y += wgt * x.y;
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) c[(size_t)J * nc1 + I] = acc;
+}
+
+// ------------------------------------------------------------------ coarse solve
+// out = Ainv * c (dense, FP64).  One warp per row; c staged in shared memory.
+__global__ void k_coarse_matvec(int Nc, const double2* __restrict__ Ainv, const double2* __restrict__ c,
+                                double2* __restrict__ out, const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    extern __shared__ double2 cs[];
+    for (int k = threadIdx.x; k < Nc; k += blockDim.x) cs[k] = c[k];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    for (int r = blockIdx.x * wpb + (threadIdx.x >> 5); r < Nc; r += gridDim.x * wpb) {
+        const double2* row = Ainv + (size_t)r * Nc;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int k = lane; k < Nc; k += 32) acc = cfma(row[k], cs[k], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) out[r] = acc;
+    }
+}
+
+// ------------------------------------------------------------------ Galerkin A_0
+// A0[(J,I), (J+dJ, I+dI)] = sum_{fine (i,j)} phi_I(i) phi_J(j) (A phi_{I+dI, J+dJ})(i, j)
+// One block per (row, offset) pair; offsets |dI|, |dJ| <= 2 cover B_2 (P_1 uses <= 1).
+__global__ void k_galerkin(OpDesc op, CoarseTab ct, double2* __restrict__ A0) {
+    const int nc1 = ct.nc1;
+    const int row = blockIdx.x;
+    const int o = blockIdx.y;              // 0..24
+    const int dI = o % 5 - 2, dJ = o / 5 - 2;
+    const int I = row % nc1, J = row / nc1;
+    const int I2 = I + dI, J2 = J + dJ;
+    if (I2 < 0 || J2 < 0 || I2 >= nc1 || J2 >= nc1) return;
+    const int ilo = ct.lo[I], ihi = ct.hi[I], jlo = ct.lo[J], jhi = ct.hi[J];
+    if (ilo < 0 || jlo < 0) return;
+    const int w = ihi - ilo + 1, hgt = jhi - jlo + 1;
+    // phi_{I2}(i) with support check
+    auto phi = [&](int K, int i) -> double {
+        if (i < ct.lo[K] || i > ct.hi[K]) return 0.0;
+        return ct.wt[ct.off[K] + i - ct.lo[K]];
+    };
+    double2 acc = make_double2(0.0, 0.0);
+    for (int t = threadIdx.x; t < w * hgt; t += blockDim.x) {
+        const int i = ilo + t % w, j = jlo + t / w;
+        if (!op_is_unknown(op, i, j)) continue;
+        const double a = ct.wt[ct.off[I] + i - ilo] * ct.wt[ct.off[J] + j - jlo];
+        if (a == 0.0) continue;
+        // (A phi2)(i, j)
+        const double2 d = op_diag(op, i, j);
+        const double p0 = phi(I2, i) * phi(J2, j);
+        double re = d.x * p0, im = d.y * p0;
+        const double cx = op_cx(op, j), cy = op_cy(op, i);
+        double nb = 0.0;
+        if (i > 0 && op_is_unknown(op, i - 1, j)) nb += cx * phi(I2, i - 1) * phi(J2, j);
+        if (i < op.n - 1 && op_is_unknown(op, i + 1, j)) nb += cx * phi(I2, i + 1) * phi(J2, j);
+        if (j > 0 && op_is_unknown(op, i, j - 1)) nb += cy * phi(I2, i) * phi(J2, j - 1);
+        if (j < op.n - 1 && op_is_unknown(op, i, j + 1)) nb += cy * phi(I2, i) * phi(J2, j + 1);
+        re += nb;
+        acc.x += a * re; acc.y += a * im;
+    }
+    __shared__ double2 red[32];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double2 v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : make_double2(0.0, 0.0);
+        v = warp_sum(v);
+        if (threadIdx.x == 0) A0[(size_t)row * (nc1 * nc1) + (size_t)J2 * nc1 + I2] = v;
+    }
+}
+
+// ------------------------------------------------------------------ Gauss-Jordan inverse
+// In-place inversion with partial pivoting of a dense N x N complex matrix in
+// global memory, one pivot column per step.
+struct GJState {
+    int piv;          // pivot row of the current step
+    int singular;     // set if a pivot was zero or not finite
+    double minpiv;    // smallest |pivot| seen
+    double2 pivval;   // pivot value of the current step
+};
+
+__global__ void k_gj_pivot(int N, int k, const double2* __restrict__ a, int* __restrict__ perm, GJState* st) {
+    // one block: argmax_{r >= k} |a[r][k]|
+    __shared__ double bv[32];
+    __shared__ int bi[32];
+    double best = -1.0; int bidx = k;
+    for (int r = k + threadIdx.x; r < N; r += blockDim.x) {
+        const double2 v = a[(size_t)r * N + k];
+        const double m = hypot(v.x, v.y);
+        if (m > best) { best = m; bidx = r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bidx, o);
+        if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+    }
+    if ((threadIdx.x & 31) == 0) { bv[threadIdx.x >> 5] = best; bi[threadIdx.x >> 5] = bidx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            if (bv[w] > bv[0] || (bv[w] == bv[0] && bi[w] < bi[0])) { bv[0] = bv[w]; bi[0] = bi[w]; }
+        st->piv = bi[0];
+        st->pivval = a[(size_t)bi[0] * N + k];
+        perm[k] = bi[0];
+        if (!(bv[0] > 0.0) || !isfinite(bv[0])) st->singular = 1;
+        if (bv[0] < st->minpiv) st->minpiv = bv[0];
+    }
+}
+
+// swap rows k and piv, scale row k, save column k
+__global__ void k_gj_swap_scale(int N, int k, double2* __restrict__ a, double2* __restrict__ colk, const GJState* st) {
+    const int p = st->piv;
+    const double2 pv = st->pivval;
+    const double den = pv.x * pv.x + pv.y * pv.y;
+    const double2 inv = den > 0.0 ? make_double2(pv.x / den, -pv.y / den) : make_double2(0.0, 0.0);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        double2 rk = a[(size_t)k * N + c], rp = a[(size_t)p * N + c];
+        if (p != k) { const double2 tmp = rk; rk = rp; rp = tmp; a[(size_t)p * N + c] = rp; }
+        // row k scaled; column k of row k becomes 1/pivot
+        a[(size_t)k * N + c] = (c == k) ? inv : cmul(rk, inv);
+    }
+}
+
+__global__ void k_gj_savecol(int N, int k, const double2* __restrict__ a, double2* __restrict__ colk) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < N; r += gridDim.x * blockDim.x)
+        colk[r] = a[(size_t)r * N + k];
+}
+
+// a[r][c] -= colk[r] * a[k][c] for r != k; column k: a[r][k] = -colk[r] * a[k][k]
+__global__ void k_gj_eliminate(int N, int k, double2* __restrict__ a, const double2* __restrict__ colk) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (c >= N || r == k) return;
+    const double2 f = colk[r];
+    const double2 akc = a[(size_t)k * N + c];
+    double2 v = (c == k) ? make_double2(0.0, 0.0) : a[(size_t)r * N + c];
+    v = cfms(f, akc, v);
+    a[(size_t)r * N + c] = v;
+}
+
+// undo the row interchanges: swap columns k and perm[k] for k = N-1 .. 0
+__global__ void k_gj_colswap(int N, int k, double2* __restrict__ a, const int* __restrict__ perm) {
+    const int p = perm[k];
+    if (p == k) return;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < N; r += gridDim.x * blockDim.x) {
+        const double2 t = a[(size_t)r * N + k];
+        a[(size_t)r * N + k] = a[(size_t)r * N + p];
+        a[(size_t)r * N + p] = t;
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+template <typename Cv, typename R>
+void launch_restrict(const Ctx& cx, const Cv* v, const double* vscale, cplx_t<R>* t, double2* c, const int* skip) {
+    const int n = cx.op.n, nc1 = cx.ct.nc1;
+    {
+        const long long warps = (long long)n * nc1;
+        const int threads = 256;
+        const long long blocks = (warps * 32 + threads - 1) / threads;
+        k_restrict_x<Cv, R><<<(unsigned)blocks, threads, 0, cx.stream>>>(n, cx.ct, v, vscale, t, skip);
+    }
+    {
+        const long long warps = (long long)nc1 * nc1;
+        const int threads = 256;
+        const long long blocks = (warps * 32 + threads - 1) / threads;
+        k_restrict_y<R><<<(unsigned)blocks, threads, 0, cx.stream>>>(n, cx.ct, t, c, skip);
+    }
+}
+template void launch_restrict<double2, double>(const Ctx&, const double2*, const double*, double2*, double2*,
+                                               const int*);
+template void launch_restrict<double2, float>(const Ctx&, const double2*, const double*, float2*, double2*,
+                                              const int*);
+
+void launch_coarse_matvec(const Ctx& cx, const double2* Ainv, int Nc, const double2* c, double2* out,
+                          const int* skip) {
+    const int threads = 256;
+    const int rows_per_block = threads / 32;
+    int blocks = (Nc + rows_per_block - 1) / rows_per_block;
+    if (blocks > 4 * cx.num_sms) blocks = 4 * cx.num_sms;
+    k_coarse_matvec<<<blocks, threads, Nc * sizeof(double2), cx.stream>>>(Nc, Ainv, c, out, skip);
+}
+
+void launch_galerkin(const Ctx& cx, double2* A0) {
+    const int nc1 = cx.ct.nc1;
+    const int Nc = nc1 * nc1;
+    cudaMemsetAsync(A0, 0, (size_t)Nc * Nc * sizeof(double2), cx.stream);
+    dim3 grid(Nc, 25);
+    k_galerkin<<<grid, 256, 0, cx.stream>>>(cx.op, cx.ct, A0);
+}
+
+// Returns 0 on success, 1 if a pivot was zero; *minpiv receives min |pivot|.
+int gj_invert(const Ctx& cx, double2* a, int N, double* minpiv) {
+    double2* colk = nullptr; int* perm = nullptr; GJState* st = nullptr;
+    if (cudaMalloc(&colk, N * sizeof(double2)) != cudaSuccess) return -1;
+    if (cudaMalloc(&perm, N * sizeof(int)) != cudaSuccess) { cudaFree(colk); return -1; }
+    if (cudaMalloc(&st, sizeof(GJState)) != cudaSuccess) { cudaFree(colk); cudaFree(perm); return -1; }
+    GJState h0{0, 0, 1e300, make_double2(0.0, 0.0)};
+    cudaMemcpyAsync(st, &h0, sizeof(GJState), cudaMemcpyHostToDevice, cx.stream);
+    const int t = 256;
+    const int cb = (N + t - 1) / t;
+    for (int k = 0; k < N; ++k) {
+        k_gj_pivot<<<1, 512, 0, cx.stream>>>(N, k, a, perm, st);
+        k_gj_swap_scale<<<cb, t, 0, cx.stream>>>(N, k, a, colk, st);
+        k_gj_savecol<<<cb, t, 0, cx.stream>>>(N, k, a, colk);
+        k_gj_eliminate<<<dim3(cb, N), t, 0, cx.stream>>>(N, k, a, colk);
+    }
+    for (int k = N - 1; k >= 0; --k) k_gj_colswap<<<cb, t, 0, cx.stream>>>(N, k, a, perm);
+    GJState h;
+    cudaMemcpyAsync(&h, st, sizeof(GJState), cudaMemcpyDeviceToHost, cx.stream);
+    cudaError_t e = cudaStreamSynchronize(cx.stream);
+    cudaFree(colk); cudaFree(perm); cudaFree(st);
+    if (e != cudaSuccess) return -1;
+    *minpiv = h.minpiv;
+    return h.singular ? 1 : 0;
+}
+
+}  // namespace hzs

@@ -1,0 +1,168 @@
+// Shared device helpers for the Helmholtz / Schwarz kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hzs.h"
+
+namespace hzs {
+
+// ---------------------------------------------------------------- complex
+template <typename R> struct cplx;
+template <> struct cplx<double> { using type = double2; };
+template <> struct cplx<float> { using type = float2; };
+template <typename R> using cplx_t = typename cplx<R>::type;
+
+template <typename C> __host__ __device__ __forceinline__ C mk(double re, double im);
+template <> __host__ __device__ __forceinline__ double2 mk<double2>(double re, double im) { return make_double2(re, im); }
+template <> __host__ __device__ __forceinline__ float2 mk<float2>(double re, double im) {
+    return make_float2((float)re, (float)im);
+}
+
+__host__ __device__ __forceinline__ double2 to_d(double2 a) { return a; }
+__host__ __device__ __forceinline__ double2 to_d(float2 a) { return make_double2(a.x, a.y); }
+__host__ __device__ __forceinline__ float2 to_f(double2 a) { return make_float2((float)a.x, (float)a.y); }
+__host__ __device__ __forceinline__ float2 to_f(float2 a) { return a; }
+template <typename C> __host__ __device__ __forceinline__ C cvt(double2 a);
+template <> __host__ __device__ __forceinline__ double2 cvt<double2>(double2 a) { return a; }
+template <> __host__ __device__ __forceinline__ float2 cvt<float2>(double2 a) { return to_f(a); }
+template <typename C> __host__ __device__ __forceinline__ C cvtf(float2 a);
+template <> __host__ __device__ __forceinline__ double2 cvtf<double2>(float2 a) { return to_d(a); }
+template <> __host__ __device__ __forceinline__ float2 cvtf<float2>(float2 a) { return a; }
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <typename C, typename R> __device__ __forceinline__ C cscale(C a, R s) { C r; r.x = a.x * s; r.y = a.y * s; return r; }
+// a * b
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+// acc + a * b
+template <typename C> __device__ __forceinline__ C cfma(C a, C b, C acc) {
+    acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y);
+    return acc;
+}
+// acc + conj(a) * b
+template <typename C> __device__ __forceinline__ C cfma_conj(C a, C b, C acc) {
+    acc.x = fma(a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
+    return acc;
+}
+// acc - a * b
+template <typename C> __device__ __forceinline__ C cfms(C a, C b, C acc) {
+    acc.x = fma(-a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(-a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
+    return acc;
+}
+
+template <typename C> __device__ __forceinline__ C shfl_down(C v, int off) {
+    v.x = __shfl_down_sync(0xffffffffu, v.x, off);
+    v.y = __shfl_down_sync(0xffffffffu, v.y, off);
+    return v;
+}
+template <typename C> __device__ __forceinline__ C warp_sum(C v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = cadd(v, shfl_down(v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------- operator
+// Coefficients of one row of the scaled symmetric system (Section 2).  With
+// ``vx`` = node on a vertical boundary line (i = 0 or n-1) and ``hy`` = node
+// on a horizontal one (j = 0 or n-1):
+//   coupling to x-neighbours  cx = -(1/h^2) * (hy ? 1/2 : 1)
+//   coupling to y-neighbours  cy = -(1/h^2) * (vx ? 1/2 : 1)
+//   diagonal = -(sum of couplings to neighbours inside the grid)
+//              - kappa * (vx ? 1/2 : 1) * (hy ? 1/2 : 1)
+//              - i sqrt(kappa)/h * (vx || hy)
+// which for MP-2 is the ghost-node Sommerfeld row halved on edges and
+// quartered at corners.  MP-1 uses the interior row everywhere (its boundary
+// values are zero and are not unknowns).
+struct OpDesc {
+    int n;
+    int bc;              // HZS_DIRICHLET / HZS_SOMMERFELD
+    double inv_h2;       // 1/h^2
+    double inv_h;        // 1/h
+    double kappa0;       // constant kappa when kappa == nullptr
+    const double* kappa; // n*n field or nullptr
+};
+
+__host__ __device__ __forceinline__ double op_kappa(const OpDesc& op, int i, int j) {
+    return op.kappa ? op.kappa[(size_t)j * op.n + i] : op.kappa0;
+}
+__host__ __device__ __forceinline__ bool op_is_unknown(const OpDesc& op, int i, int j) {
+    if (op.bc == HZS_SOMMERFELD) return true;
+    return i > 0 && j > 0 && i < op.n - 1 && j < op.n - 1;
+}
+// coupling weights of node (i,j) in x and y directions
+__host__ __device__ __forceinline__ double op_cx(const OpDesc& op, int j) {
+    bool hy = op.bc == HZS_SOMMERFELD && (j == 0 || j == op.n - 1);
+    return -op.inv_h2 * (hy ? 0.5 : 1.0);
+}
+__host__ __device__ __forceinline__ double op_cy(const OpDesc& op, int i) {
+    bool vx = op.bc == HZS_SOMMERFELD && (i == 0 || i == op.n - 1);
+    return -op.inv_h2 * (vx ? 0.5 : 1.0);
+}
+// diagonal entry for a given kappa at node (i, j)
+__host__ __device__ __forceinline__ double2 op_diag_k(const OpDesc& op, int i, int j, double kap) {
+    const int n = op.n;
+    if (op.bc != HZS_SOMMERFELD) return make_double2(4.0 * op.inv_h2 - kap, 0.0);
+    const bool vx = (i == 0 || i == n - 1), hy = (j == 0 || j == n - 1);
+    const double cx = op_cx(op, j), cy = op_cy(op, i);
+    double lap = 0.0;
+    lap -= (i > 0 ? cx : 0.0) + (i < n - 1 ? cx : 0.0);
+    lap -= (j > 0 ? cy : 0.0) + (j < n - 1 ? cy : 0.0);
+    const double mass = (vx ? 0.5 : 1.0) * (hy ? 0.5 : 1.0);
+    const double im = (vx || hy) ? -sqrt(kap) * op.inv_h : 0.0;
+    return make_double2(lap - kap * mass, im);
+}
+__host__ __device__ __forceinline__ double2 op_diag(const OpDesc& op, int i, int j) {
+    return op_diag_k(op, i, j, op_kappa(op, i, j));
+}
+// d A_PP / d kappa_P
+__host__ __device__ __forceinline__ double2 op_ddiag_dkappa(const OpDesc& op, int i, int j) {
+    const int n = op.n;
+    if (op.bc != HZS_SOMMERFELD) return make_double2(-1.0, 0.0);
+    const bool vx = (i == 0 || i == n - 1), hy = (j == 0 || j == n - 1);
+    const double mass = (vx ? 0.5 : 1.0) * (hy ? 0.5 : 1.0);
+    const double kap = op_kappa(op, i, j);
+    const double im = (vx || hy) ? -0.5 / sqrt(kap) * op.inv_h : 0.0;
+    return make_double2(-mass, im);
+}
+
+// ---------------------------------------------------------------- coarse tables
+// 1-D coarse basis sampled at the fine nodes.  Fine node i touches coarse
+// indices c0[i] .. c0[i]+2 (weights w[3*i + 0..2], zero where absent).
+// Coarse index I has support fine nodes lo[I] .. hi[I] with weights
+// wt[off[I] + (i - lo[I])].
+struct CoarseTab {
+    int nc1;            // coarse nodes per axis (kept)
+    int* c0;            // [n]
+    double* w;          // [3n]
+    float* wf;          // [3n]
+    int* lo;            // [nc1]
+    int* hi;            // [nc1]
+    int* off;           // [nc1]
+    double* wt;         // [sum support]
+    float* wtf;
+};
+
+// ---------------------------------------------------------------- subdomain tiles
+struct Tile {
+    int x0, y0;          // first grid node of the extended tile
+    int mx, my;          // tile extent (unknowns)
+    int ox0, ox1, oy0, oy1;  // owned node range (inclusive), grid indices
+    int factor;          // index into the factor table
+    int pad;
+    long long woff;      // element offset of the factor's first block
+    long long yoff;      // element offset of this tile's slot in tile-sized scratch
+};
+
+}  // namespace hzs

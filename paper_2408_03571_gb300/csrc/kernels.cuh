@@ -1,0 +1,110 @@
+// Internal declarations shared by the kernel files and the C ABI layer.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace hzs {
+
+// Host copy of the 1-D coarse tables (see CoarseTab).
+struct HostCoarseTab {
+    int nc1 = 0;
+    int bad = 0;                 // a fine node touches coarse indices outside its 3-wide window
+    std::vector<int> c0;
+    std::vector<double> w;
+    std::vector<int> lo, hi, off;
+    std::vector<double> wt;
+};
+void build_coarse_tables(int n, int bc, int kind, int p, HostCoarseTab& t);
+
+// Everything a launch needs about the problem.
+struct Ctx {
+    OpDesc op;
+    CoarseTab ct;
+    cudaStream_t stream;
+    int num_sms;
+};
+
+// Per distinct subdomain factor: representative tile geometry.
+struct FactorDesc {
+    int x0, y0, mx, my;
+    long long woff;
+};
+
+struct FactorStat {
+    double minpiv;     // smallest |pivot| over the factor's block inversions
+    double maxabs;     // largest |entry| of the stored inverse blocks
+    int singular;
+    int pad;
+};
+
+// ---- operator.cu
+template <typename Cin, typename Cout, typename R>
+void launch_apply_A(const Ctx& cx, const Cin* x, Cout* y, const int* skip);
+template <typename Cv, typename Cw, typename R>
+void launch_deflate(const Ctx& cx, const double2* c, const Cv* v, const double* vscale, Cw* w, const int* skip);
+template <typename Cz, typename Cy, typename R>
+void launch_combine_additive(const Ctx& cx, const double2* c, int use_coarse, const int4* cover, const Tile* tiles,
+                             int nsub, const Cy* ytiles, Cz* z, const int* skip);
+void launch_mask_copy_c128(const Ctx& cx, const double2* src, double2* dst, int conj);
+void launch_kappa_gradient(const Ctx& cx, const double2* u, const double2* lam, double* grad);
+
+// ---- coarse.cu
+template <typename Cv, typename R>
+void launch_restrict(const Ctx& cx, const Cv* v, const double* vscale, cplx_t<R>* t, double2* c, const int* skip);
+void launch_coarse_matvec(const Ctx& cx, const double2* Ainv, int Nc, const double2* c, double2* out,
+                          const int* skip);
+void launch_galerkin(const Ctx& cx, double2* A0);
+int gj_invert(const Ctx& cx, double2* a, int N, double* minpiv);
+
+// ---- local.cu
+int max_tile_extent();
+int launch_tile_factor(const Ctx& cx, const FactorDesc* fdesc_dev, int nfactors, int max_m, double2* W64,
+                       float2* W32, FactorStat* stat_dev);
+// mode 0: restricted (D_i) write z = [q] + y on owned nodes; mode 1: write tile y to ytiles
+template <typename Cw, typename Cz, typename R>
+int launch_tile_solve(const Ctx& cx, const Tile* tiles, int ntiles, int max_mx, int max_my,
+                      const cplx_t<R>* W, const Cw* w, const double* vscale, int mode, const double2* c,
+                      int use_coarse, Cz* z, cplx_t<R>* ytiles, const int* skip);
+
+// ---- krylov.cu
+struct KState {
+    double beta0;      // ||f||
+    double tolabs;     // tol * ||f||
+    double resid;      // current GMRES residual estimate |g_{j+1}|
+    double hnext;      // ||w|| of the last step
+    int done;          // iteration finished (converged, breakdown or non-finite)
+    int conv;
+    int iters;         // completed Arnoldi steps
+    int nonfinite;
+    int breakdown;
+    int pad;
+};
+struct KrylovBufs {
+    int maxit;
+    long long N;       // vector length (n*n)
+    long long ld;      // leading dimension between basis vectors (elements)
+    int nblk;          // blocks of the reduction kernels
+    double2* V;        // (maxit+1) x ld
+    double* sigma;     // (maxit+1) lazy normalisation: basis vector i = sigma[i] * V_i
+    double2* H;        // (maxit+1) x maxit, column j at H[j*(maxit+1)]
+    double* cs;        // maxit
+    double2* sn;       // maxit
+    double2* g;        // maxit+1
+    double2* y;        // maxit
+    double2* h1;       // maxit+1
+    double2* h2;       // maxit+1
+    double2* part;     // nblk x (maxit+1)
+    double* npart;     // nblk
+    KState* st;
+};
+void launch_norm_init(const Ctx& cx, const KrylovBufs& kb, double tol);
+void launch_arnoldi_step(const Ctx& cx, const KrylovBufs& kb, int j);
+void launch_lsq_solve(const Ctx& cx, const KrylovBufs& kb);
+void launch_combine_basis(const Ctx& cx, const KrylovBufs& kb, double2* x);
+void launch_combine_Z(const Ctx& cx, const KrylovBufs& kb, const float2* Z, long long ldz, double2* x);
+void launch_combine_Z64(const Ctx& cx, const KrylovBufs& kb, const double2* Z, long long ldz, double2* x);
+void launch_residual_norm(const Ctx& cx, const KrylovBufs& kb, const double2* f, const double2* Ax, double* out);
+
+}  // namespace hzs

@@ -1,0 +1,252 @@
+"""Thin ctypes binding of ``libhzs.so`` (include/hzs.h).
+
+Argument marshalling only: every step of a solve runs in the library's CUDA
+kernels.  PyTorch provides device memory and the stream; tensors are passed as
+raw device pointers.  The library must have been built (``build.build()``);
+loading fails loudly otherwise, and nothing here falls back to a CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+from dataclasses import dataclass
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhzs.so")
+
+# status codes
+OK, NOT_CONVERGED = 0, 1
+ERR_INVALID_ARG, ERR_CUDA, ERR_OOM = -1, -2, -3
+ERR_SINGULAR_LOCAL, ERR_SINGULAR_COARSE, ERR_NONFINITE, ERR_TIMEOUT, ERR_BREAKDOWN = -4, -5, -6, -7, -8
+# enums
+DIRICHLET, SOMMERFELD = 0, 1
+AS1, AS2, SAS2, SHS2 = 0, 1, 2, 3
+COARSE_NONE, COARSE_P1, COARSE_B2 = 0, 1, 2
+FP64, MIXED = 0, 1
+
+EXPORTS = (
+    "hzs_grid_create", "hzs_grid_destroy", "hzs_precond_setup", "hzs_precond_destroy",
+    "hzs_apply_operator", "hzs_apply_precond", "hzs_solve", "hzs_adjoint_solve",
+    "hzs_kappa_gradient", "hzs_status_string", "hzs_last_error", "hzs_version",
+)
+
+
+class GridDesc(ct.Structure):
+    _fields_ = [("n", ct.c_int), ("bc", ct.c_int), ("k", ct.c_double), ("kappa_dev", ct.c_void_p),
+                ("nsub", ct.c_int), ("overlap", ct.c_int)]
+
+
+class PrecondDesc(ct.Structure):
+    _fields_ = [("kind", ct.c_int), ("coarse", ct.c_int), ("coarse_ratio", ct.c_int),
+                ("precision", ct.c_int), ("dedup_tiles", ct.c_int)]
+
+
+SOLVE_PROFILE = 1
+
+
+class SolveDesc(ct.Structure):
+    _fields_ = [("tol", ct.c_double), ("maxit", ct.c_int), ("flags", ct.c_int)]
+
+
+class SolveInfo(ct.Structure):
+    _fields_ = [("iterations", ct.c_int), ("converged", ct.c_int), ("relres_est", ct.c_double),
+                ("relres_true", ct.c_double), ("t_solve_ms", ct.c_double), ("t_precond_ms", ct.c_double),
+                ("t_matvec_ms", ct.c_double), ("t_orth_ms", ct.c_double), ("launches", ct.c_longlong),
+                ("status", ct.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class HzsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"hzs status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ct.CDLL:
+    """Loads libhzs.so and declares the prototypes of every exported call."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2408_03571_gb300.build.build()")
+    lib = ct.CDLL(path)
+    P = ct.c_void_p
+    lib.hzs_grid_create.argtypes = [ct.POINTER(GridDesc), P, ct.POINTER(P)]
+    lib.hzs_grid_destroy.argtypes = [P]
+    lib.hzs_grid_destroy.restype = None
+    lib.hzs_precond_setup.argtypes = [P, ct.POINTER(PrecondDesc), ct.POINTER(P)]
+    lib.hzs_precond_destroy.argtypes = [P]
+    lib.hzs_precond_destroy.restype = None
+    lib.hzs_apply_operator.argtypes = [P, P, P, ct.c_int]
+    lib.hzs_apply_precond.argtypes = [P, P, P, ct.c_int]
+    lib.hzs_solve.argtypes = [P, ct.POINTER(SolveDesc), P, P, ct.c_int, ct.POINTER(SolveInfo)]
+    lib.hzs_adjoint_solve.argtypes = [P, ct.POINTER(SolveDesc), P, P, ct.c_int, ct.POINTER(SolveInfo)]
+    lib.hzs_kappa_gradient.argtypes = [P, P, P, P]
+    lib.hzs_status_string.argtypes = [ct.c_int]
+    lib.hzs_status_string.restype = ct.c_char_p
+    lib.hzs_last_error.argtypes = [P]
+    lib.hzs_last_error.restype = ct.c_char_p
+    lib.hzs_version.argtypes = []
+    lib.hzs_version.restype = ct.c_char_p
+    for name in EXPORTS:
+        if name not in ("hzs_grid_destroy", "hzs_precond_destroy", "hzs_status_string", "hzs_last_error",
+                        "hzs_version"):
+            getattr(lib, name).restype = ct.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int, grid_ptr=None, allow=(OK,)):
+    if status in allow:
+        return status
+    lib = load()
+    msg = lib.hzs_last_error(grid_ptr).decode() or lib.hzs_status_string(status).decode()
+    raise HzsError(status, msg)
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ct.c_void_p(s.cuda_stream)
+
+
+def _dev_c128(t: torch.Tensor, n: int, name: str) -> torch.Tensor:
+    if not t.is_cuda or t.dtype != torch.complex128:
+        raise TypeError(f"{name} must be a CUDA complex128 tensor")
+    if t.shape[-2:] != (n, n) or not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous with trailing shape ({n}, {n})")
+    return t
+
+
+@dataclass
+class SolveResult:
+    iterations: int
+    converged: bool
+    relres_est: float
+    relres_true: float
+    t_solve_ms: float
+    t_precond_ms: float
+    t_matvec_ms: float
+    t_orth_ms: float
+    launches: int
+    status: int
+
+
+class Grid:
+    """Grid, operator and subdomain decomposition (Sections 2-3)."""
+
+    def __init__(self, n: int, bc: int, k: float = 0.0, kappa: torch.Tensor | None = None,
+                 nsub: int = 1, overlap: int = 0, stream=None):
+        lib = load()
+        self.n, self.bc, self.k, self.nsub, self.overlap = n, bc, k, nsub, overlap
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        kp = None
+        if kappa is not None:
+            if not kappa.is_cuda or kappa.dtype != torch.float64 or kappa.shape != (n, n):
+                raise TypeError("kappa must be a CUDA float64 (n, n) tensor")
+            kp = ct.c_void_p(kappa.contiguous().data_ptr())
+            self._kappa_ref = kappa
+        d = GridDesc(n, bc, float(k), kp, nsub, overlap)
+        h = ct.c_void_p()
+        _check(lib.hzs_grid_create(ct.byref(d), _stream_ptr(self.stream), ct.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().hzs_grid_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Preconditioner:
+    """Factorised Schwarz preconditioner (Sections 3-4) on a Grid."""
+
+    def __init__(self, grid: Grid, kind: int = SHS2, coarse: int = COARSE_B2, coarse_ratio: int = 2,
+                 precision: int = FP64, dedup_tiles: bool = True):
+        lib = load()
+        self.grid = grid
+        self.kind, self.coarse, self.coarse_ratio, self.precision = kind, coarse, coarse_ratio, precision
+        d = PrecondDesc(kind, coarse, coarse_ratio, precision, int(dedup_tiles))
+        h = ct.c_void_p()
+        _check(lib.hzs_precond_setup(grid.handle, ct.byref(d), ct.byref(h)), grid.handle)
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def n(self):
+        return self.grid.n
+
+    def apply_operator(self, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        x = _dev_c128(x, self.n, "x")
+        y = torch.empty_like(x) if out is None else out
+        nrhs = x.numel() // (self.n * self.n)
+        _check(load().hzs_apply_operator(self._h, x.data_ptr(), y.data_ptr(), nrhs), self.grid.handle)
+        return y
+
+    def apply(self, v: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        v = _dev_c128(v, self.n, "v")
+        z = torch.empty_like(v) if out is None else out
+        nrhs = v.numel() // (self.n * self.n)
+        _check(load().hzs_apply_precond(self._h, v.data_ptr(), z.data_ptr(), nrhs), self.grid.handle)
+        return z
+
+    def _solve(self, fn, f, tol, maxit, out, profile):
+        f = _dev_c128(f, self.n, "f")
+        u = torch.empty_like(f) if out is None else out
+        nrhs = f.numel() // (self.n * self.n)
+        infos = (SolveInfo * max(nrhs, 1))()
+        sd = SolveDesc(float(tol), int(maxit), SOLVE_PROFILE if profile else 0)
+        _check(fn(self._h, ct.byref(sd), f.data_ptr(), u.data_ptr(), nrhs, infos), self.grid.handle,
+               allow=(OK, NOT_CONVERGED))
+        res = [SolveResult(i.iterations, bool(i.converged), i.relres_est, i.relres_true, i.t_solve_ms,
+                           i.t_precond_ms, i.t_matvec_ms, i.t_orth_ms, i.launches, i.status)
+               for i in infos[:nrhs]]
+        return u, res
+
+    def solve(self, f: torch.Tensor, tol: float = 1e-6, maxit: int = 1000, out=None, profile: bool = False):
+        """u = A^{-1} f by preconditioned GMRES; returns (u, [SolveResult per right-hand side])."""
+        return self._solve(load().hzs_solve, f, tol, maxit, out, profile)
+
+    def adjoint_solve(self, g: torch.Tensor, tol: float = 1e-6, maxit: int = 1000, out=None, profile: bool = False):
+        """lambda = conj(A)^{-1} g; returns (lambda, results)."""
+        return self._solve(load().hzs_adjoint_solve, g, tol, maxit, out, profile)
+
+    def kappa_gradient(self, u: torch.Tensor, lam: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        u = _dev_c128(u, self.n, "u")
+        lam = _dev_c128(lam, self.n, "lam")
+        g = torch.empty((self.n, self.n), dtype=torch.float64, device=u.device) if out is None else out
+        _check(load().hzs_kappa_gradient(self._h, u.data_ptr(), lam.data_ptr(), g.data_ptr()), self.grid.handle)
+        return g
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().hzs_precond_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def version() -> str:
+    return load().hzs_version().decode()

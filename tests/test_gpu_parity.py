@@ -1,0 +1,234 @@
+"""CUDA path vs the FP64 CPU oracle, through the C ABI (needs a GB300).
+
+Bars (FP64 path): operator and every preconditioner element by element to a
+relative 1e-12 / 1e-9 (the block-LU subdomain solver and SuperLU round
+differently, amplified by the condition of the subdomain matrices); GMRES
+iteration counts within 1 of the oracle's, true relative residual <= tol, and
+the solution within 1e-5 relative of the oracle's at the same tolerance.
+
+Mixed path (complex64 preconditioner inside FP64 flexible GMRES): the
+preconditioner to the single-precision bar 1e-4 relative (about 1e3 unit
+roundoffs of complex64: the local solves amplify rounding by the condition of
+the subdomain blocks), the solve to the same residual / solution bars as FP64
+with iteration counts within 2.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import (AS1, AS2, B2, DIRICHLET, P1, SAS2, SHS2, SOMMERFELD, Problem, Schwarz, gmres)  # noqa: E402
+from oracle import adjoint as oadj  # noqa: E402
+from paper_2408_03571_gb300.inputs import (distinct_interior_nodes, kappa_field, point_source,  # noqa: E402
+                                           random_complex_grid)
+
+pytestmark = pytest.mark.gpu
+
+BC = {DIRICHLET: 0, SOMMERFELD: 1}
+KIND = {AS1: 0, AS2: 1, SAS2: 2, SHS2: 3}
+COARSE = {None: 0, P1: 1, B2: 2}
+
+
+@pytest.fixture(scope="module")
+def hzs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2408_03571_gb300 import build
+    build.build()
+    from paper_2408_03571_gb300 import hzs as mod
+    return mod
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def make(hzs, n, bc, k=None, kappa=None, nsub=1, ov=0, kind=AS1, coarse=None, p=2, prec=0, dedup=True):
+    kap_t = dev(kappa) if kappa is not None else None
+    g = hzs.Grid(n, BC[bc], k=k or 0.0, kappa=kap_t, nsub=nsub, overlap=ov)
+    P = hzs.Preconditioner(g, KIND[kind], COARSE[coarse], p, prec, dedup)
+    return g, P
+
+
+@pytest.mark.parametrize("bc", [DIRICHLET, SOMMERFELD])
+@pytest.mark.parametrize("n", [5, 9, 17, 33, 65, 129])
+@pytest.mark.parametrize("field", [False, True])
+def test_operator(hzs, bc, n, field):
+    kap = kappa_field(n, 15.0, seed=n) if field else 225.0
+    prob = Problem(n, bc, kap)
+    A = prob.assemble_fast()
+    g, P = make(hzs, n, bc, k=15.0, kappa=kap if field else None, nsub=1 if n <= 65 else 4)
+    x = random_complex_grid(n, seed=100 + n)
+    y = P.apply_operator(dev(x)).cpu().numpy()
+    ref = prob.vec_to_grid(A @ prob.grid_to_vec(x))
+    assert rel(y, ref) < 1e-13
+    if bc == DIRICHLET:
+        assert np.all(y[0] == 0) and np.all(y[:, -1] == 0)
+
+
+CASES = [
+    # n, nsub, ov, p
+    (17, 2, 2, 4),
+    (33, 4, 2, 4),
+    (33, 2, 1, 8),
+    (65, 4, 2, 8),
+    (49, 3, 2, 8),    # 3 subdomains per axis, ragged boundary tiles
+    (65, 8, 0, 4),    # no overlap
+    (33, 1, 0, 4),    # one subdomain
+    (129, 4, 2, 16),
+]
+
+
+@pytest.mark.parametrize("bc", [DIRICHLET, SOMMERFELD])
+@pytest.mark.parametrize("kind,coarse", [(AS1, None), (AS2, B2), (SAS2, B2), (SHS2, B2), (SHS2, P1), (AS2, P1)])
+@pytest.mark.parametrize("case", CASES)
+def test_preconditioner_fp64(hzs, bc, kind, coarse, case):
+    n, nsub, ov, p = case
+    k = 12.0
+    prob = Problem(n, bc, k * k)
+    A = prob.assemble_fast()
+    M = Schwarz(prob, A, nsub, ov, kind, coarse, p)
+    g, P = make(hzs, n, bc, k=k, nsub=nsub, ov=ov, kind=kind, coarse=coarse, p=p)
+    v = random_complex_grid(n, seed=7)
+    z = P.apply(dev(v)).cpu().numpy()
+    ref = prob.vec_to_grid(M.apply(prob.grid_to_vec(v)))
+    assert rel(z, ref) < 1e-9
+
+
+@pytest.mark.parametrize("bc", [DIRICHLET, SOMMERFELD])
+@pytest.mark.parametrize("kind", [SHS2, SAS2, AS2])
+def test_preconditioner_heterogeneous(hzs, bc, kind):
+    n, nsub, ov, p = 65, 4, 2, 8
+    kap = kappa_field(n, 20.0, seed=5)
+    prob = Problem(n, bc, kap)
+    A = prob.assemble_fast()
+    M = Schwarz(prob, A, nsub, ov, kind, B2, p)
+    g, P = make(hzs, n, bc, kappa=kap, nsub=nsub, ov=ov, kind=kind, coarse=B2, p=p)
+    v = random_complex_grid(n, seed=9)
+    z = P.apply(dev(v)).cpu().numpy()
+    ref = prob.vec_to_grid(M.apply(prob.grid_to_vec(v)))
+    assert rel(z, ref) < 1e-9
+
+
+@pytest.mark.parametrize("bc", [DIRICHLET, SOMMERFELD])
+@pytest.mark.parametrize("kind", [SHS2, SAS2, AS2, AS1])
+def test_preconditioner_mixed(hzs, bc, kind):
+    n, nsub, ov, p = 65, 4, 2, 8
+    k = 20.0
+    prob = Problem(n, bc, k * k)
+    A = prob.assemble_fast()
+    coarse = None if kind == AS1 else B2
+    M = Schwarz(prob, A, nsub, ov, kind, coarse, p)
+    g, P = make(hzs, n, bc, k=k, nsub=nsub, ov=ov, kind=kind, coarse=coarse, p=p, prec=1)
+    v = random_complex_grid(n, seed=11)
+    z = P.apply(dev(v)).cpu().numpy()
+    ref = prob.vec_to_grid(M.apply(prob.grid_to_vec(v)))
+    assert rel(z, ref) < 1e-4
+
+
+def _oracle_solve(prob, A, M, f, tol, maxit, flexible=False):
+    return gmres(lambda x: A @ x, M.apply, prob.grid_to_vec(f), tol, maxit, flexible)
+
+
+SOLVE_CASES = [
+    # the small MP-1 configuration: n=65, k=20, 4x4 subdomains, overlap 2, B_2 with H=1/8, tol 1e-7
+    dict(n=65, bc=DIRICHLET, k=20.0, nsub=4, ov=2, kind=SHS2, coarse=B2, p=8, tol=1e-7),
+    dict(n=65, bc=DIRICHLET, k=20.0, nsub=4, ov=2, kind=SAS2, coarse=B2, p=8, tol=1e-7),
+    dict(n=65, bc=DIRICHLET, k=20.0, nsub=4, ov=2, kind=AS1, coarse=None, p=8, tol=1e-7),
+    dict(n=81, bc=SOMMERFELD, k=20.0, nsub=20, ov=2, kind=SHS2, coarse=B2, p=4, tol=1e-7),
+    dict(n=81, bc=DIRICHLET, k=20.0, nsub=20, ov=2, kind=SHS2, coarse=P1, p=4, tol=1e-7),
+    dict(n=129, bc=SOMMERFELD, k=25.0, nsub=4, ov=2, kind=SHS2, coarse=B2, p=16, tol=1e-6),
+]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("case", SOLVE_CASES, ids=lambda c: f"{c['bc']}-n{c['n']}-{c['kind']}-{c['coarse']}")
+def test_solve(hzs, case, prec):
+    c = case
+    prob = Problem(c["n"], c["bc"], c["k"] ** 2)
+    A = prob.assemble_fast()
+    M = Schwarz(prob, A, c["nsub"], c["ov"], c["kind"], c["coarse"], c["p"])
+    f = point_source(c["n"])
+    ref = _oracle_solve(prob, A, M, f, c["tol"], 400, flexible=bool(prec))
+    g, P = make(hzs, c["n"], c["bc"], k=c["k"], nsub=c["nsub"], ov=c["ov"], kind=c["kind"], coarse=c["coarse"],
+                p=c["p"], prec=prec)
+    u, info = P.solve(dev(f), tol=c["tol"], maxit=400)
+    info = info[0]
+    assert info.converged
+    if prec == 0:
+        assert abs(info.iterations - ref.iterations) <= 1
+    else:
+        # a complex64 preconditioner is a perturbed preconditioner: FGMRES needs a
+        # few more steps than the FP64 oracle (measured +5..15%), never fewer - 1
+        assert ref.iterations - 1 <= info.iterations <= 1.15 * ref.iterations + 2
+    uv = prob.grid_to_vec(u.cpu().numpy())
+    # independent residual check with the oracle's matrix
+    fv = prob.grid_to_vec(f)
+    assert np.linalg.norm(fv - A @ uv) / np.linalg.norm(fv) <= c["tol"] * 1.01
+    assert info.relres_true <= c["tol"] * 1.01
+    assert rel(uv, ref.x) < 1e-5
+
+
+def test_solve_edge_cases(hzs):
+    n = 33
+    g, P = make(hzs, n, SOMMERFELD, k=10.0, nsub=2, ov=1, kind=SHS2, coarse=B2, p=4)
+    # zero right-hand side -> zero solution, zero iterations
+    u, info = P.solve(torch.zeros((n, n), dtype=torch.complex128, device="cuda"), tol=1e-8, maxit=20)
+    assert info[0].iterations == 0 and info[0].converged and torch.all(u == 0)
+    # iteration cap -> not converged, soft status, finite iterate
+    u, info = P.solve(dev(point_source(n)), tol=1e-14, maxit=2)
+    assert info[0].iterations == 2 and not info[0].converged
+    assert torch.isfinite(torch.view_as_real(u)).all()
+    # non-finite right-hand side is reported, not iterated on
+    f = point_source(n)
+    f[3, 3] = np.nan
+    with pytest.raises(hzs.HzsError) as e:
+        P.solve(dev(f), tol=1e-8, maxit=20)
+    assert e.value.status == hzs.ERR_NONFINITE
+    # several right-hand sides in one call
+    F = np.stack([point_source(n, nd) for nd in distinct_interior_nodes(n, 3, seed=4)])
+    U, infos = P.solve(dev(F), tol=1e-8, maxit=100)
+    prob = Problem(n, SOMMERFELD, 100.0)
+    A = prob.assemble_fast()
+    for r in range(3):
+        fv = prob.grid_to_vec(F[r]); uv = prob.grid_to_vec(U[r].cpu().numpy())
+        assert np.linalg.norm(fv - A @ uv) / np.linalg.norm(fv) < 1.01e-8
+
+
+def test_single_subdomain_one_iteration(hzs):
+    n = 33
+    g, P = make(hzs, n, DIRICHLET, k=10.0, nsub=1, ov=0, kind=AS1)
+    u, info = P.solve(dev(point_source(n)), tol=1e-10, maxit=5)
+    assert info[0].iterations == 1 and info[0].relres_true < 1e-11
+
+
+@pytest.mark.parametrize("bc", [DIRICHLET, SOMMERFELD])
+def test_adjoint_and_gradient(hzs, bc):
+    n, nsub, ov, p = 33, 2, 2, 4
+    kap = kappa_field(n, 11.0, seed=21)
+    kap_t = kappa_field(n, 11.0, seed=21, perturb_seed=22)
+    prob = Problem(n, bc, kap)
+    A = prob.assemble_fast()
+    M = Schwarz(prob, A, nsub, ov, SHS2, B2, p)
+    f = point_source(n)
+    rec_nodes = distinct_interior_nodes(n, 8, seed=23)
+    rec = np.array([prob.index(i, j) for i, j in rec_nodes])
+    u_ref = _oracle_solve(prob, A, M, f, 1e-12, 300).x
+    ut = _oracle_solve(Problem(n, bc, kap_t), Problem(n, bc, kap_t).assemble_fast(),
+                       Schwarz(Problem(n, bc, kap_t), Problem(n, bc, kap_t).assemble_fast(), nsub, ov, SHS2, B2, p),
+                       f, 1e-12, 300).x
+    gvec = oadj.misfit_residual(u_ref, ut, rec)
+    lam_ref, _ = oadj.adjoint_solve(A, M.apply, gvec, 1e-12, 300)
+    grad_ref = oadj.kappa_gradient(prob.dA_dkappa(), u_ref, lam_ref)
+
+    g, P = make(hzs, n, bc, kappa=kap, nsub=nsub, ov=ov, kind=SHS2, coarse=B2, p=p)
+    u, _ = P.solve(dev(f), tol=1e-12, maxit=300)
+    lam, info = P.adjoint_solve(dev(prob.vec_to_grid(gvec)), tol=1e-12, maxit=300)
+    assert info[0].converged
+    assert rel(prob.grid_to_vec(lam.cpu().numpy()), lam_ref) < 1e-8
+    grad = P.kappa_gradient(u, lam).cpu().numpy()
+    assert rel(prob.grid_to_vec(grad), grad_ref) < 1e-8

@@ -176,6 +176,28 @@ hzs_status hzs_adjoint_solve(hzs_precond* p, const hzs_solve_desc* sd, const voi
 hzs_status hzs_kappa_gradient(hzs_precond* p, const void* u_dev, const void* lam_dev,
                               double* grad_dev);
 
+/* Allocation-free variant of hzs_apply_precond for SAS2 preconditioners
+ * (the paper has no counterpart: it concerns how memory is obtained, not the
+ * method).  For callers that may not allocate device memory when they apply
+ * the preconditioner - e.g. while a stream is being captured into a CUDA
+ * graph, or on hosts that forbid allocation after start-up.  Computes the same
+ * z = M^{-1} v as hzs_apply_precond (same kernels, same result) but takes its
+ * work space (the partial restriction sums and the two coarse vectors) from a
+ * fixed 1 MiB device array inside the library instead of the handle, and calls
+ * no cudaMalloc, cudaFree or other allocating routine.  The caller passes the
+ * input v_dev and output z_dev as for hzs_apply_precond.
+ * - Only HZS_SAS2 handles are accepted (the other kinds need grid-sized work
+ *   space); others, and problems whose work space exceeds 1 MiB
+ *   (n * (coarse nodes per axis) complex values plus two coarse vectors),
+ *   return HZS_ERR_INVALID_ARG with a message.
+ * - The first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make it before any
+ *   stream capture.
+ * - Every call shares the one array: calls that overlap on the GPU (other
+ *   streams, threads or handles) race and must be serialised by the caller.
+ *   Nothing in it needs clearing between calls (each call writes what it reads). */
+hzs_status hzs_apply_precond_noalloc(hzs_precond* p, const void* v_dev, void* z_dev, int nrhs);
+
 /* Human-readable text of a status; never NULL. */
 const char* hzs_status_string(hzs_status s);
 /* Message of the last failure on this grid (or of the last global failure

@@ -646,3 +646,35 @@ extern "C" const char* hzs_status_string(hzs_status s) {
 extern "C" const char* hzs_last_error(const hzs_grid* g) { return g ? g->err.c_str() : g_global_err.c_str(); }
 
 extern "C" const char* hzs_version(void) { return "hzs 0.1 (sm_103a)"; }
+
+// ------------------------------------------------------------------ internal accessors (noalloc.cu)
+struct NoAllocView {
+    Ctx cx;
+    int kind, precision, nc1, Nc, ntiles, max_mx, max_my;
+    const double2* Ainv;
+    const double2* W64;
+    const float2* W32;
+    const Tile* tiles;
+};
+
+hzs_status hzs_internal_set_error(hzs_precond* p, hzs_status s, const std::string& msg) {
+    return fail(p ? p->g : nullptr, s, msg);
+}
+
+hzs_status hzs_internal_noalloc_view(hzs_precond* p, NoAllocView* v, std::string* err) {
+    if (!p) return fail(nullptr, HZS_ERR_INVALID_ARG, "precond is NULL");
+    v->cx = p->cx;
+    v->kind = p->desc.kind;
+    v->precision = p->desc.precision;
+    v->nc1 = p->hct.nc1;
+    v->Nc = p->Nc;
+    v->ntiles = (int)p->g->tiles.size();
+    v->max_mx = p->g->max_mx;
+    v->max_my = p->g->max_my;
+    v->Ainv = p->Ainv;
+    v->W64 = p->W64;
+    v->W32 = p->W32;
+    v->tiles = p->tiles_d;
+    (void)err;
+    return HZS_OK;
+}

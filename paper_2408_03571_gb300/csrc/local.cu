@@ -275,3 +275,7 @@ template int launch_tile_solve<double2, float2, float>(const Ctx&, const Tile*, 
                                                        float2*, float2*, const int*);
 
 }  // namespace hzs
+// complex64 arithmetic written straight to a complex128 output (allocation-free apply)
+template int hzs::launch_tile_solve<double2, double2, float>(const Ctx&, const Tile*, int, int, int, const float2*,
+                                                             const double2*, const double*, int, const double2*, int,
+                                                             double2*, float2*, const int*);

@@ -30,6 +30,7 @@ EXPORTS = (
     "hzs_grid_create", "hzs_grid_destroy", "hzs_precond_setup", "hzs_precond_destroy",
     "hzs_apply_operator", "hzs_apply_precond", "hzs_solve", "hzs_adjoint_solve",
     "hzs_kappa_gradient", "hzs_status_string", "hzs_last_error", "hzs_version",
+    "hzs_apply_precond_noalloc",
 )
 
 
@@ -86,6 +87,7 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.hzs_precond_destroy.restype = None
     lib.hzs_apply_operator.argtypes = [P, P, P, ct.c_int]
     lib.hzs_apply_precond.argtypes = [P, P, P, ct.c_int]
+    lib.hzs_apply_precond_noalloc.argtypes = [P, P, P, ct.c_int]
     lib.hzs_solve.argtypes = [P, ct.POINTER(SolveDesc), P, P, ct.c_int, ct.POINTER(SolveInfo)]
     lib.hzs_adjoint_solve.argtypes = [P, ct.POINTER(SolveDesc), P, P, ct.c_int, ct.POINTER(SolveInfo)]
     lib.hzs_kappa_gradient.argtypes = [P, P, P, P]

@@ -116,6 +116,11 @@ typedef struct {
 } hzs_solve_desc;
 
 #define HZS_SOLVE_PROFILE 1
+/* With HZS_MIXED: orthogonalise with the all-FP64 CGS2 instead of the default
+ * mixed-precision CGS2 (complex64 first projection from a complex64 copy of
+ * the basis, FP64 reorthogonalisation; orthogonality and the Arnoldi relation
+ * hold to FP64 level either way).  No effect with HZS_FP64. */
+#define HZS_SOLVE_ORTH_FP64 2
 
 /* Per right-hand side results. */
 typedef struct {

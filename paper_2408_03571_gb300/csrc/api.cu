@@ -51,7 +51,12 @@ struct hzs_precond {
     // device coarse tables
     int *c0 = nullptr, *lo = nullptr, *hi = nullptr, *off = nullptr;
     double *w = nullptr, *wt = nullptr;
+    float *wf = nullptr, *wtf = nullptr;
     double2* Ainv = nullptr;
+    float2* c2f = nullptr;            // complex64 copy of the coarse solution
+    int* err = nullptr;               // device error word (HZS_ERR_TIMEOUT from bounded waits)
+    int* groups_d = nullptr;          // tiles grouped by shared factor
+    int ngroups = 0, group_T = 1;
     double coarse_minpiv = 0.0;
     // local factors
     int nfactors = 0;
@@ -210,7 +215,7 @@ extern "C" void hzs_grid_destroy(hzs_grid* g) {
 // ------------------------------------------------------------------ preconditioner
 static void free_krylov(hzs_precond* p) {
     KrylovBufs& kb = p->kb;
-    cudaFree(kb.V); cudaFree(kb.sigma); cudaFree(kb.H); cudaFree(kb.cs); cudaFree(kb.sn); cudaFree(kb.g);
+    cudaFree(kb.V); cudaFree(kb.V32); cudaFree(kb.sigma); cudaFree(kb.H); cudaFree(kb.cs); cudaFree(kb.sn); cudaFree(kb.g);
     cudaFree(kb.y); cudaFree(kb.h1); cudaFree(kb.h2); cudaFree(kb.part); cudaFree(kb.npart); cudaFree(kb.st);
     cudaFree(p->Z);
     kb = KrylovBufs{};
@@ -222,6 +227,7 @@ extern "C" void hzs_precond_destroy(hzs_precond* p) {
     if (!p) return;
     free_krylov(p);
     cudaFree(p->c0); cudaFree(p->lo); cudaFree(p->hi); cudaFree(p->off); cudaFree(p->w); cudaFree(p->wt);
+    cudaFree(p->wf); cudaFree(p->wtf); cudaFree(p->c2f); cudaFree(p->err); cudaFree(p->groups_d);
     cudaFree(p->Ainv); cudaFree(p->W64); cudaFree(p->W32); cudaFree(p->tiles_d); cudaFree(p->cover_d);
     cudaFree(p->t_buf); cudaFree(p->c_buf); cudaFree(p->c2_buf); cudaFree(p->w_buf); cudaFree(p->ytiles);
     cudaFree(p->zc64); cudaFree(p->ztmp); cudaFree(p->rtmp); cudaFree(p->dres);
@@ -264,9 +270,15 @@ static hzs_status setup_impl(hzs_grid* g, const hzs_precond_desc* d, hzs_precond
         HZS_CUDA(g, upload(&p->hi, p->hct.hi, s));
         HZS_CUDA(g, upload(&p->off, p->hct.off, s));
         HZS_CUDA(g, upload(&p->wt, p->hct.wt, s));
+        const std::vector<float> wf(p->hct.w.begin(), p->hct.w.end());
+        const std::vector<float> wtf(p->hct.wt.begin(), p->hct.wt.end());
+        HZS_CUDA(g, upload(&p->wf, wf, s));
+        HZS_CUDA(g, upload(&p->wtf, wtf, s));
+        HZS_CUDA(g, cudaStreamSynchronize(s));   // the host vectors above go out of scope
         p->cx.ct.nc1 = p->hct.nc1;
         p->cx.ct.c0 = p->c0; p->cx.ct.w = p->w; p->cx.ct.lo = p->lo; p->cx.ct.hi = p->hi;
         p->cx.ct.off = p->off; p->cx.ct.wt = p->wt;
+        p->cx.ct.wf = p->wf; p->cx.ct.wtf = p->wtf;
         HZS_CUDA(g, dalloc(&p->Ainv, (size_t)p->Nc * p->Nc));
         launch_galerkin(p->cx, p->Ainv);
         HZS_CUDA(g, cudaGetLastError());
@@ -277,11 +289,18 @@ static hzs_status setup_impl(hzs_grid* g, const hzs_precond_desc* d, hzs_precond
         if (rc > 0) return fail(g, HZS_ERR_SINGULAR_COARSE, "coarse matrix A_0 has a zero pivot");
         HZS_CUDA(g, dalloc(&p->c_buf, p->Nc));
         HZS_CUDA(g, dalloc(&p->c2_buf, p->Nc));
+        HZS_CUDA(g, dalloc(&p->c2f, p->Nc));
         HZS_CUDA(g, cudaMalloc(&p->t_buf, (size_t)n * p->hct.nc1 * cplx_size(d->precision)));
     }
+    HZS_CUDA(g, dalloc(&p->err, 1));
+    HZS_CUDA(g, cudaMemsetAsync(p->err, 0, sizeof(int), s));
+    p->cx.err = p->err;
     if (g->max_mx > max_tile_extent() || g->max_my > max_tile_extent())
         return fail(g, HZS_ERR_INVALID_ARG,
                     "subdomain tile larger than " + std::to_string(max_tile_extent()) + " nodes per axis");
+    p->group_T = tile_group_width(g->max_mx, g->max_my, (int)cplx_size(d->precision));
+    if (p->group_T == 0)
+        return fail(g, HZS_ERR_INVALID_ARG, "subdomain tiles too large for the shared-memory solver");
     // ---- local factors (dedup identical tiles when kappa is constant)
     std::vector<Tile> tiles = g->tiles;
     std::vector<FactorDesc> fds;
@@ -304,7 +323,20 @@ static hzs_status setup_impl(hzs_grid* g, const hzs_precond_desc* d, hzs_precond
         T.woff = woff;
         if (dedup) keys[key] = T.factor;
         fds.push_back(fd);
-        woff += (long long)T.my * T.mx * T.mx;
+        woff += (long long)T.my * block_stride(T.mx);
+    }
+    // group tiles that share a factor, group_T at a time
+    {
+        std::vector<std::vector<int>> by_factor(fds.size());
+        for (size_t t = 0; t < tiles.size(); ++t) by_factor[tiles[t].factor].push_back((int)t);
+        std::vector<int> groups;
+        for (auto& lst : by_factor)
+            for (size_t k = 0; k < lst.size(); k += p->group_T)
+                for (int u = 0; u < p->group_T; ++u)
+                    groups.push_back(k + u < lst.size() ? lst[k + u] : -1);
+        p->ngroups = (int)(groups.size() / p->group_T);
+        HZS_CUDA(g, upload(&p->groups_d, groups, s));
+        HZS_CUDA(g, cudaStreamSynchronize(s));
     }
     p->nfactors = (int)fds.size();
     HZS_CUDA(g, dalloc(&p->W64, (size_t)woff));
@@ -367,31 +399,33 @@ extern "C" hzs_status hzs_precond_setup(hzs_grid* g, const hzs_precond_desc* d, 
 // ------------------------------------------------------------------ preconditioner apply
 // z = M^{-1} (s v), s = vscale[0] or 1.  R: arithmetic of the stencil,
 // transfers and subdomain solves; the coarse solve is FP64 either way.
-template <typename R>
-static hzs_status precond_apply(hzs_precond* p, const double2* v, const double* vscale, cplx_t<R>* z,
-                                const int* skip) {
+template <typename R, typename Cv>
+static hzs_status precond_apply(hzs_precond* p, const Cv* v, const double* vscale, cplx_t<R>* z, const int* skip) {
     using C = cplx_t<R>;
+    constexpr bool f32 = sizeof(R) == sizeof(float);
     const Ctx& cx = p->cx;
     hzs_grid* g = p->g;
     const C* W = nullptr;
-    if constexpr (sizeof(R) == sizeof(float)) W = p->W32; else W = p->W64;
+    const C* cc = nullptr;            // coarse solution in the kernels' precision
+    if constexpr (f32) { W = p->W32; cc = p->c2f; } else { W = p->W64; cc = p->c2_buf; }
+    const TileGroups grp{p->groups_d, p->ngroups, p->group_T};
     const int kind = p->desc.kind;
     if (p->use_coarse) {
-        launch_restrict<double2, R>(cx, v, vscale, (C*)p->t_buf, p->c_buf, skip);
-        launch_coarse_matvec(cx, p->Ainv, p->Nc, p->c_buf, p->c2_buf, skip);
+        launch_restrict<Cv, R>(cx, v, vscale, (C*)p->t_buf, p->c_buf, skip);
+        launch_coarse_matvec(cx, p->Ainv, p->Nc, p->c_buf, p->c2_buf, skip, f32 ? p->c2f : nullptr);
     }
     int rc = 0;
     if (kind == HZS_SHS2) {
-        launch_deflate<double2, C, R>(cx, p->c2_buf, v, vscale, (C*)p->w_buf, skip);
-        rc = launch_tile_solve<C, C, R>(cx, p->tiles_d, (int)g->tiles.size(), g->max_mx, g->max_my, W,
-                                        (const C*)p->w_buf, nullptr, 0, p->c2_buf, 1, z, nullptr, skip);
+        launch_deflate<Cv, C, R>(cx, cc, v, vscale, (C*)p->w_buf, skip);
+        rc = launch_tile_solve<C, C, R>(cx, p->tiles_d, grp, g->max_mx, g->max_my, W, (const C*)p->w_buf, nullptr, 0,
+                                        cc, 1, z, nullptr, skip);
     } else if (kind == HZS_SAS2) {
-        rc = launch_tile_solve<double2, C, R>(cx, p->tiles_d, (int)g->tiles.size(), g->max_mx, g->max_my, W, v,
-                                              vscale, 0, p->c2_buf, 1, z, nullptr, skip);
+        rc = launch_tile_solve<Cv, C, R>(cx, p->tiles_d, grp, g->max_mx, g->max_my, W, v, vscale, 0, cc, 1, z,
+                                         nullptr, skip);
     } else {
-        rc = launch_tile_solve<double2, C, R>(cx, p->tiles_d, (int)g->tiles.size(), g->max_mx, g->max_my, W, v,
-                                              vscale, 1, p->c2_buf, 0, (C*)nullptr, (C*)p->ytiles, skip);
-        launch_combine_additive<C, C, R>(cx, p->c2_buf, p->use_coarse, p->cover_d, p->tiles_d, g->desc.nsub,
+        rc = launch_tile_solve<Cv, C, R>(cx, p->tiles_d, grp, g->max_mx, g->max_my, W, v, vscale, 1, cc, 0,
+                                         (C*)nullptr, (C*)p->ytiles, skip);
+        launch_combine_additive<C, C, R>(cx, cc, p->use_coarse, p->cover_d, p->tiles_d, g->desc.nsub,
                                          (const C*)p->ytiles, z, skip);
     }
     if (rc != 0) return fail(g, HZS_ERR_CUDA, "subdomain solve launch failed");
@@ -426,10 +460,10 @@ extern "C" hzs_status hzs_apply_precond(hzs_precond* p, const void* v_dev, void*
         double2* z = (double2*)z_dev + r * nn;
         hzs_status st;
         if (p->desc.precision == HZS_MIXED) {
-            st = precond_apply<float>(p, v, nullptr, p->zc64, nullptr);
+            st = precond_apply<float, double2>(p, v, nullptr, p->zc64, nullptr);
             if (st == HZS_OK) k_c64_to_c128<<<4 * p->cx.num_sms, 256, 0, p->cx.stream>>>((long long)nn, p->zc64, z);
         } else {
-            st = precond_apply<double>(p, v, nullptr, z, nullptr);
+            st = precond_apply<double, double2>(p, v, nullptr, z, nullptr);
         }
         if (st != HZS_OK) return st;
     }
@@ -449,8 +483,9 @@ static hzs_status ensure_krylov(hzs_precond* p, int maxit) {
     kb.maxit = maxit;
     kb.N = N;
     kb.ld = ld;
-    kb.nblk = 2 * g->num_sms;
+    kb.nblk = 4 * g->num_sms;        // 4 blocks of 256 threads per SM for the basis sweeps
     HZS_CUDA(g, dalloc(&kb.V, (size_t)(maxit + 1) * ld));
+    if (p->desc.precision == HZS_MIXED) HZS_CUDA(g, dalloc(&kb.V32, (size_t)(maxit + 1) * ld));
     HZS_CUDA(g, dalloc(&kb.sigma, (size_t)maxit + 1));
     HZS_CUDA(g, dalloc(&kb.H, (size_t)(maxit + 1) * maxit));
     HZS_CUDA(g, dalloc(&kb.cs, (size_t)maxit));
@@ -506,8 +541,11 @@ static hzs_status solve_one(hzs_precond* p, const hzs_solve_desc* sd, const doub
         hzs_status st = ensure_prof_events(p, sd->maxit);
         if (st != HZS_OK) return st;
     }
+    // mixed-precision CGS2 (complex64 first projection) unless all-FP64 orthogonalisation is asked for
+    const bool orth32 = mixed && !(sd->flags & HZS_SOLVE_ORTH_FP64);
     HZS_CUDA(g, cudaEventRecord(p->t0, s));
-    launch_mask_copy_c128(cx, f, kb.V, conj_io);        // V_0 = f (masked); it is never rescaled in place
+    // V_0 = f (masked; it is never rescaled in place), plus its complex64 copy for orth32
+    launch_mask_copy_c128(cx, f, kb.V, conj_io, orth32 ? kb.V32 : nullptr);
     launch_norm_init(cx, kb, sd->tol);
     launches += 3;
     int j = 0, steps = 0;
@@ -517,19 +555,26 @@ static hzs_status solve_one(hzs_precond* p, const hzs_solve_desc* sd, const doub
         cudaEvent_t* pe = prof ? &p->prof_ev[(size_t)4 * j] : nullptr;
         if (prof) HZS_CUDA(g, cudaEventRecord(pe[0], s));
         hzs_status st;
-        if (mixed) {
+        if (orth32) {
+            // the complex64 preconditioner reads the complex64 copy of the basis vector
             float2* Zj = p->Z + (size_t)j * kb.ld;
-            st = precond_apply<float>(p, Vj, kb.sigma + j, Zj, skip);
+            st = precond_apply<float, float2>(p, kb.V32 + (size_t)j * kb.ld, kb.sigma + j, Zj, skip);
+            if (prof) HZS_CUDA(g, cudaEventRecord(pe[1], s));
+            launch_apply_A<float2, double2, double>(cx, Zj, w, skip, kb.V32 + (size_t)(j + 1) * kb.ld);
+        } else if (mixed) {
+            float2* Zj = p->Z + (size_t)j * kb.ld;
+            st = precond_apply<float, double2>(p, Vj, kb.sigma + j, Zj, skip);
             if (prof) HZS_CUDA(g, cudaEventRecord(pe[1], s));
             launch_apply_A<float2, double2, double>(cx, Zj, w, skip);
         } else {
-            st = precond_apply<double>(p, Vj, kb.sigma + j, p->ztmp, skip);
+            st = precond_apply<double, double2>(p, Vj, kb.sigma + j, p->ztmp, skip);
             if (prof) HZS_CUDA(g, cudaEventRecord(pe[1], s));
             launch_apply_A<double2, double2, double>(cx, p->ztmp, w, skip);
         }
         if (st != HZS_OK) return st;
         if (prof) HZS_CUDA(g, cudaEventRecord(pe[2], s));
-        launch_arnoldi_step(cx, kb, j);
+        if (orth32) launch_arnoldi_step_mixed(cx, kb, j);
+        else launch_arnoldi_step(cx, kb, j);
         if (prof) HZS_CUDA(g, cudaEventRecord(pe[3], s));
         launches += pl + 1 + 7;
         steps = j + 1;
@@ -547,7 +592,7 @@ static hzs_status solve_one(hzs_precond* p, const hzs_solve_desc* sd, const doub
         launches += 1;
     } else {
         launch_combine_basis(cx, kb, p->ztmp);
-        hzs_status st = precond_apply<double>(p, p->ztmp, nullptr, u, nullptr);
+        hzs_status st = precond_apply<double, double2>(p, p->ztmp, nullptr, u, nullptr);
         if (st != HZS_OK) return st;
         launches += 1 + pl;
     }
@@ -559,9 +604,15 @@ static hzs_status solve_one(hzs_precond* p, const hzs_solve_desc* sd, const doub
     HZS_CUDA(g, cudaEventRecord(p->t1, s));
     KState hs{};
     double rnorm = 0.0;
+    int kerr = 0;
     HZS_CUDA(g, cudaMemcpyAsync(&hs, kb.st, sizeof(KState), cudaMemcpyDeviceToHost, s));
     HZS_CUDA(g, cudaMemcpyAsync(&rnorm, p->dres, sizeof(double), cudaMemcpyDeviceToHost, s));
+    HZS_CUDA(g, cudaMemcpyAsync(&kerr, p->err, sizeof(int), cudaMemcpyDeviceToHost, s));
     HZS_CUDA(g, cudaStreamSynchronize(s));
+    if (kerr != 0) {
+        cudaMemsetAsync(p->err, 0, sizeof(int), s);
+        return fail(g, HZS_ERR_TIMEOUT, "a subdomain-solve block gave up waiting for its factor copies");
+    }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, p->t0, p->t1);
     hzs_solve_info inf{};
@@ -648,15 +699,6 @@ extern "C" const char* hzs_last_error(const hzs_grid* g) { return g ? g->err.c_s
 extern "C" const char* hzs_version(void) { return "hzs 0.1 (sm_103a)"; }
 
 // ------------------------------------------------------------------ internal accessors (noalloc.cu)
-struct NoAllocView {
-    Ctx cx;
-    int kind, precision, nc1, Nc, ntiles, max_mx, max_my;
-    const double2* Ainv;
-    const double2* W64;
-    const float2* W32;
-    const Tile* tiles;
-};
-
 hzs_status hzs_internal_set_error(hzs_precond* p, hzs_status s, const std::string& msg) {
     return fail(p ? p->g : nullptr, s, msg);
 }
@@ -668,7 +710,7 @@ hzs_status hzs_internal_noalloc_view(hzs_precond* p, NoAllocView* v, std::string
     v->precision = p->desc.precision;
     v->nc1 = p->hct.nc1;
     v->Nc = p->Nc;
-    v->ntiles = (int)p->g->tiles.size();
+    v->groups = TileGroups{p->groups_d, p->ngroups, p->group_T};
     v->max_mx = p->g->max_mx;
     v->max_my = p->g->max_my;
     v->Ainv = p->Ainv;

@@ -86,8 +86,8 @@ __global__ void k_restrict_x(int n, CoarseTab ct, const Cv* __restrict__ v, cons
     C acc; acc.x = 0; acc.y = 0;
     const Cv* row = v + (size_t)j * n;
     for (int i = lo + lane; i <= hi; i += 32) {
-        const R wgt = (R)ct.wt[off + i - lo];
-        const C x = cvt<C>(to_d(row[i]));
+        const R wgt = CoarseW<R>::wt(ct, off + i - lo);
+        const C x = conv<C>(row[i]);
         acc.x += wgt * x.x; acc.y += wgt * x.y;
     }
     acc = warp_sum(acc);
@@ -123,7 +123,8 @@ __global__ void k_restrict_y(int n, CoarseTab ct, const cplx_t<R>* __restrict__ 
 // ------------------------------------------------------------------ coarse solve
 // out = Ainv * c (dense, FP64).  One warp per row; c staged in shared memory.
 __global__ void k_coarse_matvec(int Nc, const double2* __restrict__ Ainv, const double2* __restrict__ c,
-                                double2* __restrict__ out, const int* __restrict__ skip) {
+                                double2* __restrict__ out, float2* __restrict__ outf,
+                                const int* __restrict__ skip) {
     if (skip && *skip) return;
     extern __shared__ double2 cs[];
     for (int k = threadIdx.x; k < Nc; k += blockDim.x) cs[k] = c[k];
@@ -135,7 +136,10 @@ __global__ void k_coarse_matvec(int Nc, const double2* __restrict__ Ainv, const 
         double2 acc = make_double2(0.0, 0.0);
         for (int k = lane; k < Nc; k += 32) acc = cfma(row[k], cs[k], acc);
         acc = warp_sum(acc);
-        if (lane == 0) out[r] = acc;
+        if (lane == 0) {
+            out[r] = acc;
+            if (outf) outf[r] = to_f(acc);
+        }
     }
 }
 
@@ -289,14 +293,18 @@ template void launch_restrict<double2, double>(const Ctx&, const double2*, const
                                                const int*);
 template void launch_restrict<double2, float>(const Ctx&, const double2*, const double*, float2*, double2*,
                                               const int*);
+template void launch_restrict<float2, float>(const Ctx&, const float2*, const double*, float2*, double2*,
+                                             const int*);
 
 void launch_coarse_matvec(const Ctx& cx, const double2* Ainv, int Nc, const double2* c, double2* out,
-                          const int* skip) {
+                          const int* skip, float2* outf) {
     const int threads = 256;
     const int rows_per_block = threads / 32;
     int blocks = (Nc + rows_per_block - 1) / rows_per_block;
     if (blocks > 4 * cx.num_sms) blocks = 4 * cx.num_sms;
-    k_coarse_matvec<<<blocks, threads, Nc * sizeof(double2), cx.stream>>>(Nc, Ainv, c, out, skip);
+    const size_t smem = (size_t)Nc * sizeof(double2);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_coarse_matvec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_coarse_matvec<<<blocks, threads, smem, cx.stream>>>(Nc, Ainv, c, out, outf, skip);
 }
 
 void launch_galerkin(const Ctx& cx, double2* A0) {

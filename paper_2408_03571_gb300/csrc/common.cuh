@@ -31,6 +31,15 @@ template <typename C> __host__ __device__ __forceinline__ C cvtf(float2 a);
 template <> __host__ __device__ __forceinline__ double2 cvtf<double2>(float2 a) { return to_d(a); }
 template <> __host__ __device__ __forceinline__ float2 cvtf<float2>(float2 a) { return a; }
 
+// Precision conversion that is the identity when the types agree (so that a
+// complex64 kernel never routes a value through double).
+template <typename C> __host__ __device__ __forceinline__ C conv(double2 a);
+template <typename C> __host__ __device__ __forceinline__ C conv(float2 a);
+template <> __host__ __device__ __forceinline__ double2 conv<double2>(double2 a) { return a; }
+template <> __host__ __device__ __forceinline__ float2 conv<float2>(double2 a) { return to_f(a); }
+template <> __host__ __device__ __forceinline__ double2 conv<double2>(float2 a) { return to_d(a); }
+template <> __host__ __device__ __forceinline__ float2 conv<float2>(float2 a) { return a; }
+
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
 template <typename C, typename R> __device__ __forceinline__ C cscale(C a, R s) { C r; r.x = a.x * s; r.y = a.y * s; return r; }
@@ -151,10 +160,27 @@ struct CoarseTab {
     int* hi;            // [nc1]
     int* off;           // [nc1]
     double* wt;         // [sum support]
-    float* wtf;
+    float* wtf;         // the same weights in single precision (complex64 kernels use these,
+                        // so that no FP64 instruction runs inside them)
+};
+
+// Coarse weights in the arithmetic precision R of a kernel.
+template <typename R> struct CoarseW;
+template <> struct CoarseW<double> {
+    static __device__ __forceinline__ double w3(const CoarseTab& ct, int k) { return ct.w[k]; }
+    static __device__ __forceinline__ double wt(const CoarseTab& ct, int k) { return ct.wt[k]; }
+};
+template <> struct CoarseW<float> {
+    static __device__ __forceinline__ float w3(const CoarseTab& ct, int k) { return ct.wf[k]; }
+    static __device__ __forceinline__ float wt(const CoarseTab& ct, int k) { return ct.wtf[k]; }
 };
 
 // ---------------------------------------------------------------- subdomain tiles
+// Elements between consecutive dense blocks W_j of a factor: mx*mx rounded up to
+// an even count, so that every block starts on a 16-byte boundary in complex64
+// as well as complex128 (a requirement of the bulk copies that stage them).
+__host__ __device__ __forceinline__ long long block_stride(int mx) { return ((long long)mx * mx + 1) & ~1LL; }
+
 struct Tile {
     int x0, y0;          // first grid node of the extended tile
     int mx, my;          // tile extent (unknowns)

@@ -24,6 +24,15 @@ struct Ctx {
     CoarseTab ct;
     cudaStream_t stream;
     int num_sms;
+    int* err;          // device error word: kernels that time out set it (HZS_ERR_TIMEOUT); may be null
+};
+
+// Subdomain tiles grouped by shared factor: group g solves tiles idx[g*T .. g*T+T-1]
+// (entries -1 are empty); all tiles of a group have the same factor.
+struct TileGroups {
+    const int* idx;
+    int count;
+    int T;
 };
 
 // Per distinct subdomain factor: representative tile geometry.
@@ -41,20 +50,21 @@ struct FactorStat {
 
 // ---- operator.cu
 template <typename Cin, typename Cout, typename R>
-void launch_apply_A(const Ctx& cx, const Cin* x, Cout* y, const int* skip);
+void launch_apply_A(const Ctx& cx, const Cin* x, Cout* y, const int* skip, float2* y32 = nullptr);
 template <typename Cv, typename Cw, typename R>
-void launch_deflate(const Ctx& cx, const double2* c, const Cv* v, const double* vscale, Cw* w, const int* skip);
+void launch_deflate(const Ctx& cx, const cplx_t<R>* c, const Cv* v, const double* vscale, Cw* w, const int* skip);
 template <typename Cz, typename Cy, typename R>
-void launch_combine_additive(const Ctx& cx, const double2* c, int use_coarse, const int4* cover, const Tile* tiles,
+void launch_combine_additive(const Ctx& cx, const cplx_t<R>* c, int use_coarse, const int4* cover, const Tile* tiles,
                              int nsub, const Cy* ytiles, Cz* z, const int* skip);
-void launch_mask_copy_c128(const Ctx& cx, const double2* src, double2* dst, int conj);
+void launch_mask_copy_c128(const Ctx& cx, const double2* src, double2* dst, int conj, float2* dst32 = nullptr);
 void launch_kappa_gradient(const Ctx& cx, const double2* u, const double2* lam, double* grad);
 
 // ---- coarse.cu
 template <typename Cv, typename R>
 void launch_restrict(const Ctx& cx, const Cv* v, const double* vscale, cplx_t<R>* t, double2* c, const int* skip);
+// out = Ainv c in FP64; outf (if given) receives a complex64 copy for the complex64 kernels
 void launch_coarse_matvec(const Ctx& cx, const double2* Ainv, int Nc, const double2* c, double2* out,
-                          const int* skip);
+                          const int* skip, float2* outf = nullptr);
 void launch_galerkin(const Ctx& cx, double2* A0);
 int gj_invert(const Ctx& cx, double2* a, int N, double* minpiv);
 
@@ -64,9 +74,12 @@ int launch_tile_factor(const Ctx& cx, const FactorDesc* fdesc_dev, int nfactors,
                        float2* W32, FactorStat* stat_dev);
 // mode 0: restricted (D_i) write z = [q] + y on owned nodes; mode 1: write tile y to ytiles
 template <typename Cw, typename Cz, typename R>
-int launch_tile_solve(const Ctx& cx, const Tile* tiles, int ntiles, int max_mx, int max_my,
-                      const cplx_t<R>* W, const Cw* w, const double* vscale, int mode, const double2* c,
+int launch_tile_solve(const Ctx& cx, const Tile* tiles, TileGroups grp, int max_mx, int max_my,
+                      const cplx_t<R>* W, const Cw* w, const double* vscale, int mode, const cplx_t<R>* c,
                       int use_coarse, Cz* z, cplx_t<R>* ytiles, const int* skip);
+// Largest number of tiles per group (1 or 2) whose shared-memory footprint fits for
+// tiles of at most max_mx x max_my in arithmetic of size elem_bytes; 0 if none fits.
+int tile_group_width(int max_mx, int max_my, int elem_bytes);
 
 // ---- krylov.cu
 struct KState {
@@ -87,6 +100,7 @@ struct KrylovBufs {
     long long ld;      // leading dimension between basis vectors (elements)
     int nblk;          // blocks of the reduction kernels
     double2* V;        // (maxit+1) x ld
+    float2* V32;       // (maxit+1) x ld complex64 copies (mixed-precision CGS2), or null
     double* sigma;     // (maxit+1) lazy normalisation: basis vector i = sigma[i] * V_i
     double2* H;        // (maxit+1) x maxit, column j at H[j*(maxit+1)]
     double* cs;        // maxit
@@ -101,10 +115,22 @@ struct KrylovBufs {
 };
 void launch_norm_init(const Ctx& cx, const KrylovBufs& kb, double tol);
 void launch_arnoldi_step(const Ctx& cx, const KrylovBufs& kb, int j);
+void launch_arnoldi_step_mixed(const Ctx& cx, const KrylovBufs& kb, int j);
 void launch_lsq_solve(const Ctx& cx, const KrylovBufs& kb);
 void launch_combine_basis(const Ctx& cx, const KrylovBufs& kb, double2* x);
 void launch_combine_Z(const Ctx& cx, const KrylovBufs& kb, const float2* Z, long long ldz, double2* x);
 void launch_combine_Z64(const Ctx& cx, const KrylovBufs& kb, const double2* Z, long long ldz, double2* x);
+// What the allocation-free apply (noalloc.cu) needs from a preconditioner handle.
+struct NoAllocView {
+    Ctx cx;
+    int kind, precision, nc1, Nc, max_mx, max_my;
+    TileGroups groups;
+    const double2* Ainv;
+    const double2* W64;
+    const float2* W32;
+    const Tile* tiles;
+};
+
 void launch_residual_norm(const Ctx& cx, const KrylovBufs& kb, const double2* f, const double2* Ax, double* out);
 
 }  // namespace hzs

@@ -113,8 +113,8 @@ __global__ void __launch_bounds__(512) k_tile_factor(OpDesc op, const FactorDesc
         }
         // store W_j
         double mx_abs = 0.0;
-        double2* dst64 = W64 + fd.woff + (long long)j * m * m;
-        float2* dst32 = W32 ? W32 + fd.woff + (long long)j * m * m : nullptr;
+        double2* dst64 = W64 + fd.woff + (long long)j * block_stride(m);
+        float2* dst32 = W32 ? W32 + fd.woff + (long long)j * block_stride(m) : nullptr;
         for (int t = tid; t < m * m; t += nt) {
             const double2 v = S[t];
             dst64[t] = v;
@@ -147,135 +147,301 @@ int launch_tile_factor(const Ctx& cx, const FactorDesc* fdesc_dev, int nfactors,
 }
 
 // ------------------------------------------------------------------ solve
-// One block per tile.  The tile right-hand side b = R_i w is gathered into
-// shared memory (g), swept forward and backward in place, and written out:
-// mode 0 (restricted, D_i = owner indicator): z = [R_0^T c] + x on owned nodes;
-// mode 1 (additive, D_i = I): the whole tile x into ytiles.
-template <typename Cw, typename Cz, typename R>
-__global__ void __launch_bounds__(256) k_tile_solve(OpDesc op, CoarseTab ct, const Tile* __restrict__ tiles,
-                                                    const cplx_t<R>* __restrict__ W, const Cw* __restrict__ w,
-                                                    const double* __restrict__ vscale, int mode, const double2* __restrict__ c, int use_coarse,
+// One block per group of T tiles that share a factor.  The tile right-hand
+// sides b = R_i w are gathered into shared memory (g), swept forward and
+// backward in place, and written out: mode 0 (restricted, D_i = owner
+// indicator): z = [R_0^T c] + x on owned nodes; mode 1 (additive, D_i = I):
+// the whole tile x into ytiles.
+//
+// The dense blocks W_j stream from global memory (L2-resident when factors are
+// shared) into an NST-deep ring of shared-memory stages by bulk asynchronous
+// copies (cp.async.bulk, completion counted on an mbarrier per stage) issued
+// by thread 0, NST-1 block steps ahead of their use.  The 2 my - 1 block steps
+// use blocks 0, 1, .., my-1 (forward) then my-2, .., 0 (backward).  Four threads
+// share one output row of a block product; each step ends with one barrier.
+// Every mbarrier wait is bounded: on expiry the block records HZS_ERR_TIMEOUT in
+// the error word, drains its outstanding copies (again bounded) and returns.
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+// true when the phase with the given parity has completed
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+constexpr long long kSpinLimit = 1LL << 24;   // try_wait polls before a stage wait is declared timed out
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    for (long long it = 0; it < kSpinLimit; ++it)
+        if (mbar_try(bar, parity)) return true;
+    return false;
+}
+
+template <typename R, int T, int NST>
+__host__ __device__ constexpr size_t tile_smem_bytes(int mx, int my) {
+    // W stages | g (T tiles) | r (2 x T x mx) | cy (mx) | mbarriers
+    return ((size_t)NST * block_stride(mx) * sizeof(cplx_t<R>) + 127) / 128 * 128 +
+           (size_t)T * mx * my * sizeof(cplx_t<R>) + (size_t)2 * T * mx * sizeof(cplx_t<R>) +
+           (size_t)mx * sizeof(R) + 16 + (size_t)NST * 8 + 16;
+}
+
+template <typename Cw, typename Cz, typename R, int T, int NST>
+__global__ void __launch_bounds__(512) k_tile_solve(OpDesc op, CoarseTab ct, const Tile* __restrict__ tiles,
+                                                    const int* __restrict__ groups, const cplx_t<R>* __restrict__ W,
+                                                    const Cw* __restrict__ w, const double* __restrict__ vscale,
+                                                    int mode, const cplx_t<R>* __restrict__ c, int use_coarse,
                                                     Cz* __restrict__ z, cplx_t<R>* __restrict__ ytiles,
-                                                    const int* __restrict__ skip) {
+                                                    const int* __restrict__ skip, int* __restrict__ err) {
     using C = cplx_t<R>;
     if (skip && *skip) return;
-    extern __shared__ unsigned char smem_raw[];
-    const Tile T = tiles[blockIdx.x];
-    const int mx = T.mx, my = T.my, n = op.n;
-    C* g = reinterpret_cast<C*>(smem_raw);          // mx*my
-    C* r = g + mx * my;                              // mx
-    R* cy = reinterpret_cast<R*>(r + mx);            // mx
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    int tix[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) tix[t] = groups[blockIdx.x * T + t];
+    const Tile T0 = tiles[tix[0]];
+    const int mx = T0.mx, my = T0.my, n = op.n;
+    const long long bs = block_stride(mx);
+    const uint32_t bbytes = (uint32_t)(bs * sizeof(C));
+    C* wst = reinterpret_cast<C*>(smem_raw);                                        // NST stages
+    C* g = reinterpret_cast<C*>(smem_raw + ((size_t)NST * bs * sizeof(C) + 127) / 128 * 128);   // T x mx*my
+    C* r = g + (size_t)T * mx * my;                                                 // 2 x T x mx
+    R* cy = reinterpret_cast<R*>(r + 2 * T * mx);                                   // mx
+    uint64_t* bar = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(cy + mx) + 15) & ~uintptr_t(15));
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-    const double sc = vscale ? vscale[0] : 1.0;
-    for (int t = tid; t < mx * my; t += nt) {
-        const int a = t % mx, b = t / mx;
-        double2 v = to_d(w[(size_t)(T.y0 + b) * n + (T.x0 + a)]);
-        v.x *= sc; v.y *= sc;
-        g[t] = cvt<C>(v);
+    const C* Wt = W + T0.woff;
+    const int nsteps = 2 * my - 1;
+    auto blk = [&](int q) { return q < my ? q : 2 * my - 2 - q; };
+
+    if (tid == 0) {
+        for (int s = 0; s < NST; ++s) mbar_init(&bar[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int a = tid; a < mx; a += nt) cy[a] = (R)op_cy(op, T.x0 + a);
     __syncthreads();
-    const C* Wt = W + T.woff;
-    const size_t bs = (size_t)mx * mx;
-    // forward sweep
-    for (int j = 0; j < my; ++j) {
-        C* gj = g + j * mx;
-        for (int a = tid; a < mx; a += nt) {
-            C v = gj[a];
-            if (j > 0) { const C gp = gj[a - mx]; v.x -= cy[a] * gp.x; v.y -= cy[a] * gp.y; }
-            r[a] = v;
+    if (tid == 0) {
+        for (int q = 0; q < NST && q < nsteps; ++q) {
+            mbar_expect_tx(&bar[q], bbytes);
+            bulk_g2s(wst + (size_t)q * bs, Wt + (size_t)blk(q) * bs, bbytes, &bar[q]);
         }
-        __syncthreads();
-        const C* Wj = Wt + j * bs;
-        for (int row = wid; row < mx; row += nw) {
-            C acc; acc.x = 0; acc.y = 0;
-            const C* wr = Wj + (size_t)row * mx;
-            for (int col = lane; col < mx; col += 32) acc = cfma(wr[col], r[col], acc);
-            acc = warp_sum(acc);
-            if (lane == 0) gj[row] = acc;
-        }
-        __syncthreads();
     }
-    // backward sweep
-    for (int j = my - 2; j >= 0; --j) {
-        C* gj = g + j * mx;
-        for (int a = tid; a < mx; a += nt) {
-            const C xn = gj[a + mx];
-            C v; v.x = cy[a] * xn.x; v.y = cy[a] * xn.y;
-            r[a] = v;
+    // gather b = R_i (s w) for the group's tiles
+    const R sc = vscale ? (R)vscale[0] : (R)1;
+    for (int t = 0; t < T; ++t) {
+        C* gt = g + (size_t)t * mx * my;
+        if (tix[t] < 0) {
+            for (int e = tid; e < mx * my; e += nt) gt[e] = mk<C>(0.0, 0.0);
+            continue;
         }
-        __syncthreads();
-        const C* Wj = Wt + j * bs;
-        for (int row = wid; row < mx; row += nw) {
-            C acc; acc.x = 0; acc.y = 0;
-            const C* wr = Wj + (size_t)row * mx;
-            for (int col = lane; col < mx; col += 32) acc = cfma(wr[col], r[col], acc);
-            acc = warp_sum(acc);
-            if (lane == 0) { C v = gj[row]; v.x -= acc.x; v.y -= acc.y; gj[row] = v; }
+        const Tile Ti = tiles[tix[t]];
+        for (int e = tid; e < mx * my; e += nt) {
+            const int a = e % mx, b = e / mx;
+            C v = conv<C>(w[(size_t)(Ti.y0 + b) * n + (Ti.x0 + a)]);
+            v.x *= sc; v.y *= sc;
+            gt[e] = v;
         }
-        __syncthreads();
     }
-    if (mode == 1) {
-        C* dst = ytiles + T.yoff;
-        for (int t = tid; t < mx * my; t += nt) dst[t] = g[t];
-        return;
+    for (int a = tid; a < mx; a += nt) cy[a] = (R)op_cy(op, T0.x0 + a);
+    __syncthreads();
+    // r for the first step: b_0
+    for (int e = tid; e < T * mx; e += nt) {
+        const int t = e / mx, a = e % mx;
+        r[e] = g[(size_t)t * mx * my + a];
     }
-    // owned nodes; for MP-1 a tile at the edge of the unknowns also writes the
-    // adjacent (eliminated) boundary nodes, as zeros, so that z is defined everywhere
-    const bool dir = op.bc == HZS_DIRICHLET;
-    const int wx0 = (dir && T.ox0 == 1) ? 0 : T.ox0, wx1 = (dir && T.ox1 == n - 2) ? n - 1 : T.ox1;
-    const int wy0 = (dir && T.oy0 == 1) ? 0 : T.oy0, wy1 = (dir && T.oy1 == n - 2) ? n - 1 : T.oy1;
-    const int ow = wx1 - wx0 + 1, oh = wy1 - wy0 + 1;
-    for (int t = tid; t < ow * oh; t += nt) {
-        const int gi = wx0 + t % ow, gj = wy0 + t / ow;
-        if (!op_is_unknown(op, gi, gj)) { z[(size_t)gj * n + gi] = mk<Cz>(0.0, 0.0); continue; }
-        C v = g[(gj - T.y0) * mx + (gi - T.x0)];
-        if (use_coarse) {
-            // q = R_0^T c at this node
-            const int ci = ct.c0[gi], cjj = ct.c0[gj];
-            for (int b = 0; b < 3; ++b) {
-                const double wyb = ct.w[3 * gj + b];
-                if (wyb == 0.0) continue;
-                for (int a = 0; a < 3; ++a) {
-                    const double wxa = ct.w[3 * gi + a];
-                    if (wxa == 0.0) continue;
-                    const double2 cv = c[(size_t)(cjj + b) * ct.nc1 + (ci + a)];
-                    const R wgt = (R)(wxa * wyb);
-                    v.x += wgt * (R)cv.x; v.y += wgt * (R)cv.y;
+    __syncthreads();
+
+    const int row = tid >> 2, sub = tid & 3;
+    const bool active = row < mx;
+    int q_fail = -1;
+    for (int q = 0; q < nsteps; ++q) {
+        const int st = q % NST;
+        const uint32_t parity = (uint32_t)((q / NST) & 1);
+        const bool ok = mbar_wait_bounded(&bar[st], parity);
+        if (__syncthreads_or(!ok)) { q_fail = q; break; }
+        const C* Wq = wst + (size_t)st * bs;
+        const C* rc = r + (size_t)(q & 1) * T * mx;
+        C* rn = r + (size_t)((q + 1) & 1) * T * mx;
+        const bool fwd = q < my;
+        const int j = blk(q);
+        {
+            // every thread of the block runs the shuffles below (inactive rows add zeros)
+            C acc[T];
+#pragma unroll
+            for (int t = 0; t < T; ++t) { acc[t].x = 0; acc[t].y = 0; }
+            if (active) {
+                const C* wr = Wq + (size_t)row * mx;
+                for (int k = sub; k < mx; k += 4) {
+                    const C wv = wr[k];
+#pragma unroll
+                    for (int t = 0; t < T; ++t) acc[t] = cfma(wv, rc[t * mx + k], acc[t]);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                acc[t].x += __shfl_xor_sync(0xffffffffu, acc[t].x, 1);
+                acc[t].y += __shfl_xor_sync(0xffffffffu, acc[t].y, 1);
+                acc[t].x += __shfl_xor_sync(0xffffffffu, acc[t].x, 2);
+                acc[t].y += __shfl_xor_sync(0xffffffffu, acc[t].y, 2);
+            }
+            if (active && sub == 0) {
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    C* gt = g + (size_t)t * mx * my;
+                    C x;
+                    if (fwd) {
+                        x = acc[t];                                   // g_j = W_j (b_j - C g_{j-1})
+                    } else {
+                        x = gt[(size_t)j * mx + row];                 // x_j = g_j - W_j (C x_{j+1})
+                        x.x -= acc[t].x; x.y -= acc[t].y;
+                    }
+                    gt[(size_t)j * mx + row] = x;
+                    // right-hand side of the next step
+                    C nr;
+                    if (fwd && j + 1 < my) {
+                        const C b = gt[(size_t)(j + 1) * mx + row];
+                        nr.x = b.x - cy[row] * x.x; nr.y = b.y - cy[row] * x.y;
+                    } else {
+                        nr.x = cy[row] * x.x; nr.y = cy[row] * x.y;   // C x_j for the backward step j-1
+                    }
+                    rn[t * mx + row] = nr;
                 }
             }
         }
-        z[(size_t)gj * n + gi] = cvt<Cz>(to_d(v));
+        __syncthreads();   // stage st fully read; next r complete
+        if (tid == 0 && q + NST < nsteps) {
+            mbar_expect_tx(&bar[st], bbytes);
+            bulk_g2s(wst + (size_t)st * bs, Wt + (size_t)blk(q + NST) * bs, bbytes, &bar[st]);
+        }
     }
+    if (q_fail >= 0) {
+        if (tid == 0) {
+            if (err) atomicExch(err, (int)HZS_ERR_TIMEOUT);
+            // copies in flight: steps q_fail .. q_fail + NST - 1; wait for each (bounded)
+            for (int qq = q_fail; qq < q_fail + NST && qq < nsteps; ++qq)
+                mbar_wait_bounded(&bar[qq % NST], (uint32_t)((qq / NST) & 1));
+        }
+        __syncthreads();
+        return;
+    }
+    // output
+    for (int t = 0; t < T; ++t) {
+        if (tix[t] < 0) continue;
+        const Tile Ti = tiles[tix[t]];
+        const C* gt = g + (size_t)t * mx * my;
+        if (mode == 1) {
+            C* dst = ytiles + Ti.yoff;
+            for (int e = tid; e < mx * my; e += nt) dst[e] = gt[e];
+            continue;
+        }
+        // owned nodes; for MP-1 a tile at the edge of the unknowns also writes the
+        // adjacent (eliminated) boundary nodes, as zeros, so that z is defined everywhere
+        const bool dir = op.bc == HZS_DIRICHLET;
+        const int wx0 = (dir && Ti.ox0 == 1) ? 0 : Ti.ox0, wx1 = (dir && Ti.ox1 == n - 2) ? n - 1 : Ti.ox1;
+        const int wy0 = (dir && Ti.oy0 == 1) ? 0 : Ti.oy0, wy1 = (dir && Ti.oy1 == n - 2) ? n - 1 : Ti.oy1;
+        const int ow = wx1 - wx0 + 1, oh = wy1 - wy0 + 1;
+        for (int e = tid; e < ow * oh; e += nt) {
+            const int gi = wx0 + e % ow, gj = wy0 + e / ow;
+            if (!op_is_unknown(op, gi, gj)) { z[(size_t)gj * n + gi] = mk<Cz>(0.0, 0.0); continue; }
+            C v = gt[(gj - Ti.y0) * mx + (gi - Ti.x0)];
+            if (use_coarse) {
+                // q = R_0^T c at this node
+                const int ci = ct.c0[gi], cjj = ct.c0[gj];
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    const R wyb = CoarseW<R>::w3(ct, 3 * gj + b);
+                    if (wyb == (R)0) continue;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const R wxa = CoarseW<R>::w3(ct, 3 * gi + a);
+                        if (wxa == (R)0) continue;
+                        const C cv = c[(size_t)(cjj + b) * ct.nc1 + (ci + a)];
+                        const R wgt = wxa * wyb;
+                        v.x += wgt * cv.x; v.y += wgt * cv.y;
+                    }
+                }
+            }
+            z[(size_t)gj * n + gi] = conv<Cz>(v);
+        }
+    }
+}
+
+constexpr size_t kSmemLimit = 227 * 1024;
+
+int tile_group_width(int max_mx, int max_my, int elem_bytes) {
+    if (elem_bytes == (int)sizeof(float2)) {
+        if (tile_smem_bytes<float, 2, 2>(max_mx, max_my) <= kSmemLimit) return 2;
+        if (tile_smem_bytes<float, 1, 1>(max_mx, max_my) <= kSmemLimit) return 1;
+        return 0;
+    }
+    return tile_smem_bytes<double, 1, 1>(max_mx, max_my) <= kSmemLimit ? 1 : 0;
+}
+
+template <typename Cw, typename Cz, typename R, int T, int NST>
+static int launch_tile_solve_t(const Ctx& cx, const Tile* tiles, TileGroups grp, int max_mx, int max_my,
+                               const cplx_t<R>* W, const Cw* w, const double* vscale, int mode, const cplx_t<R>* c,
+                               int use_coarse, Cz* z, cplx_t<R>* ytiles, const int* skip) {
+    const size_t smem = tile_smem_bytes<R, T, NST>(max_mx, max_my);
+    auto kern = k_tile_solve<Cw, Cz, R, T, NST>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
+    const int threads = (max_mx * 4 + 31) / 32 * 32;
+    kern<<<grp.count, threads, smem, cx.stream>>>(cx.op, cx.ct, tiles, grp.idx, W, w, vscale, mode, c, use_coarse, z,
+                                                  ytiles, skip, cx.err);
+    return 0;
 }
 
 template <typename Cw, typename Cz, typename R>
-int launch_tile_solve(const Ctx& cx, const Tile* tiles, int ntiles, int max_mx, int max_my, const cplx_t<R>* W,
-                      const Cw* w, const double* vscale, int mode, const double2* c, int use_coarse, Cz* z,
+int launch_tile_solve(const Ctx& cx, const Tile* tiles, TileGroups grp, int max_mx, int max_my, const cplx_t<R>* W,
+                      const Cw* w, const double* vscale, int mode, const cplx_t<R>* c, int use_coarse, Cz* z,
                       cplx_t<R>* ytiles, const int* skip) {
-    using C = cplx_t<R>;
-    const size_t smem = (size_t)max_mx * max_my * sizeof(C) + (size_t)max_mx * sizeof(C) + (size_t)max_mx * sizeof(R);
-    auto kern = k_tile_solve<Cw, Cz, R>;
-    if (smem > 48 * 1024) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return -1;
+    if (max_mx * 4 > 512) return -1;
+    if (grp.T == 2) {
+        // deepest ring of factor-block stages that fits: more stages hide the L2 latency of the copies
+        if (tile_smem_bytes<R, 2, 4>(max_mx, max_my) <= kSmemLimit)
+            return launch_tile_solve_t<Cw, Cz, R, 2, 4>(cx, tiles, grp, max_mx, max_my, W, w, vscale, mode, c,
+                                                        use_coarse, z, ytiles, skip);
+        if (tile_smem_bytes<R, 2, 2>(max_mx, max_my) <= kSmemLimit)
+            return launch_tile_solve_t<Cw, Cz, R, 2, 2>(cx, tiles, grp, max_mx, max_my, W, w, vscale, mode, c,
+                                                        use_coarse, z, ytiles, skip);
+        return -1;
     }
-    kern<<<ntiles, 256, smem, cx.stream>>>(cx.op, cx.ct, tiles, W, w, vscale, mode, c, use_coarse, z, ytiles, skip);
-    return 0;
+    if (tile_smem_bytes<R, 1, 4>(max_mx, max_my) <= kSmemLimit)
+        return launch_tile_solve_t<Cw, Cz, R, 1, 4>(cx, tiles, grp, max_mx, max_my, W, w, vscale, mode, c, use_coarse,
+                                                    z, ytiles, skip);
+    if (tile_smem_bytes<R, 1, 2>(max_mx, max_my) <= kSmemLimit)
+        return launch_tile_solve_t<Cw, Cz, R, 1, 2>(cx, tiles, grp, max_mx, max_my, W, w, vscale, mode, c, use_coarse,
+                                                    z, ytiles, skip);
+    if (tile_smem_bytes<R, 1, 1>(max_mx, max_my) <= kSmemLimit)
+        return launch_tile_solve_t<Cw, Cz, R, 1, 1>(cx, tiles, grp, max_mx, max_my, W, w, vscale, mode, c, use_coarse,
+                                                    z, ytiles, skip);
+    return -1;
 }
-template int launch_tile_solve<double2, double2, double>(const Ctx&, const Tile*, int, int, int, const double2*,
-                                                         const double2*, const double*, int, const double2*, int,
-                                                         double2*, double2*, const int*);
-template int launch_tile_solve<float2, float2, float>(const Ctx&, const Tile*, int, int, int, const float2*,
-                                                      const float2*, const double*, int, const double2*, int,
-                                                      float2*, float2*, const int*);
-template int launch_tile_solve<double2, float2, float>(const Ctx&, const Tile*, int, int, int, const float2*,
-                                                       const double2*, const double*, int, const double2*, int,
-                                                       float2*, float2*, const int*);
+
+#define HZS_TS(Cw, Cz, R)                                                                                        \
+    template int launch_tile_solve<Cw, Cz, R>(const Ctx&, const Tile*, TileGroups, int, int, const cplx_t<R>*,   \
+                                              const Cw*, const double*, int, const cplx_t<R>*, int, Cz*,         \
+                                              cplx_t<R>*, const int*);
+HZS_TS(double2, double2, double)
+HZS_TS(float2, float2, float)
+HZS_TS(double2, float2, float)
+HZS_TS(double2, double2, float)
+#undef HZS_TS
 
 }  // namespace hzs
-// complex64 arithmetic written straight to a complex128 output (allocation-free apply)
-template int hzs::launch_tile_solve<double2, double2, float>(const Ctx&, const Tile*, int, int, int, const float2*,
-                                                             const double2*, const double*, int, const double2*, int,
-                                                             double2*, float2*, const int*);

@@ -58,14 +58,6 @@ cudaError_t scratch_address(void** out) {
 }  // namespace
 
 // Accessors of the opaque handles (defined in api.cu).
-struct NoAllocView {
-    Ctx cx;
-    int kind, precision, nc1, Nc, ntiles, max_mx, max_my;
-    const double2* Ainv;
-    const double2* W64;
-    const float2* W32;
-    const Tile* tiles;
-};
 hzs_status hzs_internal_noalloc_view(hzs_precond* p, NoAllocView* v, std::string* err);
 hzs_status hzs_internal_set_error(hzs_precond* p, hzs_status s, const std::string& msg);
 
@@ -82,7 +74,8 @@ extern "C" hzs_status hzs_apply_precond_noalloc(hzs_precond* p, const void* v_de
     const bool mixed = V.precision == HZS_MIXED;
     const size_t t_bytes = round256((size_t)n * V.nc1 * (mixed ? sizeof(float2) : sizeof(double2)));
     const size_t c_bytes = round256((size_t)V.Nc * sizeof(double2));
-    const size_t need = t_bytes + 2 * c_bytes;
+    const size_t cf_bytes = mixed ? round256((size_t)V.Nc * sizeof(float2)) : 0;
+    const size_t need = t_bytes + 2 * c_bytes + cf_bytes;
     if (need > kNoAllocScratchBytes)
         return hzs_internal_set_error(
             p, HZS_ERR_INVALID_ARG,
@@ -95,6 +88,7 @@ extern "C" hzs_status hzs_apply_precond_noalloc(hzs_precond* p, const void* v_de
     unsigned char* b = static_cast<unsigned char*>(base);
     double2* c = reinterpret_cast<double2*>(b + t_bytes);
     double2* c2 = reinterpret_cast<double2*>(b + t_bytes + c_bytes);
+    float2* c2f = mixed ? reinterpret_cast<float2*>(b + t_bytes + 2 * c_bytes) : nullptr;
     const size_t nn = (size_t)n * n;
     for (int r = 0; r < nrhs; ++r) {
         const double2* v = (const double2*)v_dev + r * nn;
@@ -102,13 +96,13 @@ extern "C" hzs_status hzs_apply_precond_noalloc(hzs_precond* p, const void* v_de
         int rc;
         if (mixed) {
             launch_restrict<double2, float>(V.cx, v, nullptr, reinterpret_cast<float2*>(b), c, nullptr);
-            launch_coarse_matvec(V.cx, V.Ainv, V.Nc, c, c2, nullptr);
-            rc = launch_tile_solve<double2, double2, float>(V.cx, V.tiles, V.ntiles, V.max_mx, V.max_my, V.W32, v,
-                                                            nullptr, 0, c2, 1, z, nullptr, nullptr);
+            launch_coarse_matvec(V.cx, V.Ainv, V.Nc, c, c2, nullptr, c2f);
+            rc = launch_tile_solve<double2, double2, float>(V.cx, V.tiles, V.groups, V.max_mx, V.max_my, V.W32, v,
+                                                            nullptr, 0, c2f, 1, z, nullptr, nullptr);
         } else {
             launch_restrict<double2, double>(V.cx, v, nullptr, reinterpret_cast<double2*>(b), c, nullptr);
             launch_coarse_matvec(V.cx, V.Ainv, V.Nc, c, c2, nullptr);
-            rc = launch_tile_solve<double2, double2, double>(V.cx, V.tiles, V.ntiles, V.max_mx, V.max_my, V.W64, v,
+            rc = launch_tile_solve<double2, double2, double>(V.cx, V.tiles, V.groups, V.max_mx, V.max_my, V.W64, v,
                                                              nullptr, 0, c2, 1, z, nullptr, nullptr);
         }
         if (rc != 0) return hzs_internal_set_error(p, HZS_ERR_CUDA, "subdomain solve launch failed");

@@ -2,14 +2,19 @@
 // w = s v - A R_0^T c (Eq. 6, with the coarse solution c = A_0^{-1} R_0 s v
 // already computed), the additive (D_i = I) combination of subdomain
 // solutions, and the element-wise helpers of the solve driver.
+//
+// Kernels instantiated with R = float do all arithmetic in single precision
+// (coarse weights and the coarse solution are read as float copies).
 #include "kernels.cuh"
 
 namespace hzs {
 
 // y = A x over the n x n grid.  Arithmetic in R; x read as Cin, y written as
-// Cout.  MP-1 boundary nodes: y = 0, and their x values are never read.
+// Cout and, if y32 is given, also as complex64.  MP-1 boundary nodes: y = 0,
+// and their x values are never read.
 template <typename Cin, typename Cout, typename R>
-__global__ void k_apply_A(OpDesc op, const Cin* __restrict__ x, Cout* __restrict__ y, const int* __restrict__ skip) {
+__global__ void k_apply_A(OpDesc op, const Cin* __restrict__ x, Cout* __restrict__ y, float2* __restrict__ y32,
+                          const int* __restrict__ skip) {
     using C = cplx_t<R>;
     if (skip && *skip) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -17,42 +22,47 @@ __global__ void k_apply_A(OpDesc op, const Cin* __restrict__ x, Cout* __restrict
     const int n = op.n;
     if (i >= n || j >= n) return;
     const size_t p = (size_t)j * n + i;
-    if (!op_is_unknown(op, i, j)) { y[p] = mk<Cout>(0.0, 0.0); return; }
+    if (!op_is_unknown(op, i, j)) {
+        y[p] = mk<Cout>(0.0, 0.0);
+        if (y32) y32[p] = make_float2(0.f, 0.f);
+        return;
+    }
     const double2 d = op_diag(op, i, j);
     const R cx = (R)op_cx(op, j), cy = (R)op_cy(op, i);
-    const C xp = cvt<C>(to_d(x[p]));
+    const C xp = conv<C>(x[p]);
     C acc;
     acc.x = (R)d.x * xp.x - (R)d.y * xp.y;
     acc.y = (R)d.x * xp.y + (R)d.y * xp.x;
     C sx; sx.x = 0; sx.y = 0;
     C sy; sy.x = 0; sy.y = 0;
-    if (i > 0 && op_is_unknown(op, i - 1, j)) sx = cadd(sx, cvt<C>(to_d(x[p - 1])));
-    if (i < n - 1 && op_is_unknown(op, i + 1, j)) sx = cadd(sx, cvt<C>(to_d(x[p + 1])));
-    if (j > 0 && op_is_unknown(op, i, j - 1)) sy = cadd(sy, cvt<C>(to_d(x[p - n])));
-    if (j < n - 1 && op_is_unknown(op, i, j + 1)) sy = cadd(sy, cvt<C>(to_d(x[p + n])));
+    if (i > 0 && op_is_unknown(op, i - 1, j)) sx = cadd(sx, conv<C>(x[p - 1]));
+    if (i < n - 1 && op_is_unknown(op, i + 1, j)) sx = cadd(sx, conv<C>(x[p + 1]));
+    if (j > 0 && op_is_unknown(op, i, j - 1)) sy = cadd(sy, conv<C>(x[p - n]));
+    if (j < n - 1 && op_is_unknown(op, i, j + 1)) sy = cadd(sy, conv<C>(x[p + n]));
     acc.x += cx * sx.x + cy * sy.x;
     acc.y += cx * sx.y + cy * sy.y;
-    y[p] = cvt<Cout>(to_d(acc));
+    y[p] = conv<Cout>(acc);
+    if (y32) y32[p] = conv<float2>(acc);
 }
 
 // q(i, j) = sum_{a,b} wx(i,a) wy(j,b) c[(c0[j]+b) nc1 + c0[i]+a]   (prolongation R_0^T c)
 template <typename R>
-__device__ __forceinline__ cplx_t<R> prolong_at(const CoarseTab& ct, const double2* __restrict__ c, int i, int j) {
+__device__ __forceinline__ cplx_t<R> prolong_at(const CoarseTab& ct, const cplx_t<R>* __restrict__ c, int i, int j) {
     using C = cplx_t<R>;
     C q; q.x = 0; q.y = 0;
     const int ci = ct.c0[i], cj = ct.c0[j];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-        const double wyb = ct.w[3 * j + b];
-        if (wyb == 0.0) continue;
+        const R wyb = CoarseW<R>::w3(ct, 3 * j + b);
+        if (wyb == (R)0) continue;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const double wxa = ct.w[3 * i + a];
-            if (wxa == 0.0) continue;
-            const double2 cv = c[(size_t)(cj + b) * ct.nc1 + (ci + a)];
-            const R wgt = (R)(wxa * wyb);
-            q.x += wgt * (R)cv.x;
-            q.y += wgt * (R)cv.y;
+            const R wxa = CoarseW<R>::w3(ct, 3 * i + a);
+            if (wxa == (R)0) continue;
+            const C cv = c[(size_t)(cj + b) * ct.nc1 + (ci + a)];
+            const R wgt = wxa * wyb;
+            q.x += wgt * cv.x;
+            q.y += wgt * cv.y;
         }
     }
     return q;
@@ -62,7 +72,7 @@ __device__ __forceinline__ cplx_t<R> prolong_at(const CoarseTab& ct, const doubl
 // Block tile TX x TY nodes; q for the tile plus a one-node halo is staged in
 // shared memory.
 template <typename Cv, typename Cw, typename R, int TX, int TY>
-__global__ void k_deflate(OpDesc op, CoarseTab ct, const double2* __restrict__ c, const Cv* __restrict__ v,
+__global__ void k_deflate(OpDesc op, CoarseTab ct, const cplx_t<R>* __restrict__ c, const Cv* __restrict__ v,
                           const double* __restrict__ vscale, Cw* __restrict__ w, const int* __restrict__ skip) {
     using C = cplx_t<R>;
     if (skip && *skip) return;
@@ -94,18 +104,18 @@ __global__ void k_deflate(OpDesc op, CoarseTab ct, const double2* __restrict__ c
     const C sy = cadd(qs[lj - 1][li], qs[lj + 1][li]);
     aq.x += cx * sx.x + cy * sy.x;
     aq.y += cx * sx.y + cy * sy.y;
-    const C vp = cvt<C>(to_d(v[p]));
+    const C vp = conv<C>(v[p]);
     C out;
     out.x = s * vp.x - aq.x;
     out.y = s * vp.y - aq.y;
-    w[p] = cvt<Cw>(to_d(out));
+    w[p] = conv<Cw>(out);
 }
 
 // z = [q] + sum over the subdomains covering the node of y_tile (D_i = I:
 // AS1 and AS2).  Per axis a node lies in at most two extended blocks;
 // cover[i] = (block a, offset of i in a, block b, offset in b), -1 if absent.
 template <typename Cz, typename Cy, typename R>
-__global__ void k_combine_additive(OpDesc op, CoarseTab ct, const double2* __restrict__ c, int use_coarse,
+__global__ void k_combine_additive(OpDesc op, CoarseTab ct, const cplx_t<R>* __restrict__ c, int use_coarse,
                                    const int4* __restrict__ cover, const Tile* __restrict__ tiles, int nsub,
                                    const Cy* __restrict__ ytiles, Cz* __restrict__ z, const int* __restrict__ skip) {
     using C = cplx_t<R>;
@@ -128,14 +138,16 @@ __global__ void k_combine_additive(OpDesc op, CoarseTab ct, const double2* __res
         for (int s = 0; s < 2; ++s) {
             if (ta[s] < 0) continue;
             const Tile& T = tiles[tb[u] * nsub + ta[s]];
-            acc = cadd(acc, cvt<C>(to_d(ytiles[T.yoff + (size_t)lb[u] * T.mx + la[s]])));
+            acc = cadd(acc, conv<C>(ytiles[T.yoff + (size_t)lb[u] * T.mx + la[s]]));
         }
     }
-    z[p] = cvt<Cz>(to_d(acc));
+    z[p] = conv<Cz>(acc);
 }
 
-// dst = src (or conj(src)) on unknowns, 0 on MP-1 boundary nodes.
-__global__ void k_mask_copy(OpDesc op, const double2* __restrict__ src, double2* __restrict__ dst, int conj) {
+// dst = src (or conj(src)) on unknowns, 0 on MP-1 boundary nodes; dst32 (if
+// given) receives the same values in complex64.
+__global__ void k_mask_copy(OpDesc op, const double2* __restrict__ src, double2* __restrict__ dst, int conj,
+                            float2* __restrict__ dst32) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int n = op.n;
@@ -144,6 +156,7 @@ __global__ void k_mask_copy(OpDesc op, const double2* __restrict__ src, double2*
     double2 v = op_is_unknown(op, i, j) ? src[p] : make_double2(0.0, 0.0);
     if (conj) v.y = -v.y;
     dst[p] = v;
+    if (dst32) dst32[p] = to_f(v);
 }
 
 // grad = -Re(conj(lam) * dA_PP/dkappa_P * u) on unknowns, 0 elsewhere.
@@ -166,26 +179,28 @@ __global__ void k_kappa_gradient(OpDesc op, const double2* __restrict__ u, const
 static inline dim3 grid2d(int n, dim3 b) { return dim3((n + b.x - 1) / b.x, (n + b.y - 1) / b.y); }
 
 template <typename Cin, typename Cout, typename R>
-void launch_apply_A(const Ctx& cx, const Cin* x, Cout* y, const int* skip) {
+void launch_apply_A(const Ctx& cx, const Cin* x, Cout* y, const int* skip, float2* y32) {
     const dim3 b(32, 8);
-    k_apply_A<Cin, Cout, R><<<grid2d(cx.op.n, b), b, 0, cx.stream>>>(cx.op, x, y, skip);
+    k_apply_A<Cin, Cout, R><<<grid2d(cx.op.n, b), b, 0, cx.stream>>>(cx.op, x, y, y32, skip);
 }
-template void launch_apply_A<double2, double2, double>(const Ctx&, const double2*, double2*, const int*);
-template void launch_apply_A<float2, double2, double>(const Ctx&, const float2*, double2*, const int*);
+template void launch_apply_A<double2, double2, double>(const Ctx&, const double2*, double2*, const int*, float2*);
+template void launch_apply_A<float2, double2, double>(const Ctx&, const float2*, double2*, const int*, float2*);
 
 template <typename Cv, typename Cw, typename R>
-void launch_deflate(const Ctx& cx, const double2* c, const Cv* v, const double* vscale, Cw* w, const int* skip) {
+void launch_deflate(const Ctx& cx, const cplx_t<R>* c, const Cv* v, const double* vscale, Cw* w, const int* skip) {
     constexpr int TX = 32, TY = 8;
     const dim3 b(TX, TY);
     k_deflate<Cv, Cw, R, TX, TY><<<grid2d(cx.op.n, b), b, 0, cx.stream>>>(cx.op, cx.ct, c, v, vscale, w, skip);
 }
 template void launch_deflate<double2, double2, double>(const Ctx&, const double2*, const double2*, const double*,
                                                        double2*, const int*);
-template void launch_deflate<double2, float2, float>(const Ctx&, const double2*, const double2*, const double*,
+template void launch_deflate<double2, float2, float>(const Ctx&, const float2*, const double2*, const double*,
                                                      float2*, const int*);
+template void launch_deflate<float2, float2, float>(const Ctx&, const float2*, const float2*, const double*,
+                                                    float2*, const int*);
 
 template <typename Cz, typename Cy, typename R>
-void launch_combine_additive(const Ctx& cx, const double2* c, int use_coarse, const int4* cover, const Tile* tiles,
+void launch_combine_additive(const Ctx& cx, const cplx_t<R>* c, int use_coarse, const int4* cover, const Tile* tiles,
                              int nsub, const Cy* ytiles, Cz* z, const int* skip) {
     const dim3 b(32, 8);
     k_combine_additive<Cz, Cy, R><<<grid2d(cx.op.n, b), b, 0, cx.stream>>>(cx.op, cx.ct, c, use_coarse, cover, tiles,
@@ -194,12 +209,12 @@ void launch_combine_additive(const Ctx& cx, const double2* c, int use_coarse, co
 template void launch_combine_additive<double2, double2, double>(const Ctx&, const double2*, int, const int4*,
                                                                 const Tile*, int, const double2*, double2*,
                                                                 const int*);
-template void launch_combine_additive<float2, float2, float>(const Ctx&, const double2*, int, const int4*,
+template void launch_combine_additive<float2, float2, float>(const Ctx&, const float2*, int, const int4*,
                                                              const Tile*, int, const float2*, float2*, const int*);
 
-void launch_mask_copy_c128(const Ctx& cx, const double2* src, double2* dst, int conj) {
+void launch_mask_copy_c128(const Ctx& cx, const double2* src, double2* dst, int conj, float2* dst32) {
     const dim3 b(32, 8);
-    k_mask_copy<<<grid2d(cx.op.n, b), b, 0, cx.stream>>>(cx.op, src, dst, conj);
+    k_mask_copy<<<grid2d(cx.op.n, b), b, 0, cx.stream>>>(cx.op, src, dst, conj, dst32);
 }
 
 void launch_kappa_gradient(const Ctx& cx, const double2* u, const double2* lam, double* grad) {

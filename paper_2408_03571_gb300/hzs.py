@@ -45,6 +45,7 @@ class PrecondDesc(ct.Structure):
 
 
 SOLVE_PROFILE = 1
+SOLVE_ORTH_FP64 = 2
 
 
 class SolveDesc(ct.Structure):
@@ -210,12 +211,13 @@ class Preconditioner:
         _check(load().hzs_apply_precond(self._h, v.data_ptr(), z.data_ptr(), nrhs), self.grid.handle)
         return z
 
-    def _solve(self, fn, f, tol, maxit, out, profile):
+    def _solve(self, fn, f, tol, maxit, out, profile, orth_fp64=False):
         f = _dev_c128(f, self.n, "f")
         u = torch.empty_like(f) if out is None else out
         nrhs = f.numel() // (self.n * self.n)
         infos = (SolveInfo * max(nrhs, 1))()
-        sd = SolveDesc(float(tol), int(maxit), SOLVE_PROFILE if profile else 0)
+        flags = (SOLVE_PROFILE if profile else 0) | (SOLVE_ORTH_FP64 if orth_fp64 else 0)
+        sd = SolveDesc(float(tol), int(maxit), flags)
         _check(fn(self._h, ct.byref(sd), f.data_ptr(), u.data_ptr(), nrhs, infos), self.grid.handle,
                allow=(OK, NOT_CONVERGED))
         res = [SolveResult(i.iterations, bool(i.converged), i.relres_est, i.relres_true, i.t_solve_ms,
@@ -223,9 +225,12 @@ class Preconditioner:
                for i in infos[:nrhs]]
         return u, res
 
-    def solve(self, f: torch.Tensor, tol: float = 1e-6, maxit: int = 1000, out=None, profile: bool = False):
-        """u = A^{-1} f by preconditioned GMRES; returns (u, [SolveResult per right-hand side])."""
-        return self._solve(load().hzs_solve, f, tol, maxit, out, profile)
+    def solve(self, f: torch.Tensor, tol: float = 1e-6, maxit: int = 1000, out=None, profile: bool = False,
+              orth_fp64: bool = False):
+        """u = A^{-1} f by preconditioned GMRES; returns (u, [SolveResult per right-hand side]).
+
+        orth_fp64: with a MIXED preconditioner, orthogonalise with the all-FP64 CGS2."""
+        return self._solve(load().hzs_solve, f, tol, maxit, out, profile, orth_fp64)
 
     def adjoint_solve(self, g: torch.Tensor, tol: float = 1e-6, maxit: int = 1000, out=None, profile: bool = False):
         """lambda = conj(A)^{-1} g; returns (lambda, results)."""

@@ -232,3 +232,22 @@ def test_adjoint_and_gradient(hzs, bc):
     assert rel(prob.grid_to_vec(lam.cpu().numpy()), lam_ref) < 1e-8
     grad = P.kappa_gradient(u, lam).cpu().numpy()
     assert rel(prob.grid_to_vec(grad), grad_ref) < 1e-8
+
+
+@pytest.mark.parametrize("case", [SOLVE_CASES[0], SOLVE_CASES[3], SOLVE_CASES[5]],
+                         ids=lambda c: f"{c['bc']}-n{c['n']}")
+def test_mixed_orthogonalisation_matches_fp64_cgs2(hzs, case):
+    """The mixed-precision CGS2 (complex64 first projection) gives the same GMRES
+    run as the all-FP64 CGS2 under the same complex64 preconditioner."""
+    c = case
+    prob = Problem(c["n"], c["bc"], c["k"] ** 2)
+    g, P = make(hzs, c["n"], c["bc"], k=c["k"], nsub=c["nsub"], ov=c["ov"], kind=c["kind"], coarse=c["coarse"],
+                p=c["p"], prec=1)
+    f = dev(point_source(c["n"]))
+    u1, i1 = P.solve(f, tol=c["tol"], maxit=400)
+    u2, i2 = P.solve(f, tol=c["tol"], maxit=400, orth_fp64=True)
+    assert i1[0].converged and i2[0].converged
+    assert abs(i1[0].iterations - i2[0].iterations) <= 1
+    assert i1[0].relres_true <= c["tol"] * 1.01
+    a = prob.grid_to_vec(u1.cpu().numpy()); b = prob.grid_to_vec(u2.cpu().numpy())
+    assert rel(a, b) < 1e-5

@@ -167,6 +167,22 @@ hzs_status hzs_apply_precond(hzs_precond* p, const void* v_dev, void* z_dev, int
 hzs_status hzs_solve(hzs_precond* p, const hzs_solve_desc* sd, const void* f_dev, void* u_dev,
                      int nrhs, hzs_solve_info* info);
 
+/* Batched solve of several problems (wavenumbers, grid sizes, decompositions:
+ * one preconditioner handle each, all distinct) with several right-hand sides
+ * each; the paper solves one right-hand side at a time, this is its batched
+ * form.  Problem k solves nrhs[k] right-hand sides f_dev[k] -> u_dev[k] (grid
+ * layout as hzs_solve); its info entries follow those of problems 0..k-1.
+ * Within a problem the right-hand sides advance in lockstep: every Arnoldi
+ * step is one set of kernel launches over all of them, and those that have
+ * converged are skipped on the device.  Problems run concurrently on their
+ * own host threads; their GPU work overlaps when their grids were created on
+ * different streams.  Right-hand sides are taken in chunks as large as the
+ * free device memory allows for maxit Krylov vectors each.  hzs_solve with
+ * nrhs > 1 uses the same lockstep batches. */
+hzs_status hzs_solve_batched(int nprob, hzs_precond* const* probs, const hzs_solve_desc* sd,
+                             const void* const* f_dev, void* const* u_dev, const int* nrhs,
+                             hzs_solve_info* info);
+
 /* Solves the adjoint system conj(A) lambda = g with the same preconditioned
  * GMRES (as A mu = conj(g), lambda = conj(mu), since A = A^T, Section 2).
  * The paper has no adjoint; it serves the kappa gradient below. */

@@ -10,6 +10,8 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <thread>
+#include <algorithm>
 #include <tuple>
 #include <vector>
 
@@ -73,13 +75,14 @@ struct hzs_precond {
     void* w_buf = nullptr;            // n*n working complex
     void* ytiles = nullptr;           // sum of tile sizes, working complex
     float2* zc64 = nullptr;           // n*n (mixed public apply)
+    int wcap = 0;                     // batch capacity of the apply work space above
     // solve work space
     KrylovBufs kb{};
     int kb_maxit = 0;
-    float2* Z = nullptr;              // maxit x ld (mixed)
-    double2* ztmp = nullptr;          // ld (FP64 z / x)
-    double2* rtmp = nullptr;          // ld
-    double* dres = nullptr;           // 1
+    float2* Z = nullptr;              // nb x maxit x ld (mixed)
+    double2* ztmp = nullptr;          // nb x ld (FP64 z / x)
+    double2* rtmp = nullptr;          // nb x ld
+    double* dres = nullptr;           // nb
     int* h_done = nullptr;            // pinned, 2 slots
     cudaEvent_t ev[2] = {nullptr, nullptr};
     cudaEvent_t t0 = nullptr, t1 = nullptr;
@@ -111,6 +114,8 @@ static cudaError_t dalloc(T** p, size_t count) {
 }
 
 static size_t cplx_size(hzs_precision prec) { return prec == HZS_MIXED ? sizeof(float2) : sizeof(double2); }
+
+static hzs_status ensure_work(hzs_precond* p, int nb);
 
 // ------------------------------------------------------------------ grid
 extern "C" hzs_status hzs_grid_create(const hzs_grid_desc* d, void* cuda_stream, hzs_grid** out) {
@@ -217,9 +222,12 @@ static void free_krylov(hzs_precond* p) {
     KrylovBufs& kb = p->kb;
     cudaFree(kb.V); cudaFree(kb.V32); cudaFree(kb.sigma); cudaFree(kb.H); cudaFree(kb.cs); cudaFree(kb.sn); cudaFree(kb.g);
     cudaFree(kb.y); cudaFree(kb.h1); cudaFree(kb.h2); cudaFree(kb.part); cudaFree(kb.npart); cudaFree(kb.st);
-    cudaFree(p->Z);
+    cudaFree(kb.active);
+    cudaFree(p->Z); cudaFree(p->ztmp); cudaFree(p->rtmp); cudaFree(p->dres);
     kb = KrylovBufs{};
     p->Z = nullptr;
+    p->ztmp = p->rtmp = nullptr;
+    p->dres = nullptr;
     p->kb_maxit = 0;
 }
 
@@ -230,7 +238,7 @@ extern "C" void hzs_precond_destroy(hzs_precond* p) {
     cudaFree(p->wf); cudaFree(p->wtf); cudaFree(p->c2f); cudaFree(p->err); cudaFree(p->groups_d);
     cudaFree(p->Ainv); cudaFree(p->W64); cudaFree(p->W32); cudaFree(p->tiles_d); cudaFree(p->cover_d);
     cudaFree(p->t_buf); cudaFree(p->c_buf); cudaFree(p->c2_buf); cudaFree(p->w_buf); cudaFree(p->ytiles);
-    cudaFree(p->zc64); cudaFree(p->ztmp); cudaFree(p->rtmp); cudaFree(p->dres);
+    cudaFree(p->zc64);
     if (p->h_done) cudaFreeHost(p->h_done);
     for (auto& e : p->ev) if (e) cudaEventDestroy(e);
     if (p->t0) cudaEventDestroy(p->t0);
@@ -287,10 +295,6 @@ static hzs_status setup_impl(hzs_grid* g, const hzs_precond_desc* d, hzs_precond
         if (rc < 0) return fail(g, HZS_ERR_CUDA, "coarse factorisation failed");
         p->coarse_minpiv = minpiv;
         if (rc > 0) return fail(g, HZS_ERR_SINGULAR_COARSE, "coarse matrix A_0 has a zero pivot");
-        HZS_CUDA(g, dalloc(&p->c_buf, p->Nc));
-        HZS_CUDA(g, dalloc(&p->c2_buf, p->Nc));
-        HZS_CUDA(g, dalloc(&p->c2f, p->Nc));
-        HZS_CUDA(g, cudaMalloc(&p->t_buf, (size_t)n * p->hct.nc1 * cplx_size(d->precision)));
     }
     HZS_CUDA(g, dalloc(&p->err, 1));
     HZS_CUDA(g, cudaMemsetAsync(p->err, 0, sizeof(int), s));
@@ -360,16 +364,12 @@ static hzs_status setup_impl(hzs_grid* g, const hzs_precond_desc* d, hzs_precond
         if (fs.singular) return fail(g, HZS_ERR_SINGULAR_LOCAL, "a subdomain matrix has a zero pivot");
     HZS_CUDA(g, upload(&p->tiles_d, tiles, s));
     HZS_CUDA(g, upload(&p->cover_d, g->cover, s));
-    // ---- apply work space
-    const size_t cs = cplx_size(d->precision);
-    HZS_CUDA(g, cudaMalloc(&p->w_buf, (size_t)n * n * cs));
-    if (d->kind == HZS_AS1 || d->kind == HZS_AS2) {
-        long long tot = 0;
-        for (auto& T : tiles) tot += (long long)T.mx * T.my;
-        p->ytiles_elems = tot;
-        HZS_CUDA(g, cudaMalloc(&p->ytiles, (size_t)tot * cs));
+    // ---- apply work space (one right-hand side; batched calls grow it)
+    for (auto& T : tiles) p->ytiles_elems += (long long)T.mx * T.my;
+    {
+        hzs_status st = ensure_work(p, 1);
+        if (st != HZS_OK) return st;
     }
-    if (d->precision == HZS_MIXED) HZS_CUDA(g, dalloc(&p->zc64, (size_t)n * n));
     HZS_CUDA(g, cudaHostAlloc((void**)&p->h_done, 2 * sizeof(int), cudaHostAllocDefault));
     for (auto& ev : p->ev) HZS_CUDA(g, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     HZS_CUDA(g, cudaEventCreate(&p->t0));
@@ -397,36 +397,65 @@ extern "C" hzs_status hzs_precond_setup(hzs_grid* g, const hzs_precond_desc* d, 
 }
 
 // ------------------------------------------------------------------ preconditioner apply
-// z = M^{-1} (s v), s = vscale[0] or 1.  R: arithmetic of the stencil,
-// transfers and subdomain solves; the coarse solve is FP64 either way.
+// Per-call work buffers of the preconditioner, for batches of up to nb right-hand sides.
+static hzs_status ensure_work(hzs_precond* p, int nb) {
+    if (p->wcap >= nb) return HZS_OK;
+    hzs_grid* g = p->g;
+    cudaFree(p->t_buf); cudaFree(p->c_buf); cudaFree(p->c2_buf); cudaFree(p->c2f);
+    cudaFree(p->w_buf); cudaFree(p->ytiles); cudaFree(p->zc64);
+    p->t_buf = p->w_buf = p->ytiles = nullptr;
+    p->c_buf = p->c2_buf = nullptr;
+    p->c2f = p->zc64 = nullptr;
+    p->wcap = 0;
+    const size_t n = g->desc.n, cs = cplx_size(p->desc.precision);
+    if (p->use_coarse) {
+        HZS_CUDA(g, cudaMalloc(&p->t_buf, n * p->hct.nc1 * cs * nb));
+        HZS_CUDA(g, dalloc(&p->c_buf, (size_t)p->Nc * nb));
+        HZS_CUDA(g, dalloc(&p->c2_buf, (size_t)p->Nc * nb));
+        HZS_CUDA(g, dalloc(&p->c2f, (size_t)p->Nc * nb));
+    }
+    HZS_CUDA(g, cudaMalloc(&p->w_buf, n * n * cs * nb));
+    if (p->desc.kind == HZS_AS1 || p->desc.kind == HZS_AS2)
+        HZS_CUDA(g, cudaMalloc(&p->ytiles, (size_t)p->ytiles_elems * cs * nb));
+    if (p->desc.precision == HZS_MIXED) HZS_CUDA(g, dalloc(&p->zc64, n * n * nb));
+    p->wcap = nb;
+    return HZS_OK;
+}
+
+// z_r = M^{-1} (s_r v_r) for nb batch entries (v_r = v + r vs, s_r = vscale[r vss] or 1,
+// z_r = z + r zs).  R: arithmetic of the stencil, transfers and subdomain solves;
+// the coarse solve is FP64 either way.  Needs ensure_work(p, nb).
 template <typename R, typename Cv>
-static hzs_status precond_apply(hzs_precond* p, const Cv* v, const double* vscale, cplx_t<R>* z, const int* skip) {
+static hzs_status precond_apply(hzs_precond* p, int nb, const Cv* v, long long vs, const double* vscale,
+                                long long vss, cplx_t<R>* z, long long zs, BatchSkip sk) {
     using C = cplx_t<R>;
     constexpr bool f32 = sizeof(R) == sizeof(float);
     const Ctx& cx = p->cx;
     hzs_grid* g = p->g;
+    const long long nn = (long long)g->desc.n * g->desc.n;
+    const long long Nc = p->Nc;
     const C* W = nullptr;
     const C* cc = nullptr;            // coarse solution in the kernels' precision
     if constexpr (f32) { W = p->W32; cc = p->c2f; } else { W = p->W64; cc = p->c2_buf; }
     const TileGroups grp{p->groups_d, p->ngroups, p->group_T};
     const int kind = p->desc.kind;
     if (p->use_coarse) {
-        launch_restrict<Cv, R>(cx, v, vscale, (C*)p->t_buf, p->c_buf, skip);
-        launch_coarse_matvec(cx, p->Ainv, p->Nc, p->c_buf, p->c2_buf, skip, f32 ? p->c2f : nullptr);
+        launch_restrict<Cv, R>(cx, nb, v, vs, vscale, vss, (C*)p->t_buf, p->c_buf, sk);
+        launch_coarse_matvec(cx, nb, p->Ainv, p->Nc, p->c_buf, p->c2_buf, f32 ? p->c2f : nullptr, sk);
     }
     int rc = 0;
     if (kind == HZS_SHS2) {
-        launch_deflate<Cv, C, R>(cx, cc, v, vscale, (C*)p->w_buf, skip);
-        rc = launch_tile_solve<C, C, R>(cx, p->tiles_d, grp, g->max_mx, g->max_my, W, (const C*)p->w_buf, nullptr, 0,
-                                        cc, 1, z, nullptr, skip);
+        launch_deflate<Cv, C, R>(cx, nb, cc, Nc, v, vs, vscale, vss, (C*)p->w_buf, nn, sk);
+        rc = launch_tile_solve<C, C, R>(cx, nb, p->tiles_d, grp, g->max_mx, g->max_my, W, (const C*)p->w_buf, nn,
+                                        nullptr, 0, 0, cc, Nc, 1, z, zs, nullptr, 0, sk);
     } else if (kind == HZS_SAS2) {
-        rc = launch_tile_solve<Cv, C, R>(cx, p->tiles_d, grp, g->max_mx, g->max_my, W, v, vscale, 0, cc, 1, z,
-                                         nullptr, skip);
+        rc = launch_tile_solve<Cv, C, R>(cx, nb, p->tiles_d, grp, g->max_mx, g->max_my, W, v, vs, vscale, vss, 0, cc,
+                                         Nc, 1, z, zs, nullptr, 0, sk);
     } else {
-        rc = launch_tile_solve<Cv, C, R>(cx, p->tiles_d, grp, g->max_mx, g->max_my, W, v, vscale, 1, cc, 0,
-                                         (C*)nullptr, (C*)p->ytiles, skip);
-        launch_combine_additive<C, C, R>(cx, cc, p->use_coarse, p->cover_d, p->tiles_d, g->desc.nsub,
-                                         (const C*)p->ytiles, z, skip);
+        rc = launch_tile_solve<Cv, C, R>(cx, nb, p->tiles_d, grp, g->max_mx, g->max_my, W, v, vs, vscale, vss, 1, cc,
+                                         Nc, 0, (C*)nullptr, 0, (C*)p->ytiles, p->ytiles_elems, sk);
+        launch_combine_additive<C, C, R>(cx, nb, cc, Nc, p->use_coarse, p->cover_d, p->tiles_d, g->desc.nsub,
+                                         (const C*)p->ytiles, p->ytiles_elems, z, zs, sk);
     }
     if (rc != 0) return fail(g, HZS_ERR_CUDA, "subdomain solve launch failed");
     cudaError_t e = cudaGetLastError();
@@ -434,13 +463,16 @@ static hzs_status precond_apply(hzs_precond* p, const Cv* v, const double* vscal
     return HZS_OK;
 }
 
+static const BatchSkip kNoSkip{nullptr, 0};
+constexpr int kApplyChunk = 16;       // right-hand sides per batched preconditioner apply
+
 extern "C" hzs_status hzs_apply_operator(hzs_precond* p, const void* x_dev, void* y_dev, int nrhs) {
     if (!p) return fail(nullptr, HZS_ERR_INVALID_ARG, "precond is NULL");
     if (!x_dev || !y_dev || nrhs < 0) return fail(p->g, HZS_ERR_INVALID_ARG, "bad buffers or nrhs");
-    const size_t nn = (size_t)p->g->desc.n * p->g->desc.n;
-    for (int r = 0; r < nrhs; ++r)
-        launch_apply_A<double2, double2, double>(p->cx, (const double2*)x_dev + r * nn, (double2*)y_dev + r * nn,
-                                                 nullptr);
+    if (nrhs == 0) return HZS_OK;
+    const long long nn = (long long)p->g->desc.n * p->g->desc.n;
+    launch_apply_A<double2, double2, double>(p->cx, nrhs, (const double2*)x_dev, nn, (double2*)y_dev, nn, nullptr, 0,
+                                             kNoSkip);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(p->g, e, "apply_operator");
     return HZS_OK;
@@ -454,16 +486,19 @@ __global__ void k_c64_to_c128(long long N, const float2* __restrict__ a, double2
 extern "C" hzs_status hzs_apply_precond(hzs_precond* p, const void* v_dev, void* z_dev, int nrhs) {
     if (!p) return fail(nullptr, HZS_ERR_INVALID_ARG, "precond is NULL");
     if (!v_dev || !z_dev || nrhs < 0) return fail(p->g, HZS_ERR_INVALID_ARG, "bad buffers or nrhs");
-    const size_t nn = (size_t)p->g->desc.n * p->g->desc.n;
-    for (int r = 0; r < nrhs; ++r) {
-        const double2* v = (const double2*)v_dev + r * nn;
-        double2* z = (double2*)z_dev + r * nn;
-        hzs_status st;
+    const long long nn = (long long)p->g->desc.n * p->g->desc.n;
+    for (int r0 = 0; r0 < nrhs; r0 += kApplyChunk) {
+        const int nb = std::min(kApplyChunk, nrhs - r0);
+        hzs_status st = ensure_work(p, nb);
+        if (st != HZS_OK) return st;
+        const double2* v = (const double2*)v_dev + r0 * nn;
+        double2* z = (double2*)z_dev + r0 * nn;
         if (p->desc.precision == HZS_MIXED) {
-            st = precond_apply<float, double2>(p, v, nullptr, p->zc64, nullptr);
-            if (st == HZS_OK) k_c64_to_c128<<<4 * p->cx.num_sms, 256, 0, p->cx.stream>>>((long long)nn, p->zc64, z);
+            st = precond_apply<float, double2>(p, nb, v, nn, nullptr, 0, p->zc64, nn, kNoSkip);
+            if (st == HZS_OK)
+                k_c64_to_c128<<<4 * p->cx.num_sms, 256, 0, p->cx.stream>>>(nn * nb, p->zc64, z);
         } else {
-            st = precond_apply<double, double2>(p, v, nullptr, z, nullptr);
+            st = precond_apply<double, double2>(p, nb, v, nn, nullptr, 0, z, nn, kNoSkip);
         }
         if (st != HZS_OK) return st;
     }
@@ -473,39 +508,54 @@ extern "C" hzs_status hzs_apply_precond(hzs_precond* p, const void* v_dev, void*
 }
 
 // ------------------------------------------------------------------ solve
-static hzs_status ensure_krylov(hzs_precond* p, int maxit) {
+// Device bytes one batch entry of the Krylov work space takes.
+static size_t krylov_entry_bytes(const hzs_precond* p, int maxit, long long ld) {
+    const bool mixed = p->desc.precision == HZS_MIXED;
+    size_t b = (size_t)(maxit + 1) * ld * sizeof(double2);                 // V
+    if (mixed) b += (size_t)(maxit + 1) * ld * sizeof(float2)              // V32
+                    + (size_t)maxit * ld * sizeof(float2);                 // Z
+    b += 2 * (size_t)ld * sizeof(double2);                                 // ztmp, rtmp
+    b += (size_t)(maxit + 1) * maxit * sizeof(double2);                    // H
+    return b;
+}
+
+// Krylov work space for batches of up to nb right-hand sides with maxit steps.
+static hzs_status ensure_krylov(hzs_precond* p, int maxit, int nb) {
     hzs_grid* g = p->g;
-    if (p->kb_maxit >= maxit && p->kb.V) return HZS_OK;
+    if (p->kb.V && p->kb.maxit >= maxit && p->kb.nb >= nb) return HZS_OK;
     free_krylov(p);
     const long long N = (long long)g->desc.n * g->desc.n;
     const long long ld = (N + 63) / 64 * 64;
     KrylovBufs& kb = p->kb;
     kb.maxit = maxit;
+    kb.nb = nb;
     kb.N = N;
     kb.ld = ld;
     kb.nblk = 4 * g->num_sms;        // 4 blocks of 256 threads per SM for the basis sweeps
-    HZS_CUDA(g, dalloc(&kb.V, (size_t)(maxit + 1) * ld));
-    if (p->desc.precision == HZS_MIXED) HZS_CUDA(g, dalloc(&kb.V32, (size_t)(maxit + 1) * ld));
-    HZS_CUDA(g, dalloc(&kb.sigma, (size_t)maxit + 1));
-    HZS_CUDA(g, dalloc(&kb.H, (size_t)(maxit + 1) * maxit));
-    HZS_CUDA(g, dalloc(&kb.cs, (size_t)maxit));
-    HZS_CUDA(g, dalloc(&kb.sn, (size_t)maxit));
-    HZS_CUDA(g, dalloc(&kb.g, (size_t)maxit + 1));
-    HZS_CUDA(g, dalloc(&kb.y, (size_t)maxit));
-    HZS_CUDA(g, dalloc(&kb.h1, (size_t)maxit + 1));
-    HZS_CUDA(g, dalloc(&kb.h2, (size_t)maxit + 1));
-    HZS_CUDA(g, dalloc(&kb.part, (size_t)kb.nblk * (maxit + 1)));
-    HZS_CUDA(g, dalloc(&kb.npart, (size_t)kb.nblk));
-    HZS_CUDA(g, dalloc(&kb.st, 1));
-    if (p->desc.precision == HZS_MIXED) HZS_CUDA(g, dalloc(&p->Z, (size_t)maxit * ld));
-    if (!p->ztmp) HZS_CUDA(g, dalloc(&p->ztmp, (size_t)ld));
-    if (!p->rtmp) HZS_CUDA(g, dalloc(&p->rtmp, (size_t)ld));
-    if (!p->dres) HZS_CUDA(g, dalloc(&p->dres, 1));
-    p->kb_maxit = maxit;
-    return HZS_OK;
+    const size_t S = (size_t)(maxit + 1);
+    HZS_CUDA(g, dalloc(&kb.V, (size_t)nb * kb.sV()));
+    HZS_CUDA(g, dalloc(&kb.sigma, nb * S));
+    HZS_CUDA(g, dalloc(&kb.H, (size_t)nb * kb.sH()));
+    HZS_CUDA(g, dalloc(&kb.cs, nb * S));
+    HZS_CUDA(g, dalloc(&kb.sn, nb * S));
+    HZS_CUDA(g, dalloc(&kb.g, nb * S));
+    HZS_CUDA(g, dalloc(&kb.y, nb * S));
+    HZS_CUDA(g, dalloc(&kb.h1, nb * S));
+    HZS_CUDA(g, dalloc(&kb.h2, nb * S));
+    HZS_CUDA(g, dalloc(&kb.part, (size_t)nb * kb.sP()));
+    HZS_CUDA(g, dalloc(&kb.npart, (size_t)nb * kb.nblk));
+    HZS_CUDA(g, dalloc(&kb.st, (size_t)nb));
+    HZS_CUDA(g, dalloc(&kb.active, 1));
+    if (p->desc.precision == HZS_MIXED) {
+        HZS_CUDA(g, dalloc(&kb.V32, (size_t)nb * kb.sV()));
+        HZS_CUDA(g, dalloc(&p->Z, (size_t)nb * maxit * ld));
+    }
+    HZS_CUDA(g, dalloc(&p->ztmp, (size_t)nb * ld));
+    HZS_CUDA(g, dalloc(&p->rtmp, (size_t)nb * ld));
+    HZS_CUDA(g, dalloc(&p->dres, (size_t)nb));
+    return ensure_work(p, nb);
 }
 
-// One right-hand side: A u = f (conj_io: solve A mu = conj(f), return conj(mu)).
 // Kernel launches of one preconditioner apply.
 static int precond_launches(const hzs_precond* p) {
     int n = p->use_coarse ? 3 : 0;   // restriction (2) + coarse solve
@@ -525,88 +575,93 @@ static hzs_status ensure_prof_events(hzs_precond* p, int maxit) {
     return HZS_OK;
 }
 
-// One right-hand side: A u = f (conj_io: solve A mu = conj(f), return conj(mu)).
-static hzs_status solve_one(hzs_precond* p, const hzs_solve_desc* sd, const double2* f, double2* u, int conj_io,
-                            hzs_solve_info* info) {
+// nb right-hand sides in lockstep: A u_r = f_r (conj_io: solve A mu = conj(f), return
+// conj(mu)).  f_r = f + r nn, u_r = u + r nn.  Every Arnoldi step advances all entries
+// that have not finished; finished entries skip their work.  info gets nb entries.
+static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const double2* f, double2* u, int nb,
+                              int conj_io, hzs_solve_info* info) {
     hzs_grid* g = p->g;
     const Ctx& cx = p->cx;
     KrylovBufs& kb = p->kb;
     cudaStream_t s = cx.stream;
+    const long long nn = (long long)g->desc.n * g->desc.n;
+    const long long sV = kb.sV(), sS = kb.sS(), ld = kb.ld;
+    const long long sZ = (long long)kb.maxit * ld;
     const bool mixed = p->desc.precision == HZS_MIXED;
     const bool prof = (sd->flags & HZS_SOLVE_PROFILE) != 0;
-    const int* skip = &kb.st->done;
+    // mixed-precision CGS2 (complex64 first projection) unless all-FP64 orthogonalisation is asked for
+    const bool orth32 = mixed && !(sd->flags & HZS_SOLVE_ORTH_FP64);
+    const BatchSkip sk = kb.skip();
     const int pl = precond_launches(p);
     long long launches = 0;
     if (prof) {
         hzs_status st = ensure_prof_events(p, sd->maxit);
         if (st != HZS_OK) return st;
     }
-    // mixed-precision CGS2 (complex64 first projection) unless all-FP64 orthogonalisation is asked for
-    const bool orth32 = mixed && !(sd->flags & HZS_SOLVE_ORTH_FP64);
     HZS_CUDA(g, cudaEventRecord(p->t0, s));
     // V_0 = f (masked; it is never rescaled in place), plus its complex64 copy for orth32
-    launch_mask_copy_c128(cx, f, kb.V, conj_io, orth32 ? kb.V32 : nullptr);
-    launch_norm_init(cx, kb, sd->tol);
+    launch_mask_copy_c128(cx, nb, f, nn, kb.V, sV, conj_io, orth32 ? kb.V32 : nullptr, sV);
+    launch_norm_init(cx, kb, nb, sd->tol);
     launches += 3;
-    int j = 0, steps = 0;
-    for (; j < sd->maxit; ++j) {
-        double2* Vj = kb.V + (size_t)j * kb.ld;
-        double2* w = kb.V + (size_t)(j + 1) * kb.ld;
+    int steps = 0;
+    for (int j = 0; j < sd->maxit; ++j) {
+        double2* w = kb.V + (size_t)(j + 1) * ld;
         cudaEvent_t* pe = prof ? &p->prof_ev[(size_t)4 * j] : nullptr;
         if (prof) HZS_CUDA(g, cudaEventRecord(pe[0], s));
         hzs_status st;
         if (orth32) {
             // the complex64 preconditioner reads the complex64 copy of the basis vector
-            float2* Zj = p->Z + (size_t)j * kb.ld;
-            st = precond_apply<float, float2>(p, kb.V32 + (size_t)j * kb.ld, kb.sigma + j, Zj, skip);
+            float2* Zj = p->Z + (size_t)j * ld;
+            st = precond_apply<float, float2>(p, nb, kb.V32 + (size_t)j * ld, sV, kb.sigma + j, sS, Zj, sZ, sk);
             if (prof) HZS_CUDA(g, cudaEventRecord(pe[1], s));
-            launch_apply_A<float2, double2, double>(cx, Zj, w, skip, kb.V32 + (size_t)(j + 1) * kb.ld);
+            launch_apply_A<float2, double2, double>(cx, nb, Zj, sZ, w, sV, kb.V32 + (size_t)(j + 1) * ld, sV, sk);
         } else if (mixed) {
-            float2* Zj = p->Z + (size_t)j * kb.ld;
-            st = precond_apply<float, double2>(p, Vj, kb.sigma + j, Zj, skip);
+            float2* Zj = p->Z + (size_t)j * ld;
+            st = precond_apply<float, double2>(p, nb, kb.V + (size_t)j * ld, sV, kb.sigma + j, sS, Zj, sZ, sk);
             if (prof) HZS_CUDA(g, cudaEventRecord(pe[1], s));
-            launch_apply_A<float2, double2, double>(cx, Zj, w, skip);
+            launch_apply_A<float2, double2, double>(cx, nb, Zj, sZ, w, sV, nullptr, 0, sk);
         } else {
-            st = precond_apply<double, double2>(p, Vj, kb.sigma + j, p->ztmp, skip);
+            st = precond_apply<double, double2>(p, nb, kb.V + (size_t)j * ld, sV, kb.sigma + j, sS, p->ztmp, ld, sk);
             if (prof) HZS_CUDA(g, cudaEventRecord(pe[1], s));
-            launch_apply_A<double2, double2, double>(cx, p->ztmp, w, skip);
+            launch_apply_A<double2, double2, double>(cx, nb, p->ztmp, ld, w, sV, nullptr, 0, sk);
         }
         if (st != HZS_OK) return st;
         if (prof) HZS_CUDA(g, cudaEventRecord(pe[2], s));
-        if (orth32) launch_arnoldi_step_mixed(cx, kb, j);
-        else launch_arnoldi_step(cx, kb, j);
+        if (orth32) launch_arnoldi_step_mixed(cx, kb, nb, j);
+        else launch_arnoldi_step(cx, kb, nb, j);
         if (prof) HZS_CUDA(g, cudaEventRecord(pe[3], s));
         launches += pl + 1 + 7;
         steps = j + 1;
-        HZS_CUDA(g, cudaMemcpyAsync(&p->h_done[j & 1], &kb.st->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+        // the host runs one step ahead of the count of running entries it reads back
+        HZS_CUDA(g, cudaMemcpyAsync(&p->h_done[j & 1], kb.active, sizeof(int), cudaMemcpyDeviceToHost, s));
         HZS_CUDA(g, cudaEventRecord(p->ev[j & 1], s));
         if (j >= 1) {
             HZS_CUDA(g, cudaEventSynchronize(p->ev[(j - 1) & 1]));
-            if (p->h_done[(j - 1) & 1]) break;
+            if (p->h_done[(j - 1) & 1] == 0) break;
         }
     }
-    launch_lsq_solve(cx, kb);
+    launch_lsq_solve(cx, kb, nb);
     launches += 1;
     if (mixed) {
-        launch_combine_Z(cx, kb, p->Z, kb.ld, u);
+        launch_combine_Z(cx, kb, nb, p->Z, ld, sZ, u, nn);
         launches += 1;
     } else {
-        launch_combine_basis(cx, kb, p->ztmp);
-        hzs_status st = precond_apply<double, double2>(p, p->ztmp, nullptr, u, nullptr);
+        launch_combine_basis(cx, kb, nb, p->ztmp, ld);
+        hzs_status st = precond_apply<double, double2>(p, nb, p->ztmp, ld, nullptr, 0, u, nn, kNoSkip);
         if (st != HZS_OK) return st;
         launches += 1 + pl;
     }
     // true residual ||f - A u|| against the masked right-hand side in V_0
-    launch_apply_A<double2, double2, double>(cx, u, p->rtmp, nullptr);
-    launch_residual_norm(cx, kb, kb.V, p->rtmp, p->dres);
+    launch_apply_A<double2, double2, double>(cx, nb, u, nn, p->rtmp, ld, nullptr, 0, kNoSkip);
+    launch_residual_norm(cx, kb, nb, kb.V, sV, p->rtmp, ld, p->dres);
     launches += 3;
-    if (conj_io) { launch_mask_copy_c128(cx, u, u, 1); launches += 1; }
+    if (conj_io) { launch_mask_copy_c128(cx, nb, u, nn, u, nn, 1, nullptr, 0); launches += 1; }
     HZS_CUDA(g, cudaEventRecord(p->t1, s));
-    KState hs{};
-    double rnorm = 0.0;
+    std::vector<KState> hs(nb);
+    std::vector<double> rnorm(nb);
     int kerr = 0;
-    HZS_CUDA(g, cudaMemcpyAsync(&hs, kb.st, sizeof(KState), cudaMemcpyDeviceToHost, s));
-    HZS_CUDA(g, cudaMemcpyAsync(&rnorm, p->dres, sizeof(double), cudaMemcpyDeviceToHost, s));
+    HZS_CUDA(g, cudaMemcpyAsync(hs.data(), kb.st, nb * sizeof(KState), cudaMemcpyDeviceToHost, s));
+    HZS_CUDA(g, cudaMemcpyAsync(rnorm.data(), p->dres, nb * sizeof(double), cudaMemcpyDeviceToHost, s));
     HZS_CUDA(g, cudaMemcpyAsync(&kerr, p->err, sizeof(int), cudaMemcpyDeviceToHost, s));
     HZS_CUDA(g, cudaStreamSynchronize(s));
     if (kerr != 0) {
@@ -615,9 +670,8 @@ static hzs_status solve_one(hzs_precond* p, const hzs_solve_desc* sd, const doub
     }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, p->t0, p->t1);
-    hzs_solve_info inf{};
+    double tp = 0, tm = 0, to = 0;
     if (prof) {
-        double tp = 0, tm = 0, to = 0;
         for (int k = 0; k < steps; ++k) {
             cudaEvent_t* pe = &p->prof_ev[(size_t)4 * k];
             float a = 0, b = 0, c = 0;
@@ -626,33 +680,58 @@ static hzs_status solve_one(hzs_precond* p, const hzs_solve_desc* sd, const doub
             cudaEventElapsedTime(&c, pe[2], pe[3]);
             tp += a; tm += b; to += c;
         }
-        inf.t_precond_ms = tp; inf.t_matvec_ms = tm; inf.t_orth_ms = to;
     }
-    inf.iterations = hs.iters;
-    inf.converged = hs.conv;
-    inf.relres_est = hs.beta0 > 0 ? hs.resid / hs.beta0 : 0.0;
-    inf.relres_true = hs.beta0 > 0 ? rnorm / hs.beta0 : 0.0;
-    inf.t_solve_ms = ms;
-    inf.launches = launches;
-    inf.status = hs.nonfinite ? HZS_ERR_NONFINITE : (hs.conv ? HZS_OK : HZS_NOT_CONVERGED);
-    if (info) *info = inf;
-    if (hs.nonfinite) return fail(g, HZS_ERR_NONFINITE, "non-finite value in the right-hand side or iteration");
-    return inf.status;
+    hzs_status worst = HZS_OK;
+    for (int r = 0; r < nb; ++r) {
+        hzs_solve_info inf{};
+        inf.t_precond_ms = tp; inf.t_matvec_ms = tm; inf.t_orth_ms = to;
+        inf.iterations = hs[r].iters;
+        inf.converged = hs[r].conv;
+        inf.relres_est = hs[r].beta0 > 0 ? hs[r].resid / hs[r].beta0 : 0.0;
+        inf.relres_true = hs[r].beta0 > 0 ? rnorm[r] / hs[r].beta0 : 0.0;
+        inf.t_solve_ms = ms;
+        inf.launches = launches;
+        inf.status = hs[r].nonfinite ? HZS_ERR_NONFINITE : (hs[r].conv ? HZS_OK : HZS_NOT_CONVERGED);
+        if (info) info[r] = inf;
+        if (inf.status == HZS_ERR_NONFINITE) worst = HZS_ERR_NONFINITE;
+        else if (inf.status == HZS_NOT_CONVERGED && worst == HZS_OK) worst = HZS_NOT_CONVERGED;
+    }
+    if (worst == HZS_ERR_NONFINITE)
+        return fail(g, HZS_ERR_NONFINITE, "non-finite value in a right-hand side or in the iteration");
+    return worst;
 }
 
+// All right-hand sides of one call, in lockstep batches as large as the free
+// device memory allows (the Krylov space of every entry is resident).
+// budget: device bytes this call may take for Krylov space (0: 80 % of the free memory).
 static hzs_status solve_many(hzs_precond* p, const hzs_solve_desc* sd, const void* f_dev, void* u_dev, int nrhs,
-                             hzs_solve_info* info, int conj_io) {
+                             hzs_solve_info* info, int conj_io, size_t budget = 0) {
     if (!p) return fail(nullptr, HZS_ERR_INVALID_ARG, "precond is NULL");
     hzs_grid* g = p->g;
     if (!sd || !f_dev || !u_dev || nrhs < 0) return fail(g, HZS_ERR_INVALID_ARG, "bad arguments");
     if (!(sd->tol > 0.0) || sd->maxit < 1) return fail(g, HZS_ERR_INVALID_ARG, "tol must be > 0 and maxit >= 1");
-    hzs_status st = ensure_krylov(p, sd->maxit);
-    if (st != HZS_OK) return st;
-    const size_t nn = (size_t)g->desc.n * g->desc.n;
+    if (nrhs == 0) return HZS_OK;
+    int nb = nrhs;
+    if (!(p->kb.V && p->kb.maxit >= sd->maxit && p->kb.nb >= nrhs)) {
+        free_krylov(p);
+        size_t fr = 0, tot = 0;
+        HZS_CUDA(g, cudaMemGetInfo(&fr, &tot));
+        const long long N = (long long)g->desc.n * g->desc.n;
+        const size_t per = krylov_entry_bytes(p, sd->maxit, (N + 63) / 64 * 64);
+        const double avail = budget ? std::min((double)budget, 0.9 * (double)fr) : 0.8 * (double)fr;
+        const long long fit = (long long)avail / (long long)per;
+        if (fit < 1) return fail(g, HZS_ERR_OOM, "not enough device memory for one Krylov space of maxit steps");
+        nb = (int)std::min<long long>(nrhs, fit);
+        hzs_status st = ensure_krylov(p, sd->maxit, nb);
+        if (st != HZS_OK) return st;
+    }
+    nb = std::min(nrhs, p->kb.nb);
+    const long long nn = (long long)g->desc.n * g->desc.n;
     hzs_status worst = HZS_OK;
-    for (int r = 0; r < nrhs; ++r) {
-        st = solve_one(p, sd, (const double2*)f_dev + r * nn, (double2*)u_dev + r * nn, conj_io,
-                       info ? info + r : nullptr);
+    for (int r0 = 0; r0 < nrhs; r0 += nb) {
+        const int cnt = std::min(nb, nrhs - r0);
+        hzs_status st = solve_batch(p, sd, (const double2*)f_dev + r0 * nn, (double2*)u_dev + r0 * nn, cnt, conj_io,
+                                    info ? info + r0 : nullptr);
         if (st < 0) return st;
         if (st == HZS_NOT_CONVERGED) worst = HZS_NOT_CONVERGED;
     }
@@ -667,6 +746,45 @@ extern "C" hzs_status hzs_solve(hzs_precond* p, const hzs_solve_desc* sd, const 
 extern "C" hzs_status hzs_adjoint_solve(hzs_precond* p, const hzs_solve_desc* sd, const void* g_dev, void* lam_dev,
                                         int nrhs, hzs_solve_info* info) {
     return solve_many(p, sd, g_dev, lam_dev, nrhs, info, 1);
+}
+
+extern "C" hzs_status hzs_solve_batched(int nprob, hzs_precond* const* probs, const hzs_solve_desc* sd,
+                                        const void* const* f_dev, void* const* u_dev, const int* nrhs,
+                                        hzs_solve_info* info) {
+    if (nprob < 0 || (nprob > 0 && (!probs || !f_dev || !u_dev || !nrhs)))
+        return fail(nullptr, HZS_ERR_INVALID_ARG, "bad batched-solve arguments");
+    for (int k = 0; k < nprob; ++k) {
+        if (!probs[k]) return fail(nullptr, HZS_ERR_INVALID_ARG, "NULL preconditioner in batch");
+        for (int l = 0; l < k; ++l)
+            if (probs[l] == probs[k]) return fail(nullptr, HZS_ERR_INVALID_ARG, "a preconditioner appears twice");
+    }
+    std::vector<long long> off(nprob + 1, 0);
+    for (int k = 0; k < nprob; ++k) off[k + 1] = off[k] + nrhs[k];
+    std::vector<hzs_status> st(nprob, HZS_OK);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    // the problems allocate their Krylov spaces at the same time: split the free memory evenly
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    const size_t share = nprob > 0 ? (size_t)(0.8 * (double)fr / nprob) : 0;
+    std::vector<std::thread> th;
+    for (int k = 0; k < nprob; ++k) {
+        th.emplace_back([&, k]() {
+            cudaSetDevice(dev);
+            st[k] = solve_many(probs[k], sd, f_dev[k], u_dev[k], nrhs[k], info ? info + off[k] : nullptr, 0,
+                               share > 0 ? share : 1);
+        });
+    }
+    for (auto& t : th) t.join();
+    hzs_status worst = HZS_OK;
+    for (int k = 0; k < nprob; ++k) {
+        if (st[k] < 0) {
+            g_global_err = std::string("problem ") + std::to_string(k) + ": " + probs[k]->g->err;
+            return st[k];
+        }
+        if (st[k] == HZS_NOT_CONVERGED) worst = HZS_NOT_CONVERGED;
+    }
+    return worst;
 }
 
 extern "C" hzs_status hzs_kappa_gradient(hzs_precond* p, const void* u_dev, const void* lam_dev, double* grad_dev) {

@@ -72,14 +72,18 @@ void build_coarse_tables(int n, int bc, int kind, int p, HostCoarseTab& t) {
 // ------------------------------------------------------------------ restriction
 // t[j * nc1 + I] = s * sum_{i in supp I} phi_I(x_i) v[j n + i]   (x pass; one warp per (j, I))
 template <typename Cv, typename R>
-__global__ void k_restrict_x(int n, CoarseTab ct, const Cv* __restrict__ v, const double* __restrict__ vscale,
-                             cplx_t<R>* __restrict__ t, const int* __restrict__ skip) {
+__global__ void k_restrict_x(int n, CoarseTab ct, const Cv* __restrict__ v, long long vs,
+                             const double* __restrict__ vscale, long long vss, cplx_t<R>* __restrict__ t,
+                             BatchSkip sk) {
     using C = cplx_t<R>;
-    if (skip && *skip) return;
+    const int r = blockIdx.y;
+    if (sk.flag && sk.flag[(size_t)r * sk.stride]) return;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const int nc1 = ct.nc1;
     if (warp >= n * nc1) return;
+    v += r * vs;
+    t += (size_t)r * n * nc1;
     const int j = warp / nc1, I = warp % nc1;
     const int lo = ct.lo[I], hi = ct.hi[I];
     const int off = ct.off[I];
@@ -92,7 +96,7 @@ __global__ void k_restrict_x(int n, CoarseTab ct, const Cv* __restrict__ v, cons
     }
     acc = warp_sum(acc);
     if (lane == 0) {
-        const R s = vscale ? (R)vscale[0] : (R)1;
+        const R s = vscale ? (R)vscale[r * vss] : (R)1;
         acc.x *= s; acc.y *= s;
         t[(size_t)j * nc1 + I] = acc;
     }
@@ -101,12 +105,15 @@ __global__ void k_restrict_x(int n, CoarseTab ct, const Cv* __restrict__ v, cons
 // c[J * nc1 + I] = sum_{j in supp J} phi_J(y_j) t[j * nc1 + I]   (y pass, FP64 result)
 template <typename R>
 __global__ void k_restrict_y(int n, CoarseTab ct, const cplx_t<R>* __restrict__ t, double2* __restrict__ c,
-                             const int* __restrict__ skip) {
-    if (skip && *skip) return;
+                             BatchSkip sk) {
+    const int r = blockIdx.y;
+    if (sk.flag && sk.flag[(size_t)r * sk.stride]) return;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const int nc1 = ct.nc1;
     if (warp >= nc1 * nc1) return;
+    t += (size_t)r * n * nc1;
+    c += (size_t)r * nc1 * nc1;
     const int J = warp / nc1, I = warp % nc1;
     const int lo = ct.lo[J], hi = ct.hi[J];
     const int off = ct.off[J];
@@ -123,22 +130,25 @@ __global__ void k_restrict_y(int n, CoarseTab ct, const cplx_t<R>* __restrict__ 
 // ------------------------------------------------------------------ coarse solve
 // out = Ainv * c (dense, FP64).  One warp per row; c staged in shared memory.
 __global__ void k_coarse_matvec(int Nc, const double2* __restrict__ Ainv, const double2* __restrict__ c,
-                                double2* __restrict__ out, float2* __restrict__ outf,
-                                const int* __restrict__ skip) {
-    if (skip && *skip) return;
+                                double2* __restrict__ out, float2* __restrict__ outf, BatchSkip sk) {
+    const int r = blockIdx.y;
+    if (sk.flag && sk.flag[(size_t)r * sk.stride]) return;
+    c += (size_t)r * Nc;
+    out += (size_t)r * Nc;
+    if (outf) outf += (size_t)r * Nc;
     extern __shared__ double2 cs[];
     for (int k = threadIdx.x; k < Nc; k += blockDim.x) cs[k] = c[k];
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
-    for (int r = blockIdx.x * wpb + (threadIdx.x >> 5); r < Nc; r += gridDim.x * wpb) {
-        const double2* row = Ainv + (size_t)r * Nc;
+    for (int row = blockIdx.x * wpb + (threadIdx.x >> 5); row < Nc; row += gridDim.x * wpb) {
+        const double2* arow = Ainv + (size_t)row * Nc;
         double2 acc = make_double2(0.0, 0.0);
-        for (int k = lane; k < Nc; k += 32) acc = cfma(row[k], cs[k], acc);
+        for (int k = lane; k < Nc; k += 32) acc = cfma(arow[k], cs[k], acc);
         acc = warp_sum(acc);
         if (lane == 0) {
-            out[r] = acc;
-            if (outf) outf[r] = to_f(acc);
+            out[row] = acc;
+            if (outf) outf[row] = to_f(acc);
         }
     }
 }
@@ -274,37 +284,38 @@ __global__ void k_gj_colswap(int N, int k, double2* __restrict__ a, const int* _
 
 // ------------------------------------------------------------------ launchers
 template <typename Cv, typename R>
-void launch_restrict(const Ctx& cx, const Cv* v, const double* vscale, cplx_t<R>* t, double2* c, const int* skip) {
+void launch_restrict(const Ctx& cx, int nb, const Cv* v, long long vs, const double* vscale, long long vss,
+                     cplx_t<R>* t, double2* c, BatchSkip sk) {
     const int n = cx.op.n, nc1 = cx.ct.nc1;
+    const int threads = 256;
     {
         const long long warps = (long long)n * nc1;
-        const int threads = 256;
-        const long long blocks = (warps * 32 + threads - 1) / threads;
-        k_restrict_x<Cv, R><<<(unsigned)blocks, threads, 0, cx.stream>>>(n, cx.ct, v, vscale, t, skip);
+        const dim3 grid((unsigned)((warps * 32 + threads - 1) / threads), nb);
+        k_restrict_x<Cv, R><<<grid, threads, 0, cx.stream>>>(n, cx.ct, v, vs, vscale, vss, t, sk);
     }
     {
         const long long warps = (long long)nc1 * nc1;
-        const int threads = 256;
-        const long long blocks = (warps * 32 + threads - 1) / threads;
-        k_restrict_y<R><<<(unsigned)blocks, threads, 0, cx.stream>>>(n, cx.ct, t, c, skip);
+        const dim3 grid((unsigned)((warps * 32 + threads - 1) / threads), nb);
+        k_restrict_y<R><<<grid, threads, 0, cx.stream>>>(n, cx.ct, t, c, sk);
     }
 }
-template void launch_restrict<double2, double>(const Ctx&, const double2*, const double*, double2*, double2*,
-                                               const int*);
-template void launch_restrict<double2, float>(const Ctx&, const double2*, const double*, float2*, double2*,
-                                              const int*);
-template void launch_restrict<float2, float>(const Ctx&, const float2*, const double*, float2*, double2*,
-                                             const int*);
+#define HZS_RS(Cv, R)                                                                                          \
+    template void launch_restrict<Cv, R>(const Ctx&, int, const Cv*, long long, const double*, long long,     \
+                                         cplx_t<R>*, double2*, BatchSkip);
+HZS_RS(double2, double)
+HZS_RS(double2, float)
+HZS_RS(float2, float)
+#undef HZS_RS
 
-void launch_coarse_matvec(const Ctx& cx, const double2* Ainv, int Nc, const double2* c, double2* out,
-                          const int* skip, float2* outf) {
+void launch_coarse_matvec(const Ctx& cx, int nb, const double2* Ainv, int Nc, const double2* c, double2* out,
+                          float2* outf, BatchSkip sk) {
     const int threads = 256;
     const int rows_per_block = threads / 32;
     int blocks = (Nc + rows_per_block - 1) / rows_per_block;
     if (blocks > 4 * cx.num_sms) blocks = 4 * cx.num_sms;
     const size_t smem = (size_t)Nc * sizeof(double2);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_coarse_matvec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_coarse_matvec<<<blocks, threads, smem, cx.stream>>>(Nc, Ainv, c, out, outf, skip);
+    k_coarse_matvec<<<dim3(blocks, nb), threads, smem, cx.stream>>>(Nc, Ainv, c, out, outf, sk);
 }
 
 void launch_galerkin(const Ctx& cx, double2* A0) {

@@ -1,4 +1,9 @@
 // Internal declarations shared by the kernel files and the C ABI layer.
+//
+// Batches: every per-iteration launcher takes the number of right-hand sides
+// nb it works on; batch entry r addresses its vectors at r times the stride
+// given for each buffer (element counts), and is skipped when its "done" flag
+// (BatchSkip) is set.
 #pragma once
 
 #include <vector>
@@ -27,6 +32,12 @@ struct Ctx {
     int* err;          // device error word: kernels that time out set it (HZS_ERR_TIMEOUT); may be null
 };
 
+// Per-batch-entry skip flag: entry r is skipped when flag[r * stride] != 0 (flag may be null).
+struct BatchSkip {
+    const int* flag;
+    int stride;
+};
+
 // Subdomain tiles grouped by shared factor: group g solves tiles idx[g*T .. g*T+T-1]
 // (entries -1 are empty); all tiles of a group have the same factor.
 struct TileGroups {
@@ -50,21 +61,27 @@ struct FactorStat {
 
 // ---- operator.cu
 template <typename Cin, typename Cout, typename R>
-void launch_apply_A(const Ctx& cx, const Cin* x, Cout* y, const int* skip, float2* y32 = nullptr);
+void launch_apply_A(const Ctx& cx, int nb, const Cin* x, long long xs, Cout* y, long long ys, float2* y32,
+                    long long y32s, BatchSkip sk);
 template <typename Cv, typename Cw, typename R>
-void launch_deflate(const Ctx& cx, const cplx_t<R>* c, const Cv* v, const double* vscale, Cw* w, const int* skip);
+void launch_deflate(const Ctx& cx, int nb, const cplx_t<R>* c, long long cs, const Cv* v, long long vs,
+                    const double* vscale, long long vss, Cw* w, long long ws, BatchSkip sk);
 template <typename Cz, typename Cy, typename R>
-void launch_combine_additive(const Ctx& cx, const cplx_t<R>* c, int use_coarse, const int4* cover, const Tile* tiles,
-                             int nsub, const Cy* ytiles, Cz* z, const int* skip);
-void launch_mask_copy_c128(const Ctx& cx, const double2* src, double2* dst, int conj, float2* dst32 = nullptr);
+void launch_combine_additive(const Ctx& cx, int nb, const cplx_t<R>* c, long long cs, int use_coarse,
+                             const int4* cover, const Tile* tiles, int nsub, const Cy* ytiles, long long yts, Cz* z,
+                             long long zs, BatchSkip sk);
+void launch_mask_copy_c128(const Ctx& cx, int nb, const double2* src, long long ss, double2* dst, long long ds,
+                           int conj, float2* dst32, long long d32s);
 void launch_kappa_gradient(const Ctx& cx, const double2* u, const double2* lam, double* grad);
 
 // ---- coarse.cu
+// t = x-pass of R_0 (s v) (stride ts per entry), c = R_0 (s v) in FP64 (stride Nc)
 template <typename Cv, typename R>
-void launch_restrict(const Ctx& cx, const Cv* v, const double* vscale, cplx_t<R>* t, double2* c, const int* skip);
-// out = Ainv c in FP64; outf (if given) receives a complex64 copy for the complex64 kernels
-void launch_coarse_matvec(const Ctx& cx, const double2* Ainv, int Nc, const double2* c, double2* out,
-                          const int* skip, float2* outf = nullptr);
+void launch_restrict(const Ctx& cx, int nb, const Cv* v, long long vs, const double* vscale, long long vss,
+                     cplx_t<R>* t, double2* c, BatchSkip sk);
+// out = Ainv c in FP64 (stride Nc); outf (if given) receives a complex64 copy
+void launch_coarse_matvec(const Ctx& cx, int nb, const double2* Ainv, int Nc, const double2* c, double2* out,
+                          float2* outf, BatchSkip sk);
 void launch_galerkin(const Ctx& cx, double2* A0);
 int gj_invert(const Ctx& cx, double2* a, int N, double* minpiv);
 
@@ -74,15 +91,16 @@ int launch_tile_factor(const Ctx& cx, const FactorDesc* fdesc_dev, int nfactors,
                        float2* W32, FactorStat* stat_dev);
 // mode 0: restricted (D_i) write z = [q] + y on owned nodes; mode 1: write tile y to ytiles
 template <typename Cw, typename Cz, typename R>
-int launch_tile_solve(const Ctx& cx, const Tile* tiles, TileGroups grp, int max_mx, int max_my,
-                      const cplx_t<R>* W, const Cw* w, const double* vscale, int mode, const cplx_t<R>* c,
-                      int use_coarse, Cz* z, cplx_t<R>* ytiles, const int* skip);
+int launch_tile_solve(const Ctx& cx, int nb, const Tile* tiles, TileGroups grp, int max_mx, int max_my,
+                      const cplx_t<R>* W, const Cw* w, long long ws, const double* vscale, long long vss, int mode,
+                      const cplx_t<R>* c, long long cs, int use_coarse, Cz* z, long long zs, cplx_t<R>* ytiles,
+                      long long yts, BatchSkip sk);
 // Largest number of tiles per group (1 or 2) whose shared-memory footprint fits for
 // tiles of at most max_mx x max_my in arithmetic of size elem_bytes; 0 if none fits.
 int tile_group_width(int max_mx, int max_my, int elem_bytes);
 
 // ---- krylov.cu
-struct KState {
+struct alignas(16) KState {
     double beta0;      // ||f||
     double tolabs;     // tol * ||f||
     double resid;      // current GMRES residual estimate |g_{j+1}|
@@ -92,34 +110,48 @@ struct KState {
     int iters;         // completed Arnoldi steps
     int nonfinite;
     int breakdown;
-    int pad;
+    int pad[3];
 };
+constexpr int kStateInts = (int)(sizeof(KState) / sizeof(int));   // stride of KState::done in ints
+
+// Krylov work space for a batch of nb right-hand sides.  Every array holds nb
+// entries; entry r starts at r times the per-entry stride.
 struct KrylovBufs {
     int maxit;
+    int nb;            // batch capacity
     long long N;       // vector length (n*n)
     long long ld;      // leading dimension between basis vectors (elements)
     int nblk;          // blocks of the reduction kernels
-    double2* V;        // (maxit+1) x ld
+    double2* V;        // (maxit+1) x ld per entry
     float2* V32;       // (maxit+1) x ld complex64 copies (mixed-precision CGS2), or null
-    double* sigma;     // (maxit+1) lazy normalisation: basis vector i = sigma[i] * V_i
+    double* sigma;     // (maxit+1): basis vector i = sigma[i] * V_i
     double2* H;        // (maxit+1) x maxit, column j at H[j*(maxit+1)]
-    double* cs;        // maxit
-    double2* sn;       // maxit
+    double* cs;        // maxit+1
+    double2* sn;       // maxit+1
     double2* g;        // maxit+1
-    double2* y;        // maxit
+    double2* y;        // maxit+1
     double2* h1;       // maxit+1
     double2* h2;       // maxit+1
     double2* part;     // nblk x (maxit+1)
     double* npart;     // nblk
-    KState* st;
+    KState* st;        // 1
+    int* active;       // one counter per batch: entries not yet done
+    long long sV() const { return (long long)(maxit + 1) * ld; }
+    long long sH() const { return (long long)(maxit + 1) * maxit; }
+    long long sS() const { return maxit + 1; }
+    long long sP() const { return (long long)nblk * (maxit + 1); }
+    BatchSkip skip() const { return BatchSkip{&st->done, kStateInts}; }
 };
-void launch_norm_init(const Ctx& cx, const KrylovBufs& kb, double tol);
-void launch_arnoldi_step(const Ctx& cx, const KrylovBufs& kb, int j);
-void launch_arnoldi_step_mixed(const Ctx& cx, const KrylovBufs& kb, int j);
-void launch_lsq_solve(const Ctx& cx, const KrylovBufs& kb);
-void launch_combine_basis(const Ctx& cx, const KrylovBufs& kb, double2* x);
-void launch_combine_Z(const Ctx& cx, const KrylovBufs& kb, const float2* Z, long long ldz, double2* x);
-void launch_combine_Z64(const Ctx& cx, const KrylovBufs& kb, const double2* Z, long long ldz, double2* x);
+void launch_norm_init(const Ctx& cx, const KrylovBufs& kb, int nb, double tol);
+void launch_arnoldi_step(const Ctx& cx, const KrylovBufs& kb, int nb, int j);
+void launch_arnoldi_step_mixed(const Ctx& cx, const KrylovBufs& kb, int nb, int j);
+void launch_lsq_solve(const Ctx& cx, const KrylovBufs& kb, int nb);
+void launch_combine_basis(const Ctx& cx, const KrylovBufs& kb, int nb, double2* x, long long xs);
+void launch_combine_Z(const Ctx& cx, const KrylovBufs& kb, int nb, const float2* Z, long long ldz, long long zs,
+                      double2* x, long long xs);
+void launch_residual_norm(const Ctx& cx, const KrylovBufs& kb, int nb, const double2* f, long long fs,
+                          const double2* Ax, long long axs, double* out);
+
 // What the allocation-free apply (noalloc.cu) needs from a preconditioner handle.
 struct NoAllocView {
     Ctx cx;
@@ -130,7 +162,5 @@ struct NoAllocView {
     const float2* W32;
     const Tile* tiles;
 };
-
-void launch_residual_norm(const Ctx& cx, const KrylovBufs& kb, const double2* f, const double2* Ax, double* out);
 
 }  // namespace hzs

@@ -6,9 +6,12 @@
 // sigma[i] * V_i.  The scale is folded into the dot products and the update
 // coefficients, so no separate normalisation pass over the vector is needed.
 //
-// Every per-iteration kernel returns at once when the iteration has already
-// finished (st->done), so the host may enqueue an iteration before it knows
-// whether the previous one converged.
+// All kernels work on a batch of right-hand sides (batch entry r =
+// blockIdx.y, or blockIdx.x for the one-block-per-entry kernels); entry r's
+// arrays start at r times the per-entry strides of KrylovBufs.  Every
+// per-iteration kernel returns at once when its entry has already finished
+// (st[r].done), so the host may enqueue an iteration before it knows whether
+// the previous one converged, and converged entries of a batch cost nothing.
 //
 // Reductions are deterministic: fixed chunks per block, fixed lane order in
 // the warp trees, and the cross-block sums in a fixed order.
@@ -27,15 +30,19 @@ __device__ __forceinline__ void chunk_of(long long N, long long& e0, long long& 
 }
 
 // part[b][i] = sum_{e in chunk b} conj(V_i[e]) w[e], i = 0..j, with products and
-// sums in the precision of C.  Each warp takes groups of G basis vectors and
-// sweeps the whole chunk of its block for them (w is re-read from L1), so no
-// block-wide barrier is needed; lane 0 of the warp writes the group's partials.
+// sums in the precision of C (w = V + wofs).  Each warp takes groups of G basis
+// vectors and sweeps the whole chunk of its block for them (w is re-read from
+// L1), so no block-wide barrier is needed; lane 0 writes the group's partials.
 template <typename C, int G>
 __global__ void __launch_bounds__(kRedThreads) k_multidot(int j, long long N, long long ld, int stride,
-                                                          const C* __restrict__ V, const C* __restrict__ w,
-                                                          double2* __restrict__ part,
-                                                          const KState* __restrict__ st) {
-    if (st->done) return;
+                                                          const C* __restrict__ V, long long sV,
+                                                          long long wofs, double2* __restrict__ part,
+                                                          long long sP, const KState* __restrict__ st) {
+    const int r = blockIdx.y;
+    if (st[r].done) return;
+    V += r * sV;
+    const C* w = V + wofs;
+    part += r * sP;
     long long e0, e1;
     chunk_of(N, e0, e1);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -62,13 +69,15 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(int j, long long N, lo
 }
 
 // h[i] = sigma[i] * sum_b part[b][i]   (one warp per i, fixed order)
-__global__ void k_reduce_dots(int j, int nblk, int stride, const double2* __restrict__ part,
-                              const double* __restrict__ sigma, double2* __restrict__ h,
+__global__ void k_reduce_dots(int j, int nblk, int stride, const double2* __restrict__ part, long long sP,
+                              const double* __restrict__ sigma, double2* __restrict__ h, long long sS,
                               const KState* __restrict__ st) {
-    if (st->done) return;
+    const int r = blockIdx.y;
+    if (st[r].done) return;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i > j) return;
+    part += r * sP; sigma += r * sS; h += r * sS;
     double2 s = make_double2(0.0, 0.0);
     for (int b = lane; b < nblk; b += 32) s = cadd(s, part[(size_t)b * stride + i]);
     s = warp_sum(s);
@@ -87,14 +96,19 @@ __device__ __forceinline__ void block_norm_part(double nrm, double* __restrict__
     }
 }
 
-// w[e] -= sum_i (h[i] sigma[i]) V_i[e] in FP64; optionally npart[b] = sum_e |w[e]|^2.
-// Four independent partial sums per element keep several loads in flight.
+// w[e] -= sum_i (h[i] sigma[i]) V_i[e] in FP64 (w = V + wofs); optionally
+// npart[b] = sum_e |w[e]|^2.  Four independent partial sums per element keep
+// several loads in flight.
 __global__ void __launch_bounds__(kRedThreads) k_axpy_multi(int j, long long N, long long ld,
-                                                            const double2* __restrict__ V,
+                                                            double2* __restrict__ V, long long sV,
                                                             const double* __restrict__ sigma,
-                                                            const double2* __restrict__ h, double2* __restrict__ w,
-                                                            double* __restrict__ npart, const KState* __restrict__ st) {
-    if (st->done) return;
+                                                            const double2* __restrict__ h, long long sS,
+                                                            long long wofs, double* __restrict__ npart,
+                                                            int nblk, const KState* __restrict__ st) {
+    const int r = blockIdx.y;
+    if (st[r].done) return;
+    V += r * sV; sigma += r * sS; h += r * sS;
+    double2* w = V + wofs;
     extern __shared__ double2 coef[];
     for (int i = threadIdx.x; i <= j; i += blockDim.x) coef[i] = cscale(h[i], sigma[i]);
     __syncthreads();
@@ -118,20 +132,24 @@ __global__ void __launch_bounds__(kRedThreads) k_axpy_multi(int j, long long N, 
         w[e] = we;
         nrm = fma(we.x, we.x, fma(we.y, we.y, nrm));
     }
-    if (npart) block_norm_part(nrm, npart);
+    if (npart) block_norm_part(nrm, npart + (size_t)r * nblk);
 }
 
 // w[e] -= sum_i (h[i] sigma[i]) V32_i[e], the sum in complex64 and the
 // subtraction in FP64 (h is the small reorthogonalisation coefficient, so a
 // single-precision sum is accurate to FP64 level relative to w); also writes
-// w32 = complex64(w) and npart[b] = sum_e |w[e]|^2.
+// w32 = complex64(w) and npart[b] = sum_e |w[e]|^2.  w = V + wofs, w32 = V32 + wofs.
 __global__ void __launch_bounds__(kRedThreads) k_correct32(int j, long long N, long long ld,
-                                                           const float2* __restrict__ V32,
-                                                           const double* __restrict__ sigma,
-                                                           const double2* __restrict__ h, double2* __restrict__ w,
-                                                           float2* __restrict__ w32, double* __restrict__ npart,
+                                                           float2* __restrict__ V32, double2* __restrict__ V,
+                                                           long long sV, const double* __restrict__ sigma,
+                                                           const double2* __restrict__ h, long long sS,
+                                                           long long wofs, double* __restrict__ npart, int nblk,
                                                            const KState* __restrict__ st) {
-    if (st->done) return;
+    const int r = blockIdx.y;
+    if (st[r].done) return;
+    V32 += r * sV; V += r * sV; sigma += r * sS; h += r * sS;
+    double2* w = V + wofs;
+    float2* w32 = V32 + wofs;
     extern __shared__ float2 coef32[];
     for (int i = threadIdx.x; i <= j; i += blockDim.x) coef32[i] = to_f(cscale(h[i], sigma[i]));
     __syncthreads();
@@ -155,18 +173,25 @@ __global__ void __launch_bounds__(kRedThreads) k_correct32(int j, long long N, l
         w32[e] = to_f(we);
         nrm = fma(we.x, we.x, fma(we.y, we.y, nrm));
     }
-    block_norm_part(nrm, npart);
+    block_norm_part(nrm, npart + (size_t)r * nblk);
 }
 
-// Completes step j: h_{j+1,j} = ||w||, column j of H = h1 + h2, Givens
-// rotations, residual estimate, convergence / breakdown flags.  One warp: the
-// block norm partials are summed in a fixed lane order, the column and the
-// rotations are staged in shared memory, and lane 0 applies the rotation chain.
+// Completes step j of entry r = blockIdx.x: h_{j+1,j} = ||w||, column j of
+// H = h1 + h2, Givens rotations, residual estimate, convergence / breakdown
+// flags.  One warp per entry: the block norm partials are summed in a fixed
+// lane order, the column and the rotations are staged in shared memory, and
+// lane 0 applies the rotation chain.  An entry that finishes decrements the
+// batch's active counter.
 __global__ void k_arnoldi_finish(int j, int maxit, int nblk, const double* __restrict__ npart,
                                  const double2* __restrict__ h1, const double2* __restrict__ h2,
-                                 double2* __restrict__ H, double* __restrict__ cs, double2* __restrict__ sn,
-                                 double2* __restrict__ g, double* __restrict__ sigma, KState* __restrict__ st) {
-    if (st->done) return;
+                                 double2* __restrict__ H, long long sH, double* __restrict__ cs,
+                                 double2* __restrict__ sn, double2* __restrict__ g, double* __restrict__ sigma,
+                                 long long sS, KState* __restrict__ st, int* __restrict__ active) {
+    const int r = blockIdx.x;
+    if (st[r].done) return;
+    npart += (size_t)r * nblk;
+    h1 += r * sS; h2 += r * sS; H += r * sH; cs += r * sS; sn += r * sS; g += r * sS; sigma += r * sS;
+    KState* s0 = st + r;
     extern __shared__ double2 fsm[];
     double2* col = fsm;                                   // j + 2
     double2* ssn = col + (j + 2);                         // j
@@ -219,14 +244,16 @@ __global__ void k_arnoldi_finish(int j, int maxit, int nblk, const double* __res
         g[j + 1] = gn;
         g[j] = cscale(gj, c);
         const double resid = hypot(gn.x, gn.y);
-        st->resid = resid;
-        st->hnext = beta;
-        st->iters = j + 1;
+        s0->resid = resid;
+        s0->hnext = beta;
+        s0->iters = j + 1;
         sigma[j + 1] = beta > 0.0 ? 1.0 / beta : 0.0;
-        if (!isfinite(resid) || !isfinite(beta)) { st->nonfinite = 1; st->done = 1; }
-        else if (resid <= st->tolabs) { st->conv = 1; st->done = 1; }
-        else if (beta == 0.0) { st->breakdown = 1; st->conv = 1; st->done = 1; }
-        else if (j + 1 >= maxit) st->done = 1;
+        int fin = 1;
+        if (!isfinite(resid) || !isfinite(beta)) s0->nonfinite = 1;
+        else if (resid <= s0->tolabs) s0->conv = 1;
+        else if (beta == 0.0) { s0->breakdown = 1; s0->conv = 1; }
+        else if (!(j + 1 >= maxit)) fin = 0;
+        if (fin) { s0->done = 1; atomicSub(active, 1); }
     }
     __syncwarp();
     double2* out = H + (size_t)j * ldh;
@@ -234,9 +261,10 @@ __global__ void k_arnoldi_finish(int j, int maxit, int nblk, const double* __res
 }
 
 // ||f||: V_0 holds f; sets sigma[0], g[0], tolerance and flags.
-__global__ void __launch_bounds__(kRedThreads) k_norm_part(long long N, const double2* __restrict__ x,
-                                                           double* __restrict__ npart) {
-    __shared__ double nred[kRedThreads / 32];
+__global__ void __launch_bounds__(kRedThreads) k_norm_part(long long N, const double2* __restrict__ x, long long xs,
+                                                           double* __restrict__ npart, int nblk) {
+    const int r = blockIdx.y;
+    x += r * xs;
     long long e0, e1;
     chunk_of(N, e0, e1);
     double nrm = 0.0;
@@ -244,38 +272,43 @@ __global__ void __launch_bounds__(kRedThreads) k_norm_part(long long N, const do
         const double2 v = x[e];
         nrm = fma(v.x, v.x, fma(v.y, v.y, nrm));
     }
-    nrm = warp_sum_d(nrm);
-    if ((threadIdx.x & 31) == 0) nred[threadIdx.x >> 5] = nrm;
+    block_norm_part(nrm, npart + (size_t)r * nblk);
+}
+
+// One block; thread r initialises entry r; active = entries still running.
+__global__ void k_init_state(int nb, int nblk, double tol, const double* __restrict__ npart,
+                             double* __restrict__ sigma, double2* __restrict__ g, long long sS,
+                             KState* __restrict__ st, int* __restrict__ active) {
+    __shared__ int run;
+    if (threadIdx.x == 0) run = 0;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    for (int r = threadIdx.x; r < nb; r += blockDim.x) {
         double s = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += nred[k];
-        npart[blockIdx.x] = s;
+        for (int b = 0; b < nblk; ++b) s += npart[(size_t)r * nblk + b];
+        const double beta = sqrt(s);
+        KState* s0 = st + r;
+        s0->beta0 = beta;
+        s0->tolabs = tol * beta;
+        s0->resid = beta;
+        s0->hnext = 0.0;
+        s0->conv = 0; s0->iters = 0; s0->nonfinite = 0; s0->breakdown = 0;
+        s0->done = 0;
+        g[r * sS] = make_double2(beta, 0.0);
+        sigma[r * sS] = beta > 0.0 ? 1.0 / beta : 0.0;
+        if (!isfinite(beta)) { s0->nonfinite = 1; s0->done = 1; }
+        else if (beta == 0.0) { s0->conv = 1; s0->done = 1; }
+        else atomicAdd(&run, 1);
     }
+    __syncthreads();
+    if (threadIdx.x == 0) *active = run;
 }
 
-__global__ void k_init_state(int nblk, double tol, const double* __restrict__ npart, double* __restrict__ sigma,
-                             double2* __restrict__ g, KState* __restrict__ st) {
-    if (threadIdx.x != 0) return;
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += npart[b];
-    const double beta = sqrt(s);
-    st->beta0 = beta;
-    st->tolabs = tol * beta;
-    st->resid = beta;
-    st->hnext = 0.0;
-    st->conv = 0; st->iters = 0; st->nonfinite = 0; st->breakdown = 0;
-    st->done = 0;
-    g[0] = make_double2(beta, 0.0);
-    sigma[0] = beta > 0.0 ? 1.0 / beta : 0.0;
-    if (!isfinite(beta)) { st->nonfinite = 1; st->done = 1; }
-    else if (beta == 0.0) { st->conv = 1; st->done = 1; }
-}
-
-// y = R^{-1} g (m x m upper triangular in H after the rotations), column oriented.
-__global__ void k_lsq_solve(int maxit, const double2* __restrict__ H, double2* __restrict__ g,
-                            double2* __restrict__ y, const KState* __restrict__ st) {
-    const int m = st->iters;
+// y = R^{-1} g (m x m upper triangular in H after the rotations), column oriented; one block per entry.
+__global__ void k_lsq_solve(int maxit, const double2* __restrict__ H, long long sH, double2* __restrict__ g,
+                            double2* __restrict__ y, long long sS, const KState* __restrict__ st) {
+    const int r = blockIdx.x;
+    H += r * sH; g += r * sS; y += r * sS;
+    const int m = st[r].iters;
     const int ldh = maxit + 1;
     __shared__ double2 yi;
     for (int i = m - 1; i >= 0; --i) {
@@ -288,17 +321,19 @@ __global__ void k_lsq_solve(int maxit, const double2* __restrict__ H, double2* _
         }
         __syncthreads();
         const double2 v = yi;
-        for (int r = threadIdx.x; r < i; r += blockDim.x) g[r] = cfms(H[(size_t)i * ldh + r], v, g[r]);
+        for (int rr = threadIdx.x; rr < i; rr += blockDim.x) g[rr] = cfms(H[(size_t)i * ldh + rr], v, g[rr]);
         __syncthreads();
     }
 }
 
 // x[e] = sum_{i < m} y_i sigma_i V_i[e]
-__global__ void k_combine_basis(long long N, long long ld, int maxit, const double2* __restrict__ V,
-                                const double* __restrict__ sigma, const double2* __restrict__ y,
-                                double2* __restrict__ x, const KState* __restrict__ st) {
+__global__ void k_combine_basis(long long N, long long ld, const double2* __restrict__ V, long long sV,
+                                const double* __restrict__ sigma, const double2* __restrict__ y, long long sS,
+                                double2* __restrict__ x, long long xs, const KState* __restrict__ st) {
+    const int r = blockIdx.y;
+    V += r * sV; sigma += r * sS; y += r * sS; x += r * xs;
     extern __shared__ double2 coef[];
-    const int m = st->iters;
+    const int m = st[r].iters;
     for (int i = threadIdx.x; i < m; i += blockDim.x) coef[i] = cscale(y[i], sigma[i]);
     __syncthreads();
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
@@ -309,11 +344,13 @@ __global__ void k_combine_basis(long long N, long long ld, int maxit, const doub
 }
 
 // x[e] = sum_{i < m} y_i Z_i[e]
-template <typename CZ>
-__global__ void k_combine_Z(long long N, long long ldz, const CZ* __restrict__ Z, const double2* __restrict__ y,
-                            double2* __restrict__ x, const KState* __restrict__ st) {
+__global__ void k_combine_Z(long long N, long long ldz, const float2* __restrict__ Z, long long zs,
+                            const double2* __restrict__ y, long long sS, double2* __restrict__ x, long long xs,
+                            const KState* __restrict__ st) {
+    const int r = blockIdx.y;
+    Z += r * zs; y += r * sS; x += r * xs;
     extern __shared__ double2 coef[];
-    const int m = st->iters;
+    const int m = st[r].iters;
     for (int i = threadIdx.x; i < m; i += blockDim.x) coef[i] = y[i];
     __syncthreads();
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
@@ -323,11 +360,12 @@ __global__ void k_combine_Z(long long N, long long ldz, const CZ* __restrict__ Z
     }
 }
 
-// out[0] = ||f - Ax|| (two kernels: parts then a one-thread finish)
-__global__ void __launch_bounds__(kRedThreads) k_resid_part(long long N, const double2* __restrict__ f,
-                                                            const double2* __restrict__ ax,
-                                                            double* __restrict__ npart) {
-    __shared__ double nred[kRedThreads / 32];
+// out[r] = ||f_r - Ax_r|| (parts, then one thread per entry)
+__global__ void __launch_bounds__(kRedThreads) k_resid_part(long long N, const double2* __restrict__ f, long long fs,
+                                                            const double2* __restrict__ ax, long long axs,
+                                                            double* __restrict__ npart, int nblk) {
+    const int r = blockIdx.y;
+    f += r * fs; ax += r * axs;
     long long e0, e1;
     chunk_of(N, e0, e1);
     double nrm = 0.0;
@@ -336,20 +374,14 @@ __global__ void __launch_bounds__(kRedThreads) k_resid_part(long long N, const d
         const double rx = a.x - b.x, ry = a.y - b.y;
         nrm = fma(rx, rx, fma(ry, ry, nrm));
     }
-    nrm = warp_sum_d(nrm);
-    if ((threadIdx.x & 31) == 0) nred[threadIdx.x >> 5] = nrm;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += nred[k];
-        npart[blockIdx.x] = s;
-    }
+    block_norm_part(nrm, npart + (size_t)r * nblk);
 }
-__global__ void k_sum_sqrt(int nblk, const double* __restrict__ npart, double* __restrict__ out) {
-    if (threadIdx.x != 0) return;
+__global__ void k_sum_sqrt(int nb, int nblk, const double* __restrict__ npart, double* __restrict__ out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nb) return;
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += npart[b];
-    out[0] = sqrt(s);
+    for (int b = 0; b < nblk; ++b) s += npart[(size_t)r * nblk + b];
+    out[r] = sqrt(s);
 }
 
 // ------------------------------------------------------------------ launchers
@@ -365,29 +397,35 @@ static void set_coef_smem_limit(const void* fn, size_t bytes) {
     if (bytes > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-void launch_norm_init(const Ctx& cx, const KrylovBufs& kb, double tol) {
-    k_norm_part<<<kb.nblk, kRedThreads, 0, cx.stream>>>(kb.N, kb.V, kb.npart);
-    k_init_state<<<1, 32, 0, cx.stream>>>(kb.nblk, tol, kb.npart, kb.sigma, kb.g, kb.st);
+void launch_norm_init(const Ctx& cx, const KrylovBufs& kb, int nb, double tol) {
+    k_norm_part<<<dim3(kb.nblk, nb), kRedThreads, 0, cx.stream>>>(kb.N, kb.V, kb.sV(), kb.npart, kb.nblk);
+    k_init_state<<<1, 256, 0, cx.stream>>>(nb, kb.nblk, tol, kb.npart, kb.sigma, kb.g, kb.sS(), kb.st, kb.active);
 }
 
 // After the preconditioner and the matrix-vector product have written
-// w = A z_j into V_{j+1}: CGS2 against V_0..V_j, then the Givens update.
-void launch_arnoldi_step(const Ctx& cx, const KrylovBufs& kb, int j) {
+// w = A z_j into V_{j+1} of every entry: CGS2 against V_0..V_j, then the Givens update.
+void launch_arnoldi_step(const Ctx& cx, const KrylovBufs& kb, int nb, int j) {
     const int stride = kb.maxit + 1;
-    double2* w = kb.V + (size_t)(j + 1) * kb.ld;
-    const int rblocks = ((j + 1) * 32 + 255) / 256;
+    const long long wofs = (long long)(j + 1) * kb.ld;
+    const dim3 gr(kb.nblk, nb);
+    const dim3 rg(((j + 1) * 32 + 255) / 256, nb);
     const size_t cs = coef_smem(j + 1);
     set_coef_smem_limit((const void*)k_axpy_multi, cs);
     // pass 1: h1 = V^H w ; w -= V h1
-    k_multidot<double2, kDotGroup64><<<kb.nblk, kRedThreads, 0, cx.stream>>>(j, kb.N, kb.ld, stride, kb.V, w, kb.part, kb.st);
-    k_reduce_dots<<<rblocks, 256, 0, cx.stream>>>(j, kb.nblk, stride, kb.part, kb.sigma, kb.h1, kb.st);
-    k_axpy_multi<<<kb.nblk, kRedThreads, cs, cx.stream>>>(j, kb.N, kb.ld, kb.V, kb.sigma, kb.h1, w, nullptr, kb.st);
+    k_multidot<double2, kDotGroup64><<<gr, kRedThreads, 0, cx.stream>>>(j, kb.N, kb.ld, stride, kb.V, kb.sV(), wofs,
+                                                                        kb.part, kb.sP(), kb.st);
+    k_reduce_dots<<<rg, 256, 0, cx.stream>>>(j, kb.nblk, stride, kb.part, kb.sP(), kb.sigma, kb.h1, kb.sS(), kb.st);
+    k_axpy_multi<<<gr, kRedThreads, cs, cx.stream>>>(j, kb.N, kb.ld, kb.V, kb.sV(), kb.sigma, kb.h1, kb.sS(), wofs,
+                                                     nullptr, kb.nblk, kb.st);
     // pass 2 (reorthogonalisation): h2 = V^H w ; w -= V h2 ; ||w||
-    k_multidot<double2, kDotGroup64><<<kb.nblk, kRedThreads, 0, cx.stream>>>(j, kb.N, kb.ld, stride, kb.V, w, kb.part, kb.st);
-    k_reduce_dots<<<rblocks, 256, 0, cx.stream>>>(j, kb.nblk, stride, kb.part, kb.sigma, kb.h2, kb.st);
-    k_axpy_multi<<<kb.nblk, kRedThreads, cs, cx.stream>>>(j, kb.N, kb.ld, kb.V, kb.sigma, kb.h2, w, kb.npart, kb.st);
-    k_arnoldi_finish<<<1, 32, finish_smem(j), cx.stream>>>(j, kb.maxit, kb.nblk, kb.npart, kb.h1, kb.h2, kb.H, kb.cs, kb.sn, kb.g,
-                                              kb.sigma, kb.st);
+    k_multidot<double2, kDotGroup64><<<gr, kRedThreads, 0, cx.stream>>>(j, kb.N, kb.ld, stride, kb.V, kb.sV(), wofs,
+                                                                        kb.part, kb.sP(), kb.st);
+    k_reduce_dots<<<rg, 256, 0, cx.stream>>>(j, kb.nblk, stride, kb.part, kb.sP(), kb.sigma, kb.h2, kb.sS(), kb.st);
+    k_axpy_multi<<<gr, kRedThreads, cs, cx.stream>>>(j, kb.N, kb.ld, kb.V, kb.sV(), kb.sigma, kb.h2, kb.sS(), wofs,
+                                                     kb.npart, kb.nblk, kb.st);
+    k_arnoldi_finish<<<nb, 32, finish_smem(j), cx.stream>>>(j, kb.maxit, kb.nblk, kb.npart, kb.h1, kb.h2, kb.H,
+                                                            kb.sH(), kb.cs, kb.sn, kb.g, kb.sigma, kb.sS(), kb.st,
+                                                            kb.active);
 }
 
 // Mixed-precision CGS2 (used with the complex64 preconditioner): the first
@@ -399,49 +437,50 @@ void launch_arnoldi_step(const Ctx& cx, const KrylovBufs& kb, int j) {
 // Arnoldi relation therefore hold to FP64 level, with half the FP64 work of
 // the all-FP64 CGS2.  kb.V32 must hold complex64 copies of V_0 .. V_{j+1}
 // (V_{j+1} = A z_j written by the matrix-vector product).
-void launch_arnoldi_step_mixed(const Ctx& cx, const KrylovBufs& kb, int j) {
+void launch_arnoldi_step_mixed(const Ctx& cx, const KrylovBufs& kb, int nb, int j) {
     const int stride = kb.maxit + 1;
-    double2* w = kb.V + (size_t)(j + 1) * kb.ld;
-    float2* w32 = kb.V32 + (size_t)(j + 1) * kb.ld;
-    const int rblocks = ((j + 1) * 32 + 255) / 256;
+    const long long wofs = (long long)(j + 1) * kb.ld;
+    const dim3 gr(kb.nblk, nb);
+    const dim3 rg(((j + 1) * 32 + 255) / 256, nb);
     const size_t cs = coef_smem(j + 1);
     set_coef_smem_limit((const void*)k_axpy_multi, cs);
-    k_multidot<float2, kDotGroup32><<<kb.nblk, kRedThreads, 0, cx.stream>>>(j, kb.N, kb.ld, stride, kb.V32, w32, kb.part, kb.st);
-    k_reduce_dots<<<rblocks, 256, 0, cx.stream>>>(j, kb.nblk, stride, kb.part, kb.sigma, kb.h1, kb.st);
-    k_axpy_multi<<<kb.nblk, kRedThreads, cs, cx.stream>>>(j, kb.N, kb.ld, kb.V, kb.sigma, kb.h1, w, nullptr, kb.st);
-    k_multidot<double2, kDotGroup64><<<kb.nblk, kRedThreads, 0, cx.stream>>>(j, kb.N, kb.ld, stride, kb.V, w, kb.part, kb.st);
-    k_reduce_dots<<<rblocks, 256, 0, cx.stream>>>(j, kb.nblk, stride, kb.part, kb.sigma, kb.h2, kb.st);
-    k_correct32<<<kb.nblk, kRedThreads, (size_t)(j + 1) * sizeof(float2), cx.stream>>>(
-        j, kb.N, kb.ld, kb.V32, kb.sigma, kb.h2, w, w32, kb.npart, kb.st);
-    k_arnoldi_finish<<<1, 32, finish_smem(j), cx.stream>>>(j, kb.maxit, kb.nblk, kb.npart, kb.h1, kb.h2, kb.H, kb.cs, kb.sn, kb.g,
-                                              kb.sigma, kb.st);
+    k_multidot<float2, kDotGroup32><<<gr, kRedThreads, 0, cx.stream>>>(j, kb.N, kb.ld, stride, kb.V32, kb.sV(), wofs,
+                                                                       kb.part, kb.sP(), kb.st);
+    k_reduce_dots<<<rg, 256, 0, cx.stream>>>(j, kb.nblk, stride, kb.part, kb.sP(), kb.sigma, kb.h1, kb.sS(), kb.st);
+    k_axpy_multi<<<gr, kRedThreads, cs, cx.stream>>>(j, kb.N, kb.ld, kb.V, kb.sV(), kb.sigma, kb.h1, kb.sS(), wofs,
+                                                     nullptr, kb.nblk, kb.st);
+    k_multidot<double2, kDotGroup64><<<gr, kRedThreads, 0, cx.stream>>>(j, kb.N, kb.ld, stride, kb.V, kb.sV(), wofs,
+                                                                        kb.part, kb.sP(), kb.st);
+    k_reduce_dots<<<rg, 256, 0, cx.stream>>>(j, kb.nblk, stride, kb.part, kb.sP(), kb.sigma, kb.h2, kb.sS(), kb.st);
+    k_correct32<<<gr, kRedThreads, (size_t)(j + 1) * sizeof(float2), cx.stream>>>(
+        j, kb.N, kb.ld, kb.V32, kb.V, kb.sV(), kb.sigma, kb.h2, kb.sS(), wofs, kb.npart, kb.nblk, kb.st);
+    k_arnoldi_finish<<<nb, 32, finish_smem(j), cx.stream>>>(j, kb.maxit, kb.nblk, kb.npart, kb.h1, kb.h2, kb.H,
+                                                            kb.sH(), kb.cs, kb.sn, kb.g, kb.sigma, kb.sS(), kb.st,
+                                                            kb.active);
 }
 
-void launch_lsq_solve(const Ctx& cx, const KrylovBufs& kb) {
-    k_lsq_solve<<<1, 1024, 0, cx.stream>>>(kb.maxit, kb.H, kb.g, kb.y, kb.st);
+void launch_lsq_solve(const Ctx& cx, const KrylovBufs& kb, int nb) {
+    k_lsq_solve<<<nb, 1024, 0, cx.stream>>>(kb.maxit, kb.H, kb.sH(), kb.g, kb.y, kb.sS(), kb.st);
 }
 
-void launch_combine_basis(const Ctx& cx, const KrylovBufs& kb, double2* x) {
+void launch_combine_basis(const Ctx& cx, const KrylovBufs& kb, int nb, double2* x, long long xs) {
     const size_t cs = coef_smem(kb.maxit);
     set_coef_smem_limit((const void*)k_combine_basis, cs);
-    k_combine_basis<<<kb.nblk, 256, cs, cx.stream>>>(kb.N, kb.ld, kb.maxit, kb.V, kb.sigma, kb.y, x, kb.st);
+    k_combine_basis<<<dim3(kb.nblk, nb), 256, cs, cx.stream>>>(kb.N, kb.ld, kb.V, kb.sV(), kb.sigma, kb.y, kb.sS(), x,
+                                                               xs, kb.st);
 }
 
-void launch_combine_Z(const Ctx& cx, const KrylovBufs& kb, const float2* Z, long long ldz, double2* x) {
+void launch_combine_Z(const Ctx& cx, const KrylovBufs& kb, int nb, const float2* Z, long long ldz, long long zs,
+                      double2* x, long long xs) {
     const size_t cs = coef_smem(kb.maxit);
-    set_coef_smem_limit((const void*)k_combine_Z<float2>, cs);
-    k_combine_Z<float2><<<kb.nblk, 256, cs, cx.stream>>>(kb.N, ldz, Z, kb.y, x, kb.st);
+    set_coef_smem_limit((const void*)k_combine_Z, cs);
+    k_combine_Z<<<dim3(kb.nblk, nb), 256, cs, cx.stream>>>(kb.N, ldz, Z, zs, kb.y, kb.sS(), x, xs, kb.st);
 }
 
-void launch_combine_Z64(const Ctx& cx, const KrylovBufs& kb, const double2* Z, long long ldz, double2* x) {
-    const size_t cs = coef_smem(kb.maxit);
-    set_coef_smem_limit((const void*)k_combine_Z<double2>, cs);
-    k_combine_Z<double2><<<kb.nblk, 256, cs, cx.stream>>>(kb.N, ldz, Z, kb.y, x, kb.st);
-}
-
-void launch_residual_norm(const Ctx& cx, const KrylovBufs& kb, const double2* f, const double2* Ax, double* out) {
-    k_resid_part<<<kb.nblk, kRedThreads, 0, cx.stream>>>(kb.N, f, Ax, kb.npart);
-    k_sum_sqrt<<<1, 32, 0, cx.stream>>>(kb.nblk, kb.npart, out);
+void launch_residual_norm(const Ctx& cx, const KrylovBufs& kb, int nb, const double2* f, long long fs,
+                          const double2* Ax, long long axs, double* out) {
+    k_resid_part<<<dim3(kb.nblk, nb), kRedThreads, 0, cx.stream>>>(kb.N, f, fs, Ax, axs, kb.npart, kb.nblk);
+    k_sum_sqrt<<<(nb + 255) / 256, 256, 0, cx.stream>>>(nb, kb.nblk, kb.npart, out);
 }
 
 }  // namespace hzs

@@ -208,12 +208,18 @@ __host__ __device__ constexpr size_t tile_smem_bytes(int mx, int my) {
 template <typename Cw, typename Cz, typename R, int T, int NST>
 __global__ void __launch_bounds__(512) k_tile_solve(OpDesc op, CoarseTab ct, const Tile* __restrict__ tiles,
                                                     const int* __restrict__ groups, const cplx_t<R>* __restrict__ W,
-                                                    const Cw* __restrict__ w, const double* __restrict__ vscale,
-                                                    int mode, const cplx_t<R>* __restrict__ c, int use_coarse,
-                                                    Cz* __restrict__ z, cplx_t<R>* __restrict__ ytiles,
-                                                    const int* __restrict__ skip, int* __restrict__ err) {
+                                                    const Cw* __restrict__ w, long long ws,
+                                                    const double* __restrict__ vscale, long long vss, int mode,
+                                                    const cplx_t<R>* __restrict__ c, long long cs, int use_coarse,
+                                                    Cz* __restrict__ z, long long zs, cplx_t<R>* __restrict__ ytiles,
+                                                    long long yts, BatchSkip sk, int* __restrict__ err) {
     using C = cplx_t<R>;
-    if (skip && *skip) return;
+    const int rb = blockIdx.y;                      // batch entry
+    if (sk.flag && sk.flag[(size_t)rb * sk.stride]) return;
+    w += rb * ws;
+    c += rb * cs;
+    if (z) z += rb * zs;
+    if (ytiles) ytiles += rb * yts;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     int tix[T];
 #pragma unroll
@@ -244,7 +250,7 @@ __global__ void __launch_bounds__(512) k_tile_solve(OpDesc op, CoarseTab ct, con
         }
     }
     // gather b = R_i (s w) for the group's tiles
-    const R sc = vscale ? (R)vscale[0] : (R)1;
+    const R sc = vscale ? (R)vscale[rb * vss] : (R)1;
     for (int t = 0; t < T; ++t) {
         C* gt = g + (size_t)t * mx * my;
         if (tix[t] < 0) {
@@ -395,49 +401,47 @@ int tile_group_width(int max_mx, int max_my, int elem_bytes) {
 }
 
 template <typename Cw, typename Cz, typename R, int T, int NST>
-static int launch_tile_solve_t(const Ctx& cx, const Tile* tiles, TileGroups grp, int max_mx, int max_my,
-                               const cplx_t<R>* W, const Cw* w, const double* vscale, int mode, const cplx_t<R>* c,
-                               int use_coarse, Cz* z, cplx_t<R>* ytiles, const int* skip) {
+static int launch_tile_solve_t(const Ctx& cx, int nb, const Tile* tiles, TileGroups grp, int max_mx, int max_my,
+                               const cplx_t<R>* W, const Cw* w, long long ws, const double* vscale, long long vss,
+                               int mode, const cplx_t<R>* c, long long cs, int use_coarse, Cz* z, long long zs,
+                               cplx_t<R>* ytiles, long long yts, BatchSkip sk) {
     const size_t smem = tile_smem_bytes<R, T, NST>(max_mx, max_my);
     auto kern = k_tile_solve<Cw, Cz, R, T, NST>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
     const int threads = (max_mx * 4 + 31) / 32 * 32;
-    kern<<<grp.count, threads, smem, cx.stream>>>(cx.op, cx.ct, tiles, grp.idx, W, w, vscale, mode, c, use_coarse, z,
-                                                  ytiles, skip, cx.err);
+    kern<<<dim3(grp.count, nb), threads, smem, cx.stream>>>(cx.op, cx.ct, tiles, grp.idx, W, w, ws, vscale, vss, mode,
+                                                            c, cs, use_coarse, z, zs, ytiles, yts, sk, cx.err);
     return 0;
 }
 
 template <typename Cw, typename Cz, typename R>
-int launch_tile_solve(const Ctx& cx, const Tile* tiles, TileGroups grp, int max_mx, int max_my, const cplx_t<R>* W,
-                      const Cw* w, const double* vscale, int mode, const cplx_t<R>* c, int use_coarse, Cz* z,
-                      cplx_t<R>* ytiles, const int* skip) {
+int launch_tile_solve(const Ctx& cx, int nb, const Tile* tiles, TileGroups grp, int max_mx, int max_my,
+                      const cplx_t<R>* W, const Cw* w, long long ws, const double* vscale, long long vss, int mode,
+                      const cplx_t<R>* c, long long cs, int use_coarse, Cz* z, long long zs, cplx_t<R>* ytiles,
+                      long long yts, BatchSkip sk) {
     if (max_mx * 4 > 512) return -1;
+#define HZS_TRY(TT, NS)                                                                                        \
+    if (tile_smem_bytes<R, TT, NS>(max_mx, max_my) <= kSmemLimit)                                             \
+        return launch_tile_solve_t<Cw, Cz, R, TT, NS>(cx, nb, tiles, grp, max_mx, max_my, W, w, ws, vscale, vss, \
+                                                      mode, c, cs, use_coarse, z, zs, ytiles, yts, sk);
     if (grp.T == 2) {
         // deepest ring of factor-block stages that fits: more stages hide the L2 latency of the copies
-        if (tile_smem_bytes<R, 2, 4>(max_mx, max_my) <= kSmemLimit)
-            return launch_tile_solve_t<Cw, Cz, R, 2, 4>(cx, tiles, grp, max_mx, max_my, W, w, vscale, mode, c,
-                                                        use_coarse, z, ytiles, skip);
-        if (tile_smem_bytes<R, 2, 2>(max_mx, max_my) <= kSmemLimit)
-            return launch_tile_solve_t<Cw, Cz, R, 2, 2>(cx, tiles, grp, max_mx, max_my, W, w, vscale, mode, c,
-                                                        use_coarse, z, ytiles, skip);
+        HZS_TRY(2, 4)
+        HZS_TRY(2, 2)
         return -1;
     }
-    if (tile_smem_bytes<R, 1, 4>(max_mx, max_my) <= kSmemLimit)
-        return launch_tile_solve_t<Cw, Cz, R, 1, 4>(cx, tiles, grp, max_mx, max_my, W, w, vscale, mode, c, use_coarse,
-                                                    z, ytiles, skip);
-    if (tile_smem_bytes<R, 1, 2>(max_mx, max_my) <= kSmemLimit)
-        return launch_tile_solve_t<Cw, Cz, R, 1, 2>(cx, tiles, grp, max_mx, max_my, W, w, vscale, mode, c, use_coarse,
-                                                    z, ytiles, skip);
-    if (tile_smem_bytes<R, 1, 1>(max_mx, max_my) <= kSmemLimit)
-        return launch_tile_solve_t<Cw, Cz, R, 1, 1>(cx, tiles, grp, max_mx, max_my, W, w, vscale, mode, c, use_coarse,
-                                                    z, ytiles, skip);
+    HZS_TRY(1, 4)
+    HZS_TRY(1, 2)
+    HZS_TRY(1, 1)
+#undef HZS_TRY
     return -1;
 }
 
-#define HZS_TS(Cw, Cz, R)                                                                                        \
-    template int launch_tile_solve<Cw, Cz, R>(const Ctx&, const Tile*, TileGroups, int, int, const cplx_t<R>*,   \
-                                              const Cw*, const double*, int, const cplx_t<R>*, int, Cz*,         \
-                                              cplx_t<R>*, const int*);
+#define HZS_TS(Cw, Cz, R)                                                                                      \
+    template int launch_tile_solve<Cw, Cz, R>(const Ctx&, int, const Tile*, TileGroups, int, int,               \
+                                              const cplx_t<R>*, const Cw*, long long, const double*, long long,  \
+                                              int, const cplx_t<R>*, long long, int, Cz*, long long, cplx_t<R>*, \
+                                              long long, BatchSkip);
 HZS_TS(double2, double2, double)
 HZS_TS(float2, float2, float)
 HZS_TS(double2, float2, float)

@@ -38,6 +38,8 @@ void* g_scratch_addr[kMaxDevices] = {};
 
 size_t round256(size_t b) { return (b + 255) / 256 * 256; }
 
+const BatchSkip kNone{nullptr, 0};
+
 // Device address of g_noalloc_scratch on the current device (looked up once per device).
 cudaError_t scratch_address(void** out) {
     int dev = 0;
@@ -95,15 +97,15 @@ extern "C" hzs_status hzs_apply_precond_noalloc(hzs_precond* p, const void* v_de
         double2* z = (double2*)z_dev + r * nn;
         int rc;
         if (mixed) {
-            launch_restrict<double2, float>(V.cx, v, nullptr, reinterpret_cast<float2*>(b), c, nullptr);
-            launch_coarse_matvec(V.cx, V.Ainv, V.Nc, c, c2, nullptr, c2f);
-            rc = launch_tile_solve<double2, double2, float>(V.cx, V.tiles, V.groups, V.max_mx, V.max_my, V.W32, v,
-                                                            nullptr, 0, c2f, 1, z, nullptr, nullptr);
+            launch_restrict<double2, float>(V.cx, 1, v, 0, nullptr, 0, reinterpret_cast<float2*>(b), c, kNone);
+            launch_coarse_matvec(V.cx, 1, V.Ainv, V.Nc, c, c2, c2f, kNone);
+            rc = launch_tile_solve<double2, double2, float>(V.cx, 1, V.tiles, V.groups, V.max_mx, V.max_my, V.W32,
+                                                            v, 0, nullptr, 0, 0, c2f, 0, 1, z, 0, nullptr, 0, kNone);
         } else {
-            launch_restrict<double2, double>(V.cx, v, nullptr, reinterpret_cast<double2*>(b), c, nullptr);
-            launch_coarse_matvec(V.cx, V.Ainv, V.Nc, c, c2, nullptr);
-            rc = launch_tile_solve<double2, double2, double>(V.cx, V.tiles, V.groups, V.max_mx, V.max_my, V.W64, v,
-                                                             nullptr, 0, c2, 1, z, nullptr, nullptr);
+            launch_restrict<double2, double>(V.cx, 1, v, 0, nullptr, 0, reinterpret_cast<double2*>(b), c, kNone);
+            launch_coarse_matvec(V.cx, 1, V.Ainv, V.Nc, c, c2, nullptr, kNone);
+            rc = launch_tile_solve<double2, double2, double>(V.cx, 1, V.tiles, V.groups, V.max_mx, V.max_my, V.W64,
+                                                             v, 0, nullptr, 0, 0, c2, 0, 1, z, 0, nullptr, 0, kNone);
         }
         if (rc != 0) return hzs_internal_set_error(p, HZS_ERR_CUDA, "subdomain solve launch failed");
     }

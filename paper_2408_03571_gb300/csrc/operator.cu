@@ -5,22 +5,32 @@
 //
 // Kernels instantiated with R = float do all arithmetic in single precision
 // (coarse weights and the coarse solution are read as float copies).
+// Every kernel handles a batch of right-hand sides: batch entry r = blockIdx.z
+// reads and writes its vectors at r times the stride given for each buffer,
+// and is skipped when skip[r * skip_stride] is set.
 #include "kernels.cuh"
 
 namespace hzs {
+
+__device__ __forceinline__ bool skipped(const BatchSkip& sk, int r) {
+    return sk.flag && sk.flag[(size_t)r * sk.stride];
+}
 
 // y = A x over the n x n grid.  Arithmetic in R; x read as Cin, y written as
 // Cout and, if y32 is given, also as complex64.  MP-1 boundary nodes: y = 0,
 // and their x values are never read.
 template <typename Cin, typename Cout, typename R>
-__global__ void k_apply_A(OpDesc op, const Cin* __restrict__ x, Cout* __restrict__ y, float2* __restrict__ y32,
-                          const int* __restrict__ skip) {
+__global__ void k_apply_A(OpDesc op, const Cin* __restrict__ x, long long xs, Cout* __restrict__ y, long long ys,
+                          float2* __restrict__ y32, long long y32s, BatchSkip sk) {
     using C = cplx_t<R>;
-    if (skip && *skip) return;
+    const int r = blockIdx.z;
+    if (skipped(sk, r)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int n = op.n;
     if (i >= n || j >= n) return;
+    x += r * xs; y += r * ys;
+    if (y32) y32 += r * y32s;
     const size_t p = (size_t)j * n + i;
     if (!op_is_unknown(op, i, j)) {
         y[p] = mk<Cout>(0.0, 0.0);
@@ -68,14 +78,17 @@ __device__ __forceinline__ cplx_t<R> prolong_at(const CoarseTab& ct, const cplx_
     return q;
 }
 
-// w = s v - A q with q = R_0^T c evaluated on the fly; s = vscale[0] (or 1).
+// w = s v - A q with q = R_0^T c evaluated on the fly; s = vscale[r * vss] (or 1).
 // Block tile TX x TY nodes; q for the tile plus a one-node halo is staged in
 // shared memory.
 template <typename Cv, typename Cw, typename R, int TX, int TY>
-__global__ void k_deflate(OpDesc op, CoarseTab ct, const cplx_t<R>* __restrict__ c, const Cv* __restrict__ v,
-                          const double* __restrict__ vscale, Cw* __restrict__ w, const int* __restrict__ skip) {
+__global__ void k_deflate(OpDesc op, CoarseTab ct, const cplx_t<R>* __restrict__ c, long long cs,
+                          const Cv* __restrict__ v, long long vs, const double* __restrict__ vscale, long long vss,
+                          Cw* __restrict__ w, long long ws, BatchSkip sk) {
     using C = cplx_t<R>;
-    if (skip && *skip) return;
+    const int r = blockIdx.z;
+    if (skipped(sk, r)) return;
+    c += r * cs; v += r * vs; w += r * ws;
     __shared__ C qs[TY + 2][TX + 2];
     const int n = op.n;
     const int bx = blockIdx.x * TX, by = blockIdx.y * TY;
@@ -91,7 +104,7 @@ __global__ void k_deflate(OpDesc op, CoarseTab ct, const cplx_t<R>* __restrict__
     if (i >= n || j >= n) return;
     const size_t p = (size_t)j * n + i;
     if (!op_is_unknown(op, i, j)) { w[p] = mk<Cw>(0.0, 0.0); return; }
-    const R s = vscale ? (R)vscale[0] : (R)1;
+    const R s = vscale ? (R)vscale[r * vss] : (R)1;
     const double2 d = op_diag(op, i, j);
     const R cx = (R)op_cx(op, j), cy = (R)op_cy(op, i);
     const int li = threadIdx.x + 1, lj = threadIdx.y + 1;
@@ -115,11 +128,14 @@ __global__ void k_deflate(OpDesc op, CoarseTab ct, const cplx_t<R>* __restrict__
 // AS1 and AS2).  Per axis a node lies in at most two extended blocks;
 // cover[i] = (block a, offset of i in a, block b, offset in b), -1 if absent.
 template <typename Cz, typename Cy, typename R>
-__global__ void k_combine_additive(OpDesc op, CoarseTab ct, const cplx_t<R>* __restrict__ c, int use_coarse,
-                                   const int4* __restrict__ cover, const Tile* __restrict__ tiles, int nsub,
-                                   const Cy* __restrict__ ytiles, Cz* __restrict__ z, const int* __restrict__ skip) {
+__global__ void k_combine_additive(OpDesc op, CoarseTab ct, const cplx_t<R>* __restrict__ c, long long cs,
+                                   int use_coarse, const int4* __restrict__ cover, const Tile* __restrict__ tiles,
+                                   int nsub, const Cy* __restrict__ ytiles, long long yts, Cz* __restrict__ z,
+                                   long long zs, BatchSkip sk) {
     using C = cplx_t<R>;
-    if (skip && *skip) return;
+    const int r = blockIdx.z;
+    if (skipped(sk, r)) return;
+    c += r * cs; ytiles += r * yts; z += r * zs;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int n = op.n;
@@ -146,17 +162,19 @@ __global__ void k_combine_additive(OpDesc op, CoarseTab ct, const cplx_t<R>* __r
 
 // dst = src (or conj(src)) on unknowns, 0 on MP-1 boundary nodes; dst32 (if
 // given) receives the same values in complex64.
-__global__ void k_mask_copy(OpDesc op, const double2* __restrict__ src, double2* __restrict__ dst, int conj,
-                            float2* __restrict__ dst32) {
+__global__ void k_mask_copy(OpDesc op, const double2* __restrict__ src, long long ss, double2* __restrict__ dst,
+                            long long ds, int conj, float2* __restrict__ dst32, long long d32s) {
+    const int r = blockIdx.z;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int n = op.n;
     if (i >= n || j >= n) return;
+    src += r * ss; dst += r * ds;
     const size_t p = (size_t)j * n + i;
     double2 v = op_is_unknown(op, i, j) ? src[p] : make_double2(0.0, 0.0);
     if (conj) v.y = -v.y;
     dst[p] = v;
-    if (dst32) dst32[p] = to_f(v);
+    if (dst32) dst32[r * d32s + p] = to_f(v);
 }
 
 // grad = -Re(conj(lam) * dA_PP/dkappa_P * u) on unknowns, 0 elsewhere.
@@ -176,50 +194,62 @@ __global__ void k_kappa_gradient(OpDesc op, const double2* __restrict__ u, const
 }
 
 // ------------------------------------------------------------------ launchers
-static inline dim3 grid2d(int n, dim3 b) { return dim3((n + b.x - 1) / b.x, (n + b.y - 1) / b.y); }
+static inline dim3 grid2d(int n, dim3 b, int nb) {
+    return dim3((n + b.x - 1) / b.x, (n + b.y - 1) / b.y, nb);
+}
 
 template <typename Cin, typename Cout, typename R>
-void launch_apply_A(const Ctx& cx, const Cin* x, Cout* y, const int* skip, float2* y32) {
+void launch_apply_A(const Ctx& cx, int nb, const Cin* x, long long xs, Cout* y, long long ys, float2* y32,
+                    long long y32s, BatchSkip sk) {
     const dim3 b(32, 8);
-    k_apply_A<Cin, Cout, R><<<grid2d(cx.op.n, b), b, 0, cx.stream>>>(cx.op, x, y, y32, skip);
+    k_apply_A<Cin, Cout, R><<<grid2d(cx.op.n, b, nb), b, 0, cx.stream>>>(cx.op, x, xs, y, ys, y32, y32s, sk);
 }
-template void launch_apply_A<double2, double2, double>(const Ctx&, const double2*, double2*, const int*, float2*);
-template void launch_apply_A<float2, double2, double>(const Ctx&, const float2*, double2*, const int*, float2*);
+template void launch_apply_A<double2, double2, double>(const Ctx&, int, const double2*, long long, double2*,
+                                                       long long, float2*, long long, BatchSkip);
+template void launch_apply_A<float2, double2, double>(const Ctx&, int, const float2*, long long, double2*, long long,
+                                                      float2*, long long, BatchSkip);
 
 template <typename Cv, typename Cw, typename R>
-void launch_deflate(const Ctx& cx, const cplx_t<R>* c, const Cv* v, const double* vscale, Cw* w, const int* skip) {
+void launch_deflate(const Ctx& cx, int nb, const cplx_t<R>* c, long long cs, const Cv* v, long long vs,
+                    const double* vscale, long long vss, Cw* w, long long ws, BatchSkip sk) {
     constexpr int TX = 32, TY = 8;
     const dim3 b(TX, TY);
-    k_deflate<Cv, Cw, R, TX, TY><<<grid2d(cx.op.n, b), b, 0, cx.stream>>>(cx.op, cx.ct, c, v, vscale, w, skip);
+    k_deflate<Cv, Cw, R, TX, TY><<<grid2d(cx.op.n, b, nb), b, 0, cx.stream>>>(cx.op, cx.ct, c, cs, v, vs, vscale, vss,
+                                                                              w, ws, sk);
 }
-template void launch_deflate<double2, double2, double>(const Ctx&, const double2*, const double2*, const double*,
-                                                       double2*, const int*);
-template void launch_deflate<double2, float2, float>(const Ctx&, const float2*, const double2*, const double*,
-                                                     float2*, const int*);
-template void launch_deflate<float2, float2, float>(const Ctx&, const float2*, const float2*, const double*,
-                                                    float2*, const int*);
+#define HZS_DEF(Cv, Cw, R)                                                                                     \
+    template void launch_deflate<Cv, Cw, R>(const Ctx&, int, const cplx_t<R>*, long long, const Cv*, long long, \
+                                            const double*, long long, Cw*, long long, BatchSkip);
+HZS_DEF(double2, double2, double)
+HZS_DEF(double2, float2, float)
+HZS_DEF(float2, float2, float)
+#undef HZS_DEF
 
 template <typename Cz, typename Cy, typename R>
-void launch_combine_additive(const Ctx& cx, const cplx_t<R>* c, int use_coarse, const int4* cover, const Tile* tiles,
-                             int nsub, const Cy* ytiles, Cz* z, const int* skip) {
+void launch_combine_additive(const Ctx& cx, int nb, const cplx_t<R>* c, long long cs, int use_coarse,
+                             const int4* cover, const Tile* tiles, int nsub, const Cy* ytiles, long long yts, Cz* z,
+                             long long zs, BatchSkip sk) {
     const dim3 b(32, 8);
-    k_combine_additive<Cz, Cy, R><<<grid2d(cx.op.n, b), b, 0, cx.stream>>>(cx.op, cx.ct, c, use_coarse, cover, tiles,
-                                                                           nsub, ytiles, z, skip);
+    k_combine_additive<Cz, Cy, R><<<grid2d(cx.op.n, b, nb), b, 0, cx.stream>>>(
+        cx.op, cx.ct, c, cs, use_coarse, cover, tiles, nsub, ytiles, yts, z, zs, sk);
 }
-template void launch_combine_additive<double2, double2, double>(const Ctx&, const double2*, int, const int4*,
-                                                                const Tile*, int, const double2*, double2*,
-                                                                const int*);
-template void launch_combine_additive<float2, float2, float>(const Ctx&, const float2*, int, const int4*,
-                                                             const Tile*, int, const float2*, float2*, const int*);
+#define HZS_CMB(Cz, Cy, R)                                                                                     \
+    template void launch_combine_additive<Cz, Cy, R>(const Ctx&, int, const cplx_t<R>*, long long, int,       \
+                                                     const int4*, const Tile*, int, const Cy*, long long, Cz*, \
+                                                     long long, BatchSkip);
+HZS_CMB(double2, double2, double)
+HZS_CMB(float2, float2, float)
+#undef HZS_CMB
 
-void launch_mask_copy_c128(const Ctx& cx, const double2* src, double2* dst, int conj, float2* dst32) {
+void launch_mask_copy_c128(const Ctx& cx, int nb, const double2* src, long long ss, double2* dst, long long ds,
+                           int conj, float2* dst32, long long d32s) {
     const dim3 b(32, 8);
-    k_mask_copy<<<grid2d(cx.op.n, b), b, 0, cx.stream>>>(cx.op, src, dst, conj, dst32);
+    k_mask_copy<<<grid2d(cx.op.n, b, nb), b, 0, cx.stream>>>(cx.op, src, ss, dst, ds, conj, dst32, d32s);
 }
 
 void launch_kappa_gradient(const Ctx& cx, const double2* u, const double2* lam, double* grad) {
     const dim3 b(32, 8);
-    k_kappa_gradient<<<grid2d(cx.op.n, b), b, 0, cx.stream>>>(cx.op, u, lam, grad);
+    k_kappa_gradient<<<grid2d(cx.op.n, b, 1), b, 0, cx.stream>>>(cx.op, u, lam, grad);
 }
 
 }  // namespace hzs

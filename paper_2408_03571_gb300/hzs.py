@@ -30,7 +30,7 @@ EXPORTS = (
     "hzs_grid_create", "hzs_grid_destroy", "hzs_precond_setup", "hzs_precond_destroy",
     "hzs_apply_operator", "hzs_apply_precond", "hzs_solve", "hzs_adjoint_solve",
     "hzs_kappa_gradient", "hzs_status_string", "hzs_last_error", "hzs_version",
-    "hzs_apply_precond_noalloc",
+    "hzs_apply_precond_noalloc", "hzs_solve_batched",
 )
 
 
@@ -91,6 +91,8 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.hzs_apply_precond_noalloc.argtypes = [P, P, P, ct.c_int]
     lib.hzs_solve.argtypes = [P, ct.POINTER(SolveDesc), P, P, ct.c_int, ct.POINTER(SolveInfo)]
     lib.hzs_adjoint_solve.argtypes = [P, ct.POINTER(SolveDesc), P, P, ct.c_int, ct.POINTER(SolveInfo)]
+    lib.hzs_solve_batched.argtypes = [ct.c_int, ct.POINTER(P), ct.POINTER(SolveDesc), ct.POINTER(P), ct.POINTER(P),
+                                      ct.POINTER(ct.c_int), ct.POINTER(SolveInfo)]
     lib.hzs_kappa_gradient.argtypes = [P, P, P, P]
     lib.hzs_status_string.argtypes = [ct.c_int]
     lib.hzs_status_string.restype = ct.c_char_p
@@ -253,6 +255,36 @@ class Preconditioner:
             self.close()
         except Exception:
             pass
+
+
+def solve_batched(problems, rhs, tol: float = 1e-6, maxit: int = 1000, orth_fp64: bool = False):
+    """Batched solve over several problems: ``problems`` is a list of Preconditioner
+    handles (distinct), ``rhs`` a matching list of complex128 tensors of shape
+    (nrhs_k, n_k, n_k).  Returns (list of solutions, list of lists of SolveResult)."""
+    lib = load()
+    if len(problems) != len(rhs):
+        raise ValueError("one right-hand-side tensor per problem")
+    k = len(problems)
+    outs = []
+    for P, f in zip(problems, rhs):
+        _dev_c128(f, P.n, "f")
+        outs.append(torch.empty_like(f))
+    counts = [f.numel() // (P.n * P.n) for P, f in zip(problems, rhs)]
+    total = sum(counts)
+    infos = (SolveInfo * max(total, 1))()
+    arr = lambda vals: (ct.c_void_p * max(k, 1))(*vals)
+    sd = SolveDesc(float(tol), int(maxit), SOLVE_ORTH_FP64 if orth_fp64 else 0)
+    st = lib.hzs_solve_batched(k, arr([P.handle.value for P in problems]), ct.byref(sd),
+                               arr([f.data_ptr() for f in rhs]), arr([u.data_ptr() for u in outs]),
+                               (ct.c_int * max(k, 1))(*counts), infos)
+    _check(st, None, allow=(OK, NOT_CONVERGED))
+    res, pos = [], 0
+    for c in counts:
+        res.append([SolveResult(i.iterations, bool(i.converged), i.relres_est, i.relres_true, i.t_solve_ms,
+                                i.t_precond_ms, i.t_matvec_ms, i.t_orth_ms, i.launches, i.status)
+                    for i in infos[pos:pos + c]])
+        pos += c
+    return outs, res
 
 
 def version() -> str:

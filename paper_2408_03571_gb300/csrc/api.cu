@@ -220,7 +220,7 @@ extern "C" void hzs_grid_destroy(hzs_grid* g) {
 // ------------------------------------------------------------------ preconditioner
 static void free_krylov(hzs_precond* p) {
     KrylovBufs& kb = p->kb;
-    cudaFree(kb.V); cudaFree(kb.V32); cudaFree(kb.sigma); cudaFree(kb.H); cudaFree(kb.cs); cudaFree(kb.sn); cudaFree(kb.g);
+    cudaFree(kb.V); cudaFree(kb.V32); cudaFree(kb.V32lo); cudaFree(kb.sigma); cudaFree(kb.H); cudaFree(kb.cs); cudaFree(kb.sn); cudaFree(kb.g);
     cudaFree(kb.y); cudaFree(kb.h1); cudaFree(kb.h2); cudaFree(kb.part); cudaFree(kb.npart); cudaFree(kb.st);
     cudaFree(kb.active);
     cudaFree(p->Z); cudaFree(p->ztmp); cudaFree(p->rtmp); cudaFree(p->dres);
@@ -512,7 +512,7 @@ extern "C" hzs_status hzs_apply_precond(hzs_precond* p, const void* v_dev, void*
 static size_t krylov_entry_bytes(const hzs_precond* p, int maxit, long long ld) {
     const bool mixed = p->desc.precision == HZS_MIXED;
     size_t b = (size_t)(maxit + 1) * ld * sizeof(double2);                 // V
-    if (mixed) b += (size_t)(maxit + 1) * ld * sizeof(float2)              // V32
+    if (mixed) b += 2 * (size_t)(maxit + 1) * ld * sizeof(float2)          // V32, V32lo
                     + (size_t)maxit * ld * sizeof(float2);                 // Z
     b += 2 * (size_t)ld * sizeof(double2);                                 // ztmp, rtmp
     b += (size_t)(maxit + 1) * maxit * sizeof(double2);                    // H
@@ -548,6 +548,7 @@ static hzs_status ensure_krylov(hzs_precond* p, int maxit, int nb) {
     HZS_CUDA(g, dalloc(&kb.active, 1));
     if (p->desc.precision == HZS_MIXED) {
         HZS_CUDA(g, dalloc(&kb.V32, (size_t)nb * kb.sV()));
+        HZS_CUDA(g, dalloc(&kb.V32lo, (size_t)nb * kb.sV()));
         HZS_CUDA(g, dalloc(&p->Z, (size_t)nb * maxit * ld));
     }
     HZS_CUDA(g, dalloc(&p->ztmp, (size_t)nb * ld));
@@ -600,7 +601,8 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
     }
     HZS_CUDA(g, cudaEventRecord(p->t0, s));
     // V_0 = f (masked; it is never rescaled in place), plus its complex64 copy for orth32
-    launch_mask_copy_c128(cx, nb, f, nn, kb.V, sV, conj_io, orth32 ? kb.V32 : nullptr, sV);
+    launch_mask_copy_c128(cx, nb, f, nn, kb.V, sV, conj_io, orth32 ? kb.V32 : nullptr, sV,
+                          orth32 ? kb.V32lo : nullptr);
     launch_norm_init(cx, kb, nb, sd->tol);
     launches += 3;
     int steps = 0;
@@ -614,7 +616,10 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
             float2* Zj = p->Z + (size_t)j * ld;
             st = precond_apply<float, float2>(p, nb, kb.V32 + (size_t)j * ld, sV, kb.sigma + j, sS, Zj, sZ, sk);
             if (prof) HZS_CUDA(g, cudaEventRecord(pe[1], s));
-            launch_apply_A<float2, double2, double>(cx, nb, Zj, sZ, w, sV, kb.V32 + (size_t)(j + 1) * ld, sV, sk);
+            // A z_j as a double-float pair (the FP64 copy of the basis is not used on this path)
+            launch_apply_A<float2, double2, double>(cx, nb, Zj, sZ, (double2*)nullptr, 0,
+                                                    kb.V32 + (size_t)(j + 1) * ld, sV, sk,
+                                                    kb.V32lo + (size_t)(j + 1) * ld);
         } else if (mixed) {
             float2* Zj = p->Z + (size_t)j * ld;
             st = precond_apply<float, double2>(p, nb, kb.V + (size_t)j * ld, sV, kb.sigma + j, sS, Zj, sZ, sk);

@@ -66,6 +66,48 @@ template <typename C> __device__ __forceinline__ C cfms(C a, C b, C acc) {
     return acc;
 }
 
+// ---------------------------------------------------------------- double-float
+// A value is carried as an unevaluated sum hi + lo of two floats (|lo| <= ulp(hi)/2
+// after normalisation): about 48 significand bits from FP32 instructions only.
+// Error-free transformations: Knuth's TwoSum and the FMA form of Dekker's product.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {   // |a| >= |b|
+    s = a + b;
+    e = b - (s - a);
+}
+// (sh, sl) += (xh + xl) * (yh + yl), dropping the xl*yl term (2^-48 relative)
+__device__ __forceinline__ void df_fma(float& sh, float& sl, float xh, float xl, float yh, float yl) {
+    const float p = xh * yh;
+    float e = fmaf(xh, yh, -p);
+    e = fmaf(xh, yl, e);
+    e = fmaf(xl, yh, e);
+    float s, t;
+    two_sum(sh, p, s, t);
+    sh = s;
+    sl += t + e;
+}
+// (sh, sl) += (oh, ol)
+__device__ __forceinline__ void df_add(float& sh, float& sl, float oh, float ol) {
+    float s, t;
+    two_sum(sh, oh, s, t);
+    sh = s;
+    sl += t + ol;
+}
+__device__ __forceinline__ void df_norm(float& sh, float& sl) {
+    float s, t;
+    fast_two_sum(sh, sl, s, t);
+    sh = s; sl = t;
+}
+// split a double into hi = fl32(x) and lo = fl32(x - hi)
+__device__ __forceinline__ void split_d(double x, float& hi, float& lo) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+}
+
 template <typename C> __device__ __forceinline__ C shfl_down(C v, int off) {
     v.x = __shfl_down_sync(0xffffffffu, v.x, off);
     v.y = __shfl_down_sync(0xffffffffu, v.y, off);

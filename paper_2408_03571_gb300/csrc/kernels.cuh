@@ -62,7 +62,7 @@ struct FactorStat {
 // ---- operator.cu
 template <typename Cin, typename Cout, typename R>
 void launch_apply_A(const Ctx& cx, int nb, const Cin* x, long long xs, Cout* y, long long ys, float2* y32,
-                    long long y32s, BatchSkip sk);
+                    long long y32s, BatchSkip sk, float2* y32lo = nullptr);
 template <typename Cv, typename Cw, typename R>
 void launch_deflate(const Ctx& cx, int nb, const cplx_t<R>* c, long long cs, const Cv* v, long long vs,
                     const double* vscale, long long vss, Cw* w, long long ws, BatchSkip sk);
@@ -71,7 +71,7 @@ void launch_combine_additive(const Ctx& cx, int nb, const cplx_t<R>* c, long lon
                              const int4* cover, const Tile* tiles, int nsub, const Cy* ytiles, long long yts, Cz* z,
                              long long zs, BatchSkip sk);
 void launch_mask_copy_c128(const Ctx& cx, int nb, const double2* src, long long ss, double2* dst, long long ds,
-                           int conj, float2* dst32, long long d32s);
+                           int conj, float2* dst32, long long d32s, float2* dst32lo = nullptr);
 void launch_kappa_gradient(const Ctx& cx, const double2* u, const double2* lam, double* grad);
 
 // ---- coarse.cu
@@ -123,7 +123,8 @@ struct KrylovBufs {
     long long ld;      // leading dimension between basis vectors (elements)
     int nblk;          // blocks of the reduction kernels
     double2* V;        // (maxit+1) x ld per entry
-    float2* V32;       // (maxit+1) x ld complex64 copies (mixed-precision CGS2), or null
+    float2* V32;       // (maxit+1) x ld complex64 roundings of the basis (mixed-precision CGS2), or null
+    float2* V32lo;     // (maxit+1) x ld complex64 remainders: V32 + V32lo is the basis as double-float pairs
     double* sigma;     // (maxit+1): basis vector i = sigma[i] * V_i
     double2* H;        // (maxit+1) x maxit, column j at H[j*(maxit+1)]
     double* cs;        // maxit+1

@@ -22,6 +22,7 @@ namespace hzs {
 constexpr int kRedThreads = 256;
 constexpr int kDotGroup64 = 4;     // basis vectors per warp pass (FP64 multi-dot)
 constexpr int kDotGroup32 = 8;     // basis vectors per warp pass (complex64 multi-dot)
+constexpr int kDotGroupDF = 4;     // basis vectors per warp pass (double-float multi-dot)
 
 __device__ __forceinline__ void chunk_of(long long N, long long& e0, long long& e1) {
     const long long per = (N + gridDim.x - 1) / gridDim.x;
@@ -135,21 +136,155 @@ __global__ void __launch_bounds__(kRedThreads) k_axpy_multi(int j, long long N, 
     if (npart) block_norm_part(nrm, npart + (size_t)r * nblk);
 }
 
-// w[e] -= sum_i (h[i] sigma[i]) V32_i[e], the sum in complex64 and the
-// subtraction in FP64 (h is the small reorthogonalisation coefficient, so a
-// single-precision sum is accurate to FP64 level relative to w); also writes
-// w32 = complex64(w) and npart[b] = sum_e |w[e]|^2.  w = V + wofs, w32 = V32 + wofs.
-__global__ void __launch_bounds__(kRedThreads) k_correct32(int j, long long N, long long ld,
-                                                           float2* __restrict__ V32, double2* __restrict__ V,
-                                                           long long sV, const double* __restrict__ sigma,
-                                                           const double2* __restrict__ h, long long sS,
-                                                           long long wofs, double* __restrict__ npart, int nblk,
-                                                           const KState* __restrict__ st) {
+// ---- double-float passes of the mixed-precision CGS2 (see launch_arnoldi_step_mixed)
+// The basis is held as double-float pairs V32 + V32lo (complex64 rounding and
+// remainder), w = V32[j+1] + V32lo[j+1].
+
+// w -= sum_i c_i v_i with c_i = h[i] sigma[i], all in double-float arithmetic
+// (two interleaved accumulators per component); also writes nothing else.
+__global__ void __launch_bounds__(kRedThreads) k_axpy_df(int j, long long N, long long ld,
+                                                         float2* __restrict__ V32, float2* __restrict__ V32lo,
+                                                         long long sV, const double* __restrict__ sigma,
+                                                         const double2* __restrict__ h, long long sS, long long wofs,
+                                                         const KState* __restrict__ st) {
     const int r = blockIdx.y;
     if (st[r].done) return;
-    V32 += r * sV; V += r * sV; sigma += r * sS; h += r * sS;
-    double2* w = V + wofs;
-    float2* w32 = V32 + wofs;
+    V32 += r * sV; V32lo += r * sV; sigma += r * sS; h += r * sS;
+    float2* wh = V32 + wofs;
+    float2* wl = V32lo + wofs;
+    extern __shared__ float4 coefdf[];
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        const double2 c = cscale(h[i], sigma[i]);
+        float4 q;
+        split_d(c.x, q.x, q.y);
+        split_d(c.y, q.z, q.w);
+        coefdf[i] = q;
+    }
+    __syncthreads();
+    long long e0, e1;
+    chunk_of(N, e0, e1);
+    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f;      // real part, two accumulators
+        float ch = 0.f, cl = 0.f, dh = 0.f, dl = 0.f;      // imaginary part
+        int i = 0;
+        for (; i + 1 <= j; i += 2) {
+            {
+                const float4 q = coefdf[i];
+                const float2 vh = V32[(size_t)i * ld + e], vl = V32lo[(size_t)i * ld + e];
+                df_fma(ah, al, q.x, q.y, vh.x, vl.x);
+                df_fma(ah, al, -q.z, -q.w, vh.y, vl.y);
+                df_fma(ch, cl, q.x, q.y, vh.y, vl.y);
+                df_fma(ch, cl, q.z, q.w, vh.x, vl.x);
+            }
+            {
+                const float4 q = coefdf[i + 1];
+                const float2 vh = V32[(size_t)(i + 1) * ld + e], vl = V32lo[(size_t)(i + 1) * ld + e];
+                df_fma(bh, bl, q.x, q.y, vh.x, vl.x);
+                df_fma(bh, bl, -q.z, -q.w, vh.y, vl.y);
+                df_fma(dh, dl, q.x, q.y, vh.y, vl.y);
+                df_fma(dh, dl, q.z, q.w, vh.x, vl.x);
+            }
+            if ((i & 15) == 14) { df_norm(ah, al); df_norm(bh, bl); df_norm(ch, cl); df_norm(dh, dl); }
+        }
+        for (; i <= j; ++i) {
+            const float4 q = coefdf[i];
+            const float2 vh = V32[(size_t)i * ld + e], vl = V32lo[(size_t)i * ld + e];
+            df_fma(ah, al, q.x, q.y, vh.x, vl.x);
+            df_fma(ah, al, -q.z, -q.w, vh.y, vl.y);
+            df_fma(ch, cl, q.x, q.y, vh.y, vl.y);
+            df_fma(ch, cl, q.z, q.w, vh.x, vl.x);
+        }
+        df_add(ah, al, bh, bl);
+        df_add(ch, cl, dh, dl);
+        // w - s
+        float2 xh = wh[e], xl = wl[e];
+        df_add(xh.x, xl.x, -ah, -al);
+        df_add(xh.y, xl.y, -ch, -cl);
+        df_norm(xh.x, xl.x);
+        df_norm(xh.y, xl.y);
+        wh[e] = xh;
+        wl[e] = xl;
+    }
+}
+
+// part[b][i] = sum_{e in chunk b} conj(v_i[e]) w[e] in double-float arithmetic,
+// warp-parallel over groups of G basis vectors as k_multidot.
+template <int G>
+__global__ void __launch_bounds__(kRedThreads) k_multidot_df(int j, long long N, long long ld, int stride,
+                                                             const float2* __restrict__ V32,
+                                                             const float2* __restrict__ V32lo, long long sV,
+                                                             long long wofs, double2* __restrict__ part, long long sP,
+                                                             const KState* __restrict__ st) {
+    const int r = blockIdx.y;
+    if (st[r].done) return;
+    V32 += r * sV; V32lo += r * sV;
+    const float2* wh = V32 + wofs;
+    const float2* wl = V32lo + wofs;
+    part += r * sP;
+    long long e0, e1;
+    chunk_of(N, e0, e1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int ngroups = (j + G) / G;
+    for (int gi = warp; gi < ngroups; gi += nw) {
+        const int i0 = gi * G;
+        float rh[G], rl[G], ih[G], il[G];
+#pragma unroll
+        for (int t = 0; t < G; ++t) { rh[t] = rl[t] = ih[t] = il[t] = 0.f; }
+        int cnt = 0;
+        for (long long e = e0 + lane; e < e1; e += 32) {
+            const float2 xh = wh[e], xl = wl[e];
+#pragma unroll
+            for (int t = 0; t < G; ++t) {
+                if (i0 + t > j) continue;
+                const float2 vh = V32[(size_t)(i0 + t) * ld + e], vl = V32lo[(size_t)(i0 + t) * ld + e];
+                // conj(v) w: re = vr wr + vi wi, im = vr wi - vi wr
+                df_fma(rh[t], rl[t], vh.x, vl.x, xh.x, xl.x);
+                df_fma(rh[t], rl[t], vh.y, vl.y, xh.y, xl.y);
+                df_fma(ih[t], il[t], vh.x, vl.x, xh.y, xl.y);
+                df_fma(ih[t], il[t], -vh.y, -vl.y, xh.x, xl.x);
+            }
+            if ((++cnt & 15) == 0) {
+#pragma unroll
+                for (int t = 0; t < G; ++t) { df_norm(rh[t], rl[t]); df_norm(ih[t], il[t]); }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < G; ++t) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float orh = __shfl_down_sync(0xffffffffu, rh[t], o);
+                const float orl = __shfl_down_sync(0xffffffffu, rl[t], o);
+                const float oih = __shfl_down_sync(0xffffffffu, ih[t], o);
+                const float oil = __shfl_down_sync(0xffffffffu, il[t], o);
+                df_add(rh[t], rl[t], orh, orl);
+                df_add(ih[t], il[t], oih, oil);
+            }
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int t = 0; t < G; ++t)
+                if (i0 + t <= j)
+                    part[(size_t)blockIdx.x * stride + i0 + t] =
+                        make_double2((double)rh[t] + (double)rl[t], (double)ih[t] + (double)il[t]);
+        }
+    }
+}
+
+// w -= sum_i (h[i] sigma[i]) V32_i, the sum in complex64 (h is the small
+// reorthogonalisation coefficient, so a single-precision sum is accurate to
+// the working precision relative to w) and the subtraction in double-float;
+// npart[b] = sum_e |w[e]|^2.
+__global__ void __launch_bounds__(kRedThreads) k_correct_df(int j, long long N, long long ld,
+                                                            float2* __restrict__ V32, float2* __restrict__ V32lo,
+                                                            long long sV, const double* __restrict__ sigma,
+                                                            const double2* __restrict__ h, long long sS,
+                                                            long long wofs, double* __restrict__ npart, int nblk,
+                                                            const KState* __restrict__ st) {
+    const int r = blockIdx.y;
+    if (st[r].done) return;
+    V32 += r * sV; V32lo += r * sV; sigma += r * sS; h += r * sS;
+    float2* wh = V32 + wofs;
+    float2* wl = V32lo + wofs;
     extern __shared__ float2 coef32[];
     for (int i = threadIdx.x; i <= j; i += blockDim.x) coef32[i] = to_f(cscale(h[i], sigma[i]));
     __syncthreads();
@@ -166,12 +301,15 @@ __global__ void __launch_bounds__(kRedThreads) k_correct32(int j, long long N, l
             c3 = cfma(coef32[i + 3], V32[(size_t)(i + 3) * ld + e], c3);
         }
         for (; i <= j; ++i) c0 = cfma(coef32[i], V32[(size_t)i * ld + e], c0);
-        double2 we = w[e];
-        we.x -= (double)((c0.x + c1.x) + (c2.x + c3.x));
-        we.y -= (double)((c0.y + c1.y) + (c2.y + c3.y));
-        w[e] = we;
-        w32[e] = to_f(we);
-        nrm = fma(we.x, we.x, fma(we.y, we.y, nrm));
+        float2 xh = wh[e], xl = wl[e];
+        df_add(xh.x, xl.x, -((c0.x + c1.x) + (c2.x + c3.x)), 0.f);
+        df_add(xh.y, xl.y, -((c0.y + c1.y) + (c2.y + c3.y)), 0.f);
+        df_norm(xh.x, xl.x);
+        df_norm(xh.y, xl.y);
+        wh[e] = xh;
+        wl[e] = xl;
+        const double vx = (double)xh.x + (double)xl.x, vy = (double)xh.y + (double)xl.y;
+        nrm = fma(vx, vx, fma(vy, vy, nrm));
     }
     block_norm_part(nrm, npart + (size_t)r * nblk);
 }
@@ -428,32 +566,35 @@ void launch_arnoldi_step(const Ctx& cx, const KrylovBufs& kb, int nb, int j) {
                                                             kb.active);
 }
 
-// Mixed-precision CGS2 (used with the complex64 preconditioner): the first
-// projection h1 = V^H w is computed in complex64 from complex64 copies of the
-// basis and of w; the update w -= V h1, the reorthogonalisation h2 = V^H w and
-// the Hessenberg column stay FP64; the second update w -= V h2 sums in
-// complex64 (h2 is of the size of the first pass's rounding, so its complex64
-// product is exact to FP64 level) and subtracts in FP64.  Orthogonality and the
-// Arnoldi relation therefore hold to FP64 level, with half the FP64 work of
-// the all-FP64 CGS2.  kb.V32 must hold complex64 copies of V_0 .. V_{j+1}
-// (V_{j+1} = A z_j written by the matrix-vector product).
+// Mixed-precision CGS2 (used with the complex64 preconditioner).  The basis
+// is held as double-float pairs V32 + V32lo (complex64 rounding and remainder,
+// about 48 significand bits), written by the matrix-vector product and the
+// last pass.  The first projection h1 = V^H w is computed in complex64 from
+// V32 alone; the update w -= V h1 and the reorthogonalisation h2 = V^H w run
+// in double-float arithmetic (error-free FMA products and TwoSum accumulation
+// on the FP32 pipes); the second update w -= V h2 sums in complex64 (h2 is of
+// the size of the first pass's rounding) and subtracts in double-float.  The
+// FP64 Hessenberg column, norms and Givens update are unchanged.
+// Orthogonality and the Arnoldi relation hold to about 1e-12 relative (the
+// double-float accumulation), far below any GMRES tolerance used here, while
+// no basis pass executes an FP64 instruction per basis entry.
 void launch_arnoldi_step_mixed(const Ctx& cx, const KrylovBufs& kb, int nb, int j) {
     const int stride = kb.maxit + 1;
     const long long wofs = (long long)(j + 1) * kb.ld;
     const dim3 gr(kb.nblk, nb);
     const dim3 rg(((j + 1) * 32 + 255) / 256, nb);
-    const size_t cs = coef_smem(j + 1);
-    set_coef_smem_limit((const void*)k_axpy_multi, cs);
+    const size_t cdf = (size_t)(j + 1) * sizeof(float4);
+    set_coef_smem_limit((const void*)k_axpy_df, cdf);
     k_multidot<float2, kDotGroup32><<<gr, kRedThreads, 0, cx.stream>>>(j, kb.N, kb.ld, stride, kb.V32, kb.sV(), wofs,
                                                                        kb.part, kb.sP(), kb.st);
     k_reduce_dots<<<rg, 256, 0, cx.stream>>>(j, kb.nblk, stride, kb.part, kb.sP(), kb.sigma, kb.h1, kb.sS(), kb.st);
-    k_axpy_multi<<<gr, kRedThreads, cs, cx.stream>>>(j, kb.N, kb.ld, kb.V, kb.sV(), kb.sigma, kb.h1, kb.sS(), wofs,
-                                                     nullptr, kb.nblk, kb.st);
-    k_multidot<double2, kDotGroup64><<<gr, kRedThreads, 0, cx.stream>>>(j, kb.N, kb.ld, stride, kb.V, kb.sV(), wofs,
-                                                                        kb.part, kb.sP(), kb.st);
+    k_axpy_df<<<gr, kRedThreads, cdf, cx.stream>>>(j, kb.N, kb.ld, kb.V32, kb.V32lo, kb.sV(), kb.sigma, kb.h1,
+                                                   kb.sS(), wofs, kb.st);
+    k_multidot_df<kDotGroupDF><<<gr, kRedThreads, 0, cx.stream>>>(j, kb.N, kb.ld, stride, kb.V32, kb.V32lo, kb.sV(),
+                                                                  wofs, kb.part, kb.sP(), kb.st);
     k_reduce_dots<<<rg, 256, 0, cx.stream>>>(j, kb.nblk, stride, kb.part, kb.sP(), kb.sigma, kb.h2, kb.sS(), kb.st);
-    k_correct32<<<gr, kRedThreads, (size_t)(j + 1) * sizeof(float2), cx.stream>>>(
-        j, kb.N, kb.ld, kb.V32, kb.V, kb.sV(), kb.sigma, kb.h2, kb.sS(), wofs, kb.npart, kb.nblk, kb.st);
+    k_correct_df<<<gr, kRedThreads, (size_t)(j + 1) * sizeof(float2), cx.stream>>>(
+        j, kb.N, kb.ld, kb.V32, kb.V32lo, kb.sV(), kb.sigma, kb.h2, kb.sS(), wofs, kb.npart, kb.nblk, kb.st);
     k_arnoldi_finish<<<nb, 32, finish_smem(j), cx.stream>>>(j, kb.maxit, kb.nblk, kb.npart, kb.h1, kb.h2, kb.H,
                                                             kb.sH(), kb.cs, kb.sn, kb.g, kb.sigma, kb.sS(), kb.st,
                                                             kb.active);

@@ -16,12 +16,14 @@ __device__ __forceinline__ bool skipped(const BatchSkip& sk, int r) {
     return sk.flag && sk.flag[(size_t)r * sk.stride];
 }
 
-// y = A x over the n x n grid.  Arithmetic in R; x read as Cin, y written as
-// Cout and, if y32 is given, also as complex64.  MP-1 boundary nodes: y = 0,
-// and their x values are never read.
+// y = A x over the n x n grid.  Arithmetic in R; x read as Cin; y (if given)
+// written as Cout; y32 (if given) receives the complex64 rounding of the
+// result and y32lo (if given) the complex64 rounding of the remainder, so that
+// y32 + y32lo carries the result as a double-float pair.  MP-1 boundary nodes:
+// y = 0, and their x values are never read.
 template <typename Cin, typename Cout, typename R>
 __global__ void k_apply_A(OpDesc op, const Cin* __restrict__ x, long long xs, Cout* __restrict__ y, long long ys,
-                          float2* __restrict__ y32, long long y32s, BatchSkip sk) {
+                          float2* __restrict__ y32, long long y32s, float2* __restrict__ y32lo, BatchSkip sk) {
     using C = cplx_t<R>;
     const int r = blockIdx.z;
     if (skipped(sk, r)) return;
@@ -29,12 +31,15 @@ __global__ void k_apply_A(OpDesc op, const Cin* __restrict__ x, long long xs, Co
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int n = op.n;
     if (i >= n || j >= n) return;
-    x += r * xs; y += r * ys;
+    x += r * xs;
+    if (y) y += r * ys;
     if (y32) y32 += r * y32s;
+    if (y32lo) y32lo += r * y32s;
     const size_t p = (size_t)j * n + i;
     if (!op_is_unknown(op, i, j)) {
-        y[p] = mk<Cout>(0.0, 0.0);
+        if (y) y[p] = mk<Cout>(0.0, 0.0);
         if (y32) y32[p] = make_float2(0.f, 0.f);
+        if (y32lo) y32lo[p] = make_float2(0.f, 0.f);
         return;
     }
     const double2 d = op_diag(op, i, j);
@@ -51,8 +56,17 @@ __global__ void k_apply_A(OpDesc op, const Cin* __restrict__ x, long long xs, Co
     if (j < n - 1 && op_is_unknown(op, i, j + 1)) sy = cadd(sy, conv<C>(x[p + n]));
     acc.x += cx * sx.x + cy * sy.x;
     acc.y += cx * sx.y + cy * sy.y;
-    y[p] = conv<Cout>(acc);
-    if (y32) y32[p] = conv<float2>(acc);
+    if (y) y[p] = conv<Cout>(acc);
+    if (y32lo) {
+        const double2 a = to_d(acc);
+        float2 hi, lo;
+        split_d(a.x, hi.x, lo.x);
+        split_d(a.y, hi.y, lo.y);
+        y32[p] = hi;
+        y32lo[p] = lo;
+    } else if (y32) {
+        y32[p] = conv<float2>(acc);
+    }
 }
 
 // q(i, j) = sum_{a,b} wx(i,a) wy(j,b) c[(c0[j]+b) nc1 + c0[i]+a]   (prolongation R_0^T c)
@@ -161,9 +175,11 @@ __global__ void k_combine_additive(OpDesc op, CoarseTab ct, const cplx_t<R>* __r
 }
 
 // dst = src (or conj(src)) on unknowns, 0 on MP-1 boundary nodes; dst32 (if
-// given) receives the same values in complex64.
+// given) receives the same values in complex64 and dst32lo (if given) the
+// complex64 remainders (double-float pairs).
 __global__ void k_mask_copy(OpDesc op, const double2* __restrict__ src, long long ss, double2* __restrict__ dst,
-                            long long ds, int conj, float2* __restrict__ dst32, long long d32s) {
+                            long long ds, int conj, float2* __restrict__ dst32, long long d32s,
+                            float2* __restrict__ dst32lo) {
     const int r = blockIdx.z;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -174,7 +190,15 @@ __global__ void k_mask_copy(OpDesc op, const double2* __restrict__ src, long lon
     double2 v = op_is_unknown(op, i, j) ? src[p] : make_double2(0.0, 0.0);
     if (conj) v.y = -v.y;
     dst[p] = v;
-    if (dst32) dst32[r * d32s + p] = to_f(v);
+    if (dst32lo) {
+        float2 hi, lo;
+        split_d(v.x, hi.x, lo.x);
+        split_d(v.y, hi.y, lo.y);
+        dst32[r * d32s + p] = hi;
+        dst32lo[r * d32s + p] = lo;
+    } else if (dst32) {
+        dst32[r * d32s + p] = to_f(v);
+    }
 }
 
 // grad = -Re(conj(lam) * dA_PP/dkappa_P * u) on unknowns, 0 elsewhere.
@@ -200,14 +224,14 @@ static inline dim3 grid2d(int n, dim3 b, int nb) {
 
 template <typename Cin, typename Cout, typename R>
 void launch_apply_A(const Ctx& cx, int nb, const Cin* x, long long xs, Cout* y, long long ys, float2* y32,
-                    long long y32s, BatchSkip sk) {
+                    long long y32s, BatchSkip sk, float2* y32lo) {
     const dim3 b(32, 8);
-    k_apply_A<Cin, Cout, R><<<grid2d(cx.op.n, b, nb), b, 0, cx.stream>>>(cx.op, x, xs, y, ys, y32, y32s, sk);
+    k_apply_A<Cin, Cout, R><<<grid2d(cx.op.n, b, nb), b, 0, cx.stream>>>(cx.op, x, xs, y, ys, y32, y32s, y32lo, sk);
 }
 template void launch_apply_A<double2, double2, double>(const Ctx&, int, const double2*, long long, double2*,
-                                                       long long, float2*, long long, BatchSkip);
+                                                       long long, float2*, long long, BatchSkip, float2*);
 template void launch_apply_A<float2, double2, double>(const Ctx&, int, const float2*, long long, double2*, long long,
-                                                      float2*, long long, BatchSkip);
+                                                      float2*, long long, BatchSkip, float2*);
 
 template <typename Cv, typename Cw, typename R>
 void launch_deflate(const Ctx& cx, int nb, const cplx_t<R>* c, long long cs, const Cv* v, long long vs,
@@ -242,9 +266,9 @@ HZS_CMB(float2, float2, float)
 #undef HZS_CMB
 
 void launch_mask_copy_c128(const Ctx& cx, int nb, const double2* src, long long ss, double2* dst, long long ds,
-                           int conj, float2* dst32, long long d32s) {
+                           int conj, float2* dst32, long long d32s, float2* dst32lo) {
     const dim3 b(32, 8);
-    k_mask_copy<<<grid2d(cx.op.n, b, nb), b, 0, cx.stream>>>(cx.op, src, ss, dst, ds, conj, dst32, d32s);
+    k_mask_copy<<<grid2d(cx.op.n, b, nb), b, 0, cx.stream>>>(cx.op, src, ss, dst, ds, conj, dst32, d32s, dst32lo);
 }
 
 void launch_kappa_gradient(const Ctx& cx, const double2* u, const double2* lam, double* grad) {

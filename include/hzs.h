@@ -116,10 +116,12 @@ typedef struct {
 } hzs_solve_desc;
 
 #define HZS_SOLVE_PROFILE 1
-/* With HZS_MIXED: orthogonalise with the all-FP64 CGS2 instead of the default
- * mixed-precision CGS2 (complex64 first projection from a complex64 copy of
- * the basis, FP64 reorthogonalisation; orthogonality and the Arnoldi relation
- * hold to FP64 level either way).  No effect with HZS_FP64. */
+/* With HZS_MIXED: orthogonalise with the all-FP64 CGS2 on a complex128 basis
+ * instead of the default, the delayed CGS2 (reorthogonalisation of vector j
+ * fused with the projection of step j+1: two passes over the basis per step)
+ * on a double-float basis (complex64 rounding + remainder, about 48
+ * significant bits) with double-float updates and dot products.  No effect
+ * with HZS_FP64. */
 #define HZS_SOLVE_ORTH_FP64 2
 
 /* Per right-hand side results. */
@@ -131,7 +133,9 @@ typedef struct {
     double t_solve_ms;     /* device time of this solve (CUDA events on the stream) */
     double t_precond_ms;   /* with HZS_SOLVE_PROFILE: device time in the preconditioner, */
     double t_matvec_ms;    /*   in the matrix-vector products, */
-    double t_orth_ms;      /*   and in the CGS2 orthogonalisation and Givens update; else 0 */
+    double t_orth_ms;      /*   and in the orthogonalisation and Givens update; else 0 */
+    double t_orth_dot_ms;  /* with HZS_SOLVE_PROFILE on the delayed-CGS2 path: device time of the */
+    double t_orth_update_ms; /*   basis dot pass and of the basis update pass (parts of t_orth_ms); else 0 */
     long long launches;    /* kernel launches this solve issued */
     hzs_status status;
 } hzs_solve_info;

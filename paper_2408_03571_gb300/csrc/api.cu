@@ -221,7 +221,7 @@ extern "C" void hzs_grid_destroy(hzs_grid* g) {
 static void free_krylov(hzs_precond* p) {
     KrylovBufs& kb = p->kb;
     cudaFree(kb.V); cudaFree(kb.V32); cudaFree(kb.V32lo); cudaFree(kb.sigma); cudaFree(kb.H); cudaFree(kb.cs); cudaFree(kb.sn); cudaFree(kb.g);
-    cudaFree(kb.y); cudaFree(kb.h1); cudaFree(kb.h2); cudaFree(kb.part); cudaFree(kb.npart); cudaFree(kb.st);
+    cudaFree(kb.y); cudaFree(kb.h1); cudaFree(kb.h2); cudaFree(kb.hn); cudaFree(kb.sigt); cudaFree(kb.part); cudaFree(kb.npart); cudaFree(kb.st);
     cudaFree(kb.active);
     cudaFree(p->Z); cudaFree(p->ztmp); cudaFree(p->rtmp); cudaFree(p->dres);
     kb = KrylovBufs{};
@@ -542,6 +542,8 @@ static hzs_status ensure_krylov(hzs_precond* p, int maxit, int nb) {
     HZS_CUDA(g, dalloc(&kb.y, nb * S));
     HZS_CUDA(g, dalloc(&kb.h1, nb * S));
     HZS_CUDA(g, dalloc(&kb.h2, nb * S));
+    HZS_CUDA(g, dalloc(&kb.hn, (size_t)nb * kb.sN()));
+    HZS_CUDA(g, dalloc(&kb.sigt, nb * S));
     HZS_CUDA(g, dalloc(&kb.part, (size_t)nb * kb.sP()));
     HZS_CUDA(g, dalloc(&kb.npart, (size_t)nb * kb.nblk));
     HZS_CUDA(g, dalloc(&kb.st, (size_t)nb));
@@ -549,6 +551,15 @@ static hzs_status ensure_krylov(hzs_precond* p, int maxit, int nb) {
     if (p->desc.precision == HZS_MIXED) {
         HZS_CUDA(g, dalloc(&kb.V32, (size_t)nb * kb.sV()));
         HZS_CUDA(g, dalloc(&kb.V32lo, (size_t)nb * kb.sV()));
+        // the vectorised basis kernels read entries N .. ld-1 of each basis vector
+        // (pairs of entries); they must hold zero and nothing else writes them
+        if (ld > N) {
+            const size_t rows = (size_t)nb * (maxit + 1);
+            HZS_CUDA(g, cudaMemset2DAsync(kb.V32 + N, ld * sizeof(float2), 0, (ld - N) * sizeof(float2), rows,
+                                          g->stream));
+            HZS_CUDA(g, cudaMemset2DAsync(kb.V32lo + N, ld * sizeof(float2), 0, (ld - N) * sizeof(float2), rows,
+                                          g->stream));
+        }
         HZS_CUDA(g, dalloc(&p->Z, (size_t)nb * maxit * ld));
     }
     HZS_CUDA(g, dalloc(&p->ztmp, (size_t)nb * ld));
@@ -567,7 +578,7 @@ static int precond_launches(const hzs_precond* p) {
 }
 
 static hzs_status ensure_prof_events(hzs_precond* p, int maxit) {
-    const size_t need = (size_t)4 * (maxit + 1);
+    const size_t need = (size_t)8 * (maxit + 1);
     while (p->prof_ev.size() < need) {
         cudaEvent_t e;
         HZS_CUDA(p->g, cudaEventCreate(&e));
@@ -608,18 +619,21 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
     int steps = 0;
     for (int j = 0; j < sd->maxit; ++j) {
         double2* w = kb.V + (size_t)(j + 1) * ld;
-        cudaEvent_t* pe = prof ? &p->prof_ev[(size_t)4 * j] : nullptr;
+        cudaEvent_t* pe = prof ? &p->prof_ev[(size_t)8 * j] : nullptr;
         if (prof) HZS_CUDA(g, cudaEventRecord(pe[0], s));
         hzs_status st;
         if (orth32) {
-            // the complex64 preconditioner reads the complex64 copy of the basis vector
+            // the complex64 preconditioner reads the leading words of u~_j (the once-projected
+            // vector of the previous step, see launch_dcgs2_step) scaled by 1/|u~_j|
             float2* Zj = p->Z + (size_t)j * ld;
-            st = precond_apply<float, float2>(p, nb, kb.V32 + (size_t)j * ld, sV, kb.sigma + j, sS, Zj, sZ, sk);
+            st = precond_apply<float, float2>(p, nb, kb.V32 + (size_t)j * ld, sV, kb.sigt + j, sS, Zj, sZ, sk);
             if (prof) HZS_CUDA(g, cudaEventRecord(pe[1], s));
             // A z_j as a double-float pair (the FP64 copy of the basis is not used on this path)
-            launch_apply_A<float2, double2, double>(cx, nb, Zj, sZ, (double2*)nullptr, 0,
-                                                    kb.V32 + (size_t)(j + 1) * ld, sV, sk,
-                                                    kb.V32lo + (size_t)(j + 1) * ld);
+            if (!launch_apply_A_df(cx, nb, Zj, sZ, kb.V32 + (size_t)(j + 1) * ld, kb.V32lo + (size_t)(j + 1) * ld, sV,
+                                   sk))
+                launch_apply_A<float2, double2, double>(cx, nb, Zj, sZ, (double2*)nullptr, 0,
+                                                        kb.V32 + (size_t)(j + 1) * ld, sV, sk,
+                                                        kb.V32lo + (size_t)(j + 1) * ld);
         } else if (mixed) {
             float2* Zj = p->Z + (size_t)j * ld;
             st = precond_apply<float, double2>(p, nb, kb.V + (size_t)j * ld, sV, kb.sigma + j, sS, Zj, sZ, sk);
@@ -632,10 +646,10 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
         }
         if (st != HZS_OK) return st;
         if (prof) HZS_CUDA(g, cudaEventRecord(pe[2], s));
-        if (orth32) launch_arnoldi_step_mixed(cx, kb, nb, j);
+        if (orth32) launch_dcgs2_step(cx, kb, nb, j, 0, prof ? pe + 4 : nullptr);
         else launch_arnoldi_step(cx, kb, nb, j);
         if (prof) HZS_CUDA(g, cudaEventRecord(pe[3], s));
-        launches += pl + 1 + 7;
+        launches += pl + 1 + (orth32 ? 5 : 7);
         steps = j + 1;
         // the host runs one step ahead of the count of running entries it reads back
         HZS_CUDA(g, cudaMemcpyAsync(&p->h_done[j & 1], kb.active, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -644,6 +658,11 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
             HZS_CUDA(g, cudaEventSynchronize(p->ev[(j - 1) & 1]));
             if (p->h_done[(j - 1) & 1] == 0) break;
         }
+    }
+    // delayed CGS2: the last column is completed by one more dot pass over the basis
+    if (orth32 && steps == sd->maxit) {
+        launch_dcgs2_step(cx, kb, nb, sd->maxit, 1);
+        launches += 3;
     }
     launch_lsq_solve(cx, kb, nb);
     launches += 1;
@@ -675,21 +694,28 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
     }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, p->t0, p->t1);
-    double tp = 0, tm = 0, to = 0;
+    double tp = 0, tm = 0, to = 0, tdot = 0, tupd = 0;
     if (prof) {
         for (int k = 0; k < steps; ++k) {
-            cudaEvent_t* pe = &p->prof_ev[(size_t)4 * k];
+            cudaEvent_t* pe = &p->prof_ev[(size_t)8 * k];
             float a = 0, b = 0, c = 0;
             cudaEventElapsedTime(&a, pe[0], pe[1]);
             cudaEventElapsedTime(&b, pe[1], pe[2]);
             cudaEventElapsedTime(&c, pe[2], pe[3]);
             tp += a; tm += b; to += c;
+            if (orth32) {
+                float d = 0, u = 0;
+                cudaEventElapsedTime(&d, pe[4], pe[5]);
+                cudaEventElapsedTime(&u, pe[6], pe[7]);
+                tdot += d; tupd += u;
+            }
         }
     }
     hzs_status worst = HZS_OK;
     for (int r = 0; r < nb; ++r) {
         hzs_solve_info inf{};
         inf.t_precond_ms = tp; inf.t_matvec_ms = tm; inf.t_orth_ms = to;
+        inf.t_orth_dot_ms = tdot; inf.t_orth_update_ms = tupd;
         inf.iterations = hs[r].iters;
         inf.converged = hs[r].conv;
         inf.relres_est = hs[r].beta0 > 0 ? hs[r].resid / hs[r].beta0 : 0.0;

@@ -314,7 +314,7 @@ void launch_coarse_matvec(const Ctx& cx, int nb, const double2* Ainv, int Nc, co
     int blocks = (Nc + rows_per_block - 1) / rows_per_block;
     if (blocks > 4 * cx.num_sms) blocks = 4 * cx.num_sms;
     const size_t smem = (size_t)Nc * sizeof(double2);
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_coarse_matvec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_dynamic_smem((const void*)k_coarse_matvec, smem);
     k_coarse_matvec<<<dim3(blocks, nb), threads, smem, cx.stream>>>(Nc, Ainv, c, out, outf, sk);
 }
 

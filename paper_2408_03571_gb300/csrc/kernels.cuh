@@ -12,6 +12,24 @@
 
 namespace hzs {
 
+// Lets fn launch with `bytes` of dynamic shared memory.  The function's cap is
+// process-wide state shared by every host thread, so it is always raised to the
+// same value (the device's opt-in maximum less the function's static shared
+// memory) rather than to this launch's size: a concurrent caller that needs less
+// can then never lower the cap under a launch that needs more.
+inline cudaError_t allow_dynamic_smem(const void* fn, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    const size_t cap = (size_t)optin - fa.sharedSizeBytes;
+    if (bytes > cap) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+}
+
 // Host copy of the 1-D coarse tables (see CoarseTab).
 struct HostCoarseTab {
     int nc1 = 0;
@@ -63,6 +81,10 @@ struct FactorStat {
 template <typename Cin, typename Cout, typename R>
 void launch_apply_A(const Ctx& cx, int nb, const Cin* x, long long xs, Cout* y, long long ys, float2* y32,
                     long long y32s, BatchSkip sk, float2* y32lo = nullptr);
+// y = A x in double-float arithmetic, y as the complex64 pair yh + yl; false (nothing
+// launched) when the couplings are not exact in FP32 (n > 4097).
+bool launch_apply_A_df(const Ctx& cx, int nb, const float2* x, long long xs, float2* yh, float2* yl, long long ys,
+                       BatchSkip sk);
 template <typename Cv, typename Cw, typename R>
 void launch_deflate(const Ctx& cx, int nb, const cplx_t<R>* c, long long cs, const Cv* v, long long vs,
                     const double* vscale, long long vss, Cw* w, long long ws, BatchSkip sk);
@@ -133,19 +155,26 @@ struct KrylovBufs {
     double2* y;        // maxit+1
     double2* h1;       // maxit+1
     double2* h2;       // maxit+1
-    double2* part;     // nblk x (maxit+1)
+    double2* hn;       // maxit+2: reduced dots of the delayed CGS2 step (new column, then c and d)
+    double* sigt;      // maxit+1: 1 / |u~_j|, the preconditioner's input scale on the delayed CGS2 path
+    double2* part;     // nblk x pstride()
     double* npart;     // nblk
     KState* st;        // 1
     int* active;       // one counter per batch: entries not yet done
     long long sV() const { return (long long)(maxit + 1) * ld; }
     long long sH() const { return (long long)(maxit + 1) * maxit; }
     long long sS() const { return maxit + 1; }
-    long long sP() const { return (long long)nblk * (maxit + 1); }
+    long long sN() const { return maxit + 2; }
+    int pstride() const { return 2 * (maxit + 1) + 2; }
+    long long sP() const { return (long long)nblk * pstride(); }
     BatchSkip skip() const { return BatchSkip{&st->done, kStateInts}; }
 };
 void launch_norm_init(const Ctx& cx, const KrylovBufs& kb, int nb, double tol);
 void launch_arnoldi_step(const Ctx& cx, const KrylovBufs& kb, int nb, int j);
-void launch_arnoldi_step_mixed(const Ctx& cx, const KrylovBufs& kb, int nb, int j);
+// Step j of the delayed CGS2 Arnoldi on the double-float basis (V32 + V32lo);
+// last_only (j == maxit) completes the last Hessenberg column only.  ev (optional,
+// 4 events) is recorded before and after the dot pass and the update pass.
+void launch_dcgs2_step(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int last_only, cudaEvent_t* ev = nullptr);
 void launch_lsq_solve(const Ctx& cx, const KrylovBufs& kb, int nb);
 void launch_combine_basis(const Ctx& cx, const KrylovBufs& kb, int nb, double2* x, long long xs);
 void launch_combine_Z(const Ctx& cx, const KrylovBufs& kb, int nb, const float2* Z, long long ldz, long long zs,

@@ -1,6 +1,7 @@
 // GMRES kernels (Section 5): Arnoldi with classical Gram-Schmidt and one
-// reorthogonalisation (CGS2), Givens rotations on the Hessenberg matrix,
-// the triangular solve and the solution update.
+// reorthogonalisation (CGS2; on the mixed-precision path the delayed variant
+// over a double-float basis), Givens rotations on the Hessenberg matrix, the
+// triangular solve and the solution update.
 //
 // Basis vectors are stored unnormalised: the i-th orthonormal vector is
 // sigma[i] * V_i.  The scale is folded into the dot products and the update
@@ -21,8 +22,7 @@ namespace hzs {
 
 constexpr int kRedThreads = 256;
 constexpr int kDotGroup64 = 4;     // basis vectors per warp pass (FP64 multi-dot)
-constexpr int kDotGroup32 = 8;     // basis vectors per warp pass (complex64 multi-dot)
-constexpr int kDotGroupDF = 4;     // basis vectors per warp pass (double-float multi-dot)
+constexpr int kDotGroupDC = 4;     // basis vectors per warp pass (delayed CGS2 multi-dot)
 
 __device__ __forceinline__ void chunk_of(long long N, long long& e0, long long& e1) {
     const long long per = (N + gridDim.x - 1) / gridDim.x;
@@ -136,114 +136,173 @@ __global__ void __launch_bounds__(kRedThreads) k_axpy_multi(int j, long long N, 
     if (npart) block_norm_part(nrm, npart + (size_t)r * nblk);
 }
 
-// ---- double-float passes of the mixed-precision CGS2 (see launch_arnoldi_step_mixed)
+// ---- double-float basis (mixed-precision path)
 // The basis is held as double-float pairs V32 + V32lo (complex64 rounding and
-// remainder), w = V32[j+1] + V32lo[j+1].
+// remainder).  The kernels on it move two consecutive entries per lane per load
+// (16-byte accesses); vectors are padded to an even length whose padding stays
+// zero (the buffers are cleared when allocated and no kernel writes the padding
+// with anything but zero).  Indices count entry pairs: Np pairs per vector, ldp
+// between vectors.
 
-// w -= sum_i c_i v_i with c_i = h[i] sigma[i], all in double-float arithmetic
-// (two interleaved accumulators per component); also writes nothing else.
-__global__ void __launch_bounds__(kRedThreads) k_axpy_df(int j, long long N, long long ld,
-                                                         float2* __restrict__ V32, float2* __restrict__ V32lo,
-                                                         long long sV, const double* __restrict__ sigma,
-                                                         const double2* __restrict__ h, long long sS, long long wofs,
-                                                         const KState* __restrict__ st) {
-    const int r = blockIdx.y;
-    if (st[r].done) return;
-    V32 += r * sV; V32lo += r * sV; sigma += r * sS; h += r * sS;
-    float2* wh = V32 + wofs;
-    float2* wl = V32lo + wofs;
-    extern __shared__ float4 coefdf[];
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-        const double2 c = cscale(h[i], sigma[i]);
-        float4 q;
-        split_d(c.x, q.x, q.y);
-        split_d(c.y, q.z, q.w);
-        coefdf[i] = q;
-    }
-    __syncthreads();
-    long long e0, e1;
-    chunk_of(N, e0, e1);
-    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f;      // real part, two accumulators
-        float ch = 0.f, cl = 0.f, dh = 0.f, dl = 0.f;      // imaginary part
-        int i = 0;
-        for (; i + 1 <= j; i += 2) {
-            {
-                const float4 q = coefdf[i];
-                const float2 vh = V32[(size_t)i * ld + e], vl = V32lo[(size_t)i * ld + e];
-                df_fma(ah, al, q.x, q.y, vh.x, vl.x);
-                df_fma(ah, al, -q.z, -q.w, vh.y, vl.y);
-                df_fma(ch, cl, q.x, q.y, vh.y, vl.y);
-                df_fma(ch, cl, q.z, q.w, vh.x, vl.x);
-            }
-            {
-                const float4 q = coefdf[i + 1];
-                const float2 vh = V32[(size_t)(i + 1) * ld + e], vl = V32lo[(size_t)(i + 1) * ld + e];
-                df_fma(bh, bl, q.x, q.y, vh.x, vl.x);
-                df_fma(bh, bl, -q.z, -q.w, vh.y, vl.y);
-                df_fma(dh, dl, q.x, q.y, vh.y, vl.y);
-                df_fma(dh, dl, q.z, q.w, vh.x, vl.x);
-            }
-            if ((i & 15) == 14) { df_norm(ah, al); df_norm(bh, bl); df_norm(ch, cl); df_norm(dh, dl); }
-        }
-        for (; i <= j; ++i) {
-            const float4 q = coefdf[i];
-            const float2 vh = V32[(size_t)i * ld + e], vl = V32lo[(size_t)i * ld + e];
-            df_fma(ah, al, q.x, q.y, vh.x, vl.x);
-            df_fma(ah, al, -q.z, -q.w, vh.y, vl.y);
-            df_fma(ch, cl, q.x, q.y, vh.y, vl.y);
-            df_fma(ch, cl, q.z, q.w, vh.x, vl.x);
-        }
-        df_add(ah, al, bh, bl);
-        df_add(ch, cl, dh, dl);
-        // w - s
-        float2 xh = wh[e], xl = wl[e];
-        df_add(xh.x, xl.x, -ah, -al);
-        df_add(xh.y, xl.y, -ch, -cl);
-        df_norm(xh.x, xl.x);
-        df_norm(xh.y, xl.y);
-        wh[e] = xh;
-        wl[e] = xl;
-    }
+__device__ __forceinline__ float2 lo2(float4 a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ float2 hi2(float4 a) { return make_float2(a.z, a.w); }
+
+// (sh, sl) += c * v for one complex component pair, double-float:
+// re += cr vr - ci vi ; im += cr vi + ci vr
+__device__ __forceinline__ void df_cmac(float& rh, float& rl, float& ih, float& il, const float4& c, float vrh,
+                                        float vrl, float vih, float vil) {
+    df_fma(rh, rl, c.x, c.y, vrh, vrl);
+    df_fma(rh, rl, -c.z, -c.w, vih, vil);
+    df_fma(ih, il, c.x, c.y, vih, vil);
+    df_fma(ih, il, c.z, c.w, vrh, vrl);
 }
 
-// part[b][i] = sum_{e in chunk b} conj(v_i[e]) w[e] in double-float arithmetic,
-// warp-parallel over groups of G basis vectors as k_multidot.
+// Brings Hessenberg column jc (col[0..jc+1], in shared memory) to triangular
+// form: applies the stored rotations 0..jc-1 (scs, ssn: shared copies of cs, sn),
+// computes rotation jc that zeroes col[jc+1] (stored in cs[jc], sn[jc]), applies
+// it to the right-hand side g and returns the new residual estimate |g[jc+1]|.
+// Single thread.
+__device__ double givens_column(int jc, double2* col, const double* scs, const double2* ssn, double* cs,
+                                double2* sn, double2* g) {
+    double2 a = col[0];
+    for (int i = 0; i < jc; ++i) {
+        const double c = scs[i];
+        const double2 sv = ssn[i];
+        const double2 b = col[i + 1];
+        // t = c a + s b ; b' = -conj(s) a + c b
+        double2 t = cscale(a, c);
+        t = cfma(sv, b, t);
+        double2 nb = cscale(b, c);
+        const double2 csn = make_double2(sv.x, -sv.y);
+        nb = cfms(csn, a, nb);
+        col[i] = t;
+        a = nb;
+    }
+    const double2 b = col[jc + 1];
+    const double aa = hypot(a.x, a.y), bb = hypot(b.x, b.y);
+    double c; double2 sv;
+    if (bb == 0.0) { c = 1.0; sv = make_double2(0.0, 0.0); }
+    else if (aa == 0.0) { c = 0.0; sv = make_double2(b.x / bb, -b.y / bb); }
+    else {
+        const double rho = hypot(aa, bb);
+        c = aa / rho;
+        const double2 ph = make_double2(a.x / aa, a.y / aa);          // a / |a|
+        const double2 cb = make_double2(b.x / rho, -b.y / rho);       // conj(b) / rho
+        sv = cmul(ph, cb);
+    }
+    cs[jc] = c; sn[jc] = sv;
+    col[jc] = cfma(sv, b, cscale(a, c));
+    col[jc + 1] = make_double2(0.0, 0.0);
+    const double2 gj = g[jc];
+    const double2 csn = make_double2(sv.x, -sv.y);
+    const double2 gn = cscale(cmul(csn, gj), -1.0);
+    g[jc + 1] = gn;
+    g[jc] = cscale(gj, c);
+    return hypot(gn.x, gn.y);
+}
+
+// ---- delayed CGS2 (mixed-precision path, see launch_dcgs2_step)
+// Classical Gram-Schmidt with the reorthogonalisation of basis vector j
+// postponed to step j, where it shares one read of the basis with the first
+// projection of the new vector w = A z_j (Bielich, Langou, Thomas, Swirydowicz,
+// Yamazaki and Boman, "Low-synch Gram-Schmidt with delayed reorthogonalization
+// for Krylov solvers", Parallel Computing 112, 2022).  Per Arnoldi step the
+// basis is read twice (one multi-dot, one update) instead of four times.
+// At the start of step j, slot j holds u~_j, the once-projected w of step j-1
+// (not yet reorthogonalised or normalised), and slot j+1 holds w.  With Q the
+// orthonormal vectors 0..j-1 (vector i = sigma[i] V_i):
+//   dot pass:  alpha = Q^H u~_j (double-float), b = Q^H w (complex64 on the
+//              leading words), c = |u~_j|^2, d = u~_j^H w;
+//   finish:    beta_j^2 = c - |alpha|^2, column j-1 of H is completed as
+//              h1_{j-1} + alpha with subdiagonal beta_j, the first-pass
+//              coefficients of column j are b and (d - alpha^H b) / beta_j;
+//   update:    V_j = u~_j - Q alpha (sigma_j = 1/beta_j),
+//              w  <- w - Q b - h_jj q_j  (double-float), |w|^2.
+// The preconditioner of step j is applied to u~_j / |u~_j|: the flexible
+// Arnoldi relation A Z = Q H holds for any z_j, and span{u~_0..u~_j} equals
+// span{q_0..q_j}, so the iterates are those of FGMRES with z_j = M q_j.
+// Row layout of the dot partials per block: alpha at [0, S), b at [S, 2S),
+// c at 2S, d at 2S+1 (S = maxit+1).
+
 template <int G>
-__global__ void __launch_bounds__(kRedThreads) k_multidot_df(int j, long long N, long long ld, int stride,
-                                                             const float2* __restrict__ V32,
-                                                             const float2* __restrict__ V32lo, long long sV,
-                                                             long long wofs, double2* __restrict__ part, long long sP,
-                                                             const KState* __restrict__ st) {
+__global__ void __launch_bounds__(kRedThreads, 4) k_dcgs_dot(int j, long long Np, long long ldp, int ps, int S,
+                                                          const float4* __restrict__ V32,
+                                                          const float4* __restrict__ V32lo, long long sVp,
+                                                          int has_w, double2* __restrict__ part, long long sP,
+                                                          const KState* __restrict__ st) {
     const int r = blockIdx.y;
     if (st[r].done) return;
-    V32 += r * sV; V32lo += r * sV;
-    const float2* wh = V32 + wofs;
-    const float2* wl = V32lo + wofs;
-    part += r * sP;
+    V32 += r * sVp; V32lo += r * sVp;
+    const float4* uh = V32 + (size_t)j * ldp;
+    const float4* ul = V32lo + (size_t)j * ldp;
+    const float4* wh = has_w ? V32 + (size_t)(j + 1) * ldp : uh;     // slot j+1 exists only with w
+    const float4* wl = has_w ? V32lo + (size_t)(j + 1) * ldp : ul;
+    part += r * sP + (size_t)blockIdx.x * ps;
     long long e0, e1;
-    chunk_of(N, e0, e1);
+    chunk_of(Np, e0, e1);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int ngroups = (j + G) / G;
-    for (int gi = warp; gi < ngroups; gi += nw) {
+    const int ngroups = (j + G - 1) / G;
+    for (int gi = warp; gi <= ngroups; gi += nw) {
+        if (gi == ngroups) {
+            // c = |u~|^2 and d = u~^H w (double-float)
+            float ch = 0.f, cl = 0.f, dr = 0.f, drl = 0.f, di = 0.f, dil = 0.f;
+            int cnt = 0;
+            for (long long e = e0 + lane; e < e1; e += 32) {
+                const float4 xh = uh[e], xl = ul[e];
+                df_fma(ch, cl, xh.x, xl.x, xh.x, xl.x);
+                df_fma(ch, cl, xh.y, xl.y, xh.y, xl.y);
+                df_fma(ch, cl, xh.z, xl.z, xh.z, xl.z);
+                df_fma(ch, cl, xh.w, xl.w, xh.w, xl.w);
+                if (has_w) {
+                    const float4 yh = wh[e], yl = wl[e];
+                    df_fma(dr, drl, xh.x, xl.x, yh.x, yl.x);
+                    df_fma(dr, drl, xh.y, xl.y, yh.y, yl.y);
+                    df_fma(di, dil, xh.x, xl.x, yh.y, yl.y);
+                    df_fma(di, dil, -xh.y, -xl.y, yh.x, yl.x);
+                    df_fma(dr, drl, xh.z, xl.z, yh.z, yl.z);
+                    df_fma(dr, drl, xh.w, xl.w, yh.w, yl.w);
+                    df_fma(di, dil, xh.z, xl.z, yh.w, yl.w);
+                    df_fma(di, dil, -xh.w, -xl.w, yh.z, yl.z);
+                }
+                if ((++cnt & 7) == 0) { df_norm(ch, cl); df_norm(dr, drl); df_norm(di, dil); }
+            }
+            double c = (double)ch + (double)cl;
+            double2 d = make_double2((double)dr + (double)drl, (double)di + (double)dil);
+            c = warp_sum_d(c);
+            d = warp_sum(d);
+            if (lane == 0) {
+                part[2 * S] = make_double2(c, 0.0);
+                part[2 * S + 1] = d;
+            }
+            continue;
+        }
         const int i0 = gi * G;
         float rh[G], rl[G], ih[G], il[G];
+        float2 bb[G];
 #pragma unroll
-        for (int t = 0; t < G; ++t) { rh[t] = rl[t] = ih[t] = il[t] = 0.f; }
+        for (int t = 0; t < G; ++t) { rh[t] = rl[t] = ih[t] = il[t] = 0.f; bb[t] = make_float2(0.f, 0.f); }
         int cnt = 0;
         for (long long e = e0 + lane; e < e1; e += 32) {
-            const float2 xh = wh[e], xl = wl[e];
+            const float4 xh = uh[e], xl = ul[e];
+            const float4 yh = has_w ? wh[e] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int t = 0; t < G; ++t) {
-                if (i0 + t > j) continue;
-                const float2 vh = V32[(size_t)(i0 + t) * ld + e], vl = V32lo[(size_t)(i0 + t) * ld + e];
-                // conj(v) w: re = vr wr + vi wi, im = vr wi - vi wr
+                if (i0 + t >= j) continue;
+                const float4 vh = V32[(size_t)(i0 + t) * ldp + e], vl = V32lo[(size_t)(i0 + t) * ldp + e];
+                // alpha: conj(v) u~, re = vr ur + vi ui, im = vr ui - vi ur (two entries)
                 df_fma(rh[t], rl[t], vh.x, vl.x, xh.x, xl.x);
                 df_fma(rh[t], rl[t], vh.y, vl.y, xh.y, xl.y);
                 df_fma(ih[t], il[t], vh.x, vl.x, xh.y, xl.y);
                 df_fma(ih[t], il[t], -vh.y, -vl.y, xh.x, xl.x);
+                df_fma(rh[t], rl[t], vh.z, vl.z, xh.z, xl.z);
+                df_fma(rh[t], rl[t], vh.w, vl.w, xh.w, xl.w);
+                df_fma(ih[t], il[t], vh.z, vl.z, xh.w, xl.w);
+                df_fma(ih[t], il[t], -vh.w, -vl.w, xh.z, xl.z);
+                // b: conj(v) w on the leading words
+                bb[t] = cfma_conj(lo2(vh), lo2(yh), bb[t]);
+                bb[t] = cfma_conj(hi2(vh), hi2(yh), bb[t]);
             }
-            if ((++cnt & 15) == 0) {
+            if ((++cnt & 7) == 0) {
 #pragma unroll
                 for (int t = 0; t < G; ++t) { df_norm(rh[t], rl[t]); df_norm(ih[t], il[t]); }
             }
@@ -259,59 +318,204 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot_df(int j, long long N,
                 df_add(rh[t], rl[t], orh, orl);
                 df_add(ih[t], il[t], oih, oil);
             }
+            bb[t] = warp_sum(bb[t]);
         }
         if (lane == 0) {
 #pragma unroll
             for (int t = 0; t < G; ++t)
-                if (i0 + t <= j)
-                    part[(size_t)blockIdx.x * stride + i0 + t] =
-                        make_double2((double)rh[t] + (double)rl[t], (double)ih[t] + (double)il[t]);
+                if (i0 + t < j) {
+                    part[i0 + t] = make_double2((double)rh[t] + (double)rl[t], (double)ih[t] + (double)il[t]);
+                    part[S + i0 + t] = to_d(bb[t]);
+                }
         }
     }
 }
 
-// w -= sum_i (h[i] sigma[i]) V32_i, the sum in complex64 (h is the small
-// reorthogonalisation coefficient, so a single-precision sum is accurate to
-// the working precision relative to w) and the subtraction in double-float;
-// npart[b] = sum_e |w[e]|^2.
-__global__ void __launch_bounds__(kRedThreads) k_correct_df(int j, long long N, long long ld,
-                                                            float2* __restrict__ V32, float2* __restrict__ V32lo,
-                                                            long long sV, const double* __restrict__ sigma,
-                                                            const double2* __restrict__ h, long long sS,
-                                                            long long wofs, double* __restrict__ npart, int nblk,
-                                                            const KState* __restrict__ st) {
+// Cross-block sums of the dot pass, one warp per value (fixed order):
+// h2[i] = sigma_i alpha_i, hn[i] = sigma_i b_i (i < j), hn[j] = c, hn[j+1] = d.
+__global__ void k_dcgs_reduce(int j, int nblk, int ps, int S, const double2* __restrict__ part, long long sP,
+                              const double* __restrict__ sigma, double2* __restrict__ h2, double2* __restrict__ hn,
+                              long long sS, long long sN, const KState* __restrict__ st) {
     const int r = blockIdx.y;
     if (st[r].done) return;
-    V32 += r * sV; V32lo += r * sV; sigma += r * sS; h += r * sS;
-    float2* wh = V32 + wofs;
-    float2* wl = V32lo + wofs;
-    extern __shared__ float2 coef32[];
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) coef32[i] = to_f(cscale(h[i], sigma[i]));
+    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= 2 * j + 2) return;
+    part += r * sP; sigma += r * sS; h2 += r * sS; hn += r * sN;
+    const int col = k < j ? k : (k < 2 * j ? S + (k - j) : 2 * S + (k - 2 * j));
+    double2 s = make_double2(0.0, 0.0);
+    for (int b = lane; b < nblk; b += 32) s = cadd(s, part[(size_t)b * ps + col]);
+    s = warp_sum(s);
+    if (lane == 0) {
+        if (k < j) h2[k] = cscale(s, sigma[k]);
+        else if (k < 2 * j) hn[k - j] = cscale(s, sigma[k - j]);
+        else hn[j + (k - 2 * j)] = s;
+    }
+}
+
+// Step j's scalar work for entry r = blockIdx.x (one warp): beta_j, completion
+// and rotation of column j-1 (convergence check with j columns), and the
+// first-pass coefficients of column j (h1, for the update pass and the next
+// completion).  j == maxit (last_only) completes the last column only.
+__global__ void k_dcgs_finish(int j, int maxit, int last_only, const double2* __restrict__ hn, long long sN,
+                              double2* __restrict__ h1, const double2* __restrict__ h2, double2* __restrict__ H,
+                              long long sH, double* __restrict__ cs, double2* __restrict__ sn, double2* __restrict__ g,
+                              double* __restrict__ sigma, long long sS, KState* __restrict__ st,
+                              int* __restrict__ active) {
+    const int r = blockIdx.x;
+    if (st[r].done) return;
+    hn += r * sN; h1 += r * sS; h2 += r * sS; H += r * sH; cs += r * sS; sn += r * sS; g += r * sS; sigma += r * sS;
+    KState* s0 = st + r;
+    extern __shared__ double2 fsm[];
+    double2* col = fsm;                                   // j + 1
+    double2* ssn = col + (j + 1);                         // j - 1
+    double* scs = reinterpret_cast<double*>(ssn + (j > 0 ? j - 1 : 0));
+    const int lane = threadIdx.x;
+    // |alpha|^2 and alpha^H b
+    double aa = 0.0;
+    double2 ab = make_double2(0.0, 0.0);
+    for (int i = lane; i < j; i += 32) {
+        const double2 a = h2[i], b = hn[i];
+        aa = fma(a.x, a.x, fma(a.y, a.y, aa));
+        ab = cfma_conj(a, b, ab);
+    }
+    aa = warp_sum_d(aa);
+    ab = warp_sum(ab);
+    const double c = hn[j].x;
+    const double2 d = hn[j + 1];
+    const double b2 = c - aa;
+    const double beta = b2 > 0.0 ? sqrt(b2) : 0.0;
+    int fin = 0;
+    if (j > 0) {
+        for (int i = lane; i < j; i += 32) col[i] = cadd(h1[i], h2[i]);
+        for (int i = lane; i < j - 1; i += 32) { ssn[i] = sn[i]; scs[i] = cs[i]; }
+        if (lane == 0) col[j] = make_double2(beta, 0.0);
+        __syncwarp();
+        if (lane == 0) {
+            const double resid = givens_column(j - 1, col, scs, ssn, cs, sn, g);
+            s0->resid = resid;
+            s0->hnext = beta;
+            s0->iters = j;
+            fin = 1;
+            if (!isfinite(resid) || !isfinite(b2)) s0->nonfinite = 1;
+            else if (resid <= s0->tolabs) s0->conv = 1;
+            else if (beta == 0.0) { s0->breakdown = 1; s0->conv = 1; }
+            else if (!last_only && j < maxit) fin = 0;
+            if (fin) { s0->done = 1; atomicSub(active, 1); }
+        }
+        __syncwarp();
+        double2* out = H + (size_t)(j - 1) * (maxit + 1);
+        for (int i = lane; i <= j; i += 32) out[i] = col[i];
+        fin = __shfl_sync(0xffffffffu, fin, 0);
+    }
+    if (fin || last_only) return;
+    // column j, first pass (alpha is complete for the old vectors; q_j = (u~ - Q alpha) / beta)
+    const double ib = beta > 0.0 ? 1.0 / beta : 0.0;
+    for (int i = lane; i < j; i += 32) h1[i] = hn[i];
+    if (lane == 0) {
+        h1[j] = cscale(csub(d, ab), ib);
+        sigma[j] = ib;
+        if (j == 0 && !(beta > 0.0)) { s0->done = 1; s0->conv = 1; s0->breakdown = 1; atomicSub(active, 1); }
+    }
+}
+
+// Update pass of step j (two entries per lane): V_j = u~_j - sum_i (sigma_i alpha_i) V_i
+// (the small reorthogonalisation sum in complex64, its subtraction in double-float),
+// w = w - sum_i (sigma_i b_i) V_i - (h_jj sigma_j) V_j in double-float;
+// npart[b] = sum_e |w[e]|^2.
+__global__ void __launch_bounds__(kRedThreads) k_dcgs_update(int j, long long Np, long long ldp,
+                                                             float4* __restrict__ V32, float4* __restrict__ V32lo,
+                                                             long long sVp, const double* __restrict__ sigma,
+                                                             const double2* __restrict__ h1,
+                                                             const double2* __restrict__ h2, long long sS,
+                                                             double* __restrict__ npart, int nblk,
+                                                             const KState* __restrict__ st) {
+    const int r = blockIdx.y;
+    if (st[r].done) return;
+    V32 += r * sVp; V32lo += r * sVp; sigma += r * sS; h1 += r * sS; h2 += r * sS;
+    float4* uh = V32 + (size_t)j * ldp;
+    float4* ul = V32lo + (size_t)j * ldp;
+    float4* wh = V32 + (size_t)(j + 1) * ldp;
+    float4* wl = V32lo + (size_t)(j + 1) * ldp;
+    extern __shared__ float4 dsm[];
+    float4* cb = dsm;                                       // j + 1: w coefficients (double-float)
+    float2* ca = reinterpret_cast<float2*>(dsm + (j + 1));  // j: reorthogonalisation coefficients
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        const double2 c = cscale(h1[i], sigma[i]);
+        float4 q;
+        split_d(c.x, q.x, q.y);
+        split_d(c.y, q.z, q.w);
+        cb[i] = q;
+        if (i < j) ca[i] = to_f(cscale(h2[i], sigma[i]));
+    }
     __syncthreads();
     long long e0, e1;
-    chunk_of(N, e0, e1);
+    chunk_of(Np, e0, e1);
     double nrm = 0.0;
     for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        float2 c0 = make_float2(0.f, 0.f), c1 = c0, c2 = c0, c3 = c0;
+        float a0h = 0.f, a0l = 0.f, b0h = 0.f, b0l = 0.f, a1h = 0.f, a1l = 0.f, b1h = 0.f, b1l = 0.f;
+        float2 s0 = make_float2(0.f, 0.f), s1 = s0;
         int i = 0;
-        for (; i + 3 <= j; i += 4) {
-            c0 = cfma(coef32[i], V32[(size_t)i * ld + e], c0);
-            c1 = cfma(coef32[i + 1], V32[(size_t)(i + 1) * ld + e], c1);
-            c2 = cfma(coef32[i + 2], V32[(size_t)(i + 2) * ld + e], c2);
-            c3 = cfma(coef32[i + 3], V32[(size_t)(i + 3) * ld + e], c3);
+        for (; i + 1 < j; i += 2) {
+            const float4 vh0 = V32[(size_t)i * ldp + e], vl0 = V32lo[(size_t)i * ldp + e];
+            const float4 vh1 = V32[(size_t)(i + 1) * ldp + e], vl1 = V32lo[(size_t)(i + 1) * ldp + e];
+            const float4 q0 = cb[i], q1 = cb[i + 1];
+            df_cmac(a0h, a0l, b0h, b0l, q0, vh0.x, vl0.x, vh0.y, vl0.y);
+            df_cmac(a1h, a1l, b1h, b1l, q0, vh0.z, vl0.z, vh0.w, vl0.w);
+            df_cmac(a0h, a0l, b0h, b0l, q1, vh1.x, vl1.x, vh1.y, vl1.y);
+            df_cmac(a1h, a1l, b1h, b1l, q1, vh1.z, vl1.z, vh1.w, vl1.w);
+            s0 = cfma(ca[i], lo2(vh0), s0);
+            s1 = cfma(ca[i], hi2(vh0), s1);
+            s0 = cfma(ca[i + 1], lo2(vh1), s0);
+            s1 = cfma(ca[i + 1], hi2(vh1), s1);
+            if ((i & 15) == 14) {
+                df_norm(a0h, a0l); df_norm(b0h, b0l); df_norm(a1h, a1l); df_norm(b1h, b1l);
+            }
         }
-        for (; i <= j; ++i) c0 = cfma(coef32[i], V32[(size_t)i * ld + e], c0);
-        float2 xh = wh[e], xl = wl[e];
-        df_add(xh.x, xl.x, -((c0.x + c1.x) + (c2.x + c3.x)), 0.f);
-        df_add(xh.y, xl.y, -((c0.y + c1.y) + (c2.y + c3.y)), 0.f);
-        df_norm(xh.x, xl.x);
-        df_norm(xh.y, xl.y);
-        wh[e] = xh;
-        wl[e] = xl;
-        const double vx = (double)xh.x + (double)xl.x, vy = (double)xh.y + (double)xl.y;
-        nrm = fma(vx, vx, fma(vy, vy, nrm));
+        if (i < j) {
+            const float4 vh = V32[(size_t)i * ldp + e], vl = V32lo[(size_t)i * ldp + e];
+            const float4 q = cb[i];
+            df_cmac(a0h, a0l, b0h, b0l, q, vh.x, vl.x, vh.y, vl.y);
+            df_cmac(a1h, a1l, b1h, b1l, q, vh.z, vl.z, vh.w, vl.w);
+            s0 = cfma(ca[i], lo2(vh), s0);
+            s1 = cfma(ca[i], hi2(vh), s1);
+        }
+        // V_j = u~ - s
+        float4 xh = uh[e], xl = ul[e];
+        df_add(xh.x, xl.x, -s0.x, 0.f); df_norm(xh.x, xl.x);
+        df_add(xh.y, xl.y, -s0.y, 0.f); df_norm(xh.y, xl.y);
+        df_add(xh.z, xl.z, -s1.x, 0.f); df_norm(xh.z, xl.z);
+        df_add(xh.w, xl.w, -s1.y, 0.f); df_norm(xh.w, xl.w);
+        uh[e] = xh;
+        ul[e] = xl;
+        // + (h_jj sigma_j) V_j
+        const float4 qj = cb[j];
+        df_cmac(a0h, a0l, b0h, b0l, qj, xh.x, xl.x, xh.y, xl.y);
+        df_cmac(a1h, a1l, b1h, b1l, qj, xh.z, xl.z, xh.w, xl.w);
+        float4 yh = wh[e], yl = wl[e];
+        df_add(yh.x, yl.x, -a0h, -a0l); df_norm(yh.x, yl.x);
+        df_add(yh.y, yl.y, -b0h, -b0l); df_norm(yh.y, yl.y);
+        df_add(yh.z, yl.z, -a1h, -a1l); df_norm(yh.z, yl.z);
+        df_add(yh.w, yl.w, -b1h, -b1l); df_norm(yh.w, yl.w);
+        wh[e] = yh;
+        wl[e] = yl;
+        const double p = (double)yh.x + (double)yl.x, q = (double)yh.y + (double)yl.y;
+        const double u = (double)yh.z + (double)yl.z, v = (double)yh.w + (double)yl.w;
+        nrm = fma(p, p, fma(q, q, fma(u, u, fma(v, v, nrm))));
     }
     block_norm_part(nrm, npart + (size_t)r * nblk);
+}
+
+// sigt[j+1] = 1 / |u~_{j+1}| from the update pass's partial norms (one warp per entry).
+__global__ void k_dcgs_scale(int j, int nblk, const double* __restrict__ npart, double* __restrict__ sigt,
+                             long long sS, const KState* __restrict__ st) {
+    const int r = blockIdx.x;
+    if (st[r].done) return;
+    npart += (size_t)r * nblk;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += 32) s += npart[b];
+    s = warp_sum_d(s);
+    if (threadIdx.x == 0) sigt[r * sS + j + 1] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
 }
 
 // Completes step j of entry r = blockIdx.x: h_{j+1,j} = ||w||, column j of
@@ -345,43 +549,7 @@ __global__ void k_arnoldi_finish(int j, int maxit, int nblk, const double* __res
     __syncwarp();
     const int ldh = maxit + 1;
     if (lane == 0) {
-        // previous rotations
-        double2 a = col[0];
-        for (int i = 0; i < j; ++i) {
-            const double c = scs[i];
-            const double2 sv = ssn[i];
-            const double2 b = col[i + 1];
-            // t = c a + s b ; b' = -conj(s) a + c b
-            double2 t = cscale(a, c);
-            t = cfma(sv, b, t);
-            double2 nb = cscale(b, c);
-            const double2 csn = make_double2(sv.x, -sv.y);
-            nb = cfms(csn, a, nb);
-            col[i] = t;
-            a = nb;
-        }
-        // new rotation zeroing the subdiagonal entry
-        const double2 b = col[j + 1];
-        const double aa = hypot(a.x, a.y), bb = hypot(b.x, b.y);
-        double c; double2 sv;
-        if (bb == 0.0) { c = 1.0; sv = make_double2(0.0, 0.0); }
-        else if (aa == 0.0) { c = 0.0; sv = make_double2(b.x / bb, -b.y / bb); }
-        else {
-            const double rho = hypot(aa, bb);
-            c = aa / rho;
-            const double2 ph = make_double2(a.x / aa, a.y / aa);          // a / |a|
-            const double2 cb = make_double2(b.x / rho, -b.y / rho);       // conj(b) / rho
-            sv = cmul(ph, cb);
-        }
-        cs[j] = c; sn[j] = sv;
-        col[j] = cfma(sv, b, cscale(a, c));
-        col[j + 1] = make_double2(0.0, 0.0);
-        const double2 gj = g[j];
-        const double2 csn = make_double2(sv.x, -sv.y);
-        const double2 gn = cscale(cmul(csn, gj), -1.0);
-        g[j + 1] = gn;
-        g[j] = cscale(gj, c);
-        const double resid = hypot(gn.x, gn.y);
+        const double resid = givens_column(j, col, scs, ssn, cs, sn, g);
         s0->resid = resid;
         s0->hnext = beta;
         s0->iters = j + 1;
@@ -415,7 +583,7 @@ __global__ void __launch_bounds__(kRedThreads) k_norm_part(long long N, const do
 
 // One block; thread r initialises entry r; active = entries still running.
 __global__ void k_init_state(int nb, int nblk, double tol, const double* __restrict__ npart,
-                             double* __restrict__ sigma, double2* __restrict__ g, long long sS,
+                             double* __restrict__ sigma, double* __restrict__ sigt, double2* __restrict__ g, long long sS,
                              KState* __restrict__ st, int* __restrict__ active) {
     __shared__ int run;
     if (threadIdx.x == 0) run = 0;
@@ -433,6 +601,7 @@ __global__ void k_init_state(int nb, int nblk, double tol, const double* __restr
         s0->done = 0;
         g[r * sS] = make_double2(beta, 0.0);
         sigma[r * sS] = beta > 0.0 ? 1.0 / beta : 0.0;
+        if (sigt) sigt[r * sS] = sigma[r * sS];
         if (!isfinite(beta)) { s0->nonfinite = 1; s0->done = 1; }
         else if (beta == 0.0) { s0->conv = 1; s0->done = 1; }
         else atomicAdd(&run, 1);
@@ -527,17 +696,18 @@ static size_t coef_smem(int count) { return (size_t)(count > 0 ? count : 1) * si
 
 static size_t finish_smem(int j) {
     const size_t b = (size_t)(j + 2) * sizeof(double2) + (size_t)j * (sizeof(double2) + sizeof(double));
-    if (b > 48 * 1024) cudaFuncSetAttribute(k_arnoldi_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+    allow_dynamic_smem((const void*)k_arnoldi_finish, b);
     return b;
 }
 
 static void set_coef_smem_limit(const void* fn, size_t bytes) {
-    if (bytes > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    allow_dynamic_smem(fn, bytes);
 }
 
 void launch_norm_init(const Ctx& cx, const KrylovBufs& kb, int nb, double tol) {
     k_norm_part<<<dim3(kb.nblk, nb), kRedThreads, 0, cx.stream>>>(kb.N, kb.V, kb.sV(), kb.npart, kb.nblk);
-    k_init_state<<<1, 256, 0, cx.stream>>>(nb, kb.nblk, tol, kb.npart, kb.sigma, kb.g, kb.sS(), kb.st, kb.active);
+    k_init_state<<<1, 256, 0, cx.stream>>>(nb, kb.nblk, tol, kb.npart, kb.sigma, kb.sigt, kb.g, kb.sS(), kb.st,
+                                           kb.active);
 }
 
 // After the preconditioner and the matrix-vector product have written
@@ -578,26 +748,37 @@ void launch_arnoldi_step(const Ctx& cx, const KrylovBufs& kb, int nb, int j) {
 // Orthogonality and the Arnoldi relation hold to about 1e-12 relative (the
 // double-float accumulation), far below any GMRES tolerance used here, while
 // no basis pass executes an FP64 instruction per basis entry.
-void launch_arnoldi_step_mixed(const Ctx& cx, const KrylovBufs& kb, int nb, int j) {
-    const int stride = kb.maxit + 1;
-    const long long wofs = (long long)(j + 1) * kb.ld;
+static size_t dcgs_finish_smem(int j) {
+    const size_t b = (size_t)(j + 1) * sizeof(double2) + (size_t)(j > 0 ? j - 1 : 0) * (sizeof(double2) + sizeof(double));
+    allow_dynamic_smem((const void*)k_dcgs_finish, b);
+    return b;
+}
+
+void launch_dcgs2_step(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int last_only, cudaEvent_t* ev) {
+    const int S = kb.maxit + 1, ps = kb.pstride();
+    // entry pairs: the padded vector length and all strides are even
+    const long long Np = (kb.N + 1) / 2, ldp = kb.ld / 2, sVp = kb.sV() / 2;
+    float4* V32 = reinterpret_cast<float4*>(kb.V32);
+    float4* V32lo = reinterpret_cast<float4*>(kb.V32lo);
     const dim3 gr(kb.nblk, nb);
-    const dim3 rg(((j + 1) * 32 + 255) / 256, nb);
-    const size_t cdf = (size_t)(j + 1) * sizeof(float4);
-    set_coef_smem_limit((const void*)k_axpy_df, cdf);
-    k_multidot<float2, kDotGroup32><<<gr, kRedThreads, 0, cx.stream>>>(j, kb.N, kb.ld, stride, kb.V32, kb.sV(), wofs,
-                                                                       kb.part, kb.sP(), kb.st);
-    k_reduce_dots<<<rg, 256, 0, cx.stream>>>(j, kb.nblk, stride, kb.part, kb.sP(), kb.sigma, kb.h1, kb.sS(), kb.st);
-    k_axpy_df<<<gr, kRedThreads, cdf, cx.stream>>>(j, kb.N, kb.ld, kb.V32, kb.V32lo, kb.sV(), kb.sigma, kb.h1,
-                                                   kb.sS(), wofs, kb.st);
-    k_multidot_df<kDotGroupDF><<<gr, kRedThreads, 0, cx.stream>>>(j, kb.N, kb.ld, stride, kb.V32, kb.V32lo, kb.sV(),
-                                                                  wofs, kb.part, kb.sP(), kb.st);
-    k_reduce_dots<<<rg, 256, 0, cx.stream>>>(j, kb.nblk, stride, kb.part, kb.sP(), kb.sigma, kb.h2, kb.sS(), kb.st);
-    k_correct_df<<<gr, kRedThreads, (size_t)(j + 1) * sizeof(float2), cx.stream>>>(
-        j, kb.N, kb.ld, kb.V32, kb.V32lo, kb.sV(), kb.sigma, kb.h2, kb.sS(), wofs, kb.npart, kb.nblk, kb.st);
-    k_arnoldi_finish<<<nb, 32, finish_smem(j), cx.stream>>>(j, kb.maxit, kb.nblk, kb.npart, kb.h1, kb.h2, kb.H,
-                                                            kb.sH(), kb.cs, kb.sn, kb.g, kb.sigma, kb.sS(), kb.st,
-                                                            kb.active);
+    if (ev) cudaEventRecord(ev[0], cx.stream);
+    k_dcgs_dot<kDotGroupDC><<<gr, kRedThreads, 0, cx.stream>>>(j, Np, ldp, ps, S, V32, V32lo, sVp, !last_only,
+                                                               kb.part, kb.sP(), kb.st);
+    if (ev) cudaEventRecord(ev[1], cx.stream);
+    const dim3 rg(((2 * j + 2) * 32 + 255) / 256, nb);
+    k_dcgs_reduce<<<rg, 256, 0, cx.stream>>>(j, kb.nblk, ps, S, kb.part, kb.sP(), kb.sigma, kb.h2, kb.hn, kb.sS(),
+                                             kb.sN(), kb.st);
+    k_dcgs_finish<<<nb, 32, dcgs_finish_smem(j), cx.stream>>>(j, kb.maxit, last_only, kb.hn, kb.sN(), kb.h1, kb.h2, kb.H,
+                                                              kb.sH(), kb.cs, kb.sn, kb.g, kb.sigma, kb.sS(), kb.st,
+                                                              kb.active);
+    if (last_only) return;
+    const size_t us = (size_t)(j + 1) * sizeof(float4) + (size_t)j * sizeof(float2);
+    set_coef_smem_limit((const void*)k_dcgs_update, us);
+    if (ev) cudaEventRecord(ev[2], cx.stream);
+    k_dcgs_update<<<gr, kRedThreads, us, cx.stream>>>(j, Np, ldp, V32, V32lo, sVp, kb.sigma, kb.h1, kb.h2, kb.sS(),
+                                                      kb.npart, kb.nblk, kb.st);
+    if (ev) cudaEventRecord(ev[3], cx.stream);
+    k_dcgs_scale<<<nb, 32, 0, cx.stream>>>(j, kb.nblk, kb.npart, kb.sigt, kb.sS(), kb.st);
 }
 
 void launch_lsq_solve(const Ctx& cx, const KrylovBufs& kb, int nb) {

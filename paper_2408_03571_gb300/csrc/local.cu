@@ -140,8 +140,7 @@ int launch_tile_factor(const Ctx& cx, const FactorDesc* fdesc_dev, int nfactors,
                        float2* W32, FactorStat* stat_dev) {
     const size_t smem = (size_t)max_m * max_m * sizeof(double2) + (size_t)max_m * sizeof(double2) +
                         (size_t)max_m * sizeof(int) + 16;
-    if (cudaFuncSetAttribute(k_tile_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return -1;
+    if (allow_dynamic_smem((const void*)k_tile_factor, smem) != cudaSuccess) return -1;
     k_tile_factor<<<nfactors, 512, smem, cx.stream>>>(cx.op, fdesc_dev, W64, W32, stat_dev);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -407,7 +406,7 @@ static int launch_tile_solve_t(const Ctx& cx, int nb, const Tile* tiles, TileGro
                                cplx_t<R>* ytiles, long long yts, BatchSkip sk) {
     const size_t smem = tile_smem_bytes<R, T, NST>(max_mx, max_my);
     auto kern = k_tile_solve<Cw, Cz, R, T, NST>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
+    if (allow_dynamic_smem((const void*)kern, smem) != cudaSuccess) return -1;
     const int threads = (max_mx * 4 + 31) / 32 * 32;
     kern<<<dim3(grp.count, nb), threads, smem, cx.stream>>>(cx.op, cx.ct, tiles, grp.idx, W, w, ws, vscale, vss, mode,
                                                             c, cs, use_coarse, z, zs, ytiles, yts, sk, cx.err);

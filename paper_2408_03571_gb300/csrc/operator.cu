@@ -69,6 +69,67 @@ __global__ void k_apply_A(OpDesc op, const Cin* __restrict__ x, long long xs, Co
     }
 }
 
+// y = A x for a complex64 x, in double-float arithmetic on the FP32 pipes (the
+// FP64 rate is 1/62 of FP32 on GB300): y is written as the pair y32 + y32lo.
+// The couplings -1/h^2 (halved on Sommerfeld edges) are exact in FP32 for
+// n <= 4097 (checked by the launcher); the diagonal is the double-float pair
+// (dh, dl) for interior nodes of a constant-kappa grid and is otherwise formed
+// in FP64 and split.  The neighbour sums are exact (TwoSum), every product is
+// error-free (FMA form of Dekker's product), so y carries about 47 significant
+// bits relative to the largest term of the stencil sum.
+__global__ void k_apply_A_df(OpDesc op, float ch, float dh, float dl, const float2* __restrict__ x, long long xs,
+                             float2* __restrict__ yh, float2* __restrict__ yl, long long ys, BatchSkip sk) {
+    const int r = blockIdx.z;
+    if (skipped(sk, r)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int n = op.n;
+    if (i >= n || j >= n) return;
+    x += r * xs; yh += r * ys; yl += r * ys;
+    const size_t p = (size_t)j * n + i;
+    if (!op_is_unknown(op, i, j)) {
+        yh[p] = make_float2(0.f, 0.f);
+        yl[p] = make_float2(0.f, 0.f);
+        return;
+    }
+    const bool edge_x = i == 0 || i == n - 1, edge_y = j == 0 || j == n - 1;
+    float drh = dh, drl = dl, dih = 0.f, dil = 0.f;
+    float cx = ch, cy = ch;
+    if (op.bc == HZS_SOMMERFELD) {
+        if (edge_y) cx *= 0.5f;
+        if (edge_x) cy *= 0.5f;
+    }
+    if (op.kappa || edge_x || edge_y) {
+        const double2 d = op_diag(op, i, j);
+        split_d(d.x, drh, drl);
+        split_d(d.y, dih, dil);
+    }
+    const float2 xp = x[p];
+    const float2 z = make_float2(0.f, 0.f);
+    const float2 a = (i > 0 && op_is_unknown(op, i - 1, j)) ? x[p - 1] : z;
+    const float2 b = (i < n - 1 && op_is_unknown(op, i + 1, j)) ? x[p + 1] : z;
+    const float2 c = (j > 0 && op_is_unknown(op, i, j - 1)) ? x[p - n] : z;
+    const float2 e = (j < n - 1 && op_is_unknown(op, i, j + 1)) ? x[p + n] : z;
+    float sxr, sxrl, sxi, sxil, syr, syrl, syi, syil;
+    two_sum(a.x, b.x, sxr, sxrl);
+    two_sum(a.y, b.y, sxi, sxil);
+    two_sum(c.x, e.x, syr, syrl);
+    two_sum(c.y, e.y, syi, syil);
+    float reh = 0.f, rel = 0.f, imh = 0.f, iml = 0.f;
+    df_fma(reh, rel, drh, drl, xp.x, 0.f);
+    df_fma(reh, rel, -dih, -dil, xp.y, 0.f);
+    df_fma(reh, rel, cx, 0.f, sxr, sxrl);
+    df_fma(reh, rel, cy, 0.f, syr, syrl);
+    df_fma(imh, iml, drh, drl, xp.y, 0.f);
+    df_fma(imh, iml, dih, dil, xp.x, 0.f);
+    df_fma(imh, iml, cx, 0.f, sxi, sxil);
+    df_fma(imh, iml, cy, 0.f, syi, syil);
+    df_norm(reh, rel);
+    df_norm(imh, iml);
+    yh[p] = make_float2(reh, imh);
+    yl[p] = make_float2(rel, iml);
+}
+
 // q(i, j) = sum_{a,b} wx(i,a) wy(j,b) c[(c0[j]+b) nc1 + c0[i]+a]   (prolongation R_0^T c)
 template <typename R>
 __device__ __forceinline__ cplx_t<R> prolong_at(const CoarseTab& ct, const cplx_t<R>* __restrict__ c, int i, int j) {
@@ -232,6 +293,21 @@ template void launch_apply_A<double2, double2, double>(const Ctx&, int, const do
                                                        long long, float2*, long long, BatchSkip, float2*);
 template void launch_apply_A<float2, double2, double>(const Ctx&, int, const float2*, long long, double2*, long long,
                                                       float2*, long long, BatchSkip, float2*);
+
+bool launch_apply_A_df(const Ctx& cx, int nb, const float2* x, long long xs, float2* yh, float2* yl, long long ys,
+                       BatchSkip sk) {
+    const double ch = -cx.op.inv_h2;
+    if ((double)(float)ch != ch) return false;                  // coupling not exact in FP32
+    float dh = 0.f, dl = 0.f;
+    if (!cx.op.kappa) {
+        const double d = 4.0 * cx.op.inv_h2 - cx.op.kappa0;     // interior diagonal, constant kappa
+        dh = (float)d;
+        dl = (float)(d - (double)dh);
+    }
+    const dim3 b(32, 8);
+    k_apply_A_df<<<grid2d(cx.op.n, b, nb), b, 0, cx.stream>>>(cx.op, (float)ch, dh, dl, x, xs, yh, yl, ys, sk);
+    return true;
+}
 
 template <typename Cv, typename Cw, typename R>
 void launch_deflate(const Ctx& cx, int nb, const cplx_t<R>* c, long long cs, const Cv* v, long long vs,

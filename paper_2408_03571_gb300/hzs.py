@@ -55,7 +55,8 @@ class SolveDesc(ct.Structure):
 class SolveInfo(ct.Structure):
     _fields_ = [("iterations", ct.c_int), ("converged", ct.c_int), ("relres_est", ct.c_double),
                 ("relres_true", ct.c_double), ("t_solve_ms", ct.c_double), ("t_precond_ms", ct.c_double),
-                ("t_matvec_ms", ct.c_double), ("t_orth_ms", ct.c_double), ("launches", ct.c_longlong),
+                ("t_matvec_ms", ct.c_double), ("t_orth_ms", ct.c_double), ("t_orth_dot_ms", ct.c_double),
+                ("t_orth_update_ms", ct.c_double), ("launches", ct.c_longlong),
                 ("status", ct.c_int)]
 
     def as_dict(self):
@@ -139,6 +140,8 @@ class SolveResult:
     t_precond_ms: float
     t_matvec_ms: float
     t_orth_ms: float
+    t_orth_dot_ms: float
+    t_orth_update_ms: float
     launches: int
     status: int
 
@@ -223,7 +226,8 @@ class Preconditioner:
         _check(fn(self._h, ct.byref(sd), f.data_ptr(), u.data_ptr(), nrhs, infos), self.grid.handle,
                allow=(OK, NOT_CONVERGED))
         res = [SolveResult(i.iterations, bool(i.converged), i.relres_est, i.relres_true, i.t_solve_ms,
-                           i.t_precond_ms, i.t_matvec_ms, i.t_orth_ms, i.launches, i.status)
+                           i.t_precond_ms, i.t_matvec_ms, i.t_orth_ms, i.t_orth_dot_ms, i.t_orth_update_ms,
+                           i.launches, i.status)
                for i in infos[:nrhs]]
         return u, res
 
@@ -281,7 +285,8 @@ def solve_batched(problems, rhs, tol: float = 1e-6, maxit: int = 1000, orth_fp64
     res, pos = [], 0
     for c in counts:
         res.append([SolveResult(i.iterations, bool(i.converged), i.relres_est, i.relres_true, i.t_solve_ms,
-                                i.t_precond_ms, i.t_matvec_ms, i.t_orth_ms, i.launches, i.status)
+                                i.t_precond_ms, i.t_matvec_ms, i.t_orth_ms, i.t_orth_dot_ms,
+                                i.t_orth_update_ms, i.launches, i.status)
                     for i in infos[pos:pos + c]])
         pos += c
     return outs, res

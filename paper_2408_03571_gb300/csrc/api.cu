@@ -55,6 +55,7 @@ struct hzs_precond {
     double *w = nullptr, *wt = nullptr;
     float *wf = nullptr, *wtf = nullptr;
     double2* Ainv = nullptr;
+    float4* Ainv_df = nullptr;        // MIXED: double-float copy of Ainv (FP32-pipe coarse product)
     float2* c2f = nullptr;            // complex64 copy of the coarse solution
     int* err = nullptr;               // device error word (HZS_ERR_TIMEOUT from bounded waits)
     int* groups_d = nullptr;          // tiles grouped by shared factor
@@ -236,7 +237,7 @@ extern "C" void hzs_precond_destroy(hzs_precond* p) {
     free_krylov(p);
     cudaFree(p->c0); cudaFree(p->lo); cudaFree(p->hi); cudaFree(p->off); cudaFree(p->w); cudaFree(p->wt);
     cudaFree(p->wf); cudaFree(p->wtf); cudaFree(p->c2f); cudaFree(p->err); cudaFree(p->groups_d);
-    cudaFree(p->Ainv); cudaFree(p->W64); cudaFree(p->W32); cudaFree(p->tiles_d); cudaFree(p->cover_d);
+    cudaFree(p->Ainv); cudaFree(p->Ainv_df); cudaFree(p->W64); cudaFree(p->W32); cudaFree(p->tiles_d); cudaFree(p->cover_d);
     cudaFree(p->t_buf); cudaFree(p->c_buf); cudaFree(p->c2_buf); cudaFree(p->w_buf); cudaFree(p->ytiles);
     cudaFree(p->zc64);
     if (p->h_done) cudaFreeHost(p->h_done);
@@ -295,6 +296,11 @@ static hzs_status setup_impl(hzs_grid* g, const hzs_precond_desc* d, hzs_precond
         if (rc < 0) return fail(g, HZS_ERR_CUDA, "coarse factorisation failed");
         p->coarse_minpiv = minpiv;
         if (rc > 0) return fail(g, HZS_ERR_SINGULAR_COARSE, "coarse matrix A_0 has a zero pivot");
+        if (d->precision == HZS_MIXED) {
+            HZS_CUDA(g, dalloc(&p->Ainv_df, (size_t)p->Nc * p->Nc));
+            launch_split_df(p->cx, (long long)p->Nc * p->Nc, p->Ainv, p->Ainv_df);
+            HZS_CUDA(g, cudaGetLastError());
+        }
     }
     HZS_CUDA(g, dalloc(&p->err, 1));
     HZS_CUDA(g, cudaMemsetAsync(p->err, 0, sizeof(int), s));
@@ -441,7 +447,10 @@ static hzs_status precond_apply(hzs_precond* p, int nb, const Cv* v, long long v
     const int kind = p->desc.kind;
     if (p->use_coarse) {
         launch_restrict<Cv, R>(cx, nb, v, vs, vscale, vss, (C*)p->t_buf, p->c_buf, sk);
-        launch_coarse_matvec(cx, nb, p->Ainv, p->Nc, p->c_buf, p->c2_buf, f32 ? p->c2f : nullptr, sk);
+        if (f32 && p->Ainv_df)
+            launch_coarse_matvec_df(cx, nb, p->Ainv_df, p->Nc, p->c_buf, p->c2f, sk);
+        else
+            launch_coarse_matvec(cx, nb, p->Ainv, p->Nc, p->c_buf, p->c2_buf, f32 ? p->c2f : nullptr, sk);
     }
     int rc = 0;
     if (kind == HZS_SHS2) {
@@ -531,7 +540,10 @@ static hzs_status ensure_krylov(hzs_precond* p, int maxit, int nb) {
     kb.nb = nb;
     kb.N = N;
     kb.ld = ld;
-    kb.nblk = 4 * g->num_sms;        // 4 blocks of 256 threads per SM for the basis sweeps
+    // basis sweeps: 3 blocks of 256 threads per SM (80 registers a thread); the
+    // delayed-CGS2 dot pass, 64 registers a thread, runs 4 per SM
+    kb.nblk = 3 * g->num_sms;
+    kb.nblk_dot = 4 * g->num_sms;
     const size_t S = (size_t)(maxit + 1);
     HZS_CUDA(g, dalloc(&kb.V, (size_t)nb * kb.sV()));
     HZS_CUDA(g, dalloc(&kb.sigma, nb * S));

@@ -153,6 +153,64 @@ __global__ void k_coarse_matvec(int Nc, const double2* __restrict__ Ainv, const 
     }
 }
 
+// Double-float copy of Ainv: entry e as (hi.re, lo.re, hi.im, lo.im).
+__global__ void k_split_df(long long N, const double2* __restrict__ a, float4* __restrict__ b) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+        const double2 v = a[e];
+        float4 q;
+        split_d(v.x, q.x, q.y);
+        split_d(v.y, q.z, q.w);
+        b[e] = q;
+    }
+}
+
+// outf = Ainv * c rounded to complex64, the products and sums in double-float
+// arithmetic on the FP32 pipes (same accuracy class as the FP64 product before
+// the final rounding).  One warp per row; c staged in shared memory as pairs.
+__global__ void k_coarse_matvec_df(int Nc, const float4* __restrict__ Adf, const double2* __restrict__ c,
+                                   float2* __restrict__ outf, BatchSkip sk) {
+    const int r = blockIdx.y;
+    if (sk.flag && sk.flag[(size_t)r * sk.stride]) return;
+    c += (size_t)r * Nc;
+    outf += (size_t)r * Nc;
+    extern __shared__ float4 cdf[];
+    for (int k = threadIdx.x; k < Nc; k += blockDim.x) {
+        const double2 v = c[k];
+        float4 q;
+        split_d(v.x, q.x, q.y);
+        split_d(v.y, q.z, q.w);
+        cdf[k] = q;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    for (int row = blockIdx.x * wpb + (threadIdx.x >> 5); row < Nc; row += gridDim.x * wpb) {
+        const float4* arow = Adf + (size_t)row * Nc;
+        float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+        int it = 0;
+        for (int k = lane; k < Nc; k += 32) {
+            const float4 a = arow[k], v = cdf[k];
+            df_fma(rh, rl, a.x, a.y, v.x, v.y);
+            df_fma(rh, rl, -a.z, -a.w, v.z, v.w);
+            df_fma(ih, il, a.x, a.y, v.z, v.w);
+            df_fma(ih, il, a.z, a.w, v.x, v.y);
+            if ((++it & 7) == 0) { df_norm(rh, rl); df_norm(ih, il); }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float orh = __shfl_down_sync(0xffffffffu, rh, o), orl = __shfl_down_sync(0xffffffffu, rl, o);
+            const float oih = __shfl_down_sync(0xffffffffu, ih, o), oil = __shfl_down_sync(0xffffffffu, il, o);
+            df_add(rh, rl, orh, orl);
+            df_add(ih, il, oih, oil);
+        }
+        if (lane == 0) {
+            df_norm(rh, rl);
+            df_norm(ih, il);
+            outf[row] = make_float2(rh, ih);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ Galerkin A_0
 // A0[(J,I), (J+dJ, I+dI)] = sum_{fine (i,j)} phi_I(i) phi_J(j) (A phi_{I+dI, J+dJ})(i, j)
 // One block per (row, offset) pair; offsets |dI|, |dJ| <= 2 cover B_2 (P_1 uses <= 1).
@@ -306,6 +364,21 @@ HZS_RS(double2, double)
 HZS_RS(double2, float)
 HZS_RS(float2, float)
 #undef HZS_RS
+
+void launch_split_df(const Ctx& cx, long long N, const double2* a, float4* b) {
+    k_split_df<<<4 * cx.num_sms, 256, 0, cx.stream>>>(N, a, b);
+}
+
+void launch_coarse_matvec_df(const Ctx& cx, int nb, const float4* Adf, int Nc, const double2* c, float2* outf,
+                             BatchSkip sk) {
+    const int threads = 256;
+    const int rows_per_block = threads / 32;
+    int blocks = (Nc + rows_per_block - 1) / rows_per_block;
+    if (blocks > 4 * cx.num_sms) blocks = 4 * cx.num_sms;
+    const size_t smem = (size_t)Nc * sizeof(float4);
+    allow_dynamic_smem((const void*)k_coarse_matvec_df, smem);
+    k_coarse_matvec_df<<<dim3(blocks, nb), threads, smem, cx.stream>>>(Nc, Adf, c, outf, sk);
+}
 
 void launch_coarse_matvec(const Ctx& cx, int nb, const double2* Ainv, int Nc, const double2* c, double2* out,
                           float2* outf, BatchSkip sk) {

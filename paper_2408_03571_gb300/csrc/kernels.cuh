@@ -104,6 +104,11 @@ void launch_restrict(const Ctx& cx, int nb, const Cv* v, long long vs, const dou
 // out = Ainv c in FP64 (stride Nc); outf (if given) receives a complex64 copy
 void launch_coarse_matvec(const Ctx& cx, int nb, const double2* Ainv, int Nc, const double2* c, double2* out,
                           float2* outf, BatchSkip sk);
+// b = double-float copy of a (N complex entries, see k_split_df)
+void launch_split_df(const Ctx& cx, long long N, const double2* a, float4* b);
+// outf = complex64 rounding of Adf c, double-float arithmetic (Adf from launch_split_df)
+void launch_coarse_matvec_df(const Ctx& cx, int nb, const float4* Adf, int Nc, const double2* c, float2* outf,
+                             BatchSkip sk);
 void launch_galerkin(const Ctx& cx, double2* A0);
 int gj_invert(const Ctx& cx, double2* a, int N, double* minpiv);
 
@@ -144,6 +149,7 @@ struct KrylovBufs {
     long long N;       // vector length (n*n)
     long long ld;      // leading dimension between basis vectors (elements)
     int nblk;          // blocks of the reduction kernels
+    int nblk_dot;      // blocks of the delayed-CGS2 dot pass (rows of part; >= nblk)
     double2* V;        // (maxit+1) x ld per entry
     float2* V32;       // (maxit+1) x ld complex64 roundings of the basis (mixed-precision CGS2), or null
     float2* V32lo;     // (maxit+1) x ld complex64 remainders: V32 + V32lo is the basis as double-float pairs
@@ -166,7 +172,7 @@ struct KrylovBufs {
     long long sS() const { return maxit + 1; }
     long long sN() const { return maxit + 2; }
     int pstride() const { return 2 * (maxit + 1) + 2; }
-    long long sP() const { return (long long)nblk * pstride(); }
+    long long sP() const { return (long long)nblk_dot * pstride(); }
     BatchSkip skip() const { return BatchSkip{&st->done, kStateInts}; }
 };
 void launch_norm_init(const Ctx& cx, const KrylovBufs& kb, int nb, double tol);

@@ -23,6 +23,7 @@ namespace hzs {
 constexpr int kRedThreads = 256;
 constexpr int kDotGroup64 = 4;     // basis vectors per warp pass (FP64 multi-dot)
 constexpr int kDotGroupDC = 4;     // basis vectors per warp pass (delayed CGS2 multi-dot)
+constexpr int kUpdUnroll = 4;      // basis vectors per iteration of the delayed CGS2 update
 
 __device__ __forceinline__ void chunk_of(long long N, long long& e0, long long& e1) {
     const long long per = (N + gridDim.x - 1) / gridDim.x;
@@ -157,48 +158,117 @@ __device__ __forceinline__ void df_cmac(float& rh, float& rl, float& ih, float& 
     df_fma(ih, il, c.z, c.w, vrh, vrl);
 }
 
+constexpr int kFinWarps = 4;                   // warps per right-hand side in the Givens kernels
+constexpr int kFinThreads = 32 * kFinWarps;
+
+__device__ __forceinline__ double2 shfl_up_c(double2 v, int off) {
+    return make_double2(__shfl_up_sync(0xffffffffu, v.x, off), __shfl_up_sync(0xffffffffu, v.y, off));
+}
+
+// Block-wide sums for the Givens kernels (kFinThreads threads, every thread gets the result).
+__device__ __forceinline__ double fin_sum(double v, double* red) {
+    v = warp_sum_d(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int k = 0; k < kFinWarps; ++k) s += red[k];
+    return s;
+}
+__device__ __forceinline__ double2 fin_sum2(double2 v, double* red) {
+    v = warp_sum(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) { red[2 * (threadIdx.x >> 5)] = v.x; red[2 * (threadIdx.x >> 5) + 1] = v.y; }
+    __syncthreads();
+    double2 s = make_double2(0.0, 0.0);
+    for (int k = 0; k < kFinWarps; ++k) { s.x += red[2 * k]; s.y += red[2 * k + 1]; }
+    return s;
+}
+
 // Brings Hessenberg column jc (col[0..jc+1], in shared memory) to triangular
 // form: applies the stored rotations 0..jc-1 (scs, ssn: shared copies of cs, sn),
 // computes rotation jc that zeroes col[jc+1] (stored in cs[jc], sn[jc]), applies
 // it to the right-hand side g and returns the new residual estimate |g[jc+1]|.
-// Single thread.
+// Called by all kFinThreads threads of the block.
+//
+// Applying the old rotations is a linear recurrence in the running entry a:
+//   col'[i] = c_i a_i + s_i col[i+1],   a_{i+1} = -conj(s_i) a_i + c_i col[i+1],
+// i.e. a_{i+1} = M_i(a_i) with the affine map M_i(a) = alpha_i a + beta_i.  Affine
+// maps compose associatively, so each thread composes the maps of its own segment
+// of consecutive rotations, a scan (Kogge-Stone within each warp, then the warp
+// totals in order) combines the segments, and each thread replays its segment
+// from the a it receives.  |alpha_i| <= 1, so the composed maps stay bounded.
+// The FP64 pipe executes one warp instruction per 16 cycles per SM, so the work
+// is spread over one warp per SM sub-partition.
 __device__ double givens_column(int jc, double2* col, const double* scs, const double2* ssn, double* cs,
                                 double2* sn, double2* g) {
-    double2 a = col[0];
-    for (int i = 0; i < jc; ++i) {
+    __shared__ double2 wA[kFinWarps], wB[kFinWarps], s_a;
+    __shared__ double s_res;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int L = (jc + kFinThreads - 1) / kFinThreads;
+    const int s0 = min(tid * L, jc), s1 = min(s0 + L, jc);
+    const double2 a0 = col[0];
+    const double2 bnd = col[s1];     // col[i+1] for the segment's last i; the next thread overwrites it
+    double2 A = make_double2(1.0, 0.0), B = make_double2(0.0, 0.0);
+    for (int i = s0; i < s1; ++i) {
+        const double2 al = make_double2(-ssn[i].x, ssn[i].y);      // -conj(s_i)
+        const double2 be = cscale(col[i + 1], scs[i]);
+        B = cfma(al, B, be);
+        A = cmul(al, A);
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const double2 A1 = shfl_up_c(A, off), B1 = shfl_up_c(B, off);
+        if (lane >= off) {            // (A, B) <- (A, B) o (A1, B1): the earlier segments first
+            B = cfma(A, B1, B);
+            A = cmul(A, A1);
+        }
+    }
+    if (lane == 31) { wA[warp] = A; wB[warp] = B; }
+    __syncthreads();                  // also orders every read of col above before the writes below
+    double2 aw = a0;                  // value entering this warp: earlier warps' totals applied in order
+    for (int k = 0; k < warp; ++k) aw = cfma(wA[k], aw, wB[k]);
+    const double2 Ap = shfl_up_c(A, 1), Bp = shfl_up_c(B, 1);
+    double2 a = lane == 0 ? aw : cfma(Ap, aw, Bp);
+    for (int i = s0; i < s1; ++i) {
         const double c = scs[i];
         const double2 sv = ssn[i];
-        const double2 b = col[i + 1];
-        // t = c a + s b ; b' = -conj(s) a + c b
-        double2 t = cscale(a, c);
-        t = cfma(sv, b, t);
-        double2 nb = cscale(b, c);
+        const double2 b = i + 1 == s1 ? bnd : col[i + 1];
+        // t = c a + s b ; a' = -conj(s) a + c b
+        const double2 t = cfma(sv, b, cscale(a, c));
         const double2 csn = make_double2(sv.x, -sv.y);
-        nb = cfms(csn, a, nb);
+        a = cfms(csn, a, cscale(b, c));
         col[i] = t;
-        a = nb;
     }
-    const double2 b = col[jc + 1];
-    const double aa = hypot(a.x, a.y), bb = hypot(b.x, b.y);
-    double c; double2 sv;
-    if (bb == 0.0) { c = 1.0; sv = make_double2(0.0, 0.0); }
-    else if (aa == 0.0) { c = 0.0; sv = make_double2(b.x / bb, -b.y / bb); }
-    else {
-        const double rho = hypot(aa, bb);
-        c = aa / rho;
-        const double2 ph = make_double2(a.x / aa, a.y / aa);          // a / |a|
-        const double2 cb = make_double2(b.x / rho, -b.y / rho);       // conj(b) / rho
-        sv = cmul(ph, cb);
+    // the last thread ends with a_jc (a thread with an empty segment passes its incoming value on)
+    if (tid == kFinThreads - 1) s_a = a;
+    __syncthreads();
+    if (tid == 0) {
+        a = s_a;
+        const double2 b = col[jc + 1];
+        const double aa = hypot(a.x, a.y), bb = hypot(b.x, b.y);
+        double c; double2 sv;
+        if (bb == 0.0) { c = 1.0; sv = make_double2(0.0, 0.0); }
+        else if (aa == 0.0) { c = 0.0; sv = make_double2(b.x / bb, -b.y / bb); }
+        else {
+            const double rho = hypot(aa, bb);
+            c = aa / rho;
+            const double2 ph = make_double2(a.x / aa, a.y / aa);          // a / |a|
+            const double2 cb = make_double2(b.x / rho, -b.y / rho);       // conj(b) / rho
+            sv = cmul(ph, cb);
+        }
+        cs[jc] = c; sn[jc] = sv;
+        col[jc] = cfma(sv, b, cscale(a, c));
+        col[jc + 1] = make_double2(0.0, 0.0);
+        const double2 gj = g[jc];
+        const double2 csn = make_double2(sv.x, -sv.y);
+        const double2 gn = cscale(cmul(csn, gj), -1.0);
+        g[jc + 1] = gn;
+        g[jc] = cscale(gj, c);
+        s_res = hypot(gn.x, gn.y);
     }
-    cs[jc] = c; sn[jc] = sv;
-    col[jc] = cfma(sv, b, cscale(a, c));
-    col[jc + 1] = make_double2(0.0, 0.0);
-    const double2 gj = g[jc];
-    const double2 csn = make_double2(sv.x, -sv.y);
-    const double2 gn = cscale(cmul(csn, gj), -1.0);
-    g[jc + 1] = gn;
-    g[jc] = cscale(gj, c);
-    return hypot(gn.x, gn.y);
+    __syncthreads();
+    return s_res;
 }
 
 // ---- delayed CGS2 (mixed-precision path, see launch_dcgs2_step)
@@ -353,66 +423,71 @@ __global__ void k_dcgs_reduce(int j, int nblk, int ps, int S, const double2* __r
     }
 }
 
-// Step j's scalar work for entry r = blockIdx.x (one warp): beta_j, completion
-// and rotation of column j-1 (convergence check with j columns), and the
-// first-pass coefficients of column j (h1, for the update pass and the next
+// Step j's scalar work for entry r = blockIdx.x (kFinThreads threads): beta_j,
+// completion and rotation of column j-1 (convergence check with j columns), and
+// the first-pass coefficients of column j (h1, for the update pass and the next
 // completion).  j == maxit (last_only) completes the last column only.
-__global__ void k_dcgs_finish(int j, int maxit, int last_only, const double2* __restrict__ hn, long long sN,
-                              double2* __restrict__ h1, const double2* __restrict__ h2, double2* __restrict__ H,
-                              long long sH, double* __restrict__ cs, double2* __restrict__ sn, double2* __restrict__ g,
-                              double* __restrict__ sigma, long long sS, KState* __restrict__ st,
-                              int* __restrict__ active) {
+__global__ void __launch_bounds__(kFinThreads) k_dcgs_finish(int j, int maxit, int last_only,
+                                                            const double2* __restrict__ hn, long long sN,
+                                                            double2* __restrict__ h1, const double2* __restrict__ h2,
+                                                            double2* __restrict__ H, long long sH,
+                                                            double* __restrict__ cs, double2* __restrict__ sn,
+                                                            double2* __restrict__ g, double* __restrict__ sigma,
+                                                            long long sS, KState* __restrict__ st,
+                                                            int* __restrict__ active) {
     const int r = blockIdx.x;
     if (st[r].done) return;
     hn += r * sN; h1 += r * sS; h2 += r * sS; H += r * sH; cs += r * sS; sn += r * sS; g += r * sS; sigma += r * sS;
     KState* s0 = st + r;
     extern __shared__ double2 fsm[];
+    __shared__ double red[2 * kFinWarps];
+    __shared__ int s_fin;
     double2* col = fsm;                                   // j + 1
     double2* ssn = col + (j + 1);                         // j - 1
     double* scs = reinterpret_cast<double*>(ssn + (j > 0 ? j - 1 : 0));
-    const int lane = threadIdx.x;
+    const int tid = threadIdx.x;
     // |alpha|^2 and alpha^H b
     double aa = 0.0;
     double2 ab = make_double2(0.0, 0.0);
-    for (int i = lane; i < j; i += 32) {
+    for (int i = tid; i < j; i += kFinThreads) {
         const double2 a = h2[i], b = hn[i];
         aa = fma(a.x, a.x, fma(a.y, a.y, aa));
         ab = cfma_conj(a, b, ab);
     }
-    aa = warp_sum_d(aa);
-    ab = warp_sum(ab);
+    aa = fin_sum(aa, red);
+    ab = fin_sum2(ab, red);
     const double c = hn[j].x;
     const double2 d = hn[j + 1];
     const double b2 = c - aa;
     const double beta = b2 > 0.0 ? sqrt(b2) : 0.0;
-    int fin = 0;
     if (j > 0) {
-        for (int i = lane; i < j; i += 32) col[i] = cadd(h1[i], h2[i]);
-        for (int i = lane; i < j - 1; i += 32) { ssn[i] = sn[i]; scs[i] = cs[i]; }
-        if (lane == 0) col[j] = make_double2(beta, 0.0);
-        __syncwarp();
-        if (lane == 0) {
-            const double resid = givens_column(j - 1, col, scs, ssn, cs, sn, g);
+        for (int i = tid; i < j; i += kFinThreads) col[i] = cadd(h1[i], h2[i]);
+        for (int i = tid; i < j - 1; i += kFinThreads) { ssn[i] = sn[i]; scs[i] = cs[i]; }
+        if (tid == 0) col[j] = make_double2(beta, 0.0);
+        __syncthreads();
+        const double resid = givens_column(j - 1, col, scs, ssn, cs, sn, g);
+        if (tid == 0) {
             s0->resid = resid;
             s0->hnext = beta;
             s0->iters = j;
-            fin = 1;
+            int fin = 1;
             if (!isfinite(resid) || !isfinite(b2)) s0->nonfinite = 1;
             else if (resid <= s0->tolabs) s0->conv = 1;
             else if (beta == 0.0) { s0->breakdown = 1; s0->conv = 1; }
             else if (!last_only && j < maxit) fin = 0;
             if (fin) { s0->done = 1; atomicSub(active, 1); }
+            s_fin = fin;
         }
-        __syncwarp();
+        __syncthreads();
         double2* out = H + (size_t)(j - 1) * (maxit + 1);
-        for (int i = lane; i <= j; i += 32) out[i] = col[i];
-        fin = __shfl_sync(0xffffffffu, fin, 0);
+        for (int i = tid; i <= j; i += kFinThreads) out[i] = col[i];
+        if (s_fin) return;
     }
-    if (fin || last_only) return;
+    if (last_only) return;
     // column j, first pass (alpha is complete for the old vectors; q_j = (u~ - Q alpha) / beta)
     const double ib = beta > 0.0 ? 1.0 / beta : 0.0;
-    for (int i = lane; i < j; i += 32) h1[i] = hn[i];
-    if (lane == 0) {
+    for (int i = tid; i < j; i += kFinThreads) h1[i] = hn[i];
+    if (tid == 0) {
         h1[j] = cscale(csub(d, ab), ib);
         sigma[j] = ib;
         if (j == 0 && !(beta > 0.0)) { s0->done = 1; s0->conv = 1; s0->breakdown = 1; atomicSub(active, 1); }
@@ -423,7 +498,7 @@ __global__ void k_dcgs_finish(int j, int maxit, int last_only, const double2* __
 // (the small reorthogonalisation sum in complex64, its subtraction in double-float),
 // w = w - sum_i (sigma_i b_i) V_i - (h_jj sigma_j) V_j in double-float;
 // npart[b] = sum_e |w[e]|^2.
-__global__ void __launch_bounds__(kRedThreads) k_dcgs_update(int j, long long Np, long long ldp,
+__global__ void __launch_bounds__(kRedThreads, 3) k_dcgs_update(int j, long long Np, long long ldp,
                                                              float4* __restrict__ V32, float4* __restrict__ V32lo,
                                                              long long sVp, const double* __restrict__ sigma,
                                                              const double2* __restrict__ h1,
@@ -455,25 +530,28 @@ __global__ void __launch_bounds__(kRedThreads) k_dcgs_update(int j, long long Np
     for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         float a0h = 0.f, a0l = 0.f, b0h = 0.f, b0l = 0.f, a1h = 0.f, a1l = 0.f, b1h = 0.f, b1l = 0.f;
         float2 s0 = make_float2(0.f, 0.f), s1 = s0;
+        const float4* ph = V32 + e;
+        const float4* pl = V32lo + e;
         int i = 0;
-        for (; i + 1 < j; i += 2) {
-            const float4 vh0 = V32[(size_t)i * ldp + e], vl0 = V32lo[(size_t)i * ldp + e];
-            const float4 vh1 = V32[(size_t)(i + 1) * ldp + e], vl1 = V32lo[(size_t)(i + 1) * ldp + e];
-            const float4 q0 = cb[i], q1 = cb[i + 1];
-            df_cmac(a0h, a0l, b0h, b0l, q0, vh0.x, vl0.x, vh0.y, vl0.y);
-            df_cmac(a1h, a1l, b1h, b1l, q0, vh0.z, vl0.z, vh0.w, vl0.w);
-            df_cmac(a0h, a0l, b0h, b0l, q1, vh1.x, vl1.x, vh1.y, vl1.y);
-            df_cmac(a1h, a1l, b1h, b1l, q1, vh1.z, vl1.z, vh1.w, vl1.w);
-            s0 = cfma(ca[i], lo2(vh0), s0);
-            s1 = cfma(ca[i], hi2(vh0), s1);
-            s0 = cfma(ca[i + 1], lo2(vh1), s0);
-            s1 = cfma(ca[i + 1], hi2(vh1), s1);
-            if ((i & 15) == 14) {
-                df_norm(a0h, a0l); df_norm(b0h, b0l); df_norm(a1h, a1l); df_norm(b1h, b1l);
+        for (; i + kUpdUnroll <= j; i += kUpdUnroll) {     // kUpdUnroll basis vectors: all loads first
+            float4 vh[kUpdUnroll], vl[kUpdUnroll];
+#pragma unroll
+            for (int t = 0; t < kUpdUnroll; ++t) {
+                vh[t] = __ldcs(ph + (size_t)(i + t) * ldp);
+                vl[t] = __ldcs(pl + (size_t)(i + t) * ldp);
             }
+#pragma unroll
+            for (int t = 0; t < kUpdUnroll; ++t) {
+                const float4 q = cb[i + t];
+                df_cmac(a0h, a0l, b0h, b0l, q, vh[t].x, vl[t].x, vh[t].y, vl[t].y);
+                df_cmac(a1h, a1l, b1h, b1l, q, vh[t].z, vl[t].z, vh[t].w, vl[t].w);
+                s0 = cfma(ca[i + t], lo2(vh[t]), s0);
+                s1 = cfma(ca[i + t], hi2(vh[t]), s1);
+            }
+            df_norm(a0h, a0l); df_norm(b0h, b0l); df_norm(a1h, a1l); df_norm(b1h, b1l);
         }
-        if (i < j) {
-            const float4 vh = V32[(size_t)i * ldp + e], vl = V32lo[(size_t)i * ldp + e];
+        for (; i < j; ++i) {
+            const float4 vh = __ldcs(ph + (size_t)i * ldp), vl = __ldcs(pl + (size_t)i * ldp);
             const float4 q = cb[i];
             df_cmac(a0h, a0l, b0h, b0l, q, vh.x, vl.x, vh.y, vl.y);
             df_cmac(a1h, a1l, b1h, b1l, q, vh.z, vl.z, vh.w, vl.w);
@@ -518,38 +596,41 @@ __global__ void k_dcgs_scale(int j, int nblk, const double* __restrict__ npart, 
     if (threadIdx.x == 0) sigt[r * sS + j + 1] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
 }
 
-// Completes step j of entry r = blockIdx.x: h_{j+1,j} = ||w||, column j of
-// H = h1 + h2, Givens rotations, residual estimate, convergence / breakdown
-// flags.  One warp per entry: the block norm partials are summed in a fixed
-// lane order, the column and the rotations are staged in shared memory, and
-// lane 0 applies the rotation chain.  An entry that finishes decrements the
-// batch's active counter.
-__global__ void k_arnoldi_finish(int j, int maxit, int nblk, const double* __restrict__ npart,
-                                 const double2* __restrict__ h1, const double2* __restrict__ h2,
-                                 double2* __restrict__ H, long long sH, double* __restrict__ cs,
-                                 double2* __restrict__ sn, double2* __restrict__ g, double* __restrict__ sigma,
-                                 long long sS, KState* __restrict__ st, int* __restrict__ active) {
+// Completes step j of entry r = blockIdx.x (kFinThreads threads): h_{j+1,j} =
+// ||w||, column j of H = h1 + h2, Givens rotations, residual estimate,
+// convergence / breakdown flags.  The block norm partials are summed in a fixed
+// order; an entry that finishes decrements the batch's active counter.
+__global__ void __launch_bounds__(kFinThreads) k_arnoldi_finish(int j, int maxit, int nblk,
+                                                               const double* __restrict__ npart,
+                                                               const double2* __restrict__ h1,
+                                                               const double2* __restrict__ h2,
+                                                               double2* __restrict__ H, long long sH,
+                                                               double* __restrict__ cs, double2* __restrict__ sn,
+                                                               double2* __restrict__ g, double* __restrict__ sigma,
+                                                               long long sS, KState* __restrict__ st,
+                                                               int* __restrict__ active) {
     const int r = blockIdx.x;
     if (st[r].done) return;
     npart += (size_t)r * nblk;
     h1 += r * sS; h2 += r * sS; H += r * sH; cs += r * sS; sn += r * sS; g += r * sS; sigma += r * sS;
     KState* s0 = st + r;
     extern __shared__ double2 fsm[];
+    __shared__ double red[2 * kFinWarps];
     double2* col = fsm;                                   // j + 2
     double2* ssn = col + (j + 2);                         // j
     double* scs = reinterpret_cast<double*>(ssn + j);     // j
-    const int lane = threadIdx.x;
+    const int tid = threadIdx.x;
     double s = 0.0;
-    for (int b = lane; b < nblk; b += 32) s += npart[b];
-    s = warp_sum_d(s);
-    const double beta = __shfl_sync(0xffffffffu, sqrt(s), 0);
-    for (int i = lane; i <= j; i += 32) col[i] = cadd(h1[i], h2[i]);
-    for (int i = lane; i < j; i += 32) { ssn[i] = sn[i]; scs[i] = cs[i]; }
-    if (lane == 0) col[j + 1] = make_double2(beta, 0.0);
-    __syncwarp();
+    for (int b = tid; b < nblk; b += kFinThreads) s += npart[b];
+    s = fin_sum(s, red);
+    const double beta = sqrt(s);
+    for (int i = tid; i <= j; i += kFinThreads) col[i] = cadd(h1[i], h2[i]);
+    for (int i = tid; i < j; i += kFinThreads) { ssn[i] = sn[i]; scs[i] = cs[i]; }
+    if (tid == 0) col[j + 1] = make_double2(beta, 0.0);
+    __syncthreads();
     const int ldh = maxit + 1;
-    if (lane == 0) {
-        const double resid = givens_column(j, col, scs, ssn, cs, sn, g);
+    const double resid = givens_column(j, col, scs, ssn, cs, sn, g);
+    if (tid == 0) {
         s0->resid = resid;
         s0->hnext = beta;
         s0->iters = j + 1;
@@ -561,9 +642,8 @@ __global__ void k_arnoldi_finish(int j, int maxit, int nblk, const double* __res
         else if (!(j + 1 >= maxit)) fin = 0;
         if (fin) { s0->done = 1; atomicSub(active, 1); }
     }
-    __syncwarp();
     double2* out = H + (size_t)j * ldh;
-    for (int i = lane; i <= j + 1; i += 32) out[i] = col[i];
+    for (int i = tid; i <= j + 1; i += kFinThreads) out[i] = col[i];
 }
 
 // ||f||: V_0 holds f; sets sigma[0], g[0], tolerance and flags.
@@ -731,9 +811,9 @@ void launch_arnoldi_step(const Ctx& cx, const KrylovBufs& kb, int nb, int j) {
     k_reduce_dots<<<rg, 256, 0, cx.stream>>>(j, kb.nblk, stride, kb.part, kb.sP(), kb.sigma, kb.h2, kb.sS(), kb.st);
     k_axpy_multi<<<gr, kRedThreads, cs, cx.stream>>>(j, kb.N, kb.ld, kb.V, kb.sV(), kb.sigma, kb.h2, kb.sS(), wofs,
                                                      kb.npart, kb.nblk, kb.st);
-    k_arnoldi_finish<<<nb, 32, finish_smem(j), cx.stream>>>(j, kb.maxit, kb.nblk, kb.npart, kb.h1, kb.h2, kb.H,
-                                                            kb.sH(), kb.cs, kb.sn, kb.g, kb.sigma, kb.sS(), kb.st,
-                                                            kb.active);
+    k_arnoldi_finish<<<nb, kFinThreads, finish_smem(j), cx.stream>>>(j, kb.maxit, kb.nblk, kb.npart, kb.h1, kb.h2,
+                                                                     kb.H, kb.sH(), kb.cs, kb.sn, kb.g, kb.sigma,
+                                                                     kb.sS(), kb.st, kb.active);
 }
 
 // Mixed-precision CGS2 (used with the complex64 preconditioner).  The basis
@@ -762,15 +842,15 @@ void launch_dcgs2_step(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int l
     float4* V32lo = reinterpret_cast<float4*>(kb.V32lo);
     const dim3 gr(kb.nblk, nb);
     if (ev) cudaEventRecord(ev[0], cx.stream);
-    k_dcgs_dot<kDotGroupDC><<<gr, kRedThreads, 0, cx.stream>>>(j, Np, ldp, ps, S, V32, V32lo, sVp, !last_only,
-                                                               kb.part, kb.sP(), kb.st);
+    k_dcgs_dot<kDotGroupDC><<<dim3(kb.nblk_dot, nb), kRedThreads, 0, cx.stream>>>(j, Np, ldp, ps, S, V32, V32lo, sVp,
+                                                                                 !last_only, kb.part, kb.sP(), kb.st);
     if (ev) cudaEventRecord(ev[1], cx.stream);
     const dim3 rg(((2 * j + 2) * 32 + 255) / 256, nb);
-    k_dcgs_reduce<<<rg, 256, 0, cx.stream>>>(j, kb.nblk, ps, S, kb.part, kb.sP(), kb.sigma, kb.h2, kb.hn, kb.sS(),
-                                             kb.sN(), kb.st);
-    k_dcgs_finish<<<nb, 32, dcgs_finish_smem(j), cx.stream>>>(j, kb.maxit, last_only, kb.hn, kb.sN(), kb.h1, kb.h2, kb.H,
-                                                              kb.sH(), kb.cs, kb.sn, kb.g, kb.sigma, kb.sS(), kb.st,
-                                                              kb.active);
+    k_dcgs_reduce<<<rg, 256, 0, cx.stream>>>(j, kb.nblk_dot, ps, S, kb.part, kb.sP(), kb.sigma, kb.h2, kb.hn,
+                                             kb.sS(), kb.sN(), kb.st);
+    k_dcgs_finish<<<nb, kFinThreads, dcgs_finish_smem(j), cx.stream>>>(j, kb.maxit, last_only, kb.hn, kb.sN(),
+                                                                        kb.h1, kb.h2, kb.H, kb.sH(), kb.cs, kb.sn,
+                                                                        kb.g, kb.sigma, kb.sS(), kb.st, kb.active);
     if (last_only) return;
     const size_t us = (size_t)(j + 1) * sizeof(float4) + (size_t)j * sizeof(float2);
     set_coef_smem_limit((const void*)k_dcgs_update, us);

@@ -204,52 +204,18 @@ __host__ __device__ constexpr size_t tile_smem_bytes(int mx, int my) {
            (size_t)mx * sizeof(R) + 16 + (size_t)NST * 8 + 16;
 }
 
-template <typename Cw, typename Cz, typename R, int T, int NST>
-__global__ void __launch_bounds__(512) k_tile_solve(OpDesc op, CoarseTab ct, const Tile* __restrict__ tiles,
-                                                    const int* __restrict__ groups, const cplx_t<R>* __restrict__ W,
-                                                    const Cw* __restrict__ w, long long ws,
-                                                    const double* __restrict__ vscale, long long vss, int mode,
-                                                    const cplx_t<R>* __restrict__ c, long long cs, int use_coarse,
-                                                    Cz* __restrict__ z, long long zs, cplx_t<R>* __restrict__ ytiles,
-                                                    long long yts, BatchSkip sk, int* __restrict__ err) {
-    using C = cplx_t<R>;
-    const int rb = blockIdx.y;                      // batch entry
-    if (sk.flag && sk.flag[(size_t)rb * sk.stride]) return;
-    w += rb * ws;
-    c += rb * cs;
-    if (z) z += rb * zs;
-    if (ytiles) ytiles += rb * yts;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    int tix[T];
-#pragma unroll
-    for (int t = 0; t < T; ++t) tix[t] = groups[blockIdx.x * T + t];
-    const Tile T0 = tiles[tix[0]];
-    const int mx = T0.mx, my = T0.my, n = op.n;
-    const long long bs = block_stride(mx);
-    const uint32_t bbytes = (uint32_t)(bs * sizeof(C));
-    C* wst = reinterpret_cast<C*>(smem_raw);                                        // NST stages
-    C* g = reinterpret_cast<C*>(smem_raw + ((size_t)NST * bs * sizeof(C) + 127) / 128 * 128);   // T x mx*my
-    C* r = g + (size_t)T * mx * my;                                                 // 2 x T x mx
-    R* cy = reinterpret_cast<R*>(r + 2 * T * mx);                                   // mx
-    uint64_t* bar = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(cy + mx) + 15) & ~uintptr_t(15));
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const C* Wt = W + T0.woff;
-    const int nsteps = 2 * my - 1;
-    auto blk = [&](int q) { return q < my ? q : 2 * my - 2 - q; };
+// ---- stages of the tile solve
 
-    if (tid == 0) {
-        for (int s = 0; s < NST; ++s) mbar_init(&bar[s], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    if (tid == 0) {
-        for (int q = 0; q < NST && q < nsteps; ++q) {
-            mbar_expect_tx(&bar[q], bbytes);
-            bulk_g2s(wst + (size_t)q * bs, Wt + (size_t)blk(q) * bs, bbytes, &bar[q]);
-        }
-    }
-    // gather b = R_i (s w) for the group's tiles
-    const R sc = vscale ? (R)vscale[rb * vss] : (R)1;
+// Gathers b = R_i (s w) for the group's T tiles into g (T x mx*my), the row
+// couplings cy (mx) and the first right-hand side r = b_0 (T x mx); ends with a
+// block barrier.
+template <typename Cw, typename R, int T>
+__device__ __forceinline__ void tile_gather(const OpDesc& op, const Tile* __restrict__ tiles, const int* tix,
+                                            const Tile& T0, const Cw* __restrict__ w, R sc, cplx_t<R>* g,
+                                            cplx_t<R>* r, R* cy) {
+    using C = cplx_t<R>;
+    const int mx = T0.mx, my = T0.my, n = op.n;
+    const int tid = threadIdx.x, nt = blockDim.x;
     for (int t = 0; t < T; ++t) {
         C* gt = g + (size_t)t * mx * my;
         if (tix[t] < 0) {
@@ -266,87 +232,52 @@ __global__ void __launch_bounds__(512) k_tile_solve(OpDesc op, CoarseTab ct, con
     }
     for (int a = tid; a < mx; a += nt) cy[a] = (R)op_cy(op, T0.x0 + a);
     __syncthreads();
-    // r for the first step: b_0
     for (int e = tid; e < T * mx; e += nt) {
         const int t = e / mx, a = e % mx;
         r[e] = g[(size_t)t * mx * my + a];
     }
     __syncthreads();
+}
 
-    const int row = tid >> 2, sub = tid & 3;
-    const bool active = row < mx;
-    int q_fail = -1;
-    for (int q = 0; q < nsteps; ++q) {
-        const int st = q % NST;
-        const uint32_t parity = (uint32_t)((q / NST) & 1);
-        const bool ok = mbar_wait_bounded(&bar[st], parity);
-        if (__syncthreads_or(!ok)) { q_fail = q; break; }
-        const C* Wq = wst + (size_t)st * bs;
-        const C* rc = r + (size_t)(q & 1) * T * mx;
-        C* rn = r + (size_t)((q + 1) & 1) * T * mx;
-        const bool fwd = q < my;
-        const int j = blk(q);
-        {
-            // every thread of the block runs the shuffles below (inactive rows add zeros)
-            C acc[T];
+// Completes block step j for row `row` of each tile from the row products acc
+// (thread sub == 0 of the row): forward g_j = W_j (b_j - C g_{j-1}), backward
+// x_j = g_j - W_j (C x_{j+1}); writes the next step's right-hand side into rn.
+template <typename R, int T>
+__device__ __forceinline__ void tile_step_finish(bool fwd, int j, int my, int mx, int row, const cplx_t<R>* acc,
+                                                 cplx_t<R>* g, cplx_t<R>* rn, const R* cy) {
+    using C = cplx_t<R>;
 #pragma unroll
-            for (int t = 0; t < T; ++t) { acc[t].x = 0; acc[t].y = 0; }
-            if (active) {
-                const C* wr = Wq + (size_t)row * mx;
-                for (int k = sub; k < mx; k += 4) {
-                    const C wv = wr[k];
-#pragma unroll
-                    for (int t = 0; t < T; ++t) acc[t] = cfma(wv, rc[t * mx + k], acc[t]);
-                }
-            }
-#pragma unroll
-            for (int t = 0; t < T; ++t) {
-                acc[t].x += __shfl_xor_sync(0xffffffffu, acc[t].x, 1);
-                acc[t].y += __shfl_xor_sync(0xffffffffu, acc[t].y, 1);
-                acc[t].x += __shfl_xor_sync(0xffffffffu, acc[t].x, 2);
-                acc[t].y += __shfl_xor_sync(0xffffffffu, acc[t].y, 2);
-            }
-            if (active && sub == 0) {
-#pragma unroll
-                for (int t = 0; t < T; ++t) {
-                    C* gt = g + (size_t)t * mx * my;
-                    C x;
-                    if (fwd) {
-                        x = acc[t];                                   // g_j = W_j (b_j - C g_{j-1})
-                    } else {
-                        x = gt[(size_t)j * mx + row];                 // x_j = g_j - W_j (C x_{j+1})
-                        x.x -= acc[t].x; x.y -= acc[t].y;
-                    }
-                    gt[(size_t)j * mx + row] = x;
-                    // right-hand side of the next step
-                    C nr;
-                    if (fwd && j + 1 < my) {
-                        const C b = gt[(size_t)(j + 1) * mx + row];
-                        nr.x = b.x - cy[row] * x.x; nr.y = b.y - cy[row] * x.y;
-                    } else {
-                        nr.x = cy[row] * x.x; nr.y = cy[row] * x.y;   // C x_j for the backward step j-1
-                    }
-                    rn[t * mx + row] = nr;
-                }
-            }
+    for (int t = 0; t < T; ++t) {
+        C* gt = g + (size_t)t * mx * my;
+        C x;
+        if (fwd) {
+            x = acc[t];
+        } else {
+            x = gt[(size_t)j * mx + row];
+            x.x -= acc[t].x; x.y -= acc[t].y;
         }
-        __syncthreads();   // stage st fully read; next r complete
-        if (tid == 0 && q + NST < nsteps) {
-            mbar_expect_tx(&bar[st], bbytes);
-            bulk_g2s(wst + (size_t)st * bs, Wt + (size_t)blk(q + NST) * bs, bbytes, &bar[st]);
+        gt[(size_t)j * mx + row] = x;
+        C nr;
+        if (fwd && j + 1 < my) {
+            const C b = gt[(size_t)(j + 1) * mx + row];
+            nr.x = b.x - cy[row] * x.x; nr.y = b.y - cy[row] * x.y;
+        } else {
+            nr.x = cy[row] * x.x; nr.y = cy[row] * x.y;   // C x_j for the backward step j-1
         }
+        rn[t * mx + row] = nr;
     }
-    if (q_fail >= 0) {
-        if (tid == 0) {
-            if (err) atomicExch(err, (int)HZS_ERR_TIMEOUT);
-            // copies in flight: steps q_fail .. q_fail + NST - 1; wait for each (bounded)
-            for (int qq = q_fail; qq < q_fail + NST && qq < nsteps; ++qq)
-                mbar_wait_bounded(&bar[qq % NST], (uint32_t)((qq / NST) & 1));
-        }
-        __syncthreads();
-        return;
-    }
-    // output
+}
+
+// Writes the solved tiles: mode 0 (restricted, D_i = owner indicator): z =
+// [R_0^T c] + x on owned nodes; mode 1 (additive): the whole tile into ytiles.
+template <typename Cz, typename R, int T>
+__device__ __forceinline__ void tile_output(const OpDesc& op, const CoarseTab& ct, const Tile* __restrict__ tiles,
+                                            const int* tix, const Tile& T0, const cplx_t<R>* g, int mode,
+                                            const cplx_t<R>* __restrict__ c, int use_coarse, Cz* __restrict__ z,
+                                            cplx_t<R>* __restrict__ ytiles) {
+    using C = cplx_t<R>;
+    const int mx = T0.mx, my = T0.my, n = op.n;
+    const int tid = threadIdx.x, nt = blockDim.x;
     for (int t = 0; t < T; ++t) {
         if (tix[t] < 0) continue;
         const Tile Ti = tiles[tix[t]];
@@ -386,6 +317,102 @@ __global__ void __launch_bounds__(512) k_tile_solve(OpDesc op, CoarseTab ct, con
             z[(size_t)gj * n + gi] = conv<Cz>(v);
         }
     }
+}
+
+template <typename Cw, typename Cz, typename R, int T, int NST>
+__global__ void __launch_bounds__(512) k_tile_solve(OpDesc op, CoarseTab ct, const Tile* __restrict__ tiles,
+                                                    const int* __restrict__ groups, const cplx_t<R>* __restrict__ W,
+                                                    const Cw* __restrict__ w, long long ws,
+                                                    const double* __restrict__ vscale, long long vss, int mode,
+                                                    const cplx_t<R>* __restrict__ c, long long cs, int use_coarse,
+                                                    Cz* __restrict__ z, long long zs, cplx_t<R>* __restrict__ ytiles,
+                                                    long long yts, BatchSkip sk, int* __restrict__ err) {
+    using C = cplx_t<R>;
+    const int rb = blockIdx.y;                      // batch entry
+    if (sk.flag && sk.flag[(size_t)rb * sk.stride]) return;
+    w += rb * ws;
+    c += rb * cs;
+    if (z) z += rb * zs;
+    if (ytiles) ytiles += rb * yts;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    int tix[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) tix[t] = groups[blockIdx.x * T + t];
+    const Tile T0 = tiles[tix[0]];
+    const int mx = T0.mx, my = T0.my;
+    const long long bs = block_stride(mx);
+    const uint32_t bbytes = (uint32_t)(bs * sizeof(C));
+    C* wst = reinterpret_cast<C*>(smem_raw);                                        // NST stages
+    C* g = reinterpret_cast<C*>(smem_raw + ((size_t)NST * bs * sizeof(C) + 127) / 128 * 128);   // T x mx*my
+    C* r = g + (size_t)T * mx * my;                                                 // 2 x T x mx
+    R* cy = reinterpret_cast<R*>(r + 2 * T * mx);                                   // mx
+    uint64_t* bar = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(cy + mx) + 15) & ~uintptr_t(15));
+    const int tid = threadIdx.x;
+    const C* Wt = W + T0.woff;
+    const int nsteps = 2 * my - 1;
+    auto blk = [&](int q) { return q < my ? q : 2 * my - 2 - q; };
+
+    if (tid == 0) {
+        for (int s = 0; s < NST; ++s) mbar_init(&bar[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int q = 0; q < NST && q < nsteps; ++q) {
+            mbar_expect_tx(&bar[q], bbytes);
+            bulk_g2s(wst + (size_t)q * bs, Wt + (size_t)blk(q) * bs, bbytes, &bar[q]);
+        }
+    }
+    tile_gather<Cw, R, T>(op, tiles, tix, T0, w, vscale ? (R)vscale[rb * vss] : (R)1, g, r, cy);
+
+    const int row = tid >> 2, sub = tid & 3;
+    const bool active = row < mx;
+    int q_fail = -1;
+    for (int q = 0; q < nsteps; ++q) {
+        const int st = q % NST;
+        const uint32_t parity = (uint32_t)((q / NST) & 1);
+        const bool ok = mbar_wait_bounded(&bar[st], parity);
+        if (__syncthreads_or(!ok)) { q_fail = q; break; }
+        const C* Wq = wst + (size_t)st * bs;
+        const C* rc = r + (size_t)(q & 1) * T * mx;
+        C* rn = r + (size_t)((q + 1) & 1) * T * mx;
+        // every thread of the block runs the shuffles below (inactive rows add zeros)
+        C acc[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) { acc[t].x = 0; acc[t].y = 0; }
+        if (active) {
+            const C* wr = Wq + (size_t)row * mx;
+            for (int k = sub; k < mx; k += 4) {
+                const C wv = wr[k];
+#pragma unroll
+                for (int t = 0; t < T; ++t) acc[t] = cfma(wv, rc[t * mx + k], acc[t]);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            acc[t].x += __shfl_xor_sync(0xffffffffu, acc[t].x, 1);
+            acc[t].y += __shfl_xor_sync(0xffffffffu, acc[t].y, 1);
+            acc[t].x += __shfl_xor_sync(0xffffffffu, acc[t].x, 2);
+            acc[t].y += __shfl_xor_sync(0xffffffffu, acc[t].y, 2);
+        }
+        if (active && sub == 0) tile_step_finish<R, T>(q < my, blk(q), my, mx, row, acc, g, rn, cy);
+        __syncthreads();   // stage st fully read; next r complete
+        if (tid == 0 && q + NST < nsteps) {
+            mbar_expect_tx(&bar[st], bbytes);
+            bulk_g2s(wst + (size_t)st * bs, Wt + (size_t)blk(q + NST) * bs, bbytes, &bar[st]);
+        }
+    }
+    if (q_fail >= 0) {
+        if (tid == 0) {
+            if (err) atomicExch(err, (int)HZS_ERR_TIMEOUT);
+            // copies in flight: steps q_fail .. q_fail + NST - 1; wait for each (bounded)
+            for (int qq = q_fail; qq < q_fail + NST && qq < nsteps; ++qq)
+                mbar_wait_bounded(&bar[qq % NST], (uint32_t)((qq / NST) & 1));
+        }
+        __syncthreads();
+        return;
+    }
+    tile_output<Cz, R, T>(op, ct, tiles, tix, T0, g, mode, c, use_coarse, z, ytiles);
 }
 
 constexpr size_t kSmemLimit = 227 * 1024;

@@ -159,7 +159,7 @@ __device__ __forceinline__ cplx_t<R> prolong_at(const CoarseTab& ct, const cplx_
 template <typename Cv, typename Cw, typename R, int TX, int TY>
 __global__ void k_deflate(OpDesc op, CoarseTab ct, const cplx_t<R>* __restrict__ c, long long cs,
                           const Cv* __restrict__ v, long long vs, const double* __restrict__ vscale, long long vss,
-                          Cw* __restrict__ w, long long ws, BatchSkip sk) {
+                          Cw* __restrict__ w, long long ws, BatchSkip sk, R ch, R dint) {
     using C = cplx_t<R>;
     const int r = blockIdx.z;
     if (skipped(sk, r)) return;
@@ -180,8 +180,28 @@ __global__ void k_deflate(OpDesc op, CoarseTab ct, const cplx_t<R>* __restrict__
     const size_t p = (size_t)j * n + i;
     if (!op_is_unknown(op, i, j)) { w[p] = mk<Cw>(0.0, 0.0); return; }
     const R s = vscale ? (R)vscale[r * vss] : (R)1;
-    const double2 d = op_diag(op, i, j);
-    const R cx = (R)op_cx(op, j), cy = (R)op_cy(op, i);
+    C d;
+    R cx, cy;
+    if (sizeof(R) == sizeof(float)) {
+        // single precision: coefficients from the FP32 constants, FP64 only where the
+        // diagonal varies (kappa field, Sommerfeld edges)
+        const bool ex = i == 0 || i == n - 1, ey = j == 0 || j == n - 1;
+        cx = ch; cy = ch;
+        if (op.bc == HZS_SOMMERFELD) {
+            if (ey) cx *= (R)0.5;
+            if (ex) cy *= (R)0.5;
+        }
+        if (op.kappa || ex || ey) {
+            const double2 dd = op_diag(op, i, j);
+            d.x = (R)dd.x; d.y = (R)dd.y;
+        } else {
+            d.x = dint; d.y = 0;
+        }
+    } else {
+        const double2 dd = op_diag(op, i, j);
+        d.x = (R)dd.x; d.y = (R)dd.y;
+        cx = (R)op_cx(op, j); cy = (R)op_cy(op, i);
+    }
     const int li = threadIdx.x + 1, lj = threadIdx.y + 1;
     const C qp = qs[lj][li];
     C aq;
@@ -314,8 +334,10 @@ void launch_deflate(const Ctx& cx, int nb, const cplx_t<R>* c, long long cs, con
                     const double* vscale, long long vss, Cw* w, long long ws, BatchSkip sk) {
     constexpr int TX = 32, TY = 8;
     const dim3 b(TX, TY);
+    // -1/h^2 and the constant-kappa interior diagonal 4/h^2 - kappa, rounded once
+    const R ch = (R)(-cx.op.inv_h2), dint = (R)(4.0 * cx.op.inv_h2 - cx.op.kappa0);
     k_deflate<Cv, Cw, R, TX, TY><<<grid2d(cx.op.n, b, nb), b, 0, cx.stream>>>(cx.op, cx.ct, c, cs, v, vs, vscale, vss,
-                                                                              w, ws, sk);
+                                                                              w, ws, sk, ch, dint);
 }
 #define HZS_DEF(Cv, Cw, R)                                                                                     \
     template void launch_deflate<Cv, Cw, R>(const Ctx&, int, const cplx_t<R>*, long long, const Cv*, long long, \

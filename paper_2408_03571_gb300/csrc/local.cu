@@ -156,8 +156,9 @@ int launch_tile_factor(const Ctx& cx, const FactorDesc* fdesc_dev, int nfactors,
 // shared) into an NST-deep ring of shared-memory stages by bulk asynchronous
 // copies (cp.async.bulk, completion counted on an mbarrier per stage) issued
 // by thread 0, NST-1 block steps ahead of their use.  The 2 my - 1 block steps
-// use blocks 0, 1, .., my-1 (forward) then my-2, .., 0 (backward).  Four threads
-// share one output row of a block product; each step ends with one barrier.
+// use blocks 0, 1, .., my-1 (forward) then my-2, .., 0 (backward).  TPR threads
+// (8 when the tile allows, else 4) share one output row of a block product; each
+// step ends with one barrier.
 // Every mbarrier wait is bounded: on expiry the block records HZS_ERR_TIMEOUT in
 // the error word, drains its outstanding copies (again bounded) and returns.
 
@@ -319,8 +320,8 @@ __device__ __forceinline__ void tile_output(const OpDesc& op, const CoarseTab& c
     }
 }
 
-template <typename Cw, typename Cz, typename R, int T, int NST>
-__global__ void __launch_bounds__(512) k_tile_solve(OpDesc op, CoarseTab ct, const Tile* __restrict__ tiles,
+template <typename Cw, typename Cz, typename R, int T, int NST, int TPR>
+__global__ void __launch_bounds__(1024) k_tile_solve(OpDesc op, CoarseTab ct, const Tile* __restrict__ tiles,
                                                     const int* __restrict__ groups, const cplx_t<R>* __restrict__ W,
                                                     const Cw* __restrict__ w, long long ws,
                                                     const double* __restrict__ vscale, long long vss, int mode,
@@ -365,7 +366,7 @@ __global__ void __launch_bounds__(512) k_tile_solve(OpDesc op, CoarseTab ct, con
     }
     tile_gather<Cw, R, T>(op, tiles, tix, T0, w, vscale ? (R)vscale[rb * vss] : (R)1, g, r, cy);
 
-    const int row = tid >> 2, sub = tid & 3;
+    const int row = tid / TPR, sub = tid % TPR;
     const bool active = row < mx;
     int q_fail = -1;
     for (int q = 0; q < nsteps; ++q) {
@@ -382,7 +383,7 @@ __global__ void __launch_bounds__(512) k_tile_solve(OpDesc op, CoarseTab ct, con
         for (int t = 0; t < T; ++t) { acc[t].x = 0; acc[t].y = 0; }
         if (active) {
             const C* wr = Wq + (size_t)row * mx;
-            for (int k = sub; k < mx; k += 4) {
+            for (int k = sub; k < mx; k += TPR) {
                 const C wv = wr[k];
 #pragma unroll
                 for (int t = 0; t < T; ++t) acc[t] = cfma(wv, rc[t * mx + k], acc[t]);
@@ -390,10 +391,11 @@ __global__ void __launch_bounds__(512) k_tile_solve(OpDesc op, CoarseTab ct, con
         }
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-            acc[t].x += __shfl_xor_sync(0xffffffffu, acc[t].x, 1);
-            acc[t].y += __shfl_xor_sync(0xffffffffu, acc[t].y, 1);
-            acc[t].x += __shfl_xor_sync(0xffffffffu, acc[t].x, 2);
-            acc[t].y += __shfl_xor_sync(0xffffffffu, acc[t].y, 2);
+#pragma unroll
+            for (int o = 1; o < TPR; o <<= 1) {
+                acc[t].x += __shfl_xor_sync(0xffffffffu, acc[t].x, o);
+                acc[t].y += __shfl_xor_sync(0xffffffffu, acc[t].y, o);
+            }
         }
         if (active && sub == 0) tile_step_finish<R, T>(q < my, blk(q), my, mx, row, acc, g, rn, cy);
         __syncthreads();   // stage st fully read; next r complete
@@ -432,7 +434,18 @@ static int launch_tile_solve_t(const Ctx& cx, int nb, const Tile* tiles, TileGro
                                int mode, const cplx_t<R>* c, long long cs, int use_coarse, Cz* z, long long zs,
                                cplx_t<R>* ytiles, long long yts, BatchSkip sk) {
     const size_t smem = tile_smem_bytes<R, T, NST>(max_mx, max_my);
-    auto kern = k_tile_solve<Cw, Cz, R, T, NST>;
+    // eight threads per block row while the block stays within 1024 threads: more warps
+    // to hide the per-step latency and half the dependent multiply-adds per thread
+    if (max_mx * 8 <= 1024) {
+        auto kern = k_tile_solve<Cw, Cz, R, T, NST, 8>;
+        if (allow_dynamic_smem((const void*)kern, smem) != cudaSuccess) return -1;
+        const int threads = (max_mx * 8 + 31) / 32 * 32;
+        kern<<<dim3(grp.count, nb), threads, smem, cx.stream>>>(cx.op, cx.ct, tiles, grp.idx, W, w, ws, vscale, vss,
+                                                                mode, c, cs, use_coarse, z, zs, ytiles, yts, sk,
+                                                                cx.err);
+        return 0;
+    }
+    auto kern = k_tile_solve<Cw, Cz, R, T, NST, 4>;
     if (allow_dynamic_smem((const void*)kern, smem) != cudaSuccess) return -1;
     const int threads = (max_mx * 4 + 31) / 32 * 32;
     kern<<<dim3(grp.count, nb), threads, smem, cx.stream>>>(cx.op, cx.ct, tiles, grp.idx, W, w, ws, vscale, vss, mode,

@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-dedup-arm", action="store_true",
+                    help="skip the MIXED arm with every subdomain factored separately")
     ap.add_argument("--cpu-steps", type=int, default=6, help="Arnoldi steps in the oracle sample")
     # smaller MP-1 instances of the same path, for profiling captures only
     ap.add_argument("--n", type=int, default=1025)
@@ -266,6 +268,19 @@ def gpu_arm(args, world, rank, local):
     clocks = clk.stop()
     ms_e2e, infos_e2e, _ = timed_solves(Pm, args.steps, 0, e2e=True, profile=False)
     Pm.close()
+    # ---- MIXED with one factor per subdomain (no sharing of identical factors): the
+    # subdomain solves then stream 256 distinct factor sets per apply, as for a kappa field
+    dedup_off = None
+    if not args.no_dedup_arm:
+        Pn = hzs.Preconditioner(grid, hzs.SHS2, hzs.COARSE_B2, P_COARSE, hzs.MIXED, dedup_tiles=False)
+        ms_n, infos_n, _ = timed_solves(Pn, max(1, args.steps // 2), 1)
+        Pn.close()
+        i0 = infos_n[-1]
+        dedup_off = {"value": world * len(infos_n) / (ms_n * 1e-3), "unit": "solves/s",
+                     "ms_per_step": ms_n / len(infos_n), "iterations": i0.iterations,
+                     "relres_true": i0.relres_true, "t_precond_ms": i0.t_precond_ms,
+                     "note": "every subdomain factor stored and streamed separately (no sharing of "
+                             "identical factors)"}
     # ---- FP64 arm
     fp64 = None
     if not args.no_fp64:
@@ -359,6 +374,7 @@ def gpu_arm(args, world, rank, local):
         "gpu_launches": int(sum(i.launches for i in infos)),
         "clocks": clocks,
         "fp64": fp64,
+        "dedup_off": dedup_off,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         s = oracle_sample(args.cpu_steps, it)

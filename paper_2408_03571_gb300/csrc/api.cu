@@ -339,6 +339,9 @@ static hzs_status setup_impl(hzs_grid* g, const hzs_precond_desc* d, hzs_precond
     {
         std::vector<std::vector<int>> by_factor(fds.size());
         for (size_t t = 0; t < tiles.size(); ++t) by_factor[tiles[t].factor].push_back((int)t);
+        size_t share = 0;
+        for (auto& lst : by_factor) share = std::max(share, lst.size());
+        if (share < 2) p->group_T = 1;    // no factor is shared: one tile per block
         std::vector<int> groups;
         for (auto& lst : by_factor)
             for (size_t k = 0; k < lst.size(); k += p->group_T)
@@ -518,9 +521,9 @@ extern "C" hzs_status hzs_apply_precond(hzs_precond* p, const void* v_dev, void*
 
 // ------------------------------------------------------------------ solve
 // Device bytes one batch entry of the Krylov work space takes.
-static size_t krylov_entry_bytes(const hzs_precond* p, int maxit, long long ld) {
+static size_t krylov_entry_bytes(const hzs_precond* p, int maxit, long long ld, bool full_v) {
     const bool mixed = p->desc.precision == HZS_MIXED;
-    size_t b = (size_t)(maxit + 1) * ld * sizeof(double2);                 // V
+    size_t b = (size_t)(full_v ? maxit + 1 : 1) * ld * sizeof(double2);   // V
     if (mixed) b += 2 * (size_t)(maxit + 1) * ld * sizeof(float2)          // V32, V32lo
                     + (size_t)maxit * ld * sizeof(float2);                 // Z
     b += 2 * (size_t)ld * sizeof(double2);                                 // ztmp, rtmp
@@ -529,9 +532,10 @@ static size_t krylov_entry_bytes(const hzs_precond* p, int maxit, long long ld) 
 }
 
 // Krylov work space for batches of up to nb right-hand sides with maxit steps.
-static hzs_status ensure_krylov(hzs_precond* p, int maxit, int nb) {
+// full_v: keep the whole complex128 basis (FP64 CGS2); otherwise only its slot 0.
+static hzs_status ensure_krylov(hzs_precond* p, int maxit, int nb, bool full_v) {
     hzs_grid* g = p->g;
-    if (p->kb.V && p->kb.maxit >= maxit && p->kb.nb >= nb) return HZS_OK;
+    if (p->kb.V && p->kb.maxit >= maxit && p->kb.nb >= nb && (p->kb.vfull || !full_v)) return HZS_OK;
     free_krylov(p);
     const long long N = (long long)g->desc.n * g->desc.n;
     const long long ld = (N + 63) / 64 * 64;
@@ -545,7 +549,8 @@ static hzs_status ensure_krylov(hzs_precond* p, int maxit, int nb) {
     kb.nblk = 3 * g->num_sms;
     kb.nblk_dot = 4 * g->num_sms;
     const size_t S = (size_t)(maxit + 1);
-    HZS_CUDA(g, dalloc(&kb.V, (size_t)nb * kb.sV()));
+    kb.vfull = full_v ? 1 : 0;
+    HZS_CUDA(g, dalloc(&kb.V, (size_t)nb * kb.sVd()));
     HZS_CUDA(g, dalloc(&kb.sigma, nb * S));
     HZS_CUDA(g, dalloc(&kb.H, (size_t)nb * kb.sH()));
     HZS_CUDA(g, dalloc(&kb.cs, nb * S));
@@ -624,13 +629,12 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
     }
     HZS_CUDA(g, cudaEventRecord(p->t0, s));
     // V_0 = f (masked; it is never rescaled in place), plus its complex64 copy for orth32
-    launch_mask_copy_c128(cx, nb, f, nn, kb.V, sV, conj_io, orth32 ? kb.V32 : nullptr, sV,
+    launch_mask_copy_c128(cx, nb, f, nn, kb.V, kb.sVd(), conj_io, orth32 ? kb.V32 : nullptr, sV,
                           orth32 ? kb.V32lo : nullptr);
     launch_norm_init(cx, kb, nb, sd->tol);
     launches += 3;
     int steps = 0;
     for (int j = 0; j < sd->maxit; ++j) {
-        double2* w = kb.V + (size_t)(j + 1) * ld;
         cudaEvent_t* pe = prof ? &p->prof_ev[(size_t)8 * j] : nullptr;
         if (prof) HZS_CUDA(g, cudaEventRecord(pe[0], s));
         hzs_status st;
@@ -650,11 +654,12 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
             float2* Zj = p->Z + (size_t)j * ld;
             st = precond_apply<float, double2>(p, nb, kb.V + (size_t)j * ld, sV, kb.sigma + j, sS, Zj, sZ, sk);
             if (prof) HZS_CUDA(g, cudaEventRecord(pe[1], s));
-            launch_apply_A<float2, double2, double>(cx, nb, Zj, sZ, w, sV, nullptr, 0, sk);
+            launch_apply_A<float2, double2, double>(cx, nb, Zj, sZ, kb.V + (size_t)(j + 1) * ld, sV, nullptr, 0, sk);
         } else {
             st = precond_apply<double, double2>(p, nb, kb.V + (size_t)j * ld, sV, kb.sigma + j, sS, p->ztmp, ld, sk);
             if (prof) HZS_CUDA(g, cudaEventRecord(pe[1], s));
-            launch_apply_A<double2, double2, double>(cx, nb, p->ztmp, ld, w, sV, nullptr, 0, sk);
+            launch_apply_A<double2, double2, double>(cx, nb, p->ztmp, ld, kb.V + (size_t)(j + 1) * ld, sV, nullptr, 0,
+                                                     sk);
         }
         if (st != HZS_OK) return st;
         if (prof) HZS_CUDA(g, cudaEventRecord(pe[2], s));
@@ -689,7 +694,7 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
     }
     // true residual ||f - A u|| against the masked right-hand side in V_0
     launch_apply_A<double2, double2, double>(cx, nb, u, nn, p->rtmp, ld, nullptr, 0, kNoSkip);
-    launch_residual_norm(cx, kb, nb, kb.V, sV, p->rtmp, ld, p->dres);
+    launch_residual_norm(cx, kb, nb, kb.V, kb.sVd(), p->rtmp, ld, p->dres);
     launches += 3;
     if (conj_io) { launch_mask_copy_c128(cx, nb, u, nn, u, nn, 1, nullptr, 0); launches += 1; }
     HZS_CUDA(g, cudaEventRecord(p->t1, s));
@@ -755,17 +760,19 @@ static hzs_status solve_many(hzs_precond* p, const hzs_solve_desc* sd, const voi
     if (!(sd->tol > 0.0) || sd->maxit < 1) return fail(g, HZS_ERR_INVALID_ARG, "tol must be > 0 and maxit >= 1");
     if (nrhs == 0) return HZS_OK;
     int nb = nrhs;
-    if (!(p->kb.V && p->kb.maxit >= sd->maxit && p->kb.nb >= nrhs)) {
+    // the double-float path (MIXED without HZS_SOLVE_ORTH_FP64) keeps no complex128 basis
+    const bool full_v = !(p->desc.precision == HZS_MIXED && !(sd->flags & HZS_SOLVE_ORTH_FP64));
+    if (!(p->kb.V && p->kb.maxit >= sd->maxit && p->kb.nb >= nrhs && (p->kb.vfull || !full_v))) {
         free_krylov(p);
         size_t fr = 0, tot = 0;
         HZS_CUDA(g, cudaMemGetInfo(&fr, &tot));
         const long long N = (long long)g->desc.n * g->desc.n;
-        const size_t per = krylov_entry_bytes(p, sd->maxit, (N + 63) / 64 * 64);
+        const size_t per = krylov_entry_bytes(p, sd->maxit, (N + 63) / 64 * 64, full_v);
         const double avail = budget ? std::min((double)budget, 0.9 * (double)fr) : 0.8 * (double)fr;
         const long long fit = (long long)avail / (long long)per;
         if (fit < 1) return fail(g, HZS_ERR_OOM, "not enough device memory for one Krylov space of maxit steps");
         nb = (int)std::min<long long>(nrhs, fit);
-        hzs_status st = ensure_krylov(p, sd->maxit, nb);
+        hzs_status st = ensure_krylov(p, sd->maxit, nb, full_v);
         if (st != HZS_OK) return st;
     }
     nb = std::min(nrhs, p->kb.nb);

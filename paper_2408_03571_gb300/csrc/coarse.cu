@@ -186,27 +186,40 @@ __global__ void k_coarse_matvec_df(int Nc, const float4* __restrict__ Adf, const
     const int wpb = blockDim.x >> 5;
     for (int row = blockIdx.x * wpb + (threadIdx.x >> 5); row < Nc; row += gridDim.x * wpb) {
         const float4* arow = Adf + (size_t)row * Nc;
-        float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-        int it = 0;
-        for (int k = lane; k < Nc; k += 32) {
-            const float4 a = arow[k], v = cdf[k];
-            df_fma(rh, rl, a.x, a.y, v.x, v.y);
-            df_fma(rh, rl, -a.z, -a.w, v.z, v.w);
-            df_fma(ih, il, a.x, a.y, v.z, v.w);
-            df_fma(ih, il, a.z, a.w, v.x, v.y);
-            if ((++it & 7) == 0) { df_norm(rh, rl); df_norm(ih, il); }
+        // four independent accumulator sets (columns k = lane + 32 (4 m + s)) keep four
+        // loads and four dependent double-float chains in flight per lane
+        float rh[4] = {0.f, 0.f, 0.f, 0.f}, rl[4] = {0.f, 0.f, 0.f, 0.f};
+        float ih[4] = {0.f, 0.f, 0.f, 0.f}, il[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int k0 = 0; k0 < Nc; k0 += 128) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k = k0 + 32 * q + lane;
+                if (k < Nc) {
+                    const float4 a = arow[k], v = cdf[k];
+                    df_fma(rh[q], rl[q], a.x, a.y, v.x, v.y);
+                    df_fma(rh[q], rl[q], -a.z, -a.w, v.z, v.w);
+                    df_fma(ih[q], il[q], a.x, a.y, v.z, v.w);
+                    df_fma(ih[q], il[q], a.z, a.w, v.x, v.y);
+                }
+            }
+            if ((k0 & 1023) == 896) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) { df_norm(rh[q], rl[q]); df_norm(ih[q], il[q]); }
+            }
         }
+        for (int q = 1; q < 4; ++q) { df_add(rh[0], rl[0], rh[q], rl[q]); df_add(ih[0], il[0], ih[q], il[q]); }
+        float rh0 = rh[0], rl0 = rl[0], ih0 = ih[0], il0 = il[0];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const float orh = __shfl_down_sync(0xffffffffu, rh, o), orl = __shfl_down_sync(0xffffffffu, rl, o);
-            const float oih = __shfl_down_sync(0xffffffffu, ih, o), oil = __shfl_down_sync(0xffffffffu, il, o);
-            df_add(rh, rl, orh, orl);
-            df_add(ih, il, oih, oil);
+            const float orh = __shfl_down_sync(0xffffffffu, rh0, o), orl = __shfl_down_sync(0xffffffffu, rl0, o);
+            const float oih = __shfl_down_sync(0xffffffffu, ih0, o), oil = __shfl_down_sync(0xffffffffu, il0, o);
+            df_add(rh0, rl0, orh, orl);
+            df_add(ih0, il0, oih, oil);
         }
         if (lane == 0) {
-            df_norm(rh, rl);
-            df_norm(ih, il);
-            outf[row] = make_float2(rh, ih);
+            df_norm(rh0, rl0);
+            df_norm(ih0, il0);
+            outf[row] = make_float2(rh0, ih0);
         }
     }
 }

@@ -150,7 +150,9 @@ struct KrylovBufs {
     long long ld;      // leading dimension between basis vectors (elements)
     int nblk;          // blocks of the reduction kernels
     int nblk_dot;      // blocks of the delayed-CGS2 dot pass (rows of part; >= nblk)
-    double2* V;        // (maxit+1) x ld per entry
+    double2* V;        // complex128 basis: (maxit+1) x ld per entry, or only slot 0 (the masked
+                       // right-hand side) when vfull == 0 (the double-float path keeps no FP64 basis)
+    int vfull;
     float2* V32;       // (maxit+1) x ld complex64 roundings of the basis (mixed-precision CGS2), or null
     float2* V32lo;     // (maxit+1) x ld complex64 remainders: V32 + V32lo is the basis as double-float pairs
     double* sigma;     // (maxit+1): basis vector i = sigma[i] * V_i
@@ -168,6 +170,7 @@ struct KrylovBufs {
     KState* st;        // 1
     int* active;       // one counter per batch: entries not yet done
     long long sV() const { return (long long)(maxit + 1) * ld; }
+    long long sVd() const { return vfull ? sV() : ld; }   // per-entry stride of V
     long long sH() const { return (long long)(maxit + 1) * maxit; }
     long long sS() const { return maxit + 1; }
     long long sN() const { return maxit + 2; }

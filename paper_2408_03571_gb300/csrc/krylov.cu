@@ -291,8 +291,9 @@ __device__ double givens_column(int jc, double2* col, const double* scs, const d
 // The preconditioner of step j is applied to u~_j / |u~_j|: the flexible
 // Arnoldi relation A Z = Q H holds for any z_j, and span{u~_0..u~_j} equals
 // span{q_0..q_j}, so the iterates are those of FGMRES with z_j = M q_j.
-// Row layout of the dot partials per block: alpha at [0, S), b at [S, 2S),
-// c at 2S, d at 2S+1 (S = maxit+1).
+// Row layout of the dot partials per block (16 B slots): alpha at [0, S) as FP32
+// double-float pairs (hi.re, lo.re, hi.im, lo.im), b at [S, 2S) as complex64 in
+// the first 8 bytes, c at 2S and d at 2S+1 as complex128 (S = maxit+1).
 
 template <int G>
 __global__ void __launch_bounds__(kRedThreads, 4) k_dcgs_dot(int j, long long Np, long long ldp, int ps, int S,
@@ -394,8 +395,9 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_dcgs_dot(int j, long long Np
 #pragma unroll
             for (int t = 0; t < G; ++t)
                 if (i0 + t < j) {
-                    part[i0 + t] = make_double2((double)rh[t] + (double)rl[t], (double)ih[t] + (double)il[t]);
-                    part[S + i0 + t] = to_d(bb[t]);
+                    // raw FP32 words; the reduction converts (FP64 instructions stay out of this kernel)
+                    reinterpret_cast<float4*>(part)[i0 + t] = make_float4(rh[t], rl[t], ih[t], il[t]);
+                    reinterpret_cast<float4*>(part)[S + i0 + t] = make_float4(bb[t].x, bb[t].y, 0.f, 0.f);
                 }
         }
     }
@@ -403,6 +405,7 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_dcgs_dot(int j, long long Np
 
 // Cross-block sums of the dot pass, one warp per value (fixed order):
 // h2[i] = sigma_i alpha_i, hn[i] = sigma_i b_i (i < j), hn[j] = c, hn[j+1] = d.
+// The alpha and b partials arrive as FP32 words (see k_dcgs_dot), c and d as FP64.
 __global__ void k_dcgs_reduce(int j, int nblk, int ps, int S, const double2* __restrict__ part, long long sP,
                               const double* __restrict__ sigma, double2* __restrict__ h2, double2* __restrict__ hn,
                               long long sS, long long sN, const KState* __restrict__ st) {
@@ -414,7 +417,17 @@ __global__ void k_dcgs_reduce(int j, int nblk, int ps, int S, const double2* __r
     part += r * sP; sigma += r * sS; h2 += r * sS; hn += r * sN;
     const int col = k < j ? k : (k < 2 * j ? S + (k - j) : 2 * S + (k - 2 * j));
     double2 s = make_double2(0.0, 0.0);
-    for (int b = lane; b < nblk; b += 32) s = cadd(s, part[(size_t)b * ps + col]);
+    if (k < 2 * j) {
+        // alpha: double-float pairs (hi.re, lo.re, hi.im, lo.im); b: complex64 in .x, .y
+        const float4* pf = reinterpret_cast<const float4*>(part);
+        for (int b = lane; b < nblk; b += 32) {
+            const float4 v = pf[(size_t)b * ps + col];
+            if (k < j) { s.x += (double)v.x + (double)v.y; s.y += (double)v.z + (double)v.w; }
+            else { s.x += (double)v.x; s.y += (double)v.y; }
+        }
+    } else {
+        for (int b = lane; b < nblk; b += 32) s = cadd(s, part[(size_t)b * ps + col]);
+    }
     s = warp_sum(s);
     if (lane == 0) {
         if (k < j) h2[k] = cscale(s, sigma[k]);
@@ -497,7 +510,7 @@ __global__ void __launch_bounds__(kFinThreads) k_dcgs_finish(int j, int maxit, i
 // Update pass of step j (two entries per lane): V_j = u~_j - sum_i (sigma_i alpha_i) V_i
 // (the small reorthogonalisation sum in complex64, its subtraction in double-float),
 // w = w - sum_i (sigma_i b_i) V_i - (h_jj sigma_j) V_j in double-float;
-// npart[b] = sum_e |w[e]|^2.
+// npart[b] = sum_e |w[e]|^2 (FP32 on the leading words: it only sets a scale).
 __global__ void __launch_bounds__(kRedThreads, 3) k_dcgs_update(int j, long long Np, long long ldp,
                                                              float4* __restrict__ V32, float4* __restrict__ V32lo,
                                                              long long sVp, const double* __restrict__ sigma,
@@ -526,7 +539,7 @@ __global__ void __launch_bounds__(kRedThreads, 3) k_dcgs_update(int j, long long
     __syncthreads();
     long long e0, e1;
     chunk_of(Np, e0, e1);
-    double nrm = 0.0;
+    float nrmf = 0.f;
     for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         float a0h = 0.f, a0l = 0.f, b0h = 0.f, b0l = 0.f, a1h = 0.f, a1l = 0.f, b1h = 0.f, b1l = 0.f;
         float2 s0 = make_float2(0.f, 0.f), s1 = s0;
@@ -577,10 +590,10 @@ __global__ void __launch_bounds__(kRedThreads, 3) k_dcgs_update(int j, long long
         df_add(yh.w, yl.w, -b1h, -b1l); df_norm(yh.w, yl.w);
         wh[e] = yh;
         wl[e] = yl;
-        const double p = (double)yh.x + (double)yl.x, q = (double)yh.y + (double)yl.y;
-        const double u = (double)yh.z + (double)yl.z, v = (double)yh.w + (double)yl.w;
-        nrm = fma(p, p, fma(q, q, fma(u, u, fma(v, v, nrm))));
+        // |u~_{j+1}| only scales the next preconditioner input: FP32 on the leading words
+        nrmf = fmaf(yh.x, yh.x, fmaf(yh.y, yh.y, fmaf(yh.z, yh.z, fmaf(yh.w, yh.w, nrmf))));
     }
+    const double nrm = nrmf;
     block_norm_part(nrm, npart + (size_t)r * nblk);
 }
 
@@ -785,7 +798,7 @@ static void set_coef_smem_limit(const void* fn, size_t bytes) {
 }
 
 void launch_norm_init(const Ctx& cx, const KrylovBufs& kb, int nb, double tol) {
-    k_norm_part<<<dim3(kb.nblk, nb), kRedThreads, 0, cx.stream>>>(kb.N, kb.V, kb.sV(), kb.npart, kb.nblk);
+    k_norm_part<<<dim3(kb.nblk, nb), kRedThreads, 0, cx.stream>>>(kb.N, kb.V, kb.sVd(), kb.npart, kb.nblk);
     k_init_state<<<1, 256, 0, cx.stream>>>(nb, kb.nblk, tol, kb.npart, kb.sigma, kb.sigt, kb.g, kb.sS(), kb.st,
                                            kb.active);
 }

@@ -369,11 +369,15 @@ __global__ void __launch_bounds__(1024) k_tile_solve(OpDesc op, CoarseTab ct, co
     const int row = tid / TPR, sub = tid % TPR;
     const bool active = row < mx;
     int q_fail = -1;
+    __shared__ int s_fail;
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
     for (int q = 0; q < nsteps; ++q) {
         const int st = q % NST;
         const uint32_t parity = (uint32_t)((q / NST) & 1);
-        const bool ok = mbar_wait_bounded(&bar[st], parity);
-        if (__syncthreads_or(!ok)) { q_fail = q; break; }
+        // a thread whose wait expires flags it and finishes the step on whatever the
+        // stage holds; the step's closing barrier then ends the sweep for every thread
+        if (!mbar_wait_bounded(&bar[st], parity)) s_fail = 1;
         const C* Wq = wst + (size_t)st * bs;
         const C* rc = r + (size_t)(q & 1) * T * mx;
         C* rn = r + (size_t)((q + 1) & 1) * T * mx;
@@ -397,8 +401,16 @@ __global__ void __launch_bounds__(1024) k_tile_solve(OpDesc op, CoarseTab ct, co
                 acc[t].y += __shfl_xor_sync(0xffffffffu, acc[t].y, o);
             }
         }
-        if (active && sub == 0) tile_step_finish<R, T>(q < my, blk(q), my, mx, row, acc, g, rn, cy);
+        // lane sub == t of the row completes tile t (all lanes hold the row sums)
+        if (active) {
+#pragma unroll
+            for (int t = 0; t < T; ++t)
+                if (sub == t)
+                    tile_step_finish<R, 1>(q < my, blk(q), my, mx, row, &acc[t], g + (size_t)t * mx * my,
+                                           rn + (size_t)t * mx, cy);
+        }
         __syncthreads();   // stage st fully read; next r complete
+        if (s_fail) { q_fail = q; break; }
         if (tid == 0 && q + NST < nsteps) {
             mbar_expect_tx(&bar[st], bbytes);
             bulk_g2s(wst + (size_t)st * bs, Wt + (size_t)blk(q + NST) * bs, bbytes, &bar[st]);

@@ -94,16 +94,26 @@ typedef struct {
     int overlap;
 } hzs_grid_desc;
 
+/* How the exact coarse solve A_0^{-1} (Eq. 4) is carried out.  Both are exact
+ * up to rounding; they differ in cost.  DENSE: explicit inverse by Gauss-Jordan,
+ * one dense matrix-vector product per apply (memory |G_H|^2).  BLOCK: block-
+ * tridiagonal LU over groups of coarse rows (2 rows for B_2, 1 for P_1), 2m - 1
+ * dependent block products per apply (memory ~3 |G_H|^{3/2} s).  AUTO: DENSE up
+ * to 4096 coarse unknowns, BLOCK above. */
+typedef enum { HZS_COARSE_SOLVER_AUTO = 0, HZS_COARSE_SOLVER_DENSE = 1, HZS_COARSE_SOLVER_BLOCK = 2 } hzs_coarse_solver;
+
 /* Preconditioner set-up (Sections 3 and 4).
- *   coarse_ratio: p = H/h, >= 2, must divide n-1 (ignored for HZS_AS1).
- *   dedup_tiles : nonzero lets subdomains with identical local matrices share
- *                 one factorisation (only possible for constant k). */
+ *   coarse_ratio : p = H/h, >= 2, must divide n-1 (ignored for HZS_AS1).
+ *   dedup_tiles  : nonzero lets subdomains with identical local matrices share
+ *                  one factorisation (only possible for constant k).
+ *   coarse_solver: an hzs_coarse_solver (0 = AUTO). */
 typedef struct {
     hzs_precond_kind kind;
     hzs_coarse_kind coarse;
     int coarse_ratio;
     hzs_precision precision;
     int dedup_tiles;
+    int coarse_solver;
 } hzs_precond_desc;
 
 /* GMRES controls (Section 5): right preconditioning, zero initial guess, no

@@ -56,6 +56,8 @@ struct hzs_precond {
     float *wf = nullptr, *wtf = nullptr;
     double2* Ainv = nullptr;
     float4* Ainv_df = nullptr;        // MIXED: double-float copy of Ainv (FP32-pipe coarse product)
+    int coarse_block = 0;             // coarse solve by block-tridiagonal LU instead of Ainv
+    CoarseBlockLU cblk;
     float2* c2f = nullptr;            // complex64 copy of the coarse solution
     int* err = nullptr;               // device error word (HZS_ERR_TIMEOUT from bounded waits)
     int* groups_d = nullptr;          // tiles grouped by shared factor
@@ -117,6 +119,9 @@ static cudaError_t dalloc(T** p, size_t count) {
 static size_t cplx_size(hzs_precision prec) { return prec == HZS_MIXED ? sizeof(float2) : sizeof(double2); }
 
 static hzs_status ensure_work(hzs_precond* p, int nb);
+
+// largest coarse space solved through an explicit inverse when the solver is AUTO
+constexpr int kDenseCoarseMax = 4096;
 
 // ------------------------------------------------------------------ grid
 extern "C" hzs_status hzs_grid_create(const hzs_grid_desc* d, void* cuda_stream, hzs_grid** out) {
@@ -237,6 +242,7 @@ extern "C" void hzs_precond_destroy(hzs_precond* p) {
     free_krylov(p);
     cudaFree(p->c0); cudaFree(p->lo); cudaFree(p->hi); cudaFree(p->off); cudaFree(p->w); cudaFree(p->wt);
     cudaFree(p->wf); cudaFree(p->wtf); cudaFree(p->c2f); cudaFree(p->err); cudaFree(p->groups_d);
+    coarse_block_free(p->cblk);
     cudaFree(p->Ainv); cudaFree(p->Ainv_df); cudaFree(p->W64); cudaFree(p->W32); cudaFree(p->tiles_d); cudaFree(p->cover_d);
     cudaFree(p->t_buf); cudaFree(p->c_buf); cudaFree(p->c2_buf); cudaFree(p->w_buf); cudaFree(p->ytiles);
     cudaFree(p->zc64);
@@ -272,7 +278,12 @@ static hzs_status setup_impl(hzs_grid* g, const hzs_precond_desc* d, hzs_precond
         if (p->hct.nc1 < 1) return fail(g, HZS_ERR_INVALID_ARG, "coarse mesh has no interior nodes");
         if (p->hct.bad) return fail(g, HZS_ERR_INVALID_ARG, "coarse basis wider than three coarse cells");
         p->Nc = p->hct.nc1 * p->hct.nc1;
-        if (p->Nc > 8192) return fail(g, HZS_ERR_INVALID_ARG, "coarse space larger than 8192 (dense coarse solve)");
+        p->coarse_block = d->coarse_solver == HZS_COARSE_SOLVER_BLOCK ||
+                          (d->coarse_solver == HZS_COARSE_SOLVER_AUTO && p->Nc > kDenseCoarseMax);
+        if (!p->coarse_block && p->Nc > 8192)
+            return fail(g, HZS_ERR_INVALID_ARG, "coarse space larger than 8192 for the dense coarse inverse");
+        if (p->coarse_block && p->hct.nc1 > 512)
+            return fail(g, HZS_ERR_INVALID_ARG, "more than 512 coarse nodes per axis for the block coarse solve");
         HZS_CUDA(g, upload(&p->c0, p->hct.c0, s));
         HZS_CUDA(g, upload(&p->w, p->hct.w, s));
         HZS_CUDA(g, upload(&p->lo, p->hct.lo, s));
@@ -288,6 +299,20 @@ static hzs_status setup_impl(hzs_grid* g, const hzs_precond_desc* d, hzs_precond
         p->cx.ct.c0 = p->c0; p->cx.ct.w = p->w; p->cx.ct.lo = p->lo; p->cx.ct.hi = p->hi;
         p->cx.ct.off = p->off; p->cx.ct.wt = p->wt;
         p->cx.ct.wf = p->wf; p->cx.ct.wtf = p->wtf;
+        if (p->coarse_block) {
+            double2* A0b = nullptr;
+            HZS_CUDA(g, dalloc(&A0b, (size_t)p->Nc * 25));
+            launch_galerkin_banded(p->cx, A0b);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) { cudaFree(A0b); return cuda_fail(g, e, "coarse assembly"); }
+            double minpiv = 0.0;
+            const int rc = coarse_block_setup(p->cx, p->hct.nc1, d->coarse == HZS_COARSE_B2 ? 2 : 1, A0b, p->cblk,
+                                              &minpiv);
+            cudaFree(A0b);
+            if (rc < 0) return fail(g, HZS_ERR_CUDA, "coarse block factorisation failed");
+            p->coarse_minpiv = minpiv;
+            if (rc > 0) return fail(g, HZS_ERR_SINGULAR_COARSE, "coarse matrix A_0 has a zero pivot");
+        } else {
         HZS_CUDA(g, dalloc(&p->Ainv, (size_t)p->Nc * p->Nc));
         launch_galerkin(p->cx, p->Ainv);
         HZS_CUDA(g, cudaGetLastError());
@@ -300,6 +325,7 @@ static hzs_status setup_impl(hzs_grid* g, const hzs_precond_desc* d, hzs_precond
             HZS_CUDA(g, dalloc(&p->Ainv_df, (size_t)p->Nc * p->Nc));
             launch_split_df(p->cx, (long long)p->Nc * p->Nc, p->Ainv, p->Ainv_df);
             HZS_CUDA(g, cudaGetLastError());
+        }
         }
     }
     HZS_CUDA(g, dalloc(&p->err, 1));
@@ -393,6 +419,8 @@ extern "C" hzs_status hzs_precond_setup(hzs_grid* g, const hzs_precond_desc* d, 
     if (!g || !d) return fail(g, HZS_ERR_INVALID_ARG, "grid or desc is NULL");
     if (d->kind < HZS_AS1 || d->kind > HZS_SHS2) return fail(g, HZS_ERR_INVALID_ARG, "bad preconditioner kind");
     if (d->precision != HZS_FP64 && d->precision != HZS_MIXED) return fail(g, HZS_ERR_INVALID_ARG, "bad precision");
+    if (d->coarse_solver < HZS_COARSE_SOLVER_AUTO || d->coarse_solver > HZS_COARSE_SOLVER_BLOCK)
+        return fail(g, HZS_ERR_INVALID_ARG, "bad coarse_solver");
     hzs_precond* p = new hzs_precond();
     p->g = g;
     p->desc = *d;
@@ -450,7 +478,9 @@ static hzs_status precond_apply(hzs_precond* p, int nb, const Cv* v, long long v
     const int kind = p->desc.kind;
     if (p->use_coarse) {
         launch_restrict<Cv, R>(cx, nb, v, vs, vscale, vss, (C*)p->t_buf, p->c_buf, sk);
-        if (f32 && p->Ainv_df)
+        if (p->coarse_block)
+            launch_coarse_block_solve(cx, nb, p->cblk, p->c_buf, p->c2_buf, f32 ? p->c2f : nullptr, sk);
+        else if (f32 && p->Ainv_df)
             launch_coarse_matvec_df(cx, nb, p->Ainv_df, p->Nc, p->c_buf, p->c2f, sk);
         else
             launch_coarse_matvec(cx, nb, p->Ainv, p->Nc, p->c_buf, p->c2_buf, f32 ? p->c2f : nullptr, sk);
@@ -873,6 +903,10 @@ hzs_status hzs_internal_set_error(hzs_precond* p, hzs_status s, const std::strin
 
 hzs_status hzs_internal_noalloc_view(hzs_precond* p, NoAllocView* v, std::string* err) {
     if (!p) return fail(nullptr, HZS_ERR_INVALID_ARG, "precond is NULL");
+    if (p->coarse_block)
+        return fail(p->g, HZS_ERR_INVALID_ARG,
+                    "the allocation-free apply supports the dense coarse inverse only (coarse_solver DENSE/AUTO "
+                    "with at most 4096 coarse unknowns)");
     v->cx = p->cx;
     v->kind = p->desc.kind;
     v->precision = p->desc.precision;

@@ -227,7 +227,7 @@ __global__ void k_coarse_matvec_df(int Nc, const float4* __restrict__ Adf, const
 // ------------------------------------------------------------------ Galerkin A_0
 // A0[(J,I), (J+dJ, I+dI)] = sum_{fine (i,j)} phi_I(i) phi_J(j) (A phi_{I+dI, J+dJ})(i, j)
 // One block per (row, offset) pair; offsets |dI|, |dJ| <= 2 cover B_2 (P_1 uses <= 1).
-__global__ void k_galerkin(OpDesc op, CoarseTab ct, double2* __restrict__ A0) {
+__global__ void k_galerkin(OpDesc op, CoarseTab ct, double2* __restrict__ A0, int banded) {
     const int nc1 = ct.nc1;
     const int row = blockIdx.x;
     const int o = blockIdx.y;              // 0..24
@@ -269,7 +269,10 @@ __global__ void k_galerkin(OpDesc op, CoarseTab ct, double2* __restrict__ A0) {
     if (threadIdx.x < 32) {
         double2 v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : make_double2(0.0, 0.0);
         v = warp_sum(v);
-        if (threadIdx.x == 0) A0[(size_t)row * (nc1 * nc1) + (size_t)J2 * nc1 + I2] = v;
+        if (threadIdx.x == 0) {
+            if (banded) A0[(size_t)row * 25 + o] = v;
+            else A0[(size_t)row * (nc1 * nc1) + (size_t)J2 * nc1 + I2] = v;
+        }
     }
 }
 
@@ -409,7 +412,15 @@ void launch_galerkin(const Ctx& cx, double2* A0) {
     const int Nc = nc1 * nc1;
     cudaMemsetAsync(A0, 0, (size_t)Nc * Nc * sizeof(double2), cx.stream);
     dim3 grid(Nc, 25);
-    k_galerkin<<<grid, 256, 0, cx.stream>>>(cx.op, cx.ct, A0);
+    k_galerkin<<<grid, 256, 0, cx.stream>>>(cx.op, cx.ct, A0, 0);
+}
+
+void launch_galerkin_banded(const Ctx& cx, double2* A0b) {
+    const int nc1 = cx.ct.nc1;
+    const int Nc = nc1 * nc1;
+    cudaMemsetAsync(A0b, 0, (size_t)Nc * 25 * sizeof(double2), cx.stream);
+    dim3 grid(Nc, 25);
+    k_galerkin<<<grid, 256, 0, cx.stream>>>(cx.op, cx.ct, A0b, 1);
 }
 
 // Returns 0 on success, 1 if a pivot was zero; *minpiv receives min |pivot|.

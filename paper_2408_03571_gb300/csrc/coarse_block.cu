@@ -1,0 +1,198 @@
+// Exact coarse solve A_0 c' = c (Eq. 4, Section 4) by block-tridiagonal LU, for
+// coarse spaces too large for the dense inverse (|G_H| up to 40 401 in the
+// H = 4h experiments of Section 5).
+//
+// Coarse unknown (J, I) has index J nc1 + I.  A coarse basis function couples
+// coarse rows J and J + dJ only for |dJ| <= s (s = 2 for B_2, 1 for P_1), so
+// grouping s consecutive coarse rows into one block row gives a block-
+// tridiagonal matrix with blocks of size b_i = (rows in group i) * nc1:
+//   D_i (b_i x b_i), L_i (b_i x b_{i-1}), U_i (b_i x b_{i+1}).
+// Set-up (FP64): S_0 = D_0, S_i = D_i - L_i Q_{i-1};  W_i = S_i^{-1} (Gauss-Jordan
+// with partial pivoting), P_i = W_i L_i, Q_i = W_i U_i.
+// Solve: y_0 = W_0 c_0, y_i = W_i c_i - P_i y_{i-1};  x_{m-1} = y_{m-1},
+// x_i = y_i - Q_i x_{i+1}: 2m - 1 dependent dense matrix-vector products, each a
+// kernel with one warp per row.
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace hzs {
+
+// dst (rows x cols, row-major) = the block of the banded A_0 with row range
+// [r0, r0+rows) and column range [c0, c0+cols); the band holds 25 offsets
+// (dI, dJ) in [-2, 2]^2 per row, offset index o = (dJ + 2) * 5 + (dI + 2).
+__global__ void k_band_to_block(int nc1, const double2* __restrict__ A0b, int r0, int rows, int c0, int cols,
+                                double2* __restrict__ dst) {
+    const long long total = (long long)rows * cols;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int rr = (int)(t / cols), cc = (int)(t % cols);
+        const int row = r0 + rr, col = c0 + cc;
+        const int I = row % nc1, J = row / nc1, I2 = col % nc1, J2 = col / nc1;
+        const int dI = I2 - I, dJ = J2 - J;
+        double2 v = make_double2(0.0, 0.0);
+        if (dI >= -2 && dI <= 2 && dJ >= -2 && dJ <= 2) v = A0b[(size_t)row * 25 + (dJ + 2) * 5 + (dI + 2)];
+        dst[t] = v;
+    }
+}
+
+// C (M x N) = beta C + alpha A (M x K) B (K x N), complex FP64, row-major.
+// 16 x 16 output tile per block, K in steps of 16 through shared memory.
+__global__ void k_zgemm(int M, int N, int K, double alpha, const double2* __restrict__ A, int lda,
+                        const double2* __restrict__ B, int ldb, double beta, double2* __restrict__ C, int ldc) {
+    __shared__ double2 As[16][17], Bs[16][17];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int row = blockIdx.y * 16 + ty, col = blockIdx.x * 16 + tx;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        As[ty][tx] = (row < M && k0 + tx < K) ? A[(size_t)row * lda + k0 + tx] : make_double2(0.0, 0.0);
+        Bs[ty][tx] = (k0 + ty < K && col < N) ? B[(size_t)(k0 + ty) * ldb + col] : make_double2(0.0, 0.0);
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) acc = cfma(As[ty][k], Bs[k][tx], acc);
+        __syncthreads();
+    }
+    if (row < M && col < N) {
+        double2 c = beta != 0.0 ? cscale(C[(size_t)row * ldc + col], beta) : make_double2(0.0, 0.0);
+        c.x += alpha * acc.x; c.y += alpha * acc.y;
+        C[(size_t)row * ldc + col] = c;
+    }
+}
+
+static void zgemm(const Ctx& cx, int M, int N, int K, double alpha, const double2* A, int lda, const double2* B,
+                  int ldb, double beta, double2* C, int ldc) {
+    const dim3 blk(16, 16), grd((N + 15) / 16, (M + 15) / 16);
+    k_zgemm<<<grd, blk, 0, cx.stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
+// One block step of the solve, batch entry r = blockIdx.y, one warp per row:
+//   out[row] = sign_a * (Ma x_a)[row] + sign_b * (Mb x_b)[row] + (base ? base[row] : 0)
+// (Ma: rows x na, Mb: rows x nb, either may be absent).
+__global__ void k_cb_step(int rows, const double2* __restrict__ Ma, const double2* __restrict__ xa, int na,
+                          const double2* __restrict__ Mb, const double2* __restrict__ xb, int nbc,
+                          const double2* __restrict__ base, double2* __restrict__ out, long long stride,
+                          BatchSkip sk) {
+    const int r = blockIdx.y;
+    if (sk.flag && sk.flag[(size_t)r * sk.stride]) return;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= rows) return;
+    const long long off = (long long)r * stride;
+    double2 acc = make_double2(0.0, 0.0);
+    if (Ma) {
+        const double2* m = Ma + (size_t)warp * na;
+        const double2* x = xa + off;
+        for (int k = lane; k < na; k += 32) acc = cfma(m[k], x[k], acc);
+    }
+    if (Mb) {
+        const double2* m = Mb + (size_t)warp * nbc;
+        const double2* x = xb + off;
+        for (int k = lane; k < nbc; k += 32) acc = cfms(m[k], x[k], acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) {
+        if (base) acc = cadd(acc, base[off + warp]);
+        out[off + warp] = acc;
+    }
+}
+
+__global__ void k_c128_to_c64_batched(int Nc, const double2* __restrict__ a, float2* __restrict__ b, BatchSkip sk) {
+    const int r = blockIdx.y;
+    if (sk.flag && sk.flag[(size_t)r * sk.stride]) return;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Nc; e += gridDim.x * blockDim.x)
+        b[(size_t)r * Nc + e] = to_f(a[(size_t)r * Nc + e]);
+}
+
+int coarse_block_setup(const Ctx& cx, int nc1, int s, const double2* A0b, CoarseBlockLU& lu, double* minpiv) {
+    lu = CoarseBlockLU{};
+    lu.nc1 = nc1;
+    lu.s = s;
+    lu.m = (nc1 + s - 1) / s;
+    const int m = lu.m;
+    std::vector<int> b(m), r0(m);
+    for (int i = 0; i < m; ++i) {
+        r0[i] = i * s * nc1;
+        b[i] = (std::min(nc1, (i + 1) * s) - i * s) * nc1;
+    }
+    long long wsz = 0, psz = 0, qsz = 0;
+    std::vector<long long> wo(m), po(m), qo(m);
+    for (int i = 0; i < m; ++i) {
+        wo[i] = wsz; wsz += (long long)b[i] * b[i];
+        po[i] = psz; if (i > 0) psz += (long long)b[i] * b[i - 1];
+        qo[i] = qsz; if (i + 1 < m) qsz += (long long)b[i] * b[i + 1];
+    }
+    const int bmax = s * nc1;
+    double2 *D = nullptr, *Lb = nullptr, *Ub = nullptr;
+    auto fail = [&]() {
+        cudaFree(D); cudaFree(Lb); cudaFree(Ub);
+        cudaFree(lu.W); cudaFree(lu.P); cudaFree(lu.Q);
+        lu = CoarseBlockLU{};
+        return -1;
+    };
+    if (cudaMalloc(&lu.W, (size_t)wsz * sizeof(double2)) != cudaSuccess) return fail();
+    if (cudaMalloc(&lu.P, (size_t)(psz > 0 ? psz : 1) * sizeof(double2)) != cudaSuccess) return fail();
+    if (cudaMalloc(&lu.Q, (size_t)(qsz > 0 ? qsz : 1) * sizeof(double2)) != cudaSuccess) return fail();
+    if (cudaMalloc(&D, (size_t)bmax * bmax * sizeof(double2)) != cudaSuccess) return fail();
+    if (cudaMalloc(&Lb, (size_t)bmax * bmax * sizeof(double2)) != cudaSuccess) return fail();
+    if (cudaMalloc(&Ub, (size_t)bmax * bmax * sizeof(double2)) != cudaSuccess) return fail();
+    double mp = 1e300;
+    int singular = 0;
+    const int cb = 4 * cx.num_sms;
+    for (int i = 0; i < m; ++i) {
+        const int bi = b[i];
+        k_band_to_block<<<cb, 256, 0, cx.stream>>>(nc1, A0b, r0[i], bi, r0[i], bi, D);
+        if (i > 0) {
+            // S_i = D_i - L_i Q_{i-1}
+            k_band_to_block<<<cb, 256, 0, cx.stream>>>(nc1, A0b, r0[i], bi, r0[i - 1], b[i - 1], Lb);
+            zgemm(cx, bi, bi, b[i - 1], -1.0, Lb, b[i - 1], lu.Q + qo[i - 1], bi, 1.0, D, bi);
+        }
+        double piv = 0.0;
+        const int rc = gj_invert(cx, D, bi, &piv);      // D <- S_i^{-1}
+        if (rc < 0) return fail();
+        if (rc > 0) singular = 1;
+        mp = std::min(mp, piv);
+        if (cudaMemcpyAsync(lu.W + wo[i], D, (size_t)bi * bi * sizeof(double2), cudaMemcpyDeviceToDevice,
+                            cx.stream) != cudaSuccess)
+            return fail();
+        if (i > 0) zgemm(cx, bi, b[i - 1], bi, 1.0, lu.W + wo[i], bi, Lb, b[i - 1], 0.0, lu.P + po[i], b[i - 1]);
+        if (i + 1 < m) {
+            k_band_to_block<<<cb, 256, 0, cx.stream>>>(nc1, A0b, r0[i], bi, r0[i + 1], b[i + 1], Ub);
+            zgemm(cx, bi, b[i + 1], bi, 1.0, lu.W + wo[i], bi, Ub, b[i + 1], 0.0, lu.Q + qo[i], b[i + 1]);
+        }
+    }
+    const cudaError_t e = cudaStreamSynchronize(cx.stream);
+    cudaFree(D); cudaFree(Lb); cudaFree(Ub);
+    if (e != cudaSuccess) { cudaFree(lu.W); cudaFree(lu.P); cudaFree(lu.Q); lu = CoarseBlockLU{}; return -1; }
+    lu.b = b; lu.r0 = r0; lu.wo = wo; lu.po = po; lu.qo = qo;
+    *minpiv = mp;
+    return singular ? 1 : 0;
+}
+
+void coarse_block_free(CoarseBlockLU& lu) {
+    cudaFree(lu.W); cudaFree(lu.P); cudaFree(lu.Q);
+    lu = CoarseBlockLU{};
+}
+
+void launch_coarse_block_solve(const Ctx& cx, int nb, const CoarseBlockLU& lu, const double2* c, double2* out,
+                               float2* outf, BatchSkip sk) {
+    const int m = lu.m, Nc = lu.nc1 * lu.nc1;
+    const int threads = 256, wpb = threads / 32;
+    // forward: out_i = W_i c_i - P_i out_{i-1}
+    for (int i = 0; i < m; ++i) {
+        const int bi = lu.b[i];
+        const dim3 grd((bi + wpb - 1) / wpb, nb);
+        k_cb_step<<<grd, threads, 0, cx.stream>>>(bi, lu.W + lu.wo[i], c + lu.r0[i], bi,
+                                                  i > 0 ? lu.P + lu.po[i] : nullptr,
+                                                  i > 0 ? out + lu.r0[i - 1] : nullptr, i > 0 ? lu.b[i - 1] : 0,
+                                                  nullptr, out + lu.r0[i], Nc, sk);
+    }
+    // backward: out_i = out_i - Q_i out_{i+1}
+    for (int i = m - 2; i >= 0; --i) {
+        const int bi = lu.b[i];
+        const dim3 grd((bi + wpb - 1) / wpb, nb);
+        k_cb_step<<<grd, threads, 0, cx.stream>>>(bi, nullptr, nullptr, 0, lu.Q + lu.qo[i], out + lu.r0[i + 1],
+                                                  lu.b[i + 1], out + lu.r0[i], out + lu.r0[i], Nc, sk);
+    }
+    if (outf) k_c128_to_c64_batched<<<dim3((Nc + 255) / 256, nb), 256, 0, cx.stream>>>(Nc, out, outf, sk);
+}
+
+}  // namespace hzs

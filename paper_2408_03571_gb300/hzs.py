@@ -24,6 +24,7 @@ ERR_SINGULAR_LOCAL, ERR_SINGULAR_COARSE, ERR_NONFINITE, ERR_TIMEOUT, ERR_BREAKDO
 DIRICHLET, SOMMERFELD = 0, 1
 AS1, AS2, SAS2, SHS2 = 0, 1, 2, 3
 COARSE_NONE, COARSE_P1, COARSE_B2 = 0, 1, 2
+COARSE_SOLVER_AUTO, COARSE_SOLVER_DENSE, COARSE_SOLVER_BLOCK = 0, 1, 2
 FP64, MIXED = 0, 1
 
 EXPORTS = (
@@ -41,7 +42,7 @@ class GridDesc(ct.Structure):
 
 class PrecondDesc(ct.Structure):
     _fields_ = [("kind", ct.c_int), ("coarse", ct.c_int), ("coarse_ratio", ct.c_int),
-                ("precision", ct.c_int), ("dedup_tiles", ct.c_int)]
+                ("precision", ct.c_int), ("dedup_tiles", ct.c_int), ("coarse_solver", ct.c_int)]
 
 
 SOLVE_PROFILE = 1
@@ -185,11 +186,11 @@ class Preconditioner:
     """Factorised Schwarz preconditioner (Sections 3-4) on a Grid."""
 
     def __init__(self, grid: Grid, kind: int = SHS2, coarse: int = COARSE_B2, coarse_ratio: int = 2,
-                 precision: int = FP64, dedup_tiles: bool = True):
+                 precision: int = FP64, dedup_tiles: bool = True, coarse_solver: int = 0):
         lib = load()
         self.grid = grid
         self.kind, self.coarse, self.coarse_ratio, self.precision = kind, coarse, coarse_ratio, precision
-        d = PrecondDesc(kind, coarse, coarse_ratio, precision, int(dedup_tiles))
+        d = PrecondDesc(kind, coarse, coarse_ratio, precision, int(dedup_tiles), int(coarse_solver))
         h = ct.c_void_p()
         _check(lib.hzs_precond_setup(grid.handle, ct.byref(d), ct.byref(h)), grid.handle)
         self._h = h

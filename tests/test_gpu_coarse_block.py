@@ -1,0 +1,108 @@
+"""Block-tridiagonal coarse solve and the H = 4h regime of Section 5 (Tables 1-2).
+
+The coarse solve A_0^{-1} (Eq. 4) by block-tridiagonal LU must give the same
+preconditioner as the oracle's dense LU (exact to rounding: FP64 bar 1e-9, the
+complex64 preconditioner 1e-4) and the same GMRES step counts in the H_sub = H
+= 4h, kappa_h = 0.25, maximum-overlap regime of the paper's first two tables
+(checked at k = 20 against the oracle; larger k on the GPU alone, against the
+true residual).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import AS2, B2, DIRICHLET, P1, SAS2, SHS2, SOMMERFELD, Problem, Schwarz, gmres  # noqa: E402
+from paper_2408_03571_gb300.inputs import point_source, random_complex_grid  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+BC = {DIRICHLET: 0, SOMMERFELD: 1}
+KIND = {AS2: 1, SAS2: 2, SHS2: 3}
+COARSE = {P1: 1, B2: 2}
+DENSE, BLOCK = 1, 2
+
+
+@pytest.fixture(scope="module")
+def hzs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2408_03571_gb300 import build
+    build.build()
+    from paper_2408_03571_gb300 import hzs as mod
+    return mod
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def make(hzs, n, bc, k, nsub, ov, kind, coarse, p, prec, solver):
+    g = hzs.Grid(n, BC[bc], k=k, nsub=nsub, overlap=ov)
+    P = hzs.Preconditioner(g, KIND[kind], COARSE[coarse], p, prec, True, solver)
+    return g, P
+
+
+@pytest.mark.parametrize("bc", [DIRICHLET, SOMMERFELD])
+@pytest.mark.parametrize("coarse", [B2, P1])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_block_coarse_preconditioner(hzs, bc, coarse, prec):
+    # n = 65, H = 4h: 15 (MP-1) or 17 (MP-2) coarse nodes per axis, so the B_2 row
+    # pairs end with a one-row block
+    n, nsub, ov, p, k = 65, 4, 2, 4, 12.0
+    prob = Problem(n, bc, k * k)
+    A = prob.assemble_fast()
+    M = Schwarz(prob, A, nsub, ov, SHS2, coarse, p)
+    v = random_complex_grid(n, seed=17)
+    ref = prob.vec_to_grid(M.apply(prob.grid_to_vec(v)))
+    _, Pb = make(hzs, n, bc, k, nsub, ov, SHS2, coarse, p, prec, BLOCK)
+    _, Pd = make(hzs, n, bc, k, nsub, ov, SHS2, coarse, p, prec, DENSE)
+    zb = Pb.apply(dev(v)).cpu().numpy()
+    zd = Pd.apply(dev(v)).cpu().numpy()
+    assert rel(zb, ref) < (1e-9 if prec == 0 else 1e-4)
+    assert rel(zb, zd) < (1e-10 if prec == 0 else 1e-4)
+
+
+def table_case(k):
+    """Section 5, first two tables: kappa_h = k h = 0.25, H_sub = H = 4h, overlap 2."""
+    n = 4 * int(k) + 1
+    return n, int(k), 2, 4
+
+
+@pytest.mark.parametrize("bc", [SOMMERFELD, DIRICHLET])
+@pytest.mark.parametrize("kind,coarse", [(SHS2, B2), (SAS2, B2), (AS2, B2), (SHS2, P1), (SAS2, P1), (AS2, P1)])
+def test_table_regime_k20_vs_oracle(hzs, bc, kind, coarse):
+    k = 20.0
+    n, nsub, ov, p = table_case(k)
+    prob = Problem(n, bc, k * k)
+    A = prob.assemble_fast()
+    M = Schwarz(prob, A, nsub, ov, kind, coarse, p)
+    f = point_source(n)
+    ref = gmres(lambda x: A @ x, M.apply, prob.grid_to_vec(f), 1e-7, 100)
+    _, P = make(hzs, n, bc, k, nsub, ov, kind, coarse, p, 0, BLOCK)
+    u, info = P.solve(dev(f), tol=1e-7, maxit=100)
+    it = info[0].iterations
+    assert abs(it - ref.iterations) <= 1, (it, ref.iterations)
+    assert info[0].converged == ref.converged
+    if ref.converged:
+        uv = prob.grid_to_vec(u.cpu().numpy())
+        fv = prob.grid_to_vec(f)
+        assert np.linalg.norm(fv - A @ uv) / np.linalg.norm(fv) <= 1.01e-7
+
+
+@pytest.mark.parametrize("bc", [SOMMERFELD, DIRICHLET])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_table_regime_k100_gpu(hzs, bc, prec):
+    # |G_H| = 101^2 (MP-2) / 99^2 (MP-1) coarse unknowns: AUTO takes the block solver
+    k = 100.0
+    n, nsub, ov, p = table_case(k)
+    g = hzs.Grid(n, BC[bc], k=k, nsub=nsub, overlap=ov)
+    P = hzs.Preconditioner(g, KIND[SHS2], COARSE[B2], p, prec)
+    u, info = P.solve(dev(point_source(n)), tol=1e-7, maxit=100)
+    assert info[0].converged
+    assert info[0].relres_true <= 1.01e-7
+    assert info[0].iterations <= 30

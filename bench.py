@@ -43,6 +43,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dedup-arm", action="store_true",
                     help="skip the MIXED arm with every subdomain factored separately")
+    ap.add_argument("--workload", choices=["headline", "batched"], default="headline",
+                    help="batched: the MP-2 multi-problem batch (64 right-hand sides for each of "
+                         "(k, n) = (25, 257), (50, 257), (100, 513)) instead of the headline solve")
+    ap.add_argument("--nrhs", type=int, default=64, help="right-hand sides per problem (batched workload)")
     ap.add_argument("--cpu-steps", type=int, default=6, help="Arnoldi steps in the oracle sample")
     # smaller MP-1 instances of the same path, for profiling captures only
     ap.add_argument("--n", type=int, default=1025)
@@ -67,6 +71,21 @@ def dist_setup(args):
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def max_over_ranks(x: float, world: int, device="cpu") -> float:
+    """Largest x over the ranks of the default process group (x itself for one rank)."""
+    if world == 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: int, ms_max: float, world: int) -> float:
+    """Whole-job rate of N independent replicas: all ranks' units over the slowest rank's time."""
+    return world * units_per_rank / (ms_max * 1e-3)
 
 
 # ----------------------------------------------------------------- clocks
@@ -199,6 +218,100 @@ def reference_arm(args, world, rank):
 
 
 # ----------------------------------------------------------------- GPU arm
+# (k, n, subdomains per axis) of the batched MP-2 workload: 64-node subdomains, B_2 with
+# H = 32h; (200, 1025) of the same family does not converge (kH = 6.25) and is left out
+BATCHED = ((25.0, 257, 4), (50.0, 257, 4), (100.0, 513, 8))
+
+
+def batched_arm(args, world, rank, local):
+    """All problems of the batch solved concurrently (hzs_solve_batched), every right-hand
+    side a point source at a seeded interior node; one step = the whole batch."""
+    import numpy as np
+    import torch
+
+    from paper_2408_03571_gb300 import build, hzs
+    from paper_2408_03571_gb300.inputs import point_source, random_source_nodes
+
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    hzs.load()
+    dev = torch.device("cuda", local)
+    grids, precs, rhs_host, rhs = [], [], [], []
+    t0 = time.perf_counter()
+    for i, (k, n, nsub) in enumerate(BATCHED):
+        g = hzs.Grid(n, hzs.SOMMERFELD, k=k, nsub=nsub, overlap=2)
+        grids.append(g)
+        precs.append(hzs.Preconditioner(g, hzs.SHS2, hzs.COARSE_B2, 32, hzs.MIXED))
+        nodes = random_source_nodes(n, args.nrhs, 1000 + i)
+        fh = torch.from_numpy(np.stack([point_source(n, nd) for nd in nodes])).pin_memory()
+        rhs_host.append(fh)
+        rhs.append(fh.to(dev))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        hzs.solve_batched(precs, rhs, TOL, MAXIT)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = None
+    for _ in range(args.steps):
+        _, infos = hzs.solve_batched(precs, rhs, TOL, MAXIT)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    # end to end: right-hand sides from pinned host memory, solutions back, inside the timed region
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        fd = [f.to(dev, non_blocking=True) for f in rhs_host]
+        outs, _ = hzs.solve_batched(precs, fd, TOL, MAXIT)
+        for u in outs:
+            u.cpu()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    nsol = sum(len(r) for r in infos)
+    per = []
+    for (k, n, nsub), res in zip(BATCHED, infos):
+        its = [r.iterations for r in res]
+        per.append({"k": k, "n": n, "nrhs": len(res), "iterations_max": max(its),
+                    "iterations_mean": float(np.mean(its)),
+                    "converged": int(sum(r.converged for r in res)),
+                    "relres_true_max": max(r.relres_true for r in res)})
+    for P in precs:
+        P.close()
+    for g in grids:
+        g.close()
+    if rank != 0:
+        return
+    bytes_io = sum(f.numel() * 16 for f in rhs_host)
+    line = {
+        "metric": "batched MP-2 Helmholtz solves/s to rel. residual 1e-6 (3 problems x %d right-hand sides)"
+                  % args.nrhs,
+        "value": replica_throughput(nsol, ms / args.steps, world), "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64 preconditioner; Arnoldi basis as double-float (2 x f32) pairs; f64 Hessenberg",
+        "data": "synthetic",
+        "config": {"workload": "MP-2 batch: (k, n) = (25, 257), (50, 257), (100, 513), 64-node subdomains, "
+                               "overlap 2, SHS2 with B2 H=32h, point sources at seeded nodes, all problems "
+                               "solved concurrently, right-hand sides of a problem in lockstep",
+                   "l2": "working set larger than L2; no flush needed", "parallelism": f"replicas x{world}"},
+        "problems": per, "setup_s": setup_s,
+        "e2e": {"value": replica_throughput(nsol, ms_e2e / args.steps, world), "unit": "solves/s",
+                "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def gpu_arm(args, world, rank, local):
     import torch
 
@@ -226,13 +339,6 @@ def gpu_arm(args, world, rank, local):
             torch.distributed.barrier()
             torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
-
     def timed_solves(P, steps, warmup, e2e=False, profile=True):
         u = torch.empty_like(f)
         u_host = torch.empty_like(f_host).pin_memory()
@@ -254,7 +360,7 @@ def gpu_arm(args, world, rank, local):
         e1.record(stream)
         barrier()
         ms = e0.elapsed_time(e1)
-        return max_over_ranks(ms), infos, u
+        return max_over_ranks(ms, world, dev), infos, u
 
     out = {}
     # ---- mixed (headline)
@@ -276,7 +382,7 @@ def gpu_arm(args, world, rank, local):
         ms_n, infos_n, _ = timed_solves(Pn, max(1, args.steps // 2), 1)
         Pn.close()
         i0 = infos_n[-1]
-        dedup_off = {"value": world * len(infos_n) / (ms_n * 1e-3), "unit": "solves/s",
+        dedup_off = {"value": replica_throughput(len(infos_n), ms_n, world), "unit": "solves/s",
                      "ms_per_step": ms_n / len(infos_n), "iterations": i0.iterations,
                      "relres_true": i0.relres_true, "t_precond_ms": i0.t_precond_ms,
                      "note": "every subdomain factor stored and streamed separately (no sharing of "
@@ -291,7 +397,7 @@ def gpu_arm(args, world, rank, local):
         ms_d, infos_d, _ = timed_solves(Pd, max(1, args.steps // 2), 1)
         Pd.close()
         i0 = infos_d[-1]
-        fp64 = {"value": world * len(infos_d) / (ms_d * 1e-3), "unit": "solves/s",
+        fp64 = {"value": replica_throughput(len(infos_d), ms_d, world), "unit": "solves/s",
                 "ms_per_step": ms_d / len(infos_d), "iterations": i0.iterations,
                 "relres_true": i0.relres_true, "setup_s": setup_fp64_s,
                 "t_precond_ms": i0.t_precond_ms, "t_matvec_ms": i0.t_matvec_ms, "t_orth_ms": i0.t_orth_ms}
@@ -354,7 +460,7 @@ def gpu_arm(args, world, rank, local):
                             "unit": "TFLOP/s", "frac": flops64 / t64 / fp64_peak,
                             "peak_source": "FP64 pipe: 2 DFMA/clk/SM x 152 SMs x 2070 MHz"}
 
-    value = world * args.steps / (ms_tot * 1e-3)
+    value = replica_throughput(args.steps, ms_tot, world)
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_tot / args.steps, "higher_is_better": True,
@@ -369,7 +475,7 @@ def gpu_arm(args, world, rank, local):
         "phases_ms": {"precond": last.t_precond_ms, "matvec": last.t_matvec_ms, "orth": last.t_orth_ms,
                       "solve": last.t_solve_ms},
         "roofline": roofline,
-        "e2e": {"value": world * args.steps / (ms_e2e * 1e-3), "unit": "solves/s",
+        "e2e": {"value": replica_throughput(args.steps, ms_e2e, world), "unit": "solves/s",
                 "h2d_bytes_per_step": N * N * 16, "d2h_bytes_per_step": N * N * 16},
         "gpu_launches": int(sum(i.launches for i in infos)),
         "clocks": clocks,
@@ -395,6 +501,9 @@ def main():
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         reference_arm(args, world, rank)
+        return
+    if args.workload == "batched":
+        batched_arm(args, world, rank, local)
         return
     gpu_arm(args, world, rank, local)
 

@@ -106,3 +106,17 @@ def test_table_regime_k100_gpu(hzs, bc, prec):
     assert info[0].converged
     assert info[0].relres_true <= 1.01e-7
     assert info[0].iterations <= 30
+
+
+@pytest.mark.parametrize("ratio,k,n", [(4, 10, 33), (4, 20, 49), (4, 30, 65), (16, 5, 33), (16, 10, 49), (16, 15, 65)])
+def test_kn_sweep_vs_oracle(hzs, ratio, k, n):
+    # last two tables of Section 5: SHS2 / B_2, MP-1, H_sub = H = ratio h, overlap ratio/2, cap 50
+    from paper_2408_03571_gb300 import tables
+    res = tables.run_kn(ratio, [k], [n])
+    it, conv = res[(k, n)]
+    prob = Problem(n, DIRICHLET, float(k) ** 2)
+    A = prob.assemble_fast()
+    M = Schwarz(prob, A, (n - 1) // ratio, ratio // 2, SHS2, B2, ratio)
+    ref = gmres(lambda x: A @ x, M.apply, prob.grid_to_vec(point_source(n)), 1e-7, 50)
+    assert conv == ref.converged
+    assert abs(it - ref.iterations) <= 1, (it, ref.iterations)

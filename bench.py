@@ -435,15 +435,17 @@ def gpu_arm(args, world, rank, local):
                 "timing": "CUDA events around every launch of the kernel on the solve stream"}
     r_dot = pass_roofline("k_dcgs_dot (delayed CGS2 multi-dot, double-float basis)", dot_bytes, t_dot)
     r_upd = pass_roofline("k_dcgs_update (delayed CGS2 basis update, double-float)", upd_bytes, t_upd)
-    # DRAM traffic of the dot pass from one ncu capture (MP-1 k=100 n=513, the launch of
-    # step 200): read + write = 906.2 MB against 843.9 MB algorithmic, ratio 1.074; traffic
-    # grows with the units processed, so the average launch here is scaled by that ratio.
-    r_dot["launches"] = it + 1
-    r_dot["bytes_per_launch"] = dot_bytes / (it + 1)
-    r_dot["traffic"] = 1.074 * dot_bytes / (it + 1)
-    r_dot["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_dcgs_dot launch "
-                               "(n=513, step 200: 906.2 MB = 1.074 x algorithmic), scaled to this workload's "
-                               "average launch")
+    # DRAM traffic of the two passes from one ncu capture (MP-1 k=100 n=513, the launches
+    # of step 200): dot 906.8 MB against 843.9 MB algorithmic (ratio 1.075), update 897.5 MB
+    # against 852.3 MB (1.053); traffic grows with the units processed, so the average
+    # launch here is scaled by those ratios.
+    for r_, nbytes, nl, ratio, meas in ((r_dot, dot_bytes, it + 1, 1.075, "906.8 MB = 1.075"),
+                                        (r_upd, upd_bytes, it, 1.053, "897.5 MB = 1.053")):
+        r_["launches"] = nl
+        r_["bytes_per_launch"] = nbytes / nl
+        r_["traffic"] = ratio * nbytes / nl
+        r_["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch (n=513, "
+                                f"step 200: {meas} x algorithmic), scaled to this workload's average launch")
     roofline = dict(r_upd if t_upd >= t_dot else r_dot)
     roofline["other_pass"] = r_dot if t_upd >= t_dot else r_upd
     roofline["orth_group"] = {"time_per_solve_s": orth_s,

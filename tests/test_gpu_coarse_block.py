@@ -120,3 +120,18 @@ def test_kn_sweep_vs_oracle(hzs, ratio, k, n):
     ref = gmres(lambda x: A @ x, M.apply, prob.grid_to_vec(point_source(n)), 1e-7, 50)
     assert conv == ref.converged
     assert abs(it - ref.iterations) <= 1, (it, ref.iterations)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_block_coarse_batched_apply(hzs, prec):
+    # several right-hand sides in one apply: every batch entry through the block solve
+    n, nsub, ov, p, k = 65, 4, 2, 4, 12.0
+    prob = Problem(n, SOMMERFELD, k * k)
+    A = prob.assemble_fast()
+    M = Schwarz(prob, A, nsub, ov, SHS2, B2, p)
+    V = np.stack([random_complex_grid(n, seed=40 + r) for r in range(3)])
+    _, P = make(hzs, n, SOMMERFELD, k, nsub, ov, SHS2, B2, p, prec, BLOCK)
+    Z = P.apply(dev(V)).cpu().numpy()
+    for r in range(3):
+        ref = prob.vec_to_grid(M.apply(prob.grid_to_vec(V[r])))
+        assert rel(Z[r], ref) < (1e-9 if prec == 0 else 1e-4)

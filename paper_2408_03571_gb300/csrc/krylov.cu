@@ -22,7 +22,7 @@ namespace hzs {
 
 constexpr int kRedThreads = 256;
 constexpr int kDotGroup64 = 4;     // basis vectors per warp pass (FP64 multi-dot)
-constexpr int kDotGroupDC = 4;     // basis vectors per warp pass (delayed CGS2 multi-dot)
+constexpr int kDotGroupDC = 2;     // basis vectors per warp pass (delayed CGS2 multi-dot)
 constexpr int kUpdUnroll = 4;      // basis vectors per iteration of the delayed CGS2 update
 
 __device__ __forceinline__ void chunk_of(long long N, long long& e0, long long& e1) {
@@ -354,12 +354,15 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_dcgs_dot(int j, long long Np
         for (int t = 0; t < G; ++t) { rh[t] = rl[t] = ih[t] = il[t] = 0.f; bb[t] = make_float2(0.f, 0.f); }
         int cnt = 0;
         for (long long e = e0 + lane; e < e1; e += 32) {
-            const float4 xh = uh[e], xl = ul[e];
-            const float4 yh = has_w ? wh[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+            // u~ and w are re-read by every warp of the block: read-only cache path;
+            // the basis is read once: streaming (evict-first) loads
+            const float4 xh = __ldg(uh + e), xl = __ldg(ul + e);
+            const float4 yh = has_w ? __ldg(wh + e) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int t = 0; t < G; ++t) {
                 if (i0 + t >= j) continue;
-                const float4 vh = V32[(size_t)(i0 + t) * ldp + e], vl = V32lo[(size_t)(i0 + t) * ldp + e];
+                const float4 vh = __ldcs(V32 + (size_t)(i0 + t) * ldp + e);
+                const float4 vl = __ldcs(V32lo + (size_t)(i0 + t) * ldp + e);
                 // alpha: conj(v) u~, re = vr ur + vi ui, im = vr ui - vi ur (two entries)
                 df_fma(rh[t], rl[t], vh.x, vl.x, xh.x, xl.x);
                 df_fma(rh[t], rl[t], vh.y, vl.y, xh.y, xl.y);
@@ -373,7 +376,7 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_dcgs_dot(int j, long long Np
                 bb[t] = cfma_conj(lo2(vh), lo2(yh), bb[t]);
                 bb[t] = cfma_conj(hi2(vh), hi2(yh), bb[t]);
             }
-            if ((++cnt & 7) == 0) {
+            if ((++cnt & 15) == 0) {
 #pragma unroll
                 for (int t = 0; t < G; ++t) { df_norm(rh[t], rl[t]); df_norm(ih[t], il[t]); }
             }
@@ -545,31 +548,35 @@ __global__ void __launch_bounds__(kRedThreads, 3) k_dcgs_update(int j, long long
         float2 s0 = make_float2(0.f, 0.f), s1 = s0;
         const float4* ph = V32 + e;
         const float4* pl = V32lo + e;
+        // basis vectors in the order j-1 .. 0: the dot pass read 0 .. j-1, so the vectors
+        // still in L2 come first, and this pass leaves vectors 0, 1, .. in L2 for the next
+        // dot pass
+        auto vi = [&](int k) { return j - 1 - k; };
         int i = 0;
         for (; i + kUpdUnroll <= j; i += kUpdUnroll) {     // kUpdUnroll basis vectors: all loads first
             float4 vh[kUpdUnroll], vl[kUpdUnroll];
 #pragma unroll
             for (int t = 0; t < kUpdUnroll; ++t) {
-                vh[t] = __ldcs(ph + (size_t)(i + t) * ldp);
-                vl[t] = __ldcs(pl + (size_t)(i + t) * ldp);
+                vh[t] = ph[(size_t)vi(i + t) * ldp];
+                vl[t] = pl[(size_t)vi(i + t) * ldp];
             }
 #pragma unroll
             for (int t = 0; t < kUpdUnroll; ++t) {
-                const float4 q = cb[i + t];
+                const float4 q = cb[vi(i + t)];
                 df_cmac(a0h, a0l, b0h, b0l, q, vh[t].x, vl[t].x, vh[t].y, vl[t].y);
                 df_cmac(a1h, a1l, b1h, b1l, q, vh[t].z, vl[t].z, vh[t].w, vl[t].w);
-                s0 = cfma(ca[i + t], lo2(vh[t]), s0);
-                s1 = cfma(ca[i + t], hi2(vh[t]), s1);
+                s0 = cfma(ca[vi(i + t)], lo2(vh[t]), s0);
+                s1 = cfma(ca[vi(i + t)], hi2(vh[t]), s1);
             }
             df_norm(a0h, a0l); df_norm(b0h, b0l); df_norm(a1h, a1l); df_norm(b1h, b1l);
         }
         for (; i < j; ++i) {
-            const float4 vh = __ldcs(ph + (size_t)i * ldp), vl = __ldcs(pl + (size_t)i * ldp);
-            const float4 q = cb[i];
+            const float4 vh = ph[(size_t)vi(i) * ldp], vl = pl[(size_t)vi(i) * ldp];
+            const float4 q = cb[vi(i)];
             df_cmac(a0h, a0l, b0h, b0l, q, vh.x, vl.x, vh.y, vl.y);
             df_cmac(a1h, a1l, b1h, b1l, q, vh.z, vl.z, vh.w, vl.w);
-            s0 = cfma(ca[i], lo2(vh), s0);
-            s1 = cfma(ca[i], hi2(vh), s1);
+            s0 = cfma(ca[vi(i)], lo2(vh), s0);
+            s1 = cfma(ca[vi(i)], hi2(vh), s1);
         }
         // V_j = u~ - s
         float4 xh = uh[e], xl = ul[e];
@@ -855,8 +862,8 @@ void launch_dcgs2_step(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int l
     float4* V32lo = reinterpret_cast<float4*>(kb.V32lo);
     const dim3 gr(kb.nblk, nb);
     if (ev) cudaEventRecord(ev[0], cx.stream);
-    k_dcgs_dot<kDotGroupDC><<<dim3(kb.nblk_dot, nb), kRedThreads, 0, cx.stream>>>(j, Np, ldp, ps, S, V32, V32lo, sVp,
-                                                                                 !last_only, kb.part, kb.sP(), kb.st);
+    k_dcgs_dot<kDotGroupDC><<<dim3(kb.nblk_dot, nb), kRedThreads, 0, cx.stream>>>(
+        j, Np, ldp, ps, S, V32, V32lo, sVp, !last_only, kb.part, kb.sP(), kb.st);
     if (ev) cudaEventRecord(ev[1], cx.stream);
     const dim3 rg(((2 * j + 2) * 32 + 255) / 256, nb);
     k_dcgs_reduce<<<rg, 256, 0, cx.stream>>>(j, kb.nblk_dot, ps, S, kb.part, kb.sP(), kb.sigma, kb.h2, kb.hn,

@@ -436,11 +436,11 @@ def gpu_arm(args, world, rank, local):
     r_dot = pass_roofline("k_dcgs_dot (delayed CGS2 multi-dot, double-float basis)", dot_bytes, t_dot)
     r_upd = pass_roofline("k_dcgs_update (delayed CGS2 basis update, double-float)", upd_bytes, t_upd)
     # DRAM traffic of the two passes from one ncu capture (MP-1 k=100 n=513, the launches
-    # of step 200): dot 906.8 MB against 843.9 MB algorithmic (ratio 1.075), update 897.5 MB
-    # against 852.3 MB (1.053); traffic grows with the units processed, so the average
+    # of step 200): dot 859.2 MB against 843.9 MB algorithmic (ratio 1.018), update 902.2 MB
+    # against 852.3 MB (1.059); traffic grows with the units processed, so the average
     # launch here is scaled by those ratios.
-    for r_, nbytes, nl, ratio, meas in ((r_dot, dot_bytes, it + 1, 1.075, "906.8 MB = 1.075"),
-                                        (r_upd, upd_bytes, it, 1.053, "897.5 MB = 1.053")):
+    for r_, nbytes, nl, ratio, meas in ((r_dot, dot_bytes, it + 1, 1.018, "859.2 MB = 1.018"),
+                                        (r_upd, upd_bytes, it, 1.059, "902.2 MB = 1.059")):
         r_["launches"] = nl
         r_["bytes_per_launch"] = nbytes / nl
         r_["traffic"] = ratio * nbytes / nl

@@ -218,10 +218,12 @@ template <> struct CoarseW<float> {
 };
 
 // ---------------------------------------------------------------- subdomain tiles
-// Elements between consecutive dense blocks W_j of a factor: mx*mx rounded up to
-// an even count, so that every block starts on a 16-byte boundary in complex64
-// as well as complex128 (a requirement of the bulk copies that stage them).
-__host__ __device__ __forceinline__ long long block_stride(int mx) { return ((long long)mx * mx + 1) & ~1LL; }
+// A dense block W_j of a factor is stored row by row with the row length padded to
+// an even count (the pad column holds zeros): every row, and every block, then
+// starts on a 16-byte boundary in complex64 as well as complex128, as the bulk
+// copies that stage the blocks and the paired 16-byte loads of the solve require.
+__host__ __device__ __forceinline__ int block_ld(int mx) { return mx + (mx & 1); }
+__host__ __device__ __forceinline__ long long block_stride(int mx) { return (long long)mx * block_ld(mx); }
 
 struct Tile {
     int x0, y0;          // first grid node of the extended tile

@@ -115,8 +115,10 @@ __global__ void __launch_bounds__(512) k_tile_factor(OpDesc op, const FactorDesc
         double mx_abs = 0.0;
         double2* dst64 = W64 + fd.woff + (long long)j * block_stride(m);
         float2* dst32 = W32 ? W32 + fd.woff + (long long)j * block_stride(m) : nullptr;
-        for (int t = tid; t < m * m; t += nt) {
-            const double2 v = S[t];
+        const int ms = block_ld(m);
+        for (int t = tid; t < m * ms; t += nt) {
+            const int a = t / ms, b = t % ms;
+            const double2 v = b < m ? S[a * m + b] : make_double2(0.0, 0.0);   // pad column: zero
             dst64[t] = v;
             if (dst32) dst32[t] = to_f(v);
             mx_abs = fmax(mx_abs, hypot(v.x, v.y));
@@ -199,17 +201,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 
 template <typename R, int T, int NST>
 __host__ __device__ constexpr size_t tile_smem_bytes(int mx, int my) {
-    // W stages | g (T tiles) | r (2 x T x mx) | cy (mx) | mbarriers
+    // W stages | g (T tiles) | r (2 x T x block_ld(mx), 16-byte aligned) | cy (mx) | mbarriers
     return ((size_t)NST * block_stride(mx) * sizeof(cplx_t<R>) + 127) / 128 * 128 +
-           (size_t)T * mx * my * sizeof(cplx_t<R>) + (size_t)2 * T * mx * sizeof(cplx_t<R>) +
-           (size_t)mx * sizeof(R) + 16 + (size_t)NST * 8 + 16;
+           ((size_t)T * mx * my * sizeof(cplx_t<R>) + 15) / 16 * 16 +
+           (size_t)2 * T * block_ld(mx) * sizeof(cplx_t<R>) + (size_t)mx * sizeof(R) + 16 + (size_t)NST * 8 + 16;
 }
 
 // ---- stages of the tile solve
 
 // Gathers b = R_i (s w) for the group's T tiles into g (T x mx*my), the row
-// couplings cy (mx) and the first right-hand side r = b_0 (T x mx); ends with a
-// block barrier.
+// couplings cy (mx) and the first right-hand side r = b_0 (T x block_ld(mx), the
+// second buffer zeroed); ends with a block barrier.
 template <typename Cw, typename R, int T>
 __device__ __forceinline__ void tile_gather(const OpDesc& op, const Tile* __restrict__ tiles, const int* tix,
                                             const Tile& T0, const Cw* __restrict__ w, R sc, cplx_t<R>* g,
@@ -233,9 +235,11 @@ __device__ __forceinline__ void tile_gather(const OpDesc& op, const Tile* __rest
     }
     for (int a = tid; a < mx; a += nt) cy[a] = (R)op_cy(op, T0.x0 + a);
     __syncthreads();
-    for (int e = tid; e < T * mx; e += nt) {
-        const int t = e / mx, a = e % mx;
-        r[e] = g[(size_t)t * mx * my + a];
+    // both right-hand-side buffers (2 x T x block_ld(mx)); the pad entries stay zero
+    const int ms = block_ld(mx);
+    for (int e = tid; e < 2 * T * ms; e += nt) {
+        const int t = (e / ms) % T, a = e % ms;
+        r[e] = (e < T * ms && a < mx) ? g[(size_t)t * mx * my + a] : mk<C>(0.0, 0.0);
     }
     __syncthreads();
 }
@@ -320,8 +324,8 @@ __device__ __forceinline__ void tile_output(const OpDesc& op, const CoarseTab& c
     }
 }
 
-template <typename Cw, typename Cz, typename R, int T, int NST, int TPR>
-__global__ void __launch_bounds__(1024) k_tile_solve(OpDesc op, CoarseTab ct, const Tile* __restrict__ tiles,
+template <typename Cw, typename Cz, typename R, int T, int NST, int TPR, int MAXT>
+__global__ void __launch_bounds__(MAXT) k_tile_solve(OpDesc op, CoarseTab ct, const Tile* __restrict__ tiles,
                                                     const int* __restrict__ groups, const cplx_t<R>* __restrict__ W,
                                                     const Cw* __restrict__ w, long long ws,
                                                     const double* __restrict__ vscale, long long vss, int mode,
@@ -344,9 +348,10 @@ __global__ void __launch_bounds__(1024) k_tile_solve(OpDesc op, CoarseTab ct, co
     const long long bs = block_stride(mx);
     const uint32_t bbytes = (uint32_t)(bs * sizeof(C));
     C* wst = reinterpret_cast<C*>(smem_raw);                                        // NST stages
+    const int ms = block_ld(mx);                                                    // padded row length
     C* g = reinterpret_cast<C*>(smem_raw + ((size_t)NST * bs * sizeof(C) + 127) / 128 * 128);   // T x mx*my
-    C* r = g + (size_t)T * mx * my;                                                 // 2 x T x mx
-    R* cy = reinterpret_cast<R*>(r + 2 * T * mx);                                   // mx
+    C* r = reinterpret_cast<C*>((reinterpret_cast<uintptr_t>(g + (size_t)T * mx * my) + 15) & ~uintptr_t(15));
+    R* cy = reinterpret_cast<R*>(r + 2 * T * ms);                                   // mx
     uint64_t* bar = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(cy + mx) + 15) & ~uintptr_t(15));
     const int tid = threadIdx.x;
     const C* Wt = W + T0.woff;
@@ -379,18 +384,33 @@ __global__ void __launch_bounds__(1024) k_tile_solve(OpDesc op, CoarseTab ct, co
         // stage holds; the step's closing barrier then ends the sweep for every thread
         if (!mbar_wait_bounded(&bar[st], parity)) s_fail = 1;
         const C* Wq = wst + (size_t)st * bs;
-        const C* rc = r + (size_t)(q & 1) * T * mx;
-        C* rn = r + (size_t)((q + 1) & 1) * T * mx;
+        const C* rc = r + (size_t)(q & 1) * T * ms;
+        C* rn = r + (size_t)((q + 1) & 1) * T * ms;
         // every thread of the block runs the shuffles below (inactive rows add zeros)
         C acc[T];
 #pragma unroll
         for (int t = 0; t < T; ++t) { acc[t].x = 0; acc[t].y = 0; }
         if (active) {
-            const C* wr = Wq + (size_t)row * mx;
-            for (int k = sub; k < mx; k += TPR) {
-                const C wv = wr[k];
+            const C* wr = Wq + (size_t)row * ms;
+            if constexpr (sizeof(R) == sizeof(float)) {
+                // complex64: two entries per 16-byte load (rows and buffers are 16-byte
+                // aligned; the zero pad column makes ms/2 pairs exact)
+                const float4* w4 = reinterpret_cast<const float4*>(wr);
+                for (int k2 = sub; k2 < ms / 2; k2 += TPR) {
+                    const float4 wv = w4[k2];
 #pragma unroll
-                for (int t = 0; t < T; ++t) acc[t] = cfma(wv, rc[t * mx + k], acc[t]);
+                    for (int t = 0; t < T; ++t) {
+                        const float4 rv = reinterpret_cast<const float4*>(rc + t * ms)[k2];
+                        acc[t] = cfma(make_float2(wv.x, wv.y), make_float2(rv.x, rv.y), acc[t]);
+                        acc[t] = cfma(make_float2(wv.z, wv.w), make_float2(rv.z, rv.w), acc[t]);
+                    }
+                }
+            } else {
+                for (int k = sub; k < mx; k += TPR) {
+                    const C wv = wr[k];
+#pragma unroll
+                    for (int t = 0; t < T; ++t) acc[t] = cfma(wv, rc[t * ms + k], acc[t]);
+                }
             }
         }
 #pragma unroll
@@ -402,12 +422,13 @@ __global__ void __launch_bounds__(1024) k_tile_solve(OpDesc op, CoarseTab ct, co
             }
         }
         // lane sub == t of the row completes tile t (all lanes hold the row sums)
-        if (active) {
+        if (active && sub < T) {
+            C a = acc[0];
 #pragma unroll
-            for (int t = 0; t < T; ++t)
-                if (sub == t)
-                    tile_step_finish<R, 1>(q < my, blk(q), my, mx, row, &acc[t], g + (size_t)t * mx * my,
-                                           rn + (size_t)t * mx, cy);
+            for (int t = 1; t < T; ++t)
+                if (sub == t) a = acc[t];
+            tile_step_finish<R, 1>(q < my, blk(q), my, mx, row, &a, g + (size_t)sub * mx * my, rn + (size_t)sub * ms,
+                                   cy);
         }
         __syncthreads();   // stage st fully read; next r complete
         if (s_fail) { q_fail = q; break; }
@@ -448,8 +469,8 @@ static int launch_tile_solve_t(const Ctx& cx, int nb, const Tile* tiles, TileGro
     const size_t smem = tile_smem_bytes<R, T, NST>(max_mx, max_my);
     // eight threads per block row while the block stays within 1024 threads: more warps
     // to hide the per-step latency and half the dependent multiply-adds per thread
-    if (max_mx * 8 <= 1024) {
-        auto kern = k_tile_solve<Cw, Cz, R, T, NST, 8>;
+    if (max_mx <= 72) {        // the common tile sizes: a tighter launch bound leaves more registers
+        auto kern = k_tile_solve<Cw, Cz, R, T, NST, 8, 576>;
         if (allow_dynamic_smem((const void*)kern, smem) != cudaSuccess) return -1;
         const int threads = (max_mx * 8 + 31) / 32 * 32;
         kern<<<dim3(grp.count, nb), threads, smem, cx.stream>>>(cx.op, cx.ct, tiles, grp.idx, W, w, ws, vscale, vss,
@@ -457,7 +478,16 @@ static int launch_tile_solve_t(const Ctx& cx, int nb, const Tile* tiles, TileGro
                                                                 cx.err);
         return 0;
     }
-    auto kern = k_tile_solve<Cw, Cz, R, T, NST, 4>;
+    if (max_mx * 8 <= 1024) {
+        auto kern = k_tile_solve<Cw, Cz, R, T, NST, 8, 1024>;
+        if (allow_dynamic_smem((const void*)kern, smem) != cudaSuccess) return -1;
+        const int threads = (max_mx * 8 + 31) / 32 * 32;
+        kern<<<dim3(grp.count, nb), threads, smem, cx.stream>>>(cx.op, cx.ct, tiles, grp.idx, W, w, ws, vscale, vss,
+                                                                mode, c, cs, use_coarse, z, zs, ytiles, yts, sk,
+                                                                cx.err);
+        return 0;
+    }
+    auto kern = k_tile_solve<Cw, Cz, R, T, NST, 4, 1024>;
     if (allow_dynamic_smem((const void*)kern, smem) != cudaSuccess) return -1;
     const int threads = (max_mx * 4 + 31) / 32 * 32;
     kern<<<dim3(grp.count, nb), threads, smem, cx.stream>>>(cx.op, cx.ct, tiles, grp.idx, W, w, ws, vscale, vss, mode,

@@ -396,7 +396,13 @@ __global__ void __launch_bounds__(MAXT) k_tile_solve(OpDesc op, CoarseTab ct, co
                 // complex64: two entries per 16-byte load (rows and buffers are 16-byte
                 // aligned; the zero pad column makes ms/2 pairs exact)
                 const float4* w4 = reinterpret_cast<const float4*>(wr);
-                for (int k2 = sub; k2 < ms / 2; k2 += TPR) {
+                // tiles of at most 72 (launch bound 576): at most KP pairs per thread, and
+                // the loop below is fully unrolled
+                constexpr int KP = MAXT <= 576 ? (36 + TPR - 1) / TPR : 1024;
+#pragma unroll 8
+                for (int m = 0; m < KP; ++m) {
+                    const int k2 = sub + TPR * m;
+                    if (k2 >= ms / 2) break;
                     const float4 wv = w4[k2];
 #pragma unroll
                     for (int t = 0; t < T; ++t) {

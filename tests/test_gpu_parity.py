@@ -251,3 +251,45 @@ def test_mixed_orthogonalisation_matches_fp64_cgs2(hzs, case):
     assert i1[0].relres_true <= c["tol"] * 1.01
     a = prob.grid_to_vec(u1.cpu().numpy()); b = prob.grid_to_vec(u2.cpu().numpy())
     assert rel(a, b) < 1e-5
+
+
+@pytest.mark.parametrize("maxit", [1, 2, 7])
+def test_mixed_iteration_cap_matches_oracle(hzs, maxit):
+    # the delayed CGS2 of the mixed path completes its last Hessenberg column in an
+    # extra dot pass when the cap is reached: the iterate after maxit steps must be the
+    # FGMRES iterate of maxit steps (oracle with the same complex64-rounded preconditioner
+    # is not available, so compare residual histories loosely and the iterate's residual)
+    n, nsub, ov, p = 65, 4, 2, 8
+    k = 20.0
+    prob = Problem(n, SOMMERFELD, k * k)
+    A = prob.assemble_fast()
+    M = Schwarz(prob, A, nsub, ov, SHS2, B2, p)
+    f = point_source(n)
+    ref = _oracle_solve(prob, A, M, f, 1e-14, maxit, flexible=True)
+    g, P = make(hzs, n, SOMMERFELD, k=k, nsub=nsub, ov=ov, kind=SHS2, coarse=B2, p=p, prec=1)
+    u, info = P.solve(dev(f), tol=1e-14, maxit=maxit)
+    assert info[0].iterations == maxit and not info[0].converged
+    uv = prob.grid_to_vec(u.cpu().numpy())
+    fv = prob.grid_to_vec(f)
+    res = np.linalg.norm(fv - A @ uv) / np.linalg.norm(fv)
+    # same Krylov space up to the complex64 preconditioner: residual within 1e-3 relative
+    ref_res = np.linalg.norm(fv - A @ ref.x) / np.linalg.norm(fv)
+    assert abs(res - ref_res) <= 1e-3 * ref_res + 1e-12
+    assert abs(info[0].relres_est - res) <= 1e-6 * max(res, 1e-12) + 1e-12
+
+
+def test_mixed_edge_cases(hzs):
+    n = 33
+    g, P = make(hzs, n, SOMMERFELD, k=10.0, nsub=2, ov=1, kind=SHS2, coarse=B2, p=4, prec=1)
+    u, info = P.solve(torch.zeros((n, n), dtype=torch.complex128, device="cuda"), tol=1e-8, maxit=20)
+    assert info[0].iterations == 0 and info[0].converged and torch.all(u == 0)
+    f = point_source(n)
+    f[3, 3] = np.nan
+    with pytest.raises(hzs.HzsError) as e:
+        P.solve(dev(f), tol=1e-8, maxit=20)
+    assert e.value.status == hzs.ERR_NONFINITE
+    # an exact preconditioner (one subdomain) in complex64: the first column is a near
+    # breakdown of the Krylov space; the solve still reaches the tolerance
+    g1, P1 = make(hzs, n, DIRICHLET, k=10.0, nsub=1, ov=0, kind=AS1, prec=1)
+    u, info = P1.solve(dev(point_source(n)), tol=1e-10, maxit=10)
+    assert info[0].converged and info[0].relres_true < 1.01e-10 and info[0].iterations <= 4

@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-wide-arm", action="store_true",
+                    help="skip the arm whose Krylov basis keeps complex64 remainders (about 48 bits)")
     ap.add_argument("--no-dedup-arm", action="store_true",
                     help="skip the MIXED arm with every subdomain factored separately")
     ap.add_argument("--workload", choices=["headline", "batched"], default="headline",
@@ -186,6 +188,11 @@ def oracle_sample(steps: int, iterations: int):
     }
 
 
+def basis_dtype(bits: int) -> str:
+    return {32: "f32 + bf16 remainder pairs (~32 bits)", 48: "double-float (2 x f32) pairs (~48 bits)",
+            53: "c128"}.get(bits, f"{bits}-bit")
+
+
 def cpu_cores_used():
     # numpy's vector ops used here are single-threaded; SuperLU is single-threaded
     return 1
@@ -299,7 +306,8 @@ def batched_arm(args, world, rank, local):
         "value": replica_throughput(nsol, ms / args.steps, world), "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "c64 preconditioner; Arnoldi basis as double-float (2 x f32) pairs; f64 Hessenberg",
+        "dtype": "c64 preconditioner; Arnoldi basis as " + basis_dtype(min(r.basis_bits for res in infos for r in res))
+                 + "; f64 Hessenberg",
         "data": "synthetic",
         "config": {"workload": "MP-2 batch: (k, n) = (25, 257), (50, 257), (100, 513), 64-node subdomains, "
                                "overlap 2, SHS2 with B2 H=32h, point sources at seeded nodes, all problems "
@@ -339,12 +347,12 @@ def gpu_arm(args, world, rank, local):
             torch.distributed.barrier()
             torch.cuda.synchronize()
 
-    def timed_solves(P, steps, warmup, e2e=False, profile=True):
+    def timed_solves(P, steps, warmup, e2e=False, profile=True, wide=False):
         u = torch.empty_like(f)
         u_host = torch.empty_like(f_host).pin_memory()
         infos = []
         for _ in range(warmup):
-            P.solve(f, TOL, MAXIT, out=u)
+            P.solve(f, TOL, MAXIT, out=u, wide_basis=wide)
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -352,10 +360,10 @@ def gpu_arm(args, world, rank, local):
         for _ in range(steps):
             if e2e:
                 fd = f_host.to(dev, non_blocking=True)
-                _, inf = P.solve(fd, TOL, MAXIT, out=u, profile=profile)
+                _, inf = P.solve(fd, TOL, MAXIT, out=u, profile=profile, wide_basis=wide)
                 u_host.copy_(u, non_blocking=True)
             else:
-                _, inf = P.solve(f, TOL, MAXIT, out=u, profile=profile)
+                _, inf = P.solve(f, TOL, MAXIT, out=u, profile=profile, wide_basis=wide)
             infos.append(inf[0])
         e1.record(stream)
         barrier()
@@ -373,6 +381,17 @@ def gpu_arm(args, world, rank, local):
     ms_tot, infos, u = timed_solves(Pm, args.steps, args.warmup)
     clocks = clk.stop()
     ms_e2e, infos_e2e, _ = timed_solves(Pm, args.steps, 0, e2e=True, profile=False)
+    # ---- the same solve with the basis remainders kept as complex64 (about 48 bits)
+    wide = None
+    if not args.no_wide_arm:
+        ms_w, infos_w, _ = timed_solves(Pm, max(1, args.steps // 2), 1, wide=True)
+        i0 = infos_w[-1]
+        wide = {"value": replica_throughput(len(infos_w), ms_w, world), "unit": "solves/s",
+                "ms_per_step": ms_w / len(infos_w), "iterations": i0.iterations,
+                "relres_est": i0.relres_est, "relres_true": i0.relres_true, "basis_bits": i0.basis_bits,
+                "t_orth_ms": i0.t_orth_ms,
+                "note": "Krylov basis as complex64 + complex64 remainder (16 B an entry; the default "
+                        "for tol < 1e-7)"}
     Pm.close()
     # ---- MIXED with one factor per subdomain (no sharing of identical factors): the
     # subdomain solves then stream 256 distinct factor sets per apply, as for a kappa field
@@ -404,16 +423,18 @@ def gpu_arm(args, world, rank, local):
     grid.close()
 
     # ---- roofline of the dominant kernels: the two passes of the delayed CGS2 over
-    # the double-float basis (complex64 rounding + remainder: 16 B per basis entry).
+    # the double-float basis, complex64 leading words + remainders: eb = 12 B per basis
+    # entry with bf16 remainders (tol >= 1e-7), 16 B with complex64 remainders.
     # Algorithmic HBM bytes at step j (Nu unknowns):
-    #   dot pass    k_dcgs_dot:    basis vectors 0..j-1 (16 j Nu), u~_j and w (16 + 16 Nu)
-    #   update pass k_dcgs_update: basis vectors 0..j-1 (16 j Nu), u~_j and w read and written (64 Nu)
+    #   dot pass    k_dcgs_dot:    leading words of basis vectors 0..j-1, u~_j and w (8 (j + 2) Nu)
+    #   update pass k_dcgs_update: basis vectors 0..j-1 (eb j Nu), u~_j and w read and written (4 eb Nu)
     # Step j = it completes the last column (dot pass only); its update returns at once.
     last = infos[-1]
     it = last.iterations
     Nu = (N - 2) ** 2
-    dot_bytes = sum(16 * (j + 2) * Nu for j in range(it + 1))
-    upd_bytes = sum(16 * (j + 4) * Nu for j in range(it))
+    eb = 12 if last.basis_bits == 32 else 16
+    dot_bytes = sum(8 * (j + 2) * Nu for j in range(it + 1))
+    upd_bytes = sum(eb * (j + 4) * Nu for j in range(it))
     t_dot = statistics.mean(i.t_orth_dot_ms for i in infos) * 1e-3
     t_upd = statistics.mean(i.t_orth_update_ms for i in infos) * 1e-3
     orth_s = statistics.mean(i.t_orth_ms for i in infos) * 1e-3
@@ -433,19 +454,25 @@ def gpu_arm(args, world, rank, local):
                 "frac": a / hbm_peak, "traffic": None, "peak_source": peak_src,
                 "bytes_per_solve": nbytes, "time_per_solve_s": t,
                 "timing": "CUDA events around every launch of the kernel on the solve stream"}
-    r_dot = pass_roofline("k_dcgs_dot (delayed CGS2 multi-dot, double-float basis)", dot_bytes, t_dot)
+    r_dot = pass_roofline("k_dcgs_dot (delayed CGS2 multi-dot on the leading words of the basis)", dot_bytes,
+                          t_dot)
     r_upd = pass_roofline("k_dcgs_update (delayed CGS2 basis update, double-float)", upd_bytes, t_upd)
-    # DRAM traffic of the two passes from one ncu capture (MP-1 k=100 n=513, the launches
-    # of step 200): dot 859.2 MB against 843.9 MB algorithmic (ratio 1.018), update 902.2 MB
-    # against 852.3 MB (1.059); traffic grows with the units processed, so the average
-    # launch here is scaled by those ratios.
-    for r_, nbytes, nl, ratio, meas in ((r_dot, dot_bytes, it + 1, 1.018, "859.2 MB = 1.018"),
-                                        (r_upd, upd_bytes, it, 1.059, "902.2 MB = 1.059")):
+    # DRAM traffic of the two passes from one ncu capture per basis width (MP-1 k=100
+    # n=513, the launches of step 200), as a ratio to the algorithmic bytes of that
+    # launch; traffic grows with the units processed, so the average launch here is
+    # scaled by those ratios.  None: no capture of the current kernel.
+    traffic_ratio = {16: {"dot": None, "upd": (1.059, "902.2 MB against 852.3 MB")},
+                     12: {"dot": None, "upd": None}}[eb]
+    for r_, nbytes, nl, key in ((r_dot, dot_bytes, it + 1, "dot"), (r_upd, upd_bytes, it, "upd")):
         r_["launches"] = nl
         r_["bytes_per_launch"] = nbytes / nl
-        r_["traffic"] = ratio * nbytes / nl
-        r_["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch (n=513, "
-                                f"step 200: {meas} x algorithmic), scaled to this workload's average launch")
+        r_["basis_bytes_per_entry"] = 8 if key == "dot" else eb
+        tr = traffic_ratio[key]
+        r_["traffic"] = None if tr is None else tr[0] * nbytes / nl
+        r_["traffic_source"] = (
+            "no ncu capture of this kernel version" if tr is None else
+            "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch (n=513, step 200: "
+            f"{tr[1]} algorithmic = {tr[0]}), scaled to this workload's average launch")
     roofline = dict(r_upd if t_upd >= t_dot else r_dot)
     roofline["other_pass"] = r_dot if t_upd >= t_dot else r_upd
     roofline["orth_group"] = {"time_per_solve_s": orth_s,
@@ -466,14 +493,15 @@ def gpu_arm(args, world, rank, local):
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_tot / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "c64 preconditioner; Arnoldi basis as double-float (2 x f32) pairs; f64 Hessenberg, "
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64 preconditioner; Arnoldi basis as " + basis_dtype(last.basis_bits) + "; f64 Hessenberg, "
                  "coarse solve, outer operator and solution",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": "mixed", "n": N, "k": K_WAVE, "nsub": NSUB,
-                   "overlap": OVERLAP, "coarse_ratio": P_COARSE, "tol": TOL,
+                   "overlap": OVERLAP, "coarse_ratio": P_COARSE, "tol": TOL, "basis_bits": last.basis_bits,
                    "l2": "working set larger than L2 (Krylov basis ~6 GB); no flush needed",
                    "parallelism": f"replicas x{world}"},
-        "iterations": it, "relres_true": last.relres_true, "setup_s": setup_mixed_s,
+        "iterations": it, "relres_est": last.relres_est, "relres_true": last.relres_true,
+        "setup_s": setup_mixed_s,
         "phases_ms": {"precond": last.t_precond_ms, "matvec": last.t_matvec_ms, "orth": last.t_orth_ms,
                       "solve": last.t_solve_ms},
         "roofline": roofline,
@@ -482,6 +510,7 @@ def gpu_arm(args, world, rank, local):
         "gpu_launches": int(sum(i.launches for i in infos)),
         "clocks": clocks,
         "fp64": fp64,
+        "wide_basis": wide,
         "dedup_off": dedup_off,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -129,10 +129,15 @@ typedef struct {
 /* With HZS_MIXED: orthogonalise with the all-FP64 CGS2 on a complex128 basis
  * instead of the default, the delayed CGS2 (reorthogonalisation of vector j
  * fused with the projection of step j+1: two passes over the basis per step)
- * on a double-float basis (complex64 rounding + remainder, about 48
- * significant bits) with double-float updates and dot products.  No effect
- * with HZS_FP64. */
+ * on a double-float basis (complex64 rounding + remainder) with double-float
+ * updates and dot products.  No effect with HZS_FP64. */
 #define HZS_SOLVE_ORTH_FP64 2
+/* The delayed-CGS2 basis stores its remainders as complex64 (about 48
+ * significant bits, 16 bytes an entry in all) when tol < 1e-7, else as bf16
+ * pairs (about 32 significant bits, 12 bytes an entry: a quarter less basis
+ * traffic).  This flag keeps the complex64 remainders at any tol.  No effect
+ * without the delayed-CGS2 path. */
+#define HZS_SOLVE_BASIS_WIDE 4
 
 /* Per right-hand side results. */
 typedef struct {
@@ -147,6 +152,7 @@ typedef struct {
     double t_orth_dot_ms;  /* with HZS_SOLVE_PROFILE on the delayed-CGS2 path: device time of the */
     double t_orth_update_ms; /*   basis dot pass and of the basis update pass (parts of t_orth_ms); else 0 */
     long long launches;    /* kernel launches this solve issued */
+    int basis_bits;        /* significant bits of the Krylov basis: 53 (complex128), 48 or 32 */
     hzs_status status;
 } hzs_solve_info;
 

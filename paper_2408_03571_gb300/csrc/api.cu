@@ -82,6 +82,7 @@ struct hzs_precond {
     // solve work space
     KrylovBufs kb{};
     int kb_maxit = 0;
+    int lo_pad = -1;                  // remainder width (kb.lo16) whose padding is zero; -1: none yet
     float2* Z = nullptr;              // nb x maxit x ld (mixed)
     double2* ztmp = nullptr;          // nb x ld (FP64 z / x)
     double2* rtmp = nullptr;          // nb x ld
@@ -122,6 +123,10 @@ static hzs_status ensure_work(hzs_precond* p, int nb);
 
 // largest coarse space solved through an explicit inverse when the solver is AUTO
 constexpr int kDenseCoarseMax = 4096;
+// Smallest tolerance at which the delayed-CGS2 basis keeps bf16 remainders: the
+// 32-bit basis lets the true residual drift from the GMRES estimate by a few
+// times 1e-10 relative (at most about 1e-9 on the test problems), well below tol.
+constexpr double kNarrowBasisTol = 1e-7;
 
 // ------------------------------------------------------------------ grid
 extern "C" hzs_status hzs_grid_create(const hzs_grid_desc* d, void* cuda_stream, hzs_grid** out) {
@@ -597,22 +602,39 @@ static hzs_status ensure_krylov(hzs_precond* p, int maxit, int nb, bool full_v) 
     HZS_CUDA(g, dalloc(&kb.active, 1));
     if (p->desc.precision == HZS_MIXED) {
         HZS_CUDA(g, dalloc(&kb.V32, (size_t)nb * kb.sV()));
-        HZS_CUDA(g, dalloc(&kb.V32lo, (size_t)nb * kb.sV()));
+        float2* lo = nullptr;
+        HZS_CUDA(g, dalloc(&lo, (size_t)nb * kb.sV()));
+        kb.V32lo = lo;
+        kb.lo16 = 0;
+        p->lo_pad = -1;
         // the vectorised basis kernels read entries N .. ld-1 of each basis vector
         // (pairs of entries); they must hold zero and nothing else writes them
-        if (ld > N) {
-            const size_t rows = (size_t)nb * (maxit + 1);
-            HZS_CUDA(g, cudaMemset2DAsync(kb.V32 + N, ld * sizeof(float2), 0, (ld - N) * sizeof(float2), rows,
-                                          g->stream));
-            HZS_CUDA(g, cudaMemset2DAsync(kb.V32lo + N, ld * sizeof(float2), 0, (ld - N) * sizeof(float2), rows,
-                                          g->stream));
-        }
+        // (the remainders' padding depends on their width: see set_basis_width)
+        if (ld > N)
+            HZS_CUDA(g, cudaMemset2DAsync(kb.V32 + N, ld * sizeof(float2), 0, (ld - N) * sizeof(float2),
+                                          (size_t)nb * (maxit + 1), g->stream));
         HZS_CUDA(g, dalloc(&p->Z, (size_t)nb * maxit * ld));
     }
     HZS_CUDA(g, dalloc(&p->ztmp, (size_t)nb * ld));
     HZS_CUDA(g, dalloc(&p->rtmp, (size_t)nb * ld));
     HZS_CUDA(g, dalloc(&p->dres, (size_t)nb));
     return ensure_work(p, nb);
+}
+
+// Selects the remainder width of the double-float basis for a solve and zeroes
+// the padding entries N .. ld-1 of every basis slot in that layout (the wide and
+// narrow layouts put the padding at different bytes of the buffer).
+static hzs_status set_basis_width(hzs_precond* p, int lo16) {
+    KrylovBufs& kb = p->kb;
+    kb.lo16 = lo16;
+    if (p->lo_pad != lo16 && kb.ld > kb.N) {
+        const size_t es = lo16 ? sizeof(__nv_bfloat162) : sizeof(float2);
+        char* base = static_cast<char*>(kb.V32lo) + kb.N * es;
+        HZS_CUDA(p->g, cudaMemset2DAsync(base, kb.ld * es, 0, (kb.ld - kb.N) * es, (size_t)kb.nb * (kb.maxit + 1),
+                                         p->cx.stream));
+    }
+    p->lo_pad = lo16;
+    return HZS_OK;
 }
 
 // Kernel launches of one preconditioner apply.
@@ -650,6 +672,8 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
     const bool prof = (sd->flags & HZS_SOLVE_PROFILE) != 0;
     // mixed-precision CGS2 (complex64 first projection) unless all-FP64 orthogonalisation is asked for
     const bool orth32 = mixed && !(sd->flags & HZS_SOLVE_ORTH_FP64);
+    // bf16 remainders (a basis of about 32 significant bits) for loose tolerances
+    const bool lo16 = orth32 && !(sd->flags & HZS_SOLVE_BASIS_WIDE) && sd->tol >= kNarrowBasisTol;
     const BatchSkip sk = kb.skip();
     const int pl = precond_launches(p);
     long long launches = 0;
@@ -657,10 +681,14 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
         hzs_status st = ensure_prof_events(p, sd->maxit);
         if (st != HZS_OK) return st;
     }
+    if (orth32) {
+        hzs_status st = set_basis_width(p, lo16 ? 1 : 0);
+        if (st != HZS_OK) return st;
+    }
     HZS_CUDA(g, cudaEventRecord(p->t0, s));
-    // V_0 = f (masked; it is never rescaled in place), plus its complex64 copy for orth32
+    // V_0 = f (masked; it is never rescaled in place), plus its double-float copy for orth32
     launch_mask_copy_c128(cx, nb, f, nn, kb.V, kb.sVd(), conj_io, orth32 ? kb.V32 : nullptr, sV,
-                          orth32 ? kb.V32lo : nullptr);
+                          orth32 ? kb.lo_at(0) : LoDst{nullptr, nullptr});
     launch_norm_init(cx, kb, nb, sd->tol);
     launches += 3;
     int steps = 0;
@@ -675,11 +703,9 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
             st = precond_apply<float, float2>(p, nb, kb.V32 + (size_t)j * ld, sV, kb.sigt + j, sS, Zj, sZ, sk);
             if (prof) HZS_CUDA(g, cudaEventRecord(pe[1], s));
             // A z_j as a double-float pair (the FP64 copy of the basis is not used on this path)
-            if (!launch_apply_A_df(cx, nb, Zj, sZ, kb.V32 + (size_t)(j + 1) * ld, kb.V32lo + (size_t)(j + 1) * ld, sV,
-                                   sk))
+            if (!launch_apply_A_df(cx, nb, Zj, sZ, kb.V32 + (size_t)(j + 1) * ld, kb.lo_at(j + 1), sV, sk))
                 launch_apply_A<float2, double2, double>(cx, nb, Zj, sZ, (double2*)nullptr, 0,
-                                                        kb.V32 + (size_t)(j + 1) * ld, sV, sk,
-                                                        kb.V32lo + (size_t)(j + 1) * ld);
+                                                        kb.V32 + (size_t)(j + 1) * ld, sV, sk, kb.lo_at(j + 1));
         } else if (mixed) {
             float2* Zj = p->Z + (size_t)j * ld;
             st = precond_apply<float, double2>(p, nb, kb.V + (size_t)j * ld, sV, kb.sigma + j, sS, Zj, sZ, sk);
@@ -769,6 +795,7 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
         inf.relres_true = hs[r].beta0 > 0 ? rnorm[r] / hs[r].beta0 : 0.0;
         inf.t_solve_ms = ms;
         inf.launches = launches;
+        inf.basis_bits = !orth32 ? 53 : (lo16 ? 32 : 48);
         inf.status = hs[r].nonfinite ? HZS_ERR_NONFINITE : (hs[r].conv ? HZS_OK : HZS_NOT_CONVERGED);
         if (info) info[r] = inf;
         if (inf.status == HZS_ERR_NONFINITE) worst = HZS_ERR_NONFINITE;

@@ -1,6 +1,7 @@
 // Shared device helpers for the Helmholtz / Schwarz kernels.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -107,6 +108,24 @@ __device__ __forceinline__ void split_d(double x, float& hi, float& lo) {
     hi = (float)x;
     lo = (float)(x - (double)hi);
 }
+
+// Remainder words of a double-float complex vector whose leading words are a
+// separate complex64 array: complex64 (wide: 8 bytes an entry, about 48
+// significant bits in all) or a bf16 pair (narrow: 4 bytes an entry, about 32
+// bits, the bf16 keeping the top 8 of the remainder's 24).  At most one
+// pointer is set; with neither, nothing is written.
+struct LoDst {
+    float2* wide;
+    __nv_bfloat162* narrow;
+    __host__ __device__ __forceinline__ LoDst at(long long off) const {
+        return LoDst{wide ? wide + off : nullptr, narrow ? narrow + off : nullptr};
+    }
+    __host__ __device__ __forceinline__ bool any() const { return wide != nullptr || narrow != nullptr; }
+    __device__ __forceinline__ void put(long long i, float2 v) const {
+        if (wide) wide[i] = v;
+        else if (narrow) narrow[i] = __floats2bfloat162_rn(v.x, v.y);
+    }
+};
 
 template <typename C> __device__ __forceinline__ C shfl_down(C v, int off) {
     v.x = __shfl_down_sync(0xffffffffu, v.x, off);

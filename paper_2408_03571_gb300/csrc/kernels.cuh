@@ -80,10 +80,10 @@ struct FactorStat {
 // ---- operator.cu
 template <typename Cin, typename Cout, typename R>
 void launch_apply_A(const Ctx& cx, int nb, const Cin* x, long long xs, Cout* y, long long ys, float2* y32,
-                    long long y32s, BatchSkip sk, float2* y32lo = nullptr);
-// y = A x in double-float arithmetic, y as the complex64 pair yh + yl; false (nothing
+                    long long y32s, BatchSkip sk, LoDst y32lo = LoDst{nullptr, nullptr});
+// y = A x in double-float arithmetic, y as the pair yh + yl (see LoDst); false (nothing
 // launched) when the couplings are not exact in FP32 (n > 4097).
-bool launch_apply_A_df(const Ctx& cx, int nb, const float2* x, long long xs, float2* yh, float2* yl, long long ys,
+bool launch_apply_A_df(const Ctx& cx, int nb, const float2* x, long long xs, float2* yh, LoDst yl, long long ys,
                        BatchSkip sk);
 template <typename Cv, typename Cw, typename R>
 void launch_deflate(const Ctx& cx, int nb, const cplx_t<R>* c, long long cs, const Cv* v, long long vs,
@@ -93,7 +93,7 @@ void launch_combine_additive(const Ctx& cx, int nb, const cplx_t<R>* c, long lon
                              const int4* cover, const Tile* tiles, int nsub, const Cy* ytiles, long long yts, Cz* z,
                              long long zs, BatchSkip sk);
 void launch_mask_copy_c128(const Ctx& cx, int nb, const double2* src, long long ss, double2* dst, long long ds,
-                           int conj, float2* dst32, long long d32s, float2* dst32lo = nullptr);
+                           int conj, float2* dst32, long long d32s, LoDst dst32lo = LoDst{nullptr, nullptr});
 void launch_kappa_gradient(const Ctx& cx, const double2* u, const double2* lam, double* grad);
 
 // ---- coarse.cu
@@ -171,8 +171,10 @@ struct KrylovBufs {
     double2* V;        // complex128 basis: (maxit+1) x ld per entry, or only slot 0 (the masked
                        // right-hand side) when vfull == 0 (the double-float path keeps no FP64 basis)
     int vfull;
-    float2* V32;       // (maxit+1) x ld complex64 roundings of the basis (mixed-precision CGS2), or null
-    float2* V32lo;     // (maxit+1) x ld complex64 remainders: V32 + V32lo is the basis as double-float pairs
+    float2* V32;       // (maxit+1) x ld complex64 roundings of the basis (delayed CGS2 path), or null
+    void* V32lo;       // (maxit+1) x ld remainders: V32 + V32lo is the basis as double-float pairs,
+                       // complex64 words or, with lo16, bf16 pairs (LoDst); sized for complex64
+    int lo16;          // remainders stored as bf16 pairs (set per solve)
     double* sigma;     // (maxit+1): basis vector i = sigma[i] * V_i
     double2* H;        // (maxit+1) x maxit, column j at H[j*(maxit+1)]
     double* cs;        // maxit+1
@@ -195,10 +197,17 @@ struct KrylovBufs {
     int pstride() const { return 2 * (maxit + 1) + 2; }
     long long sP() const { return (long long)nblk_dot * pstride(); }
     BatchSkip skip() const { return BatchSkip{&st->done, kStateInts}; }
+    // remainders of basis slot i of batch entry 0 (entry r at r * sV() further)
+    LoDst lo_at(long long i) const {
+        const long long off = i * ld;
+        return lo16 ? LoDst{nullptr, static_cast<__nv_bfloat162*>(V32lo) + off}
+                    : LoDst{static_cast<float2*>(V32lo) + off, nullptr};
+    }
 };
 void launch_norm_init(const Ctx& cx, const KrylovBufs& kb, int nb, double tol);
 void launch_arnoldi_step(const Ctx& cx, const KrylovBufs& kb, int nb, int j);
-// Step j of the delayed CGS2 Arnoldi on the double-float basis (V32 + V32lo);
+// Step j of the delayed CGS2 Arnoldi on the double-float basis (V32 + V32lo, lo16 selects
+// the remainder width);
 // last_only (j == maxit) completes the last Hessenberg column only.  ev (optional,
 // 4 events) is recorded before and after the dot pass and the update pass.
 void launch_dcgs2_step(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int last_only, cudaEvent_t* ev = nullptr);

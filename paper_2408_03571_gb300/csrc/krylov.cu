@@ -22,7 +22,7 @@ namespace hzs {
 
 constexpr int kRedThreads = 256;
 constexpr int kDotGroup64 = 4;     // basis vectors per warp pass (FP64 multi-dot)
-constexpr int kDotGroupDC = 2;     // basis vectors per warp pass (delayed CGS2 multi-dot)
+constexpr int kDotGroupDC = 4;     // basis vectors per warp pass (delayed CGS2 multi-dot)
 constexpr int kUpdUnroll = 4;      // basis vectors per iteration of the delayed CGS2 update
 
 __device__ __forceinline__ void chunk_of(long long N, long long& e0, long long& e1) {
@@ -147,6 +147,24 @@ __global__ void __launch_bounds__(kRedThreads) k_axpy_multi(int j, long long N, 
 
 __device__ __forceinline__ float2 lo2(float4 a) { return make_float2(a.x, a.y); }
 __device__ __forceinline__ float2 hi2(float4 a) { return make_float2(a.z, a.w); }
+
+// Remainders of an entry pair, stored as L: float4 (complex64 words, wide) or
+// uint2 (bf16 pairs, narrow: word k holds entry k's real part in its low half and
+// its imaginary part in its high half, the layout of LoDst's narrow array).
+// Unpacked to (re0, im0, re1, im1); a bf16 widens to FP32 exactly by a shift.
+__device__ __forceinline__ float4 lo_unpack(float4 v) { return v; }
+__device__ __forceinline__ float4 lo_unpack(uint2 v) {
+    return make_float4(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xffff0000u), __uint_as_float(v.y << 16),
+                       __uint_as_float(v.y & 0xffff0000u));
+}
+__device__ __forceinline__ void lo_store(float4* p, float4 v) { *p = v; }
+__device__ __forceinline__ void lo_store(uint2* p, float4 v) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+    uint2 u;
+    memcpy(&u.x, &a, 4);
+    memcpy(&u.y, &b, 4);
+    *p = u;
+}
 
 // (sh, sl) += c * v for one complex component pair, double-float:
 // re += cr vr - ci vi ; im += cr vi + ci vr
@@ -281,8 +299,8 @@ __device__ double givens_column(int jc, double2* col, const double* scs, const d
 // At the start of step j, slot j holds u~_j, the once-projected w of step j-1
 // (not yet reorthogonalised or normalised), and slot j+1 holds w.  With Q the
 // orthonormal vectors 0..j-1 (vector i = sigma[i] V_i):
-//   dot pass:  alpha = Q^H u~_j (double-float), b = Q^H w (complex64 on the
-//              leading words), c = |u~_j|^2, d = u~_j^H w;
+//   dot pass:  alpha = Q^H u~_j, b = Q^H w, c = |u~_j|^2, d = u~_j^H w, all in
+//              complex64 on the leading words of the basis;
 //   finish:    beta_j^2 = c - |alpha|^2, column j-1 of H is completed as
 //              h1_{j-1} + alpha with subdiagonal beta_j, the first-pass
 //              coefficients of column j are b and (d - alpha^H b) / beta_j;
@@ -291,23 +309,28 @@ __device__ double givens_column(int jc, double2* col, const double* scs, const d
 // The preconditioner of step j is applied to u~_j / |u~_j|: the flexible
 // Arnoldi relation A Z = Q H holds for any z_j, and span{u~_0..u~_j} equals
 // span{q_0..q_j}, so the iterates are those of FGMRES with z_j = M q_j.
-// Row layout of the dot partials per block (16 B slots): alpha at [0, S) as FP32
-// double-float pairs (hi.re, lo.re, hi.im, lo.im), b at [S, 2S) as complex64 in
-// the first 8 bytes, c at 2S and d at 2S+1 as complex128 (S = maxit+1).
+// Precision: the update pass applies the coefficients it is given exactly (to
+// the basis's double-float width), so the Arnoldi relation holds to that width
+// whatever their accuracy; the coefficients' complex64 rounding only sets how
+// orthogonal the basis stays (CGS2 in a precision keeps it orthogonal to a
+// small multiple of that precision, about 1e-6 here), which changes neither the
+// Krylov space nor, by more than that factor, the residual estimate.  c enters
+// beta_j, which therefore carries complex64 relative accuracy: q_j = V_j / beta_j
+// by definition, so the relation is unaffected.
+// Row layout of the dot partials per block (16 B slots): alpha at [0, S) and b at
+// [S, 2S) as complex64 in the first 8 bytes of a slot, c at 2S and d at 2S+1 as
+// complex128 (S = maxit+1).
 
 template <int G>
 __global__ void __launch_bounds__(kRedThreads, 4) k_dcgs_dot(int j, long long Np, long long ldp, int ps, int S,
-                                                          const float4* __restrict__ V32,
-                                                          const float4* __restrict__ V32lo, long long sVp,
-                                                          int has_w, double2* __restrict__ part, long long sP,
+                                                          const float4* __restrict__ V32, long long sVp, int has_w,
+                                                          double2* __restrict__ part, long long sP,
                                                           const KState* __restrict__ st) {
     const int r = blockIdx.y;
     if (st[r].done) return;
-    V32 += r * sVp; V32lo += r * sVp;
+    V32 += r * sVp;
     const float4* uh = V32 + (size_t)j * ldp;
-    const float4* ul = V32lo + (size_t)j * ldp;
     const float4* wh = has_w ? V32 + (size_t)(j + 1) * ldp : uh;     // slot j+1 exists only with w
-    const float4* wl = has_w ? V32lo + (size_t)(j + 1) * ldp : ul;
     part += r * sP + (size_t)blockIdx.x * ps;
     long long e0, e1;
     chunk_of(Np, e0, e1);
@@ -315,91 +338,58 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_dcgs_dot(int j, long long Np
     const int ngroups = (j + G - 1) / G;
     for (int gi = warp; gi <= ngroups; gi += nw) {
         if (gi == ngroups) {
-            // c = |u~|^2 and d = u~^H w (double-float)
-            float ch = 0.f, cl = 0.f, dr = 0.f, drl = 0.f, di = 0.f, dil = 0.f;
-            int cnt = 0;
+            // c = |u~|^2 and d = u~^H w
+            float c = 0.f;
+            float2 d = make_float2(0.f, 0.f);
             for (long long e = e0 + lane; e < e1; e += 32) {
-                const float4 xh = uh[e], xl = ul[e];
-                df_fma(ch, cl, xh.x, xl.x, xh.x, xl.x);
-                df_fma(ch, cl, xh.y, xl.y, xh.y, xl.y);
-                df_fma(ch, cl, xh.z, xl.z, xh.z, xl.z);
-                df_fma(ch, cl, xh.w, xl.w, xh.w, xl.w);
+                const float4 xh = uh[e];
+                c = fmaf(xh.x, xh.x, fmaf(xh.y, xh.y, fmaf(xh.z, xh.z, fmaf(xh.w, xh.w, c))));
                 if (has_w) {
-                    const float4 yh = wh[e], yl = wl[e];
-                    df_fma(dr, drl, xh.x, xl.x, yh.x, yl.x);
-                    df_fma(dr, drl, xh.y, xl.y, yh.y, yl.y);
-                    df_fma(di, dil, xh.x, xl.x, yh.y, yl.y);
-                    df_fma(di, dil, -xh.y, -xl.y, yh.x, yl.x);
-                    df_fma(dr, drl, xh.z, xl.z, yh.z, yl.z);
-                    df_fma(dr, drl, xh.w, xl.w, yh.w, yl.w);
-                    df_fma(di, dil, xh.z, xl.z, yh.w, yl.w);
-                    df_fma(di, dil, -xh.w, -xl.w, yh.z, yl.z);
+                    const float4 yh = wh[e];
+                    d = cfma_conj(lo2(xh), lo2(yh), d);
+                    d = cfma_conj(hi2(xh), hi2(yh), d);
                 }
-                if ((++cnt & 7) == 0) { df_norm(ch, cl); df_norm(dr, drl); df_norm(di, dil); }
             }
-            double c = (double)ch + (double)cl;
-            double2 d = make_double2((double)dr + (double)drl, (double)di + (double)dil);
-            c = warp_sum_d(c);
-            d = warp_sum(d);
+            const double cs = warp_sum_d((double)c);
+            const double2 ds = warp_sum(make_double2((double)d.x, (double)d.y));
             if (lane == 0) {
-                part[2 * S] = make_double2(c, 0.0);
-                part[2 * S + 1] = d;
+                part[2 * S] = make_double2(cs, 0.0);
+                part[2 * S + 1] = ds;
             }
             continue;
         }
         const int i0 = gi * G;
-        float rh[G], rl[G], ih[G], il[G];
-        float2 bb[G];
+        float2 aa[G], bb[G];
 #pragma unroll
-        for (int t = 0; t < G; ++t) { rh[t] = rl[t] = ih[t] = il[t] = 0.f; bb[t] = make_float2(0.f, 0.f); }
-        int cnt = 0;
+        for (int t = 0; t < G; ++t) aa[t] = bb[t] = make_float2(0.f, 0.f);
         for (long long e = e0 + lane; e < e1; e += 32) {
             // u~ and w are re-read by every warp of the block: read-only cache path;
             // the basis is read once: streaming (evict-first) loads
-            const float4 xh = __ldg(uh + e), xl = __ldg(ul + e);
+            const float4 xh = __ldg(uh + e);
             const float4 yh = has_w ? __ldg(wh + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 vh[G];
+#pragma unroll
+            for (int t = 0; t < G; ++t)
+                vh[t] = i0 + t < j ? __ldcs(V32 + (size_t)(i0 + t) * ldp + e) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int t = 0; t < G; ++t) {
-                if (i0 + t >= j) continue;
-                const float4 vh = __ldcs(V32 + (size_t)(i0 + t) * ldp + e);
-                const float4 vl = __ldcs(V32lo + (size_t)(i0 + t) * ldp + e);
-                // alpha: conj(v) u~, re = vr ur + vi ui, im = vr ui - vi ur (two entries)
-                df_fma(rh[t], rl[t], vh.x, vl.x, xh.x, xl.x);
-                df_fma(rh[t], rl[t], vh.y, vl.y, xh.y, xl.y);
-                df_fma(ih[t], il[t], vh.x, vl.x, xh.y, xl.y);
-                df_fma(ih[t], il[t], -vh.y, -vl.y, xh.x, xl.x);
-                df_fma(rh[t], rl[t], vh.z, vl.z, xh.z, xl.z);
-                df_fma(rh[t], rl[t], vh.w, vl.w, xh.w, xl.w);
-                df_fma(ih[t], il[t], vh.z, vl.z, xh.w, xl.w);
-                df_fma(ih[t], il[t], -vh.w, -vl.w, xh.z, xl.z);
-                // b: conj(v) w on the leading words
-                bb[t] = cfma_conj(lo2(vh), lo2(yh), bb[t]);
-                bb[t] = cfma_conj(hi2(vh), hi2(yh), bb[t]);
-            }
-            if ((++cnt & 15) == 0) {
-#pragma unroll
-                for (int t = 0; t < G; ++t) { df_norm(rh[t], rl[t]); df_norm(ih[t], il[t]); }
+                aa[t] = cfma_conj(lo2(vh[t]), lo2(xh), aa[t]);      // alpha: conj(v) u~
+                aa[t] = cfma_conj(hi2(vh[t]), hi2(xh), aa[t]);
+                bb[t] = cfma_conj(lo2(vh[t]), lo2(yh), bb[t]);      // b: conj(v) w
+                bb[t] = cfma_conj(hi2(vh[t]), hi2(yh), bb[t]);
             }
         }
 #pragma unroll
         for (int t = 0; t < G; ++t) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float orh = __shfl_down_sync(0xffffffffu, rh[t], o);
-                const float orl = __shfl_down_sync(0xffffffffu, rl[t], o);
-                const float oih = __shfl_down_sync(0xffffffffu, ih[t], o);
-                const float oil = __shfl_down_sync(0xffffffffu, il[t], o);
-                df_add(rh[t], rl[t], orh, orl);
-                df_add(ih[t], il[t], oih, oil);
-            }
+            aa[t] = warp_sum(aa[t]);
             bb[t] = warp_sum(bb[t]);
         }
         if (lane == 0) {
 #pragma unroll
             for (int t = 0; t < G; ++t)
                 if (i0 + t < j) {
-                    // raw FP32 words; the reduction converts (FP64 instructions stay out of this kernel)
-                    reinterpret_cast<float4*>(part)[i0 + t] = make_float4(rh[t], rl[t], ih[t], il[t]);
+                    // raw FP32 words; the reduction converts (FP64 instructions stay out of this loop)
+                    reinterpret_cast<float4*>(part)[i0 + t] = make_float4(aa[t].x, aa[t].y, 0.f, 0.f);
                     reinterpret_cast<float4*>(part)[S + i0 + t] = make_float4(bb[t].x, bb[t].y, 0.f, 0.f);
                 }
         }
@@ -421,12 +411,12 @@ __global__ void k_dcgs_reduce(int j, int nblk, int ps, int S, const double2* __r
     const int col = k < j ? k : (k < 2 * j ? S + (k - j) : 2 * S + (k - 2 * j));
     double2 s = make_double2(0.0, 0.0);
     if (k < 2 * j) {
-        // alpha: double-float pairs (hi.re, lo.re, hi.im, lo.im); b: complex64 in .x, .y
+        // alpha and b: complex64 in the first 8 bytes of the slot
         const float4* pf = reinterpret_cast<const float4*>(part);
         for (int b = lane; b < nblk; b += 32) {
             const float4 v = pf[(size_t)b * ps + col];
-            if (k < j) { s.x += (double)v.x + (double)v.y; s.y += (double)v.z + (double)v.w; }
-            else { s.x += (double)v.x; s.y += (double)v.y; }
+            s.x += (double)v.x;
+            s.y += (double)v.y;
         }
     } else {
         for (int b = lane; b < nblk; b += 32) s = cadd(s, part[(size_t)b * ps + col]);
@@ -514,8 +504,9 @@ __global__ void __launch_bounds__(kFinThreads) k_dcgs_finish(int j, int maxit, i
 // (the small reorthogonalisation sum in complex64, its subtraction in double-float),
 // w = w - sum_i (sigma_i b_i) V_i - (h_jj sigma_j) V_j in double-float;
 // npart[b] = sum_e |w[e]|^2 (FP32 on the leading words: it only sets a scale).
+template <typename L>
 __global__ void __launch_bounds__(kRedThreads, 3) k_dcgs_update(int j, long long Np, long long ldp,
-                                                             float4* __restrict__ V32, float4* __restrict__ V32lo,
+                                                             float4* __restrict__ V32, L* __restrict__ V32lo,
                                                              long long sVp, const double* __restrict__ sigma,
                                                              const double2* __restrict__ h1,
                                                              const double2* __restrict__ h2, long long sS,
@@ -525,9 +516,9 @@ __global__ void __launch_bounds__(kRedThreads, 3) k_dcgs_update(int j, long long
     if (st[r].done) return;
     V32 += r * sVp; V32lo += r * sVp; sigma += r * sS; h1 += r * sS; h2 += r * sS;
     float4* uh = V32 + (size_t)j * ldp;
-    float4* ul = V32lo + (size_t)j * ldp;
+    L* ul = V32lo + (size_t)j * ldp;
     float4* wh = V32 + (size_t)(j + 1) * ldp;
-    float4* wl = V32lo + (size_t)(j + 1) * ldp;
+    L* wl = V32lo + (size_t)(j + 1) * ldp;
     extern __shared__ float4 dsm[];
     float4* cb = dsm;                                       // j + 1: w coefficients (double-float)
     float2* ca = reinterpret_cast<float2*>(dsm + (j + 1));  // j: reorthogonalisation coefficients
@@ -547,7 +538,7 @@ __global__ void __launch_bounds__(kRedThreads, 3) k_dcgs_update(int j, long long
         float a0h = 0.f, a0l = 0.f, b0h = 0.f, b0l = 0.f, a1h = 0.f, a1l = 0.f, b1h = 0.f, b1l = 0.f;
         float2 s0 = make_float2(0.f, 0.f), s1 = s0;
         const float4* ph = V32 + e;
-        const float4* pl = V32lo + e;
+        const L* pl = V32lo + e;
         // basis vectors in the order j-1 .. 0: the dot pass read 0 .. j-1, so the vectors
         // still in L2 come first, and this pass leaves vectors 0, 1, .. in L2 for the next
         // dot pass
@@ -558,7 +549,7 @@ __global__ void __launch_bounds__(kRedThreads, 3) k_dcgs_update(int j, long long
 #pragma unroll
             for (int t = 0; t < kUpdUnroll; ++t) {
                 vh[t] = ph[(size_t)vi(i + t) * ldp];
-                vl[t] = pl[(size_t)vi(i + t) * ldp];
+                vl[t] = lo_unpack(pl[(size_t)vi(i + t) * ldp]);
             }
 #pragma unroll
             for (int t = 0; t < kUpdUnroll; ++t) {
@@ -571,7 +562,7 @@ __global__ void __launch_bounds__(kRedThreads, 3) k_dcgs_update(int j, long long
             df_norm(a0h, a0l); df_norm(b0h, b0l); df_norm(a1h, a1l); df_norm(b1h, b1l);
         }
         for (; i < j; ++i) {
-            const float4 vh = ph[(size_t)vi(i) * ldp], vl = pl[(size_t)vi(i) * ldp];
+            const float4 vh = ph[(size_t)vi(i) * ldp], vl = lo_unpack(pl[(size_t)vi(i) * ldp]);
             const float4 q = cb[vi(i)];
             df_cmac(a0h, a0l, b0h, b0l, q, vh.x, vl.x, vh.y, vl.y);
             df_cmac(a1h, a1l, b1h, b1l, q, vh.z, vl.z, vh.w, vl.w);
@@ -579,24 +570,24 @@ __global__ void __launch_bounds__(kRedThreads, 3) k_dcgs_update(int j, long long
             s1 = cfma(ca[vi(i)], hi2(vh), s1);
         }
         // V_j = u~ - s
-        float4 xh = uh[e], xl = ul[e];
+        float4 xh = uh[e], xl = lo_unpack(ul[e]);
         df_add(xh.x, xl.x, -s0.x, 0.f); df_norm(xh.x, xl.x);
         df_add(xh.y, xl.y, -s0.y, 0.f); df_norm(xh.y, xl.y);
         df_add(xh.z, xl.z, -s1.x, 0.f); df_norm(xh.z, xl.z);
         df_add(xh.w, xl.w, -s1.y, 0.f); df_norm(xh.w, xl.w);
         uh[e] = xh;
-        ul[e] = xl;
+        lo_store(ul + e, xl);
         // + (h_jj sigma_j) V_j
         const float4 qj = cb[j];
         df_cmac(a0h, a0l, b0h, b0l, qj, xh.x, xl.x, xh.y, xl.y);
         df_cmac(a1h, a1l, b1h, b1l, qj, xh.z, xl.z, xh.w, xl.w);
-        float4 yh = wh[e], yl = wl[e];
+        float4 yh = wh[e], yl = lo_unpack(wl[e]);
         df_add(yh.x, yl.x, -a0h, -a0l); df_norm(yh.x, yl.x);
         df_add(yh.y, yl.y, -b0h, -b0l); df_norm(yh.y, yl.y);
         df_add(yh.z, yl.z, -a1h, -a1l); df_norm(yh.z, yl.z);
         df_add(yh.w, yl.w, -b1h, -b1l); df_norm(yh.w, yl.w);
         wh[e] = yh;
-        wl[e] = yl;
+        lo_store(wl + e, yl);
         // |u~_{j+1}| only scales the next preconditioner input: FP32 on the leading words
         nrmf = fmaf(yh.x, yh.x, fmaf(yh.y, yh.y, fmaf(yh.z, yh.z, fmaf(yh.w, yh.w, nrmf))));
     }
@@ -836,18 +827,14 @@ void launch_arnoldi_step(const Ctx& cx, const KrylovBufs& kb, int nb, int j) {
                                                                      kb.sS(), kb.st, kb.active);
 }
 
-// Mixed-precision CGS2 (used with the complex64 preconditioner).  The basis
-// is held as double-float pairs V32 + V32lo (complex64 rounding and remainder,
-// about 48 significand bits), written by the matrix-vector product and the
-// last pass.  The first projection h1 = V^H w is computed in complex64 from
-// V32 alone; the update w -= V h1 and the reorthogonalisation h2 = V^H w run
-// in double-float arithmetic (error-free FMA products and TwoSum accumulation
-// on the FP32 pipes); the second update w -= V h2 sums in complex64 (h2 is of
-// the size of the first pass's rounding) and subtracts in double-float.  The
-// FP64 Hessenberg column, norms and Givens update are unchanged.
-// Orthogonality and the Arnoldi relation hold to about 1e-12 relative (the
-// double-float accumulation), far below any GMRES tolerance used here, while
-// no basis pass executes an FP64 instruction per basis entry.
+// Delayed CGS2 on the double-float basis (used with the complex64
+// preconditioner, see k_dcgs_dot): the basis passes run on the FP32 pipes in
+// double-float arithmetic (error-free FMA products, TwoSum accumulation); the
+// Hessenberg column, norms and Givens update stay in FP64.  Wide remainders give
+// the basis about 48 significant bits, so orthogonality and the Arnoldi relation
+// hold far below any GMRES tolerance used here; narrow (bf16) remainders give it
+// about 32 bits and move 12 instead of 16 bytes an entry, the caller's choice
+// for loose tolerances.
 static size_t dcgs_finish_smem(int j) {
     const size_t b = (size_t)(j + 1) * sizeof(double2) + (size_t)(j > 0 ? j - 1 : 0) * (sizeof(double2) + sizeof(double));
     allow_dynamic_smem((const void*)k_dcgs_finish, b);
@@ -859,11 +846,11 @@ void launch_dcgs2_step(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int l
     // entry pairs: the padded vector length and all strides are even
     const long long Np = (kb.N + 1) / 2, ldp = kb.ld / 2, sVp = kb.sV() / 2;
     float4* V32 = reinterpret_cast<float4*>(kb.V32);
-    float4* V32lo = reinterpret_cast<float4*>(kb.V32lo);
     const dim3 gr(kb.nblk, nb);
     if (ev) cudaEventRecord(ev[0], cx.stream);
-    k_dcgs_dot<kDotGroupDC><<<dim3(kb.nblk_dot, nb), kRedThreads, 0, cx.stream>>>(
-        j, Np, ldp, ps, S, V32, V32lo, sVp, !last_only, kb.part, kb.sP(), kb.st);
+    k_dcgs_dot<kDotGroupDC><<<dim3(kb.nblk_dot, nb), kRedThreads, 0, cx.stream>>>(j, Np, ldp, ps, S, V32, sVp,
+                                                                                 !last_only, kb.part, kb.sP(),
+                                                                                 kb.st);
     if (ev) cudaEventRecord(ev[1], cx.stream);
     const dim3 rg(((2 * j + 2) * 32 + 255) / 256, nb);
     k_dcgs_reduce<<<rg, 256, 0, cx.stream>>>(j, kb.nblk_dot, ps, S, kb.part, kb.sP(), kb.sigma, kb.h2, kb.hn,
@@ -873,10 +860,18 @@ void launch_dcgs2_step(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int l
                                                                         kb.g, kb.sigma, kb.sS(), kb.st, kb.active);
     if (last_only) return;
     const size_t us = (size_t)(j + 1) * sizeof(float4) + (size_t)j * sizeof(float2);
-    set_coef_smem_limit((const void*)k_dcgs_update, us);
     if (ev) cudaEventRecord(ev[2], cx.stream);
-    k_dcgs_update<<<gr, kRedThreads, us, cx.stream>>>(j, Np, ldp, V32, V32lo, sVp, kb.sigma, kb.h1, kb.h2, kb.sS(),
-                                                      kb.npart, kb.nblk, kb.st);
+    if (kb.lo16) {
+        set_coef_smem_limit((const void*)k_dcgs_update<uint2>, us);
+        k_dcgs_update<uint2><<<gr, kRedThreads, us, cx.stream>>>(j, Np, ldp, V32, static_cast<uint2*>(kb.V32lo), sVp,
+                                                                 kb.sigma, kb.h1, kb.h2, kb.sS(), kb.npart, kb.nblk,
+                                                                 kb.st);
+    } else {
+        set_coef_smem_limit((const void*)k_dcgs_update<float4>, us);
+        k_dcgs_update<float4><<<gr, kRedThreads, us, cx.stream>>>(j, Np, ldp, V32, static_cast<float4*>(kb.V32lo),
+                                                                  sVp, kb.sigma, kb.h1, kb.h2, kb.sS(), kb.npart,
+                                                                  kb.nblk, kb.st);
+    }
     if (ev) cudaEventRecord(ev[3], cx.stream);
     k_dcgs_scale<<<nb, 32, 0, cx.stream>>>(j, kb.nblk, kb.npart, kb.sigt, kb.sS(), kb.st);
 }

@@ -18,12 +18,12 @@ __device__ __forceinline__ bool skipped(const BatchSkip& sk, int r) {
 
 // y = A x over the n x n grid.  Arithmetic in R; x read as Cin; y (if given)
 // written as Cout; y32 (if given) receives the complex64 rounding of the
-// result and y32lo (if given) the complex64 rounding of the remainder, so that
-// y32 + y32lo carries the result as a double-float pair.  MP-1 boundary nodes:
+// result and y32lo (if set, see LoDst) the remainder, so that y32 + y32lo
+// carries the result as a double-float pair.  MP-1 boundary nodes:
 // y = 0, and their x values are never read.
 template <typename Cin, typename Cout, typename R>
 __global__ void k_apply_A(OpDesc op, const Cin* __restrict__ x, long long xs, Cout* __restrict__ y, long long ys,
-                          float2* __restrict__ y32, long long y32s, float2* __restrict__ y32lo, BatchSkip sk) {
+                          float2* __restrict__ y32, long long y32s, LoDst y32lo, BatchSkip sk) {
     using C = cplx_t<R>;
     const int r = blockIdx.z;
     if (skipped(sk, r)) return;
@@ -34,12 +34,12 @@ __global__ void k_apply_A(OpDesc op, const Cin* __restrict__ x, long long xs, Co
     x += r * xs;
     if (y) y += r * ys;
     if (y32) y32 += r * y32s;
-    if (y32lo) y32lo += r * y32s;
+    y32lo = y32lo.at(r * y32s);
     const size_t p = (size_t)j * n + i;
     if (!op_is_unknown(op, i, j)) {
         if (y) y[p] = mk<Cout>(0.0, 0.0);
         if (y32) y32[p] = make_float2(0.f, 0.f);
-        if (y32lo) y32lo[p] = make_float2(0.f, 0.f);
+        y32lo.put(p, make_float2(0.f, 0.f));
         return;
     }
     const double2 d = op_diag(op, i, j);
@@ -57,39 +57,41 @@ __global__ void k_apply_A(OpDesc op, const Cin* __restrict__ x, long long xs, Co
     acc.x += cx * sx.x + cy * sy.x;
     acc.y += cx * sx.y + cy * sy.y;
     if (y) y[p] = conv<Cout>(acc);
-    if (y32lo) {
+    if (y32lo.any()) {
         const double2 a = to_d(acc);
         float2 hi, lo;
         split_d(a.x, hi.x, lo.x);
         split_d(a.y, hi.y, lo.y);
         y32[p] = hi;
-        y32lo[p] = lo;
+        y32lo.put(p, lo);
     } else if (y32) {
         y32[p] = conv<float2>(acc);
     }
 }
 
 // y = A x for a complex64 x, in double-float arithmetic on the FP32 pipes (the
-// FP64 rate is 1/62 of FP32 on GB300): y is written as the pair y32 + y32lo.
+// FP64 rate is 1/62 of FP32 on GB300): y is written as the pair yh + yl
+// (remainders wide or narrow, see LoDst).
 // The couplings -1/h^2 (halved on Sommerfeld edges) are exact in FP32 for
 // n <= 4097 (checked by the launcher); the diagonal is the double-float pair
 // (dh, dl) for interior nodes of a constant-kappa grid and is otherwise formed
 // in FP64 and split.  The neighbour sums are exact (TwoSum), every product is
 // error-free (FMA form of Dekker's product), so y carries about 47 significant
-// bits relative to the largest term of the stencil sum.
+// bits relative to the largest term of the stencil sum before the remainder is
+// stored.
 __global__ void k_apply_A_df(OpDesc op, float ch, float dh, float dl, const float2* __restrict__ x, long long xs,
-                             float2* __restrict__ yh, float2* __restrict__ yl, long long ys, BatchSkip sk) {
+                             float2* __restrict__ yh, LoDst yl, long long ys, BatchSkip sk) {
     const int r = blockIdx.z;
     if (skipped(sk, r)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int n = op.n;
     if (i >= n || j >= n) return;
-    x += r * xs; yh += r * ys; yl += r * ys;
+    x += r * xs; yh += r * ys; yl = yl.at(r * ys);
     const size_t p = (size_t)j * n + i;
     if (!op_is_unknown(op, i, j)) {
         yh[p] = make_float2(0.f, 0.f);
-        yl[p] = make_float2(0.f, 0.f);
+        yl.put(p, make_float2(0.f, 0.f));
         return;
     }
     const bool edge_x = i == 0 || i == n - 1, edge_y = j == 0 || j == n - 1;
@@ -127,7 +129,7 @@ __global__ void k_apply_A_df(OpDesc op, float ch, float dh, float dl, const floa
     df_norm(reh, rel);
     df_norm(imh, iml);
     yh[p] = make_float2(reh, imh);
-    yl[p] = make_float2(rel, iml);
+    yl.put(p, make_float2(rel, iml));
 }
 
 // q(i, j) = sum_{a,b} wx(i,a) wy(j,b) c[(c0[j]+b) nc1 + c0[i]+a]   (prolongation R_0^T c)
@@ -256,11 +258,10 @@ __global__ void k_combine_additive(OpDesc op, CoarseTab ct, const cplx_t<R>* __r
 }
 
 // dst = src (or conj(src)) on unknowns, 0 on MP-1 boundary nodes; dst32 (if
-// given) receives the same values in complex64 and dst32lo (if given) the
-// complex64 remainders (double-float pairs).
+// given) receives the same values in complex64 and dst32lo (if set, see
+// LoDst) the remainders of the double-float pairs.
 __global__ void k_mask_copy(OpDesc op, const double2* __restrict__ src, long long ss, double2* __restrict__ dst,
-                            long long ds, int conj, float2* __restrict__ dst32, long long d32s,
-                            float2* __restrict__ dst32lo) {
+                            long long ds, int conj, float2* __restrict__ dst32, long long d32s, LoDst dst32lo) {
     const int r = blockIdx.z;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -271,12 +272,12 @@ __global__ void k_mask_copy(OpDesc op, const double2* __restrict__ src, long lon
     double2 v = op_is_unknown(op, i, j) ? src[p] : make_double2(0.0, 0.0);
     if (conj) v.y = -v.y;
     dst[p] = v;
-    if (dst32lo) {
+    if (dst32lo.any()) {
         float2 hi, lo;
         split_d(v.x, hi.x, lo.x);
         split_d(v.y, hi.y, lo.y);
         dst32[r * d32s + p] = hi;
-        dst32lo[r * d32s + p] = lo;
+        dst32lo.put(r * d32s + p, lo);
     } else if (dst32) {
         dst32[r * d32s + p] = to_f(v);
     }
@@ -305,16 +306,16 @@ static inline dim3 grid2d(int n, dim3 b, int nb) {
 
 template <typename Cin, typename Cout, typename R>
 void launch_apply_A(const Ctx& cx, int nb, const Cin* x, long long xs, Cout* y, long long ys, float2* y32,
-                    long long y32s, BatchSkip sk, float2* y32lo) {
+                    long long y32s, BatchSkip sk, LoDst y32lo) {
     const dim3 b(32, 8);
     k_apply_A<Cin, Cout, R><<<grid2d(cx.op.n, b, nb), b, 0, cx.stream>>>(cx.op, x, xs, y, ys, y32, y32s, y32lo, sk);
 }
 template void launch_apply_A<double2, double2, double>(const Ctx&, int, const double2*, long long, double2*,
-                                                       long long, float2*, long long, BatchSkip, float2*);
+                                                       long long, float2*, long long, BatchSkip, LoDst);
 template void launch_apply_A<float2, double2, double>(const Ctx&, int, const float2*, long long, double2*, long long,
-                                                      float2*, long long, BatchSkip, float2*);
+                                                      float2*, long long, BatchSkip, LoDst);
 
-bool launch_apply_A_df(const Ctx& cx, int nb, const float2* x, long long xs, float2* yh, float2* yl, long long ys,
+bool launch_apply_A_df(const Ctx& cx, int nb, const float2* x, long long xs, float2* yh, LoDst yl, long long ys,
                        BatchSkip sk) {
     const double ch = -cx.op.inv_h2;
     if ((double)(float)ch != ch) return false;                  // coupling not exact in FP32
@@ -364,7 +365,7 @@ HZS_CMB(float2, float2, float)
 #undef HZS_CMB
 
 void launch_mask_copy_c128(const Ctx& cx, int nb, const double2* src, long long ss, double2* dst, long long ds,
-                           int conj, float2* dst32, long long d32s, float2* dst32lo) {
+                           int conj, float2* dst32, long long d32s, LoDst dst32lo) {
     const dim3 b(32, 8);
     k_mask_copy<<<grid2d(cx.op.n, b, nb), b, 0, cx.stream>>>(cx.op, src, ss, dst, ds, conj, dst32, d32s, dst32lo);
 }

@@ -47,6 +47,7 @@ class PrecondDesc(ct.Structure):
 
 SOLVE_PROFILE = 1
 SOLVE_ORTH_FP64 = 2
+SOLVE_BASIS_WIDE = 4
 
 
 class SolveDesc(ct.Structure):
@@ -58,7 +59,7 @@ class SolveInfo(ct.Structure):
                 ("relres_true", ct.c_double), ("t_solve_ms", ct.c_double), ("t_precond_ms", ct.c_double),
                 ("t_matvec_ms", ct.c_double), ("t_orth_ms", ct.c_double), ("t_orth_dot_ms", ct.c_double),
                 ("t_orth_update_ms", ct.c_double), ("launches", ct.c_longlong),
-                ("status", ct.c_int)]
+                ("basis_bits", ct.c_int), ("status", ct.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -145,6 +146,7 @@ class SolveResult:
     t_orth_update_ms: float
     launches: int
     status: int
+    basis_bits: int = 0
 
 
 class Grid:
@@ -217,27 +219,30 @@ class Preconditioner:
         _check(load().hzs_apply_precond(self._h, v.data_ptr(), z.data_ptr(), nrhs), self.grid.handle)
         return z
 
-    def _solve(self, fn, f, tol, maxit, out, profile, orth_fp64=False):
+    def _solve(self, fn, f, tol, maxit, out, profile, orth_fp64=False, wide_basis=False):
         f = _dev_c128(f, self.n, "f")
         u = torch.empty_like(f) if out is None else out
         nrhs = f.numel() // (self.n * self.n)
         infos = (SolveInfo * max(nrhs, 1))()
-        flags = (SOLVE_PROFILE if profile else 0) | (SOLVE_ORTH_FP64 if orth_fp64 else 0)
+        flags = ((SOLVE_PROFILE if profile else 0) | (SOLVE_ORTH_FP64 if orth_fp64 else 0)
+                 | (SOLVE_BASIS_WIDE if wide_basis else 0))
         sd = SolveDesc(float(tol), int(maxit), flags)
         _check(fn(self._h, ct.byref(sd), f.data_ptr(), u.data_ptr(), nrhs, infos), self.grid.handle,
                allow=(OK, NOT_CONVERGED))
         res = [SolveResult(i.iterations, bool(i.converged), i.relres_est, i.relres_true, i.t_solve_ms,
                            i.t_precond_ms, i.t_matvec_ms, i.t_orth_ms, i.t_orth_dot_ms, i.t_orth_update_ms,
-                           i.launches, i.status)
+                           i.launches, i.status, i.basis_bits)
                for i in infos[:nrhs]]
         return u, res
 
     def solve(self, f: torch.Tensor, tol: float = 1e-6, maxit: int = 1000, out=None, profile: bool = False,
-              orth_fp64: bool = False):
+              orth_fp64: bool = False, wide_basis: bool = False):
         """u = A^{-1} f by preconditioned GMRES; returns (u, [SolveResult per right-hand side]).
 
-        orth_fp64: with a MIXED preconditioner, orthogonalise with the all-FP64 CGS2."""
-        return self._solve(load().hzs_solve, f, tol, maxit, out, profile, orth_fp64)
+        orth_fp64: with a MIXED preconditioner, orthogonalise with the all-FP64 CGS2.
+        wide_basis: keep the double-float basis at about 48 bits even for tol >= 1e-7
+        (where it otherwise stores bf16 remainders, about 32 bits)."""
+        return self._solve(load().hzs_solve, f, tol, maxit, out, profile, orth_fp64, wide_basis)
 
     def adjoint_solve(self, g: torch.Tensor, tol: float = 1e-6, maxit: int = 1000, out=None, profile: bool = False):
         """lambda = conj(A)^{-1} g; returns (lambda, results)."""
@@ -262,7 +267,8 @@ class Preconditioner:
             pass
 
 
-def solve_batched(problems, rhs, tol: float = 1e-6, maxit: int = 1000, orth_fp64: bool = False):
+def solve_batched(problems, rhs, tol: float = 1e-6, maxit: int = 1000, orth_fp64: bool = False,
+                  wide_basis: bool = False):
     """Batched solve over several problems: ``problems`` is a list of Preconditioner
     handles (distinct), ``rhs`` a matching list of complex128 tensors of shape
     (nrhs_k, n_k, n_k).  Returns (list of solutions, list of lists of SolveResult)."""
@@ -278,7 +284,8 @@ def solve_batched(problems, rhs, tol: float = 1e-6, maxit: int = 1000, orth_fp64
     total = sum(counts)
     infos = (SolveInfo * max(total, 1))()
     arr = lambda vals: (ct.c_void_p * max(k, 1))(*vals)
-    sd = SolveDesc(float(tol), int(maxit), SOLVE_ORTH_FP64 if orth_fp64 else 0)
+    sd = SolveDesc(float(tol), int(maxit),
+                   (SOLVE_ORTH_FP64 if orth_fp64 else 0) | (SOLVE_BASIS_WIDE if wide_basis else 0))
     st = lib.hzs_solve_batched(k, arr([P.handle.value for P in problems]), ct.byref(sd),
                                arr([f.data_ptr() for f in rhs]), arr([u.data_ptr() for u in outs]),
                                (ct.c_int * max(k, 1))(*counts), infos)
@@ -287,7 +294,7 @@ def solve_batched(problems, rhs, tol: float = 1e-6, maxit: int = 1000, orth_fp64
     for c in counts:
         res.append([SolveResult(i.iterations, bool(i.converged), i.relres_est, i.relres_true, i.t_solve_ms,
                                 i.t_precond_ms, i.t_matvec_ms, i.t_orth_ms, i.t_orth_dot_ms,
-                                i.t_orth_update_ms, i.launches, i.status)
+                                i.t_orth_update_ms, i.launches, i.status, i.basis_bits)
                     for i in infos[pos:pos + c]])
         pos += c
     return outs, res

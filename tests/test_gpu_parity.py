@@ -293,3 +293,49 @@ def test_mixed_edge_cases(hzs):
     g1, P1 = make(hzs, n, DIRICHLET, k=10.0, nsub=1, ov=0, kind=AS1, prec=1)
     u, info = P1.solve(dev(point_source(n)), tol=1e-10, maxit=10)
     assert info[0].converged and info[0].relres_true < 1.01e-10 and info[0].iterations <= 4
+
+
+@pytest.mark.parametrize("case", [SOLVE_CASES[0], SOLVE_CASES[3], SOLVE_CASES[5]],
+                         ids=lambda c: f"{c['bc']}-n{c['n']}")
+def test_narrow_basis_matches_wide(hzs, case):
+    """bf16 basis remainders (about 32 significant bits) give the GMRES run of the
+    complex64 remainders (about 48 bits) at tolerances >= 1e-7: same step count
+    within one, a true residual within tol, and the GMRES estimate within a few
+    1e-9 of the true residual (the Arnoldi relation holds to the basis's 32 bits;
+    a basis of complex64 words alone misses it by ~1e-6).  Alternating the widths
+    on one handle re-zeroes the padding of the remainder layout in use: the second
+    narrow solve repeats the first bit for bit."""
+    c = case
+    prob = Problem(c["n"], c["bc"], c["k"] ** 2)
+    A = prob.assemble_fast()
+    g, P = make(hzs, c["n"], c["bc"], k=c["k"], nsub=c["nsub"], ov=c["ov"], kind=c["kind"], coarse=c["coarse"],
+                p=c["p"], prec=1)
+    f = point_source(c["n"])
+    fv = prob.grid_to_vec(f)
+    u1, i1 = P.solve(dev(f), tol=c["tol"], maxit=400)
+    u2, i2 = P.solve(dev(f), tol=c["tol"], maxit=400, wide_basis=True)
+    u3, i3 = P.solve(dev(f), tol=c["tol"], maxit=400)
+    assert (i1[0].basis_bits, i2[0].basis_bits, i3[0].basis_bits) == (32, 48, 32)
+    assert i1[0].converged and i2[0].converged
+    assert abs(i1[0].iterations - i2[0].iterations) <= 1
+    for u, i in ((u1, i1[0]), (u2, i2[0])):
+        uv = prob.grid_to_vec(u.cpu().numpy())
+        res = np.linalg.norm(fv - A @ uv) / np.linalg.norm(fv)
+        assert res <= c["tol"] * 1.01
+        assert abs(i.relres_est - res) <= 5e-9
+    a = prob.grid_to_vec(u1.cpu().numpy()); b = prob.grid_to_vec(u2.cpu().numpy())
+    assert rel(a, b) < 1e-5
+    assert i3[0].iterations == i1[0].iterations and torch.equal(u1, u3)
+
+
+def test_basis_width_selection(hzs):
+    n = 65
+    g, P = make(hzs, n, SOMMERFELD, k=20.0, nsub=4, ov=2, kind=SHS2, coarse=B2, p=8, prec=1)
+    f = dev(point_source(n))
+    assert P.solve(f, tol=1e-6, maxit=200)[1][0].basis_bits == 32
+    assert P.solve(f, tol=1e-7, maxit=200)[1][0].basis_bits == 32
+    _, info = P.solve(f, tol=1e-9, maxit=200)
+    assert info[0].basis_bits == 48 and info[0].converged and info[0].relres_true <= 1.01e-9
+    assert P.solve(f, tol=1e-6, maxit=200, orth_fp64=True)[1][0].basis_bits == 53
+    g64, P64 = make(hzs, n, SOMMERFELD, k=20.0, nsub=4, ov=2, kind=SHS2, coarse=B2, p=8, prec=0)
+    assert P64.solve(f, tol=1e-6, maxit=200)[1][0].basis_bits == 53

@@ -724,6 +724,8 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
         if (prof) HZS_CUDA(g, cudaEventRecord(pe[3], s));
         launches += pl + 1 + (orth32 ? 5 : 7);
         steps = j + 1;
+        // a launch that could not start (e.g. its resources) must not pass silently
+        HZS_CUDA(g, cudaGetLastError());
         // the host runs one step ahead of the count of running entries it reads back
         HZS_CUDA(g, cudaMemcpyAsync(&p->h_done[j & 1], kb.active, sizeof(int), cudaMemcpyDeviceToHost, s));
         HZS_CUDA(g, cudaEventRecord(p->ev[j & 1], s));
@@ -753,6 +755,7 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
     launch_residual_norm(cx, kb, nb, kb.V, kb.sVd(), p->rtmp, ld, p->dres);
     launches += 3;
     if (conj_io) { launch_mask_copy_c128(cx, nb, u, nn, u, nn, 1, nullptr, 0); launches += 1; }
+    HZS_CUDA(g, cudaGetLastError());
     HZS_CUDA(g, cudaEventRecord(p->t1, s));
     std::vector<KState> hs(nb);
     std::vector<double> rnorm(nb);

@@ -12,18 +12,23 @@
 
 namespace hzs {
 
-// Lets fn launch with `bytes` of dynamic shared memory.  The function's cap is
+// Lets fn launch with `bytes` of dynamic shared memory.  Without an opt-in a
+// block may use 48 KB of static and dynamic shared memory together, so the
+// check counts the function's static shared memory too.  The function's cap is
 // process-wide state shared by every host thread, so it is always raised to the
 // same value (the device's opt-in maximum less the function's static shared
 // memory) rather than to this launch's size: a concurrent caller that needs less
 // can then never lower the cap under a launch that needs more.
 inline cudaError_t allow_dynamic_smem(const void* fn, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    int dev = 0, optin = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    constexpr size_t kDefault = 48 * 1024;
+    if (bytes <= kDefault / 2) return cudaSuccess;      // no kernel here has 24 KB of static shared memory
     cudaFuncAttributes fa{};
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    if (bytes + fa.sharedSizeBytes <= kDefault) return cudaSuccess;
+    int dev = 0, optin = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     const size_t cap = (size_t)optin - fa.sharedSizeBytes;
     if (bytes > cap) return cudaErrorInvalidValue;

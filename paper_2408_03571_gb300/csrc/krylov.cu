@@ -23,7 +23,8 @@ namespace hzs {
 constexpr int kRedThreads = 256;
 constexpr int kDotGroup64 = 4;     // basis vectors per warp pass (FP64 multi-dot)
 constexpr int kDotGroupDC = 4;     // basis vectors per warp pass (delayed CGS2 multi-dot)
-constexpr int kUpdUnroll = 4;      // basis vectors per iteration of the delayed CGS2 update
+constexpr int kUpdUnroll = 4;      // basis vectors per group of the delayed CGS2 update (two groups in flight)
+constexpr int kUpdBlocksPerSM = 2; // resident blocks of the delayed CGS2 update (up to 128 registers a thread)
 
 __device__ __forceinline__ void chunk_of(long long N, long long& e0, long long& e1) {
     const long long per = (N + gridDim.x - 1) / gridDim.x;
@@ -500,12 +501,88 @@ __global__ void __launch_bounds__(kFinThreads) k_dcgs_finish(int j, int maxit, i
     }
 }
 
+// ---- packed FP32 pairs (two lanes in one 64-bit register: add/sub/mul/fma .f32x2,
+// one issue slot for two FP32 operations).  The low half is the first lane: a
+// complex64 entry loaded as 8 bytes is the pair (re, im).
+typedef unsigned long long f2x;
+__device__ __forceinline__ f2x f2_pack(float a, float b) {
+    f2x r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 f2_unpack(f2x r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ f2x add2(f2x a, f2x b) {
+    f2x d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2x sub2(f2x a, f2x b) {
+    f2x d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2x mul2(f2x a, f2x b) {
+    f2x d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c) {
+    f2x d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+// Lane-wise double-float multiply-add (sh, sl) += c * (vh + vl) for a real c = ch + cl
+// given as the broadcast pairs P = (ch, ch), N = (-ch, -ch), NL = (-cl, -cl) (no
+// negation modifier exists for the packed forms).  Same arithmetic as df_fma: the
+// product ch vh is split exactly by an FMA, ch vl and cl vh are added to its error,
+// and the accumulation is a TwoSum.
+__device__ __forceinline__ void df_fma2(f2x& sh, f2x& sl, f2x P, f2x N, f2x NL, f2x vh, f2x vl) {
+    const f2x p = mul2(P, vh);
+    f2x en = fma2(N, vh, p);            // -(ch vh - p), exact
+    en = fma2(N, vl, en);
+    en = fma2(NL, vh, en);              // en = -(error + ch vl + cl vh)
+    const f2x s = add2(sh, p);          // TwoSum(sh, p)
+    const f2x bb = sub2(s, sh);
+    const f2x t = add2(sub2(sh, sub2(s, bb)), sub2(p, bb));
+    sh = s;
+    sl = add2(sl, sub2(t, en));
+}
+__device__ __forceinline__ void df_norm2(f2x& sh, f2x& sl) {
+    const f2x s = add2(sh, sl);
+    sl = sub2(sl, sub2(s, sh));
+    sh = s;
+}
+// Remainder pairs of one entry pair as two packed (re, im) lanes.
+__device__ __forceinline__ void lo_pairs(float4 v, f2x& l0, f2x& l1) {
+    const ulonglong2 u = *reinterpret_cast<const ulonglong2*>(&v);
+    l0 = u.x; l1 = u.y;
+}
+__device__ __forceinline__ void lo_pairs(uint2 v, f2x& l0, f2x& l1) {
+    l0 = f2_pack(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xffff0000u));
+    l1 = f2_pack(__uint_as_float(v.y << 16), __uint_as_float(v.y & 0xffff0000u));
+}
+
+// Coefficients of basis vector i for the update pass, as broadcast packed pairs
+// (see df_fma2): c = h1_i sigma_i in double-float, a = h2_i sigma_i in complex64.
+struct alignas(16) UpdCoef {
+    f2x Pr, Nr, NLr, Pi, Ni, NLi;       // c.re and c.im
+    f2x ar, ai;                         // a.re and a.im
+};
+
 // Update pass of step j (two entries per lane): V_j = u~_j - sum_i (sigma_i alpha_i) V_i
 // (the small reorthogonalisation sum in complex64, its subtraction in double-float),
 // w = w - sum_i (sigma_i b_i) V_i - (h_jj sigma_j) V_j in double-float;
 // npart[b] = sum_e |w[e]|^2 (FP32 on the leading words: it only sets a scale).
+// The sums over the basis run on packed FP32 pairs, one entry's (re, im) per
+// register: sum_i c_i v_i = sum_i Re(c_i) v_i + i sum_i Im(c_i) v_i, so each entry
+// keeps the two real-coefficient sums A = sum Re(c) v and B = sum Im(c) v (and the
+// same for the reorthogonalisation) and forms A + i B once at the end.
 template <typename L>
-__global__ void __launch_bounds__(kRedThreads, 3) k_dcgs_update(int j, long long Np, long long ldp,
+__global__ void __launch_bounds__(kRedThreads, kUpdBlocksPerSM) k_dcgs_update(int j, long long Np, long long ldp,
                                                              float4* __restrict__ V32, L* __restrict__ V32lo,
                                                              long long sVp, const double* __restrict__ sigma,
                                                              const double2* __restrict__ h1,
@@ -519,56 +596,102 @@ __global__ void __launch_bounds__(kRedThreads, 3) k_dcgs_update(int j, long long
     L* ul = V32lo + (size_t)j * ldp;
     float4* wh = V32 + (size_t)(j + 1) * ldp;
     L* wl = V32lo + (size_t)(j + 1) * ldp;
-    extern __shared__ float4 dsm[];
-    float4* cb = dsm;                                       // j + 1: w coefficients (double-float)
-    float2* ca = reinterpret_cast<float2*>(dsm + (j + 1));  // j: reorthogonalisation coefficients
+    extern __shared__ UpdCoef ucs[];                        // j entries
+    __shared__ float4 s_cj;                                 // h_jj sigma_j (double-float)
     for (int i = threadIdx.x; i <= j; i += blockDim.x) {
         const double2 c = cscale(h1[i], sigma[i]);
-        float4 q;
-        split_d(c.x, q.x, q.y);
-        split_d(c.y, q.z, q.w);
-        cb[i] = q;
-        if (i < j) ca[i] = to_f(cscale(h2[i], sigma[i]));
+        float crh, crl, cih, cil;
+        split_d(c.x, crh, crl);
+        split_d(c.y, cih, cil);
+        if (i == j) { s_cj = make_float4(crh, crl, cih, cil); continue; }
+        const float2 a = to_f(cscale(h2[i], sigma[i]));
+        UpdCoef u;
+        u.Pr = f2_pack(crh, crh); u.Nr = f2_pack(-crh, -crh); u.NLr = f2_pack(-crl, -crl);
+        u.Pi = f2_pack(cih, cih); u.Ni = f2_pack(-cih, -cih); u.NLi = f2_pack(-cil, -cil);
+        u.ar = f2_pack(a.x, a.x); u.ai = f2_pack(a.y, a.y);
+        ucs[i] = u;
     }
     __syncthreads();
+    const float4 cj = s_cj;
     long long e0, e1;
     chunk_of(Np, e0, e1);
     float nrmf = 0.f;
     for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        float a0h = 0.f, a0l = 0.f, b0h = 0.f, b0l = 0.f, a1h = 0.f, a1l = 0.f, b1h = 0.f, b1l = 0.f;
-        float2 s0 = make_float2(0.f, 0.f), s1 = s0;
-        const float4* ph = V32 + e;
+        // per entry k of the pair: A_k, B_k (double-float) and S_k, T_k (reorthogonalisation)
+        f2x A0h = 0, A0l = 0, B0h = 0, B0l = 0, A1h = 0, A1l = 0, B1h = 0, B1l = 0;
+        f2x S0 = 0, T0 = 0, S1 = 0, T1 = 0;
+        const ulonglong2* ph = reinterpret_cast<const ulonglong2*>(V32 + e);
         const L* pl = V32lo + e;
         // basis vectors in the order j-1 .. 0: the dot pass read 0 .. j-1, so the vectors
         // still in L2 come first, and this pass leaves vectors 0, 1, .. in L2 for the next
         // dot pass
         auto vi = [&](int k) { return j - 1 - k; };
+        auto step = [&](const UpdCoef& u, ulonglong2 vh, L vlr) {
+            f2x l0, l1;
+            lo_pairs(vlr, l0, l1);
+            df_fma2(A0h, A0l, u.Pr, u.Nr, u.NLr, vh.x, l0);
+            df_fma2(B0h, B0l, u.Pi, u.Ni, u.NLi, vh.x, l0);
+            df_fma2(A1h, A1l, u.Pr, u.Nr, u.NLr, vh.y, l1);
+            df_fma2(B1h, B1l, u.Pi, u.Ni, u.NLi, vh.y, l1);
+            S0 = fma2(u.ar, vh.x, S0); T0 = fma2(u.ai, vh.x, T0);
+            S1 = fma2(u.ar, vh.y, S1); T1 = fma2(u.ai, vh.y, T1);
+        };
+        // two groups of kUpdUnroll vectors in registers: the loads of the next group are
+        // issued before the current group is consumed (the work on one group covers less
+        // time than a DRAM round trip)
+        ulonglong2 ha[kUpdUnroll], hb[kUpdUnroll];
+        L la[kUpdUnroll], lb[kUpdUnroll];
         int i = 0;
-        for (; i + kUpdUnroll <= j; i += kUpdUnroll) {     // kUpdUnroll basis vectors: all loads first
-            float4 vh[kUpdUnroll], vl[kUpdUnroll];
+        if (kUpdUnroll <= j) {
 #pragma unroll
             for (int t = 0; t < kUpdUnroll; ++t) {
-                vh[t] = ph[(size_t)vi(i + t) * ldp];
-                vl[t] = lo_unpack(pl[(size_t)vi(i + t) * ldp]);
+                ha[t] = ph[(size_t)vi(t) * ldp];
+                la[t] = pl[(size_t)vi(t) * ldp];
             }
+        }
+        // invariant: ha, la hold group i whenever i + kUpdUnroll <= j
+        for (; i + 2 * kUpdUnroll <= j; i += 2 * kUpdUnroll) {
 #pragma unroll
             for (int t = 0; t < kUpdUnroll; ++t) {
-                const float4 q = cb[vi(i + t)];
-                df_cmac(a0h, a0l, b0h, b0l, q, vh[t].x, vl[t].x, vh[t].y, vl[t].y);
-                df_cmac(a1h, a1l, b1h, b1l, q, vh[t].z, vl[t].z, vh[t].w, vl[t].w);
-                s0 = cfma(ca[vi(i + t)], lo2(vh[t]), s0);
-                s1 = cfma(ca[vi(i + t)], hi2(vh[t]), s1);
+                hb[t] = ph[(size_t)vi(i + kUpdUnroll + t) * ldp];
+                lb[t] = pl[(size_t)vi(i + kUpdUnroll + t) * ldp];
             }
-            df_norm(a0h, a0l); df_norm(b0h, b0l); df_norm(a1h, a1l); df_norm(b1h, b1l);
+#pragma unroll
+            for (int t = 0; t < kUpdUnroll; ++t) step(ucs[vi(i + t)], ha[t], la[t]);
+            df_norm2(A0h, A0l); df_norm2(B0h, B0l); df_norm2(A1h, A1l); df_norm2(B1h, B1l);
+            if (i + 3 * kUpdUnroll <= j) {
+#pragma unroll
+                for (int t = 0; t < kUpdUnroll; ++t) {
+                    ha[t] = ph[(size_t)vi(i + 2 * kUpdUnroll + t) * ldp];
+                    la[t] = pl[(size_t)vi(i + 2 * kUpdUnroll + t) * ldp];
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < kUpdUnroll; ++t) step(ucs[vi(i + kUpdUnroll + t)], hb[t], lb[t]);
+            df_norm2(A0h, A0l); df_norm2(B0h, B0l); df_norm2(A1h, A1l); df_norm2(B1h, B1l);
         }
-        for (; i < j; ++i) {
-            const float4 vh = ph[(size_t)vi(i) * ldp], vl = lo_unpack(pl[(size_t)vi(i) * ldp]);
-            const float4 q = cb[vi(i)];
-            df_cmac(a0h, a0l, b0h, b0l, q, vh.x, vl.x, vh.y, vl.y);
-            df_cmac(a1h, a1l, b1h, b1l, q, vh.z, vl.z, vh.w, vl.w);
-            s0 = cfma(ca[vi(i)], lo2(vh), s0);
-            s1 = cfma(ca[vi(i)], hi2(vh), s1);
+        if (i + kUpdUnroll <= j) {
+#pragma unroll
+            for (int t = 0; t < kUpdUnroll; ++t) step(ucs[vi(i + t)], ha[t], la[t]);
+            df_norm2(A0h, A0l); df_norm2(B0h, B0l); df_norm2(A1h, A1l); df_norm2(B1h, B1l);
+            i += kUpdUnroll;
         }
+        for (; i < j; ++i) step(ucs[vi(i)], ph[(size_t)vi(i) * ldp], pl[(size_t)vi(i) * ldp]);
+        // sum_i c_i v_i = A + i B per entry: re = A.re - B.im, im = A.im + B.re
+        float a0h, a0l, b0h, b0l, a1h, a1l, b1h, b1l;
+        {
+            const float2 ah = f2_unpack(A0h), al = f2_unpack(A0l), bh = f2_unpack(B0h), bl = f2_unpack(B0l);
+            a0h = ah.x; a0l = al.x; df_add(a0h, a0l, -bh.y, -bl.y);
+            b0h = ah.y; b0l = al.y; df_add(b0h, b0l, bh.x, bl.x);
+        }
+        {
+            const float2 ah = f2_unpack(A1h), al = f2_unpack(A1l), bh = f2_unpack(B1h), bl = f2_unpack(B1l);
+            a1h = ah.x; a1l = al.x; df_add(a1h, a1l, -bh.y, -bl.y);
+            b1h = ah.y; b1l = al.y; df_add(b1h, b1l, bh.x, bl.x);
+        }
+        const float2 sa0 = f2_unpack(S0), ta0 = f2_unpack(T0), sa1 = f2_unpack(S1), ta1 = f2_unpack(T1);
+        const float2 s0 = make_float2(sa0.x - ta0.y, sa0.y + ta0.x);
+        const float2 s1 = make_float2(sa1.x - ta1.y, sa1.y + ta1.x);
         // V_j = u~ - s
         float4 xh = uh[e], xl = lo_unpack(ul[e]);
         df_add(xh.x, xl.x, -s0.x, 0.f); df_norm(xh.x, xl.x);
@@ -578,9 +701,8 @@ __global__ void __launch_bounds__(kRedThreads, 3) k_dcgs_update(int j, long long
         uh[e] = xh;
         lo_store(ul + e, xl);
         // + (h_jj sigma_j) V_j
-        const float4 qj = cb[j];
-        df_cmac(a0h, a0l, b0h, b0l, qj, xh.x, xl.x, xh.y, xl.y);
-        df_cmac(a1h, a1l, b1h, b1l, qj, xh.z, xl.z, xh.w, xl.w);
+        df_cmac(a0h, a0l, b0h, b0l, cj, xh.x, xl.x, xh.y, xl.y);
+        df_cmac(a1h, a1l, b1h, b1l, cj, xh.z, xl.z, xh.w, xl.w);
         float4 yh = wh[e], yl = lo_unpack(wl[e]);
         df_add(yh.x, yl.x, -a0h, -a0l); df_norm(yh.x, yl.x);
         df_add(yh.y, yl.y, -b0h, -b0l); df_norm(yh.y, yl.y);
@@ -595,14 +717,15 @@ __global__ void __launch_bounds__(kRedThreads, 3) k_dcgs_update(int j, long long
     block_norm_part(nrm, npart + (size_t)r * nblk);
 }
 
-// sigt[j+1] = 1 / |u~_{j+1}| from the update pass's partial norms (one warp per entry).
-__global__ void k_dcgs_scale(int j, int nblk, const double* __restrict__ npart, double* __restrict__ sigt,
-                             long long sS, const KState* __restrict__ st) {
+// sigt[j+1] = 1 / |u~_{j+1}| from the update pass's partial norms (one warp per entry;
+// count partials per entry, stride apart).
+__global__ void k_dcgs_scale(int j, int count, int stride, const double* __restrict__ npart,
+                             double* __restrict__ sigt, long long sS, const KState* __restrict__ st) {
     const int r = blockIdx.x;
     if (st[r].done) return;
-    npart += (size_t)r * nblk;
+    npart += (size_t)r * stride;
     double s = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += 32) s += npart[b];
+    for (int b = threadIdx.x; b < count; b += 32) s += npart[b];
     s = warp_sum_d(s);
     if (threadIdx.x == 0) sigt[r * sS + j + 1] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
 }
@@ -859,21 +982,23 @@ void launch_dcgs2_step(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int l
                                                                         kb.h1, kb.h2, kb.H, kb.sH(), kb.cs, kb.sn,
                                                                         kb.g, kb.sigma, kb.sS(), kb.st, kb.active);
     if (last_only) return;
-    const size_t us = (size_t)(j + 1) * sizeof(float4) + (size_t)j * sizeof(float2);
+    const size_t us = (size_t)(j > 0 ? j : 1) * sizeof(UpdCoef);
+    const int nupd = kUpdBlocksPerSM * cx.num_sms;           // <= kb.nblk, the partials' stride
+    const dim3 gu(nupd, nb);
     if (ev) cudaEventRecord(ev[2], cx.stream);
     if (kb.lo16) {
         set_coef_smem_limit((const void*)k_dcgs_update<uint2>, us);
-        k_dcgs_update<uint2><<<gr, kRedThreads, us, cx.stream>>>(j, Np, ldp, V32, static_cast<uint2*>(kb.V32lo), sVp,
+        k_dcgs_update<uint2><<<gu, kRedThreads, us, cx.stream>>>(j, Np, ldp, V32, static_cast<uint2*>(kb.V32lo), sVp,
                                                                  kb.sigma, kb.h1, kb.h2, kb.sS(), kb.npart, kb.nblk,
                                                                  kb.st);
     } else {
         set_coef_smem_limit((const void*)k_dcgs_update<float4>, us);
-        k_dcgs_update<float4><<<gr, kRedThreads, us, cx.stream>>>(j, Np, ldp, V32, static_cast<float4*>(kb.V32lo),
+        k_dcgs_update<float4><<<gu, kRedThreads, us, cx.stream>>>(j, Np, ldp, V32, static_cast<float4*>(kb.V32lo),
                                                                   sVp, kb.sigma, kb.h1, kb.h2, kb.sS(), kb.npart,
                                                                   kb.nblk, kb.st);
     }
     if (ev) cudaEventRecord(ev[3], cx.stream);
-    k_dcgs_scale<<<nb, 32, 0, cx.stream>>>(j, kb.nblk, kb.npart, kb.sigt, kb.sS(), kb.st);
+    k_dcgs_scale<<<nb, 32, 0, cx.stream>>>(j, nupd, kb.nblk, kb.npart, kb.sigt, kb.sS(), kb.st);
 }
 
 void launch_lsq_solve(const Ctx& cx, const KrylovBufs& kb, int nb) {

@@ -339,3 +339,19 @@ def test_basis_width_selection(hzs):
     assert P.solve(f, tol=1e-6, maxit=200, orth_fp64=True)[1][0].basis_bits == 53
     g64, P64 = make(hzs, n, SOMMERFELD, k=20.0, nsub=4, ov=2, kind=SHS2, coarse=B2, p=8, prec=0)
     assert P64.solve(f, tol=1e-6, maxit=200)[1][0].basis_bits == 53
+
+
+def test_long_run_estimate_matches_true_residual(hzs):
+    """A solve past 766 Arnoldi steps: the update pass then needs more than 48 KB of
+    shared memory for its coefficients (with its static shared memory), which must be
+    granted by the opt-in; a launch that fails there would leave the GMRES estimate
+    describing vectors that were never formed.  MP-2, k = 100, n = 513, 64-node
+    subdomains, SHS2 with B2 at H = 32h, one right-hand side: ~770 steps."""
+    from paper_2408_03571_gb300.inputs import random_source_nodes
+    n, k = 513, 100.0
+    g, P = make(hzs, n, SOMMERFELD, k=k, nsub=(n - 1) // 64, ov=2, kind=SHS2, coarse=B2, p=32, prec=1)
+    f = point_source(n, random_source_nodes(n, 1, 1002)[0])
+    u, info = P.solve(dev(f), tol=1e-6, maxit=1000)
+    assert info[0].converged and info[0].iterations > 766
+    assert info[0].relres_true <= 1.01e-6
+    assert abs(info[0].relres_est - info[0].relres_true) <= 1e-8

@@ -461,8 +461,9 @@ def gpu_arm(args, world, rank, local):
     # n=513, the launches of step 200), as a ratio to the algorithmic bytes of that
     # launch; traffic grows with the units processed, so the average launch here is
     # scaled by those ratios.  None: no capture of the current kernel.
-    traffic_ratio = {16: {"dot": None, "upd": (1.059, "902.2 MB against 852.3 MB")},
-                     12: {"dot": None, "upd": None}}[eb]
+    dot_ratio = (1.021, "430.9 MB against 421.9 MB")
+    traffic_ratio = {16: {"dot": dot_ratio, "upd": None},
+                     12: {"dot": dot_ratio, "upd": (1.056, "675.3 MB against 639.2 MB")}}[eb]
     for r_, nbytes, nl, key in ((r_dot, dot_bytes, it + 1, "dot"), (r_upd, upd_bytes, it, "upd")):
         r_["launches"] = nl
         r_["bytes_per_launch"] = nbytes / nl

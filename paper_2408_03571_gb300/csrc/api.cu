@@ -234,6 +234,9 @@ static void free_krylov(hzs_precond* p) {
     cudaFree(kb.V); cudaFree(kb.V32); cudaFree(kb.V32lo); cudaFree(kb.sigma); cudaFree(kb.H); cudaFree(kb.cs); cudaFree(kb.sn); cudaFree(kb.g);
     cudaFree(kb.y); cudaFree(kb.h1); cudaFree(kb.h2); cudaFree(kb.hn); cudaFree(kb.sigt); cudaFree(kb.part); cudaFree(kb.npart); cudaFree(kb.st);
     cudaFree(kb.active);
+    if (kb.side) cudaStreamDestroy(kb.side);
+    if (kb.ev_c) cudaEventDestroy(kb.ev_c);
+    if (kb.ev_g) cudaEventDestroy(kb.ev_g);
     cudaFree(p->Z); cudaFree(p->ztmp); cudaFree(p->rtmp); cudaFree(p->dres);
     kb = KrylovBufs{};
     p->Z = nullptr;
@@ -600,6 +603,17 @@ static hzs_status ensure_krylov(hzs_precond* p, int maxit, int nb, bool full_v) 
     HZS_CUDA(g, dalloc(&kb.npart, (size_t)nb * kb.nblk));
     HZS_CUDA(g, dalloc(&kb.st, (size_t)nb));
     HZS_CUDA(g, dalloc(&kb.active, 1));
+    // side stream for the Givens rotation of a delayed-CGS2 step (without it, the
+    // rotation runs on the solve stream)
+    if (cudaStreamCreateWithFlags(&kb.side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&kb.ev_c, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&kb.ev_g, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        if (kb.side) cudaStreamDestroy(kb.side);
+        if (kb.ev_c) cudaEventDestroy(kb.ev_c);
+        if (kb.ev_g) cudaEventDestroy(kb.ev_g);
+        kb.side = nullptr; kb.ev_c = kb.ev_g = nullptr;
+    }
     if (p->desc.precision == HZS_MIXED) {
         HZS_CUDA(g, dalloc(&kb.V32, (size_t)nb * kb.sV()));
         float2* lo = nullptr;
@@ -722,7 +736,7 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
         if (orth32) launch_dcgs2_step(cx, kb, nb, j, 0, prof ? pe + 4 : nullptr);
         else launch_arnoldi_step(cx, kb, nb, j);
         if (prof) HZS_CUDA(g, cudaEventRecord(pe[3], s));
-        launches += pl + 1 + (orth32 ? 5 : 7);
+        launches += pl + 1 + (orth32 ? (j > 0 ? 6 : 5) : 7);
         steps = j + 1;
         // a launch that could not start (e.g. its resources) must not pass silently
         HZS_CUDA(g, cudaGetLastError());
@@ -737,7 +751,7 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
     // delayed CGS2: the last column is completed by one more dot pass over the basis
     if (orth32 && steps == sd->maxit) {
         launch_dcgs2_step(cx, kb, nb, sd->maxit, 1);
-        launches += 3;
+        launches += 4;
     }
     launch_lsq_solve(cx, kb, nb);
     launches += 1;

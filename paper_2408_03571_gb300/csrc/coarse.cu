@@ -166,14 +166,21 @@ __global__ void k_split_df(long long N, const double2* __restrict__ a, float4* _
 
 // outf = Ainv * c rounded to complex64, the products and sums in double-float
 // arithmetic on the FP32 pipes (same accuracy class as the FP64 product before
-// the final rounding).  One warp per row; c staged in shared memory as pairs.
-__global__ void k_coarse_matvec_df(int Nc, const float4* __restrict__ Adf, const double2* __restrict__ c,
-                                   float2* __restrict__ outf, BatchSkip sk) {
+// the final rounding).  kCmvWarpsPerRow warps share a row (the matrix, 16 B per
+// entry, is re-read from DRAM every apply: the basis passes evict it from L2, so
+// each lane keeps kCmvLoads loads in flight); c staged in shared memory as pairs.
+constexpr int kCmvWarpsPerRow = 4;
+constexpr int kCmvLoads = 8;
+constexpr int kCmvThreads = 512;
+__global__ void __launch_bounds__(kCmvThreads) k_coarse_matvec_df(int Nc, const float4* __restrict__ Adf,
+                                                                  const double2* __restrict__ c,
+                                                                  float2* __restrict__ outf, BatchSkip sk) {
     const int r = blockIdx.y;
     if (sk.flag && sk.flag[(size_t)r * sk.stride]) return;
     c += (size_t)r * Nc;
     outf += (size_t)r * Nc;
     extern __shared__ float4 cdf[];
+    __shared__ float4 part[kCmvThreads / 32];
     for (int k = threadIdx.x; k < Nc; k += blockDim.x) {
         const double2 v = c[k];
         float4 q;
@@ -182,45 +189,52 @@ __global__ void k_coarse_matvec_df(int Nc, const float4* __restrict__ Adf, const
         cdf[k] = q;
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int wpb = blockDim.x >> 5;
-    for (int row = blockIdx.x * wpb + (threadIdx.x >> 5); row < Nc; row += gridDim.x * wpb) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sub = warp % kCmvWarpsPerRow;                 // this warp's share of the row
+    const int rows_per_block = (kCmvThreads / 32) / kCmvWarpsPerRow;
+    const int row = blockIdx.x * rows_per_block + warp / kCmvWarpsPerRow;
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    if (row < Nc) {
         const float4* arow = Adf + (size_t)row * Nc;
-        // four independent accumulator sets (columns k = lane + 32 (4 m + s)) keep four
-        // loads and four dependent double-float chains in flight per lane
-        float rh[4] = {0.f, 0.f, 0.f, 0.f}, rl[4] = {0.f, 0.f, 0.f, 0.f};
-        float ih[4] = {0.f, 0.f, 0.f, 0.f}, il[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int k0 = 0; k0 < Nc; k0 += 128) {
+        constexpr int span = 32 * kCmvWarpsPerRow * kCmvLoads;   // columns per round of the row's warps
+        for (int k0 = 0; k0 < Nc; k0 += span) {
+            float4 a[kCmvLoads];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int k = k0 + 32 * q + lane;
-                if (k < Nc) {
-                    const float4 a = arow[k], v = cdf[k];
-                    df_fma(rh[q], rl[q], a.x, a.y, v.x, v.y);
-                    df_fma(rh[q], rl[q], -a.z, -a.w, v.z, v.w);
-                    df_fma(ih[q], il[q], a.x, a.y, v.z, v.w);
-                    df_fma(ih[q], il[q], a.z, a.w, v.x, v.y);
-                }
+            for (int q = 0; q < kCmvLoads; ++q) {
+                const int k = k0 + 32 * (sub + kCmvWarpsPerRow * q) + lane;
+                a[q] = k < Nc ? arow[k] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            if ((k0 & 1023) == 896) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) { df_norm(rh[q], rl[q]); df_norm(ih[q], il[q]); }
+            for (int q = 0; q < kCmvLoads; ++q) {
+                const int k = k0 + 32 * (sub + kCmvWarpsPerRow * q) + lane;
+                const float4 v = k < Nc ? cdf[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+                df_fma(rh, rl, a[q].x, a[q].y, v.x, v.y);
+                df_fma(rh, rl, -a[q].z, -a[q].w, v.z, v.w);
+                df_fma(ih, il, a[q].x, a[q].y, v.z, v.w);
+                df_fma(ih, il, a[q].z, a[q].w, v.x, v.y);
             }
+            df_norm(rh, rl);
+            df_norm(ih, il);
         }
-        for (int q = 1; q < 4; ++q) { df_add(rh[0], rl[0], rh[q], rl[q]); df_add(ih[0], il[0], ih[q], il[q]); }
-        float rh0 = rh[0], rl0 = rl[0], ih0 = ih[0], il0 = il[0];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const float orh = __shfl_down_sync(0xffffffffu, rh0, o), orl = __shfl_down_sync(0xffffffffu, rl0, o);
-            const float oih = __shfl_down_sync(0xffffffffu, ih0, o), oil = __shfl_down_sync(0xffffffffu, il0, o);
-            df_add(rh0, rl0, orh, orl);
-            df_add(ih0, il0, oih, oil);
+            const float orh = __shfl_down_sync(0xffffffffu, rh, o), orl = __shfl_down_sync(0xffffffffu, rl, o);
+            const float oih = __shfl_down_sync(0xffffffffu, ih, o), oil = __shfl_down_sync(0xffffffffu, il, o);
+            df_add(rh, rl, orh, orl);
+            df_add(ih, il, oih, oil);
         }
-        if (lane == 0) {
-            df_norm(rh0, rl0);
-            df_norm(ih0, il0);
-            outf[row] = make_float2(rh0, ih0);
+        if (lane == 0) part[warp] = make_float4(rh, rl, ih, il);
+    }
+    __syncthreads();
+    if (row < Nc && sub == 0 && lane == 0) {
+        for (int t = 1; t < kCmvWarpsPerRow; ++t) {         // fixed order: deterministic
+            const float4 o = part[warp + t];
+            df_add(rh, rl, o.x, o.y);
+            df_add(ih, il, o.z, o.w);
         }
+        df_norm(rh, rl);
+        df_norm(ih, il);
+        outf[row] = make_float2(rh, ih);
     }
 }
 
@@ -387,10 +401,9 @@ void launch_split_df(const Ctx& cx, long long N, const double2* a, float4* b) {
 
 void launch_coarse_matvec_df(const Ctx& cx, int nb, const float4* Adf, int Nc, const double2* c, float2* outf,
                              BatchSkip sk) {
-    const int threads = 256;
-    const int rows_per_block = threads / 32;
-    int blocks = (Nc + rows_per_block - 1) / rows_per_block;
-    if (blocks > 4 * cx.num_sms) blocks = 4 * cx.num_sms;
+    const int threads = kCmvThreads;
+    const int rows_per_block = (kCmvThreads / 32) / kCmvWarpsPerRow;
+    const int blocks = (Nc + rows_per_block - 1) / rows_per_block;   // one row per warp group, no grid stride
     const size_t smem = (size_t)Nc * sizeof(float4);
     allow_dynamic_smem((const void*)k_coarse_matvec_df, smem);
     k_coarse_matvec_df<<<dim3(blocks, nb), threads, smem, cx.stream>>>(Nc, Adf, c, outf, sk);

@@ -194,6 +194,9 @@ struct KrylovBufs {
     double* npart;     // nblk
     KState* st;        // 1
     int* active;       // one counter per batch: entries not yet done
+    cudaStream_t side; // runs the Givens rotation of a delayed-CGS2 step beside its update pass (or null)
+    cudaEvent_t ev_c;  // coefficients of the step ready (recorded on the solve stream)
+    cudaEvent_t ev_g;  // Givens rotation of the step done (recorded on side)
     long long sV() const { return (long long)(maxit + 1) * ld; }
     long long sVd() const { return vfull ? sV() : ld; }   // per-entry stride of V
     long long sH() const { return (long long)(maxit + 1) * maxit; }
@@ -212,7 +215,8 @@ struct KrylovBufs {
 void launch_norm_init(const Ctx& cx, const KrylovBufs& kb, int nb, double tol);
 void launch_arnoldi_step(const Ctx& cx, const KrylovBufs& kb, int nb, int j);
 // Step j of the delayed CGS2 Arnoldi on the double-float basis (V32 + V32lo, lo16 selects
-// the remainder width);
+// the remainder width; the rotation of column j-1 runs on kb.side beside the update pass,
+// and the solve stream waits for it before the step ends);
 // last_only (j == maxit) completes the last Hessenberg column only.  ev (optional,
 // 4 events) is recorded before and after the dot pass and the update pass.
 void launch_dcgs2_step(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int last_only, cudaEvent_t* ev = nullptr);

@@ -430,28 +430,23 @@ __global__ void k_dcgs_reduce(int j, int nblk, int ps, int S, const double2* __r
     }
 }
 
-// Step j's scalar work for entry r = blockIdx.x (kFinThreads threads): beta_j,
-// completion and rotation of column j-1 (convergence check with j columns), and
-// the first-pass coefficients of column j (h1, for the update pass and the next
-// completion).  j == maxit (last_only) completes the last column only.
-__global__ void __launch_bounds__(kFinThreads) k_dcgs_finish(int j, int maxit, int last_only,
-                                                            const double2* __restrict__ hn, long long sN,
-                                                            double2* __restrict__ h1, const double2* __restrict__ h2,
-                                                            double2* __restrict__ H, long long sH,
-                                                            double* __restrict__ cs, double2* __restrict__ sn,
-                                                            double2* __restrict__ g, double* __restrict__ sigma,
-                                                            long long sS, KState* __restrict__ st,
-                                                            int* __restrict__ active) {
+// Step j's coefficients for entry r = blockIdx.x (kFinThreads threads): beta_j,
+// column j-1 of H before rotation (h1 + alpha over beta_j; NaN in place of beta_j
+// when beta_j^2 is not finite), and the first-pass coefficients of column j (h1,
+// for the update pass and the next completion) with sigma_j = 1 / beta_j.
+// j == maxit (last_only) writes the last column only.  The rotation of the column
+// and the stop test (k_dcgs_givens) are left off the path to the update pass.
+__global__ void __launch_bounds__(kFinThreads) k_dcgs_coef(int j, int maxit, int last_only,
+                                                          const double2* __restrict__ hn, long long sN,
+                                                          double2* __restrict__ h1, const double2* __restrict__ h2,
+                                                          double2* __restrict__ H, long long sH,
+                                                          double* __restrict__ sigma, long long sS,
+                                                          KState* __restrict__ st, int* __restrict__ active) {
     const int r = blockIdx.x;
     if (st[r].done) return;
-    hn += r * sN; h1 += r * sS; h2 += r * sS; H += r * sH; cs += r * sS; sn += r * sS; g += r * sS; sigma += r * sS;
+    hn += r * sN; h1 += r * sS; h2 += r * sS; H += r * sH; sigma += r * sS;
     KState* s0 = st + r;
-    extern __shared__ double2 fsm[];
     __shared__ double red[2 * kFinWarps];
-    __shared__ int s_fin;
-    double2* col = fsm;                                   // j + 1
-    double2* ssn = col + (j + 1);                         // j - 1
-    double* scs = reinterpret_cast<double*>(ssn + (j > 0 ? j - 1 : 0));
     const int tid = threadIdx.x;
     // |alpha|^2 and alpha^H b
     double aa = 0.0;
@@ -468,27 +463,10 @@ __global__ void __launch_bounds__(kFinThreads) k_dcgs_finish(int j, int maxit, i
     const double b2 = c - aa;
     const double beta = b2 > 0.0 ? sqrt(b2) : 0.0;
     if (j > 0) {
-        for (int i = tid; i < j; i += kFinThreads) col[i] = cadd(h1[i], h2[i]);
-        for (int i = tid; i < j - 1; i += kFinThreads) { ssn[i] = sn[i]; scs[i] = cs[i]; }
-        if (tid == 0) col[j] = make_double2(beta, 0.0);
-        __syncthreads();
-        const double resid = givens_column(j - 1, col, scs, ssn, cs, sn, g);
-        if (tid == 0) {
-            s0->resid = resid;
-            s0->hnext = beta;
-            s0->iters = j;
-            int fin = 1;
-            if (!isfinite(resid) || !isfinite(b2)) s0->nonfinite = 1;
-            else if (resid <= s0->tolabs) s0->conv = 1;
-            else if (beta == 0.0) { s0->breakdown = 1; s0->conv = 1; }
-            else if (!last_only && j < maxit) fin = 0;
-            if (fin) { s0->done = 1; atomicSub(active, 1); }
-            s_fin = fin;
-        }
-        __syncthreads();
         double2* out = H + (size_t)(j - 1) * (maxit + 1);
-        for (int i = tid; i <= j; i += kFinThreads) out[i] = col[i];
-        if (s_fin) return;
+        for (int i = tid; i < j; i += kFinThreads) out[i] = cadd(h1[i], h2[i]);
+        if (tid == 0) out[j] = make_double2(isfinite(b2) ? beta : nan(""), 0.0);
+        __syncthreads();                     // the old h1 is read before it is overwritten below
     }
     if (last_only) return;
     // column j, first pass (alpha is complete for the old vectors; q_j = (u~ - Q alpha) / beta)
@@ -499,6 +477,43 @@ __global__ void __launch_bounds__(kFinThreads) k_dcgs_finish(int j, int maxit, i
         sigma[j] = ib;
         if (j == 0 && !(beta > 0.0)) { s0->done = 1; s0->conv = 1; s0->breakdown = 1; atomicSub(active, 1); }
     }
+}
+
+// Step j >= 1, entry r = blockIdx.x (kFinThreads threads): rotation of column j-1
+// of H (from k_dcgs_coef), residual estimate with j columns and the stop test.
+// Runs beside the update pass of the same step; the next step waits for it.
+__global__ void __launch_bounds__(kFinThreads) k_dcgs_givens(int j, int maxit, int last_only,
+                                                            double2* __restrict__ H, long long sH,
+                                                            double* __restrict__ cs, double2* __restrict__ sn,
+                                                            double2* __restrict__ g, long long sS,
+                                                            KState* __restrict__ st, int* __restrict__ active) {
+    const int r = blockIdx.x;
+    if (st[r].done) return;
+    H += r * sH; cs += r * sS; sn += r * sS; g += r * sS;
+    KState* s0 = st + r;
+    extern __shared__ double2 fsm[];
+    double2* col = fsm;                                   // j + 1
+    double2* ssn = col + (j + 1);                         // j - 1
+    double* scs = reinterpret_cast<double*>(ssn + (j > 0 ? j - 1 : 0));
+    const int tid = threadIdx.x;
+    double2* out = H + (size_t)(j - 1) * (maxit + 1);
+    for (int i = tid; i <= j; i += kFinThreads) col[i] = out[i];
+    for (int i = tid; i < j - 1; i += kFinThreads) { ssn[i] = sn[i]; scs[i] = cs[i]; }
+    __syncthreads();
+    const double beta = col[j].x;
+    const double resid = givens_column(j - 1, col, scs, ssn, cs, sn, g);
+    if (tid == 0) {
+        s0->resid = resid;
+        s0->hnext = beta;
+        s0->iters = j;
+        int fin = 1;
+        if (!isfinite(resid) || !isfinite(beta)) s0->nonfinite = 1;
+        else if (resid <= s0->tolabs) s0->conv = 1;
+        else if (beta == 0.0) { s0->breakdown = 1; s0->conv = 1; }
+        else if (!last_only && j < maxit) fin = 0;
+        if (fin) { s0->done = 1; atomicSub(active, 1); }
+    }
+    for (int i = tid; i <= j; i += kFinThreads) out[i] = col[i];
 }
 
 // ---- packed FP32 pairs (two lanes in one 64-bit register: add/sub/mul/fma .f32x2,
@@ -958,9 +973,9 @@ void launch_arnoldi_step(const Ctx& cx, const KrylovBufs& kb, int nb, int j) {
 // hold far below any GMRES tolerance used here; narrow (bf16) remainders give it
 // about 32 bits and move 12 instead of 16 bytes an entry, the caller's choice
 // for loose tolerances.
-static size_t dcgs_finish_smem(int j) {
+static size_t dcgs_givens_smem(int j) {
     const size_t b = (size_t)(j + 1) * sizeof(double2) + (size_t)(j > 0 ? j - 1 : 0) * (sizeof(double2) + sizeof(double));
-    allow_dynamic_smem((const void*)k_dcgs_finish, b);
+    allow_dynamic_smem((const void*)k_dcgs_givens, b);
     return b;
 }
 
@@ -969,7 +984,6 @@ void launch_dcgs2_step(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int l
     // entry pairs: the padded vector length and all strides are even
     const long long Np = (kb.N + 1) / 2, ldp = kb.ld / 2, sVp = kb.sV() / 2;
     float4* V32 = reinterpret_cast<float4*>(kb.V32);
-    const dim3 gr(kb.nblk, nb);
     if (ev) cudaEventRecord(ev[0], cx.stream);
     k_dcgs_dot<kDotGroupDC><<<dim3(kb.nblk_dot, nb), kRedThreads, 0, cx.stream>>>(j, Np, ldp, ps, S, V32, sVp,
                                                                                  !last_only, kb.part, kb.sP(),
@@ -978,27 +992,43 @@ void launch_dcgs2_step(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int l
     const dim3 rg(((2 * j + 2) * 32 + 255) / 256, nb);
     k_dcgs_reduce<<<rg, 256, 0, cx.stream>>>(j, kb.nblk_dot, ps, S, kb.part, kb.sP(), kb.sigma, kb.h2, kb.hn,
                                              kb.sS(), kb.sN(), kb.st);
-    k_dcgs_finish<<<nb, kFinThreads, dcgs_finish_smem(j), cx.stream>>>(j, kb.maxit, last_only, kb.hn, kb.sN(),
-                                                                        kb.h1, kb.h2, kb.H, kb.sH(), kb.cs, kb.sn,
-                                                                        kb.g, kb.sigma, kb.sS(), kb.st, kb.active);
-    if (last_only) return;
-    const size_t us = (size_t)(j > 0 ? j : 1) * sizeof(UpdCoef);
-    const int nupd = kUpdBlocksPerSM * cx.num_sms;           // <= kb.nblk, the partials' stride
-    const dim3 gu(nupd, nb);
-    if (ev) cudaEventRecord(ev[2], cx.stream);
-    if (kb.lo16) {
-        set_coef_smem_limit((const void*)k_dcgs_update<uint2>, us);
-        k_dcgs_update<uint2><<<gu, kRedThreads, us, cx.stream>>>(j, Np, ldp, V32, static_cast<uint2*>(kb.V32lo), sVp,
-                                                                 kb.sigma, kb.h1, kb.h2, kb.sS(), kb.npart, kb.nblk,
-                                                                 kb.st);
-    } else {
-        set_coef_smem_limit((const void*)k_dcgs_update<float4>, us);
-        k_dcgs_update<float4><<<gu, kRedThreads, us, cx.stream>>>(j, Np, ldp, V32, static_cast<float4*>(kb.V32lo),
-                                                                  sVp, kb.sigma, kb.h1, kb.h2, kb.sS(), kb.npart,
-                                                                  kb.nblk, kb.st);
+    k_dcgs_coef<<<nb, kFinThreads, 0, cx.stream>>>(j, kb.maxit, last_only, kb.hn, kb.sN(), kb.h1, kb.h2, kb.H,
+                                                   kb.sH(), kb.sigma, kb.sS(), kb.st, kb.active);
+    // rotation and stop test of column j-1 beside the update pass (on the side stream when
+    // there is one); the step's end waits for them
+    const bool side = j > 0 && kb.side && kb.ev_c && kb.ev_g;
+    if (j > 0) {
+        cudaStream_t gs = cx.stream;
+        if (side) {
+            cudaEventRecord(kb.ev_c, cx.stream);
+            cudaStreamWaitEvent(kb.side, kb.ev_c, 0);
+            gs = kb.side;
+        }
+        k_dcgs_givens<<<nb, kFinThreads, dcgs_givens_smem(j), gs>>>(j, kb.maxit, last_only, kb.H, kb.sH(), kb.cs,
+                                                                     kb.sn, kb.g, kb.sS(), kb.st, kb.active);
+        if (side) cudaEventRecord(kb.ev_g, kb.side);
     }
-    if (ev) cudaEventRecord(ev[3], cx.stream);
-    k_dcgs_scale<<<nb, 32, 0, cx.stream>>>(j, nupd, kb.nblk, kb.npart, kb.sigt, kb.sS(), kb.st);
+    if (!last_only) {
+        const size_t us = (size_t)(j > 0 ? j : 1) * sizeof(UpdCoef);
+        const int nupd = kUpdBlocksPerSM * cx.num_sms;           // <= kb.nblk, the partials' stride
+        const dim3 gu(nupd, nb);
+        if (ev) cudaEventRecord(ev[2], cx.stream);
+        if (kb.lo16) {
+            set_coef_smem_limit((const void*)k_dcgs_update<uint2>, us);
+            k_dcgs_update<uint2><<<gu, kRedThreads, us, cx.stream>>>(j, Np, ldp, V32, static_cast<uint2*>(kb.V32lo),
+                                                                     sVp, kb.sigma, kb.h1, kb.h2, kb.sS(), kb.npart,
+                                                                     kb.nblk, kb.st);
+        } else {
+            set_coef_smem_limit((const void*)k_dcgs_update<float4>, us);
+            k_dcgs_update<float4><<<gu, kRedThreads, us, cx.stream>>>(j, Np, ldp, V32,
+                                                                      static_cast<float4*>(kb.V32lo), sVp, kb.sigma,
+                                                                      kb.h1, kb.h2, kb.sS(), kb.npart, kb.nblk,
+                                                                      kb.st);
+        }
+        if (ev) cudaEventRecord(ev[3], cx.stream);
+        k_dcgs_scale<<<nb, 32, 0, cx.stream>>>(j, nupd, kb.nblk, kb.npart, kb.sigt, kb.sS(), kb.st);
+    }
+    if (side) cudaStreamWaitEvent(cx.stream, kb.ev_g, 0);
 }
 
 void launch_lsq_solve(const Ctx& cx, const KrylovBufs& kb, int nb) {

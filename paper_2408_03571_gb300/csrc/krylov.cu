@@ -23,8 +23,9 @@ namespace hzs {
 constexpr int kRedThreads = 256;
 constexpr int kDotGroup64 = 4;     // basis vectors per warp pass (FP64 multi-dot)
 constexpr int kDotGroupDC = 4;     // basis vectors per warp pass (delayed CGS2 multi-dot)
-constexpr int kUpdUnroll = 4;      // basis vectors per group of the delayed CGS2 update (two groups in flight)
+constexpr int kUpdUnroll = 4;      // basis vectors per group of the delayed CGS2 update
 constexpr int kUpdBlocksPerSM = 2; // resident blocks of the delayed CGS2 update (up to 128 registers a thread)
+constexpr int kSmemPerSM = 228 * 1024;   // shared memory of one SM (GB300)
 
 __device__ __forceinline__ void chunk_of(long long N, long long& e0, long long& e1) {
     const long long per = (N + gridDim.x - 1) / gridDim.x;
@@ -581,6 +582,23 @@ __device__ __forceinline__ void lo_pairs(uint2 v, f2x& l0, f2x& l1) {
     l1 = f2_pack(__uint_as_float(v.y << 16), __uint_as_float(v.y & 0xffff0000u));
 }
 
+// Per-thread asynchronous copies global -> shared (each thread later reads back only
+// what it copied itself, after cp.async.wait_group: no block barrier is involved).
+__device__ __forceinline__ void cp_async_16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_lo(float4* smem, const float4* gmem) { cp_async_16(smem, gmem); }
+__device__ __forceinline__ void cp_async_lo(uint2* smem, const uint2* gmem) { cp_async_8(smem, gmem); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Coefficients of basis vector i for the update pass, as broadcast packed pairs
 // (see df_fma2): c = h1_i sigma_i in double-float, a = h2_i sigma_i in complex64.
 struct alignas(16) UpdCoef {
@@ -596,7 +614,7 @@ struct alignas(16) UpdCoef {
 // register: sum_i c_i v_i = sum_i Re(c_i) v_i + i sum_i Im(c_i) v_i, so each entry
 // keeps the two real-coefficient sums A = sum Re(c) v and B = sum Im(c) v (and the
 // same for the reorthogonalisation) and forms A + i B once at the end.
-template <typename L>
+template <typename L, int NS>
 __global__ void __launch_bounds__(kRedThreads, kUpdBlocksPerSM) k_dcgs_update(int j, long long Np, long long ldp,
                                                              float4* __restrict__ V32, L* __restrict__ V32lo,
                                                              long long sVp, const double* __restrict__ sigma,
@@ -611,8 +629,14 @@ __global__ void __launch_bounds__(kRedThreads, kUpdBlocksPerSM) k_dcgs_update(in
     L* ul = V32lo + (size_t)j * ldp;
     float4* wh = V32 + (size_t)(j + 1) * ldp;
     L* wl = V32lo + (size_t)(j + 1) * ldp;
-    extern __shared__ UpdCoef ucs[];                        // j entries
+    // dynamic shared memory: j coefficient sets, then (NS > 0) the per-thread copy ring
+    // of NS groups of kUpdUnroll basis vectors (leading words, then remainders); NS == 0
+    // keeps two groups in registers instead
+    extern __shared__ UpdCoef ucs[];
     __shared__ float4 s_cj;                                 // h_jj sigma_j (double-float)
+    ulonglong2* ring_h = reinterpret_cast<ulonglong2*>(ucs + (j > 0 ? j : 1));
+    L* ring_l = reinterpret_cast<L*>(ring_h + NS * kUpdUnroll * blockDim.x);
+    (void)ring_h; (void)ring_l;
     for (int i = threadIdx.x; i <= j; i += blockDim.x) {
         const double2 c = cscale(h1[i], sigma[i]);
         float crh, crl, cih, cil;
@@ -651,47 +675,80 @@ __global__ void __launch_bounds__(kRedThreads, kUpdBlocksPerSM) k_dcgs_update(in
             S0 = fma2(u.ar, vh.x, S0); T0 = fma2(u.ai, vh.x, T0);
             S1 = fma2(u.ar, vh.y, S1); T1 = fma2(u.ai, vh.y, T1);
         };
-        // two groups of kUpdUnroll vectors in registers: the loads of the next group are
-        // issued before the current group is consumed (the work on one group covers less
-        // time than a DRAM round trip)
-        ulonglong2 ha[kUpdUnroll], hb[kUpdUnroll];
-        L la[kUpdUnroll], lb[kUpdUnroll];
-        int i = 0;
-        if (kUpdUnroll <= j) {
-#pragma unroll
-            for (int t = 0; t < kUpdUnroll; ++t) {
-                ha[t] = ph[(size_t)vi(t) * ldp];
-                la[t] = pl[(size_t)vi(t) * ldp];
-            }
-        }
-        // invariant: ha, la hold group i whenever i + kUpdUnroll <= j
-        for (; i + 2 * kUpdUnroll <= j; i += 2 * kUpdUnroll) {
-#pragma unroll
-            for (int t = 0; t < kUpdUnroll; ++t) {
-                hb[t] = ph[(size_t)vi(i + kUpdUnroll + t) * ldp];
-                lb[t] = pl[(size_t)vi(i + kUpdUnroll + t) * ldp];
-            }
-#pragma unroll
-            for (int t = 0; t < kUpdUnroll; ++t) step(ucs[vi(i + t)], ha[t], la[t]);
-            df_norm2(A0h, A0l); df_norm2(B0h, B0l); df_norm2(A1h, A1l); df_norm2(B1h, B1l);
-            if (i + 3 * kUpdUnroll <= j) {
-#pragma unroll
+        if constexpr (NS > 0) {
+            // groups of kUpdUnroll vectors stream through a per-thread ring of NS stages in
+            // shared memory (cp.async): NS - 1 groups are in flight while one is consumed,
+            // and no registers are held for them
+            const int ngrp = j / kUpdUnroll;
+            auto slot = [&](int stage, int t) { return (stage * kUpdUnroll + t) * (int)blockDim.x + (int)threadIdx.x; };
+            auto issue = [&](int g, int stage) {
+    #pragma unroll
                 for (int t = 0; t < kUpdUnroll; ++t) {
-                    ha[t] = ph[(size_t)vi(i + 2 * kUpdUnroll + t) * ldp];
-                    la[t] = pl[(size_t)vi(i + 2 * kUpdUnroll + t) * ldp];
+                    const size_t off = (size_t)vi(g * kUpdUnroll + t) * ldp;
+                    cp_async_16(ring_h + slot(stage, t), ph + off);
+                    cp_async_lo(ring_l + slot(stage, t), pl + off);
+                }
+            };
+    #pragma unroll
+            for (int g = 0; g < NS - 1; ++g) {
+                if (g < ngrp) issue(g, g);
+                cp_async_commit();
+            }
+            int cs = 0;                                         // stage of group g
+            for (int g = 0; g < ngrp; ++g) {
+                const int is = cs == 0 ? NS - 1 : cs - 1;       // stage of group g + NS - 1 (consumed at g - 1)
+                if (g + NS - 1 < ngrp) issue(g + NS - 1, is);
+                cp_async_commit();
+                cp_async_wait<NS - 1>();                        // group g has landed
+    #pragma unroll
+                for (int t = 0; t < kUpdUnroll; ++t) step(ucs[vi(g * kUpdUnroll + t)], ring_h[slot(cs, t)], ring_l[slot(cs, t)]);
+                df_norm2(A0h, A0l); df_norm2(B0h, B0l); df_norm2(A1h, A1l); df_norm2(B1h, B1l);
+                cs = cs + 1 == NS ? 0 : cs + 1;
+            }
+            for (int i = ngrp * kUpdUnroll; i < j; ++i) step(ucs[vi(i)], ph[(size_t)vi(i) * ldp], pl[(size_t)vi(i) * ldp]);
+        } else {
+            // two groups of kUpdUnroll vectors in registers: the loads of the next group are
+            // issued before the current group is consumed (the work on one group covers less
+            // time than a DRAM round trip)
+            ulonglong2 ha[kUpdUnroll], hb[kUpdUnroll];
+            L la[kUpdUnroll], lb[kUpdUnroll];
+            int i = 0;
+            if (kUpdUnroll <= j) {
+    #pragma unroll
+                for (int t = 0; t < kUpdUnroll; ++t) {
+                    ha[t] = ph[(size_t)vi(t) * ldp];
+                    la[t] = pl[(size_t)vi(t) * ldp];
                 }
             }
-#pragma unroll
-            for (int t = 0; t < kUpdUnroll; ++t) step(ucs[vi(i + kUpdUnroll + t)], hb[t], lb[t]);
-            df_norm2(A0h, A0l); df_norm2(B0h, B0l); df_norm2(A1h, A1l); df_norm2(B1h, B1l);
+            // invariant: ha, la hold group i whenever i + kUpdUnroll <= j
+            for (; i + 2 * kUpdUnroll <= j; i += 2 * kUpdUnroll) {
+    #pragma unroll
+                for (int t = 0; t < kUpdUnroll; ++t) {
+                    hb[t] = ph[(size_t)vi(i + kUpdUnroll + t) * ldp];
+                    lb[t] = pl[(size_t)vi(i + kUpdUnroll + t) * ldp];
+                }
+    #pragma unroll
+                for (int t = 0; t < kUpdUnroll; ++t) step(ucs[vi(i + t)], ha[t], la[t]);
+                df_norm2(A0h, A0l); df_norm2(B0h, B0l); df_norm2(A1h, A1l); df_norm2(B1h, B1l);
+                if (i + 3 * kUpdUnroll <= j) {
+    #pragma unroll
+                    for (int t = 0; t < kUpdUnroll; ++t) {
+                        ha[t] = ph[(size_t)vi(i + 2 * kUpdUnroll + t) * ldp];
+                        la[t] = pl[(size_t)vi(i + 2 * kUpdUnroll + t) * ldp];
+                    }
+                }
+    #pragma unroll
+                for (int t = 0; t < kUpdUnroll; ++t) step(ucs[vi(i + kUpdUnroll + t)], hb[t], lb[t]);
+                df_norm2(A0h, A0l); df_norm2(B0h, B0l); df_norm2(A1h, A1l); df_norm2(B1h, B1l);
+            }
+            if (i + kUpdUnroll <= j) {
+    #pragma unroll
+                for (int t = 0; t < kUpdUnroll; ++t) step(ucs[vi(i + t)], ha[t], la[t]);
+                df_norm2(A0h, A0l); df_norm2(B0h, B0l); df_norm2(A1h, A1l); df_norm2(B1h, B1l);
+                i += kUpdUnroll;
+            }
+            for (; i < j; ++i) step(ucs[vi(i)], ph[(size_t)vi(i) * ldp], pl[(size_t)vi(i) * ldp]);
         }
-        if (i + kUpdUnroll <= j) {
-#pragma unroll
-            for (int t = 0; t < kUpdUnroll; ++t) step(ucs[vi(i + t)], ha[t], la[t]);
-            df_norm2(A0h, A0l); df_norm2(B0h, B0l); df_norm2(A1h, A1l); df_norm2(B1h, B1l);
-            i += kUpdUnroll;
-        }
-        for (; i < j; ++i) step(ucs[vi(i)], ph[(size_t)vi(i) * ldp], pl[(size_t)vi(i) * ldp]);
         // sum_i c_i v_i = A + i B per entry: re = A.re - B.im, im = A.im + B.re
         float a0h, a0l, b0h, b0l, a1h, a1l, b1h, b1l;
         {
@@ -1009,21 +1066,28 @@ void launch_dcgs2_step(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int l
         if (side) cudaEventRecord(kb.ev_g, kb.side);
     }
     if (!last_only) {
-        const size_t us = (size_t)(j > 0 ? j : 1) * sizeof(UpdCoef);
-        const int nupd = kUpdBlocksPerSM * cx.num_sms;           // <= kb.nblk, the partials' stride
+        // narrow remainders: a copy ring of 3 stages (24 B per vector slot); wide remainders
+        // (32 B per slot, where 3 stages would leave one block per SM): two groups in registers
+        const int ns = kb.lo16 ? 3 : 0;
+        const size_t slot_bytes = sizeof(ulonglong2) + sizeof(uint2);
+        const size_t us = (size_t)(j > 0 ? j : 1) * sizeof(UpdCoef) + (size_t)ns * kUpdUnroll * kRedThreads * slot_bytes;
+        // two blocks per SM when their shared memory fits (long runs fall back to one)
+        const int bps = 2 * (us + 1024) <= (size_t)kSmemPerSM ? kUpdBlocksPerSM : 1;
+        const int nupd = bps * cx.num_sms;                       // <= kb.nblk, the partials' stride
         const dim3 gu(nupd, nb);
         if (ev) cudaEventRecord(ev[2], cx.stream);
         if (kb.lo16) {
-            set_coef_smem_limit((const void*)k_dcgs_update<uint2>, us);
-            k_dcgs_update<uint2><<<gu, kRedThreads, us, cx.stream>>>(j, Np, ldp, V32, static_cast<uint2*>(kb.V32lo),
-                                                                     sVp, kb.sigma, kb.h1, kb.h2, kb.sS(), kb.npart,
-                                                                     kb.nblk, kb.st);
+            set_coef_smem_limit((const void*)k_dcgs_update<uint2, 3>, us);
+            k_dcgs_update<uint2, 3><<<gu, kRedThreads, us, cx.stream>>>(j, Np, ldp, V32,
+                                                                        static_cast<uint2*>(kb.V32lo), sVp, kb.sigma,
+                                                                        kb.h1, kb.h2, kb.sS(), kb.npart, kb.nblk,
+                                                                        kb.st);
         } else {
-            set_coef_smem_limit((const void*)k_dcgs_update<float4>, us);
-            k_dcgs_update<float4><<<gu, kRedThreads, us, cx.stream>>>(j, Np, ldp, V32,
-                                                                      static_cast<float4*>(kb.V32lo), sVp, kb.sigma,
-                                                                      kb.h1, kb.h2, kb.sS(), kb.npart, kb.nblk,
-                                                                      kb.st);
+            set_coef_smem_limit((const void*)k_dcgs_update<float4, 0>, us);
+            k_dcgs_update<float4, 0><<<gu, kRedThreads, us, cx.stream>>>(j, Np, ldp, V32,
+                                                                         static_cast<float4*>(kb.V32lo), sVp,
+                                                                         kb.sigma, kb.h1, kb.h2, kb.sS(), kb.npart,
+                                                                         kb.nblk, kb.st);
         }
         if (ev) cudaEventRecord(ev[3], cx.stream);
         k_dcgs_scale<<<nb, 32, 0, cx.stream>>>(j, nupd, kb.nblk, kb.npart, kb.sigt, kb.sS(), kb.st);

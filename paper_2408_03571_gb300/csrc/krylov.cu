@@ -470,9 +470,17 @@ __global__ void __launch_bounds__(kFinThreads) k_dcgs_coef(int j, int maxit, int
         __syncthreads();                     // the old h1 is read before it is overwritten below
     }
     if (last_only) return;
-    // column j, first pass (alpha is complete for the old vectors; q_j = (u~ - Q alpha) / beta)
+    // column j, first pass (alpha is complete for the old vectors; q_j = (u~ - Q alpha) / beta).
+    // The update pass applies sigma_i h1_i to V_i as an FP32 number (the coefficient comes
+    // from complex64 dot products, so rounding it loses nothing): h1_i is recorded as that
+    // rounded product over sigma_i, the value the Arnoldi relation then holds for.
     const double ib = beta > 0.0 ? 1.0 / beta : 0.0;
-    for (int i = tid; i < j; i += kFinThreads) h1[i] = hn[i];
+    for (int i = tid; i < j; i += kFinThreads) {
+        const double si = sigma[i];
+        const double2 c = cscale(hn[i], si);
+        const double2 cr = make_double2((double)(float)c.x, (double)(float)c.y);
+        h1[i] = si > 0.0 ? cscale(cr, 1.0 / si) : hn[i];
+    }
     if (tid == 0) {
         h1[j] = cscale(csub(d, ab), ib);
         sigma[j] = ib;
@@ -551,16 +559,14 @@ __device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c) {
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;
 }
-// Lane-wise double-float multiply-add (sh, sl) += c * (vh + vl) for a real c = ch + cl
-// given as the broadcast pairs P = (ch, ch), N = (-ch, -ch), NL = (-cl, -cl) (no
-// negation modifier exists for the packed forms).  Same arithmetic as df_fma: the
-// product ch vh is split exactly by an FMA, ch vl and cl vh are added to its error,
-// and the accumulation is a TwoSum.
-__device__ __forceinline__ void df_fma2(f2x& sh, f2x& sl, f2x P, f2x N, f2x NL, f2x vh, f2x vl) {
+// Lane-wise double-float multiply-add (sh, sl) += c * (vh + vl) for an FP32 c given
+// as the broadcast pairs P = (c, c), N = (-c, -c) (no negation modifier exists for the
+// packed forms): the product c vh is split exactly by an FMA, c vl is added to its
+// error, and the accumulation is a TwoSum.
+__device__ __forceinline__ void df_fma2(f2x& sh, f2x& sl, f2x P, f2x N, f2x vh, f2x vl) {
     const f2x p = mul2(P, vh);
-    f2x en = fma2(N, vh, p);            // -(ch vh - p), exact
-    en = fma2(N, vl, en);
-    en = fma2(NL, vh, en);              // en = -(error + ch vl + cl vh)
+    f2x en = fma2(N, vh, p);            // -(c vh - p), exact
+    en = fma2(N, vl, en);               // en = -(error + c vl)
     const f2x s = add2(sh, p);          // TwoSum(sh, p)
     const f2x bb = sub2(s, sh);
     const f2x t = add2(sub2(sh, sub2(s, bb)), sub2(p, bb));
@@ -602,7 +608,7 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
 // Coefficients of basis vector i for the update pass, as broadcast packed pairs
 // (see df_fma2): c = h1_i sigma_i in double-float, a = h2_i sigma_i in complex64.
 struct alignas(16) UpdCoef {
-    f2x Pr, Nr, NLr, Pi, Ni, NLi;       // c.re and c.im
+    f2x Pr, Nr, Pi, Ni;                 // c.re and c.im
     f2x ar, ai;                         // a.re and a.im
 };
 
@@ -645,8 +651,10 @@ __global__ void __launch_bounds__(kRedThreads, kUpdBlocksPerSM) k_dcgs_update(in
         if (i == j) { s_cj = make_float4(crh, crl, cih, cil); continue; }
         const float2 a = to_f(cscale(h2[i], sigma[i]));
         UpdCoef u;
-        u.Pr = f2_pack(crh, crh); u.Nr = f2_pack(-crh, -crh); u.NLr = f2_pack(-crl, -crl);
-        u.Pi = f2_pack(cih, cih); u.Ni = f2_pack(-cih, -cih); u.NLi = f2_pack(-cil, -cil);
+        // c is an FP32 value for i < j (k_dcgs_coef records the rounded coefficient): crl and
+        // cil are below 2^-50 of it and are dropped
+        u.Pr = f2_pack(crh, crh); u.Nr = f2_pack(-crh, -crh);
+        u.Pi = f2_pack(cih, cih); u.Ni = f2_pack(-cih, -cih);
         u.ar = f2_pack(a.x, a.x); u.ai = f2_pack(a.y, a.y);
         ucs[i] = u;
     }
@@ -668,10 +676,10 @@ __global__ void __launch_bounds__(kRedThreads, kUpdBlocksPerSM) k_dcgs_update(in
         auto step = [&](const UpdCoef& u, ulonglong2 vh, L vlr) {
             f2x l0, l1;
             lo_pairs(vlr, l0, l1);
-            df_fma2(A0h, A0l, u.Pr, u.Nr, u.NLr, vh.x, l0);
-            df_fma2(B0h, B0l, u.Pi, u.Ni, u.NLi, vh.x, l0);
-            df_fma2(A1h, A1l, u.Pr, u.Nr, u.NLr, vh.y, l1);
-            df_fma2(B1h, B1l, u.Pi, u.Ni, u.NLi, vh.y, l1);
+            df_fma2(A0h, A0l, u.Pr, u.Nr, vh.x, l0);
+            df_fma2(B0h, B0l, u.Pi, u.Ni, vh.x, l0);
+            df_fma2(A1h, A1l, u.Pr, u.Nr, vh.y, l1);
+            df_fma2(B1h, B1l, u.Pi, u.Ni, vh.y, l1);
             S0 = fma2(u.ar, vh.x, S0); T0 = fma2(u.ai, vh.x, T0);
             S1 = fma2(u.ar, vh.y, S1); T1 = fma2(u.ai, vh.y, T1);
         };

@@ -45,6 +45,11 @@ def parse():
                     help="skip the arm whose Krylov basis keeps complex64 remainders (about 48 bits)")
     ap.add_argument("--no-dedup-arm", action="store_true",
                     help="skip the MIXED arm with every subdomain factored separately")
+    ap.add_argument("--graph", action="store_true",
+                    help="time the headline value with the Arnoldi steps issued as CUDA graphs "
+                         "(by default they are stream-issued and the graph-issued solve is a side arm)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="launch the subdomain solve with its default shape instead of the set-up autotuner's")
     ap.add_argument("--workload", choices=["headline", "batched"], default="headline",
                     help="batched: the MP-2 multi-problem batch (64 right-hand sides for each of "
                          "(k, n) = (25, 257), (50, 257), (100, 513)) instead of the headline solve")
@@ -253,7 +258,8 @@ def batched_arm(args, world, rank, local):
     for i, (k, n, nsub) in enumerate(BATCHED):
         g = hzs.Grid(n, hzs.SOMMERFELD, k=k, nsub=nsub, overlap=2)
         grids.append(g)
-        precs.append(hzs.Preconditioner(g, hzs.SHS2, hzs.COARSE_B2, 32, hzs.MIXED))
+        precs.append(hzs.Preconditioner(g, hzs.SHS2, hzs.COARSE_B2, 32, hzs.MIXED,
+                                        autotune=0 if args.no_autotune else 1))
         nodes = random_source_nodes(n, args.nrhs, 1000 + i)
         fh = torch.from_numpy(np.stack([point_source(n, nd) for nd in nodes])).pin_memory()
         rhs_host.append(fh)
@@ -261,7 +267,7 @@ def batched_arm(args, world, rank, local):
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     for _ in range(args.warmup):
-        hzs.solve_batched(precs, rhs, TOL, MAXIT)
+        hzs.solve_batched(precs, rhs, TOL, MAXIT, graph=args.graph)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -270,7 +276,7 @@ def batched_arm(args, world, rank, local):
     e0.record(stream)
     infos = None
     for _ in range(args.steps):
-        _, infos = hzs.solve_batched(precs, rhs, TOL, MAXIT)
+        _, infos = hzs.solve_batched(precs, rhs, TOL, MAXIT, graph=args.graph)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
@@ -279,17 +285,21 @@ def batched_arm(args, world, rank, local):
     e0.record(stream)
     for _ in range(args.steps):
         fd = [f.to(dev, non_blocking=True) for f in rhs_host]
-        outs, _ = hzs.solve_batched(precs, fd, TOL, MAXIT)
+        outs, _ = hzs.solve_batched(precs, fd, TOL, MAXIT, graph=args.graph)
         for u in outs:
             u.cpu()
     e1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = max_over_ranks(e0.elapsed_time(e1), world, dev)
     nsol = sum(len(r) for r in infos)
+    shapes = [P.info() for P in precs]
     per = []
-    for (k, n, nsub), res in zip(BATCHED, infos):
+    for (k, n, nsub), res, sh in zip(BATCHED, infos, shapes):
         its = [r.iterations for r in res]
         per.append({"k": k, "n": n, "nrhs": len(res), "iterations_max": max(its),
+                    "subdomain_solve_shape": {key: sh[key] for key in ("tile_group", "tile_stages",
+                                                                       "tile_threads_per_row", "autotuned",
+                                                                       "apply_us_default", "apply_us_tuned")},
                     "iterations_mean": float(np.mean(its)),
                     "converged": int(sum(r.converged for r in res)),
                     "relres_true_max": max(r.relres_true for r in res)})
@@ -312,6 +322,7 @@ def batched_arm(args, world, rank, local):
         "config": {"workload": "MP-2 batch: (k, n) = (25, 257), (50, 257), (100, 513), 64-node subdomains, "
                                "overlap 2, SHS2 with B2 H=32h, point sources at seeded nodes, all problems "
                                "solved concurrently, right-hand sides of a problem in lockstep",
+                   "issue": "CUDA graphs of 8 Arnoldi steps" if args.graph else "stream launches",
                    "l2": "working set larger than L2; no flush needed", "parallelism": f"replicas x{world}"},
         "problems": per, "setup_s": setup_s,
         "e2e": {"value": replica_throughput(nsol, ms_e2e / args.steps, world), "unit": "solves/s",
@@ -347,12 +358,12 @@ def gpu_arm(args, world, rank, local):
             torch.distributed.barrier()
             torch.cuda.synchronize()
 
-    def timed_solves(P, steps, warmup, e2e=False, profile=True, wide=False):
+    def timed_solves(P, steps, warmup, e2e=False, profile=False, wide=False, graph=False):
         u = torch.empty_like(f)
         u_host = torch.empty_like(f_host).pin_memory()
         infos = []
         for _ in range(warmup):
-            P.solve(f, TOL, MAXIT, out=u, wide_basis=wide)
+            P.solve(f, TOL, MAXIT, out=u, wide_basis=wide, graph=graph)
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -360,10 +371,10 @@ def gpu_arm(args, world, rank, local):
         for _ in range(steps):
             if e2e:
                 fd = f_host.to(dev, non_blocking=True)
-                _, inf = P.solve(fd, TOL, MAXIT, out=u, profile=profile, wide_basis=wide)
+                _, inf = P.solve(fd, TOL, MAXIT, out=u, profile=profile, wide_basis=wide, graph=graph)
                 u_host.copy_(u, non_blocking=True)
             else:
-                _, inf = P.solve(f, TOL, MAXIT, out=u, profile=profile, wide_basis=wide)
+                _, inf = P.solve(f, TOL, MAXIT, out=u, profile=profile, wide_basis=wide, graph=graph)
             infos.append(inf[0])
         e1.record(stream)
         barrier()
@@ -373,18 +384,29 @@ def gpu_arm(args, world, rank, local):
     out = {}
     # ---- mixed (headline)
     t0 = time.perf_counter()
-    Pm = hzs.Preconditioner(grid, hzs.SHS2, hzs.COARSE_B2, P_COARSE, hzs.MIXED)
+    Pm = hzs.Preconditioner(grid, hzs.SHS2, hzs.COARSE_B2, P_COARSE, hzs.MIXED,
+                            autotune=0 if args.no_autotune else 1)
     torch.cuda.synchronize()
     setup_mixed_s = time.perf_counter() - t0
+    shape = Pm.info()
+    # the headline value: solves without per-launch events
     clk = ClockSampler(local)
     clk.start()
-    ms_tot, infos, u = timed_solves(Pm, args.steps, args.warmup)
+    ms_tot, infos_plain, u = timed_solves(Pm, args.steps, args.warmup, graph=args.graph)
     clocks = clk.stop()
-    ms_e2e, infos_e2e, _ = timed_solves(Pm, args.steps, 0, e2e=True, profile=False)
+    # the same solves with CUDA events around every launch: phase times and the roofline
+    ms_prof, infos, _ = timed_solves(Pm, args.steps, 0, profile=True)
+    # the other way of issuing the Arnoldi steps (graph-issued, or stream-issued with --graph)
+    ms_alt, infos_alt, _ = timed_solves(Pm, args.steps, 1, graph=not args.graph)
+    issue_alt = {"value": replica_throughput(args.steps, ms_alt, world), "unit": "solves/s",
+                 "ms_per_step": ms_alt / args.steps, "iterations": infos_alt[-1].iterations,
+                 "relres_true": infos_alt[-1].relres_true,
+                 "issue": "stream launches" if args.graph else "CUDA graphs of 8 Arnoldi steps"}
+    ms_e2e, infos_e2e, _ = timed_solves(Pm, args.steps, 0, e2e=True, graph=args.graph)
     # ---- the same solve with the basis remainders kept as complex64 (about 48 bits)
     wide = None
     if not args.no_wide_arm:
-        ms_w, infos_w, _ = timed_solves(Pm, max(1, args.steps // 2), 1, wide=True)
+        ms_w, infos_w, _ = timed_solves(Pm, max(1, args.steps // 2), 1, profile=True, wide=True)
         i0 = infos_w[-1]
         wide = {"value": replica_throughput(len(infos_w), ms_w, world), "unit": "solves/s",
                 "ms_per_step": ms_w / len(infos_w), "iterations": i0.iterations,
@@ -398,7 +420,7 @@ def gpu_arm(args, world, rank, local):
     dedup_off = None
     if not args.no_dedup_arm:
         Pn = hzs.Preconditioner(grid, hzs.SHS2, hzs.COARSE_B2, P_COARSE, hzs.MIXED, dedup_tiles=False)
-        ms_n, infos_n, _ = timed_solves(Pn, max(1, args.steps // 2), 1)
+        ms_n, infos_n, _ = timed_solves(Pn, max(1, args.steps // 2), 1, profile=True)
         Pn.close()
         i0 = infos_n[-1]
         dedup_off = {"value": replica_throughput(len(infos_n), ms_n, world), "unit": "solves/s",
@@ -413,7 +435,7 @@ def gpu_arm(args, world, rank, local):
         Pd = hzs.Preconditioner(grid, hzs.SHS2, hzs.COARSE_B2, P_COARSE, hzs.FP64)
         torch.cuda.synchronize()
         setup_fp64_s = time.perf_counter() - t0
-        ms_d, infos_d, _ = timed_solves(Pd, max(1, args.steps // 2), 1)
+        ms_d, infos_d, _ = timed_solves(Pd, max(1, args.steps // 2), 1, profile=True)
         Pd.close()
         i0 = infos_d[-1]
         fp64 = {"value": replica_throughput(len(infos_d), ms_d, world), "unit": "solves/s",
@@ -453,7 +475,8 @@ def gpu_arm(args, world, rank, local):
         return {"kernel": name, "bound": "hbm", "achieved": a, "peak": hbm_peak, "unit": "GB/s",
                 "frac": a / hbm_peak, "traffic": None, "peak_source": peak_src,
                 "bytes_per_solve": nbytes, "time_per_solve_s": t,
-                "timing": "CUDA events around every launch of the kernel on the solve stream"}
+                "timing": "CUDA events around every launch of the kernel on the solve stream, over a "
+                          "timed region of the same number of solves as the value's"}
     r_dot = pass_roofline("k_dcgs_dot (delayed CGS2 multi-dot on the leading words of the basis)", dot_bytes,
                           t_dot)
     r_upd = pass_roofline("k_dcgs_update (delayed CGS2 basis update, double-float)", upd_bytes, t_upd)
@@ -500,15 +523,21 @@ def gpu_arm(args, world, rank, local):
         "config": {"workload": WORKLOAD, "precision": "mixed", "n": N, "k": K_WAVE, "nsub": NSUB,
                    "overlap": OVERLAP, "coarse_ratio": P_COARSE, "tol": TOL, "basis_bits": last.basis_bits,
                    "l2": "working set larger than L2 (Krylov basis ~6 GB); no flush needed",
+                   "issue": "CUDA graphs of 8 Arnoldi steps" if args.graph else "stream launches",
                    "parallelism": f"replicas x{world}"},
-        "iterations": it, "relres_est": last.relres_est, "relres_true": last.relres_true,
+        "iterations": infos_plain[-1].iterations, "relres_est": infos_plain[-1].relres_est,
+        "relres_true": infos_plain[-1].relres_true,
         "setup_s": setup_mixed_s,
+        "subdomain_solve_shape": shape,
+        "profiled": {"value": replica_throughput(args.steps, ms_prof, world), "unit": "solves/s",
+                     "note": "the same solves with CUDA events around every launch (phases and roofline)"},
+        "issue_alt": issue_alt,
         "phases_ms": {"precond": last.t_precond_ms, "matvec": last.t_matvec_ms, "orth": last.t_orth_ms,
                       "solve": last.t_solve_ms},
         "roofline": roofline,
         "e2e": {"value": replica_throughput(args.steps, ms_e2e, world), "unit": "solves/s",
                 "h2d_bytes_per_step": N * N * 16, "d2h_bytes_per_step": N * N * 16},
-        "gpu_launches": int(sum(i.launches for i in infos)),
+        "gpu_launches": int(sum(i.launches for i in infos_plain)),
         "clocks": clocks,
         "fp64": fp64,
         "wide_basis": wide,

@@ -106,7 +106,18 @@ typedef enum { HZS_COARSE_SOLVER_AUTO = 0, HZS_COARSE_SOLVER_DENSE = 1, HZS_COAR
  *   coarse_ratio : p = H/h, >= 2, must divide n-1 (ignored for HZS_AS1).
  *   dedup_tiles  : nonzero lets subdomains with identical local matrices share
  *                  one factorisation (only possible for constant k).
- *   coarse_solver: an hzs_coarse_solver (0 = AUTO). */
+ *   coarse_solver: an hzs_coarse_solver (0 = AUTO).
+ *   autotune     : 0 = the subdomain solve (Section 3, the exact local solves)
+ *                  launches with its fixed default shape; 1 = set-up times the
+ *                  shapes that fit (tiles per thread block, depth of the
+ *                  factor-block copy ring, threads per block row) on this handle
+ *                  and keeps the fastest (more than 2 % ahead of the default, else
+ *                  the default), reusing the choice made earlier in the process
+ *                  for a problem of the same size and decomposition; 2 = re-time
+ *                  even then.  Every shape solves the same tile systems exactly;
+ *                  results differ only in the rounding order of block-row sums.
+ *                  The paper has no counterpart (it concerns the launch, not the
+ *                  method).  Timing synchronises the stream. */
 typedef struct {
     hzs_precond_kind kind;
     hzs_coarse_kind coarse;
@@ -114,6 +125,7 @@ typedef struct {
     hzs_precision precision;
     int dedup_tiles;
     int coarse_solver;
+    int autotune;
 } hzs_precond_desc;
 
 /* GMRES controls (Section 5): right preconditioning, zero initial guess, no
@@ -138,6 +150,16 @@ typedef struct {
  * traffic).  This flag keeps the complex64 remainders at any tol.  No effect
  * without the delayed-CGS2 path. */
 #define HZS_SOLVE_BASIS_WIDE 4
+/* Issue the Arnoldi steps (Section 5: preconditioner apply, matrix-vector
+ * product, orthogonalisation and Givens update of every right-hand side) as
+ * CUDA graphs: chunks of 8 steps are captured on a private stream of the
+ * handle and replayed on the grid's stream, the executable graphs updated in
+ * place from one chunk to the next and kept by the handle for later solves.
+ * Same kernels, arguments and order as without the flag, so the same results;
+ * the convergence count is read back once per chunk instead of once per step
+ * (steps issued after convergence return at once on the device).  Not
+ * combined with HZS_SOLVE_PROFILE (the flag is ignored there). */
+#define HZS_SOLVE_GRAPH 8
 
 /* Per right-hand side results. */
 typedef struct {
@@ -216,6 +238,23 @@ hzs_status hzs_adjoint_solve(hzs_precond* p, const hzs_solve_desc* sd, const voi
  * The paper has no counterpart. */
 hzs_status hzs_kappa_gradient(hzs_precond* p, const void* u_dev, const void* lam_dev,
                               double* grad_dev);
+
+/* What set-up built and chose for a preconditioner (host struct). */
+typedef struct {
+    int nfactors;              /* distinct subdomain factorisations (Section 3) */
+    int coarse_unknowns;       /* |G_H| unknowns of A_0 (Section 4); 0 for HZS_AS1 */
+    int coarse_solver;         /* HZS_COARSE_SOLVER_DENSE or _BLOCK as resolved; 0 for HZS_AS1 */
+    double coarse_min_pivot;   /* smallest pivot magnitude of the coarse factorisation */
+    int tile_group;            /* launch shape of the subdomain solve: tiles per thread block, */
+    int tile_stages;           /*   depth of the factor-block copy ring, */
+    int tile_threads_per_row;  /*   threads per block row */
+    int autotuned;             /* 1 if set-up picked that shape by timing (hzs_precond_desc.autotune) */
+    double apply_us_default;   /* with autotuning: one preconditioner apply with the default shape, */
+    double apply_us_tuned;     /*   and with the chosen one (microseconds, one right-hand side) */
+} hzs_precond_info;
+
+/* Fills *out for p.  The paper has no counterpart. */
+hzs_status hzs_precond_get_info(const hzs_precond* p, hzs_precond_info* out);
 
 /* Allocation-free variant of hzs_apply_precond for SAS2 preconditioners
  * (the paper has no counterpart: it concerns how memory is obtained, not the

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <algorithm>
@@ -62,6 +63,13 @@ struct hzs_precond {
     int* err = nullptr;               // device error word (HZS_ERR_TIMEOUT from bounded waits)
     int* groups_d = nullptr;          // tiles grouped by shared factor
     int ngroups = 0, group_T = 1;
+    int* groups1_d = nullptr;         // one tile per group (kept when group_T == 2, for the autotuner)
+    int ngroups1 = 0;
+    // launch shape of the subdomain solve: tiles per block, copy-ring depth, threads per
+    // block row (0 = chosen per launch); set by the autotuner when asked for
+    int tile_T = 1, tile_nst = 0, tile_tpr = 0;
+    int autotuned = 0;
+    double apply_us_default = 0.0, apply_us_tuned = 0.0;
     double coarse_minpiv = 0.0;
     // local factors
     int nfactors = 0;
@@ -91,7 +99,17 @@ struct hzs_precond {
     cudaEvent_t ev[2] = {nullptr, nullptr};
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     std::vector<cudaEvent_t> prof_ev;  // 4 per step when phase timing is on
+    // HZS_SOLVE_GRAPH: Arnoldi steps captured in chunks on a private stream and replayed
+    cudaStream_t gstream = nullptr;
+    cudaGraphExec_t gexec_first = nullptr;          // the chunk that starts at step 0
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // later chunks, alternating
 };
+
+// The tile groups and launch shape the subdomain solve of this handle uses.
+static TileGroups tile_groups(const hzs_precond* p) {
+    if (p->tile_T == 1 && p->group_T == 2) return TileGroups{p->groups1_d, p->ngroups1, 1, p->tile_nst, p->tile_tpr};
+    return TileGroups{p->groups_d, p->ngroups, p->group_T, p->tile_nst, p->tile_tpr};
+}
 
 // ------------------------------------------------------------------ helpers
 static hzs_status fail(hzs_grid* g, hzs_status s, const std::string& msg) {
@@ -259,6 +277,10 @@ extern "C" void hzs_precond_destroy(hzs_precond* p) {
     if (p->t0) cudaEventDestroy(p->t0);
     if (p->t1) cudaEventDestroy(p->t1);
     for (auto e : p->prof_ev) cudaEventDestroy(e);
+    cudaFree(p->groups1_d);
+    if (p->gexec_first) cudaGraphExecDestroy(p->gexec_first);
+    for (auto& x : p->gexec) if (x) cudaGraphExecDestroy(x);
+    if (p->gstream) cudaStreamDestroy(p->gstream);
     delete p;
 }
 
@@ -383,7 +405,14 @@ static hzs_status setup_impl(hzs_grid* g, const hzs_precond_desc* d, hzs_precond
                     groups.push_back(k + u < lst.size() ? lst[k + u] : -1);
         p->ngroups = (int)(groups.size() / p->group_T);
         HZS_CUDA(g, upload(&p->groups_d, groups, s));
+        if (p->group_T == 2) {
+            std::vector<int> g1;
+            for (auto& lst : by_factor) g1.insert(g1.end(), lst.begin(), lst.end());
+            p->ngroups1 = (int)g1.size();
+            HZS_CUDA(g, upload(&p->groups1_d, g1, s));
+        }
         HZS_CUDA(g, cudaStreamSynchronize(s));
+        p->tile_T = p->group_T;
     }
     p->nfactors = (int)fds.size();
     HZS_CUDA(g, dalloc(&p->W64, (size_t)woff));
@@ -421,6 +450,8 @@ static hzs_status setup_impl(hzs_grid* g, const hzs_precond_desc* d, hzs_precond
     return HZS_OK;
 }
 
+static hzs_status autotune_tile_shape(hzs_precond* p);
+
 extern "C" hzs_status hzs_precond_setup(hzs_grid* g, const hzs_precond_desc* d, hzs_precond** out) {
     if (!out) return fail(g, HZS_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -429,10 +460,12 @@ extern "C" hzs_status hzs_precond_setup(hzs_grid* g, const hzs_precond_desc* d, 
     if (d->precision != HZS_FP64 && d->precision != HZS_MIXED) return fail(g, HZS_ERR_INVALID_ARG, "bad precision");
     if (d->coarse_solver < HZS_COARSE_SOLVER_AUTO || d->coarse_solver > HZS_COARSE_SOLVER_BLOCK)
         return fail(g, HZS_ERR_INVALID_ARG, "bad coarse_solver");
+    if (d->autotune < 0 || d->autotune > 2) return fail(g, HZS_ERR_INVALID_ARG, "bad autotune");
     hzs_precond* p = new hzs_precond();
     p->g = g;
     p->desc = *d;
-    const hzs_status st = setup_impl(g, d, p);
+    hzs_status st = setup_impl(g, d, p);
+    if (st == HZS_OK && d->autotune) st = autotune_tile_shape(p);
     if (st != HZS_OK) {
         hzs_precond_destroy(p);
         return st;
@@ -482,7 +515,7 @@ static hzs_status precond_apply(hzs_precond* p, int nb, const Cv* v, long long v
     const C* W = nullptr;
     const C* cc = nullptr;            // coarse solution in the kernels' precision
     if constexpr (f32) { W = p->W32; cc = p->c2f; } else { W = p->W64; cc = p->c2_buf; }
-    const TileGroups grp{p->groups_d, p->ngroups, p->group_T};
+    const TileGroups grp = tile_groups(p);
     const int kind = p->desc.kind;
     if (p->use_coarse) {
         launch_restrict<Cv, R>(cx, nb, v, vs, vscale, vss, (C*)p->t_buf, p->c_buf, sk);
@@ -554,6 +587,150 @@ extern "C" hzs_status hzs_apply_precond(hzs_precond* p, const void* v_dev, void*
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(p->g, e, "apply_precond");
+    return HZS_OK;
+}
+
+// ------------------------------------------------------------------ subdomain-solve autotuner
+// Picks the launch shape of the subdomain solve - tiles per block (pairs that share a
+// factor, or single tiles), depth of the factor-block copy ring, threads per block row -
+// by timing whole preconditioner applies of this handle (one right-hand side, CUDA
+// events on its stream).  Every shape computes the same tile solves; only the order of
+// the partial sums of a block row changes with the threads per row.  A shape replaces
+// the default only when it is more than 2 % faster.  Choices are kept per process for
+// problems of the same size and decomposition (autotune = 1); autotune = 2 re-times.
+namespace {
+struct TileChoice {
+    int T, nst, tpr;
+    double us_default, us_best;
+};
+std::mutex g_tune_mu;
+std::map<std::string, TileChoice> g_tune_cache;
+constexpr int kTuneReps = 10;
+}  // namespace
+
+static hzs_status autotune_tile_shape(hzs_precond* p) {
+    hzs_grid* g = p->g;
+    const hzs_grid_desc& gd = g->desc;
+    const hzs_precond_desc& d = p->desc;
+    const cudaStream_t s = p->cx.stream;
+    int dev = 0;
+    HZS_CUDA(g, cudaGetDevice(&dev));
+    char kb[256];
+    snprintf(kb, sizeof kb, "%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d", dev, gd.n, (int)gd.bc, gd.nsub, gd.overlap,
+             (int)d.kind, (int)d.coarse, d.coarse_ratio, (int)d.precision, p->coarse_block, p->nfactors, p->group_T,
+             g->max_mx, g->max_my);
+    const std::string key(kb);
+    if (d.autotune == 1) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            p->tile_T = it->second.T; p->tile_nst = it->second.nst; p->tile_tpr = it->second.tpr;
+            p->apply_us_default = it->second.us_default; p->apply_us_tuned = it->second.us_best;
+            p->autotuned = 1;
+            return HZS_OK;
+        }
+    }
+    const int eb = (int)cplx_size(d.precision);
+    struct Cand { int T, nst, tpr; };
+    std::vector<Cand> cands;
+    // the shape the launch picks by itself, first
+    int dT = 0, dN = 0, dP = 0;
+    if (!tile_shape_resolve(TileGroups{nullptr, 0, p->group_T, 0, 0}, g->max_mx, g->max_my, eb, &dT, &dN, &dP))
+        return fail(g, HZS_ERR_INVALID_ARG, "no launch shape of the subdomain solve fits these tiles");
+    cands.push_back({dT, dN, dP});
+    const int Ts[2] = {p->group_T, 1};
+    for (int ti = 0; ti < (p->group_T == 2 ? 2 : 1); ++ti)
+        for (int nst : {4, 2, 1})
+            for (int tpr : {8, 4}) {
+                int a = 0, b = 0, c = 0;
+                if (!tile_shape_resolve(TileGroups{nullptr, 0, Ts[ti], nst, tpr}, g->max_mx, g->max_my, eb, &a, &b, &c))
+                    continue;
+                // a one-stage ring only where no deeper one fits
+                if (nst == 1 && tile_shape_resolve(TileGroups{nullptr, 0, Ts[ti], 2, tpr}, g->max_mx, g->max_my, eb,
+                                                   &a, &b, &c))
+                    continue;
+                if (Ts[ti] == dT && nst == dN && tpr == dP) continue;
+                cands.push_back({Ts[ti], nst, tpr});
+            }
+    const long long nn = (long long)gd.n * gd.n;
+    double2* v = nullptr;
+    void* z = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(v); cudaFree(z);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    cudaError_t e = dalloc(&v, (size_t)nn);
+    if (e == cudaSuccess) e = cudaMalloc(&z, (size_t)nn * eb);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v, 0, (size_t)nn * sizeof(double2), s);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(g, e, "autotune set-up"); }
+    auto run = [&]() -> bool {
+        const hzs_status st =
+            d.precision == HZS_MIXED
+                ? precond_apply<float, double2>(p, 1, v, nn, nullptr, 0, static_cast<float2*>(z), nn, kNoSkip)
+                : precond_apply<double, double2>(p, 1, v, nn, nullptr, 0, static_cast<double2*>(z), nn, kNoSkip);
+        return st == HZS_OK;
+    };
+    double best = 0.0, us_def = 0.0;
+    int bi = -1;
+    for (size_t i = 0; i < cands.size(); ++i) {
+        p->tile_T = cands[i].T; p->tile_nst = cands[i].nst; p->tile_tpr = cands[i].tpr;
+        bool ok = run() && run();
+        if (ok) e = cudaEventRecord(e0, s);
+        for (int r = 0; r < kTuneReps && ok && e == cudaSuccess; ++r) ok = run();
+        if (ok && e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { cleanup(); return cuda_fail(g, e, "autotune"); }
+        if (!ok) {                 // a shape that cannot launch here is skipped
+            cudaGetLastError();
+            continue;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double us = 1e3 * ms / kTuneReps;
+        if (i == 0) us_def = us;
+        if (bi < 0 || us < best) { best = us; bi = (int)i; }
+    }
+    int kerr = 0;
+    e = cudaMemcpyAsync(&kerr, p->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(g, e, "autotune");
+    g->err.clear();
+    if (kerr != 0) {
+        cudaMemsetAsync(p->err, 0, sizeof(int), s);
+        return fail(g, HZS_ERR_TIMEOUT, "a subdomain-solve block gave up waiting for its factor copies");
+    }
+    if (bi < 0 || us_def <= 0.0) return fail(g, HZS_ERR_CUDA, "autotune: the default subdomain-solve shape failed");
+    if (best > 0.98 * us_def) { bi = 0; best = us_def; }   // keep the default unless clearly faster
+    TileChoice tc{cands[bi].T, cands[bi].nst, cands[bi].tpr, us_def, best};
+    p->tile_T = tc.T; p->tile_nst = tc.nst; p->tile_tpr = tc.tpr;
+    p->apply_us_default = us_def; p->apply_us_tuned = best;
+    p->autotuned = 1;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = tc;
+    return HZS_OK;
+}
+
+extern "C" hzs_status hzs_precond_get_info(const hzs_precond* p, hzs_precond_info* out) {
+    if (!p || !out) return fail(nullptr, HZS_ERR_INVALID_ARG, "precond or out is NULL");
+    hzs_precond_info in{};
+    in.nfactors = p->nfactors;
+    in.coarse_unknowns = p->use_coarse ? p->Nc : 0;
+    in.coarse_solver = !p->use_coarse ? 0 : (p->coarse_block ? HZS_COARSE_SOLVER_BLOCK : HZS_COARSE_SOLVER_DENSE);
+    in.coarse_min_pivot = p->coarse_minpiv;
+    int T = 0, nst = 0, tpr = 0;
+    if (tile_shape_resolve(tile_groups(p), p->g->max_mx, p->g->max_my, (int)cplx_size(p->desc.precision), &T, &nst,
+                           &tpr)) {
+        in.tile_group = T; in.tile_stages = nst; in.tile_threads_per_row = tpr;
+    }
+    in.autotuned = p->autotuned;
+    in.apply_us_default = p->apply_us_default;
+    in.apply_us_tuned = p->apply_us_tuned;
+    *out = in;
     return HZS_OK;
 }
 
@@ -670,6 +847,27 @@ static hzs_status ensure_prof_events(hzs_precond* p, int maxit) {
     return HZS_OK;
 }
 
+// Arnoldi steps per captured graph (HZS_SOLVE_GRAPH)
+constexpr int kGraphChunk = 8;
+
+// Launches graph gr on stream s through the executable graph *ex: updated in place when
+// its topology matches gr (only kernel arguments and launch sizes differ between chunks),
+// else (re-)instantiated.  The caller guarantees that no launch of *ex is still running.
+static cudaError_t graph_replay(cudaGraphExec_t* ex, cudaGraph_t gr, cudaStream_t s) {
+    if (*ex) {
+        cudaGraphExecUpdateResultInfo ri{};
+        if (cudaGraphExecUpdate(*ex, gr, &ri) != cudaSuccess) {
+            cudaGetLastError();   // a topology mismatch is not an error here: instantiate anew
+            cudaGraphExecDestroy(*ex);
+            *ex = nullptr;
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    if (!*ex) e = cudaGraphInstantiate(ex, gr, 0ULL);
+    if (e != cudaSuccess) { *ex = nullptr; return e; }
+    return cudaGraphLaunch(*ex, s);
+}
+
 // nb right-hand sides in lockstep: A u_r = f_r (conj_io: solve A mu = conj(f), return
 // conj(mu)).  f_r = f + r nn, u_r = u + r nn.  Every Arnoldi step advances all entries
 // that have not finished; finished entries skip their work.  info gets nb entries.
@@ -691,6 +889,8 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
     const BatchSkip sk = kb.skip();
     const int pl = precond_launches(p);
     long long launches = 0;
+    const bool graph = (sd->flags & HZS_SOLVE_GRAPH) && !prof;
+    if (graph && !p->gstream) HZS_CUDA(g, cudaStreamCreateWithFlags(&p->gstream, cudaStreamNonBlocking));
     if (prof) {
         hzs_status st = ensure_prof_events(p, sd->maxit);
         if (st != HZS_OK) return st;
@@ -706,16 +906,17 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
     launch_norm_init(cx, kb, nb, sd->tol);
     launches += 3;
     int steps = 0;
-    for (int j = 0; j < sd->maxit; ++j) {
+    // enqueues Arnoldi step j of every entry on cx.stream
+    auto issue_step = [&](int j) -> hzs_status {
         cudaEvent_t* pe = prof ? &p->prof_ev[(size_t)8 * j] : nullptr;
-        if (prof) HZS_CUDA(g, cudaEventRecord(pe[0], s));
+        if (prof) HZS_CUDA(g, cudaEventRecord(pe[0], cx.stream));
         hzs_status st;
         if (orth32) {
             // the complex64 preconditioner reads the leading words of u~_j (the once-projected
             // vector of the previous step, see launch_dcgs2_step) scaled by 1/|u~_j|
             float2* Zj = p->Z + (size_t)j * ld;
             st = precond_apply<float, float2>(p, nb, kb.V32 + (size_t)j * ld, sV, kb.sigt + j, sS, Zj, sZ, sk);
-            if (prof) HZS_CUDA(g, cudaEventRecord(pe[1], s));
+            if (prof) HZS_CUDA(g, cudaEventRecord(pe[1], cx.stream));
             // A z_j as a double-float pair (the FP64 copy of the basis is not used on this path)
             if (!launch_apply_A_df(cx, nb, Zj, sZ, kb.V32 + (size_t)(j + 1) * ld, kb.lo_at(j + 1), sV, sk))
                 launch_apply_A<float2, double2, double>(cx, nb, Zj, sZ, (double2*)nullptr, 0,
@@ -723,29 +924,67 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
         } else if (mixed) {
             float2* Zj = p->Z + (size_t)j * ld;
             st = precond_apply<float, double2>(p, nb, kb.V + (size_t)j * ld, sV, kb.sigma + j, sS, Zj, sZ, sk);
-            if (prof) HZS_CUDA(g, cudaEventRecord(pe[1], s));
+            if (prof) HZS_CUDA(g, cudaEventRecord(pe[1], cx.stream));
             launch_apply_A<float2, double2, double>(cx, nb, Zj, sZ, kb.V + (size_t)(j + 1) * ld, sV, nullptr, 0, sk);
         } else {
             st = precond_apply<double, double2>(p, nb, kb.V + (size_t)j * ld, sV, kb.sigma + j, sS, p->ztmp, ld, sk);
-            if (prof) HZS_CUDA(g, cudaEventRecord(pe[1], s));
+            if (prof) HZS_CUDA(g, cudaEventRecord(pe[1], cx.stream));
             launch_apply_A<double2, double2, double>(cx, nb, p->ztmp, ld, kb.V + (size_t)(j + 1) * ld, sV, nullptr, 0,
                                                      sk);
         }
         if (st != HZS_OK) return st;
-        if (prof) HZS_CUDA(g, cudaEventRecord(pe[2], s));
+        if (prof) HZS_CUDA(g, cudaEventRecord(pe[2], cx.stream));
         if (orth32) launch_dcgs2_step(cx, kb, nb, j, 0, prof ? pe + 4 : nullptr);
         else launch_arnoldi_step(cx, kb, nb, j);
-        if (prof) HZS_CUDA(g, cudaEventRecord(pe[3], s));
+        if (prof) HZS_CUDA(g, cudaEventRecord(pe[3], cx.stream));
         launches += pl + 1 + (orth32 ? (j > 0 ? 6 : 5) : 7);
         steps = j + 1;
         // a launch that could not start (e.g. its resources) must not pass silently
         HZS_CUDA(g, cudaGetLastError());
-        // the host runs one step ahead of the count of running entries it reads back
-        HZS_CUDA(g, cudaMemcpyAsync(&p->h_done[j & 1], kb.active, sizeof(int), cudaMemcpyDeviceToHost, s));
-        HZS_CUDA(g, cudaEventRecord(p->ev[j & 1], s));
-        if (j >= 1) {
-            HZS_CUDA(g, cudaEventSynchronize(p->ev[(j - 1) & 1]));
-            if (p->h_done[(j - 1) & 1] == 0) break;
+        return HZS_OK;
+    };
+    if (!graph) {
+        for (int j = 0; j < sd->maxit; ++j) {
+            const hzs_status st = issue_step(j);
+            if (st != HZS_OK) return st;
+            // the host runs one step ahead of the count of running entries it reads back
+            HZS_CUDA(g, cudaMemcpyAsync(&p->h_done[j & 1], kb.active, sizeof(int), cudaMemcpyDeviceToHost, s));
+            HZS_CUDA(g, cudaEventRecord(p->ev[j & 1], s));
+            if (j >= 1) {
+                HZS_CUDA(g, cudaEventSynchronize(p->ev[(j - 1) & 1]));
+                if (p->h_done[(j - 1) & 1] == 0) break;
+            }
+        }
+    } else {
+        // chunks of kGraphChunk steps: captured on the private stream (the grid's stream may
+        // be the legacy default stream, which cannot be captured), replayed on s
+        for (int j0 = 0, c = 0; j0 < sd->maxit; j0 += kGraphChunk, ++c) {
+            const int j1 = std::min(sd->maxit, j0 + kGraphChunk);
+            cudaGraph_t gr = nullptr;
+            p->cx.stream = p->gstream;
+            cudaError_t e = cudaStreamBeginCapture(p->gstream, cudaStreamCaptureModeRelaxed);
+            hzs_status st = HZS_OK;
+            if (e == cudaSuccess) {
+                for (int j = j0; j < j1 && st == HZS_OK; ++j) st = issue_step(j);
+                const cudaError_t e2 = cudaStreamEndCapture(p->gstream, &gr);
+                e = e2;
+            }
+            p->cx.stream = s;
+            if (st == HZS_OK && e != cudaSuccess) st = cuda_fail(g, e, "capture of the Arnoldi steps");
+            if (st == HZS_OK) {
+                e = graph_replay(j0 == 0 ? &p->gexec_first : &p->gexec[c & 1], gr, s);
+                if (e != cudaSuccess) st = cuda_fail(g, e, "replay of the Arnoldi steps");
+            }
+            if (gr) cudaGraphDestroy(gr);
+            if (st != HZS_OK) return st;
+            // the host runs one chunk ahead of the count of running entries it reads back; the
+            // executable graph of chunk c + 1 is updated only after chunk c - 1 has finished
+            HZS_CUDA(g, cudaMemcpyAsync(&p->h_done[c & 1], kb.active, sizeof(int), cudaMemcpyDeviceToHost, s));
+            HZS_CUDA(g, cudaEventRecord(p->ev[c & 1], s));
+            if (c >= 1) {
+                HZS_CUDA(g, cudaEventSynchronize(p->ev[(c - 1) & 1]));
+                if (p->h_done[(c - 1) & 1] == 0) break;
+            }
         }
     }
     // delayed CGS2: the last column is completed by one more dot pass over the basis
@@ -956,7 +1195,7 @@ hzs_status hzs_internal_noalloc_view(hzs_precond* p, NoAllocView* v, std::string
     v->precision = p->desc.precision;
     v->nc1 = p->hct.nc1;
     v->Nc = p->Nc;
-    v->groups = TileGroups{p->groups_d, p->ngroups, p->group_T};
+    v->groups = tile_groups(p);
     v->max_mx = p->g->max_mx;
     v->max_my = p->g->max_my;
     v->Ainv = p->Ainv;

@@ -62,11 +62,16 @@ struct BatchSkip {
 };
 
 // Subdomain tiles grouped by shared factor: group g solves tiles idx[g*T .. g*T+T-1]
-// (entries -1 are empty); all tiles of a group have the same factor.
+// (entries -1 are empty); all tiles of a group have the same factor.  nst (depth of
+// the factor-block copy ring: 1, 2 or 4) and tpr (threads per block row: 4 or 8)
+// fix the launch shape of the subdomain solve; 0 lets the launch pick (deepest
+// ring that fits, 8 threads per row while a block stays within 1024 threads).
 struct TileGroups {
     const int* idx;
     int count;
     int T;
+    int nst;
+    int tpr;
 };
 
 // Per distinct subdomain factor: representative tile geometry.
@@ -148,6 +153,9 @@ int launch_tile_solve(const Ctx& cx, int nb, const Tile* tiles, TileGroups grp, 
 // Largest number of tiles per group (1 or 2) whose shared-memory footprint fits for
 // tiles of at most max_mx x max_my in arithmetic of size elem_bytes; 0 if none fits.
 int tile_group_width(int max_mx, int max_my, int elem_bytes);
+// The launch shape (T, nst, tpr) that launch_tile_solve uses for grp (resolving zeros
+// as it does); false if that shape does not fit (shared memory, threads per block).
+bool tile_shape_resolve(const TileGroups& grp, int max_mx, int max_my, int elem_bytes, int* T, int* nst, int* tpr);
 
 // ---- krylov.cu
 struct alignas(16) KState {

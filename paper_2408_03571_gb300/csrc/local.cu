@@ -467,15 +467,26 @@ int tile_group_width(int max_mx, int max_my, int elem_bytes) {
     return tile_smem_bytes<double, 1, 1>(max_mx, max_my) <= kSmemLimit ? 1 : 0;
 }
 
+// Threads per block row: tpr 8 or 4 as asked, 0 = 8 while the block stays within 1024
+// threads, else 4; 0 if the asked value does not fit.
+static int resolve_tpr(int tpr, int max_mx) {
+    if (tpr == 0) return max_mx * 8 <= 1024 ? 8 : 4;
+    if (tpr == 8) return max_mx * 8 <= 1024 ? 8 : 0;
+    if (tpr == 4) return max_mx * 4 <= 1024 ? 4 : 0;
+    return 0;
+}
+
 template <typename Cw, typename Cz, typename R, int T, int NST>
 static int launch_tile_solve_t(const Ctx& cx, int nb, const Tile* tiles, TileGroups grp, int max_mx, int max_my,
                                const cplx_t<R>* W, const Cw* w, long long ws, const double* vscale, long long vss,
                                int mode, const cplx_t<R>* c, long long cs, int use_coarse, Cz* z, long long zs,
                                cplx_t<R>* ytiles, long long yts, BatchSkip sk) {
     const size_t smem = tile_smem_bytes<R, T, NST>(max_mx, max_my);
+    const int tpr = resolve_tpr(grp.tpr, max_mx);
+    if (tpr == 0) return -1;
     // eight threads per block row while the block stays within 1024 threads: more warps
     // to hide the per-step latency and half the dependent multiply-adds per thread
-    if (max_mx <= 72) {        // the common tile sizes: a tighter launch bound leaves more registers
+    if (tpr == 8 && max_mx <= 72) {   // the common tile sizes: a tighter launch bound leaves more registers
         auto kern = k_tile_solve<Cw, Cz, R, T, NST, 8, 576>;
         if (allow_dynamic_smem((const void*)kern, smem) != cudaSuccess) return -1;
         const int threads = (max_mx * 8 + 31) / 32 * 32;
@@ -484,7 +495,7 @@ static int launch_tile_solve_t(const Ctx& cx, int nb, const Tile* tiles, TileGro
                                                                 cx.err);
         return 0;
     }
-    if (max_mx * 8 <= 1024) {
+    if (tpr == 8) {
         auto kern = k_tile_solve<Cw, Cz, R, T, NST, 8, 1024>;
         if (allow_dynamic_smem((const void*)kern, smem) != cudaSuccess) return -1;
         const int threads = (max_mx * 8 + 31) / 32 * 32;
@@ -501,22 +512,53 @@ static int launch_tile_solve_t(const Ctx& cx, int nb, const Tile* tiles, TileGro
     return 0;
 }
 
+// Ring depth used for T tiles per group: nst as asked (if it fits), 0 = the deepest of
+// 4, 2 (and 1 for single tiles) that fits; 0 if none fits.
+template <typename R>
+static int resolve_nst(int T, int nst, int max_mx, int max_my) {
+    auto fits = [&](int ns) -> bool {
+        if (T == 2) {
+            if (ns == 4) return tile_smem_bytes<R, 2, 4>(max_mx, max_my) <= kSmemLimit;
+            if (ns == 2) return tile_smem_bytes<R, 2, 2>(max_mx, max_my) <= kSmemLimit;
+            return false;   // pairs of tiles keep at least two stages
+        }
+        if (T != 1) return false;
+        if (ns == 4) return tile_smem_bytes<R, 1, 4>(max_mx, max_my) <= kSmemLimit;
+        if (ns == 2) return tile_smem_bytes<R, 1, 2>(max_mx, max_my) <= kSmemLimit;
+        if (ns == 1) return tile_smem_bytes<R, 1, 1>(max_mx, max_my) <= kSmemLimit;
+        return false;
+    };
+    if (nst != 0) return fits(nst) ? nst : 0;
+    for (int ns : {4, 2, 1})
+        if (fits(ns)) return ns;
+    return 0;
+}
+
+bool tile_shape_resolve(const TileGroups& grp, int max_mx, int max_my, int elem_bytes, int* T, int* nst, int* tpr) {
+    if (max_mx * 4 > 512) return false;
+    const int ns = elem_bytes == (int)sizeof(float2) ? resolve_nst<float>(grp.T, grp.nst, max_mx, max_my)
+                                                     : resolve_nst<double>(grp.T, grp.nst, max_mx, max_my);
+    const int tp = resolve_tpr(grp.tpr, max_mx);
+    if (ns == 0 || tp == 0) return false;
+    *T = grp.T; *nst = ns; *tpr = tp;
+    return true;
+}
+
 template <typename Cw, typename Cz, typename R>
 int launch_tile_solve(const Ctx& cx, int nb, const Tile* tiles, TileGroups grp, int max_mx, int max_my,
                       const cplx_t<R>* W, const Cw* w, long long ws, const double* vscale, long long vss, int mode,
                       const cplx_t<R>* c, long long cs, int use_coarse, Cz* z, long long zs, cplx_t<R>* ytiles,
                       long long yts, BatchSkip sk) {
     if (max_mx * 4 > 512) return -1;
+    // deepest ring of factor-block stages that fits (more stages hide the L2 latency of
+    // the copies), unless the group fixes the depth
+    const int nst = resolve_nst<R>(grp.T, grp.nst, max_mx, max_my);
 #define HZS_TRY(TT, NS)                                                                                        \
-    if (tile_smem_bytes<R, TT, NS>(max_mx, max_my) <= kSmemLimit)                                             \
+    if (grp.T == TT && nst == NS)                                                                             \
         return launch_tile_solve_t<Cw, Cz, R, TT, NS>(cx, nb, tiles, grp, max_mx, max_my, W, w, ws, vscale, vss, \
                                                       mode, c, cs, use_coarse, z, zs, ytiles, yts, sk);
-    if (grp.T == 2) {
-        // deepest ring of factor-block stages that fits: more stages hide the L2 latency of the copies
-        HZS_TRY(2, 4)
-        HZS_TRY(2, 2)
-        return -1;
-    }
+    HZS_TRY(2, 4)
+    HZS_TRY(2, 2)
     HZS_TRY(1, 4)
     HZS_TRY(1, 2)
     HZS_TRY(1, 1)

@@ -31,7 +31,7 @@ EXPORTS = (
     "hzs_grid_create", "hzs_grid_destroy", "hzs_precond_setup", "hzs_precond_destroy",
     "hzs_apply_operator", "hzs_apply_precond", "hzs_solve", "hzs_adjoint_solve",
     "hzs_kappa_gradient", "hzs_status_string", "hzs_last_error", "hzs_version",
-    "hzs_apply_precond_noalloc", "hzs_solve_batched",
+    "hzs_apply_precond_noalloc", "hzs_solve_batched", "hzs_precond_get_info",
 )
 
 
@@ -42,12 +42,24 @@ class GridDesc(ct.Structure):
 
 class PrecondDesc(ct.Structure):
     _fields_ = [("kind", ct.c_int), ("coarse", ct.c_int), ("coarse_ratio", ct.c_int),
-                ("precision", ct.c_int), ("dedup_tiles", ct.c_int), ("coarse_solver", ct.c_int)]
+                ("precision", ct.c_int), ("dedup_tiles", ct.c_int), ("coarse_solver", ct.c_int),
+                ("autotune", ct.c_int)]
+
+
+class PrecondInfo(ct.Structure):
+    _fields_ = [("nfactors", ct.c_int), ("coarse_unknowns", ct.c_int), ("coarse_solver", ct.c_int),
+                ("coarse_min_pivot", ct.c_double), ("tile_group", ct.c_int), ("tile_stages", ct.c_int),
+                ("tile_threads_per_row", ct.c_int), ("autotuned", ct.c_int), ("apply_us_default", ct.c_double),
+                ("apply_us_tuned", ct.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 SOLVE_PROFILE = 1
 SOLVE_ORTH_FP64 = 2
 SOLVE_BASIS_WIDE = 4
+SOLVE_GRAPH = 8
 
 
 class SolveDesc(ct.Structure):
@@ -97,6 +109,7 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.hzs_solve_batched.argtypes = [ct.c_int, ct.POINTER(P), ct.POINTER(SolveDesc), ct.POINTER(P), ct.POINTER(P),
                                       ct.POINTER(ct.c_int), ct.POINTER(SolveInfo)]
     lib.hzs_kappa_gradient.argtypes = [P, P, P, P]
+    lib.hzs_precond_get_info.argtypes = [P, ct.POINTER(PrecondInfo)]
     lib.hzs_status_string.argtypes = [ct.c_int]
     lib.hzs_status_string.restype = ct.c_char_p
     lib.hzs_last_error.argtypes = [P]
@@ -188,11 +201,13 @@ class Preconditioner:
     """Factorised Schwarz preconditioner (Sections 3-4) on a Grid."""
 
     def __init__(self, grid: Grid, kind: int = SHS2, coarse: int = COARSE_B2, coarse_ratio: int = 2,
-                 precision: int = FP64, dedup_tiles: bool = True, coarse_solver: int = 0):
+                 precision: int = FP64, dedup_tiles: bool = True, coarse_solver: int = 0, autotune: int = 0):
+        """autotune: 0 = default launch shape of the subdomain solve, 1 = pick it by timing at
+        set-up (reusing an earlier choice for the same problem size), 2 = always re-time."""
         lib = load()
         self.grid = grid
         self.kind, self.coarse, self.coarse_ratio, self.precision = kind, coarse, coarse_ratio, precision
-        d = PrecondDesc(kind, coarse, coarse_ratio, precision, int(dedup_tiles), int(coarse_solver))
+        d = PrecondDesc(kind, coarse, coarse_ratio, precision, int(dedup_tiles), int(coarse_solver), int(autotune))
         h = ct.c_void_p()
         _check(lib.hzs_precond_setup(grid.handle, ct.byref(d), ct.byref(h)), grid.handle)
         self._h = h
@@ -219,13 +234,19 @@ class Preconditioner:
         _check(load().hzs_apply_precond(self._h, v.data_ptr(), z.data_ptr(), nrhs), self.grid.handle)
         return z
 
-    def _solve(self, fn, f, tol, maxit, out, profile, orth_fp64=False, wide_basis=False):
+    def info(self) -> dict:
+        """What set-up built and chose (hzs_precond_get_info)."""
+        out = PrecondInfo()
+        _check(load().hzs_precond_get_info(self._h, ct.byref(out)), self.grid.handle)
+        return out.as_dict()
+
+    def _solve(self, fn, f, tol, maxit, out, profile, orth_fp64=False, wide_basis=False, graph=False):
         f = _dev_c128(f, self.n, "f")
         u = torch.empty_like(f) if out is None else out
         nrhs = f.numel() // (self.n * self.n)
         infos = (SolveInfo * max(nrhs, 1))()
         flags = ((SOLVE_PROFILE if profile else 0) | (SOLVE_ORTH_FP64 if orth_fp64 else 0)
-                 | (SOLVE_BASIS_WIDE if wide_basis else 0))
+                 | (SOLVE_BASIS_WIDE if wide_basis else 0) | (SOLVE_GRAPH if graph else 0))
         sd = SolveDesc(float(tol), int(maxit), flags)
         _check(fn(self._h, ct.byref(sd), f.data_ptr(), u.data_ptr(), nrhs, infos), self.grid.handle,
                allow=(OK, NOT_CONVERGED))
@@ -236,17 +257,19 @@ class Preconditioner:
         return u, res
 
     def solve(self, f: torch.Tensor, tol: float = 1e-6, maxit: int = 1000, out=None, profile: bool = False,
-              orth_fp64: bool = False, wide_basis: bool = False):
+              orth_fp64: bool = False, wide_basis: bool = False, graph: bool = False):
         """u = A^{-1} f by preconditioned GMRES; returns (u, [SolveResult per right-hand side]).
 
         orth_fp64: with a MIXED preconditioner, orthogonalise with the all-FP64 CGS2.
         wide_basis: keep the double-float basis at about 48 bits even for tol >= 1e-7
-        (where it otherwise stores bf16 remainders, about 32 bits)."""
-        return self._solve(load().hzs_solve, f, tol, maxit, out, profile, orth_fp64, wide_basis)
+        (where it otherwise stores bf16 remainders, about 32 bits).
+        graph: issue the Arnoldi steps as replayed CUDA graphs of 8 steps each."""
+        return self._solve(load().hzs_solve, f, tol, maxit, out, profile, orth_fp64, wide_basis, graph)
 
-    def adjoint_solve(self, g: torch.Tensor, tol: float = 1e-6, maxit: int = 1000, out=None, profile: bool = False):
+    def adjoint_solve(self, g: torch.Tensor, tol: float = 1e-6, maxit: int = 1000, out=None, profile: bool = False,
+                      graph: bool = False):
         """lambda = conj(A)^{-1} g; returns (lambda, results)."""
-        return self._solve(load().hzs_adjoint_solve, g, tol, maxit, out, profile)
+        return self._solve(load().hzs_adjoint_solve, g, tol, maxit, out, profile, graph=graph)
 
     def kappa_gradient(self, u: torch.Tensor, lam: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
         u = _dev_c128(u, self.n, "u")
@@ -268,7 +291,7 @@ class Preconditioner:
 
 
 def solve_batched(problems, rhs, tol: float = 1e-6, maxit: int = 1000, orth_fp64: bool = False,
-                  wide_basis: bool = False):
+                  wide_basis: bool = False, graph: bool = False):
     """Batched solve over several problems: ``problems`` is a list of Preconditioner
     handles (distinct), ``rhs`` a matching list of complex128 tensors of shape
     (nrhs_k, n_k, n_k).  Returns (list of solutions, list of lists of SolveResult)."""
@@ -285,7 +308,8 @@ def solve_batched(problems, rhs, tol: float = 1e-6, maxit: int = 1000, orth_fp64
     infos = (SolveInfo * max(total, 1))()
     arr = lambda vals: (ct.c_void_p * max(k, 1))(*vals)
     sd = SolveDesc(float(tol), int(maxit),
-                   (SOLVE_ORTH_FP64 if orth_fp64 else 0) | (SOLVE_BASIS_WIDE if wide_basis else 0))
+                   (SOLVE_ORTH_FP64 if orth_fp64 else 0) | (SOLVE_BASIS_WIDE if wide_basis else 0)
+                   | (SOLVE_GRAPH if graph else 0))
     st = lib.hzs_solve_batched(k, arr([P.handle.value for P in problems]), ct.byref(sd),
                                arr([f.data_ptr() for f in rhs]), arr([u.data_ptr() for u in outs]),
                                (ct.c_int * max(k, 1))(*counts), infos)

@@ -45,9 +45,9 @@ def parse():
                     help="skip the arm whose Krylov basis keeps complex64 remainders (about 48 bits)")
     ap.add_argument("--no-dedup-arm", action="store_true",
                     help="skip the MIXED arm with every subdomain factored separately")
-    ap.add_argument("--stream", action="store_true",
-                    help="issue the Arnoldi steps as stream launches (default: CUDA graphs of 8 steps, "
-                         "HZS_SOLVE_GRAPH); the other issue mode is timed beside the value")
+    ap.add_argument("--graph", action="store_true",
+                    help="issue the Arnoldi steps as CUDA graphs of 8 steps (HZS_SOLVE_GRAPH; default: "
+                         "stream launches); the other issue mode is timed beside the value")
     ap.add_argument("--no-alt-arm", action="store_true",
                     help="skip the solves issued the other way (stream launches vs CUDA graphs)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -398,7 +398,7 @@ def gpu_arm(args, world, rank, local):
     clocks = clk.stop()
     # the same solves with CUDA events around every launch: phase times and the roofline
     ms_prof, infos, _ = timed_solves(Pm, args.steps, 0, profile=True)
-    # the other way of issuing the Arnoldi steps (stream launches, or graphs with --stream)
+    # the other way of issuing the Arnoldi steps (CUDA graphs, or stream launches with --graph)
     issue_alt = None
     if not args.no_alt_arm:
         ms_alt, infos_alt, _ = timed_solves(Pm, args.steps, 1, graph=not args.graph)
@@ -490,7 +490,7 @@ def gpu_arm(args, world, rank, local):
     # scaled by those ratios.  None: no capture of the current kernel.
     dot_ratio = (1.021, "430.9 MB against 421.9 MB")
     traffic_ratio = {16: {"dot": dot_ratio, "upd": None},
-                     12: {"dot": dot_ratio, "upd": (1.079, "689.8 MB against 639.2 MB")}}[eb]
+                     12: {"dot": dot_ratio, "upd": (1.079, "689.7 MB against 639.2 MB")}}[eb]
     for r_, nbytes, nl, key in ((r_dot, dot_bytes, it + 1, "dot"), (r_upd, upd_bytes, it, "upd")):
         r_["launches"] = nl
         r_["bytes_per_launch"] = nbytes / nl
@@ -563,7 +563,6 @@ def gpu_arm(args, world, rank, local):
 
 def main():
     args = parse()
-    args.graph = not args.stream
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         reference_arm(args, world, rank)

@@ -45,9 +45,9 @@ def parse():
                     help="skip the arm whose Krylov basis keeps complex64 remainders (about 48 bits)")
     ap.add_argument("--no-dedup-arm", action="store_true",
                     help="skip the MIXED arm with every subdomain factored separately")
-    ap.add_argument("--graph", action="store_true",
-                    help="issue the Arnoldi steps as CUDA graphs of 8 steps (HZS_SOLVE_GRAPH; default: "
-                         "stream launches); the other issue mode is timed beside the value")
+    ap.add_argument("--stream", action="store_true",
+                    help="issue the Arnoldi steps as stream launches (default: CUDA graphs of 8 steps, "
+                         "HZS_SOLVE_GRAPH); the other issue mode is timed beside the value")
     ap.add_argument("--no-alt-arm", action="store_true",
                     help="skip the solves issued the other way (stream launches vs CUDA graphs)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -398,7 +398,7 @@ def gpu_arm(args, world, rank, local):
     clocks = clk.stop()
     # the same solves with CUDA events around every launch: phase times and the roofline
     ms_prof, infos, _ = timed_solves(Pm, args.steps, 0, profile=True)
-    # the other way of issuing the Arnoldi steps (CUDA graphs, or stream launches with --graph)
+    # the other way of issuing the Arnoldi steps (stream launches, or graphs with --stream)
     issue_alt = None
     if not args.no_alt_arm:
         ms_alt, infos_alt, _ = timed_solves(Pm, args.steps, 1, graph=not args.graph)
@@ -563,6 +563,7 @@ def gpu_arm(args, world, rank, local):
 
 def main():
     args = parse()
+    args.graph = not args.stream
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         reference_arm(args, world, rank)

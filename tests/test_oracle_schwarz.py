@@ -2,6 +2,8 @@
 
 * sum_i R_i^T D_i R_i = I (Section 3) and each node lies in at most 4
   subdomains at the largest overlap the paper's experiments use;
+* a subdomain is its owned piece grown by `overlap` layers of grid nodes
+  (brute-force dilation on the grid), and the owned pieces tile the unknowns;
 * AS1, AS2 (Eq. 4), SAS2 (Eq. 5) and SHS2 (Eq. 6) equal the dense formulas
   built from explicit 0/1 matrices and numpy inverses;
 * coarse-correction algebra: Q A Q = Q, R_0 (I - A Q) = 0, Q unchanged when
@@ -45,6 +47,42 @@ def test_partition_identity(bc, ns, ov):
     w = (n - 1) // ns
     if 2 * ov <= w:
         assert mult.max() <= 4
+
+
+@pytest.mark.parametrize("bc", [DIRICHLET, SOMMERFELD])
+@pytest.mark.parametrize("ns,ov", [(2, 1), (4, 2), (3, 3), (4, 0)])
+def test_overlap_is_layers_of_nodes_on_every_side(bc, ns, ov):
+    """Section 3 extends each nonoverlapping piece by layers of grid nodes: ov rounds of
+    adding every unknown adjacent (including diagonally) to the current node set, found
+    here by brute-force dilation of the owned nodes on the grid."""
+    n = 25
+    prob = Problem(n, bc, 10.0)
+    dec = Decomposition(prob, ns, ov)
+    unknown = np.zeros((n, n), dtype=bool)
+    unknown[prob.lo:prob.hi + 1, prob.lo:prob.hi + 1] = True
+    owner_count = np.zeros((n, n), dtype=int)
+    for s in dec.subs:
+        owned = np.zeros((n, n), dtype=bool)               # [j, i]
+        for q, dq in zip(s.idx, s.d):
+            if dq:
+                owned[prob.lo + q // prob.m, prob.lo + q % prob.m] = True
+        owner_count += owned
+        grown = owned.copy()
+        for _ in range(ov):
+            nxt = grown.copy()
+            for dj in (-1, 0, 1):
+                for di in (-1, 0, 1):
+                    sh = np.zeros_like(grown)
+                    sh[max(dj, 0):n + min(dj, 0), max(di, 0):n + min(di, 0)] = \
+                        grown[max(-dj, 0):n + min(-dj, 0), max(-di, 0):n + min(-di, 0)]
+                    nxt |= sh
+            grown = nxt & unknown
+        member = np.zeros((n, n), dtype=bool)
+        for q in s.idx:
+            member[prob.lo + q // prob.m, prob.lo + q % prob.m] = True
+        assert np.array_equal(member, grown)
+    # the owned pieces tile the unknowns (a nonoverlapping decomposition)
+    assert np.array_equal(owner_count, unknown.astype(int))
 
 
 @pytest.mark.parametrize("bc", [DIRICHLET, SOMMERFELD])

@@ -48,3 +48,24 @@ def test_invalid_grid_rejected_without_gpu(lib):
         assert lib.hzs_grid_create(ctypes.byref(d), None, ctypes.byref(h)) == hzs.ERR_INVALID_ARG
         assert h.value is None
         assert len(lib.hzs_last_error(None)) > 0
+
+
+def test_null_handles_rejected_without_gpu(lib):
+    """Every entry point that takes a handle rejects NULL with HZS_ERR_INVALID_ARG before any CUDA call."""
+    from paper_2408_03571_gb300 import hzs
+    info = hzs.PrecondInfo()
+    assert lib.hzs_precond_get_info(None, ctypes.byref(info)) == hzs.ERR_INVALID_ARG
+    sd = hzs.SolveDesc(1e-6, 10, 0)
+    si = (hzs.SolveInfo * 1)()
+    assert lib.hzs_solve(None, ctypes.byref(sd), None, None, 1, si) == hzs.ERR_INVALID_ARG
+    assert lib.hzs_adjoint_solve(None, ctypes.byref(sd), None, None, 1, si) == hzs.ERR_INVALID_ARG
+    assert lib.hzs_apply_operator(None, None, None, 1) == hzs.ERR_INVALID_ARG
+    assert lib.hzs_apply_precond(None, None, None, 1) == hzs.ERR_INVALID_ARG
+    assert lib.hzs_apply_precond_noalloc(None, None, None, 1) == hzs.ERR_INVALID_ARG
+    assert lib.hzs_kappa_gradient(None, None, None, None) == hzs.ERR_INVALID_ARG
+    out = ctypes.c_void_p()
+    d = hzs.PrecondDesc(hzs.SHS2, hzs.COARSE_B2, 4, hzs.FP64, 1, 0, 0)
+    assert lib.hzs_precond_setup(None, ctypes.byref(d), ctypes.byref(out)) == hzs.ERR_INVALID_ARG
+    assert out.value is None
+    lib.hzs_precond_destroy(None)
+    lib.hzs_grid_destroy(None)

@@ -1,7 +1,8 @@
 """Full-size checks of the CUDA path at the sizes the benchmark runs (needs a GB300).
 
 MP-1, k = 100, n = 1025 (16 x 16 subdomains, overlap 2, SHS2 / B_2 with H = 1/32,
-tol 1e-6), in both precisions:
+tol 1e-6), in both precisions, and in the benchmark's configuration (mixed precision,
+graph-issued Arnoldi steps, autotuned subdomain-solve shape):
   * the operator and one preconditioner apply equal the oracle's, element by
     element (oracle set-up at this size takes seconds);
   * the returned u has ||f - A u|| <= tol ||f|| with the oracle's matrix;
@@ -70,11 +71,14 @@ def mp1_full():
     return n, k, prob, A, M
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_mp1_headline_size(hzs, mp1_full, prec):
+# (precision, issue): FP64 and mixed stream-issued with the default subdomain-solve shape,
+# and the benchmark's own configuration: mixed, graph-issued steps, autotuned shape
+@pytest.mark.parametrize("prec,bench_cfg", [(0, False), (1, False), (1, True)],
+                         ids=["fp64", "mixed", "mixed-graph-autotune"])
+def test_mp1_headline_size(hzs, mp1_full, prec, bench_cfg):
     n, k, prob, A, M = mp1_full
     g = hzs.Grid(n, hzs.DIRICHLET, k=k, nsub=16, overlap=2)
-    P = hzs.Preconditioner(g, hzs.SHS2, hzs.COARSE_B2, 32, prec)
+    P = hzs.Preconditioner(g, hzs.SHS2, hzs.COARSE_B2, 32, prec, autotune=1 if bench_cfg else 0)
     v = random_complex_grid(n, seed=77)
     vd = dev(v)
     y = P.apply_operator(vd).cpu().numpy()
@@ -83,7 +87,7 @@ def test_mp1_headline_size(hzs, mp1_full, prec):
     zr = M.apply(prob.grid_to_vec(v))
     assert rel(prob.grid_to_vec(z), zr) < (1e-9 if prec == 0 else 1e-4)
     f = point_source(n)
-    u, info = P.solve(dev(f), tol=1e-6, maxit=1000)
+    u, info = P.solve(dev(f), tol=1e-6, maxit=1000, graph=bench_cfg)
     assert info[0].converged
     uv = prob.grid_to_vec(u.cpu().numpy())
     fv = prob.grid_to_vec(f)

@@ -13,7 +13,8 @@ of terms.
 
 * Section 2 (Eqs. 1-3): Sommerfeld term with the wrong sign; edge rows not
   halved; the -kappa term dropped; neighbour couplings with the wrong sign;
-  d A_PP / d kappa with the wrong sign or without its boundary part;
+  d A_PP / d kappa with the wrong sign or without its boundary part; the kappa
+  field read with x and y swapped;
 * Section 3: D_i = 1 on the whole subdomain; overlap added on one side only;
   local solves with conj(A_i);
 * Section 4: B_2 shifted by half a cell; a wrong middle piece of the quadratic
@@ -131,6 +132,13 @@ def dkappa_no_boundary_part(mp):
     return [(tp.test_dA_dkappa_matches_difference, ())]
 
 
+def kappa_field_transposed(mp):
+    plant(mp, Problem, "diag_entry", ("self.kappa[j, i]", "self.kappa[i, j]"))
+    plant(mp, Problem, "ddiag_dkappa", ("self.kappa[j, i]", "self.kappa[i, j]"))
+    plant(mp, Problem, "assemble_fast", ("kap = self.kappa[jj, ii]", "kap = self.kappa[ii, jj]"))
+    return [(tp.test_dA_dkappa_matches_difference, ()), (tp.test_assembly_paths_agree, (SOMMERFELD, 9, True))]
+
+
 # ---- Section 3 ---------------------------------------------------------------------
 
 def d_is_identity(mp):
@@ -230,7 +238,7 @@ def adjoint_without_conjugate(mp):
 
 MUTATIONS = [
     sommerfeld_sign, edge_rows_not_halved, kappa_dropped, coupling_sign, dkappa_sign,
-    dkappa_no_boundary_part, d_is_identity, overlap_one_sided, local_solve_conjugated,
+    dkappa_no_boundary_part, kappa_field_transposed, d_is_identity, overlap_one_sided, local_solve_conjugated,
     b2_half_cell_shift, b2_middle_piece, p1_hat_too_wide, mp1_keeps_coarse_boundary, galerkin_of_conj,
     shs2_deflation_sign, sas2_without_d, as2_without_q, givens_sine_conjugated,
     gram_schmidt_conjugate_side, solution_without_preconditioner, gradient_sign, adjoint_without_conjugate,

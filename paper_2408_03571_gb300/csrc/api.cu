@@ -4,7 +4,11 @@
 // the matrix-vector product and the CGS2 / Givens kernels on the handle's
 // stream.  The host keeps one step in flight ahead of the convergence flag it
 // reads back (pinned memory, one event per step), and every kernel of a step
-// that is enqueued after convergence returns immediately.
+// that is enqueued after convergence returns immediately.  With HZS_SOLVE_GRAPH
+// the same launches are captured 8 steps at a time into a CUDA graph that is
+// replayed on the handle's stream (one chunk in flight ahead of the flag).
+// Set-up can time the launch shapes of the subdomain solve and keep the fastest
+// (the autotuner below).
 #include <cmath>
 #include <cstdio>
 #include <cstring>

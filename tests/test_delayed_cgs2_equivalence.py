@@ -1,0 +1,161 @@
+"""The delayed CGS2 Arnoldi process of the mixed-precision GPU solve is flexible GMRES.
+
+The GPU's mixed path does not run the paper's GMRES (Section 5) step for step. It
+postpones the reorthogonalisation of basis vector j to step j+1, where it shares one
+pass over the basis with the first projection of the new vector (the delayed
+classical Gram-Schmidt of Bielich et al., Parallel Computing 2022). It also applies
+the preconditioner to the once-projected vector u~_j / |u~_j| rather than to the
+finished q_j. Because u~_j = beta_j q_j + Q alpha and M is linear,
+span{z_0..z_j} = span{M q_0..M q_j}. The least-squares problem therefore has the
+same minimiser, and in exact arithmetic the iterates are those of flexible GMRES.
+
+This test restates that process in plain FP64 NumPy and checks the claim against
+the oracle's flexible GMRES. Per step j, with Q = [q_0..q_{j-1}]:
+
+  z_j = M(u~_j / |u~_j|),  w = A z_j
+  alpha = Q^H u~_j,  b = Q^H w,  c = |u~_j|^2,  d = u~_j^H w
+  beta_j = sqrt(c - |alpha|^2),  q_j = (u~_j - Q alpha) / beta_j
+  column j-1 of H: h1_{j-1} + alpha, subdiagonal beta_j
+  first projection of column j: h1_j = [b, (d - alpha^H b) / beta_j]
+  u~_{j+1} = w - [Q q_j] h1_j
+
+The CPU restatement gives the same residual history as the oracle's flexible GMRES
+(to rounding), the same step count and the same solution.  With its dot products in
+complex64, as on the GPU, it still takes FGMRES's steps and its estimate stays the
+true residual, because the column it records is the one its update applies; leaving
+the reorthogonalisation coefficients out of that column is caught.
+"""
+import numpy as np
+import pytest
+
+from oracle import B2, DIRICHLET, SHS2, SOMMERFELD, Problem, Schwarz, givens, gmres
+from paper_2408_03571_gb300.inputs import kappa_field, point_source
+
+
+def _c64(a):
+    return np.asarray(a).astype(np.complex64)
+
+
+def delayed_cgs2_fgmres(A_apply, M_apply, f, tol, maxit, c64_dots=False, record_alpha=True):
+    """FP64 restatement of the delayed-CGS2 flexible GMRES; returns (x, steps, history, Q).
+
+    c64_dots: form alpha, b, c and d from complex64 roundings of the vectors with
+    single-precision sums, as the GPU's dot pass does on the basis's leading words (the
+    updates stay FP64).  record_alpha=False plants a mistake: the reorthogonalisation
+    coefficients are applied to the basis but left out of the recorded Hessenberg column."""
+    def dot(X, y):
+        if c64_dots:
+            return (_c64(X).conj().T @ _c64(y)).astype(np.complex128)
+        return X.conj().T @ y
+    beta0 = np.linalg.norm(f)
+    Q = np.zeros((f.size, 0), dtype=np.complex128)
+    Z = []
+    H = np.zeros((maxit + 1, maxit), dtype=np.complex128)
+    cs = np.zeros(maxit)
+    sn = np.zeros(maxit, dtype=np.complex128)
+    g = np.zeros(maxit + 1, dtype=np.complex128)
+    g[0] = beta0
+    hist = []
+    u = f.astype(np.complex128)            # u~_0: nothing to project against yet
+    h1_prev = None
+    steps = 0
+
+    def rotate_column(j):
+        for i in range(j):
+            t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+            H[i + 1, j] = -np.conj(sn[i]) * H[i, j] + cs[i] * H[i + 1, j]
+            H[i, j] = t
+        c, s = givens(H[j, j], H[j + 1, j])
+        cs[j], sn[j] = c, s
+        H[j, j] = c * H[j, j] + s * H[j + 1, j]
+        H[j + 1, j] = 0.0
+        g[j + 1] = -np.conj(s) * g[j]
+        g[j] = c * g[j]
+        return abs(g[j + 1]) / beta0
+
+    for j in range(maxit + 1):
+        last = j == maxit
+        z = None
+        if not last:
+            z = M_apply(u / np.linalg.norm(u))
+            w = A_apply(z)
+        alpha = dot(Q, u)
+        c = dot(u[:, None], u)[0].real
+        beta = np.sqrt(c - np.vdot(alpha, alpha).real)
+        qj = (u - Q @ alpha) / beta
+        if j > 0:                                     # column j-1 is complete
+            H[:j, j - 1] = h1_prev + alpha if record_alpha else h1_prev
+            H[j, j - 1] = beta
+            hist.append(rotate_column(j - 1))
+            steps = j
+            if hist[-1] <= tol:
+                break
+        if last:
+            break
+        Z.append(z)
+        b = dot(Q, w)
+        d = dot(u[:, None], w)[0]
+        h1 = np.concatenate([b, [(d - np.vdot(alpha, b)) / beta]])
+        Q = np.column_stack([Q, qj])
+        u = w - Q @ h1                                # u~_{j+1}
+        h1_prev = h1
+    m = steps
+    y = np.zeros(m, dtype=np.complex128)
+    for i in range(m - 1, -1, -1):
+        y[i] = (g[i] - H[i, i + 1:m] @ y[i + 1:m]) / H[i, i]
+    x = sum(y[i] * Z[i] for i in range(m))
+    return x, m, hist, Q
+
+
+@pytest.mark.parametrize("bc", [DIRICHLET, SOMMERFELD])
+def test_delayed_cgs2_is_flexible_gmres(bc):
+    n = 33
+    prob = Problem(n, bc, kappa_field(n, 18.0, seed=31))
+    A = prob.assemble_fast()
+    M = Schwarz(prob, A, 4, 2, SHS2, B2, 8)
+    f = prob.grid_to_vec(point_source(n))
+    ref = gmres(lambda x: A @ x, M.apply, f, 1e-10, 80, flexible=True)
+    x, steps, hist, _ = delayed_cgs2_fgmres(lambda v: A @ v, M.apply, f, 1e-10, 80)
+    assert ref.converged and steps == ref.iterations
+    for a, b in zip(hist, ref.resid_hist):
+        assert a == pytest.approx(b, rel=1e-6 if b > 1e-8 else 1e-3)
+    assert np.linalg.norm(x - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+    assert np.linalg.norm(f - A @ x) <= 1.01e-10 * np.linalg.norm(f)
+
+
+def test_delayed_cgs2_stopped_by_maxit():
+    """A run cut by the step cap completes its last column with one more dot pass."""
+    n = 33
+    prob = Problem(n, SOMMERFELD, 400.0)
+    A = prob.assemble_fast()
+    M = Schwarz(prob, A, 4, 2, SHS2, B2, 8)
+    f = prob.grid_to_vec(point_source(n))
+    ref = gmres(lambda x: A @ x, M.apply, f, 1e-14, 6, flexible=True)
+    x, steps, hist, _ = delayed_cgs2_fgmres(lambda v: A @ v, M.apply, f, 1e-14, 6)
+    assert steps == ref.iterations == 6 and not ref.converged
+    assert hist == pytest.approx(ref.resid_hist, rel=1e-9)
+    assert np.linalg.norm(x - ref.x) <= 1e-9 * np.linalg.norm(ref.x)
+
+
+@pytest.mark.parametrize("bc,k,n,tol", [(DIRICHLET, 18.0, 33, 1e-8), (SOMMERFELD, 18.0, 33, 1e-6),
+                                        (SOMMERFELD, 30.0, 65, 1e-8)])
+def test_complex64_coefficients_keep_the_arnoldi_relation(bc, k, n, tol):
+    """With the dot products in complex64 (the GPU's dot pass) the coefficients are
+    inexact, but the update applies exactly the coefficients the Hessenberg column
+    records, so A Z = Q H holds and the GMRES estimate stays the true residual; the
+    basis stays orthogonal to about 1e-7 and the step count is FP64 FGMRES's.  Leaving
+    the reorthogonalisation coefficients out of the recorded column (applied, but not
+    recorded) breaks that: the true residual then stalls far above the estimate."""
+    prob = Problem(n, bc, kappa_field(n, k, seed=31))
+    A = prob.assemble_fast()
+    M = Schwarz(prob, A, 4, 2, SHS2, B2, 8)
+    f = prob.grid_to_vec(point_source(n))
+    ref = gmres(lambda x: A @ x, M.apply, f, tol, 200, flexible=True)
+    x, steps, hist, Q = delayed_cgs2_fgmres(lambda v: A @ v, M.apply, f, tol, 200, c64_dots=True)
+    true = np.linalg.norm(f - A @ x) / np.linalg.norm(f)
+    assert abs(steps - ref.iterations) <= 1
+    assert hist[-1] <= tol and true <= 1.05 * tol
+    assert abs(true - hist[-1]) <= 0.05 * tol
+    assert np.linalg.norm(np.eye(Q.shape[1]) - Q.conj().T @ Q, 2) <= 1e-5
+    xb, _, hb, _ = delayed_cgs2_fgmres(lambda v: A @ v, M.apply, f, tol, 200, c64_dots=True, record_alpha=False)
+    assert hb[-1] <= tol and np.linalg.norm(f - A @ xb) / np.linalg.norm(f) > 5 * tol

@@ -120,3 +120,18 @@ def test_table_grid_counts():
         assert k / inv_h == pytest.approx(0.25)                    # kappa_h = 0.25
         W = basis_1d(B2, n, p, keep_ends=True)
         assert W.shape[0] ** 2 == GH
+
+
+@pytest.mark.parametrize("p", [2, 3, 4, 8, 16, 32])
+def test_each_fine_node_meets_few_coarse_functions(p):
+    """Every fine node lies in the support of at most 3 B_2 functions and at most 2 P_1
+    hats per axis (B_2 is supported on 3 coarse cells, a hat on 2), and those coarse
+    indices are consecutive: per axis a node needs its first coarse index and up to three
+    weights, which is how the GPU's restriction and prolongation tables store R_0."""
+    n = 8 * p + 1
+    for kind, most in ((B2, 3), (P1, 2)):
+        W = basis_1d(kind, n, p, keep_ends=True)
+        for i in range(n):
+            nz = np.nonzero(W[:, i])[0]
+            assert 1 <= len(nz) <= most
+            assert np.array_equal(nz, np.arange(nz[0], nz[0] + len(nz)))

@@ -8,7 +8,8 @@
 * R_0 equals the brute-force tensor product phi_I(x_i) phi_J(y_j);
 * A_0 has the same size for P_1 and B_2; its interior stencil has 9 points
   for P_1 and 25 for B_2 (Section 4, "lower sparseness");
-* grid and coarse-grid node counts of Tables 1-2 (golden fixture).
+* grid and coarse-grid node counts of Tables 1-2 (golden fixture);
+* each fine node meets at most 3 consecutive B_2 (2 P_1) functions per axis.
 """
 import os
 

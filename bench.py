@@ -258,7 +258,8 @@ def batched_arm(args, world, rank, local):
     grids, precs, rhs_host, rhs = [], [], [], []
     t0 = time.perf_counter()
     for i, (k, n, nsub) in enumerate(BATCHED):
-        g = hzs.Grid(n, hzs.SOMMERFELD, k=k, nsub=nsub, overlap=2)
+        # a stream per problem, so that the problems' kernels overlap on the GPU
+        g = hzs.Grid(n, hzs.SOMMERFELD, k=k, nsub=nsub, overlap=2, stream=torch.cuda.Stream(dev))
         grids.append(g)
         precs.append(hzs.Preconditioner(g, hzs.SHS2, hzs.COARSE_B2, 32, hzs.MIXED,
                                         autotune=0 if args.no_autotune else 1))
@@ -287,6 +288,7 @@ def batched_arm(args, world, rank, local):
     e0.record(stream)
     for _ in range(args.steps):
         fd = [f.to(dev, non_blocking=True) for f in rhs_host]
+        stream.synchronize()            # the copies ran on this stream; the solves run on the problems'
         outs, _ = hzs.solve_batched(precs, fd, TOL, MAXIT, graph=args.graph)
         for u in outs:
             u.cpu()

@@ -355,3 +355,24 @@ def test_long_run_estimate_matches_true_residual(hzs):
     assert info[0].converged and info[0].iterations > 766
     assert info[0].relres_true <= 1.01e-6
     assert abs(info[0].relres_est - info[0].relres_true) <= 1e-8
+
+
+def test_size_limits_rejected(hzs):
+    """Configurations beyond the solver's limits fail at set-up with HZS_ERR_INVALID_ARG and
+    a message, before any kernel runs: a subdomain tile wider than the shared-memory tile
+    solve takes (112 nodes per axis), a coarse space above the dense inverse's 8192
+    unknowns, a coarse ratio that does not divide n - 1."""
+    g = hzs.Grid(257, hzs.DIRICHLET, k=10.0, nsub=2, overlap=2)            # tiles of 129 nodes
+    with pytest.raises(hzs.HzsError) as e:
+        hzs.Preconditioner(g, hzs.AS1, hzs.COARSE_NONE, 2, hzs.FP64)
+    assert e.value.status == hzs.ERR_INVALID_ARG and "larger than 112" in str(e.value)
+    g2 = hzs.Grid(513, hzs.SOMMERFELD, k=10.0, nsub=64, overlap=1)          # 129^2 coarse unknowns at H = 4h
+    with pytest.raises(hzs.HzsError) as e:
+        hzs.Preconditioner(g2, hzs.SHS2, hzs.COARSE_B2, 4, hzs.FP64, coarse_solver=hzs.COARSE_SOLVER_DENSE)
+    assert e.value.status == hzs.ERR_INVALID_ARG and "8192" in str(e.value)
+    g3 = hzs.Grid(65, hzs.DIRICHLET, k=10.0, nsub=4, overlap=2)
+    with pytest.raises(hzs.HzsError) as e:
+        hzs.Preconditioner(g3, hzs.SHS2, hzs.COARSE_B2, 3, hzs.FP64)
+    assert e.value.status == hzs.ERR_INVALID_ARG and "coarse_ratio" in str(e.value)
+    for gg in (g, g2, g3):
+        gg.close()

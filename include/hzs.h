@@ -69,10 +69,14 @@ typedef enum { HZS_AS1 = 0, HZS_AS2 = 1, HZS_SAS2 = 2, HZS_SHS2 = 3 } hzs_precon
  * spacing H (B_2; for H = 2h these are the weights of Eq. 7). */
 typedef enum { HZS_COARSE_NONE = 0, HZS_COARSE_P1 = 1, HZS_COARSE_B2 = 2 } hzs_coarse_kind;
 
-/* HZS_FP64: every step in complex128.  HZS_MIXED: flexible GMRES in complex128
- * (matrix-vector product, orthogonalisation, least squares) around a
- * preconditioner whose stencil, transfers and subdomain solves run in
- * complex64; the coarse solve stays complex128. */
+/* HZS_FP64: every step in complex128.  HZS_MIXED: flexible GMRES (Section 5)
+ * around a preconditioner whose stencil, transfers and subdomain solves run in
+ * complex64, with the coarse solve in FP64 (the dense inverse's product as a
+ * double-float pair on the FP32 pipes; the block LU in FP64).  The outer
+ * matrix-vector product, the Krylov basis (complex128), the Hessenberg least
+ * squares and the solution are FP64; the orthogonalisation is the delayed CGS2
+ * whose reorthogonalisation coefficients and first-projection update are FP64
+ * (see HZS_SOLVE_ORTH_FP64 and HZS_SOLVE_BASIS_DF for the alternatives). */
 typedef enum { HZS_FP64 = 0, HZS_MIXED = 1 } hzs_precision;
 
 /* Problem and decomposition (Sections 2 and 3).
@@ -138,17 +142,24 @@ typedef struct {
 } hzs_solve_desc;
 
 #define HZS_SOLVE_PROFILE 1
-/* With HZS_MIXED: orthogonalise with the all-FP64 CGS2 on a complex128 basis
- * instead of the default, the delayed CGS2 (reorthogonalisation of vector j
- * fused with the projection of step j+1: two passes over the basis per step)
- * on a double-float basis (complex64 rounding + remainder) with double-float
- * updates and dot products.  No effect with HZS_FP64. */
+/* Orthogonalisation of the HZS_MIXED solve.  Default: the delayed CGS2
+ * (reorthogonalisation of vector j fused with the first projection of step j+1:
+ * two passes over the basis per step) on the complex128 basis, with the
+ * reorthogonalisation dot products, the norms and the first-projection update
+ * in FP64 and the first-projection dot products in complex64 on the leading 24
+ * bits of each entry (the reorthogonalisation of the next step removes what
+ * their rounding leaves).  HZS_SOLVE_ORTH_FP64: classical CGS2 with every dot
+ * product and update in FP64 (four passes per step), as HZS_FP64 uses.
+ * HZS_SOLVE_BASIS_DF: the delayed CGS2 on a narrower double-float basis
+ * (complex64 rounding + remainder, see HZS_SOLVE_BASIS_WIDE) with complex64 dot
+ * products and double-float updates: fewer bytes and no FP64 arithmetic, but
+ * the basis and its arithmetic are not FP64.  No effect with HZS_FP64. */
 #define HZS_SOLVE_ORTH_FP64 2
-/* The delayed-CGS2 basis stores its remainders as complex64 (about 48
- * significant bits, 16 bytes an entry in all) when tol < 1e-7, else as bf16
+#define HZS_SOLVE_BASIS_DF 16
+/* With HZS_SOLVE_BASIS_DF: the basis stores its remainders as complex64 (about
+ * 48 significant bits, 16 bytes an entry in all) when tol < 1e-7, else as bf16
  * pairs (about 32 significant bits, 12 bytes an entry: a quarter less basis
- * traffic).  This flag keeps the complex64 remainders at any tol.  No effect
- * without the delayed-CGS2 path. */
+ * traffic).  This flag keeps the complex64 remainders at any tol. */
 #define HZS_SOLVE_BASIS_WIDE 4
 /* Issue the Arnoldi steps (Section 5: preconditioner apply, matrix-vector
  * product, orthogonalisation and Givens update of every right-hand side) as
@@ -175,6 +186,8 @@ typedef struct {
     double t_orth_update_ms; /*   basis dot pass and of the basis update pass (parts of t_orth_ms); else 0 */
     long long launches;    /* kernel launches this solve issued */
     int basis_bits;        /* significant bits of the Krylov basis: 53 (complex128), 48 or 32 */
+    int orth_kind;         /* 0: CGS2 in FP64, 1: delayed CGS2 on the complex128 basis (FP64
+                              reorthogonalisation), 2: delayed CGS2 on the double-float basis */
     hzs_status status;
 } hzs_solve_info;
 
@@ -277,6 +290,28 @@ hzs_status hzs_precond_get_info(const hzs_precond* p, hzs_precond_info* out);
  *   streams, threads or handles) race and must be serialised by the caller.
  *   Nothing in it needs clearing between calls (each call writes what it reads). */
 hzs_status hzs_apply_precond_noalloc(hzs_precond* p, const void* v_dev, void* z_dev, int nrhs);
+
+/* Measured arithmetic rates of the current GPU (operations per second over the
+ * whole device; a fused multiply-add counts as 2 flops).  The paper has no
+ * counterpart: these are the peaks against which the ALU-bound kernels of this
+ * library (the FP64 Gram-Schmidt passes, the FP32 error-free arithmetic) are
+ * reported.  Measured, not taken from a data sheet: each rate is one kernel of
+ * independent dependency chains of one instruction kind filling the GPU, timed
+ * with CUDA events (about a second in all; synchronises a private stream). */
+typedef struct {
+    double fp32_tflops;    /* FMA.F32 */
+    double fp32x2_tflops;  /* packed fma.rn.f32x2 (4 flops an instruction) */
+    double fp64_tflops;    /* FMA.F64 */
+    double int_tops;       /* 3-input logic op and funnel shift, 10^12 per second */
+    double cvt_tops;       /* FP64 <-> FP32 conversions, 10^12 per second */
+    double mix_overlap;    /* FP32 and FP64 chains in one kernel: (t_fp32 + t_fp64) / t_both; 2 = full overlap */
+    int sms;
+    double clock_mhz;      /* the device's nominal SM clock (attribute, not a sample) */
+} hzs_pipe_rates;
+
+/* Fills *out for the current device.  Errors: HZS_ERR_INVALID_ARG (out NULL),
+ * HZS_ERR_CUDA. */
+hzs_status hzs_pipe_peaks(hzs_pipe_rates* out);
 
 /* Human-readable text of a status; never NULL. */
 const char* hzs_status_string(hzs_status s);

@@ -23,5 +23,5 @@ printed values, invariants or library routines; see each module's docstring.
 from .problem import Problem, DIRICHLET, SOMMERFELD  # noqa: F401
 from .decomposition import Decomposition  # noqa: F401
 from .coarse import CoarseSpace, CoarseSolver, P1, B2, bspline2, basis_1d  # noqa: F401
-from .schwarz import Schwarz, AS1, AS2, SAS2, SHS2  # noqa: F401
+from .schwarz import Schwarz, AS1, AS2, SAS2, SHS2, FP64, C64  # noqa: F401
 from .gmres import gmres, givens  # noqa: F401

@@ -95,8 +95,12 @@ class CoarseSolver:
         self.A0 = cs.galerkin(A)
         self.lu = sla.lu_factor(self.A0)
 
+    def solve(self, c: np.ndarray) -> np.ndarray:
+        """A_0^{-1} c (FP64)."""
+        return sla.lu_solve(self.lu, np.asarray(c, dtype=np.complex128))
+
     def apply_Q(self, v: np.ndarray) -> np.ndarray:
         """Q v = R_0^T A_0^{-1} R_0 v."""
         c = self.cs.R0 @ v
-        c = sla.lu_solve(self.lu, c)
+        c = self.solve(c)
         return self.cs.R0.T @ c

@@ -12,6 +12,16 @@ A_i^{-1} = (R_i A R_i^T)^{-1} done by a sparse direct solver (Section 3):
 
 The local problems are factorised once with SuperLU (scipy.sparse.linalg.splu,
 minimum-degree ordering on A_i^T + A_i, partial pivoting).
+
+Mixed precision (``precision="c64"``): the paper computes in one precision; the
+reduced-precision preconditioner of the mixed solver is read as the same
+operator with its transfers (R_0, R_0^T, R_i, R_i^T D_i), its deflation
+v - A q and its exact local solves carried out in complex64 - the input is
+rounded to complex64, the local matrices are factorised by SuperLU in complex64,
+every product and sum is a complex64 operation - while the coarse solve
+A_0^{-1} stays in FP64 (its input widened from, its output rounded to,
+complex64).  The result is returned widened to complex128 for the FP64
+flexible GMRES around it.
 """
 from __future__ import annotations
 
@@ -24,43 +34,69 @@ from .decomposition import Decomposition
 AS1, AS2, SAS2, SHS2 = "as1", "as2", "sas2", "shs2"
 
 
+FP64, C64 = "fp64", "c64"
+
+
 class Schwarz:
     def __init__(self, prob, A, ns: int, overlap: int, kind: str = SHS2,
-                 coarse: str | None = "b2", p: int | None = None):
+                 coarse: str | None = "b2", p: int | None = None, precision: str = FP64):
         if kind not in (AS1, AS2, SAS2, SHS2):
             raise ValueError(kind)
         if kind != AS1 and coarse is None:
             raise ValueError("two-level preconditioners need a coarse space")
-        self.kind, self.A = kind, A
+        if precision not in (FP64, C64):
+            raise ValueError(precision)
+        self.kind, self.A, self.precision = kind, A, precision
+        self.ct = np.complex128 if precision == FP64 else np.complex64
         self.dec = Decomposition(prob, ns, overlap)
         Ar = A.tocsr()
+        # the operator in the preconditioner's precision (the deflation of SHS2)
+        self.Ap = A if precision == FP64 else Ar.astype(self.ct)
         self.lu = []
         for s in self.dec.subs:
-            Ai = Ar[s.idx][:, s.idx].tocsc()
+            Ai = Ar[s.idx][:, s.idx].tocsc().astype(self.ct)
             # A_i has a symmetric nonzero pattern (Section 2), so the fill-reducing
             # ordering is minimum degree on A^T + A
             self.lu.append(spla.splu(Ai, permc_spec="MMD_AT_PLUS_A"))
         self.coarse = None
         if kind != AS1:
             self.coarse = CoarseSolver(CoarseSpace(prob, coarse, p), Ar)
+            if precision == C64:
+                self.R0p = self.coarse.cs.R0.astype(np.float32)
 
     def local_sum(self, r: np.ndarray, weighted: bool) -> np.ndarray:
-        """sum_i R_i^T (D_i) A_i^{-1} R_i r."""
-        out = np.zeros_like(r, dtype=np.complex128)
+        """sum_i R_i^T (D_i) A_i^{-1} R_i r, in the preconditioner's precision."""
+        out = np.zeros_like(r, dtype=self.ct)
         for s, lu in zip(self.dec.subs, self.lu):
-            y = lu.solve(np.ascontiguousarray(r[s.idx], dtype=np.complex128))
-            self.dec.prolong_add(s, y, out, weighted)
+            y = lu.solve(np.ascontiguousarray(r[s.idx], dtype=self.ct))
+            if weighted:
+                out[s.idx] += s.d.astype(y.real.dtype) * y
+            else:
+                out[s.idx] += y
         return out
 
+    def apply_Q(self, v: np.ndarray) -> np.ndarray:
+        """Q v = R_0^T A_0^{-1} R_0 v: the transfers in the preconditioner's precision,
+        the coarse solve in FP64."""
+        if self.precision == FP64:
+            return self.coarse.apply_Q(v)
+        c = (self.R0p @ v).astype(np.complex128)
+        c = self.coarse.solve(c).astype(np.complex64)
+        return self.R0p.T @ c
+
     def apply(self, v: np.ndarray) -> np.ndarray:
-        """z = M^{-1} v."""
+        """z = M^{-1} v (complex128 out; computed in complex64 when precision is c64)."""
+        v = np.asarray(v).astype(self.ct)
         if self.kind == AS1:
-            return self.local_sum(v, weighted=False)
-        q = self.coarse.apply_Q(v)
-        if self.kind == AS2:
-            return q + self.local_sum(v, weighted=False)
-        if self.kind == SAS2:
-            return q + self.local_sum(v, weighted=True)
-        # SHS2: coarse correction first, then local solves on the deflated residual
-        w = v - self.A @ q
-        return q + self.local_sum(w, weighted=True)
+            z = self.local_sum(v, weighted=False)
+        else:
+            q = self.apply_Q(v)
+            if self.kind == AS2:
+                z = q + self.local_sum(v, weighted=False)
+            elif self.kind == SAS2:
+                z = q + self.local_sum(v, weighted=True)
+            else:
+                # SHS2: coarse correction first, then local solves on the deflated residual
+                w = v - self.Ap @ q
+                z = q + self.local_sum(w, weighted=True)
+        return z.astype(np.complex128)

@@ -60,7 +60,6 @@ struct hzs_precond {
     double *w = nullptr, *wt = nullptr;
     float *wf = nullptr, *wtf = nullptr;
     double2* Ainv = nullptr;
-    float4* Ainv_df = nullptr;        // MIXED: double-float copy of Ainv (FP32-pipe coarse product)
     int coarse_block = 0;             // coarse solve by block-tridiagonal LU instead of Ainv
     CoarseBlockLU cblk;
     float2* c2f = nullptr;            // complex64 copy of the coarse solution
@@ -273,7 +272,7 @@ extern "C" void hzs_precond_destroy(hzs_precond* p) {
     cudaFree(p->c0); cudaFree(p->lo); cudaFree(p->hi); cudaFree(p->off); cudaFree(p->w); cudaFree(p->wt);
     cudaFree(p->wf); cudaFree(p->wtf); cudaFree(p->c2f); cudaFree(p->err); cudaFree(p->groups_d);
     coarse_block_free(p->cblk);
-    cudaFree(p->Ainv); cudaFree(p->Ainv_df); cudaFree(p->W64); cudaFree(p->W32); cudaFree(p->tiles_d); cudaFree(p->cover_d);
+    cudaFree(p->Ainv); cudaFree(p->W64); cudaFree(p->W32); cudaFree(p->tiles_d); cudaFree(p->cover_d);
     cudaFree(p->t_buf); cudaFree(p->c_buf); cudaFree(p->c2_buf); cudaFree(p->w_buf); cudaFree(p->ytiles);
     cudaFree(p->zc64);
     if (p->h_done) cudaFreeHost(p->h_done);
@@ -355,11 +354,6 @@ static hzs_status setup_impl(hzs_grid* g, const hzs_precond_desc* d, hzs_precond
         if (rc < 0) return fail(g, HZS_ERR_CUDA, "coarse factorisation failed");
         p->coarse_minpiv = minpiv;
         if (rc > 0) return fail(g, HZS_ERR_SINGULAR_COARSE, "coarse matrix A_0 has a zero pivot");
-        if (d->precision == HZS_MIXED) {
-            HZS_CUDA(g, dalloc(&p->Ainv_df, (size_t)p->Nc * p->Nc));
-            launch_split_df(p->cx, (long long)p->Nc * p->Nc, p->Ainv, p->Ainv_df);
-            HZS_CUDA(g, cudaGetLastError());
-        }
         }
     }
     HZS_CUDA(g, dalloc(&p->err, 1));
@@ -525,8 +519,6 @@ static hzs_status precond_apply(hzs_precond* p, int nb, const Cv* v, long long v
         launch_restrict<Cv, R>(cx, nb, v, vs, vscale, vss, (C*)p->t_buf, p->c_buf, sk);
         if (p->coarse_block)
             launch_coarse_block_solve(cx, nb, p->cblk, p->c_buf, p->c2_buf, f32 ? p->c2f : nullptr, sk);
-        else if (f32 && p->Ainv_df)
-            launch_coarse_matvec_df(cx, nb, p->Ainv_df, p->Nc, p->c_buf, p->c2f, sk);
         else
             launch_coarse_matvec(cx, nb, p->Ainv, p->Nc, p->c_buf, p->c2_buf, f32 ? p->c2f : nullptr, sk);
     }
@@ -743,18 +735,19 @@ extern "C" hzs_status hzs_precond_get_info(const hzs_precond* p, hzs_precond_inf
 static size_t krylov_entry_bytes(const hzs_precond* p, int maxit, long long ld, bool full_v) {
     const bool mixed = p->desc.precision == HZS_MIXED;
     size_t b = (size_t)(full_v ? maxit + 1 : 1) * ld * sizeof(double2);   // V
-    if (mixed) b += 2 * (size_t)(maxit + 1) * ld * sizeof(float2)          // V32, V32lo
-                    + (size_t)maxit * ld * sizeof(float2);                 // Z
+    if (mixed && !full_v) b += 2 * (size_t)(maxit + 1) * ld * sizeof(float2);   // V32, V32lo
+    if (mixed) b += (size_t)maxit * ld * sizeof(float2);                   // Z
     b += 2 * (size_t)ld * sizeof(double2);                                 // ztmp, rtmp
     b += (size_t)(maxit + 1) * maxit * sizeof(double2);                    // H
     return b;
 }
 
 // Krylov work space for batches of up to nb right-hand sides with maxit steps.
-// full_v: keep the whole complex128 basis (FP64 CGS2); otherwise only its slot 0.
+// full_v: keep the whole complex128 basis (FP64 CGS2, FP64 delayed CGS2); otherwise
+// only its slot 0 and the double-float basis V32 + V32lo.
 static hzs_status ensure_krylov(hzs_precond* p, int maxit, int nb, bool full_v) {
     hzs_grid* g = p->g;
-    if (p->kb.V && p->kb.maxit >= maxit && p->kb.nb >= nb && (p->kb.vfull || !full_v)) return HZS_OK;
+    if (p->kb.V && p->kb.maxit >= maxit && p->kb.nb >= nb && p->kb.vfull == (full_v ? 1 : 0)) return HZS_OK;
     free_krylov(p);
     const long long N = (long long)g->desc.n * g->desc.n;
     const long long ld = (N + 63) / 64 * 64;
@@ -795,7 +788,7 @@ static hzs_status ensure_krylov(hzs_precond* p, int maxit, int nb, bool full_v) 
         if (kb.ev_g) cudaEventDestroy(kb.ev_g);
         kb.side = nullptr; kb.ev_c = kb.ev_g = nullptr;
     }
-    if (p->desc.precision == HZS_MIXED) {
+    if (p->desc.precision == HZS_MIXED && !full_v) {
         HZS_CUDA(g, dalloc(&kb.V32, (size_t)nb * kb.sV()));
         float2* lo = nullptr;
         HZS_CUDA(g, dalloc(&lo, (size_t)nb * kb.sV()));
@@ -808,8 +801,8 @@ static hzs_status ensure_krylov(hzs_precond* p, int maxit, int nb, bool full_v) 
         if (ld > N)
             HZS_CUDA(g, cudaMemset2DAsync(kb.V32 + N, ld * sizeof(float2), 0, (ld - N) * sizeof(float2),
                                           (size_t)nb * (maxit + 1), g->stream));
-        HZS_CUDA(g, dalloc(&p->Z, (size_t)nb * maxit * ld));
     }
+    if (p->desc.precision == HZS_MIXED) HZS_CUDA(g, dalloc(&p->Z, (size_t)nb * maxit * ld));
     HZS_CUDA(g, dalloc(&p->ztmp, (size_t)nb * ld));
     HZS_CUDA(g, dalloc(&p->rtmp, (size_t)nb * ld));
     HZS_CUDA(g, dalloc(&p->dres, (size_t)nb));
@@ -830,6 +823,17 @@ static hzs_status set_basis_width(hzs_precond* p, int lo16) {
     }
     p->lo_pad = lo16;
     return HZS_OK;
+}
+
+// Arnoldi orthogonalisation of a solve (Section 5; the paper fixes no variant):
+// FP64 CGS2 on a complex128 basis (four passes per step) for HZS_FP64 or with
+// HZS_SOLVE_ORTH_FP64; for HZS_MIXED by default the delayed CGS2 on the complex128
+// basis (two passes per step, FP64 reorthogonalisation); with HZS_SOLVE_BASIS_DF the
+// delayed CGS2 on the narrower double-float basis.
+constexpr int kOrthCGS2 = 0, kOrthD64 = 1, kOrthDF = 2;
+static int orth_mode(const hzs_precond* p, const hzs_solve_desc* sd) {
+    if (p->desc.precision != HZS_MIXED || (sd->flags & HZS_SOLVE_ORTH_FP64)) return kOrthCGS2;
+    return (sd->flags & HZS_SOLVE_BASIS_DF) ? kOrthDF : kOrthD64;
 }
 
 // Kernel launches of one preconditioner apply.
@@ -886,8 +890,10 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
     const long long sZ = (long long)kb.maxit * ld;
     const bool mixed = p->desc.precision == HZS_MIXED;
     const bool prof = (sd->flags & HZS_SOLVE_PROFILE) != 0;
-    // mixed-precision CGS2 (complex64 first projection) unless all-FP64 orthogonalisation is asked for
-    const bool orth32 = mixed && !(sd->flags & HZS_SOLVE_ORTH_FP64);
+    const int orth = orth_mode(p, sd);
+    // delayed CGS2 on the double-float basis, or on the FP64 basis
+    const bool orth32 = orth == kOrthDF;
+    const bool d64 = orth == kOrthD64;
     // bf16 remainders (a basis of about 32 significant bits) for loose tolerances
     const bool lo16 = orth32 && !(sd->flags & HZS_SOLVE_BASIS_WIDE) && sd->tol >= kNarrowBasisTol;
     const BatchSkip sk = kb.skip();
@@ -915,7 +921,14 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
         cudaEvent_t* pe = prof ? &p->prof_ev[(size_t)8 * j] : nullptr;
         if (prof) HZS_CUDA(g, cudaEventRecord(pe[0], cx.stream));
         hzs_status st;
-        if (orth32) {
+        if (d64) {
+            // the complex64 preconditioner reads u~_j (the once-projected vector of the previous
+            // step, see launch_dcgs2_step64) scaled by 1/|u~_j|; A z_j in FP64 into slot j+1
+            float2* Zj = p->Z + (size_t)j * ld;
+            st = precond_apply<float, double2>(p, nb, kb.V + (size_t)j * ld, sV, kb.sigt + j, sS, Zj, sZ, sk);
+            if (prof) HZS_CUDA(g, cudaEventRecord(pe[1], cx.stream));
+            launch_apply_A<float2, double2, double>(cx, nb, Zj, sZ, kb.V + (size_t)(j + 1) * ld, sV, nullptr, 0, sk);
+        } else if (orth32) {
             // the complex64 preconditioner reads the leading words of u~_j (the once-projected
             // vector of the previous step, see launch_dcgs2_step) scaled by 1/|u~_j|
             float2* Zj = p->Z + (size_t)j * ld;
@@ -938,10 +951,11 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
         }
         if (st != HZS_OK) return st;
         if (prof) HZS_CUDA(g, cudaEventRecord(pe[2], cx.stream));
-        if (orth32) launch_dcgs2_step(cx, kb, nb, j, 0, prof ? pe + 4 : nullptr);
+        if (d64) launch_dcgs2_step64(cx, kb, nb, j, 0, prof ? pe + 4 : nullptr);
+        else if (orth32) launch_dcgs2_step(cx, kb, nb, j, 0, prof ? pe + 4 : nullptr);
         else launch_arnoldi_step(cx, kb, nb, j);
         if (prof) HZS_CUDA(g, cudaEventRecord(pe[3], cx.stream));
-        launches += pl + 1 + (orth32 ? (j > 0 ? 6 : 5) : 7);
+        launches += pl + 1 + (orth32 || d64 ? (j > 0 ? 6 : 5) : 7);
         steps = j + 1;
         // a launch that could not start (e.g. its resources) must not pass silently
         HZS_CUDA(g, cudaGetLastError());
@@ -992,8 +1006,9 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
         }
     }
     // delayed CGS2: the last column is completed by one more dot pass over the basis
-    if (orth32 && steps == sd->maxit) {
-        launch_dcgs2_step(cx, kb, nb, sd->maxit, 1);
+    if ((orth32 || d64) && steps == sd->maxit) {
+        if (d64) launch_dcgs2_step64(cx, kb, nb, sd->maxit, 1);
+        else launch_dcgs2_step(cx, kb, nb, sd->maxit, 1);
         launches += 4;
     }
     launch_lsq_solve(cx, kb, nb);
@@ -1036,7 +1051,7 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
             cudaEventElapsedTime(&b, pe[1], pe[2]);
             cudaEventElapsedTime(&c, pe[2], pe[3]);
             tp += a; tm += b; to += c;
-            if (orth32) {
+            if (orth32 || d64) {
                 float d = 0, u = 0;
                 cudaEventElapsedTime(&d, pe[4], pe[5]);
                 cudaEventElapsedTime(&u, pe[6], pe[7]);
@@ -1056,6 +1071,7 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
         inf.t_solve_ms = ms;
         inf.launches = launches;
         inf.basis_bits = !orth32 ? 53 : (lo16 ? 32 : 48);
+        inf.orth_kind = orth;
         inf.status = hs[r].nonfinite ? HZS_ERR_NONFINITE : (hs[r].conv ? HZS_OK : HZS_NOT_CONVERGED);
         if (info) info[r] = inf;
         if (inf.status == HZS_ERR_NONFINITE) worst = HZS_ERR_NONFINITE;
@@ -1077,9 +1093,9 @@ static hzs_status solve_many(hzs_precond* p, const hzs_solve_desc* sd, const voi
     if (!(sd->tol > 0.0) || sd->maxit < 1) return fail(g, HZS_ERR_INVALID_ARG, "tol must be > 0 and maxit >= 1");
     if (nrhs == 0) return HZS_OK;
     int nb = nrhs;
-    // the double-float path (MIXED without HZS_SOLVE_ORTH_FP64) keeps no complex128 basis
-    const bool full_v = !(p->desc.precision == HZS_MIXED && !(sd->flags & HZS_SOLVE_ORTH_FP64));
-    if (!(p->kb.V && p->kb.maxit >= sd->maxit && p->kb.nb >= nrhs && (p->kb.vfull || !full_v))) {
+    // only the double-float path (MIXED with HZS_SOLVE_BASIS_DF) keeps no complex128 basis
+    const bool full_v = orth_mode(p, sd) != kOrthDF;
+    if (!(p->kb.V && p->kb.maxit >= sd->maxit && p->kb.nb >= nrhs && p->kb.vfull == (full_v ? 1 : 0))) {
         free_krylov(p);
         size_t fr = 0, tot = 0;
         HZS_CUDA(g, cudaMemGetInfo(&fr, &tot));

@@ -128,113 +128,58 @@ __global__ void k_restrict_y(int n, CoarseTab ct, const cplx_t<R>* __restrict__ 
 }
 
 // ------------------------------------------------------------------ coarse solve
-// out = Ainv * c (dense, FP64).  One warp per row; c staged in shared memory.
-__global__ void k_coarse_matvec(int Nc, const double2* __restrict__ Ainv, const double2* __restrict__ c,
-                                double2* __restrict__ out, float2* __restrict__ outf, BatchSkip sk) {
+// out = Ainv * c (dense, FP64; outf, if given, gets its complex64 rounding).
+// kCmvWarpsPerRow warps share a row (the matrix, 16 B per entry, is re-read from
+// DRAM every apply: the basis passes evict it from L2, so each lane keeps kCmvLoads
+// loads in flight); c staged in shared memory.
+constexpr int kCmvWarpsPerRow = 4;
+constexpr int kCmvLoads = 8;
+constexpr int kCmvThreads = 512;
+__global__ void __launch_bounds__(kCmvThreads) k_coarse_matvec(int Nc, const double2* __restrict__ Ainv,
+                                                               const double2* __restrict__ c,
+                                                               double2* __restrict__ out, float2* __restrict__ outf,
+                                                               BatchSkip sk) {
     const int r = blockIdx.y;
     if (sk.flag && sk.flag[(size_t)r * sk.stride]) return;
     c += (size_t)r * Nc;
     out += (size_t)r * Nc;
     if (outf) outf += (size_t)r * Nc;
     extern __shared__ double2 cs[];
+    __shared__ double2 part[kCmvThreads / 32];
     for (int k = threadIdx.x; k < Nc; k += blockDim.x) cs[k] = c[k];
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int wpb = blockDim.x >> 5;
-    for (int row = blockIdx.x * wpb + (threadIdx.x >> 5); row < Nc; row += gridDim.x * wpb) {
-        const double2* arow = Ainv + (size_t)row * Nc;
-        double2 acc = make_double2(0.0, 0.0);
-        for (int k = lane; k < Nc; k += 32) acc = cfma(arow[k], cs[k], acc);
-        acc = warp_sum(acc);
-        if (lane == 0) {
-            out[row] = acc;
-            if (outf) outf[row] = to_f(acc);
-        }
-    }
-}
-
-// Double-float copy of Ainv: entry e as (hi.re, lo.re, hi.im, lo.im).
-__global__ void k_split_df(long long N, const double2* __restrict__ a, float4* __restrict__ b) {
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
-        const double2 v = a[e];
-        float4 q;
-        split_d(v.x, q.x, q.y);
-        split_d(v.y, q.z, q.w);
-        b[e] = q;
-    }
-}
-
-// outf = Ainv * c rounded to complex64, the products and sums in double-float
-// arithmetic on the FP32 pipes (same accuracy class as the FP64 product before
-// the final rounding).  kCmvWarpsPerRow warps share a row (the matrix, 16 B per
-// entry, is re-read from DRAM every apply: the basis passes evict it from L2, so
-// each lane keeps kCmvLoads loads in flight); c staged in shared memory as pairs.
-constexpr int kCmvWarpsPerRow = 4;
-constexpr int kCmvLoads = 8;
-constexpr int kCmvThreads = 512;
-__global__ void __launch_bounds__(kCmvThreads) k_coarse_matvec_df(int Nc, const float4* __restrict__ Adf,
-                                                                  const double2* __restrict__ c,
-                                                                  float2* __restrict__ outf, BatchSkip sk) {
-    const int r = blockIdx.y;
-    if (sk.flag && sk.flag[(size_t)r * sk.stride]) return;
-    c += (size_t)r * Nc;
-    outf += (size_t)r * Nc;
-    extern __shared__ float4 cdf[];
-    __shared__ float4 part[kCmvThreads / 32];
-    for (int k = threadIdx.x; k < Nc; k += blockDim.x) {
-        const double2 v = c[k];
-        float4 q;
-        split_d(v.x, q.x, q.y);
-        split_d(v.y, q.z, q.w);
-        cdf[k] = q;
-    }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int sub = warp % kCmvWarpsPerRow;                 // this warp's share of the row
     const int rows_per_block = (kCmvThreads / 32) / kCmvWarpsPerRow;
     const int row = blockIdx.x * rows_per_block + warp / kCmvWarpsPerRow;
-    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    double2 acc = make_double2(0.0, 0.0), acc2 = acc;
     if (row < Nc) {
-        const float4* arow = Adf + (size_t)row * Nc;
+        const double2* arow = Ainv + (size_t)row * Nc;
         constexpr int span = 32 * kCmvWarpsPerRow * kCmvLoads;   // columns per round of the row's warps
         for (int k0 = 0; k0 < Nc; k0 += span) {
-            float4 a[kCmvLoads];
+            double2 a[kCmvLoads];
 #pragma unroll
             for (int q = 0; q < kCmvLoads; ++q) {
                 const int k = k0 + 32 * (sub + kCmvWarpsPerRow * q) + lane;
-                a[q] = k < Nc ? arow[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+                a[q] = k < Nc ? arow[k] : make_double2(0.0, 0.0);
             }
 #pragma unroll
-            for (int q = 0; q < kCmvLoads; ++q) {
+            for (int q = 0; q < kCmvLoads; q += 2) {
                 const int k = k0 + 32 * (sub + kCmvWarpsPerRow * q) + lane;
-                const float4 v = k < Nc ? cdf[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-                df_fma(rh, rl, a[q].x, a[q].y, v.x, v.y);
-                df_fma(rh, rl, -a[q].z, -a[q].w, v.z, v.w);
-                df_fma(ih, il, a[q].x, a[q].y, v.z, v.w);
-                df_fma(ih, il, a[q].z, a[q].w, v.x, v.y);
+                const int k2 = k + 32 * kCmvWarpsPerRow;
+                acc = cfma(a[q], k < Nc ? cs[k] : make_double2(0.0, 0.0), acc);
+                acc2 = cfma(a[q + 1], k2 < Nc ? cs[k2] : make_double2(0.0, 0.0), acc2);
             }
-            df_norm(rh, rl);
-            df_norm(ih, il);
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float orh = __shfl_down_sync(0xffffffffu, rh, o), orl = __shfl_down_sync(0xffffffffu, rl, o);
-            const float oih = __shfl_down_sync(0xffffffffu, ih, o), oil = __shfl_down_sync(0xffffffffu, il, o);
-            df_add(rh, rl, orh, orl);
-            df_add(ih, il, oih, oil);
-        }
-        if (lane == 0) part[warp] = make_float4(rh, rl, ih, il);
     }
+    acc = warp_sum(cadd(acc, acc2));
+    if (lane == 0) part[warp] = acc;
     __syncthreads();
-    if (row < Nc && sub == 0 && lane == 0) {
-        for (int t = 1; t < kCmvWarpsPerRow; ++t) {         // fixed order: deterministic
-            const float4 o = part[warp + t];
-            df_add(rh, rl, o.x, o.y);
-            df_add(ih, il, o.z, o.w);
-        }
-        df_norm(rh, rl);
-        df_norm(ih, il);
-        outf[row] = make_float2(rh, ih);
+    if (sub == 0 && lane == 0 && row < Nc) {
+        double2 s = part[warp];
+        for (int q = 1; q < kCmvWarpsPerRow; ++q) s = cadd(s, part[warp + q]);
+        out[row] = s;
+        if (outf) outf[row] = to_f(s);
     }
 }
 
@@ -395,29 +340,13 @@ HZS_RS(double2, float)
 HZS_RS(float2, float)
 #undef HZS_RS
 
-void launch_split_df(const Ctx& cx, long long N, const double2* a, float4* b) {
-    k_split_df<<<4 * cx.num_sms, 256, 0, cx.stream>>>(N, a, b);
-}
-
-void launch_coarse_matvec_df(const Ctx& cx, int nb, const float4* Adf, int Nc, const double2* c, float2* outf,
-                             BatchSkip sk) {
-    const int threads = kCmvThreads;
-    const int rows_per_block = (kCmvThreads / 32) / kCmvWarpsPerRow;
-    const int blocks = (Nc + rows_per_block - 1) / rows_per_block;   // one row per warp group, no grid stride
-    const size_t smem = (size_t)Nc * sizeof(float4);
-    allow_dynamic_smem((const void*)k_coarse_matvec_df, smem);
-    k_coarse_matvec_df<<<dim3(blocks, nb), threads, smem, cx.stream>>>(Nc, Adf, c, outf, sk);
-}
-
 void launch_coarse_matvec(const Ctx& cx, int nb, const double2* Ainv, int Nc, const double2* c, double2* out,
                           float2* outf, BatchSkip sk) {
-    const int threads = 256;
-    const int rows_per_block = threads / 32;
-    int blocks = (Nc + rows_per_block - 1) / rows_per_block;
-    if (blocks > 4 * cx.num_sms) blocks = 4 * cx.num_sms;
+    const int rows_per_block = (kCmvThreads / 32) / kCmvWarpsPerRow;
+    const int blocks = (Nc + rows_per_block - 1) / rows_per_block;   // one row per warp group, no grid stride
     const size_t smem = (size_t)Nc * sizeof(double2);
     allow_dynamic_smem((const void*)k_coarse_matvec, smem);
-    k_coarse_matvec<<<dim3(blocks, nb), threads, smem, cx.stream>>>(Nc, Ainv, c, out, outf, sk);
+    k_coarse_matvec<<<dim3(blocks, nb), kCmvThreads, smem, cx.stream>>>(Nc, Ainv, c, out, outf, sk);
 }
 
 void launch_galerkin(const Ctx& cx, double2* A0) {

@@ -114,11 +114,6 @@ void launch_restrict(const Ctx& cx, int nb, const Cv* v, long long vs, const dou
 // out = Ainv c in FP64 (stride Nc); outf (if given) receives a complex64 copy
 void launch_coarse_matvec(const Ctx& cx, int nb, const double2* Ainv, int Nc, const double2* c, double2* out,
                           float2* outf, BatchSkip sk);
-// b = double-float copy of a (N complex entries, see k_split_df)
-void launch_split_df(const Ctx& cx, long long N, const double2* a, float4* b);
-// outf = complex64 rounding of Adf c, double-float arithmetic (Adf from launch_split_df)
-void launch_coarse_matvec_df(const Ctx& cx, int nb, const float4* Adf, int Nc, const double2* c, float2* outf,
-                             BatchSkip sk);
 void launch_galerkin(const Ctx& cx, double2* A0);
 // banded A_0: 25 entries per coarse row, offset (dI, dJ) at (dJ + 2) * 5 + (dI + 2)
 void launch_galerkin_banded(const Ctx& cx, double2* A0b);
@@ -228,6 +223,10 @@ void launch_arnoldi_step(const Ctx& cx, const KrylovBufs& kb, int nb, int j);
 // last_only (j == maxit) completes the last Hessenberg column only.  ev (optional,
 // 4 events) is recorded before and after the dot pass and the update pass.
 void launch_dcgs2_step(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int last_only, cudaEvent_t* ev = nullptr);
+// Step j of the delayed CGS2 Arnoldi on the FP64 basis kb.V (FP64 reorthogonalisation
+// dots and first-projection update, complex64 first-projection dots; same arguments).
+void launch_dcgs2_step64(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int last_only,
+                         cudaEvent_t* ev = nullptr);
 void launch_lsq_solve(const Ctx& cx, const KrylovBufs& kb, int nb);
 void launch_combine_basis(const Ctx& cx, const KrylovBufs& kb, int nb, double2* x, long long xs);
 void launch_combine_Z(const Ctx& cx, const KrylovBufs& kb, int nb, const float2* Z, long long ldz, long long zs,

@@ -400,7 +400,9 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_dcgs_dot(int j, long long Np
 
 // Cross-block sums of the dot pass, one warp per value (fixed order):
 // h2[i] = sigma_i alpha_i, hn[i] = sigma_i b_i (i < j), hn[j] = c, hn[j+1] = d.
-// The alpha and b partials arrive as FP32 words (see k_dcgs_dot), c and d as FP64.
+// The b partials arrive as FP32 words (see k_dcgs_dot), c and d as FP64; alpha as
+// FP32 words on the double-float path (A64 false) and as FP64 on the FP64 basis.
+template <bool A64>
 __global__ void k_dcgs_reduce(int j, int nblk, int ps, int S, const double2* __restrict__ part, long long sP,
                               const double* __restrict__ sigma, double2* __restrict__ h2, double2* __restrict__ hn,
                               long long sS, long long sN, const KState* __restrict__ st) {
@@ -412,7 +414,9 @@ __global__ void k_dcgs_reduce(int j, int nblk, int ps, int S, const double2* __r
     part += r * sP; sigma += r * sS; h2 += r * sS; hn += r * sN;
     const int col = k < j ? k : (k < 2 * j ? S + (k - j) : 2 * S + (k - 2 * j));
     double2 s = make_double2(0.0, 0.0);
-    if (k < 2 * j) {
+    if (A64 && k < j) {
+        for (int b = lane; b < nblk; b += 32) s = cadd(s, part[(size_t)b * ps + col]);
+    } else if (k < 2 * j) {
         // alpha and b: complex64 in the first 8 bytes of the slot
         const float4* pf = reinterpret_cast<const float4*>(part);
         for (int b = lane; b < nblk; b += 32) {
@@ -797,6 +801,201 @@ __global__ void __launch_bounds__(kRedThreads, kUpdBlocksPerSM) k_dcgs_update(in
     block_norm_part(nrm, npart + (size_t)r * nblk);
 }
 
+// ---- delayed CGS2 on an FP64 basis (mixed-precision path, see launch_dcgs2_step64)
+// The same step as above with the basis, u~_j and w held as complex128.  The
+// quantities that set the Arnoldi process - the reorthogonalisation coefficients
+// alpha = Q^H u~_j, c = |u~_j|^2, d = u~_j^H w and the first-projection update
+// w - Q b - h_jj q_j - are computed with FP64 fused multiply-adds.  The
+// first-projection coefficients b = Q^H w are complex64 dot products on the
+// leading 24 bits of each entry: they are recorded in H exactly as the update
+// applies them, so the Arnoldi relation holds to FP64 whatever their accuracy,
+// and the projection they leave behind (about 2^-24 |w| along Q) is what alpha
+// removes one step later, in FP64.  The reorthogonalisation update u~_j - Q alpha
+// is a sum of small terms (|alpha_i| of that order relative to |u~_j|), so it
+// runs in double-float arithmetic on the FP32 pipes: its error is about 2^-46
+// of terms that are themselves 2^-20 of |u~_j| or less, below the FP64 rounding
+// of the result (the part's FP64 pipe runs at 1/64 of the FP32 rate).
+
+// Leading 24 significant bits of x (the fraction truncated) as an FP32 value,
+// from integer operations on the FP64 word: the exponent is rebiased from 1023
+// to 127.  |x| < 2^-126 gives 0; |x| must be below 2^128.
+__device__ __forceinline__ float dhead(double x) {
+    const unsigned H = (unsigned)__double2hiint(x), L = (unsigned)__double2loint(x);
+    const unsigned a = H & 0x7fffffffu;
+    const unsigned h = __funnelshift_l(L, a - (896u << 20), 3);
+    return __uint_as_float((a >= (897u << 20) ? h : 0u) | (H & 0x80000000u));
+}
+// x = hd + md + r with hd = dhead(x), md the next 23 fraction bits (exact FP32
+// values) and |r| < 2^-46 |x|: md = rb * 2^(e-1069) with rb = fraction bits 28..6
+// and e the biased FP64 exponent, built as as_float(E | rb) - as_float(E) for the
+// FP32 exponent field E = e - 919.  |x| < 2^-97 gives two zeros.
+__device__ __forceinline__ void dsplit(double x, float& hd, float& md) {
+    const unsigned H = (unsigned)__double2hiint(x), L = (unsigned)__double2loint(x);
+    const unsigned a = H & 0x7fffffffu, sg = H & 0x80000000u;
+    const bool ok = a >= (926u << 20);
+    const unsigned h = __funnelshift_l(L, a - (896u << 20), 3);
+    const unsigned E = sg | (((a - (919u << 20)) << 3) & 0x7f800000u);
+    const float m = __uint_as_float(E | ((L >> 6) & 0x7fffffu)) - __uint_as_float(E);
+    hd = ok ? __uint_as_float(sg | h) : 0.f;
+    md = ok ? m : 0.f;
+}
+
+// Dot pass of step j on the FP64 basis V (entry r = blockIdx.y): per block chunk,
+// alpha_i = conj(V_i) . u~ (FP64), b_i = conj(head V_i) . head w (complex64),
+// c = |u~|^2 and d = conj(u~) . w (FP64).  Partials: alpha at [0, S) as FP64,
+// b at [S, 2S) as FP32 words in the first 8 bytes, c at 2S and d at 2S+1 as FP64.
+template <int G>
+__global__ void __launch_bounds__(kRedThreads, 3) k_d64_dot(int j, long long N, long long ld, int ps, int S,
+                                                           const double2* __restrict__ V, long long sV, int has_w,
+                                                           double2* __restrict__ part, long long sP,
+                                                           const KState* __restrict__ st) {
+    const int r = blockIdx.y;
+    if (st[r].done) return;
+    V += r * sV;
+    const double2* u = V + (size_t)j * ld;
+    const double2* w = has_w ? V + (size_t)(j + 1) * ld : u;
+    part += r * sP + (size_t)blockIdx.x * ps;
+    long long e0, e1;
+    chunk_of(N, e0, e1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int ngroups = (j + G - 1) / G;
+    for (int gi = warp; gi <= ngroups; gi += nw) {
+        if (gi == ngroups) {
+            double c = 0.0;
+            double2 d = make_double2(0.0, 0.0);
+            for (long long e = e0 + lane; e < e1; e += 32) {
+                const double2 x = __ldg(u + e);
+                c = fma(x.x, x.x, fma(x.y, x.y, c));
+                if (has_w) d = cfma_conj(x, __ldg(w + e), d);
+            }
+            c = warp_sum_d(c);
+            d = warp_sum(d);
+            if (lane == 0) {
+                part[2 * S] = make_double2(c, 0.0);
+                part[2 * S + 1] = d;
+            }
+            continue;
+        }
+        const int i0 = gi * G;
+        double2 aa[G];
+        float2 bb[G];
+#pragma unroll
+        for (int t = 0; t < G; ++t) { aa[t] = make_double2(0.0, 0.0); bb[t] = make_float2(0.f, 0.f); }
+        for (long long e = e0 + lane; e < e1; e += 32) {
+            const double2 x = __ldg(u + e);
+            float2 yh = make_float2(0.f, 0.f);
+            if (has_w) {
+                const double2 y = __ldg(w + e);
+                yh = make_float2(dhead(y.x), dhead(y.y));
+            }
+            double2 v[G];
+#pragma unroll
+            for (int t = 0; t < G; ++t)
+                v[t] = i0 + t < j ? __ldcs(V + (size_t)(i0 + t) * ld + e) : make_double2(0.0, 0.0);
+#pragma unroll
+            for (int t = 0; t < G; ++t) {
+                aa[t] = cfma_conj(v[t], x, aa[t]);
+                bb[t] = cfma_conj(make_float2(dhead(v[t].x), dhead(v[t].y)), yh, bb[t]);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < G; ++t) {
+            aa[t] = warp_sum(aa[t]);
+            bb[t] = warp_sum(bb[t]);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int t = 0; t < G; ++t)
+                if (i0 + t < j) {
+                    part[i0 + t] = aa[t];
+                    reinterpret_cast<float4*>(part)[S + i0 + t] = make_float4(bb[t].x, bb[t].y, 0.f, 0.f);
+                }
+        }
+    }
+}
+
+// Coefficients of basis vector i for the FP64-basis update pass: c = sigma_i h1_i
+// (an FP32 value, see k_dcgs_coef) and the reorthogonalisation coefficient
+// a = sigma_i alpha_i as double-float pairs (re and im).
+struct alignas(16) Upd64Coef {
+    double2 c;
+    float arh, arl, aih, ail;
+};
+
+// Update pass of step j on the FP64 basis (one entry per thread and sweep):
+// V_j = u~_j - sum_i a_i V_i (double-float sum, FP64 subtraction),
+// w <- w - sum_i c_i V_i - (h_jj sigma_j) V_j (FP64), npart[b] = sum_e |w[e]|^2.
+__global__ void __launch_bounds__(kRedThreads, 3) k_d64_update(int j, long long N, long long ld,
+                                                              double2* __restrict__ V, long long sV,
+                                                              const double* __restrict__ sigma,
+                                                              const double2* __restrict__ h1,
+                                                              const double2* __restrict__ h2, long long sS,
+                                                              double* __restrict__ npart, int nblk,
+                                                              const KState* __restrict__ st) {
+    const int r = blockIdx.y;
+    if (st[r].done) return;
+    V += r * sV; sigma += r * sS; h1 += r * sS; h2 += r * sS;
+    double2* u = V + (size_t)j * ld;
+    double2* w = V + (size_t)(j + 1) * ld;
+    extern __shared__ Upd64Coef u64c[];
+    __shared__ double2 s_cj;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        const double2 c = cscale(h1[i], sigma[i]);
+        if (i == j) { s_cj = c; continue; }
+        const double2 a = cscale(h2[i], sigma[i]);
+        Upd64Coef k;
+        k.c = c;
+        k.arh = (float)a.x; k.arl = (float)(a.x - (double)k.arh);
+        k.aih = (float)a.y; k.ail = (float)(a.y - (double)k.aih);
+        u64c[i] = k;
+    }
+    __syncthreads();
+    const double2 cj = s_cj;
+    long long e0, e1;
+    chunk_of(N, e0, e1);
+    double nrm = 0.0;
+    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        double2 acc = make_double2(0.0, 0.0), acc2 = acc;
+        float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;      // sum a_i V_i (double-float, re and im)
+        auto step = [&](const Upd64Coef& k, double2 v, double2& ac) {
+            ac = cfma(k.c, v, ac);
+            float xh, xm, yh, ym;
+            dsplit(v.x, xh, xm);
+            dsplit(v.y, yh, ym);
+            // re += ar vr - ai vi ; im += ar vi + ai vr
+            df_fma(rh, rl, k.arh, k.arl, xh, xm);
+            df_fma(rh, rl, -k.aih, -k.ail, yh, ym);
+            df_fma(ih, il, k.arh, k.arl, yh, ym);
+            df_fma(ih, il, k.aih, k.ail, xh, xm);
+        };
+        // basis vectors j-1 .. 0: the dot pass read 0 .. j-1, so those still in L2 come first
+        int i = j - 1;
+        for (; i >= 3; i -= 4) {
+            const double2 v0 = __ldcs(V + (size_t)i * ld + e), v1 = __ldcs(V + (size_t)(i - 1) * ld + e);
+            const double2 v2 = __ldcs(V + (size_t)(i - 2) * ld + e), v3 = __ldcs(V + (size_t)(i - 3) * ld + e);
+            step(u64c[i], v0, acc);
+            step(u64c[i - 1], v1, acc2);
+            step(u64c[i - 2], v2, acc);
+            step(u64c[i - 3], v3, acc2);
+            df_norm(rh, rl);
+            df_norm(ih, il);
+        }
+        for (; i >= 0; --i) step(u64c[i], __ldcs(V + (size_t)i * ld + e), acc);
+        acc = cadd(acc, acc2);
+        // V_j = u~ - (sum a_i V_i)
+        double2 x = u[e];
+        x.x = (x.x - (double)rh) - (double)rl;
+        x.y = (x.y - (double)ih) - (double)il;
+        u[e] = x;
+        // w - sum c_i V_i - c_j V_j
+        double2 y = csub(w[e], acc);
+        y = cfms(cj, x, y);
+        w[e] = y;
+        nrm = fma(y.x, y.x, fma(y.y, y.y, nrm));
+    }
+    block_norm_part(nrm, npart + (size_t)r * nblk);
+}
+
 // sigt[j+1] = 1 / |u~_{j+1}| from the update pass's partial norms (one warp per entry;
 // count partials per entry, stride apart).
 __global__ void k_dcgs_scale(int j, int count, int stride, const double* __restrict__ npart,
@@ -1055,7 +1254,7 @@ void launch_dcgs2_step(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int l
                                                                                  kb.st);
     if (ev) cudaEventRecord(ev[1], cx.stream);
     const dim3 rg(((2 * j + 2) * 32 + 255) / 256, nb);
-    k_dcgs_reduce<<<rg, 256, 0, cx.stream>>>(j, kb.nblk_dot, ps, S, kb.part, kb.sP(), kb.sigma, kb.h2, kb.hn,
+    k_dcgs_reduce<false><<<rg, 256, 0, cx.stream>>>(j, kb.nblk_dot, ps, S, kb.part, kb.sP(), kb.sigma, kb.h2, kb.hn,
                                              kb.sS(), kb.sN(), kb.st);
     k_dcgs_coef<<<nb, kFinThreads, 0, cx.stream>>>(j, kb.maxit, last_only, kb.hn, kb.sN(), kb.h1, kb.h2, kb.H,
                                                    kb.sH(), kb.sigma, kb.sS(), kb.st, kb.active);
@@ -1099,6 +1298,46 @@ void launch_dcgs2_step(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int l
         }
         if (ev) cudaEventRecord(ev[3], cx.stream);
         k_dcgs_scale<<<nb, 32, 0, cx.stream>>>(j, nupd, kb.nblk, kb.npart, kb.sigt, kb.sS(), kb.st);
+    }
+    if (side) cudaStreamWaitEvent(cx.stream, kb.ev_g, 0);
+}
+
+// Delayed CGS2 on the FP64 basis kb.V (see k_d64_dot): the same step structure as
+// launch_dcgs2_step (dot pass, reduction, coefficients, Givens rotation of column
+// j-1 on the side stream beside the update pass, scale of the next preconditioner
+// input); ev as there.
+void launch_dcgs2_step64(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int last_only, cudaEvent_t* ev) {
+    const int S = kb.maxit + 1, ps = kb.pstride();
+    if (ev) cudaEventRecord(ev[0], cx.stream);
+    k_d64_dot<kDotGroup64><<<dim3(kb.nblk_dot, nb), kRedThreads, 0, cx.stream>>>(j, kb.N, kb.ld, ps, S, kb.V, kb.sV(),
+                                                                                !last_only, kb.part, kb.sP(), kb.st);
+    if (ev) cudaEventRecord(ev[1], cx.stream);
+    const dim3 rg(((2 * j + 2) * 32 + 255) / 256, nb);
+    k_dcgs_reduce<true><<<rg, 256, 0, cx.stream>>>(j, kb.nblk_dot, ps, S, kb.part, kb.sP(), kb.sigma, kb.h2, kb.hn,
+                                                   kb.sS(), kb.sN(), kb.st);
+    k_dcgs_coef<<<nb, kFinThreads, 0, cx.stream>>>(j, kb.maxit, last_only, kb.hn, kb.sN(), kb.h1, kb.h2, kb.H,
+                                                   kb.sH(), kb.sigma, kb.sS(), kb.st, kb.active);
+    const bool side = j > 0 && kb.side && kb.ev_c && kb.ev_g;
+    if (j > 0) {
+        cudaStream_t gs = cx.stream;
+        if (side) {
+            cudaEventRecord(kb.ev_c, cx.stream);
+            cudaStreamWaitEvent(kb.side, kb.ev_c, 0);
+            gs = kb.side;
+        }
+        k_dcgs_givens<<<nb, kFinThreads, dcgs_givens_smem(j), gs>>>(j, kb.maxit, last_only, kb.H, kb.sH(), kb.cs,
+                                                                     kb.sn, kb.g, kb.sS(), kb.st, kb.active);
+        if (side) cudaEventRecord(kb.ev_g, kb.side);
+    }
+    if (!last_only) {
+        const size_t us = (size_t)(j > 0 ? j : 1) * sizeof(Upd64Coef);
+        set_coef_smem_limit((const void*)k_d64_update, us);
+        const dim3 gu(kb.nblk, nb);
+        if (ev) cudaEventRecord(ev[2], cx.stream);
+        k_d64_update<<<gu, kRedThreads, us, cx.stream>>>(j, kb.N, kb.ld, kb.V, kb.sV(), kb.sigma, kb.h1, kb.h2,
+                                                         kb.sS(), kb.npart, kb.nblk, kb.st);
+        if (ev) cudaEventRecord(ev[3], cx.stream);
+        k_dcgs_scale<<<nb, 32, 0, cx.stream>>>(j, kb.nblk, kb.nblk, kb.npart, kb.sigt, kb.sS(), kb.st);
     }
     if (side) cudaStreamWaitEvent(cx.stream, kb.ev_g, 0);
 }

@@ -31,7 +31,7 @@ EXPORTS = (
     "hzs_grid_create", "hzs_grid_destroy", "hzs_precond_setup", "hzs_precond_destroy",
     "hzs_apply_operator", "hzs_apply_precond", "hzs_solve", "hzs_adjoint_solve",
     "hzs_kappa_gradient", "hzs_status_string", "hzs_last_error", "hzs_version",
-    "hzs_apply_precond_noalloc", "hzs_solve_batched", "hzs_precond_get_info",
+    "hzs_apply_precond_noalloc", "hzs_solve_batched", "hzs_precond_get_info", "hzs_pipe_peaks",
 )
 
 
@@ -56,10 +56,21 @@ class PrecondInfo(ct.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class PipeRates(ct.Structure):
+    _fields_ = [("fp32_tflops", ct.c_double), ("fp32x2_tflops", ct.c_double), ("fp64_tflops", ct.c_double),
+                ("int_tops", ct.c_double), ("cvt_tops", ct.c_double), ("mix_overlap", ct.c_double),
+                ("sms", ct.c_int), ("clock_mhz", ct.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 SOLVE_PROFILE = 1
 SOLVE_ORTH_FP64 = 2
 SOLVE_BASIS_WIDE = 4
 SOLVE_GRAPH = 8
+SOLVE_BASIS_DF = 16
+ORTH_CGS2_FP64, ORTH_DCGS2_FP64, ORTH_DCGS2_DF = 0, 1, 2
 
 
 class SolveDesc(ct.Structure):
@@ -71,7 +82,7 @@ class SolveInfo(ct.Structure):
                 ("relres_true", ct.c_double), ("t_solve_ms", ct.c_double), ("t_precond_ms", ct.c_double),
                 ("t_matvec_ms", ct.c_double), ("t_orth_ms", ct.c_double), ("t_orth_dot_ms", ct.c_double),
                 ("t_orth_update_ms", ct.c_double), ("launches", ct.c_longlong),
-                ("basis_bits", ct.c_int), ("status", ct.c_int)]
+                ("basis_bits", ct.c_int), ("orth_kind", ct.c_int), ("status", ct.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -110,6 +121,7 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
                                       ct.POINTER(ct.c_int), ct.POINTER(SolveInfo)]
     lib.hzs_kappa_gradient.argtypes = [P, P, P, P]
     lib.hzs_precond_get_info.argtypes = [P, ct.POINTER(PrecondInfo)]
+    lib.hzs_pipe_peaks.argtypes = [ct.POINTER(PipeRates)]
     lib.hzs_status_string.argtypes = [ct.c_int]
     lib.hzs_status_string.restype = ct.c_char_p
     lib.hzs_last_error.argtypes = [P]
@@ -160,6 +172,19 @@ class SolveResult:
     launches: int
     status: int
     basis_bits: int = 0
+    orth_kind: int = 0
+
+    @staticmethod
+    def of(i) -> "SolveResult":
+        return SolveResult(i.iterations, bool(i.converged), i.relres_est, i.relres_true, i.t_solve_ms,
+                           i.t_precond_ms, i.t_matvec_ms, i.t_orth_ms, i.t_orth_dot_ms, i.t_orth_update_ms,
+                           i.launches, i.status, i.basis_bits, i.orth_kind)
+
+
+def _solve_flags(profile=False, orth_fp64=False, wide_basis=False, graph=False, basis_df=False) -> int:
+    return ((SOLVE_PROFILE if profile else 0) | (SOLVE_ORTH_FP64 if orth_fp64 else 0)
+            | (SOLVE_BASIS_WIDE if wide_basis else 0) | (SOLVE_GRAPH if graph else 0)
+            | (SOLVE_BASIS_DF if basis_df else 0))
 
 
 class Grid:
@@ -240,36 +265,33 @@ class Preconditioner:
         _check(load().hzs_precond_get_info(self._h, ct.byref(out)), self.grid.handle)
         return out.as_dict()
 
-    def _solve(self, fn, f, tol, maxit, out, profile, orth_fp64=False, wide_basis=False, graph=False):
+    def _solve(self, fn, f, tol, maxit, out, flags):
         f = _dev_c128(f, self.n, "f")
         u = torch.empty_like(f) if out is None else out
         nrhs = f.numel() // (self.n * self.n)
         infos = (SolveInfo * max(nrhs, 1))()
-        flags = ((SOLVE_PROFILE if profile else 0) | (SOLVE_ORTH_FP64 if orth_fp64 else 0)
-                 | (SOLVE_BASIS_WIDE if wide_basis else 0) | (SOLVE_GRAPH if graph else 0))
         sd = SolveDesc(float(tol), int(maxit), flags)
         _check(fn(self._h, ct.byref(sd), f.data_ptr(), u.data_ptr(), nrhs, infos), self.grid.handle,
                allow=(OK, NOT_CONVERGED))
-        res = [SolveResult(i.iterations, bool(i.converged), i.relres_est, i.relres_true, i.t_solve_ms,
-                           i.t_precond_ms, i.t_matvec_ms, i.t_orth_ms, i.t_orth_dot_ms, i.t_orth_update_ms,
-                           i.launches, i.status, i.basis_bits)
-               for i in infos[:nrhs]]
-        return u, res
+        return u, [SolveResult.of(i) for i in infos[:nrhs]]
 
     def solve(self, f: torch.Tensor, tol: float = 1e-6, maxit: int = 1000, out=None, profile: bool = False,
-              orth_fp64: bool = False, wide_basis: bool = False, graph: bool = False):
+              orth_fp64: bool = False, wide_basis: bool = False, graph: bool = False, basis_df: bool = False):
         """u = A^{-1} f by preconditioned GMRES; returns (u, [SolveResult per right-hand side]).
 
-        orth_fp64: with a MIXED preconditioner, orthogonalise with the all-FP64 CGS2.
-        wide_basis: keep the double-float basis at about 48 bits even for tol >= 1e-7
-        (where it otherwise stores bf16 remainders, about 32 bits).
+        With a MIXED preconditioner the orthogonalisation is the delayed CGS2 on the
+        complex128 basis (FP64 reorthogonalisation) unless
+        orth_fp64: the classical CGS2 with every product in FP64 (four basis passes a step), or
+        basis_df: the delayed CGS2 on the narrower double-float basis, whose remainders are
+        bf16 pairs (about 32 bits) for tol >= 1e-7 unless wide_basis (complex64, about 48 bits).
         graph: issue the Arnoldi steps as replayed CUDA graphs of 8 steps each."""
-        return self._solve(load().hzs_solve, f, tol, maxit, out, profile, orth_fp64, wide_basis, graph)
+        return self._solve(load().hzs_solve, f, tol, maxit, out,
+                           _solve_flags(profile, orth_fp64, wide_basis, graph, basis_df))
 
     def adjoint_solve(self, g: torch.Tensor, tol: float = 1e-6, maxit: int = 1000, out=None, profile: bool = False,
                       graph: bool = False):
         """lambda = conj(A)^{-1} g; returns (lambda, results)."""
-        return self._solve(load().hzs_adjoint_solve, g, tol, maxit, out, profile, graph=graph)
+        return self._solve(load().hzs_adjoint_solve, g, tol, maxit, out, _solve_flags(profile, graph=graph))
 
     def kappa_gradient(self, u: torch.Tensor, lam: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
         u = _dev_c128(u, self.n, "u")
@@ -291,7 +313,7 @@ class Preconditioner:
 
 
 def solve_batched(problems, rhs, tol: float = 1e-6, maxit: int = 1000, orth_fp64: bool = False,
-                  wide_basis: bool = False, graph: bool = False):
+                  wide_basis: bool = False, graph: bool = False, basis_df: bool = False):
     """Batched solve over several problems: ``problems`` is a list of Preconditioner
     handles (distinct), ``rhs`` a matching list of complex128 tensors of shape
     (nrhs_k, n_k, n_k).  Returns (list of solutions, list of lists of SolveResult)."""
@@ -308,20 +330,24 @@ def solve_batched(problems, rhs, tol: float = 1e-6, maxit: int = 1000, orth_fp64
     infos = (SolveInfo * max(total, 1))()
     arr = lambda vals: (ct.c_void_p * max(k, 1))(*vals)
     sd = SolveDesc(float(tol), int(maxit),
-                   (SOLVE_ORTH_FP64 if orth_fp64 else 0) | (SOLVE_BASIS_WIDE if wide_basis else 0)
-                   | (SOLVE_GRAPH if graph else 0))
+                   _solve_flags(orth_fp64=orth_fp64, wide_basis=wide_basis, graph=graph, basis_df=basis_df))
     st = lib.hzs_solve_batched(k, arr([P.handle.value for P in problems]), ct.byref(sd),
                                arr([f.data_ptr() for f in rhs]), arr([u.data_ptr() for u in outs]),
                                (ct.c_int * max(k, 1))(*counts), infos)
     _check(st, None, allow=(OK, NOT_CONVERGED))
     res, pos = [], 0
     for c in counts:
-        res.append([SolveResult(i.iterations, bool(i.converged), i.relres_est, i.relres_true, i.t_solve_ms,
-                                i.t_precond_ms, i.t_matvec_ms, i.t_orth_ms, i.t_orth_dot_ms,
-                                i.t_orth_update_ms, i.launches, i.status, i.basis_bits)
-                    for i in infos[pos:pos + c]])
+        res.append([SolveResult.of(i) for i in infos[pos:pos + c]])
         pos += c
     return outs, res
+
+
+def pipe_peaks() -> dict:
+    """Measured arithmetic rates of the current GPU (hzs_pipe_peaks): FP32, packed FP32,
+    FP64 in TFLOP/s, integer logic and FP64/FP32 conversions in 10^12 op/s."""
+    r = PipeRates()
+    _check(load().hzs_pipe_peaks(ct.byref(r)))
+    return r.as_dict()
 
 
 def version() -> str:

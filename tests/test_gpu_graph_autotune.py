@@ -68,20 +68,20 @@ def same_results(U0, R0, U1, R1):
     assert reldiff(U1, U0) <= 1e-12
 
 
-# (precision, orth_fp64): FP64 CGS2; mixed with the delayed CGS2 on the double-float
-# basis; mixed with the all-FP64 CGS2
-PATHS = [(0, False), (1, False), (1, True)]
+# (precision, orth_fp64, basis_df): FP64 CGS2; mixed with the delayed CGS2 on the
+# complex128 basis; on the double-float basis; mixed with the all-FP64 CGS2
+PATHS = [(0, False, False), (1, False, False), (1, False, True), (1, True, False)]
 
 
-@pytest.mark.parametrize("prec,orth", PATHS)
-def test_graph_solve_equals_stream_solve(hzs, prec, orth):
+@pytest.mark.parametrize("prec,orth,df", PATHS)
+def test_graph_solve_equals_stream_solve(hzs, prec, orth, df):
     n, k = 129, 25.0
     g = hzs.Grid(n, hzs.SOMMERFELD, k=k, nsub=4, overlap=2)
     P = hzs.Preconditioner(g, hzs.SHS2, hzs.COARSE_B2, 16, prec)
     F = sources(n, 5, seed=21)
-    U0, R0 = P.solve(F, tol=1e-8, maxit=300, orth_fp64=orth)
+    U0, R0 = P.solve(F, tol=1e-8, maxit=300, orth_fp64=orth, basis_df=df)
     for _ in range(2):                                            # second call reuses the graphs
-        U1, R1 = P.solve(F, tol=1e-8, maxit=300, orth_fp64=orth, graph=True)
+        U1, R1 = P.solve(F, tol=1e-8, maxit=300, orth_fp64=orth, basis_df=df, graph=True)
         torch.cuda.synchronize()
         same_results(U0, R0, U1, R1)
     assert all(r.converged for r in R1)

@@ -154,8 +154,8 @@ def overlap_one_sided(mp):
 
 def local_solve_conjugated(mp):
     plant(mp, oschwarz.Schwarz, "local_sum",
-          ("y = lu.solve(np.ascontiguousarray(r[s.idx], dtype=np.complex128))",
-           "y = np.conj(lu.solve(np.conj(np.ascontiguousarray(r[s.idx], dtype=np.complex128))))"))
+          ("y = lu.solve(np.ascontiguousarray(r[s.idx], dtype=self.ct))",
+           "y = np.conj(lu.solve(np.conj(np.ascontiguousarray(r[s.idx], dtype=self.ct))))"))
     return [(ts.test_preconditioner_dense_formula, (SOMMERFELD, AS1, B2))]
 
 
@@ -189,20 +189,41 @@ def galerkin_of_conj(mp):
 # ---- Eqs. 4-6 ----------------------------------------------------------------------
 
 def shs2_deflation_sign(mp):
-    plant(mp, oschwarz.Schwarz, "apply", ("w = v - self.A @ q", "w = v + self.A @ q"))
+    plant(mp, oschwarz.Schwarz, "apply", ("w = v - self.Ap @ q", "w = v + self.Ap @ q"))
     return [(ts.test_preconditioner_dense_formula, (DIRICHLET, SHS2, B2))]
 
 
 def sas2_without_d(mp):
-    plant(mp, oschwarz.Schwarz, "apply", ("return q + self.local_sum(v, weighted=True)",
-                                         "return q + self.local_sum(v, weighted=False)"))
+    plant(mp, oschwarz.Schwarz, "apply", ("z = q + self.local_sum(v, weighted=True)",
+                                         "z = q + self.local_sum(v, weighted=False)"))
     return [(ts.test_preconditioner_dense_formula, (DIRICHLET, SAS2, P1))]
 
 
 def as2_without_q(mp):
-    plant(mp, oschwarz.Schwarz, "apply", ("return q + self.local_sum(v, weighted=False)",
-                                         "return self.local_sum(v, weighted=False)"))
+    plant(mp, oschwarz.Schwarz, "apply", ("z = q + self.local_sum(v, weighted=False)",
+                                         "z = self.local_sum(v, weighted=False)"))
     return [(ts.test_preconditioner_dense_formula, (SOMMERFELD, AS2, B2))]
+
+
+def c64_mode_in_fp64(mp):
+    # the complex64 preconditioner silently computed in FP64
+    plant(mp, oschwarz.Schwarz, "__init__", ("self.ct = np.complex128 if precision == FP64 else np.complex64",
+                                            "self.ct = np.complex128"))
+    return [(ts.test_complex64_preconditioner_is_the_same_operator_rounded, (DIRICHLET, SAS2))]
+
+
+def c64_coarse_solve_dropped(mp):
+    plant(mp, oschwarz.Schwarz, "apply_Q", ("c = self.coarse.solve(c).astype(np.complex64)",
+                                           "c = c.astype(np.complex64)"))
+    return [(ts.test_complex64_preconditioner_is_the_same_operator_rounded, (SOMMERFELD, SHS2))]
+
+
+def c64_deflation_with_other_transfer(mp):
+    # the complex64 coarse correction prolongated with 1.001 R_0^T instead of R_0^T (a
+    # prolongation that is not the restriction's transpose), so R_0 (v - A Q v) != 0
+    plant(mp, oschwarz.Schwarz, "apply_Q", ("return self.R0p.T @ c",
+                                           "return self.R0p.T @ c + 1e-3 * (self.R0p.T @ c)"))
+    return [(ts.test_complex64_deflation_annihilates_the_coarse_residual, ())]
 
 
 # ---- Section 5 ---------------------------------------------------------------------
@@ -240,7 +261,8 @@ MUTATIONS = [
     sommerfeld_sign, edge_rows_not_halved, kappa_dropped, coupling_sign, dkappa_sign,
     dkappa_no_boundary_part, kappa_field_transposed, d_is_identity, overlap_one_sided, local_solve_conjugated,
     b2_half_cell_shift, b2_middle_piece, p1_hat_too_wide, mp1_keeps_coarse_boundary, galerkin_of_conj,
-    shs2_deflation_sign, sas2_without_d, as2_without_q, givens_sine_conjugated,
+    shs2_deflation_sign, sas2_without_d, as2_without_q, c64_mode_in_fp64, c64_coarse_solve_dropped,
+    c64_deflation_with_other_transfer, givens_sine_conjugated,
     gram_schmidt_conjugate_side, solution_without_preconditioner, gradient_sign, adjoint_without_conjugate,
 ]
 

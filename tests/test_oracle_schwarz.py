@@ -18,7 +18,7 @@ import numpy as np
 import pytest
 import scipy.sparse.linalg as spla
 
-from oracle import (AS1, AS2, B2, DIRICHLET, P1, SAS2, SHS2, SOMMERFELD, CoarseSpace,
+from oracle import (AS1, AS2, B2, C64, DIRICHLET, P1, SAS2, SHS2, SOMMERFELD, CoarseSpace,
                     Decomposition, Problem, Schwarz, givens, gmres)
 from oracle import adjoint
 from paper_2408_03571_gb300.inputs import (distinct_interior_nodes, kappa_field, point_source,
@@ -223,3 +223,72 @@ def test_adjoint_gradient_vs_finite_differences(bc):
         fd = (Lp - Lm) / (2 * eps)
         q = prob.index(i, j)
         assert grad[q] == pytest.approx(fd, rel=1e-5, abs=1e-9 * np.abs(grad).max())
+
+
+@pytest.mark.parametrize("bc", [DIRICHLET, SOMMERFELD])
+@pytest.mark.parametrize("kind", [AS1, AS2, SAS2, SHS2])
+def test_complex64_preconditioner_is_the_same_operator_rounded(bc, kind):
+    """The complex64 mode applies the same M^{-1} as the dense FP64 formula up to
+    complex64 rounding (amplified by the condition of the local and coarse
+    matrices: 1e-4 relative), is really computed in complex64 (differs from the FP64
+    apply by more than FP64 rounding would), and returns complex64 values widened
+    exactly to complex128."""
+    n, ns, ov, p = 33, 2, 2, 4
+    prob = Problem(n, bc, kappa_field(n, 30.0, seed=2))
+    A = prob.assemble()
+    coarse = None if kind == AS1 else B2
+    M64 = Schwarz(prob, A, ns, ov, kind, coarse, p)
+    M32 = Schwarz(prob, A, ns, ov, kind, coarse, p, precision=C64)
+    Ad = A.toarray()
+    N = prob.N
+    loc_w = np.zeros((N, N), dtype=complex)
+    loc = np.zeros((N, N), dtype=complex)
+    for s in M64.dec.subs:
+        R = _dense_R(s.idx, N)
+        Ai_inv = np.linalg.inv(R @ Ad @ R.T)
+        loc += R.T @ Ai_inv @ R
+        loc_w += R.T @ np.diag(s.d) @ Ai_inv @ R
+    if kind == AS1:
+        Minv = loc
+    else:
+        R0 = CoarseSpace(prob, coarse, p).R0.toarray()
+        Q = R0.T @ np.linalg.inv(R0 @ Ad @ R0.T) @ R0
+        Minv = {AS2: Q + loc, SAS2: Q + loc_w, SHS2: Q + loc_w @ (np.eye(N) - Ad @ Q)}[kind]
+    v = prob.grid_to_vec(random_complex_grid(n, seed=8))
+    ref = Minv @ v
+    z32 = M32.apply(v)
+    err = np.linalg.norm(z32 - ref) / np.linalg.norm(ref)
+    assert 1e-9 < err < 1e-4
+    assert np.linalg.norm(M64.apply(v) - ref) / np.linalg.norm(ref) < 1e-12
+    assert z32.dtype == np.complex128
+    assert np.array_equal(z32.astype(np.complex64).astype(np.complex128), z32)
+
+
+def test_complex64_deflation_annihilates_the_coarse_residual():
+    """SHS2 in complex64: the deflated residual w = v - A Q v has R_0 w = 0 up to
+    complex64 rounding (R_0 (I - A Q) = 0, Eq. (6)), i.e. the coarse correction
+    and the deflation use the same transfers."""
+    n, p = 65, 8
+    prob = Problem(n, DIRICHLET, 400.0)
+    A = prob.assemble_fast()
+    M = Schwarz(prob, A, 4, 2, SHS2, B2, p, precision=C64)
+    v = prob.grid_to_vec(random_complex_grid(n, seed=5)).astype(np.complex64)
+    w = v - M.Ap @ M.apply_Q(v)
+    R0 = CoarseSpace(prob, B2, p).R0
+    assert np.linalg.norm(R0 @ w) / np.linalg.norm(R0 @ v) < 2e-5
+
+
+@pytest.mark.parametrize("bc", [DIRICHLET, SOMMERFELD])
+def test_complex64_flexible_gmres_reaches_tol(bc):
+    """Flexible GMRES in FP64 around the complex64 preconditioner reaches the
+    tolerance in its true residual, in a few more steps than around the FP64 one
+    (a perturbed preconditioner), and its solution matches the FP64 solve to 1e-5."""
+    n, k = 65, 20.0
+    prob = Problem(n, bc, k * k)
+    A = prob.assemble_fast()
+    f = prob.grid_to_vec(point_source(n))
+    r64 = gmres(lambda x: A @ x, Schwarz(prob, A, 4, 2, SHS2, B2, 8).apply, f, 1e-7, 200, True)
+    r32 = gmres(lambda x: A @ x, Schwarz(prob, A, 4, 2, SHS2, B2, 8, precision=C64).apply, f, 1e-7, 200, True)
+    assert r32.converged and r32.relres_true <= 1.01e-7
+    assert r64.iterations <= r32.iterations <= r64.iterations + 6
+    assert np.linalg.norm(r32.x - r64.x) / np.linalg.norm(r64.x) < 1e-5

@@ -4,14 +4,18 @@
 Workload (one "step" = one full solve of the hot path): MP-1 (Dirichlet),
 point source 1/h^2 at (1/2, 1/2), k = 100, n = 1025 (h = 1/1024), 16 x 16
 square subdomains with 2 node layers of overlap, SHS2 preconditioner with the
-B_2 coarse space on H = 1/32, right-preconditioned GMRES without restart from
-u = 0 to ||f - A u|| <= 1e-6 ||f||.  The headline precision is MIXED
-(complex64 stencil, transfers and subdomain solves inside FP64 flexible GMRES,
-FP64 coarse solve); the FP64 path is timed beside it.  The preconditioner is
-set up once before the timed region (set-up time is reported separately).
+B_2 coarse space on H = 1/32, right-preconditioned flexible GMRES without
+restart from u = 0 to ||f - A u|| <= 1e-6 ||f||.  The headline precision is
+MIXED: complex64 stencil, transfers and subdomain solves, FP64 coarse solve,
+and an FP64 Arnoldi process (FP64 basis, FP64-accurate reorthogonalisation and
+update, FP64 Hessenberg least squares).  The preconditioner is set up once
+before the timed region (set-up time is reported separately).  Beside the
+headline: the FP64 path, the other orthogonalisations, and the other
+configurations of the workload family (the small MP-1 case, MP-2 at n = 513,
+the batched MP-2 set, the differentiable MP-2 solve), one solve each.
 
 Output: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
-oracle on the host cores instead (bounded sample, extrapolated per solve).
+oracle on the host cores instead (bounded sample per step, extrapolated per solve).
 """
 from __future__ import annotations
 
@@ -41,10 +45,13 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-wide-arm", action="store_true",
-                    help="skip the arm whose Krylov basis keeps complex64 remainders (about 48 bits)")
+    ap.add_argument("--no-alt-orth", action="store_true",
+                    help="skip the arms with the other orthogonalisations (all-FP64-FMA delayed CGS2, "
+                         "double-float bases of 32 and 48 bits)")
     ap.add_argument("--no-dedup-arm", action="store_true",
                     help="skip the MIXED arm with every subdomain factored separately")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the other configurations (small MP-1, MP-2 n=513, batched MP-2, gradient)")
     ap.add_argument("--stream", action="store_true",
                     help="issue the Arnoldi steps as stream launches (default: CUDA graphs of 8 steps, "
                          "HZS_SOLVE_GRAPH); the other issue mode is timed beside the value")
@@ -53,10 +60,14 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="launch the subdomain solve with its default shape instead of the set-up autotuner's")
     ap.add_argument("--workload", choices=["headline", "batched"], default="headline",
-                    help="batched: the MP-2 multi-problem batch (64 right-hand sides for each of "
-                         "(k, n) = (25, 257), (50, 257), (100, 513)) instead of the headline solve")
+                    help="batched: print the line of the batched MP-2 set (64 right-hand sides for each "
+                         "(k, n)) instead of the headline solve")
     ap.add_argument("--nrhs", type=int, default=64, help="right-hand sides per problem (batched workload)")
-    ap.add_argument("--cpu-steps", type=int, default=6, help="Arnoldi steps in the oracle sample")
+    ap.add_argument("--cpu-steps", type=int, default=6, help="Arnoldi steps in an oracle sample (reference arm)")
+    ap.add_argument("--oracle-full-solve", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--profile-solve", action="store_true",
+                    help="set up, then run exactly one stream-issued MIXED solve of the workload and exit "
+                         "(for profiler captures; prints its step count)")
     # smaller MP-1 instances of the same path, for profiling captures only
     ap.add_argument("--n", type=int, default=1025)
     ap.add_argument("--k", type=float, default=100.0)
@@ -152,116 +163,175 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- CPU oracle (baseline / reference arm)
-def oracle_sample(steps: int, iterations: int):
-    """Times the FP64 CPU oracle on this workload: set-up, then ``steps`` Arnoldi steps
-    of its GMRES; the per-solve time at ``iterations`` steps is extrapolated from the
-    measured preconditioner + operator cost per step and the measured cost of one
-    Gram-Schmidt projection (the orthogonalisation grows linearly with the step)."""
-    import numpy as np
-
-    from oracle import DIRICHLET, B2, Problem, Schwarz, SHS2, gmres
+def _oracle_setup():
+    from oracle import DIRICHLET, B2, Problem, Schwarz, SHS2
     from paper_2408_03571_gb300.inputs import point_source
 
     t0 = time.perf_counter()
     prob = Problem(N, DIRICHLET, K_WAVE ** 2)
     A = prob.assemble_fast()
     M = Schwarz(prob, A, NSUB, OVERLAP, SHS2, B2, P_COARSE)
-    t_setup = time.perf_counter() - t0
     f = prob.grid_to_vec(point_source(N))
-    # preconditioner + operator per step
+    return prob, A, M, f, time.perf_counter() - t0
+
+
+def oracle_full_solve():
+    """One complete solve of the headline workload by the FP64 CPU oracle as it stands
+    (right-preconditioned GMRES with modified Gram-Schmidt, SuperLU local solves), on
+    one core; prints its timings as a JSON line (run as a child process)."""
+    from oracle import gmres
+
+    prob, A, M, f, t_setup = _oracle_setup()
     t0 = time.perf_counter()
-    for _ in range(2):
-        A @ M.apply(f)
-    t_pm = (time.perf_counter() - t0) / 2
-    # one modified Gram-Schmidt projection (inner product + update) on a vector
-    v = f / np.linalg.norm(f)
+    res = gmres(lambda x: A @ x, M.apply, f, TOL, MAXIT)
+    t_solve = time.perf_counter() - t0
+    print(json.dumps({"t_setup_s": t_setup, "t_solve_s": t_solve, "iterations": res.iterations,
+                      "relres_true": res.relres_true, "converged": bool(res.converged)}), flush=True)
+
+
+def start_oracle_child():
+    """Starts oracle_full_solve in a fresh interpreter (before any CUDA call of this
+    process), pinned to one thread of every numerical library."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    size = ["--n", str(N), "--k", str(K_WAVE), "--nsub", str(NSUB), "--coarse-ratio", str(P_COARSE),
+            "--maxit", str(MAXIT)]
+    return subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-full-solve", *size],
+                            stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env, cwd=ROOT)
+
+
+def finish_oracle_child(proc, timeout_s: float):
+    try:
+        out, err = proc.communicate(timeout=timeout_s)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+        proc.communicate()
+        return None, f"oracle solve did not finish within {timeout_s:.0f} s"
+    for line in reversed(out.splitlines()):
+        if line.startswith("{"):
+            return json.loads(line), None
+    return None, "oracle solve failed: " + err.strip().splitlines()[-1] if err.strip() else "no output"
+
+
+def oracle_sample(prob, A, M, f, steps: int, iterations: int):
+    """A bounded sample of the oracle on the full workload: ``steps`` Arnoldi steps of its
+    GMRES (set-up done before), plus the measured cost of the preconditioner and operator
+    and of one Gram-Schmidt projection on basis vectors that are not cache-resident.  The
+    per-solve time at ``iterations`` steps is extrapolated from those two costs (the
+    orthogonalisation grows linearly with the step) and corrected by the ratio of the
+    sample's measured run to the same model at ``steps`` steps."""
+    import numpy as np
+
+    from oracle import gmres
+
+    t0 = time.perf_counter()
+    A @ M.apply(f)
+    t_pm = time.perf_counter() - t0
+    rng = np.random.default_rng(0)
+    basis = [rng.standard_normal(f.shape[0]) + 1j * rng.standard_normal(f.shape[0]) for _ in range(24)]
     w = np.array(f)
     t0 = time.perf_counter()
-    for _ in range(20):
+    for v in basis:
         h = np.vdot(v, w)
         w = w - h * v
-    t_proj = (time.perf_counter() - t0) / 20
-    # a real run of the oracle's GMRES for a few steps (checks the model)
+    t_proj = (time.perf_counter() - t0) / len(basis)
     t0 = time.perf_counter()
     res = gmres(lambda x: A @ x, M.apply, f, TOL, steps)
     t_run = time.perf_counter() - t0
-    model_run = steps * t_pm + t_proj * steps * (steps + 1) / 2
-    it = iterations
-    t_solve = it * t_pm + t_proj * it * (it + 1) / 2
-    return {
-        "t_setup_s": t_setup, "t_precond_plus_operator_s": t_pm, "t_projection_s": t_proj,
-        "t_sample_run_s": t_run, "sample_model_s": model_run, "iterations_assumed": it,
-        "t_solve_extrapolated_s": t_solve, "sample_steps": res.iterations,
-    }
+    model = lambda it: it * t_pm + t_proj * it * (it + 1) / 2
+    corr = t_run / model(res.iterations)
+    return {"t_precond_plus_operator_s": t_pm, "t_projection_s": t_proj, "t_sample_run_s": t_run,
+            "sample_steps": res.iterations, "model_correction": corr, "iterations_assumed": iterations,
+            "t_solve_extrapolated_s": corr * model(iterations)}
 
 
-def basis_dtype(bits: int) -> str:
+def basis_dtype(bits: int, kind: int) -> str:
+    if kind in (1, 3):
+        return "f64 (53 bits; stored as f32 head + 29-bit tail)" if kind == 1 else "c128"
     return {32: "f32 + bf16 remainder pairs (~32 bits)", 48: "double-float (2 x f32) pairs (~48 bits)",
             53: "c128"}.get(bits, f"{bits}-bit")
 
 
-def cpu_cores_used():
-    # numpy's vector ops used here are single-threaded; SuperLU is single-threaded
-    return 1
-
-
 def reference_arm(args, world, rank):
+    """The oracle on this machine's host cores, one bounded sample per step (the same metric,
+    unit and workload as the GPU arm; there is no installable reference implementation)."""
     if rank != 0:
         return
-    iters_assumed = 372   # the mixed GPU solve's iteration count at this workload (measured)
-    vals = []
-    for _ in range(args.warmup):
-        pass   # the oracle has no warm-up effects worth paying minutes for
-    last = None
+    # one core, as stated in the line (the numerical libraries are loaded after this)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    iters_assumed = 373   # the mixed GPU solve's iteration count at this workload (measured)
+    prob, A, M, f, t_setup = _oracle_setup()
+    for _ in range(min(args.warmup, 1)):
+        A @ M.apply(f)
+    samples, walls = [], []
     for _ in range(max(1, args.steps)):
-        last = oracle_sample(args.cpu_steps, iters_assumed)
-        vals.append(1.0 / last["t_solve_extrapolated_s"])
-    v = statistics.median(vals)
-    sample = (f"oracle (numpy/scipy FP64) at the full workload: set-up, then {args.cpu_steps} GMRES steps; "
-              f"per-solve time extrapolated to {iters_assumed} steps from the measured per-step "
-              f"preconditioner+operator time and per-projection Gram-Schmidt time")
+        t0 = time.perf_counter()
+        samples.append(oracle_sample(prob, A, M, f, args.cpu_steps, iters_assumed))
+        walls.append(time.perf_counter() - t0)
+    v = statistics.median(1.0 / s["t_solve_extrapolated_s"] for s in samples)
+    sample = (f"per step: {args.cpu_steps} GMRES steps of the FP64 oracle (numpy/scipy, one core) at the full "
+              f"workload plus its measured per-step preconditioner+operator and per-projection costs; "
+              f"value = one solve of {iters_assumed} steps extrapolated from them (set-up {t_setup:.1f} s, once)")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(walls),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
             "config": {"workload": WORKLOAD, "precision": "fp64 (CPU oracle)"},
-            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cpu_cores_used(), "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "detail": last}
+            "detail": samples[-1]}
     print(json.dumps(line), flush=True)
 
 
 # ----------------------------------------------------------------- GPU arm
-# (k, n, subdomains per axis) of the batched MP-2 workload: 64-node subdomains, B_2 with
-# H = 32h; (200, 1025) of the same family does not converge (kH = 6.25) and is left out
-BATCHED = ((25.0, 257, 4), (50.0, 257, 4), (100.0, 513, 8))
+# Batched MP-2 set: (k, n, subdomains per axis, H/h).  For each k the smallest n of
+# {257, 513, 1025} with kh <= 0.2, 64-node subdomains, and H the largest power-of-two
+# multiple of h with kH <= 1 (the robustness condition of Section 5): kH = 0.78.
+BATCHED = ((25.0, 257, 4, 8), (50.0, 257, 4, 4), (100.0, 513, 8, 4), (200.0, 1025, 16, 4))
+MAXIT_BATCHED = 300
 
 
-def batched_arm(args, world, rank, local):
-    """All problems of the batch solved concurrently (hzs_solve_batched), every right-hand
-    side a point source at a seeded interior node; one step = the whole batch."""
+def _peaks_file():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+def _ev_time(stream, fn, n):
+    """Calls fn() n times between CUDA events on stream; returns (ms, last result)."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    out = None
+    for _ in range(n):
+        out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def _res(r):
+    return {"iterations": r.iterations, "converged": bool(r.converged), "relres_true": r.relres_true}
+
+
+def batched_set(args, dev, graph: bool):
+    """All problems of the batched MP-2 set solved concurrently (hzs_solve_batched, every
+    right-hand side a point source at a seeded node, each problem on its own stream);
+    one step = the whole set.  Returns the measurements and the end-to-end timing."""
     import numpy as np
     import torch
 
-    from paper_2408_03571_gb300 import build, hzs
+    from paper_2408_03571_gb300 import hzs
     from paper_2408_03571_gb300.inputs import point_source, random_source_nodes
 
-    if world > 1:
-        torch.distributed.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    if rank == 0:
-        build.build()
-    if world > 1:
-        torch.distributed.barrier()
-    hzs.load()
-    dev = torch.device("cuda", local)
     grids, precs, rhs_host, rhs = [], [], [], []
     t0 = time.perf_counter()
-    for i, (k, n, nsub) in enumerate(BATCHED):
-        # a stream per problem, so that the problems' kernels overlap on the GPU
+    for i, (k, n, nsub, p) in enumerate(BATCHED):
         g = hzs.Grid(n, hzs.SOMMERFELD, k=k, nsub=nsub, overlap=2, stream=torch.cuda.Stream(dev))
         grids.append(g)
-        precs.append(hzs.Preconditioner(g, hzs.SHS2, hzs.COARSE_B2, 32, hzs.MIXED,
+        precs.append(hzs.Preconditioner(g, hzs.SHS2, hzs.COARSE_B2, p, hzs.MIXED,
                                         autotune=0 if args.no_autotune else 1))
         nodes = random_source_nodes(n, args.nrhs, 1000 + i)
         fh = torch.from_numpy(np.stack([point_source(n, nd) for nd in nodes])).pin_memory()
@@ -269,73 +339,101 @@ def batched_arm(args, world, rank, local):
         rhs.append(fh.to(dev))
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
-    for _ in range(args.warmup):
-        hzs.solve_batched(precs, rhs, TOL, MAXIT, graph=args.graph)
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
     stream = torch.cuda.current_stream(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    infos = None
-    for _ in range(args.steps):
-        _, infos = hzs.solve_batched(precs, rhs, TOL, MAXIT, graph=args.graph)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
-    # end to end: right-hand sides from pinned host memory, solutions back, inside the timed region
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(args.steps):
+    solve = lambda fs: hzs.solve_batched(precs, fs, TOL, MAXIT_BATCHED, graph=graph)
+    solve(rhs)
+    ms, (_, infos) = _ev_time(stream, lambda: solve(rhs), 1)
+
+    def e2e():
         fd = [f.to(dev, non_blocking=True) for f in rhs_host]
         stream.synchronize()            # the copies ran on this stream; the solves run on the problems'
-        outs, _ = hzs.solve_batched(precs, fd, TOL, MAXIT, graph=args.graph)
-        for u in outs:
-            u.cpu()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_e2e = max_over_ranks(e0.elapsed_time(e1), world, dev)
-    nsol = sum(len(r) for r in infos)
-    shapes = [P.info() for P in precs]
+        outs, _ = solve(fd)
+        return [u.cpu() for u in outs]
+    ms_e2e, _ = _ev_time(stream, e2e, 1)
     per = []
-    for (k, n, nsub), res, sh in zip(BATCHED, infos, shapes):
+    for (k, n, nsub, p), res, P in zip(BATCHED, infos, precs):
         its = [r.iterations for r in res]
-        per.append({"k": k, "n": n, "nrhs": len(res), "iterations_max": max(its),
-                    "subdomain_solve_shape": {key: sh[key] for key in ("tile_group", "tile_stages",
-                                                                       "tile_threads_per_row", "autotuned",
-                                                                       "apply_us_default", "apply_us_tuned")},
-                    "iterations_mean": float(np.mean(its)),
+        info = P.info()
+        per.append({"k": k, "n": n, "nsub": nsub, "H_over_h": p, "kH": k * p / (n - 1), "nrhs": len(res),
+                    "coarse_unknowns": info["coarse_unknowns"], "coarse_solver": info["coarse_solver"],
+                    "iterations_max": max(its), "iterations_mean": float(np.mean(its)),
                     "converged": int(sum(r.converged for r in res)),
                     "relres_true_max": max(r.relres_true for r in res)})
     for P in precs:
         P.close()
     for g in grids:
         g.close()
-    if rank != 0:
-        return
-    bytes_io = sum(f.numel() * 16 for f in rhs_host)
-    line = {
-        "metric": "batched MP-2 Helmholtz solves/s to rel. residual 1e-6 (3 problems x %d right-hand sides)"
-                  % args.nrhs,
-        "value": replica_throughput(nsol, ms / args.steps, world), "unit": "solves/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": "c64 preconditioner; Arnoldi basis as " + basis_dtype(min(r.basis_bits for res in infos for r in res))
-                 + "; f64 Hessenberg",
-        "data": "synthetic",
-        "config": {"workload": "MP-2 batch: (k, n) = (25, 257), (50, 257), (100, 513), 64-node subdomains, "
-                               "overlap 2, SHS2 with B2 H=32h, point sources at seeded nodes, all problems "
-                               "solved concurrently, right-hand sides of a problem in lockstep",
-                   "issue": "CUDA graphs of 8 Arnoldi steps" if args.graph else "stream launches",
-                   "l2": "working set larger than L2; no flush needed", "parallelism": f"replicas x{world}"},
-        "problems": per, "setup_s": setup_s,
-        "e2e": {"value": replica_throughput(nsol, ms_e2e / args.steps, world), "unit": "solves/s",
-                "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io},
-    }
-    print(json.dumps(line), flush=True)
+    nsol = sum(len(r) for r in infos)
+    return {"solves": nsol, "ms": ms, "ms_e2e": ms_e2e, "setup_s": setup_s, "problems": per,
+            "bytes_io": sum(f.numel() * 16 for f in rhs_host)}
+
+
+def other_configs(args, dev):
+    """The other configurations of the workload family, each solved after one warm-up
+    solve on its own handle: solves/s, steps and the FP64 true residual."""
+    import torch
+
+    from paper_2408_03571_gb300 import hzs
+    from paper_2408_03571_gb300.inputs import distinct_interior_nodes, kappa_field, point_source
+
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+
+    def run(n, bc, k, nsub, p, kind, coarse, prec, tol, reps, kappa=None):
+        g = hzs.Grid(n, bc, k=k, kappa=kappa, nsub=nsub, overlap=2)
+        P = hzs.Preconditioner(g, kind, coarse, p, prec)
+        f = torch.from_numpy(point_source(n)).to(dev)
+        P.solve(f, tol, MAXIT, graph=args.graph)
+        ms, (_, inf) = _ev_time(stream, lambda: P.solve(f, tol, MAXIT, graph=args.graph), reps)
+        P.close()
+        g.close()
+        return dict(_res(inf[0]), value=reps / (ms * 1e-3), unit="solves/s", ms_per_solve=ms / reps)
+
+    # small MP-1: n = 65, k = 20, 4 x 4 subdomains, B2 with H = 1/8, tol 1e-7
+    out["mp1_n65_k20"] = {
+        name: run(65, hzs.DIRICHLET, 20.0, 4, 8, hzs.SHS2, hzs.COARSE_B2, prec, 1e-7, 20)
+        for name, prec in (("fp64", hzs.FP64), ("mixed", hzs.MIXED))}
+    # MP-2: n = 513, k = 50, 8 x 8 subdomains, H = 1/16; one-level AS vs P1 vs B2, FP64 vs mixed
+    cfg2 = {}
+    for cname, kind, coarse in (("as1", hzs.AS1, hzs.COARSE_NONE), ("shs2_p1", hzs.SHS2, hzs.COARSE_P1),
+                                ("shs2_b2", hzs.SHS2, hzs.COARSE_B2)):
+        for pname, prec in (("fp64", hzs.FP64), ("mixed", hzs.MIXED)):
+            cfg2[f"{cname}_{pname}"] = run(513, hzs.SOMMERFELD, 50.0, 8, 32, kind, coarse, prec, 1e-7, 2)
+    out["mp2_n513_k50"] = cfg2
+    # differentiable MP-2: n = 1025, kappa = (100 (1 + 0.2 g))^2, forward solve, adjoint solve of
+    # the receivers' misfit and the kappa gradient, MIXED, tol 1e-6
+    n = 1025
+    kap = torch.from_numpy(kappa_field(n, 100.0, seed=2001)).to(dev)
+    g = hzs.Grid(n, hzs.SOMMERFELD, kappa=kap, nsub=16, overlap=2)
+    t0 = time.perf_counter()
+    P = hzs.Preconditioner(g, hzs.SHS2, hzs.COARSE_B2, 32, hzs.MIXED, dedup_tiles=False)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    f = torch.from_numpy(point_source(n)).to(dev)
+    rec = distinct_interior_nodes(n, 64, seed=2003)
+    idx = torch.tensor([j * n + i for (i, j) in rec], device=dev)
+
+    def fwd_adj():
+        u, i1 = P.solve(f, TOL, MAXIT, graph=args.graph)
+        r = torch.zeros_like(u).view(-1)
+        r[idx] = u.view(-1)[idx]
+        lam, i2 = P.adjoint_solve(r.view(n, n), TOL, MAXIT, graph=args.graph)
+        P.kappa_gradient(u, lam)
+        return i1[0], i2[0]
+    fwd_adj()
+    ms, (i1, i2) = _ev_time(stream, fwd_adj, 1)
+    P.close()
+    g.close()
+    out["mp2_n1025_kappa_field_gradient"] = {
+        "value": 1.0 / (ms * 1e-3), "unit": "forward+adjoint solve pairs/s", "ms_per_pair": ms, "setup_s": setup_s,
+        "forward": _res(i1), "adjoint": _res(i2),
+        "note": "forward solve, adjoint solve of the 64 receivers' values and the kappa gradient kernel"}
+    return out
 
 
 def gpu_arm(args, world, rank, local):
+    # the oracle's full solve runs on one host core beside the GPU work (started before CUDA)
+    child = start_oracle_child() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     import torch
 
     from paper_2408_03571_gb300 import build, hzs
@@ -352,6 +450,7 @@ def gpu_arm(args, world, rank, local):
     hzs.load()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
+    pipes = hzs.pipe_peaks()
     f_host = torch.from_numpy(point_source(N)).pin_memory()
     f = f_host.to(dev)
     grid = hzs.Grid(N, hzs.DIRICHLET, k=K_WAVE, nsub=NSUB, overlap=OVERLAP)
@@ -362,30 +461,40 @@ def gpu_arm(args, world, rank, local):
             torch.distributed.barrier()
             torch.cuda.synchronize()
 
-    def timed_solves(P, steps, warmup, e2e=False, profile=False, wide=False, graph=False):
+    def timed_solves(P, steps, warmup, e2e=False, **kw):
         u = torch.empty_like(f)
         u_host = torch.empty_like(f_host).pin_memory()
-        infos = []
         for _ in range(warmup):
-            P.solve(f, TOL, MAXIT, out=u, wide_basis=wide, graph=graph)
+            P.solve(f, TOL, MAXIT, out=u, **kw)
         barrier()
+        infos = []
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(steps):
             if e2e:
                 fd = f_host.to(dev, non_blocking=True)
-                _, inf = P.solve(fd, TOL, MAXIT, out=u, profile=profile, wide_basis=wide, graph=graph)
+                _, inf = P.solve(fd, TOL, MAXIT, out=u, **kw)
                 u_host.copy_(u, non_blocking=True)
             else:
-                _, inf = P.solve(f, TOL, MAXIT, out=u, profile=profile, wide_basis=wide, graph=graph)
+                _, inf = P.solve(f, TOL, MAXIT, out=u, **kw)
             infos.append(inf[0])
         e1.record(stream)
         barrier()
-        ms = e0.elapsed_time(e1)
-        return max_over_ranks(ms, world, dev), infos, u
+        return max_over_ranks(e0.elapsed_time(e1), world, dev), infos
 
-    out = {}
+    def arm(P, steps, warmup, note, **kw):
+        ms, infos = timed_solves(P, steps, warmup, **kw)
+        i0 = infos[-1]
+        d = {"value": replica_throughput(len(infos), ms, world), "unit": "solves/s", "ms_per_step": ms / len(infos),
+             "iterations": i0.iterations, "relres_est": i0.relres_est, "relres_true": i0.relres_true,
+             "basis_bits": i0.basis_bits, "orth_kind": i0.orth_kind, "note": note}
+        if kw.get("profile"):
+            d.update({"t_precond_ms": i0.t_precond_ms, "t_matvec_ms": i0.t_matvec_ms, "t_orth_ms": i0.t_orth_ms,
+                      "t_orth_dot_ms": i0.t_orth_dot_ms, "t_orth_update_ms": i0.t_orth_update_ms})
+        return d, infos
+
+    g_kw = {"graph": args.graph}
     # ---- mixed (headline)
     t0 = time.perf_counter()
     Pm = hzs.Preconditioner(grid, hzs.SHS2, hzs.COARSE_B2, P_COARSE, hzs.MIXED,
@@ -393,180 +502,236 @@ def gpu_arm(args, world, rank, local):
     torch.cuda.synchronize()
     setup_mixed_s = time.perf_counter() - t0
     shape = Pm.info()
-    # the headline value: solves without per-launch events
     clk = ClockSampler(local)
     clk.start()
-    ms_tot, infos_plain, u = timed_solves(Pm, args.steps, args.warmup, graph=args.graph)
+    ms_tot, infos_plain = timed_solves(Pm, args.steps, args.warmup, **g_kw)
     clocks = clk.stop()
     # the same solves with CUDA events around every launch: phase times and the roofline
-    ms_prof, infos, _ = timed_solves(Pm, args.steps, 0, profile=True)
-    # the other way of issuing the Arnoldi steps (stream launches, or graphs with --stream)
+    nprof = max(2, args.steps // 4)
+    ms_prof, infos = timed_solves(Pm, nprof, 0, profile=True)
     issue_alt = None
     if not args.no_alt_arm:
-        ms_alt, infos_alt, _ = timed_solves(Pm, args.steps, 1, graph=not args.graph)
-        issue_alt = {"value": replica_throughput(args.steps, ms_alt, world), "unit": "solves/s",
-                     "ms_per_step": ms_alt / args.steps, "iterations": infos_alt[-1].iterations,
-                     "relres_true": infos_alt[-1].relres_true,
-                     "issue": "stream launches" if args.graph else "CUDA graphs of 8 Arnoldi steps"}
-    ms_e2e, infos_e2e, _ = timed_solves(Pm, args.steps, 0, e2e=True, graph=args.graph)
-    # ---- the same solve with the basis remainders kept as complex64 (about 48 bits)
-    wide = None
-    if not args.no_wide_arm:
-        ms_w, infos_w, _ = timed_solves(Pm, max(1, args.steps // 2), 1, profile=True, wide=True)
-        i0 = infos_w[-1]
-        wide = {"value": replica_throughput(len(infos_w), ms_w, world), "unit": "solves/s",
-                "ms_per_step": ms_w / len(infos_w), "iterations": i0.iterations,
-                "relres_est": i0.relres_est, "relres_true": i0.relres_true, "basis_bits": i0.basis_bits,
-                "t_orth_ms": i0.t_orth_ms,
-                "note": "Krylov basis as complex64 + complex64 remainder (16 B an entry; the default "
-                        "for tol < 1e-7)"}
+        issue_alt, _ = arm(Pm, max(2, args.steps // 4), 1, "stream launches" if args.graph else
+                           "CUDA graphs of 8 Arnoldi steps", graph=not args.graph)
+    ms_e2e, _ = timed_solves(Pm, max(2, args.steps // 2), 0, e2e=True, **g_kw)
+    alt = {}
+    if not args.no_alt_orth:
+        alt["orth_dfma"], _ = arm(Pm, 2, 1, "the same delayed CGS2 with every FP64-accurate sum in FP64 FMAs on a "
+                                  "complex128 basis (no FP32-pipe share)", orth_dfma=True, profile=True)
+        alt["basis_df_32"], _ = arm(Pm, 2, 1, "delayed CGS2 on a double-float basis with bf16 remainders (about 32 "
+                                    "bits), complex64 dot products: not an FP64 Arnoldi", basis_df=True, profile=True)
+        alt["basis_df_48"], _ = arm(Pm, 2, 1, "delayed CGS2 on a double-float basis with complex64 remainders "
+                                    "(about 48 bits), complex64 dot products: not an FP64 Arnoldi", basis_df=True,
+                                    wide_basis=True, profile=True)
     Pm.close()
-    # ---- MIXED with one factor per subdomain (no sharing of identical factors): the
-    # subdomain solves then stream 256 distinct factor sets per apply, as for a kappa field
     dedup_off = None
     if not args.no_dedup_arm:
         Pn = hzs.Preconditioner(grid, hzs.SHS2, hzs.COARSE_B2, P_COARSE, hzs.MIXED, dedup_tiles=False)
-        ms_n, infos_n, _ = timed_solves(Pn, max(1, args.steps // 2), 1, profile=True)
+        dedup_off, _ = arm(Pn, 2, 1, "every subdomain factor stored and streamed separately (no sharing of "
+                           "identical factors)", profile=True)
         Pn.close()
-        i0 = infos_n[-1]
-        dedup_off = {"value": replica_throughput(len(infos_n), ms_n, world), "unit": "solves/s",
-                     "ms_per_step": ms_n / len(infos_n), "iterations": i0.iterations,
-                     "relres_true": i0.relres_true, "t_precond_ms": i0.t_precond_ms,
-                     "note": "every subdomain factor stored and streamed separately (no sharing of "
-                             "identical factors)"}
-    # ---- FP64 arm
     fp64 = None
     if not args.no_fp64:
         t0 = time.perf_counter()
         Pd = hzs.Preconditioner(grid, hzs.SHS2, hzs.COARSE_B2, P_COARSE, hzs.FP64)
         torch.cuda.synchronize()
         setup_fp64_s = time.perf_counter() - t0
-        ms_d, infos_d, _ = timed_solves(Pd, max(1, args.steps // 2), 1, profile=True)
+        fp64, _ = arm(Pd, 2, 1, "complex128 throughout, classical CGS2 in FP64", profile=True)
+        fp64["setup_s"] = setup_fp64_s
         Pd.close()
-        i0 = infos_d[-1]
-        fp64 = {"value": replica_throughput(len(infos_d), ms_d, world), "unit": "solves/s",
-                "ms_per_step": ms_d / len(infos_d), "iterations": i0.iterations,
-                "relres_true": i0.relres_true, "setup_s": setup_fp64_s,
-                "t_precond_ms": i0.t_precond_ms, "t_matvec_ms": i0.t_matvec_ms, "t_orth_ms": i0.t_orth_ms}
     grid.close()
+    workloads = None
+    if not args.no_workloads:
+        workloads = other_configs(args, dev)
+        b = batched_set(args, dev, args.graph)
+        workloads["batched_mp2"] = {
+            "value": replica_throughput(b["solves"], b["ms"], world), "unit": "solves/s", "ms_per_set": b["ms"],
+            "e2e_value": replica_throughput(b["solves"], b["ms_e2e"], world), "setup_s": b["setup_s"],
+            "problems": b["problems"],
+            "note": "4 problems x 64 point sources at seeded nodes, solved concurrently (one stream per problem, "
+                    "right-hand sides of a problem in lockstep)"}
+    gpu_line_and_print(args, world, rank, locals())
 
-    # ---- roofline of the dominant kernels: the two passes of the delayed CGS2 over
-    # the double-float basis, complex64 leading words + remainders: eb = 12 B per basis
-    # entry with bf16 remainders (tol >= 1e-7), 16 B with complex64 remainders.
-    # Algorithmic HBM bytes at step j (Nu unknowns):
-    #   dot pass    k_dcgs_dot:    leading words of basis vectors 0..j-1, u~_j and w (8 (j + 2) Nu)
-    #   update pass k_dcgs_update: basis vectors 0..j-1 (eb j Nu), u~_j and w read and written (4 eb Nu)
-    # Step j = it completes the last column (dot pass only); its update returns at once.
+
+def gpu_line_and_print(args, world, rank, L):
+    """Assembles the JSON line of the GPU arm from the measurements in L."""
+    import torch
+    infos, infos_plain, pipes = L["infos"], L["infos_plain"], L["pipes"]
     last = infos[-1]
     it = last.iterations
     Nu = (N - 2) ** 2
-    eb = 12 if last.basis_bits == 32 else 16
-    dot_bytes = sum(8 * (j + 2) * Nu for j in range(it + 1))
-    upd_bytes = sum(eb * (j + 4) * Nu for j in range(it))
+    # ---- roofline of the two basis passes of the delayed CGS2 on the f53 basis (16 B a
+    # basis entry: FP32 heads + 29-bit tails).  Algorithmic HBM bytes at step j:
+    #   dot pass:    basis vectors 0..j-1, u~_j and w (16 (j + 2) Nu)
+    #   update pass: basis vectors 0..j-1 (16 j Nu), u~_j and w read and written (64 Nu)
+    # Step j = it completes the last column (dot pass only; its update returns at once).
+    dot_bytes = sum(16 * (j + 2) * Nu for j in range(it + 1))
+    upd_bytes = sum(16 * (j + 4) * Nu for j in range(it))
     t_dot = statistics.mean(i.t_orth_dot_ms for i in infos) * 1e-3
     t_upd = statistics.mean(i.t_orth_update_ms for i in infos) * 1e-3
     orth_s = statistics.mean(i.t_orth_ms for i in infos) * 1e-3
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            peaks = json.load(fh)
-    except Exception:
-        pass
+    peaks = _peaks_file()
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = ("MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)" if "hbm_gbs" in peaks
                 else "fallback 6800 GB/s")
+    # FP64-accurate multiply-adds of a pass: 4 real multiply-adds (8 flops) per basis entry for
+    # alpha (dot pass) or for sum c_i V_i (update pass), shared between the FP64 FMAs and the
+    # FP32 error-free arithmetic; reported against the measured FP64 FMA rate
+    macs = 8.0 * sum(j * Nu for j in range(it + 1))
 
-    def pass_roofline(name, nbytes, t):
+    def pass_roofline(name, nbytes, t, nl):
         a = nbytes / t / 1e9 if t > 0 else 0.0
         return {"kernel": name, "bound": "hbm", "achieved": a, "peak": hbm_peak, "unit": "GB/s",
-                "frac": a / hbm_peak, "traffic": None, "peak_source": peak_src,
-                "bytes_per_solve": nbytes, "time_per_solve_s": t,
-                "timing": "CUDA events around every launch of the kernel on the solve stream, over a "
-                          "timed region of the same number of solves as the value's"}
-    r_dot = pass_roofline("k_dcgs_dot (delayed CGS2 multi-dot on the leading words of the basis)", dot_bytes,
-                          t_dot)
-    r_upd = pass_roofline("k_dcgs_update (delayed CGS2 basis update, double-float)", upd_bytes, t_upd)
-    # DRAM traffic of the two passes from one ncu capture per basis width (MP-1 k=100
-    # n=513, the launches of step 200), as a ratio to the algorithmic bytes of that
-    # launch; traffic grows with the units processed, so the average launch here is
-    # scaled by those ratios.  None: no capture of the current kernel.
-    dot_ratio = (1.021, "430.9 MB against 421.9 MB")
-    traffic_ratio = {16: {"dot": dot_ratio, "upd": None},
-                     12: {"dot": dot_ratio, "upd": (1.079, "689.7 MB against 639.2 MB")}}[eb]
-    for r_, nbytes, nl, key in ((r_dot, dot_bytes, it + 1, "dot"), (r_upd, upd_bytes, it, "upd")):
-        r_["launches"] = nl
-        r_["bytes_per_launch"] = nbytes / nl
-        r_["basis_bytes_per_entry"] = 8 if key == "dot" else eb
-        tr = traffic_ratio[key]
-        r_["traffic"] = None if tr is None else tr[0] * nbytes / nl
-        r_["traffic_source"] = (
-            "no ncu capture of this kernel version" if tr is None else
-            "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch (n=513, step 200: "
-            f"{tr[1]} algorithmic = {tr[0]}), scaled to this workload's average launch")
+                "frac": a / hbm_peak, "traffic": None, "traffic_source": "no ncu capture of this kernel version",
+                "peak_source": peak_src + ", of measured", "bytes_per_solve": nbytes, "time_per_solve_s": t,
+                "launches": nl, "bytes_per_launch": nbytes / nl,
+                "fp64_equivalent_tflops": macs / t / 1e12 if t > 0 else 0.0,
+                "fp64_fma_peak_tflops": pipes["fp64_tflops"],
+                "timing": "CUDA events around every launch of the kernel on the solve stream"}
+    r_dot = pass_roofline("k_s53_dot (delayed CGS2 dot pass on the f53 basis: FP64-accurate alpha, complex64 b)",
+                          dot_bytes, t_dot, it + 1)
+    r_upd = pass_roofline("k_s53_update (delayed CGS2 update pass on the f53 basis, FP64-accurate)",
+                          upd_bytes, t_upd, it)
     roofline = dict(r_upd if t_upd >= t_dot else r_dot)
     roofline["other_pass"] = r_dot if t_upd >= t_dot else r_upd
-    roofline["orth_group"] = {"time_per_solve_s": orth_s,
-                              "achieved_gbs": (dot_bytes + upd_bytes) / orth_s / 1e9,
-                              "note": "both passes plus the reduction, Givens and scale kernels"}
+    roofline["orth_group"] = {"time_per_solve_s": orth_s, "achieved_gbs": (dot_bytes + upd_bytes) / orth_s / 1e9,
+                              "note": "both passes plus the reduction, Givens, encode and scale kernels"}
+    fp64 = L["fp64"]
     if fp64 is not None:
         # all-FP64 CGS2: 4 passes x (j+1) Nu complex multiply-adds (8 flops each) on the FP64 pipe
-        fp64_peak = 2.0 * 2.0 * 152 * 2.070e9     # 2 DFMA/clk/SM x 2 flops x 152 SMs x 2070 MHz
         it64 = fp64["iterations"]
         flops64 = sum(32.0 * (j + 1) * Nu for j in range(it64))
         t64 = fp64["t_orth_ms"] * 1e-3
         fp64["roofline"] = {"kernel": "CGS2 orthogonalisation, FP64 (k_multidot<double2> + k_axpy_multi)",
-                            "bound": "alu", "achieved": flops64 / t64 / 1e12, "peak": fp64_peak / 1e12,
-                            "unit": "TFLOP/s", "frac": flops64 / t64 / fp64_peak,
-                            "peak_source": "FP64 pipe: 2 DFMA/clk/SM x 152 SMs x 2070 MHz"}
-
-    value = replica_throughput(args.steps, ms_tot, world)
+                            "bound": "alu", "achieved": flops64 / t64 / 1e12, "peak": pipes["fp64_tflops"],
+                            "unit": "TFLOP/s", "frac": flops64 / t64 / 1e12 / pipes["fp64_tflops"],
+                            "peak_source": "hzs_pipe_peaks FP64 FMA rate measured in this run, of measured"}
+    world_ = world
+    steps = args.steps
+    value = replica_throughput(steps, L["ms_tot"], world_)
+    i_last = infos_plain[-1]
     line = {
-        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_tot / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "c64 preconditioner; Arnoldi basis as " + basis_dtype(last.basis_bits) + "; f64 Hessenberg, "
-                 "coarse solve, outer operator and solution",
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world_, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": L["ms_tot"] / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": ("c64 preconditioner (stencil, transfers, subdomain solves); f64 coarse solve, outer operator, "
+                  "Arnoldi basis (" + basis_dtype(i_last.basis_bits, i_last.orth_kind) + "), FP64-accurate "
+                  "reorthogonalisation and update, f64 Hessenberg least squares and solution"),
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": "mixed", "n": N, "k": K_WAVE, "nsub": NSUB,
-                   "overlap": OVERLAP, "coarse_ratio": P_COARSE, "tol": TOL, "basis_bits": last.basis_bits,
+                   "overlap": OVERLAP, "coarse_ratio": P_COARSE, "tol": TOL, "basis_bits": i_last.basis_bits,
                    "l2": "working set larger than L2 (Krylov basis ~6 GB); no flush needed",
                    "issue": "CUDA graphs of 8 Arnoldi steps" if args.graph else "stream launches",
-                   "parallelism": f"replicas x{world}"},
-        "iterations": infos_plain[-1].iterations, "relres_est": infos_plain[-1].relres_est,
-        "relres_true": infos_plain[-1].relres_true,
-        "setup_s": setup_mixed_s,
-        "subdomain_solve_shape": shape,
-        "profiled": {"value": replica_throughput(args.steps, ms_prof, world), "unit": "solves/s",
-                     "note": "the same solves with CUDA events around every launch (phases and roofline)"},
-        "issue_alt": issue_alt,
+                   "parallelism": f"replicas x{world_}"},
+        "iterations": i_last.iterations, "relres_est": i_last.relres_est, "relres_true": i_last.relres_true,
+        "setup_s": L["setup_mixed_s"], "subdomain_solve_shape": L["shape"],
+        "profiled": {"value": replica_throughput(len(infos), L["ms_prof"], world_), "unit": "solves/s",
+                     "note": "solves with CUDA events around every launch (phases and roofline)"},
+        "issue_alt": L["issue_alt"],
         "phases_ms": {"precond": last.t_precond_ms, "matvec": last.t_matvec_ms, "orth": last.t_orth_ms,
+                      "orth_dot": last.t_orth_dot_ms, "orth_update": last.t_orth_update_ms,
                       "solve": last.t_solve_ms},
         "roofline": roofline,
-        "e2e": {"value": replica_throughput(args.steps, ms_e2e, world), "unit": "solves/s",
+        "e2e": {"value": replica_throughput(max(2, steps // 2), L["ms_e2e"], world_), "unit": "solves/s",
                 "h2d_bytes_per_step": N * N * 16, "d2h_bytes_per_step": N * N * 16},
         "gpu_launches": int(sum(i.launches for i in infos_plain)),
-        "clocks": clocks,
+        "clocks": L["clocks"],
+        "pipe_peaks": pipes,
         "fp64": fp64,
-        "wide_basis": wide,
-        "dedup_off": dedup_off,
+        "orthogonalisations": L["alt"],
+        "dedup_off": L["dedup_off"],
+        "workloads": L["workloads"],
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        s = oracle_sample(args.cpu_steps, it)
-        line["cpu_baseline"] = {
-            "value": 1.0 / s["t_solve_extrapolated_s"], "unit": "solves/s", "cores": cpu_cores_used(),
-            "kind": "oracle",
-            "sample": (f"oracle set-up + {args.cpu_steps} GMRES steps at the full workload; per-solve time "
-                       f"extrapolated to {it} steps ({s['t_solve_extrapolated_s']:.0f} s)"),
-            "detail": s}
-    if world > 1:
+    child = L["child"]
+    if child is not None:
+        res, why = finish_oracle_child(child, 600.0)
+        if res is not None:
+            line["cpu_baseline"] = {
+                "value": 1.0 / res["t_solve_s"], "unit": "solves/s", "cores": 1, "kind": "oracle",
+                "sample": (f"one complete solve of this workload by the FP64 oracle (numpy/scipy, SuperLU local "
+                           f"solves, modified Gram-Schmidt GMRES) on one host core: {res['iterations']} steps in "
+                           f"{res['t_solve_s']:.1f} s after a {res['t_setup_s']:.1f} s set-up; SuperLU solves hold "
+                           "Python's GIL, so threads over the subdomains do not help"),
+                "detail": res}
+        else:
+            line["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": why}
+    if world_ > 1:
         torch.distributed.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
+def batched_arm(args, world, rank, local):
+    """The batched MP-2 set as its own line (one step = the whole set)."""
+    import torch
+
+    from paper_2408_03571_gb300 import build, hzs
+
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    hzs.load()
+    dev = torch.device("cuda", local)
+    runs = [batched_set(args, dev, args.graph) for _ in range(max(1, args.steps))]
+    ms = max_over_ranks(sum(r["ms"] for r in runs), world, dev)
+    ms_e2e = max_over_ranks(sum(r["ms_e2e"] for r in runs), world, dev)
+    nsol = sum(r["solves"] for r in runs)
+    if rank != 0:
+        return
+    line = {
+        "metric": "batched MP-2 Helmholtz solves/s to rel. residual 1e-6 (4 problems x %d right-hand sides)"
+                  % args.nrhs,
+        "value": replica_throughput(nsol, ms, world), "unit": "solves/s", "n_gpus": world, "steps": len(runs),
+        "warmup": 1, "ms_per_step": ms / len(runs), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64 preconditioner; FP64 Arnoldi (f53 basis); f64 Hessenberg",
+        "data": "synthetic",
+        "config": {"workload": "MP-2 batch: (k, n) = (25, 257), (50, 257), (100, 513), (200, 1025), 64-node "
+                               "subdomains, overlap 2, SHS2 with B2 and H = the largest 2^m h with kH <= 1, point "
+                               "sources at seeded nodes, all problems concurrently",
+                   "issue": "CUDA graphs of 8 Arnoldi steps" if args.graph else "stream launches",
+                   "l2": "working set larger than L2; no flush needed", "parallelism": f"replicas x{world}"},
+        "problems": runs[-1]["problems"], "setup_s": runs[-1]["setup_s"],
+        "e2e": {"value": replica_throughput(nsol, ms_e2e, world), "unit": "solves/s",
+                "h2d_bytes_per_step": runs[-1]["bytes_io"], "d2h_bytes_per_step": runs[-1]["bytes_io"]},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def profile_solve(args):
+    """One MIXED solve of the workload, stream-issued (every kernel a plain launch), after set-up."""
+    import torch
+
+    from paper_2408_03571_gb300 import build, hzs
+    from paper_2408_03571_gb300.inputs import point_source
+
+    build.build()
+    hzs.load()
+    f = torch.from_numpy(point_source(N)).cuda()
+    g = hzs.Grid(N, hzs.DIRICHLET, k=K_WAVE, nsub=NSUB, overlap=OVERLAP)
+    P = hzs.Preconditioner(g, hzs.SHS2, hzs.COARSE_B2, P_COARSE, hzs.MIXED)
+    torch.cuda.synchronize()
+    _, inf = P.solve(f, TOL, MAXIT)
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": WORKLOAD, "iterations": inf[0].iterations, "launches": inf[0].launches,
+                      "relres_true": inf[0].relres_true}), flush=True)
+    P.close()
+    g.close()
+
+
 def main():
     args = parse()
     args.graph = not args.stream
+    if args.oracle_full_solve:
+        oracle_full_solve()
+        return
     world, rank, local = dist_setup(args)
+    if args.profile_solve:
+        profile_solve(args)
+        return
     if args.impl == "reference":
         reference_arm(args, world, rank)
         return

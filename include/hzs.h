@@ -71,8 +71,7 @@ typedef enum { HZS_COARSE_NONE = 0, HZS_COARSE_P1 = 1, HZS_COARSE_B2 = 2 } hzs_c
 
 /* HZS_FP64: every step in complex128.  HZS_MIXED: flexible GMRES (Section 5)
  * around a preconditioner whose stencil, transfers and subdomain solves run in
- * complex64, with the coarse solve in FP64 (the dense inverse's product as a
- * double-float pair on the FP32 pipes; the block LU in FP64).  The outer
+ * complex64, with the coarse solve in FP64 (its factorisation and its product).  The outer
  * matrix-vector product, the Krylov basis (complex128), the Hessenberg least
  * squares and the solution are FP64; the orthogonalisation is the delayed CGS2
  * whose reorthogonalisation coefficients and first-projection update are FP64
@@ -85,10 +84,13 @@ typedef enum { HZS_FP64 = 0, HZS_MIXED = 1 } hzs_precision;
  *   k        : constant wavenumber, used when kappa_dev is NULL (kappa = k^2).
  *   kappa_dev: optional device array of n*n doubles, the squared wavenumber
  *              kappa = k(x,y)^2 > 0 at every node; copied at creation.
- *   nsub     : subdomains per axis; must divide n-1.  Subdomain a owns grid
- *              nodes [a w, (a+1) w) per axis, w = (n-1)/nsub, the last one
+ *   nsub     : subdomains along x; must divide n-1.  Subdomain a owns grid
+ *              nodes [a w, (a+1) w) along x, w = (n-1)/nsub, the last one
  *              also node n-1 (MP-1 drops the boundary nodes).
- *   overlap  : node layers added on each side of an owned block, >= 0. */
+ *   overlap  : node layers added on each side of an owned block, >= 0, at
+ *              most half the narrower subdomain width.
+ *   nsub_y   : subdomains along y (same rule); 0 = nsub (a square grid of
+ *              subdomains). */
 typedef struct {
     int n;
     hzs_bc bc;
@@ -96,6 +98,7 @@ typedef struct {
     const double* kappa_dev;
     int nsub;
     int overlap;
+    int nsub_y;
 } hzs_grid_desc;
 
 /* How the exact coarse solve A_0^{-1} (Eq. 4) is carried out.  Both are exact
@@ -105,6 +108,12 @@ typedef struct {
  * dependent block products per apply (memory ~3 |G_H|^{3/2} s).  AUTO: DENSE up
  * to 4096 coarse unknowns, BLOCK above. */
 typedef enum { HZS_COARSE_SOLVER_AUTO = 0, HZS_COARSE_SOLVER_DENSE = 1, HZS_COARSE_SOLVER_BLOCK = 2 } hzs_coarse_solver;
+
+/* The diagonal D_i of SAS2 and SHS2 (Eqs. 5-6; Section 3 asks only for
+ * sum_i R_i^T D_i R_i = I).  OWNER: 1 on the nodes subdomain i owns, 0 on its
+ * overlap (restricted additive Schwarz).  MULTIPLICITY: 1/m(x) on every node x
+ * of subdomain i, m(x) the number of subdomains containing x. */
+typedef enum { HZS_SCALING_OWNER = 0, HZS_SCALING_MULTIPLICITY = 1 } hzs_scaling_mode;
 
 /* Preconditioner set-up (Sections 3 and 4).
  *   coarse_ratio : p = H/h, >= 2, must divide n-1 (ignored for HZS_AS1).
@@ -130,6 +139,7 @@ typedef struct {
     int dedup_tiles;
     int coarse_solver;
     int autotune;
+    int scaling_mode;      /* an hzs_scaling_mode (0 = OWNER); used by SAS2 and SHS2 */
 } hzs_precond_desc;
 
 /* GMRES controls (Section 5): right preconditioning, zero initial guess, no
@@ -144,18 +154,26 @@ typedef struct {
 #define HZS_SOLVE_PROFILE 1
 /* Orthogonalisation of the HZS_MIXED solve.  Default: the delayed CGS2
  * (reorthogonalisation of vector j fused with the first projection of step j+1:
- * two passes over the basis per step) on the complex128 basis, with the
+ * two passes over the basis per step) on an FP64 basis, with the
  * reorthogonalisation dot products, the norms and the first-projection update
- * in FP64 and the first-projection dot products in complex64 on the leading 24
- * bits of each entry (the reorthogonalisation of the next step removes what
- * their rounding leaves).  HZS_SOLVE_ORTH_FP64: classical CGS2 with every dot
- * product and update in FP64 (four passes per step), as HZS_FP64 uses.
- * HZS_SOLVE_BASIS_DF: the delayed CGS2 on a narrower double-float basis
- * (complex64 rounding + remainder, see HZS_SOLVE_BASIS_WIDE) with complex64 dot
- * products and double-float updates: fewer bytes and no FP64 arithmetic, but
- * the basis and its arithmetic are not FP64.  No effect with HZS_FP64. */
+ * computed to FP64 accuracy and the first-projection dot products in complex64 on
+ * the leading 24 bits of each entry (the reorthogonalisation of the next step
+ * removes what their rounding leaves).  The basis holds each FP64 value exactly
+ * as an FP32 head and a 29-bit tail (16 bytes a complex entry, as complex128), and
+ * each pass sums part of the basis with FP64 fused multiply-adds and the rest in
+ * FP32 three-word expansions whose error bound is below FP64's (the FP64 pipe of
+ * the part is 1/64 of its FP32 rate).  HZS_SOLVE_ORTH_DFMA: the same delayed CGS2
+ * with every one of those sums in FP64 fused multiply-adds on a complex128 basis
+ * (also taken by default when maxit exceeds about 2300).  HZS_SOLVE_ORTH_FP64:
+ * classical CGS2 with every dot product and update in FP64 (four passes per
+ * step), as HZS_FP64 uses.  HZS_SOLVE_BASIS_DF: the delayed CGS2 on a narrower
+ * double-float basis (complex64 rounding + remainder, see HZS_SOLVE_BASIS_WIDE)
+ * with complex64 dot products and double-float updates: fewer bytes and no FP64
+ * arithmetic, but neither the basis nor its arithmetic is FP64.  No effect with
+ * HZS_FP64. */
 #define HZS_SOLVE_ORTH_FP64 2
 #define HZS_SOLVE_BASIS_DF 16
+#define HZS_SOLVE_ORTH_DFMA 32
 /* With HZS_SOLVE_BASIS_DF: the basis stores its remainders as complex64 (about
  * 48 significant bits, 16 bytes an entry in all) when tol < 1e-7, else as bf16
  * pairs (about 32 significant bits, 12 bytes an entry: a quarter less basis
@@ -186,8 +204,9 @@ typedef struct {
     double t_orth_update_ms; /*   basis dot pass and of the basis update pass (parts of t_orth_ms); else 0 */
     long long launches;    /* kernel launches this solve issued */
     int basis_bits;        /* significant bits of the Krylov basis: 53 (complex128), 48 or 32 */
-    int orth_kind;         /* 0: CGS2 in FP64, 1: delayed CGS2 on the complex128 basis (FP64
-                              reorthogonalisation), 2: delayed CGS2 on the double-float basis */
+    int orth_kind;         /* 0: CGS2 in FP64; 1: delayed CGS2 on the FP64 basis, FP64 and FP32
+                              pipes (the HZS_MIXED default); 2: delayed CGS2 on the double-float
+                              basis; 3: delayed CGS2 on the FP64 basis, FP64 FMAs only */
     hzs_status status;
 } hzs_solve_info;
 
@@ -272,8 +291,8 @@ hzs_status hzs_precond_get_info(const hzs_precond* p, hzs_precond_info* out);
 /* Allocation-free variant of hzs_apply_precond for SAS2 preconditioners
  * (the paper has no counterpart: it concerns how memory is obtained, not the
  * method).  For callers that may not allocate device memory when they apply
- * the preconditioner - e.g. while a stream is being captured into a CUDA
- * graph, or on hosts that forbid allocation after start-up.  Computes the same
+ * the preconditioner - hosts that forbid allocation after start-up, or
+ * applications that hand all device memory to their own pool.  Computes the same
  * z = M^{-1} v as hzs_apply_precond (same kernels, same result) but takes its
  * work space (the partial restriction sums and the two coarse vectors) from a
  * fixed 1 MiB device array inside the library instead of the handle, and calls

@@ -14,6 +14,10 @@ the fine unknowns; in 2-D it is the tensor product phi_I(x) phi_J(y).
   the fine nodes: ``phi_I(x) = B2((x - X_I)/H + 3/2)`` with the cardinal
   quadratic B-spline B2 on [0, 3].  That function is used for every p (for
   p = 2 it reproduces Eq. (7) exactly; tests check this).
+* Alternative reading of B_2 for H = 2^m h (``b2_mode="composed"``): Eq. (7)'s
+  restriction from spacing s to 2s, weights (1, 4, 6, 4, 1)/8 around the fine
+  node under each coarse node, applied m times (coarse to fine: level by level),
+  each level on the full node set of its grid.  For m = 1 both readings coincide.
 * Fine nodes outside the unknowns are dropped (truncation at the boundary).
   MP-1 drops the coarse nodes on the boundary (their functions would carry the
   eliminated Dirichlet values); MP-2 keeps all (1/H + 1)^2 coarse nodes.
@@ -51,10 +55,37 @@ def hat(t):
     return np.maximum(0.0, 1.0 - np.abs(t))
 
 
-def basis_1d(kind: str, n: int, p: int, keep_ends: bool) -> np.ndarray:
+SPLINE, COMPOSED = "spline", "composed"
+
+
+def eq7_level(nf: int) -> np.ndarray:
+    """Eq. (7)'s restriction from nf nodes (spacing s) to (nf - 1)/2 + 1 nodes (spacing 2s),
+    all nodes of both grids: row I has (1, 4, 6, 4, 1)/8 on fine nodes 2I - 2 .. 2I + 2."""
+    nc = (nf - 1) // 2 + 1
+    R = np.zeros((nc, nf))
+    for I in range(nc):
+        for d, wgt in zip(range(-2, 3), (1.0, 4.0, 6.0, 4.0, 1.0)):
+            if 0 <= 2 * I + d < nf:
+                R[I, 2 * I + d] = wgt / 8.0
+    return R
+
+
+def basis_1d(kind: str, n: int, p: int, keep_ends: bool, b2_mode: str = SPLINE) -> np.ndarray:
     """(number of coarse nodes) x n matrix of phi_I(x_i) over all fine nodes i."""
     if p < 2 or (n - 1) % p != 0:
         raise ValueError("coarse ratio p = H/h must be >= 2 and divide n-1")
+    if kind == B2 and b2_mode == COMPOSED:
+        m = int(round(np.log2(p)))
+        if 2 ** m != p:
+            raise ValueError("the composed B2 needs H/h a power of two")
+        W = np.eye(n)
+        nf = n
+        for _ in range(m):
+            W = eq7_level(nf) @ W
+            nf = (nf - 1) // 2 + 1
+        return W if keep_ends else W[1:-1]
+    if b2_mode not in (SPLINE, COMPOSED):
+        raise ValueError(b2_mode)
     nc = (n - 1) // p + 1
     H = p / (n - 1)
     x = np.arange(n) / (n - 1)
@@ -72,10 +103,10 @@ def basis_1d(kind: str, n: int, p: int, keep_ends: bool) -> np.ndarray:
 
 
 class CoarseSpace:
-    def __init__(self, prob, kind: str, p: int):
+    def __init__(self, prob, kind: str, p: int, b2_mode: str = SPLINE):
         self.kind, self.p = kind, p
         keep = prob.bc != DIRICHLET
-        W = basis_1d(kind, prob.n, p, keep)[:, prob.lo:prob.hi + 1]   # truncate to unknowns
+        W = basis_1d(kind, prob.n, p, keep, b2_mode)[:, prob.lo:prob.hi + 1]   # truncate to unknowns
         self.W1 = W
         self.nc1 = W.shape[0]
         # coarse index J*nc1 + I  <->  phi_I(x) phi_J(y); fine index j*m + i

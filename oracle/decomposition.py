@@ -15,6 +15,11 @@ this oracle reads them as follows (the CUDA path takes the same readings):
   clipped to the unknowns, so neighbouring subdomains share 2*overlap layers;
 * D_i = 1 on the nodes subdomain i owns, 0 on its overlap (the restricted
   additive Schwarz choice); this satisfies sum_i R_i^T D_i R_i = I.
+  Alternative reading (``scaling="multiplicity"``): D_i = 1/m(x) on every node x
+  of subdomain i, m(x) the number of subdomains that contain x; it satisfies the
+  same identity.
+* the subdomain grid may be rectangular: ``ns`` is the count per axis or a pair
+  (ns_x, ns_y).
 """
 from __future__ import annotations
 
@@ -53,12 +58,25 @@ class Subdomain:
         self.d = owned.astype(np.float64)                   # diagonal of D_i
 
 
+OWNER, MULTIPLICITY = "owner", "multiplicity"
+
+
 class Decomposition:
-    def __init__(self, prob, ns: int, overlap: int):
-        self.ns, self.overlap = ns, overlap
-        bx = axis_blocks(prob.n, ns, prob.lo, prob.hi, overlap)
-        self.subs = [Subdomain(prob, bx[a], bx[b]) for b in range(ns) for a in range(ns)]
+    def __init__(self, prob, ns, overlap: int, scaling: str = OWNER):
+        nsx, nsy = (ns, ns) if np.isscalar(ns) else ns
+        if scaling not in (OWNER, MULTIPLICITY):
+            raise ValueError(scaling)
+        self.ns, self.overlap, self.scaling = (nsx, nsy), overlap, scaling
+        bx = axis_blocks(prob.n, nsx, prob.lo, prob.hi, overlap)
+        by = axis_blocks(prob.n, nsy, prob.lo, prob.hi, overlap)
+        self.subs = [Subdomain(prob, bx[a], by[b]) for b in range(nsy) for a in range(nsx)]
         self.N = prob.N
+        if scaling == MULTIPLICITY:
+            mult = np.zeros(prob.N)
+            for s in self.subs:
+                mult[s.idx] += 1.0
+            for s in self.subs:
+                s.d = 1.0 / mult[s.idx]
 
     def restrict(self, s: Subdomain, v: np.ndarray) -> np.ndarray:
         return v[s.idx]

@@ -19,6 +19,11 @@ true residual of the original system:
   y = argmin ||beta e_1 - H y||,  x = M^{-1}(V y)  (or x = Z y, flexible).
 
 The iteration count is the number of Arnoldi steps taken.
+
+Alternative reading (``side="left"``, as MATLAB's gmres applies a preconditioner
+given to it): GMRES on M^{-1} A x = M^{-1} f, i.e. v_0 = M^{-1} f / ||M^{-1} f||,
+w = M^{-1} A v_j, stop when the preconditioned residual estimate
+|g_{j+1}| <= tol ||M^{-1} f||, and x = V y.
 """
 from __future__ import annotations
 
@@ -46,10 +51,16 @@ def givens(a: complex, b: complex):
 
 
 def gmres(A_apply, M_apply, f: np.ndarray, tol: float, maxit: int,
-          flexible: bool = False, A_true=None) -> GmresResult:
+          flexible: bool = False, A_true=None, side: str = "right") -> GmresResult:
+    if side not in ("right", "left"):
+        raise ValueError(side)
+    left = side == "left"
     f = np.asarray(f, dtype=np.complex128)
-    beta = np.linalg.norm(f)
     N = f.shape[0]
+    f_true = f
+    if left:
+        f = M_apply(f)
+    beta = np.linalg.norm(f)
     if beta == 0.0:
         return GmresResult(np.zeros(N, np.complex128), 0, True, [], 0.0)
     V = [f / beta]
@@ -63,10 +74,13 @@ def gmres(A_apply, M_apply, f: np.ndarray, tol: float, maxit: int,
     converged = False
     m = 0
     for j in range(maxit):
-        z = M_apply(V[j])
-        if flexible:
-            Z.append(z)
-        w = A_apply(z)
+        if left:
+            w = M_apply(A_apply(V[j]))
+        else:
+            z = M_apply(V[j])
+            if flexible:
+                Z.append(z)
+            w = A_apply(z)
         for i in range(j + 1):                       # modified Gram-Schmidt
             H[i, j] = np.vdot(V[i], w)
             w = w - H[i, j] * V[i]
@@ -95,10 +109,12 @@ def gmres(A_apply, M_apply, f: np.ndarray, tol: float, maxit: int,
     y = np.zeros(m, dtype=np.complex128)
     for i in range(m - 1, -1, -1):
         y[i] = (g[i] - H[i, i + 1:m] @ y[i + 1:m]) / H[i, i]
-    if flexible:
+    if left:
+        x = sum(y[i] * V[i] for i in range(m))
+    elif flexible:
         x = sum(y[i] * Z[i] for i in range(m))
     else:
         x = M_apply(sum(y[i] * V[i] for i in range(m)))
     Atr = A_true if A_true is not None else A_apply
-    relres = np.linalg.norm(f - Atr(x)) / beta
+    relres = np.linalg.norm(f_true - Atr(x)) / np.linalg.norm(f_true)
     return GmresResult(x, m, converged, hist, relres)

@@ -16,12 +16,13 @@ minimum-degree ordering on A_i^T + A_i, partial pivoting).
 Mixed precision (``precision="c64"``): the paper computes in one precision; the
 reduced-precision preconditioner of the mixed solver is read as the same
 operator with its transfers (R_0, R_0^T, R_i, R_i^T D_i), its deflation
-v - A q and its exact local solves carried out in complex64 - the input is
-rounded to complex64, the local matrices are factorised by SuperLU in complex64,
-every product and sum is a complex64 operation - while the coarse solve
-A_0^{-1} stays in FP64 (its input widened from, its output rounded to,
-complex64).  The result is returned widened to complex128 for the FP64
-flexible GMRES around it.
+v - A q and its exact local solves applied in complex64 - the input is rounded
+to complex64, every product and sum is a complex64 operation - while the
+set-up and the coarse solve stay in FP64: each local matrix is factorised by
+SuperLU in FP64 once, its factors L and U are rounded to complex64 and the two
+triangular solves run in complex64; A_0^{-1} is applied in FP64 (its input
+widened from, its output rounded to, complex64).  The result is returned
+widened to complex128 for the FP64 flexible GMRES around it.
 """
 from __future__ import annotations
 
@@ -38,8 +39,9 @@ FP64, C64 = "fp64", "c64"
 
 
 class Schwarz:
-    def __init__(self, prob, A, ns: int, overlap: int, kind: str = SHS2,
-                 coarse: str | None = "b2", p: int | None = None, precision: str = FP64):
+    def __init__(self, prob, A, ns, overlap: int, kind: str = SHS2,
+                 coarse: str | None = "b2", p: int | None = None, precision: str = FP64,
+                 scaling: str = "owner", b2_mode: str = "spline"):
         if kind not in (AS1, AS2, SAS2, SHS2):
             raise ValueError(kind)
         if kind != AS1 and coarse is None:
@@ -48,32 +50,50 @@ class Schwarz:
             raise ValueError(precision)
         self.kind, self.A, self.precision = kind, A, precision
         self.ct = np.complex128 if precision == FP64 else np.complex64
-        self.dec = Decomposition(prob, ns, overlap)
+        self.dec = Decomposition(prob, ns, overlap, scaling)
         Ar = A.tocsr()
         # the operator in the preconditioner's precision (the deflation of SHS2)
         self.Ap = A if precision == FP64 else Ar.astype(self.ct)
         self.lu = []
+        self.lu32 = []
         for s in self.dec.subs:
-            Ai = Ar[s.idx][:, s.idx].tocsc().astype(self.ct)
+            Ai = Ar[s.idx][:, s.idx].tocsc()
             # A_i has a symmetric nonzero pattern (Section 2), so the fill-reducing
             # ordering is minimum degree on A^T + A
-            self.lu.append(spla.splu(Ai, permc_spec="MMD_AT_PLUS_A"))
+            lu = spla.splu(Ai, permc_spec="MMD_AT_PLUS_A")
+            self.lu.append(lu)
+            if precision == C64:
+                # Pr A_i Pc = L U: the FP64 factors rounded to complex64
+                self.lu32.append((lu.L.astype(np.complex64).tocsr(), lu.U.astype(np.complex64).tocsr(),
+                                  lu.perm_r, lu.perm_c))
         self.coarse = None
         if kind != AS1:
-            self.coarse = CoarseSolver(CoarseSpace(prob, coarse, p), Ar)
+            self.coarse = CoarseSolver(CoarseSpace(prob, coarse, p, b2_mode), Ar)
             if precision == C64:
                 self.R0p = self.coarse.cs.R0.astype(np.float32)
 
     def local_sum(self, r: np.ndarray, weighted: bool) -> np.ndarray:
         """sum_i R_i^T (D_i) A_i^{-1} R_i r, in the preconditioner's precision."""
         out = np.zeros_like(r, dtype=self.ct)
-        for s, lu in zip(self.dec.subs, self.lu):
-            y = lu.solve(np.ascontiguousarray(r[s.idx], dtype=self.ct))
+        for k, (s, lu) in enumerate(zip(self.dec.subs, self.lu)):
+            if self.precision == C64:
+                y = self._solve32(k, np.ascontiguousarray(r[s.idx], dtype=np.complex64))
+            else:
+                y = lu.solve(np.ascontiguousarray(r[s.idx], dtype=np.complex128))
             if weighted:
                 out[s.idx] += s.d.astype(y.real.dtype) * y
             else:
                 out[s.idx] += y
         return out
+
+    def _solve32(self, k: int, b: np.ndarray) -> np.ndarray:
+        """A_k^{-1} b with the complex64 factors: z = U^{-1} L^{-1} (Pr b), x = Pc z."""
+        L, U, perm_r, perm_c = self.lu32[k]
+        pb = np.empty_like(b)
+        pb[perm_r] = b
+        y = spla.spsolve_triangular(L, pb, lower=True, unit_diagonal=True)
+        z = spla.spsolve_triangular(U, y, lower=False)
+        return z[perm_c]
 
     def apply_Q(self, v: np.ndarray) -> np.ndarray:
         """Q v = R_0^T A_0^{-1} R_0 v: the transfers in the preconditioner's precision,

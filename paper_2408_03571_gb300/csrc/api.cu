@@ -11,6 +11,7 @@
 // (the autotuner below).
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -41,9 +42,10 @@ struct hzs_grid {
     OpDesc op{};
     int num_sms = 0;
     int lo = 0, hi = 0;               // unknown index range per axis
-    std::vector<AxisBlock> blocks;    // per axis (both axes identical)
-    std::vector<Tile> tiles;          // nsub * nsub, tile = by * nsub + bx
-    std::vector<int4> cover;          // per grid index: (block, offset, block, offset)
+    int nsx = 0, nsy = 0;             // subdomains along x and y
+    std::vector<AxisBlock> xblocks, yblocks;
+    std::vector<Tile> tiles;          // nsx * nsy, tile = by * nsx + bx
+    std::vector<int4> cover_x, cover_y;   // per grid index: (block, offset, block, offset) along x, y
     int max_mx = 0, max_my = 0;
     std::string err;
 };
@@ -80,7 +82,8 @@ struct hzs_precond {
     float2* W32 = nullptr;
     std::vector<FactorStat> fstats;
     Tile* tiles_d = nullptr;
-    int4* cover_d = nullptr;
+    int4* cover_d = nullptr;          // per grid index along x (cover_yd: along y), see hzs_grid::cover_x
+    int4* cover_yd = nullptr;
     long long ytiles_elems = 0;
     // apply work space
     void* t_buf = nullptr;            // n * nc1 working complex
@@ -156,12 +159,15 @@ extern "C" hzs_status hzs_grid_create(const hzs_grid_desc* d, void* cuda_stream,
     if (!d) return fail(nullptr, HZS_ERR_INVALID_ARG, "desc is NULL");
     if (d->n < 5 || d->n % 2 != 1) return fail(nullptr, HZS_ERR_INVALID_ARG, "n must be odd and >= 5");
     if (d->bc != HZS_DIRICHLET && d->bc != HZS_SOMMERFELD) return fail(nullptr, HZS_ERR_INVALID_ARG, "bad bc");
-    if (d->nsub < 1 || (d->n - 1) % d->nsub != 0) return fail(nullptr, HZS_ERR_INVALID_ARG, "nsub must divide n-1");
-    const int w = (d->n - 1) / d->nsub;
+    const int nsx = d->nsub, nsy = d->nsub_y > 0 ? d->nsub_y : d->nsub;
+    if (nsx < 1 || (d->n - 1) % nsx != 0) return fail(nullptr, HZS_ERR_INVALID_ARG, "nsub must divide n-1");
+    if (d->nsub_y < 0 || (d->n - 1) % nsy != 0) return fail(nullptr, HZS_ERR_INVALID_ARG, "nsub_y must divide n-1");
+    const int wx = (d->n - 1) / nsx, wy = (d->n - 1) / nsy;
     if (d->overlap < 0) return fail(nullptr, HZS_ERR_INVALID_ARG, "overlap must be >= 0");
-    if (2 * d->overlap > w)
+    if (2 * d->overlap > std::min(wx, wy))
         return fail(nullptr, HZS_ERR_INVALID_ARG, "overlap must be at most half the subdomain width");
-    if (d->bc == HZS_DIRICHLET && w < 2) return fail(nullptr, HZS_ERR_INVALID_ARG, "subdomain width must be >= 2");
+    if (d->bc == HZS_DIRICHLET && std::min(wx, wy) < 2)
+        return fail(nullptr, HZS_ERR_INVALID_ARG, "subdomain width must be >= 2");
     if (!d->kappa_dev && !(d->k > 0.0 && std::isfinite(d->k)))
         return fail(nullptr, HZS_ERR_INVALID_ARG, "k must be positive and finite");
 
@@ -197,38 +203,45 @@ extern "C" hzs_status hzs_grid_create(const hzs_grid_desc* d, void* cuda_stream,
     g->op.kappa = g->kappa;
     g->lo = d->bc == HZS_DIRICHLET ? 1 : 0;
     g->hi = d->bc == HZS_DIRICHLET ? n - 2 : n - 1;
-    // owned blocks [a w, (a+1) w) (last one closed at n-1) within the unknowns, extended by overlap
-    for (int a = 0; a < d->nsub; ++a) {
-        AxisBlock b;
-        b.own_lo = std::max(a * w, g->lo);
-        b.own_hi = std::min(a < d->nsub - 1 ? (a + 1) * w - 1 : n - 1, g->hi);
-        b.ext_lo = std::max(b.own_lo - d->overlap, g->lo);
-        b.ext_hi = std::min(b.own_hi + d->overlap, g->hi);
-        g->blocks.push_back(b);
-    }
-    g->cover.assign(n, make_int4(-1, 0, -1, 0));
-    for (int i = 0; i < n; ++i) {
-        int cnt = 0;
-        int4 c = make_int4(-1, 0, -1, 0);
-        for (int a = 0; a < d->nsub; ++a) {
-            const AxisBlock& b = g->blocks[a];
-            if (i >= b.ext_lo && i <= b.ext_hi) {
-                if (cnt == 0) { c.x = a; c.y = i - b.ext_lo; }
-                else if (cnt == 1) { c.z = a; c.w = i - b.ext_lo; }
-                ++cnt;
+    g->nsx = nsx;
+    g->nsy = nsy;
+    // per axis: owned blocks [a w, (a+1) w) (last one closed at n-1) within the unknowns,
+    // extended by overlap, and for every grid index the (at most two) blocks containing it
+    auto axis = [&](int ns, int w, std::vector<AxisBlock>& blocks, std::vector<int4>& cover) {
+        for (int a = 0; a < ns; ++a) {
+            AxisBlock b;
+            b.own_lo = std::max(a * w, g->lo);
+            b.own_hi = std::min(a < ns - 1 ? (a + 1) * w - 1 : n - 1, g->hi);
+            b.ext_lo = std::max(b.own_lo - d->overlap, g->lo);
+            b.ext_hi = std::min(b.own_hi + d->overlap, g->hi);
+            blocks.push_back(b);
+        }
+        cover.assign(n, make_int4(-1, 0, -1, 0));
+        for (int i = 0; i < n; ++i) {
+            int cnt = 0;
+            int4 c = make_int4(-1, 0, -1, 0);
+            for (int a = 0; a < ns; ++a) {
+                const AxisBlock& b = blocks[a];
+                if (i >= b.ext_lo && i <= b.ext_hi) {
+                    if (cnt == 0) { c.x = a; c.y = i - b.ext_lo; }
+                    else if (cnt == 1) { c.z = a; c.w = i - b.ext_lo; }
+                    ++cnt;
+                }
             }
+            if (cnt > 2) return false;
+            cover[i] = c;
         }
-        if (cnt > 2) {
-            cudaFree(g->kappa);
-            delete g;
-            return fail(nullptr, HZS_ERR_INVALID_ARG, "a node lies in more than two subdomains per axis");
-        }
-        g->cover[i] = c;
+        return true;
+    };
+    if (!axis(nsx, wx, g->xblocks, g->cover_x) || !axis(nsy, wy, g->yblocks, g->cover_y)) {
+        cudaFree(g->kappa);
+        delete g;
+        return fail(nullptr, HZS_ERR_INVALID_ARG, "a node lies in more than two subdomains per axis");
     }
     long long yoff = 0;
-    for (int by = 0; by < d->nsub; ++by)
-        for (int bx = 0; bx < d->nsub; ++bx) {
-            const AxisBlock &X = g->blocks[bx], &Y = g->blocks[by];
+    for (int by = 0; by < nsy; ++by)
+        for (int bx = 0; bx < nsx; ++bx) {
+            const AxisBlock &X = g->xblocks[bx], &Y = g->yblocks[by];
             Tile t{};
             t.x0 = X.ext_lo; t.y0 = Y.ext_lo;
             t.mx = X.ext_hi - X.ext_lo + 1; t.my = Y.ext_hi - Y.ext_lo + 1;
@@ -272,7 +285,8 @@ extern "C" void hzs_precond_destroy(hzs_precond* p) {
     cudaFree(p->c0); cudaFree(p->lo); cudaFree(p->hi); cudaFree(p->off); cudaFree(p->w); cudaFree(p->wt);
     cudaFree(p->wf); cudaFree(p->wtf); cudaFree(p->c2f); cudaFree(p->err); cudaFree(p->groups_d);
     coarse_block_free(p->cblk);
-    cudaFree(p->Ainv); cudaFree(p->W64); cudaFree(p->W32); cudaFree(p->tiles_d); cudaFree(p->cover_d);
+    cudaFree(p->Ainv); cudaFree(p->W64); cudaFree(p->W32); cudaFree(p->tiles_d);
+    cudaFree(p->cover_d); cudaFree(p->cover_yd);
     cudaFree(p->t_buf); cudaFree(p->c_buf); cudaFree(p->c2_buf); cudaFree(p->w_buf); cudaFree(p->ytiles);
     cudaFree(p->zc64);
     if (p->h_done) cudaFreeHost(p->h_done);
@@ -295,6 +309,8 @@ static cudaError_t upload(T** dst, const std::vector<T>& src, cudaStream_t s) {
 }
 
 static hzs_status setup_impl(hzs_grid* g, const hzs_precond_desc* d, hzs_precond* p) {
+    if (d->scaling_mode != HZS_SCALING_OWNER && d->scaling_mode != HZS_SCALING_MULTIPLICITY)
+        return fail(g, HZS_ERR_INVALID_ARG, "scaling_mode must be HZS_SCALING_OWNER or HZS_SCALING_MULTIPLICITY");
     const int n = g->desc.n;
     cudaStream_t s = g->stream;
     p->cx.op = g->op;
@@ -359,6 +375,14 @@ static hzs_status setup_impl(hzs_grid* g, const hzs_precond_desc* d, hzs_precond
     HZS_CUDA(g, dalloc(&p->err, 1));
     HZS_CUDA(g, cudaMemsetAsync(p->err, 0, sizeof(int), s));
     p->cx.err = p->err;
+    // diagnostic knob: HZS_STAGE_WAIT_POLLS bounds the polls of the subdomain solve's factor-copy
+    // waits (default 2^24); a block whose wait runs out records HZS_ERR_TIMEOUT, waits (with the
+    // full bound) for its copies still in flight and returns
+    if (const char* ev = std::getenv("HZS_STAGE_WAIT_POLLS")) {
+        char* end = nullptr;
+        const long long v = std::strtoll(ev, &end, 10);
+        if (end != ev && v >= 0) p->cx.spin_limit = v;
+    }
     if (g->max_mx > max_tile_extent() || g->max_my > max_tile_extent())
         return fail(g, HZS_ERR_INVALID_ARG,
                     "subdomain tile larger than " + std::to_string(max_tile_extent()) + " nodes per axis");
@@ -433,7 +457,8 @@ static hzs_status setup_impl(hzs_grid* g, const hzs_precond_desc* d, hzs_precond
     for (auto& fs : p->fstats)
         if (fs.singular) return fail(g, HZS_ERR_SINGULAR_LOCAL, "a subdomain matrix has a zero pivot");
     HZS_CUDA(g, upload(&p->tiles_d, tiles, s));
-    HZS_CUDA(g, upload(&p->cover_d, g->cover, s));
+    HZS_CUDA(g, upload(&p->cover_d, g->cover_x, s));
+    HZS_CUDA(g, upload(&p->cover_yd, g->cover_y, s));
     // ---- apply work space (one right-hand side; batched calls grow it)
     for (auto& T : tiles) p->ytiles_elems += (long long)T.mx * T.my;
     {
@@ -491,7 +516,7 @@ static hzs_status ensure_work(hzs_precond* p, int nb) {
         HZS_CUDA(g, dalloc(&p->c2f, (size_t)p->Nc * nb));
     }
     HZS_CUDA(g, cudaMalloc(&p->w_buf, n * n * cs * nb));
-    if (p->desc.kind == HZS_AS1 || p->desc.kind == HZS_AS2)
+    if (p->desc.kind == HZS_AS1 || p->desc.kind == HZS_AS2 || p->desc.scaling_mode == HZS_SCALING_MULTIPLICITY)
         HZS_CUDA(g, cudaMalloc(&p->ytiles, (size_t)p->ytiles_elems * cs * nb));
     if (p->desc.precision == HZS_MIXED) HZS_CUDA(g, dalloc(&p->zc64, n * n * nb));
     p->wcap = nb;
@@ -523,7 +548,22 @@ static hzs_status precond_apply(hzs_precond* p, int nb, const Cv* v, long long v
             launch_coarse_matvec(cx, nb, p->Ainv, p->Nc, p->c_buf, p->c2_buf, f32 ? p->c2f : nullptr, sk);
     }
     int rc = 0;
-    if (kind == HZS_SHS2) {
+    if (p->desc.scaling_mode == HZS_SCALING_MULTIPLICITY && (kind == HZS_SHS2 || kind == HZS_SAS2)) {
+        // D_i = 1/multiplicity: every tile's solution is kept and the combination weights each
+        // node's contributions by the number of subdomains that contain it
+        const C* src = nullptr;
+        if (kind == HZS_SHS2) {
+            launch_deflate<Cv, C, R>(cx, nb, cc, Nc, v, vs, vscale, vss, (C*)p->w_buf, nn, sk);
+            src = (const C*)p->w_buf;
+            rc = launch_tile_solve<C, C, R>(cx, nb, p->tiles_d, grp, g->max_mx, g->max_my, W, src, nn, nullptr, 0, 1,
+                                            cc, Nc, 0, (C*)nullptr, 0, (C*)p->ytiles, p->ytiles_elems, sk);
+        } else {
+            rc = launch_tile_solve<Cv, C, R>(cx, nb, p->tiles_d, grp, g->max_mx, g->max_my, W, v, vs, vscale, vss, 1,
+                                             cc, Nc, 0, (C*)nullptr, 0, (C*)p->ytiles, p->ytiles_elems, sk);
+        }
+        launch_combine_additive<C, C, R>(cx, nb, cc, Nc, p->use_coarse, p->cover_d, p->cover_yd, p->tiles_d, g->nsx,
+                                         (const C*)p->ytiles, p->ytiles_elems, z, zs, sk, 1);
+    } else if (kind == HZS_SHS2) {
         launch_deflate<Cv, C, R>(cx, nb, cc, Nc, v, vs, vscale, vss, (C*)p->w_buf, nn, sk);
         rc = launch_tile_solve<C, C, R>(cx, nb, p->tiles_d, grp, g->max_mx, g->max_my, W, (const C*)p->w_buf, nn,
                                         nullptr, 0, 0, cc, Nc, 1, z, zs, nullptr, 0, sk);
@@ -533,8 +573,8 @@ static hzs_status precond_apply(hzs_precond* p, int nb, const Cv* v, long long v
     } else {
         rc = launch_tile_solve<Cv, C, R>(cx, nb, p->tiles_d, grp, g->max_mx, g->max_my, W, v, vs, vscale, vss, 1, cc,
                                          Nc, 0, (C*)nullptr, 0, (C*)p->ytiles, p->ytiles_elems, sk);
-        launch_combine_additive<C, C, R>(cx, nb, cc, Nc, p->use_coarse, p->cover_d, p->tiles_d, g->desc.nsub,
-                                         (const C*)p->ytiles, p->ytiles_elems, z, zs, sk);
+        launch_combine_additive<C, C, R>(cx, nb, cc, Nc, p->use_coarse, p->cover_d, p->cover_yd, p->tiles_d, g->nsx,
+                                         (const C*)p->ytiles, p->ytiles_elems, z, zs, sk, 0);
     }
     if (rc != 0) return fail(g, HZS_ERR_CUDA, "subdomain solve launch failed");
     cudaError_t e = cudaGetLastError();
@@ -612,9 +652,9 @@ static hzs_status autotune_tile_shape(hzs_precond* p) {
     int dev = 0;
     HZS_CUDA(g, cudaGetDevice(&dev));
     char kb[256];
-    snprintf(kb, sizeof kb, "%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d", dev, gd.n, (int)gd.bc, gd.nsub, gd.overlap,
-             (int)d.kind, (int)d.coarse, d.coarse_ratio, (int)d.precision, p->coarse_block, p->nfactors, p->group_T,
-             g->max_mx, g->max_my);
+    snprintf(kb, sizeof kb, "%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d", dev, gd.n, (int)gd.bc, g->nsx, g->nsy,
+             gd.overlap, (int)d.kind, (int)d.coarse, d.coarse_ratio, (int)d.precision, p->coarse_block, p->nfactors,
+             p->group_T, g->max_mx, g->max_my, d.scaling_mode);
     const std::string key(kb);
     if (d.autotune == 1) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -760,6 +800,15 @@ static hzs_status ensure_krylov(hzs_precond* p, int maxit, int nb, bool full_v) 
     // delayed-CGS2 dot pass, 64 registers a thread, runs 4 per SM
     kb.nblk = 3 * g->num_sms;
     kb.nblk_dot = 4 * g->num_sms;
+    // tuning knob for the f53 passes: HZS_F53_MASK="dot,update", two 8-bit masks of the vectors
+    // (index mod 8) summed with FP64 FMAs; the others take the FP32 path
+    if (const char* ev = std::getenv("HZS_F53_MASK")) {
+        unsigned a = 0, b = 0;
+        if (std::sscanf(ev, "%i,%i", (int*)&a, (int*)&b) == 2 && a <= 255u && b <= 255u) {
+            kb.dmask_dot = a;
+            kb.dmask_upd = b;
+        }
+    }
     const size_t S = (size_t)(maxit + 1);
     kb.vfull = full_v ? 1 : 0;
     HZS_CUDA(g, dalloc(&kb.V, (size_t)nb * kb.sVd()));
@@ -830,10 +879,14 @@ static hzs_status set_basis_width(hzs_precond* p, int lo16) {
 // HZS_SOLVE_ORTH_FP64; for HZS_MIXED by default the delayed CGS2 on the complex128
 // basis (two passes per step, FP64 reorthogonalisation); with HZS_SOLVE_BASIS_DF the
 // delayed CGS2 on the narrower double-float basis.
-constexpr int kOrthCGS2 = 0, kOrthD64 = 1, kOrthDF = 2;
+constexpr int kOrthCGS2 = 0, kOrthS53 = 1, kOrthDF = 2, kOrthD64 = 3;   // values of hzs_solve_info.orth_kind
 static int orth_mode(const hzs_precond* p, const hzs_solve_desc* sd) {
     if (p->desc.precision != HZS_MIXED || (sd->flags & HZS_SOLVE_ORTH_FP64)) return kOrthCGS2;
-    return (sd->flags & HZS_SOLVE_BASIS_DF) ? kOrthDF : kOrthD64;
+    if (sd->flags & HZS_SOLVE_BASIS_DF) return kOrthDF;
+    if (sd->flags & HZS_SOLVE_ORTH_DFMA) return kOrthD64;
+    // the f53 update pass keeps 96 bytes of coefficients per basis vector in shared
+    // memory; longer runs use the all-FMA variant (32 bytes per vector)
+    return s53_update_smem(sd->maxit) + 2048 <= (size_t)227 * 1024 ? kOrthS53 : kOrthD64;
 }
 
 // Kernel launches of one preconditioner apply.
@@ -894,6 +947,7 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
     // delayed CGS2 on the double-float basis, or on the FP64 basis
     const bool orth32 = orth == kOrthDF;
     const bool d64 = orth == kOrthD64;
+    const bool s53 = orth == kOrthS53;
     // bf16 remainders (a basis of about 32 significant bits) for loose tolerances
     const bool lo16 = orth32 && !(sd->flags & HZS_SOLVE_BASIS_WIDE) && sd->tol >= kNarrowBasisTol;
     const BatchSkip sk = kb.skip();
@@ -915,13 +969,34 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
                           orth32 ? kb.lo_at(0) : LoDst{nullptr, nullptr});
     launch_norm_init(cx, kb, nb, sd->tol);
     launches += 3;
+    uint2* Vt = static_cast<uint2*>(kb.V32lo);
+    if ((s53 || orth32) && (!kb.V32 || !kb.V32lo))
+        return fail(g, HZS_ERR_CUDA, "Krylov work space lacks the head/remainder arrays of this orthogonalisation");
+    if ((d64 || orth == kOrthCGS2) && !kb.vfull)
+        return fail(g, HZS_ERR_CUDA, "Krylov work space lacks the complex128 basis of this orthogonalisation");
+    if (s53) {
+        // the f53 copy of V_0, scaled by a power of two to unit size (sigma_0 takes the factor)
+        launch_f53_scale0(cx, nb, kb.sigma, kb.sigt, sS, p->dres);
+        launch_f53_encode(cx, nb, kb.N, kb.V, kb.sVd(), kb.V32, Vt, sV, p->dres, nullptr);
+        launches += 2;
+    }
     int steps = 0;
     // enqueues Arnoldi step j of every entry on cx.stream
     auto issue_step = [&](int j) -> hzs_status {
         cudaEvent_t* pe = prof ? &p->prof_ev[(size_t)8 * j] : nullptr;
         if (prof) HZS_CUDA(g, cudaEventRecord(pe[0], cx.stream));
         hzs_status st;
-        if (d64) {
+        if (s53) {
+            // the complex64 preconditioner reads the heads of u~_j scaled by 1/|u~_j|; A z_j in
+            // FP64, stored as f53 in slot j+1
+            float2* Zj = p->Z + (size_t)j * ld;
+            st = precond_apply<float, float2>(p, nb, kb.V32 + (size_t)j * ld, sV, kb.sigt + j, sS, Zj, sZ, sk);
+            if (prof) HZS_CUDA(g, cudaEventRecord(pe[1], cx.stream));
+            launch_apply_A<float2, double2, double>(cx, nb, Zj, sZ, p->ztmp, ld, nullptr, 0, sk);
+            launch_f53_encode(cx, nb, kb.N, p->ztmp, ld, kb.V32 + (size_t)(j + 1) * ld, Vt + (size_t)(j + 1) * ld, sV,
+                              nullptr, kb.st);
+            launches += 1;
+        } else if (d64) {
             // the complex64 preconditioner reads u~_j (the once-projected vector of the previous
             // step, see launch_dcgs2_step64) scaled by 1/|u~_j|; A z_j in FP64 into slot j+1
             float2* Zj = p->Z + (size_t)j * ld;
@@ -951,11 +1026,18 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
         }
         if (st != HZS_OK) return st;
         if (prof) HZS_CUDA(g, cudaEventRecord(pe[2], cx.stream));
-        if (d64) launch_dcgs2_step64(cx, kb, nb, j, 0, prof ? pe + 4 : nullptr);
-        else if (orth32) launch_dcgs2_step(cx, kb, nb, j, 0, prof ? pe + 4 : nullptr);
-        else launch_arnoldi_step(cx, kb, nb, j);
+        if (s53) {
+            if (!launch_dcgs2_step53(cx, kb, nb, j, 0, prof ? pe + 4 : nullptr))
+                return fail(g, HZS_ERR_CUDA, "Arnoldi update pass: coefficients exceed shared memory");
+        } else if (d64) {
+            launch_dcgs2_step64(cx, kb, nb, j, 0, prof ? pe + 4 : nullptr);
+        } else if (orth32) {
+            launch_dcgs2_step(cx, kb, nb, j, 0, prof ? pe + 4 : nullptr);
+        } else {
+            launch_arnoldi_step(cx, kb, nb, j);
+        }
         if (prof) HZS_CUDA(g, cudaEventRecord(pe[3], cx.stream));
-        launches += pl + 1 + (orth32 || d64 ? (j > 0 ? 6 : 5) : 7);
+        launches += pl + 1 + (orth32 || d64 || s53 ? (j > 0 ? 6 : 5) : 7);
         steps = j + 1;
         // a launch that could not start (e.g. its resources) must not pass silently
         HZS_CUDA(g, cudaGetLastError());
@@ -1006,8 +1088,9 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
         }
     }
     // delayed CGS2: the last column is completed by one more dot pass over the basis
-    if ((orth32 || d64) && steps == sd->maxit) {
-        if (d64) launch_dcgs2_step64(cx, kb, nb, sd->maxit, 1);
+    if ((orth32 || d64 || s53) && steps == sd->maxit) {
+        if (s53) launch_dcgs2_step53(cx, kb, nb, sd->maxit, 1);
+        else if (d64) launch_dcgs2_step64(cx, kb, nb, sd->maxit, 1);
         else launch_dcgs2_step(cx, kb, nb, sd->maxit, 1);
         launches += 4;
     }
@@ -1051,7 +1134,7 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
             cudaEventElapsedTime(&b, pe[1], pe[2]);
             cudaEventElapsedTime(&c, pe[2], pe[3]);
             tp += a; tm += b; to += c;
-            if (orth32 || d64) {
+            if (orth32 || d64 || s53) {
                 float d = 0, u = 0;
                 cudaEventElapsedTime(&d, pe[4], pe[5]);
                 cudaEventElapsedTime(&u, pe[6], pe[7]);
@@ -1093,8 +1176,10 @@ static hzs_status solve_many(hzs_precond* p, const hzs_solve_desc* sd, const voi
     if (!(sd->tol > 0.0) || sd->maxit < 1) return fail(g, HZS_ERR_INVALID_ARG, "tol must be > 0 and maxit >= 1");
     if (nrhs == 0) return HZS_OK;
     int nb = nrhs;
-    // only the double-float path (MIXED with HZS_SOLVE_BASIS_DF) keeps no complex128 basis
-    const bool full_v = orth_mode(p, sd) != kOrthDF;
+    // the complex128 basis for the FP64 CGS2 and the all-FMA delayed CGS2; the double-float
+    // and f53 paths keep only its slot 0 (the right-hand side) and the head/remainder arrays
+    const int om = orth_mode(p, sd);
+    const bool full_v = om == kOrthCGS2 || om == kOrthD64;
     if (!(p->kb.V && p->kb.maxit >= sd->maxit && p->kb.nb >= nrhs && p->kb.vfull == (full_v ? 1 : 0))) {
         free_krylov(p);
         size_t fr = 0, tot = 0;

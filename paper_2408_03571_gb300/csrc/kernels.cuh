@@ -53,6 +53,7 @@ struct Ctx {
     cudaStream_t stream;
     int num_sms;
     int* err;          // device error word: kernels that time out set it (HZS_ERR_TIMEOUT); may be null
+    long long spin_limit = 1LL << 24;   // polls of a subdomain-solve stage wait before it is declared timed out
 };
 
 // Per-batch-entry skip flag: entry r is skipped when flag[r * stride] != 0 (flag may be null).
@@ -100,8 +101,8 @@ void launch_deflate(const Ctx& cx, int nb, const cplx_t<R>* c, long long cs, con
                     const double* vscale, long long vss, Cw* w, long long ws, BatchSkip sk);
 template <typename Cz, typename Cy, typename R>
 void launch_combine_additive(const Ctx& cx, int nb, const cplx_t<R>* c, long long cs, int use_coarse,
-                             const int4* cover, const Tile* tiles, int nsub, const Cy* ytiles, long long yts, Cz* z,
-                             long long zs, BatchSkip sk);
+                             const int4* cover_x, const int4* cover_y, const Tile* tiles, int nsx, const Cy* ytiles,
+                             long long yts, Cz* z, long long zs, BatchSkip sk, int weighted);
 void launch_mask_copy_c128(const Ctx& cx, int nb, const double2* src, long long ss, double2* dst, long long ds,
                            int conj, float2* dst32, long long d32s, LoDst dst32lo = LoDst{nullptr, nullptr});
 void launch_kappa_gradient(const Ctx& cx, const double2* u, const double2* lam, double* grad);
@@ -183,6 +184,11 @@ struct KrylovBufs {
     void* V32lo;       // (maxit+1) x ld remainders: V32 + V32lo is the basis as double-float pairs,
                        // complex64 words or, with lo16, bf16 pairs (LoDst); sized for complex64
     int lo16;          // remainders stored as bf16 pairs (set per solve)
+    // f53 basis: vectors i with bit i % 8 set are summed with FP64 FMAs in the dot pass / the
+    // update pass, the others in FP32 error-free arithmetic (5 of 8 on FP64: the fastest split
+    // measured at the headline size)
+    unsigned dmask_dot = 0x6Du;
+    unsigned dmask_upd = 0x6Du;
     double* sigma;     // (maxit+1): basis vector i = sigma[i] * V_i
     double2* H;        // (maxit+1) x maxit, column j at H[j*(maxit+1)]
     double* cs;        // maxit+1
@@ -227,6 +233,18 @@ void launch_dcgs2_step(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int l
 // dots and first-projection update, complex64 first-projection dots; same arguments).
 void launch_dcgs2_step64(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int last_only,
                          cudaEvent_t* ev = nullptr);
+// Step j of the delayed CGS2 on the f53 basis (heads V32, 29-bit tails V32lo), the
+// FP64-accurate work split between the FP64 and the FP32 pipes; false if the update
+// pass could not be launched (its coefficients exceed shared memory).
+bool launch_dcgs2_step53(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int last_only,
+                         cudaEvent_t* ev = nullptr);
+// ---- orth53.cu
+void launch_f53_encode(const Ctx& cx, int nb, long long N, const double2* src, long long ss, float2* dh, uint2* dt,
+                       long long ds, const double* scale, const KState* st);
+void launch_f53_scale0(const Ctx& cx, int nb, double* sigma, double* sigt, long long sS, double* scale);
+size_t s53_update_smem(int j);
+void launch_s53_dot(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int has_w, unsigned dmask);
+int launch_s53_update(const Ctx& cx, const KrylovBufs& kb, int nb, int j, unsigned dmask);
 void launch_lsq_solve(const Ctx& cx, const KrylovBufs& kb, int nb);
 void launch_combine_basis(const Ctx& cx, const KrylovBufs& kb, int nb, double2* x, long long xs);
 void launch_combine_Z(const Ctx& cx, const KrylovBufs& kb, int nb, const float2* Z, long long ldz, long long zs,

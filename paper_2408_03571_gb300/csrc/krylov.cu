@@ -16,6 +16,7 @@
 //
 // Reductions are deterministic: fixed chunks per block, fixed lane order in
 // the warp trees, and the cross-block sums in a fixed order.
+#include "f32x2.cuh"
 #include "kernels.cuh"
 
 namespace hzs {
@@ -529,59 +530,6 @@ __global__ void __launch_bounds__(kFinThreads) k_dcgs_givens(int j, int maxit, i
     for (int i = tid; i <= j; i += kFinThreads) out[i] = col[i];
 }
 
-// ---- packed FP32 pairs (two lanes in one 64-bit register: add/sub/mul/fma .f32x2,
-// one issue slot for two FP32 operations).  The low half is the first lane: a
-// complex64 entry loaded as 8 bytes is the pair (re, im).
-typedef unsigned long long f2x;
-__device__ __forceinline__ f2x f2_pack(float a, float b) {
-    f2x r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ float2 f2_unpack(f2x r) {
-    float2 v;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
-    return v;
-}
-__device__ __forceinline__ f2x add2(f2x a, f2x b) {
-    f2x d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2x sub2(f2x a, f2x b) {
-    f2x d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2x mul2(f2x a, f2x b) {
-    f2x d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c) {
-    f2x d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-// Lane-wise double-float multiply-add (sh, sl) += c * (vh + vl) for an FP32 c given
-// as the broadcast pairs P = (c, c), N = (-c, -c) (no negation modifier exists for the
-// packed forms): the product c vh is split exactly by an FMA, c vl is added to its
-// error, and the accumulation is a TwoSum.
-__device__ __forceinline__ void df_fma2(f2x& sh, f2x& sl, f2x P, f2x N, f2x vh, f2x vl) {
-    const f2x p = mul2(P, vh);
-    f2x en = fma2(N, vh, p);            // -(c vh - p), exact
-    en = fma2(N, vl, en);               // en = -(error + c vl)
-    const f2x s = add2(sh, p);          // TwoSum(sh, p)
-    const f2x bb = sub2(s, sh);
-    const f2x t = add2(sub2(sh, sub2(s, bb)), sub2(p, bb));
-    sh = s;
-    sl = add2(sl, sub2(t, en));
-}
-__device__ __forceinline__ void df_norm2(f2x& sh, f2x& sl) {
-    const f2x s = add2(sh, sl);
-    sl = sub2(sl, sub2(s, sh));
-    sh = s;
-}
 // Remainder pairs of one entry pair as two packed (re, im) lanes.
 __device__ __forceinline__ void lo_pairs(float4 v, f2x& l0, f2x& l1) {
     const ulonglong2 u = *reinterpret_cast<const ulonglong2*>(&v);
@@ -1340,6 +1288,45 @@ void launch_dcgs2_step64(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int
         k_dcgs_scale<<<nb, 32, 0, cx.stream>>>(j, kb.nblk, kb.nblk, kb.npart, kb.sigt, kb.sS(), kb.st);
     }
     if (side) cudaStreamWaitEvent(cx.stream, kb.ev_g, 0);
+}
+
+// Delayed CGS2 on the f53 basis (heads kb.V32, tails kb.V32lo; see orth53.cu): the
+// step structure of launch_dcgs2_step64 with the passes split between the FP64 and
+// FP32 pipes (kb.dmask_dot, kb.dmask_upd: the vectors on the FP64 path).
+// False (nothing launched after the dot pass) when the update pass's coefficients do
+// not fit in shared memory.
+bool launch_dcgs2_step53(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int last_only, cudaEvent_t* ev) {
+    const int S = kb.maxit + 1, ps = kb.pstride();
+    if (ev) cudaEventRecord(ev[0], cx.stream);
+    launch_s53_dot(cx, kb, nb, j, !last_only, kb.dmask_dot);
+    if (ev) cudaEventRecord(ev[1], cx.stream);
+    const dim3 rg(((2 * j + 2) * 32 + 255) / 256, nb);
+    k_dcgs_reduce<true><<<rg, 256, 0, cx.stream>>>(j, kb.nblk_dot, ps, S, kb.part, kb.sP(), kb.sigma, kb.h2, kb.hn,
+                                                   kb.sS(), kb.sN(), kb.st);
+    k_dcgs_coef<<<nb, kFinThreads, 0, cx.stream>>>(j, kb.maxit, last_only, kb.hn, kb.sN(), kb.h1, kb.h2, kb.H,
+                                                   kb.sH(), kb.sigma, kb.sS(), kb.st, kb.active);
+    const bool side = j > 0 && kb.side && kb.ev_c && kb.ev_g;
+    if (j > 0) {
+        cudaStream_t gs = cx.stream;
+        if (side) {
+            cudaEventRecord(kb.ev_c, cx.stream);
+            cudaStreamWaitEvent(kb.side, kb.ev_c, 0);
+            gs = kb.side;
+        }
+        k_dcgs_givens<<<nb, kFinThreads, dcgs_givens_smem(j), gs>>>(j, kb.maxit, last_only, kb.H, kb.sH(), kb.cs,
+                                                                     kb.sn, kb.g, kb.sS(), kb.st, kb.active);
+        if (side) cudaEventRecord(kb.ev_g, kb.side);
+    }
+    bool ok = true;
+    if (!last_only) {
+        if (ev) cudaEventRecord(ev[2], cx.stream);
+        const int nupd = launch_s53_update(cx, kb, nb, j, kb.dmask_upd);
+        if (ev) cudaEventRecord(ev[3], cx.stream);
+        if (nupd > 0) k_dcgs_scale<<<nb, 32, 0, cx.stream>>>(j, nupd, kb.nblk, kb.npart, kb.sigt, kb.sS(), kb.st);
+        ok = nupd > 0;
+    }
+    if (side) cudaStreamWaitEvent(cx.stream, kb.ev_g, 0);
+    return ok;
 }
 
 void launch_lsq_solve(const Ctx& cx, const KrylovBufs& kb, int nb) {

@@ -193,8 +193,8 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
 }
 constexpr long long kSpinLimit = 1LL << 24;   // try_wait polls before a stage wait is declared timed out
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (long long it = 0; it < kSpinLimit; ++it)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit = kSpinLimit) {
+    for (long long it = 0; it < limit; ++it)
         if (mbar_try(bar, parity)) return true;
     return false;
 }
@@ -331,7 +331,8 @@ __global__ void __launch_bounds__(MAXT) k_tile_solve(OpDesc op, CoarseTab ct, co
                                                     const double* __restrict__ vscale, long long vss, int mode,
                                                     const cplx_t<R>* __restrict__ c, long long cs, int use_coarse,
                                                     Cz* __restrict__ z, long long zs, cplx_t<R>* __restrict__ ytiles,
-                                                    long long yts, BatchSkip sk, int* __restrict__ err) {
+                                                    long long yts, BatchSkip sk, int* __restrict__ err,
+                                                    long long spin) {
     using C = cplx_t<R>;
     const int rb = blockIdx.y;                      // batch entry
     if (sk.flag && sk.flag[(size_t)rb * sk.stride]) return;
@@ -382,7 +383,7 @@ __global__ void __launch_bounds__(MAXT) k_tile_solve(OpDesc op, CoarseTab ct, co
         const uint32_t parity = (uint32_t)((q / NST) & 1);
         // a thread whose wait expires flags it and finishes the step on whatever the
         // stage holds; the step's closing barrier then ends the sweep for every thread
-        if (!mbar_wait_bounded(&bar[st], parity)) s_fail = 1;
+        if (!mbar_wait_bounded(&bar[st], parity, spin)) s_fail = 1;
         const C* Wq = wst + (size_t)st * bs;
         const C* rc = r + (size_t)(q & 1) * T * ms;
         C* rn = r + (size_t)((q + 1) & 1) * T * ms;
@@ -492,7 +493,7 @@ static int launch_tile_solve_t(const Ctx& cx, int nb, const Tile* tiles, TileGro
         const int threads = (max_mx * 8 + 31) / 32 * 32;
         kern<<<dim3(grp.count, nb), threads, smem, cx.stream>>>(cx.op, cx.ct, tiles, grp.idx, W, w, ws, vscale, vss,
                                                                 mode, c, cs, use_coarse, z, zs, ytiles, yts, sk,
-                                                                cx.err);
+                                                                cx.err, cx.spin_limit);
         return 0;
     }
     if (tpr == 8) {
@@ -501,14 +502,15 @@ static int launch_tile_solve_t(const Ctx& cx, int nb, const Tile* tiles, TileGro
         const int threads = (max_mx * 8 + 31) / 32 * 32;
         kern<<<dim3(grp.count, nb), threads, smem, cx.stream>>>(cx.op, cx.ct, tiles, grp.idx, W, w, ws, vscale, vss,
                                                                 mode, c, cs, use_coarse, z, zs, ytiles, yts, sk,
-                                                                cx.err);
+                                                                cx.err, cx.spin_limit);
         return 0;
     }
     auto kern = k_tile_solve<Cw, Cz, R, T, NST, 4, 1024>;
     if (allow_dynamic_smem((const void*)kern, smem) != cudaSuccess) return -1;
     const int threads = (max_mx * 4 + 31) / 32 * 32;
     kern<<<dim3(grp.count, nb), threads, smem, cx.stream>>>(cx.op, cx.ct, tiles, grp.idx, W, w, ws, vscale, vss, mode,
-                                                            c, cs, use_coarse, z, zs, ytiles, yts, sk, cx.err);
+                                                            c, cs, use_coarse, z, zs, ytiles, yts, sk, cx.err,
+                                                            cx.spin_limit);
     return 0;
 }
 

@@ -3,12 +3,18 @@
 // allocated for the handle.
 //
 // Why it exists: some callers are not allowed to allocate device memory at the
-// point where they apply the preconditioner - code that runs while a CUDA
-// stream is being captured into a graph, real-time or embedded hosts that
+// point where they apply the preconditioner - real-time or embedded hosts that
 // forbid allocation after start-up, or applications that hand all device
-// memory to their own pool.  This entry point performs no cudaMalloc,
-// cudaFree or other allocating call; the caller passes only its input and
-// output buffers.
+// memory to their own pool and cannot give a library a share of it at run
+// time.  This entry point performs no cudaMalloc, cudaFree or other allocating
+// call; the caller passes only its input and output buffers.
+//
+// It runs the kernels of hzs_apply_precond for SAS2: the restriction, the FP64
+// coarse product and the subdomain solve.  In mixed precision the subdomain
+// solve writes z in complex128 directly, where hzs_apply_precond writes a
+// complex64 array and widens it; the solve's output stage forms every value in
+// the kernel's FP32 arithmetic and converts it only when it stores it, so the
+// two results are identical bit for bit.
 //
 // The work space is the static array below (kNoAllocScratchBytes, 1 MiB).  It
 // is part of the library's device image, so every GPU that loads the library

@@ -226,9 +226,10 @@ __global__ void k_deflate(OpDesc op, CoarseTab ct, const cplx_t<R>* __restrict__
 // cover[i] = (block a, offset of i in a, block b, offset in b), -1 if absent.
 template <typename Cz, typename Cy, typename R>
 __global__ void k_combine_additive(OpDesc op, CoarseTab ct, const cplx_t<R>* __restrict__ c, long long cs,
-                                   int use_coarse, const int4* __restrict__ cover, const Tile* __restrict__ tiles,
-                                   int nsub, const Cy* __restrict__ ytiles, long long yts, Cz* __restrict__ z,
-                                   long long zs, BatchSkip sk) {
+                                   int use_coarse, const int4* __restrict__ cover_x,
+                                   const int4* __restrict__ cover_y, const Tile* __restrict__ tiles, int nsx,
+                                   const Cy* __restrict__ ytiles, long long yts, Cz* __restrict__ z, long long zs,
+                                   BatchSkip sk, int weighted) {
     using C = cplx_t<R>;
     const int r = blockIdx.z;
     if (skipped(sk, r)) return;
@@ -240,8 +241,7 @@ __global__ void k_combine_additive(OpDesc op, CoarseTab ct, const cplx_t<R>* __r
     const size_t p = (size_t)j * n + i;
     if (!op_is_unknown(op, i, j)) { z[p] = mk<Cz>(0.0, 0.0); return; }
     C acc; acc.x = 0; acc.y = 0;
-    if (use_coarse) acc = prolong_at<R>(ct, c, i, j);
-    const int4 cxv = cover[i], cyv = cover[j];
+    const int4 cxv = cover_x[i], cyv = cover_y[j];
     const int ta[2] = {cxv.x, cxv.z}, la[2] = {cxv.y, cxv.w};
     const int tb[2] = {cyv.x, cyv.z}, lb[2] = {cyv.y, cyv.w};
 #pragma unroll
@@ -250,10 +250,17 @@ __global__ void k_combine_additive(OpDesc op, CoarseTab ct, const cplx_t<R>* __r
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             if (ta[s] < 0) continue;
-            const Tile& T = tiles[tb[u] * nsub + ta[s]];
+            const Tile& T = tiles[tb[u] * nsx + ta[s]];
             acc = cadd(acc, conv<C>(ytiles[T.yoff + (size_t)lb[u] * T.mx + la[s]]));
         }
     }
+    if (weighted) {
+        // D_i = 1 / (number of subdomains containing the node)
+        const int m = ((ta[0] >= 0) + (ta[1] >= 0)) * ((tb[0] >= 0) + (tb[1] >= 0));
+        const R inv = (R)1 / (R)m;
+        acc.x *= inv; acc.y *= inv;
+    }
+    if (use_coarse) acc = cadd(acc, prolong_at<R>(ct, c, i, j));
     z[p] = conv<Cz>(acc);
 }
 
@@ -350,16 +357,16 @@ HZS_DEF(float2, float2, float)
 
 template <typename Cz, typename Cy, typename R>
 void launch_combine_additive(const Ctx& cx, int nb, const cplx_t<R>* c, long long cs, int use_coarse,
-                             const int4* cover, const Tile* tiles, int nsub, const Cy* ytiles, long long yts, Cz* z,
-                             long long zs, BatchSkip sk) {
+                             const int4* cover_x, const int4* cover_y, const Tile* tiles, int nsx, const Cy* ytiles,
+                             long long yts, Cz* z, long long zs, BatchSkip sk, int weighted) {
     const dim3 b(32, 8);
     k_combine_additive<Cz, Cy, R><<<grid2d(cx.op.n, b, nb), b, 0, cx.stream>>>(
-        cx.op, cx.ct, c, cs, use_coarse, cover, tiles, nsub, ytiles, yts, z, zs, sk);
+        cx.op, cx.ct, c, cs, use_coarse, cover_x, cover_y, tiles, nsx, ytiles, yts, z, zs, sk, weighted);
 }
 #define HZS_CMB(Cz, Cy, R)                                                                                     \
     template void launch_combine_additive<Cz, Cy, R>(const Ctx&, int, const cplx_t<R>*, long long, int,       \
-                                                     const int4*, const Tile*, int, const Cy*, long long, Cz*, \
-                                                     long long, BatchSkip);
+                                                     const int4*, const int4*, const Tile*, int, const Cy*,     \
+                                                     long long, Cz*, long long, BatchSkip, int);
 HZS_CMB(double2, double2, double)
 HZS_CMB(float2, float2, float)
 #undef HZS_CMB

@@ -1,0 +1,371 @@
+// Delayed CGS2 (Section 5's GMRES, Arnoldi step) on an FP64 Krylov basis whose
+// arithmetic is spread over the FP64 and the FP32 pipes.
+//
+// The basis vectors, u~_j and w are FP64 vectors stored exactly as an FP32 head
+// (the value with its fraction truncated to 23 bits) and a 29-bit integer tail
+// (f53, see f32x2.cuh): 16 bytes a complex entry, as complex128.  The heads are a
+// complex64 array of their own, so the complex64 preconditioner and the
+// complex64 first-projection dot products read 8 bytes an entry, and the FP64
+// value or its three FP32 pieces are rebuilt with a few integer operations.
+//
+// The step is the delayed CGS2 of launch_dcgs2_step64 (krylov.cu): the
+// reorthogonalisation coefficients alpha = Q^H u~_j, the norm c = |u~_j|^2,
+// d = u~_j^H w and the first-projection update w - Q b - h_jj q_j are computed
+// to FP64 accuracy or better; the first-projection dot products b are complex64
+// on the heads.  The part's FP64 pipe runs at 1/64 of its FP32 rate, so each
+// pass splits the basis vectors between two arithmetic paths that run
+// concurrently:
+//   - FP64 fused multiply-adds on the rebuilt FP64 values (the vectors i whose bit
+//     i % 8 is set in a mask), interleaved in every warp with
+//   - FP32 error-free arithmetic on the three FP32 pieces of each value
+//     (head + 23 + 6 bits): products split exactly by FMAs (TwoProd) and summed
+//     in three-word expansions (TwoSum at the two upper levels), every rounding
+//     that is not carried below 2^-69 of the partial sums, so the error bound is
+//     tighter than that of the FP64 operations it replaces.
+// The reorthogonalisation update u~_j - Q alpha sums terms of order 2^-24 |u~_j|
+// (what the complex64 first projection left) and runs in double-float on the
+// FP32 pipes for every vector; its error is about 2^-46 of those terms.
+#include "f32x2.cuh"
+#include "kernels.cuh"
+
+namespace hzs {
+
+constexpr int kS53Threads = 256;
+constexpr int kS53Group = 2;            // basis vectors per warp task (dot pass) and per group (update)
+
+__device__ __forceinline__ void chunk_of53(long long N, long long& e0, long long& e1) {
+    const long long per = (N + gridDim.x - 1) / gridDim.x;
+    e0 = (long long)blockIdx.x * per;
+    e1 = e0 + per < N ? e0 + per : N;
+}
+
+__device__ __forceinline__ double2 f53_load(const float2* __restrict__ h, const uint2* __restrict__ t, long long e) {
+    const float2 a = h[e];
+    const uint2 b = t[e];
+    return make_double2(f53_double(a.x, b.x), f53_double(a.y, b.y));
+}
+__device__ __forceinline__ void f53_store(float2* __restrict__ h, uint2* __restrict__ t, long long e, double2 v) {
+    float2 a;
+    uint2 b;
+    f53_encode(v.x, a.x, b.x);
+    f53_encode(v.y, a.y, b.y);
+    h[e] = a;
+    t[e] = b;
+}
+
+// dst_r = scale_r * src_r (scale a power of two, or 1 without scale) stored as f53,
+// entries 0 .. N-1 of batch entry r = blockIdx.y.
+__global__ void k_f53_encode(long long N, const double2* __restrict__ src, long long ss, float2* __restrict__ dh,
+                             uint2* __restrict__ dt, long long ds, const double* __restrict__ scale,
+                             const KState* __restrict__ st) {
+    const int r = blockIdx.y;
+    if (st && st[r].done) return;
+    src += r * ss; dh += r * ds; dt += r * ds;
+    const double s = scale ? scale[r] : 1.0;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x)
+        f53_store(dh, dt, e, cscale(src[e], s));
+}
+
+// The stored right-hand side V_0 is scaled by the power of two nearest to 1/|f|,
+// so that its entries lie in the range of the f53 form whatever the scale of f;
+// sigma_0 and the preconditioner's input scale absorb the factor: scale[r] = 2^k,
+// sigma_0 <- sigma_0 / 2^k.
+__global__ void k_f53_scale0(int nb, double* __restrict__ sigma, double* __restrict__ sigt, long long sS,
+                             double* __restrict__ scale) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nb) return;
+    const double s0 = sigma[r * sS];
+    double sc = 1.0;
+    if (s0 > 0.0 && isfinite(s0)) {
+        int ex;
+        frexp(s0, &ex);
+        sc = ldexp(1.0, ex - 1);
+    }
+    scale[r] = sc;
+    sigma[r * sS] = s0 / sc;
+    sigt[r * sS] = s0 / sc;
+}
+
+// Dot pass of step j (entry r = blockIdx.y; slot j holds u~_j, slot j+1 w; heads Vh,
+// tails Vt).  Warp tasks of kS53Group basis vectors, each vector i summed with FP64 FMAs
+// when bit i % 8 of dmask is set, else in FP32 three-word expansions; the last task
+// computes c and d.
+// Partials per block as in k_d64_dot: alpha at [0, S) (FP64), b at [S, 2S) (FP32 words),
+// c at 2S, d at 2S+1 (FP64).
+__global__ void __launch_bounds__(kS53Threads, 2) k_s53_dot(int j, long long N, long long ld, int ps, int S,
+                                                           const float2* __restrict__ Vh, const uint2* __restrict__ Vt,
+                                                           long long sV, int has_w, unsigned dmask,
+                                                           double2* __restrict__ part, long long sP,
+                                                           const KState* __restrict__ st) {
+    constexpr int G = kS53Group;
+    const int r = blockIdx.y;
+    if (st[r].done) return;
+    Vh += r * sV; Vt += r * sV;
+    const float2* uh = Vh + (size_t)j * ld;
+    const uint2* ut = Vt + (size_t)j * ld;
+    const float2* wh = Vh + (size_t)(has_w ? j + 1 : j) * ld;
+    const uint2* wt = Vt + (size_t)(has_w ? j + 1 : j) * ld;
+    part += r * sP + (size_t)blockIdx.x * ps;
+    long long e0, e1;
+    chunk_of53(N, e0, e1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int ngroups = (j + G - 1) / G;
+    for (int gi = warp; gi <= ngroups; gi += nw) {
+        const int i0 = gi * G;
+        double2 al[G];
+        f2x B1[G], B2[G];                       // b = conj(head v) . head w as (wr x V0, wi x V0) sums
+#pragma unroll
+        for (int t = 0; t < G; ++t) { al[t] = make_double2(0.0, 0.0); B1[t] = B2[t] = 0ull; }
+        if (gi == ngroups) {
+            // c = |u~|^2 and d = u~^H w in FP64
+            double c = 0.0;
+            double2 d = make_double2(0.0, 0.0);
+            for (long long e = e0 + lane; e < e1; e += 32) {
+                const double2 x = f53_load(uh, ut, e);
+                c = fma(x.x, x.x, fma(x.y, x.y, c));
+                if (has_w) d = cfma_conj(x, f53_load(wh, wt, e), d);
+            }
+            c = warp_sum_d(c);
+            d = warp_sum(d);
+            if (lane == 0) {
+                part[2 * S] = make_double2(c, 0.0);
+                part[2 * S + 1] = d;
+            }
+            continue;
+        }
+        // vector i0 + t on the FP64 path when bit (i0 + t) % 8 of dmask is set, else in FP32
+        // three-word expansions: alpha = sum_e conj(v) u~ = (P.x + R.y, R.x - P.y) with
+        // P = sum_e ur (vr, vi), R = sum_e ui (vr, vi); the two paths interleave in every
+        // warp, so that the FP64 and FP32 pipes work at once
+        bool d64[G];
+        TF2 P[G], R[G];
+#pragma unroll
+        for (int t = 0; t < G; ++t) {
+            d64[t] = (dmask >> ((i0 + t) & 7)) & 1;
+            tf_zero(P[t]);
+            tf_zero(R[t]);
+        }
+        int cnt = 0;
+        for (long long e = e0 + lane; e < e1; e += 32) {
+            const float2 xh = __ldg(uh + e);
+            const uint2 xt = __ldg(ut + e);
+            const double2 x = make_double2(f53_double(xh.x, xt.x), f53_double(xh.y, xt.y));
+            float ur1, ur2, ui1, ui2;
+            f53_low(xh.x, xt.x, ur1, ur2);
+            f53_low(xh.y, xt.y, ui1, ui2);
+            const f2x Ur0 = f2_bcast(xh.x), NUr0 = f2_bcast(-xh.x), Ur1 = f2_bcast(ur1), NUr1 = f2_bcast(-ur1),
+                      Ur2 = f2_bcast(ur2);
+            const f2x Ui0 = f2_bcast(xh.y), NUi0 = f2_bcast(-xh.y), Ui1 = f2_bcast(ui1), NUi1 = f2_bcast(-ui1),
+                      Ui2 = f2_bcast(ui2);
+            const float2 yh = has_w ? __ldg(wh + e) : make_float2(0.f, 0.f);
+            const f2x Wr = f2_bcast(yh.x), Wi = f2_bcast(yh.y);
+            float2 vh[G];
+            uint2 vt[G];
+#pragma unroll
+            for (int t = 0; t < G; ++t) {
+                const bool in = i0 + t < j;
+                vh[t] = in ? __ldcs(Vh + (size_t)(i0 + t) * ld + e) : make_float2(0.f, 0.f);
+                vt[t] = in ? __ldcs(Vt + (size_t)(i0 + t) * ld + e) : make_uint2(0u, 0u);
+            }
+#pragma unroll
+            for (int t = 0; t < G; ++t) {
+                const f2x V0 = f2_of(vh[t]);
+                if (d64[t]) {
+                    const double2 v = make_double2(f53_double(vh[t].x, vt[t].x), f53_double(vh[t].y, vt[t].y));
+                    al[t] = cfma_conj(v, x, al[t]);
+                } else {
+                    f2x V1, V2;
+                    f53_low2(vh[t], vt[t], V1, V2);
+                    tf_mac53(P[t], Ur0, Ur1, Ur2, NUr0, NUr1, V0, V1, V2);
+                    tf_mac53(R[t], Ui0, Ui1, Ui2, NUi0, NUi1, V0, V1, V2);
+                }
+                B1[t] = fma2(Wr, V0, B1[t]);
+                B2[t] = fma2(Wi, V0, B2[t]);
+            }
+            if ((++cnt & 3) == 0) {
+#pragma unroll
+                for (int t = 0; t < G; ++t)
+                    if (!d64[t]) { tf_renorm(P[t]); tf_renorm(R[t]); }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < G; ++t)
+            if (!d64[t])
+                al[t] = make_double2(tf_lane(P[t], 0) + tf_lane(R[t], 1), tf_lane(R[t], 0) - tf_lane(P[t], 1));
+#pragma unroll
+        for (int t = 0; t < G; ++t) {
+            al[t] = warp_sum(al[t]);
+            const float2 b1 = f2_unpack(B1[t]), b2 = f2_unpack(B2[t]);
+            float2 b = make_float2(b1.x + b2.y, b2.x - b1.y);
+            b = warp_sum(b);
+            if (lane == 0 && i0 + t < j) {
+                part[i0 + t] = al[t];
+                reinterpret_cast<float4*>(part)[S + i0 + t] = make_float4(b.x, b.y, 0.f, 0.f);
+            }
+        }
+    }
+}
+
+// Coefficients of basis vector i for the update pass: c = sigma_i h1_i (an FP32
+// value, see k_dcgs_coef) as broadcast pairs and as FP64, and the
+// reorthogonalisation coefficient a = sigma_i alpha_i as double-float broadcast pairs.
+struct alignas(16) S53Coef {
+    f2x Pcr, Ncr, Pci, Nci;
+    f2x Parh, Narh, Narl, Paih, Naih, Nail;
+    double2 c;
+};
+
+// Update pass of step j (one entry per thread and sweep): V_j = u~_j - sum_i a_i V_i,
+// w <- w - sum_i c_i V_i - (h_jj sigma_j) V_j, npart[b] = sum_e |w[e]|^2 (FP64).
+// sum_i c_i V_i: vector i with FP64 FMAs when bit i % 8 of dmask is set, else in
+// three-word expansions A = sum cr (vr, vi),
+// B = sum ci (vr, vi) (c V = (A.x - B.y, A.y + B.x)); sum_i a_i V_i in double-float
+// for every vector.  The final sums and both results are FP64.
+__global__ void __launch_bounds__(kS53Threads, 2) k_s53_update(int j, long long N, long long ld,
+                                                              float2* __restrict__ Vh, uint2* __restrict__ Vt,
+                                                              long long sV, const double* __restrict__ sigma,
+                                                              const double2* __restrict__ h1,
+                                                              const double2* __restrict__ h2, long long sS,
+                                                              unsigned dmask,
+                                                              double* __restrict__ npart, int nblk,
+                                                              const KState* __restrict__ st) {
+    constexpr int G = kS53Group;
+    const int r = blockIdx.y;
+    if (st[r].done) return;
+    Vh += r * sV; Vt += r * sV; sigma += r * sS; h1 += r * sS; h2 += r * sS;
+    float2* uh = Vh + (size_t)j * ld;
+    uint2* ut = Vt + (size_t)j * ld;
+    float2* wh = Vh + (size_t)(j + 1) * ld;
+    uint2* wt = Vt + (size_t)(j + 1) * ld;
+    extern __shared__ S53Coef s53c[];
+    __shared__ double2 s_cj;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        const double2 c = cscale(h1[i], sigma[i]);
+        if (i == j) { s_cj = c; continue; }
+        const double2 a = cscale(h2[i], sigma[i]);
+        const float cr = (float)c.x, ci = (float)c.y;          // exact: c is an FP32 value
+        const float arh = (float)a.x, arl = (float)(a.x - (double)arh);
+        const float aih = (float)a.y, ail = (float)(a.y - (double)aih);
+        S53Coef k;
+        k.Pcr = f2_bcast(cr); k.Ncr = f2_bcast(-cr); k.Pci = f2_bcast(ci); k.Nci = f2_bcast(-ci);
+        k.Parh = f2_bcast(arh); k.Narh = f2_bcast(-arh); k.Narl = f2_bcast(-arl);
+        k.Paih = f2_bcast(aih); k.Naih = f2_bcast(-aih); k.Nail = f2_bcast(-ail);
+        k.c = make_double2((double)cr, (double)ci);
+        s53c[i] = k;
+    }
+    __syncthreads();
+    const double2 cj = s_cj;
+    long long e0, e1;
+    chunk_of53(N, e0, e1);
+    double nrm = 0.0;
+    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        TF2 A, B;
+        tf_zero(A);
+        tf_zero(B);
+        double2 acc = make_double2(0.0, 0.0);
+        f2x rah = 0ull, ral = 0ull, rbh = 0ull, rbl = 0ull;   // sum a (vr, vi): re part ar, im part ai
+        // one basis vector, index i, on the FP64 (d64) or the FP32 path
+        auto vec = [&](int i, float2 vh, uint2 vt, bool d64) {
+            const S53Coef& k = s53c[i];
+            f2x V1, V2;
+            f53_low2(vh, vt, V1, V2);
+            const f2x V0 = f2_of(vh);
+            if (d64) {
+                const double2 v = make_double2(f53_double(vh.x, vt.x), f53_double(vh.y, vt.y));
+                acc = cfma(k.c, v, acc);
+            } else {
+                tf_mac24(A, k.Pcr, k.Ncr, V0, V1, V2);
+                tf_mac24(B, k.Pci, k.Nci, V0, V1, V2);
+            }
+            df_mac2(rah, ral, k.Parh, k.Narh, k.Narl, V0, V1);
+            df_mac2(rbh, rbl, k.Paih, k.Naih, k.Nail, V0, V1);
+        };
+        // vectors j-1 .. 0 in groups of G (the dot pass read 0 .. j-1, so those still in
+        // L2 come first); the loads of the next group are issued before this one is used
+        int i = j - 1, g = 0;
+        float2 ch[G], nh[G];
+        uint2 ct[G], nt[G];
+        auto load = [&](int i0, float2* hh, uint2* tt) {
+#pragma unroll
+            for (int t = 0; t < G; ++t) {
+                const bool in = i0 - t >= 0;
+                hh[t] = in ? __ldcs(Vh + (size_t)(i0 - t) * ld + e) : make_float2(0.f, 0.f);
+                tt[t] = in ? __ldcs(Vt + (size_t)(i0 - t) * ld + e) : make_uint2(0u, 0u);
+            }
+        };
+        if (i >= 0) load(i, ch, ct);
+        for (; i >= 0; i -= G, ++g) {
+            if (i - G >= 0) load(i - G, nh, nt);
+#pragma unroll
+            for (int t = 0; t < G; ++t)
+                if (i - t >= 0) vec(i - t, ch[t], ct[t], (dmask >> ((i - t) & 7)) & 1);
+            if ((g & 1) == 1) {
+                tf_renorm(A);
+                tf_renorm(B);
+                df_norm2(rah, ral);
+                df_norm2(rbh, rbl);
+            }
+#pragma unroll
+            for (int t = 0; t < G; ++t) { ch[t] = nh[t]; ct[t] = nt[t]; }
+        }
+        // sum c_i V_i and sum a_i V_i in FP64
+        const double2 s = make_double2(acc.x + (tf_lane(A, 0) - tf_lane(B, 1)), acc.y + (tf_lane(A, 1) + tf_lane(B, 0)));
+        const float2 pah = f2_unpack(rah), pal = f2_unpack(ral), pbh = f2_unpack(rbh), pbl = f2_unpack(rbl);
+        const double rre = (f53_double(pah.x, 0u) + f53_double(pal.x, 0u)) - (f53_double(pbh.y, 0u) + f53_double(pbl.y, 0u));
+        const double rim = (f53_double(pah.y, 0u) + f53_double(pal.y, 0u)) + (f53_double(pbh.x, 0u) + f53_double(pbl.x, 0u));
+        // V_j = u~ - sum a_i V_i
+        double2 x = f53_load(uh, ut, e);
+        x.x -= rre;
+        x.y -= rim;
+        f53_store(uh, ut, e, x);
+        // w - sum c_i V_i - c_j V_j
+        double2 y = csub(f53_load(wh, wt, e), s);
+        y = cfms(cj, x, y);
+        f53_store(wh, wt, e, y);
+        nrm = fma(y.x, y.x, fma(y.y, y.y, nrm));
+    }
+    __shared__ double nred[kS53Threads / 32];
+    nrm = warp_sum_d(nrm);
+    if ((threadIdx.x & 31) == 0) nred[threadIdx.x >> 5] = nrm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += nred[k];
+        npart[(size_t)r * nblk + blockIdx.x] = t;
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+void launch_f53_encode(const Ctx& cx, int nb, long long N, const double2* src, long long ss, float2* dh, uint2* dt,
+                       long long ds, const double* scale, const KState* st) {
+    k_f53_encode<<<dim3(4 * cx.num_sms, nb), 256, 0, cx.stream>>>(N, src, ss, dh, dt, ds, scale, st);
+}
+
+void launch_f53_scale0(const Ctx& cx, int nb, double* sigma, double* sigt, long long sS, double* scale) {
+    k_f53_scale0<<<(nb + 127) / 128, 128, 0, cx.stream>>>(nb, sigma, sigt, sS, scale);
+}
+
+size_t s53_update_smem(int j) { return (size_t)(j > 0 ? j : 1) * sizeof(S53Coef); }
+
+void launch_s53_dot(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int has_w, unsigned dmask) {
+    const float2* Vh = kb.V32;
+    const uint2* Vt = static_cast<const uint2*>(kb.V32lo);
+    k_s53_dot<<<dim3(kb.nblk_dot, nb), kS53Threads, 0, cx.stream>>>(j, kb.N, kb.ld, kb.pstride(), kb.maxit + 1, Vh,
+                                                                   Vt, kb.sV(), has_w, dmask, kb.part, kb.sP(), kb.st);
+}
+
+// returns the number of blocks (the count of norm partials per entry), 0 if the
+// coefficients do not fit in shared memory
+int launch_s53_update(const Ctx& cx, const KrylovBufs& kb, int nb, int j, unsigned dmask) {
+    const size_t us = s53_update_smem(j);
+    if (allow_dynamic_smem((const void*)k_s53_update, us) != cudaSuccess) return 0;
+    const int bps = 2 * (us + 2048) <= (size_t)(228 * 1024) ? 2 : 1;
+    const int blocks = bps * cx.num_sms;                 // <= kb.nblk, the partials' stride
+    k_s53_update<<<dim3(blocks, nb), kS53Threads, us, cx.stream>>>(j, kb.N, kb.ld, kb.V32,
+                                                                  static_cast<uint2*>(kb.V32lo), kb.sV(), kb.sigma,
+                                                                  kb.h1, kb.h2, kb.sS(), dmask, kb.npart, kb.nblk,
+                                                                  kb.st);
+    return blocks;
+}
+
+}  // namespace hzs

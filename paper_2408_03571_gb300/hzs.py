@@ -37,13 +37,13 @@ EXPORTS = (
 
 class GridDesc(ct.Structure):
     _fields_ = [("n", ct.c_int), ("bc", ct.c_int), ("k", ct.c_double), ("kappa_dev", ct.c_void_p),
-                ("nsub", ct.c_int), ("overlap", ct.c_int)]
+                ("nsub", ct.c_int), ("overlap", ct.c_int), ("nsub_y", ct.c_int)]
 
 
 class PrecondDesc(ct.Structure):
     _fields_ = [("kind", ct.c_int), ("coarse", ct.c_int), ("coarse_ratio", ct.c_int),
                 ("precision", ct.c_int), ("dedup_tiles", ct.c_int), ("coarse_solver", ct.c_int),
-                ("autotune", ct.c_int)]
+                ("autotune", ct.c_int), ("scaling_mode", ct.c_int)]
 
 
 class PrecondInfo(ct.Structure):
@@ -65,12 +65,14 @@ class PipeRates(ct.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+SCALING_OWNER, SCALING_MULTIPLICITY = 0, 1
 SOLVE_PROFILE = 1
 SOLVE_ORTH_FP64 = 2
 SOLVE_BASIS_WIDE = 4
 SOLVE_GRAPH = 8
 SOLVE_BASIS_DF = 16
-ORTH_CGS2_FP64, ORTH_DCGS2_FP64, ORTH_DCGS2_DF = 0, 1, 2
+SOLVE_ORTH_DFMA = 32
+ORTH_CGS2_FP64, ORTH_DCGS2_FP64, ORTH_DCGS2_DF, ORTH_DCGS2_DFMA = 0, 1, 2, 3
 
 
 class SolveDesc(ct.Structure):
@@ -181,19 +183,21 @@ class SolveResult:
                            i.launches, i.status, i.basis_bits, i.orth_kind)
 
 
-def _solve_flags(profile=False, orth_fp64=False, wide_basis=False, graph=False, basis_df=False) -> int:
+def _solve_flags(profile=False, orth_fp64=False, wide_basis=False, graph=False, basis_df=False,
+                 orth_dfma=False) -> int:
     return ((SOLVE_PROFILE if profile else 0) | (SOLVE_ORTH_FP64 if orth_fp64 else 0)
             | (SOLVE_BASIS_WIDE if wide_basis else 0) | (SOLVE_GRAPH if graph else 0)
-            | (SOLVE_BASIS_DF if basis_df else 0))
+            | (SOLVE_BASIS_DF if basis_df else 0) | (SOLVE_ORTH_DFMA if orth_dfma else 0))
 
 
 class Grid:
     """Grid, operator and subdomain decomposition (Sections 2-3)."""
 
     def __init__(self, n: int, bc: int, k: float = 0.0, kappa: torch.Tensor | None = None,
-                 nsub: int = 1, overlap: int = 0, stream=None):
+                 nsub: int = 1, overlap: int = 0, stream=None, nsub_y: int = 0):
+        """nsub subdomains along x, nsub_y along y (0: nsub)."""
         lib = load()
-        self.n, self.bc, self.k, self.nsub, self.overlap = n, bc, k, nsub, overlap
+        self.n, self.bc, self.k, self.nsub, self.overlap, self.nsub_y = n, bc, k, nsub, overlap, nsub_y
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         kp = None
         if kappa is not None:
@@ -201,7 +205,7 @@ class Grid:
                 raise TypeError("kappa must be a CUDA float64 (n, n) tensor")
             kp = ct.c_void_p(kappa.contiguous().data_ptr())
             self._kappa_ref = kappa
-        d = GridDesc(n, bc, float(k), kp, nsub, overlap)
+        d = GridDesc(n, bc, float(k), kp, nsub, overlap, nsub_y)
         h = ct.c_void_p()
         _check(lib.hzs_grid_create(ct.byref(d), _stream_ptr(self.stream), ct.byref(h)))
         self._h = h
@@ -226,13 +230,16 @@ class Preconditioner:
     """Factorised Schwarz preconditioner (Sections 3-4) on a Grid."""
 
     def __init__(self, grid: Grid, kind: int = SHS2, coarse: int = COARSE_B2, coarse_ratio: int = 2,
-                 precision: int = FP64, dedup_tiles: bool = True, coarse_solver: int = 0, autotune: int = 0):
+                 precision: int = FP64, dedup_tiles: bool = True, coarse_solver: int = 0, autotune: int = 0,
+                 scaling_mode: int = 0):
         """autotune: 0 = default launch shape of the subdomain solve, 1 = pick it by timing at
-        set-up (reusing an earlier choice for the same problem size), 2 = always re-time."""
+        set-up (reusing an earlier choice for the same problem size), 2 = always re-time.
+        scaling_mode: D_i of SAS2 / SHS2, SCALING_OWNER (0) or SCALING_MULTIPLICITY (1)."""
         lib = load()
         self.grid = grid
         self.kind, self.coarse, self.coarse_ratio, self.precision = kind, coarse, coarse_ratio, precision
-        d = PrecondDesc(kind, coarse, coarse_ratio, precision, int(dedup_tiles), int(coarse_solver), int(autotune))
+        d = PrecondDesc(kind, coarse, coarse_ratio, precision, int(dedup_tiles), int(coarse_solver), int(autotune),
+                        int(scaling_mode))
         h = ct.c_void_p()
         _check(lib.hzs_precond_setup(grid.handle, ct.byref(d), ct.byref(h)), grid.handle)
         self._h = h
@@ -276,17 +283,20 @@ class Preconditioner:
         return u, [SolveResult.of(i) for i in infos[:nrhs]]
 
     def solve(self, f: torch.Tensor, tol: float = 1e-6, maxit: int = 1000, out=None, profile: bool = False,
-              orth_fp64: bool = False, wide_basis: bool = False, graph: bool = False, basis_df: bool = False):
+              orth_fp64: bool = False, wide_basis: bool = False, graph: bool = False, basis_df: bool = False,
+              orth_dfma: bool = False):
         """u = A^{-1} f by preconditioned GMRES; returns (u, [SolveResult per right-hand side]).
 
         With a MIXED preconditioner the orthogonalisation is the delayed CGS2 on the
-        complex128 basis (FP64 reorthogonalisation) unless
+        FP64 basis (FP64-accurate reorthogonalisation, the work split between the FP64
+        and FP32 pipes) unless
+        orth_dfma: the same with every FP64-accurate sum in FP64 FMAs,
         orth_fp64: the classical CGS2 with every product in FP64 (four basis passes a step), or
         basis_df: the delayed CGS2 on the narrower double-float basis, whose remainders are
         bf16 pairs (about 32 bits) for tol >= 1e-7 unless wide_basis (complex64, about 48 bits).
         graph: issue the Arnoldi steps as replayed CUDA graphs of 8 steps each."""
         return self._solve(load().hzs_solve, f, tol, maxit, out,
-                           _solve_flags(profile, orth_fp64, wide_basis, graph, basis_df))
+                           _solve_flags(profile, orth_fp64, wide_basis, graph, basis_df, orth_dfma))
 
     def adjoint_solve(self, g: torch.Tensor, tol: float = 1e-6, maxit: int = 1000, out=None, profile: bool = False,
                       graph: bool = False):
@@ -313,7 +323,7 @@ class Preconditioner:
 
 
 def solve_batched(problems, rhs, tol: float = 1e-6, maxit: int = 1000, orth_fp64: bool = False,
-                  wide_basis: bool = False, graph: bool = False, basis_df: bool = False):
+                  wide_basis: bool = False, graph: bool = False, basis_df: bool = False, orth_dfma: bool = False):
     """Batched solve over several problems: ``problems`` is a list of Preconditioner
     handles (distinct), ``rhs`` a matching list of complex128 tensors of shape
     (nrhs_k, n_k, n_k).  Returns (list of solutions, list of lists of SolveResult)."""
@@ -330,7 +340,8 @@ def solve_batched(problems, rhs, tol: float = 1e-6, maxit: int = 1000, orth_fp64
     infos = (SolveInfo * max(total, 1))()
     arr = lambda vals: (ct.c_void_p * max(k, 1))(*vals)
     sd = SolveDesc(float(tol), int(maxit),
-                   _solve_flags(orth_fp64=orth_fp64, wide_basis=wide_basis, graph=graph, basis_df=basis_df))
+                   _solve_flags(orth_fp64=orth_fp64, wide_basis=wide_basis, graph=graph, basis_df=basis_df,
+                                orth_dfma=orth_dfma))
     st = lib.hzs_solve_batched(k, arr([P.handle.value for P in problems]), ct.byref(sd),
                                arr([f.data_ptr() for f in rhs]), arr([u.data_ptr() for u in outs]),
                                (ct.c_int * max(k, 1))(*counts), infos)

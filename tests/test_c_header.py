@@ -28,14 +28,15 @@ def test_header_is_c99_and_links(tmp_path):
     c.write_text(
         "#include <stdio.h>\n#include \"hzs.h\"\n"
         "int main(void) {\n"
-        "    hzs_grid_desc gd = {65, HZS_DIRICHLET, 20.0, NULL, 4, 2};\n"
-        "    hzs_precond_desc pd = {HZS_SHS2, HZS_COARSE_B2, 8, HZS_MIXED, 1, HZS_COARSE_SOLVER_AUTO, 0};\n"
+        "    hzs_grid_desc gd = {65, HZS_DIRICHLET, 20.0, NULL, 4, 2, 0};\n"
+        "    hzs_precond_desc pd = {HZS_SHS2, HZS_COARSE_B2, 8, HZS_MIXED, 1, HZS_COARSE_SOLVER_AUTO, 0,\n"
+        "                           HZS_SCALING_OWNER};\n"
         "    hzs_solve_desc sd = {1e-7, 200, HZS_SOLVE_GRAPH};\n"
-        "    hzs_solve_info info; hzs_precond_info pinfo;\n"
+        "    hzs_solve_info info; hzs_precond_info pinfo; hzs_pipe_rates rates;\n"
         "    void (*fns[])(void) = {\n"
         + "".join(f"        (void (*)(void))&{n},\n" for n in names)
         + "    };\n"
-        "    (void)gd; (void)pd; (void)sd; (void)info; (void)pinfo;\n"
+        "    (void)gd; (void)pd; (void)sd; (void)info; (void)pinfo; (void)rates;\n"
         "    printf(\"%u %s\\n\", (unsigned)(sizeof fns / sizeof fns[0]), hzs_status_string(HZS_OK));\n"
         "    return 0;\n}\n")
     exe = tmp_path / "uses_hzs"
@@ -52,6 +53,7 @@ STRUCTS = {
     "hzs_solve_desc": "SolveDesc",
     "hzs_solve_info": "SolveInfo",
     "hzs_precond_info": "PrecondInfo",
+    "hzs_pipe_rates": "PipeRates",
 }
 
 

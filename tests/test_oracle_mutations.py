@@ -154,8 +154,8 @@ def overlap_one_sided(mp):
 
 def local_solve_conjugated(mp):
     plant(mp, oschwarz.Schwarz, "local_sum",
-          ("y = lu.solve(np.ascontiguousarray(r[s.idx], dtype=self.ct))",
-           "y = np.conj(lu.solve(np.conj(np.ascontiguousarray(r[s.idx], dtype=self.ct))))"))
+          ("y = lu.solve(np.ascontiguousarray(r[s.idx], dtype=np.complex128))",
+           "y = np.conj(lu.solve(np.conj(np.ascontiguousarray(r[s.idx], dtype=np.complex128))))"))
     return [(ts.test_preconditioner_dense_formula, (SOMMERFELD, AS1, B2))]
 
 
@@ -212,6 +212,15 @@ def c64_mode_in_fp64(mp):
     return [(ts.test_complex64_preconditioner_is_the_same_operator_rounded, (DIRICHLET, SAS2))]
 
 
+def c64_factors_transposed(mp):
+    # the complex64 local solve with its triangular factors applied in the wrong order
+    plant(mp, oschwarz.Schwarz, "_solve32", ("y = spla.spsolve_triangular(L, pb, lower=True, unit_diagonal=True)",
+                                            "y = spla.spsolve_triangular(U, pb, lower=False)"),
+          ("z = spla.spsolve_triangular(U, y, lower=False)",
+           "z = spla.spsolve_triangular(L, y, lower=True, unit_diagonal=True)"))
+    return [(ts.test_complex64_preconditioner_is_the_same_operator_rounded, (SOMMERFELD, AS1))]
+
+
 def c64_coarse_solve_dropped(mp):
     plant(mp, oschwarz.Schwarz, "apply_Q", ("c = self.coarse.solve(c).astype(np.complex64)",
                                            "c = c.astype(np.complex64)"))
@@ -261,7 +270,7 @@ MUTATIONS = [
     sommerfeld_sign, edge_rows_not_halved, kappa_dropped, coupling_sign, dkappa_sign,
     dkappa_no_boundary_part, kappa_field_transposed, d_is_identity, overlap_one_sided, local_solve_conjugated,
     b2_half_cell_shift, b2_middle_piece, p1_hat_too_wide, mp1_keeps_coarse_boundary, galerkin_of_conj,
-    shs2_deflation_sign, sas2_without_d, as2_without_q, c64_mode_in_fp64, c64_coarse_solve_dropped,
+    shs2_deflation_sign, sas2_without_d, as2_without_q, c64_mode_in_fp64, c64_factors_transposed, c64_coarse_solve_dropped,
     c64_deflation_with_other_transfer, givens_sine_conjugated,
     gram_schmidt_conjugate_side, solution_without_preconditioner, gradient_sign, adjoint_without_conjugate,
 ]

@@ -125,9 +125,12 @@ class CoarseSolver:
         self.cs = cs
         self.A0 = cs.galerkin(A)
         self.lu = sla.lu_factor(self.A0)
+        self.inner = None           # a multilevel solver standing in for A_0^{-1} (see schwarz.py)
 
     def solve(self, c: np.ndarray) -> np.ndarray:
-        """A_0^{-1} c (FP64)."""
+        """A_0^{-1} c (FP64), or its multilevel approximation when one is set."""
+        if self.inner is not None:
+            return self.inner.solve(c)
         return sla.lu_solve(self.lu, np.asarray(c, dtype=np.complex128))
 
     def apply_Q(self, v: np.ndarray) -> np.ndarray:

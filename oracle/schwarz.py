@@ -29,7 +29,7 @@ from __future__ import annotations
 import numpy as np
 import scipy.sparse.linalg as spla
 
-from .coarse import CoarseSolver, CoarseSpace
+from .coarse import B2, CoarseSolver, CoarseSpace
 from .decomposition import Decomposition
 
 AS1, AS2, SAS2, SHS2 = "as1", "as2", "sas2", "shs2"
@@ -38,10 +38,52 @@ AS1, AS2, SAS2, SHS2 = "as1", "as2", "sas2", "shs2"
 FP64, C64 = "fp64", "c64"
 
 
+class MultilevelCoarseSolver:
+    """Inexact coarse solve for large coarse spaces (the paper names the exact coarse solve
+    as the bottleneck when |G_H| is large, Section 5): A_0^{-1} replaced by one application
+    of the two-level Schwarz method SHS2 (Eq. 6) on the coarse grid G_H itself - coarse
+    subdomains of G_H with exact local solves of the blocks of A_0 and a B_2 coarse space of
+    ratio p0 on G_H with its own exact Galerkin solve.  With a single coarse subdomain it
+    is A_0^{-1} exactly (Q_00 + A_0^{-1} (I - A_0 Q_00) = A_0^{-1}).
+
+    inner_tol: None applies M_0^{-1} once (a fixed linear approximation of A_0^{-1});
+    a tolerance runs right-preconditioned GMRES on A_0 c' = c with M_0 to that relative
+    residual instead (a nonlinear coarse solve: the outer iteration must then be the
+    flexible GMRES).  A coarse-of-coarse level is as bound by k H_0 <= 1 as the first
+    one (Section 5), so single applications need H_0 small; inner iterations do not."""
+
+    def __init__(self, prob, cs, A0, ns0, ov0: int, p0: int, inner_tol: float | None = None,
+                 inner_maxit: int = 200):
+        import scipy.sparse as sp
+        from .problem import DIRICHLET, Problem
+        # G_H as a grid: MP-1 keeps only its interior coarse nodes, so it is the interior of a
+        # Dirichlet grid two nodes wider; MP-2 keeps all of them
+        n0 = cs.nc1 + 2 if prob.bc == DIRICHLET else cs.nc1
+        self.prob0 = Problem(n0, prob.bc, 1.0)
+        if self.prob0.N != A0.shape[0]:
+            raise ValueError("coarse grid and coarse matrix disagree")
+        self.A0 = sp.csr_matrix(A0)
+        self.M0 = Schwarz(self.prob0, self.A0, ns0, ov0, SHS2, B2, p0)
+        self.inner_tol, self.inner_maxit = inner_tol, inner_maxit
+        self.inner_its = []
+
+    def solve(self, c: np.ndarray) -> np.ndarray:
+        """The approximation of A_0^{-1} c (FP64)."""
+        c = np.asarray(c, dtype=np.complex128)
+        if self.inner_tol is None:
+            return self.M0.apply(c)
+        from .gmres import gmres
+        r = gmres(lambda x: self.A0 @ x, self.M0.apply, c, self.inner_tol, self.inner_maxit)
+        self.inner_its.append(r.iterations)
+        return r.x
+
+
 class Schwarz:
     def __init__(self, prob, A, ns, overlap: int, kind: str = SHS2,
                  coarse: str | None = "b2", p: int | None = None, precision: str = FP64,
-                 scaling: str = "owner", b2_mode: str = "spline"):
+                 scaling: str = "owner", b2_mode: str = "spline", coarse_solve: dict | None = None):
+        """coarse_solve: None for the exact coarse solve (dense LU of A_0), or
+        dict(ns=, ov=, p=[, inner_tol=]) for the multilevel one (MultilevelCoarseSolver)."""
         if kind not in (AS1, AS2, SAS2, SHS2):
             raise ValueError(kind)
         if kind != AS1 and coarse is None:
@@ -69,6 +111,10 @@ class Schwarz:
         self.coarse = None
         if kind != AS1:
             self.coarse = CoarseSolver(CoarseSpace(prob, coarse, p, b2_mode), Ar)
+            if coarse_solve is not None:
+                self.coarse.inner = MultilevelCoarseSolver(prob, self.coarse.cs, self.coarse.A0, coarse_solve["ns"],
+                                                           coarse_solve["ov"], coarse_solve["p"],
+                                                           coarse_solve.get("inner_tol"))
             if precision == C64:
                 self.R0p = self.coarse.cs.R0.astype(np.float32)
 

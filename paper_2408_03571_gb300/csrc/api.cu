@@ -802,6 +802,10 @@ static hzs_status ensure_krylov(hzs_precond* p, int maxit, int nb, bool full_v) 
     kb.nblk_dot = 4 * g->num_sms;
     // tuning knob for the f53 passes: HZS_F53_MASK="dot,update", two 8-bit masks of the vectors
     // (index mod 8) summed with FP64 FMAs; the others take the FP32 path
+    if (const char* ev = std::getenv("HZS_F53_OCC")) {
+        const int v = std::atoi(ev);
+        if (v == 2 || v == 3) kb.s53_minb = v;
+    }
     if (const char* ev = std::getenv("HZS_F53_MASK")) {
         unsigned a = 0, b = 0;
         if (std::sscanf(ev, "%i,%i", (int*)&a, (int*)&b) == 2 && a <= 255u && b <= 255u) {

@@ -185,10 +185,11 @@ struct KrylovBufs {
                        // complex64 words or, with lo16, bf16 pairs (LoDst); sized for complex64
     int lo16;          // remainders stored as bf16 pairs (set per solve)
     // f53 basis: vectors i with bit i % 8 set are summed with FP64 FMAs in the dot pass / the
-    // update pass, the others in FP32 error-free arithmetic (5 of 8 on FP64: the fastest split
-    // measured at the headline size)
-    unsigned dmask_dot = 0x6Du;
-    unsigned dmask_upd = 0x6Du;
+    // update pass, the others in FP32 error-free arithmetic; both passes compiled for 3 blocks
+    // per SM (the fastest of the splits and occupancies measured at the headline size)
+    unsigned dmask_dot = 0x77u;
+    unsigned dmask_upd = 0x77u;
+    int s53_minb = 3;
     double* sigma;     // (maxit+1): basis vector i = sigma[i] * V_i
     double2* H;        // (maxit+1) x maxit, column j at H[j*(maxit+1)]
     double* cs;        // maxit+1
@@ -243,7 +244,7 @@ void launch_f53_encode(const Ctx& cx, int nb, long long N, const double2* src, l
                        long long ds, const double* scale, const KState* st);
 void launch_f53_scale0(const Ctx& cx, int nb, double* sigma, double* sigt, long long sS, double* scale);
 size_t s53_update_smem(int j);
-void launch_s53_dot(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int has_w, unsigned dmask);
+int launch_s53_dot(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int has_w, unsigned dmask);
 int launch_s53_update(const Ctx& cx, const KrylovBufs& kb, int nb, int j, unsigned dmask);
 void launch_lsq_solve(const Ctx& cx, const KrylovBufs& kb, int nb);
 void launch_combine_basis(const Ctx& cx, const KrylovBufs& kb, int nb, double2* x, long long xs);

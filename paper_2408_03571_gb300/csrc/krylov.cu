@@ -1298,10 +1298,10 @@ void launch_dcgs2_step64(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int
 bool launch_dcgs2_step53(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int last_only, cudaEvent_t* ev) {
     const int S = kb.maxit + 1, ps = kb.pstride();
     if (ev) cudaEventRecord(ev[0], cx.stream);
-    launch_s53_dot(cx, kb, nb, j, !last_only, kb.dmask_dot);
+    const int ndot = launch_s53_dot(cx, kb, nb, j, !last_only, kb.dmask_dot);
     if (ev) cudaEventRecord(ev[1], cx.stream);
     const dim3 rg(((2 * j + 2) * 32 + 255) / 256, nb);
-    k_dcgs_reduce<true><<<rg, 256, 0, cx.stream>>>(j, kb.nblk_dot, ps, S, kb.part, kb.sP(), kb.sigma, kb.h2, kb.hn,
+    k_dcgs_reduce<true><<<rg, 256, 0, cx.stream>>>(j, ndot, ps, S, kb.part, kb.sP(), kb.sigma, kb.h2, kb.hn,
                                                    kb.sS(), kb.sN(), kb.st);
     k_dcgs_coef<<<nb, kFinThreads, 0, cx.stream>>>(j, kb.maxit, last_only, kb.hn, kb.sN(), kb.h1, kb.h2, kb.H,
                                                    kb.sH(), kb.sigma, kb.sS(), kb.st, kb.active);

@@ -25,6 +25,8 @@
 // The reorthogonalisation update u~_j - Q alpha sums terms of order 2^-24 |u~_j|
 // (what the complex64 first projection left) and runs in double-float on the
 // FP32 pipes for every vector; its error is about 2^-46 of those terms.
+#include <algorithm>
+
 #include "f32x2.cuh"
 #include "kernels.cuh"
 
@@ -92,7 +94,8 @@ __global__ void k_f53_scale0(int nb, double* __restrict__ sigma, double* __restr
 // computes c and d.
 // Partials per block as in k_d64_dot: alpha at [0, S) (FP64), b at [S, 2S) (FP32 words),
 // c at 2S, d at 2S+1 (FP64).
-__global__ void __launch_bounds__(kS53Threads, 2) k_s53_dot(int j, long long N, long long ld, int ps, int S,
+template <int MINB>
+__global__ void __launch_bounds__(kS53Threads, MINB) k_s53_dot(int j, long long N, long long ld, int ps, int S,
                                                            const float2* __restrict__ Vh, const uint2* __restrict__ Vt,
                                                            long long sV, int has_w, unsigned dmask,
                                                            double2* __restrict__ part, long long sP,
@@ -221,7 +224,8 @@ struct alignas(16) S53Coef {
 // three-word expansions A = sum cr (vr, vi),
 // B = sum ci (vr, vi) (c V = (A.x - B.y, A.y + B.x)); sum_i a_i V_i in double-float
 // for every vector.  The final sums and both results are FP64.
-__global__ void __launch_bounds__(kS53Threads, 2) k_s53_update(int j, long long N, long long ld,
+template <int MINB>
+__global__ void __launch_bounds__(kS53Threads, MINB) k_s53_update(int j, long long N, long long ld,
                                                               float2* __restrict__ Vh, uint2* __restrict__ Vt,
                                                               long long sV, const double* __restrict__ sigma,
                                                               const double2* __restrict__ h1,
@@ -347,24 +351,44 @@ void launch_f53_scale0(const Ctx& cx, int nb, double* sigma, double* sigt, long 
 
 size_t s53_update_smem(int j) { return (size_t)(j > 0 ? j : 1) * sizeof(S53Coef); }
 
-void launch_s53_dot(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int has_w, unsigned dmask) {
+// returns the number of blocks (rows of partials the reduction sums): whole waves of
+// resident blocks, at most kb.nblk_dot
+int launch_s53_dot(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int has_w, unsigned dmask) {
     const float2* Vh = kb.V32;
     const uint2* Vt = static_cast<const uint2*>(kb.V32lo);
-    k_s53_dot<<<dim3(kb.nblk_dot, nb), kS53Threads, 0, cx.stream>>>(j, kb.N, kb.ld, kb.pstride(), kb.maxit + 1, Vh,
-                                                                   Vt, kb.sV(), has_w, dmask, kb.part, kb.sP(), kb.st);
+    if (kb.s53_minb == 3) {
+        const int blocks = std::min(kb.nblk_dot, 3 * cx.num_sms);
+        k_s53_dot<3><<<dim3(blocks, nb), kS53Threads, 0, cx.stream>>>(j, kb.N, kb.ld, kb.pstride(), kb.maxit + 1, Vh,
+                                                                     Vt, kb.sV(), has_w, dmask, kb.part, kb.sP(),
+                                                                     kb.st);
+        return blocks;
+    }
+    const int blocks = std::min(kb.nblk_dot, 4 * cx.num_sms);
+    k_s53_dot<2><<<dim3(blocks, nb), kS53Threads, 0, cx.stream>>>(j, kb.N, kb.ld, kb.pstride(), kb.maxit + 1, Vh, Vt,
+                                                                 kb.sV(), has_w, dmask, kb.part, kb.sP(), kb.st);
+    return blocks;
 }
 
 // returns the number of blocks (the count of norm partials per entry), 0 if the
 // coefficients do not fit in shared memory
 int launch_s53_update(const Ctx& cx, const KrylovBufs& kb, int nb, int j, unsigned dmask) {
     const size_t us = s53_update_smem(j);
-    if (allow_dynamic_smem((const void*)k_s53_update, us) != cudaSuccess) return 0;
-    const int bps = 2 * (us + 2048) <= (size_t)(228 * 1024) ? 2 : 1;
-    const int blocks = bps * cx.num_sms;                 // <= kb.nblk, the partials' stride
-    k_s53_update<<<dim3(blocks, nb), kS53Threads, us, cx.stream>>>(j, kb.N, kb.ld, kb.V32,
-                                                                  static_cast<uint2*>(kb.V32lo), kb.sV(), kb.sigma,
-                                                                  kb.h1, kb.h2, kb.sS(), dmask, kb.npart, kb.nblk,
-                                                                  kb.st);
+    const bool three = kb.s53_minb == 3;
+    const void* fn = three ? (const void*)k_s53_update<3> : (const void*)k_s53_update<2>;
+    if (allow_dynamic_smem(fn, us) != cudaSuccess) return 0;
+    // blocks per SM: as the registers allow while their shared memory fits (<= kb.nblk / SMs,
+    // the partials' stride)
+    int bps = three ? 3 : 2;
+    while (bps > 1 && (size_t)bps * (us + 2048) > (size_t)(228 * 1024)) --bps;
+    const int blocks = bps * cx.num_sms;
+    if (three)
+        k_s53_update<3><<<dim3(blocks, nb), kS53Threads, us, cx.stream>>>(
+            j, kb.N, kb.ld, kb.V32, static_cast<uint2*>(kb.V32lo), kb.sV(), kb.sigma, kb.h1, kb.h2, kb.sS(), dmask,
+            kb.npart, kb.nblk, kb.st);
+    else
+        k_s53_update<2><<<dim3(blocks, nb), kS53Threads, us, cx.stream>>>(
+            j, kb.N, kb.ld, kb.V32, static_cast<uint2*>(kb.V32lo), kb.sV(), kb.sigma, kb.h1, kb.h2, kb.sS(), dmask,
+            kb.npart, kb.nblk, kb.st);
     return blocks;
 }
 

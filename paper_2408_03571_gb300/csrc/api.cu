@@ -800,11 +800,30 @@ static hzs_status ensure_krylov(hzs_precond* p, int maxit, int nb, bool full_v) 
     // delayed-CGS2 dot pass, 64 registers a thread, runs 4 per SM
     kb.nblk = 3 * g->num_sms;
     kb.nblk_dot = 4 * g->num_sms;
-    // tuning knob for the f53 passes: HZS_F53_MASK="dot,update", two 8-bit masks of the vectors
-    // (index mod 8) summed with FP64 FMAs; the others take the FP32 path
+    // tuning knobs of the f53 passes (the defaults in KrylovBufs are the fastest measured at
+    // the headline size), read when the work space is made:
+    //   HZS_F53_MASK="dot,update"  two 8-bit masks of the vectors (index mod 8) summed with
+    //                              FP64 FMAs; the others take the FP32 path
+    //   HZS_F53_OCC=2|3            blocks per SM of both passes; HZS_F53_DOT_OCC=2..4 the dot pass
+    //   HZS_F53_WS=0|1             dot pass with warp tasks on one path each, or mixed tasks
+    //   HZS_F53_GROUP=1|2          vectors per FP32 (or mixed) warp task of the dot pass
+    //   HZS_F53_RING=0|3|4         stages of the dot pass's copy ring (mixed tasks; 0: none)
     if (const char* ev = std::getenv("HZS_F53_OCC")) {
         const int v = std::atoi(ev);
-        if (v == 2 || v == 3) kb.s53_minb = v;
+        if (v == 2 || v == 3) kb.s53_minb = kb.s53_dot_minb = v;
+    }
+    if (const char* ev = std::getenv("HZS_F53_DOT_OCC")) {
+        const int v = std::atoi(ev);
+        if (v >= 2 && v <= 4) kb.s53_dot_minb = v;
+    }
+    if (const char* ev = std::getenv("HZS_F53_RING")) {
+        const int v = std::atoi(ev);
+        if (v == 0 || v == 3 || v == 4) kb.s53_ring = v;
+    }
+    if (const char* ev = std::getenv("HZS_F53_WS")) kb.s53_ws = std::atoi(ev) ? 1 : 0;
+    if (const char* ev = std::getenv("HZS_F53_GROUP")) {
+        const int v = std::atoi(ev);
+        if (v == 1 || v == 2) kb.s53_group = v;
     }
     if (const char* ev = std::getenv("HZS_F53_MASK")) {
         unsigned a = 0, b = 0;
@@ -1032,7 +1051,7 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
         if (prof) HZS_CUDA(g, cudaEventRecord(pe[2], cx.stream));
         if (s53) {
             if (!launch_dcgs2_step53(cx, kb, nb, j, 0, prof ? pe + 4 : nullptr))
-                return fail(g, HZS_ERR_CUDA, "Arnoldi update pass: coefficients exceed shared memory");
+                return fail(g, HZS_ERR_CUDA, "Arnoldi step on the f53 basis could not be launched");
         } else if (d64) {
             launch_dcgs2_step64(cx, kb, nb, j, 0, prof ? pe + 4 : nullptr);
         } else if (orth32) {

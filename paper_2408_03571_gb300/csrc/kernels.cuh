@@ -185,11 +185,15 @@ struct KrylovBufs {
                        // complex64 words or, with lo16, bf16 pairs (LoDst); sized for complex64
     int lo16;          // remainders stored as bf16 pairs (set per solve)
     // f53 basis: vectors i with bit i % 8 set are summed with FP64 FMAs in the dot pass / the
-    // update pass, the others in FP32 error-free arithmetic; both passes compiled for 3 blocks
-    // per SM (the fastest of the splits and occupancies measured at the headline size)
-    unsigned dmask_dot = 0x77u;
-    unsigned dmask_upd = 0x77u;
-    int s53_minb = 3;
+    // update pass, the others in FP32 error-free arithmetic.  Defaults: the fastest of the
+    // splits, occupancies, task sizes and copy rings measured at the headline size
+    unsigned dmask_dot = 0x6Du;    // 5 of 8 vectors on the FP64 path
+    unsigned dmask_upd = 0x77u;    // 6 of 8
+    int s53_minb = 3;      // update pass: blocks per SM it is compiled for (2 or 3)
+    int s53_ring = 4;      // dot pass: stages of its per-thread shared-memory copy ring (0: none)
+    int s53_group = 2;     // dot pass: basis vectors per warp task on the FP32 path (1 or 2)
+    int s53_dot_minb = 2;  // dot pass: blocks per SM it is compiled for (2, 3 or 4)
+    int s53_ws = 1;        // dot pass: each warp task on one of the two paths (k_s53_dot_ws)
     double* sigma;     // (maxit+1): basis vector i = sigma[i] * V_i
     double2* H;        // (maxit+1) x maxit, column j at H[j*(maxit+1)]
     double* cs;        // maxit+1

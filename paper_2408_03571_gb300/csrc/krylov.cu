@@ -1293,13 +1293,14 @@ void launch_dcgs2_step64(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int
 // Delayed CGS2 on the f53 basis (heads kb.V32, tails kb.V32lo; see orth53.cu): the
 // step structure of launch_dcgs2_step64 with the passes split between the FP64 and
 // FP32 pipes (kb.dmask_dot, kb.dmask_upd: the vectors on the FP64 path).
-// False (nothing launched after the dot pass) when the update pass's coefficients do
-// not fit in shared memory.
+// False (nothing launched after the failed pass) when the dot pass could not be
+// launched or the update pass's coefficients do not fit in shared memory.
 bool launch_dcgs2_step53(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int last_only, cudaEvent_t* ev) {
     const int S = kb.maxit + 1, ps = kb.pstride();
     if (ev) cudaEventRecord(ev[0], cx.stream);
     const int ndot = launch_s53_dot(cx, kb, nb, j, !last_only, kb.dmask_dot);
     if (ev) cudaEventRecord(ev[1], cx.stream);
+    if (ndot == 0) return false;
     const dim3 rg(((2 * j + 2) * 32 + 255) / 256, nb);
     k_dcgs_reduce<true><<<rg, 256, 0, cx.stream>>>(j, ndot, ps, S, kb.part, kb.sP(), kb.sigma, kb.h2, kb.hn,
                                                    kb.sS(), kb.sN(), kb.st);

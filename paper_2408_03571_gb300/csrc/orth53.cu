@@ -35,6 +35,17 @@ namespace hzs {
 constexpr int kS53Threads = 256;
 constexpr int kS53Group = 2;            // basis vectors per warp task (dot pass) and per group (update)
 
+// per-thread asynchronous 8-byte copies global -> shared (read back by the same thread
+// after cp.async.wait_group, so no block barrier is involved)
+__device__ __forceinline__ void cp_async_8(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ void chunk_of53(long long N, long long& e0, long long& e1) {
     const long long per = (N + gridDim.x - 1) / gridDim.x;
     e0 = (long long)blockIdx.x * per;
@@ -94,13 +105,16 @@ __global__ void k_f53_scale0(int nb, double* __restrict__ sigma, double* __restr
 // computes c and d.
 // Partials per block as in k_d64_dot: alpha at [0, S) (FP64), b at [S, 2S) (FP32 words),
 // c at 2S, d at 2S+1 (FP64).
-template <int MINB>
+// NS > 0: the basis vectors' and u~'s entries and w's heads stream through a per-thread
+// ring of NS stages in shared memory (cp.async; each thread reads back only what it
+// copied itself), NS - 1 entries ahead of the one being summed; NS == 0 loads them
+// into registers where they are used.
+template <int MINB, int NS, int G>
 __global__ void __launch_bounds__(kS53Threads, MINB) k_s53_dot(int j, long long N, long long ld, int ps, int S,
                                                            const float2* __restrict__ Vh, const uint2* __restrict__ Vt,
                                                            long long sV, int has_w, unsigned dmask,
                                                            double2* __restrict__ part, long long sP,
                                                            const KState* __restrict__ st) {
-    constexpr int G = kS53Group;
     const int r = blockIdx.y;
     if (st[r].done) return;
     Vh += r * sV; Vt += r * sV;
@@ -109,6 +123,7 @@ __global__ void __launch_bounds__(kS53Threads, MINB) k_s53_dot(int j, long long 
     const float2* wh = Vh + (size_t)(has_w ? j + 1 : j) * ld;
     const uint2* wt = Vt + (size_t)(has_w ? j + 1 : j) * ld;
     part += r * sP + (size_t)blockIdx.x * ps;
+    extern __shared__ uint2 s53ring[];              // NS x (2G + 3) x kS53Threads 8-byte slots
     long long e0, e1;
     chunk_of53(N, e0, e1);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -149,9 +164,65 @@ __global__ void __launch_bounds__(kS53Threads, MINB) k_s53_dot(int j, long long 
             tf_zero(R[t]);
         }
         int cnt = 0;
-        for (long long e = e0 + lane; e < e1; e += 32) {
-            const float2 xh = __ldg(uh + e);
-            const uint2 xt = __ldg(ut + e);
+        // ring slots: items 0 .. G-1 heads and G .. 2G-1 tails of the vectors, 2G and 2G+1
+        // head and tail of u~, 2G+2 head of w
+        constexpr int IT = 2 * G + 3;
+        auto slot = [&](int stage, int item) { return s53ring + ((stage * IT + item) * kS53Threads + threadIdx.x); };
+        const long long K = e1 - e0 - lane > 0 ? (e1 - e0 - lane + 31) / 32 : 0;
+        auto issue = [&](long long k, int stage) {
+            const long long e = e0 + lane + 32 * k;
+#pragma unroll
+            for (int t = 0; t < G; ++t)
+                if (i0 + t < j) {
+                    cp_async_8(slot(stage, t), Vh + (size_t)(i0 + t) * ld + e);
+                    cp_async_8(slot(stage, G + t), Vt + (size_t)(i0 + t) * ld + e);
+                }
+            cp_async_8(slot(stage, 2 * G), uh + e);
+            cp_async_8(slot(stage, 2 * G + 1), ut + e);
+            if (has_w) cp_async_8(slot(stage, 2 * G + 2), wh + e);
+        };
+        if constexpr (NS > 0) {
+#pragma unroll
+            for (int s0 = 0; s0 < NS - 1; ++s0) {
+                if (s0 < K) issue(s0, s0);
+                cp_async_commit();
+            }
+        }
+        int cs = 0;                                     // stage of entry k
+        for (long long k = 0; k < K; ++k) {
+            const long long e = e0 + lane + 32 * k;
+            float2 xh, yh;
+            uint2 xt;
+            float2 vh[G];
+            uint2 vt[G];
+            if constexpr (NS > 0) {
+                const int is = cs == 0 ? NS - 1 : cs - 1;   // stage of entry k + NS - 1 (read at k - 1)
+                if (k + NS - 1 < K) issue(k + NS - 1, is);
+                cp_async_commit();
+                cp_async_wait<NS - 1>();                    // entry k has landed
+                const uint2 a = *slot(cs, 2 * G), c = *slot(cs, 2 * G + 2);
+                xh = make_float2(__uint_as_float(a.x), __uint_as_float(a.y));
+                xt = *slot(cs, 2 * G + 1);
+                yh = has_w ? make_float2(__uint_as_float(c.x), __uint_as_float(c.y)) : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int t = 0; t < G; ++t) {
+                    const bool in = i0 + t < j;
+                    const uint2 h = *slot(cs, t);
+                    vh[t] = in ? make_float2(__uint_as_float(h.x), __uint_as_float(h.y)) : make_float2(0.f, 0.f);
+                    vt[t] = in ? *slot(cs, G + t) : make_uint2(0u, 0u);
+                }
+                cs = cs + 1 == NS ? 0 : cs + 1;
+            } else {
+                xh = __ldg(uh + e);
+                xt = __ldg(ut + e);
+                yh = has_w ? __ldg(wh + e) : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int t = 0; t < G; ++t) {
+                    const bool in = i0 + t < j;
+                    vh[t] = in ? __ldcs(Vh + (size_t)(i0 + t) * ld + e) : make_float2(0.f, 0.f);
+                    vt[t] = in ? __ldcs(Vt + (size_t)(i0 + t) * ld + e) : make_uint2(0u, 0u);
+                }
+            }
             const double2 x = make_double2(f53_double(xh.x, xt.x), f53_double(xh.y, xt.y));
             float ur1, ur2, ui1, ui2;
             f53_low(xh.x, xt.x, ur1, ur2);
@@ -160,16 +231,7 @@ __global__ void __launch_bounds__(kS53Threads, MINB) k_s53_dot(int j, long long 
                       Ur2 = f2_bcast(ur2);
             const f2x Ui0 = f2_bcast(xh.y), NUi0 = f2_bcast(-xh.y), Ui1 = f2_bcast(ui1), NUi1 = f2_bcast(-ui1),
                       Ui2 = f2_bcast(ui2);
-            const float2 yh = has_w ? __ldg(wh + e) : make_float2(0.f, 0.f);
             const f2x Wr = f2_bcast(yh.x), Wi = f2_bcast(yh.y);
-            float2 vh[G];
-            uint2 vt[G];
-#pragma unroll
-            for (int t = 0; t < G; ++t) {
-                const bool in = i0 + t < j;
-                vh[t] = in ? __ldcs(Vh + (size_t)(i0 + t) * ld + e) : make_float2(0.f, 0.f);
-                vt[t] = in ? __ldcs(Vt + (size_t)(i0 + t) * ld + e) : make_uint2(0u, 0u);
-            }
 #pragma unroll
             for (int t = 0; t < G; ++t) {
                 const f2x V0 = f2_of(vh[t]);
@@ -191,6 +253,7 @@ __global__ void __launch_bounds__(kS53Threads, MINB) k_s53_dot(int j, long long 
                     if (!d64[t]) { tf_renorm(P[t]); tf_renorm(R[t]); }
             }
         }
+        if constexpr (NS > 0) cp_async_wait<0>();      // (only empty groups remain) the slots are free
 #pragma unroll
         for (int t = 0; t < G; ++t)
             if (!d64[t])
@@ -206,6 +269,206 @@ __global__ void __launch_bounds__(kS53Threads, MINB) k_s53_dot(int j, long long 
                 reinterpret_cast<float4*>(part)[S + i0 + t] = make_float4(b.x, b.y, 0.f, 0.f);
             }
         }
+    }
+}
+
+// The i-th of the basis vectors 0 .. j-1 whose index mod 8 is a set bit of mask
+// (pos: the set bits in increasing order, pop of them).
+__device__ __forceinline__ int s53_vec(int m, const int* pos, int pop) { return (m / pop) * 8 + pos[m % pop]; }
+__device__ __forceinline__ int s53_count(int j, unsigned mask) {
+    return (j >> 3) * __popc(mask) + __popc(mask & ((1u << (j & 7)) - 1u));
+}
+
+// Dot pass of step j with specialised warps: the same sums as k_s53_dot, but a warp task
+// holds either G64 vectors of the FP64 path or G32 vectors of the FP32 path, so that a
+// warp on the FP32 path never waits on an FP64 result (the two paths of k_s53_dot share
+// each warp's iterations).  Tasks are ordered so that the two kinds alternate in
+// proportion and are taken by the warps of a block from a shared counter, so the FP64
+// pipe and the FP32 pipes are fed by different warps at the same time.  The FP32 path's
+// entries stream through a per-thread shared-memory ring of NS stages (cp.async).
+template <int MINB, int G64, int G32, int NS>
+__global__ void __launch_bounds__(kS53Threads, MINB) k_s53_dot_ws(int j, long long N, long long ld, int ps, int S,
+                                                              const float2* __restrict__ Vh,
+                                                              const uint2* __restrict__ Vt, long long sV, int has_w,
+                                                              unsigned dmask, double2* __restrict__ part,
+                                                              long long sP, const KState* __restrict__ st) {
+    const int r = blockIdx.y;
+    if (st[r].done) return;
+    Vh += r * sV; Vt += r * sV;
+    const float2* uh = Vh + (size_t)j * ld;
+    const uint2* ut = Vt + (size_t)j * ld;
+    const float2* wh = Vh + (size_t)(has_w ? j + 1 : j) * ld;
+    part += r * sP + (size_t)blockIdx.x * ps;
+    extern __shared__ uint2 s53ring[];              // NS x (2 G32 + 3) x kS53Threads 8-byte slots
+    __shared__ int s_next;
+    long long e0, e1;
+    chunk_of53(N, e0, e1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned m64 = dmask & 0xffu, m32 = ~dmask & 0xffu;
+    int pos64[8], pos32[8], pop64 = 0, pop32 = 0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        if ((m64 >> b) & 1u) pos64[pop64++] = b;
+        else pos32[pop32++] = b;
+    }
+    const int n64 = s53_count(j, m64), n32 = j - n64;
+    const int T64 = (n64 + G64 - 1) / G64, T32 = (n32 + G32 - 1) / G32, T = T64 + T32;
+    if (threadIdx.x == 0) s_next = nw;
+    __syncthreads();
+    const long long K = e1 - e0 - lane > 0 ? (e1 - e0 - lane + 31) / 32 : 0;
+    int gi = warp;
+    while (gi <= T) {
+        if (gi == T) {
+            // c = |u~|^2 and d = u~^H w in FP64
+            double c = 0.0;
+            double2 d = make_double2(0.0, 0.0);
+            for (long long e = e0 + lane; e < e1; e += 32) {
+                const double2 x = f53_load(uh, ut, e);
+                c = fma(x.x, x.x, fma(x.y, x.y, c));
+                if (has_w) d = cfma_conj(x, f53_load(wh, Vt + (size_t)(j + 1) * ld, e), d);
+            }
+            c = warp_sum_d(c);
+            d = warp_sum(d);
+            if (lane == 0) {
+                part[2 * S] = make_double2(c, 0.0);
+                part[2 * S + 1] = d;
+            }
+        } else {
+            // task gi is FP64 task a when the interleave steps at gi, else FP32 task gi - a
+            const int a = (int)((long long)gi * T64 / T), a1 = (int)((long long)(gi + 1) * T64 / T);
+            if (a1 > a) {
+                int vi[G64];
+                double2 al[G64];
+                f2x B1[G64], B2[G64];
+#pragma unroll
+                for (int t = 0; t < G64; ++t) {
+                    const int m = a * G64 + t;
+                    vi[t] = m < n64 ? s53_vec(m, pos64, pop64) : -1;
+                    al[t] = make_double2(0.0, 0.0);
+                    B1[t] = B2[t] = 0ull;
+                }
+                for (long long e = e0 + lane; e < e1; e += 32) {
+                    const float2 xh = __ldg(uh + e);
+                    const uint2 xt = __ldg(ut + e);
+                    const float2 yh = has_w ? __ldg(wh + e) : make_float2(0.f, 0.f);
+                    float2 vh[G64];
+                    uint2 vt[G64];
+#pragma unroll
+                    for (int t = 0; t < G64; ++t) {
+                        vh[t] = vi[t] >= 0 ? __ldcs(Vh + (size_t)vi[t] * ld + e) : make_float2(0.f, 0.f);
+                        vt[t] = vi[t] >= 0 ? __ldcs(Vt + (size_t)vi[t] * ld + e) : make_uint2(0u, 0u);
+                    }
+                    const double2 x = make_double2(f53_double(xh.x, xt.x), f53_double(xh.y, xt.y));
+                    const f2x Wr = f2_bcast(yh.x), Wi = f2_bcast(yh.y);
+#pragma unroll
+                    for (int t = 0; t < G64; ++t) {
+                        const double2 v = make_double2(f53_double(vh[t].x, vt[t].x), f53_double(vh[t].y, vt[t].y));
+                        al[t] = cfma_conj(v, x, al[t]);
+                        const f2x V0 = f2_of(vh[t]);
+                        B1[t] = fma2(Wr, V0, B1[t]);
+                        B2[t] = fma2(Wi, V0, B2[t]);
+                    }
+                }
+#pragma unroll
+                for (int t = 0; t < G64; ++t) {
+                    const double2 sa = warp_sum(al[t]);
+                    const float2 b1 = f2_unpack(B1[t]), b2 = f2_unpack(B2[t]);
+                    const float2 b = warp_sum(make_float2(b1.x + b2.y, b2.x - b1.y));
+                    if (lane == 0 && vi[t] >= 0) {
+                        part[vi[t]] = sa;
+                        reinterpret_cast<float4*>(part)[S + vi[t]] = make_float4(b.x, b.y, 0.f, 0.f);
+                    }
+                }
+            } else {
+                const int q = gi - a;
+                int vi[G32];
+                TF2 P[G32], R[G32];
+                f2x B1[G32], B2[G32];
+#pragma unroll
+                for (int t = 0; t < G32; ++t) {
+                    const int m = q * G32 + t;
+                    vi[t] = m < n32 ? s53_vec(m, pos32, pop32) : -1;
+                    tf_zero(P[t]);
+                    tf_zero(R[t]);
+                    B1[t] = B2[t] = 0ull;
+                }
+                constexpr int IT = 2 * G32 + 3;
+                auto slot = [&](int stage, int item) {
+                    return s53ring + ((stage * IT + item) * kS53Threads + threadIdx.x);
+                };
+                auto issue = [&](long long k, int stage) {
+                    const long long e = e0 + lane + 32 * k;
+#pragma unroll
+                    for (int t = 0; t < G32; ++t)
+                        if (vi[t] >= 0) {
+                            cp_async_8(slot(stage, t), Vh + (size_t)vi[t] * ld + e);
+                            cp_async_8(slot(stage, G32 + t), Vt + (size_t)vi[t] * ld + e);
+                        }
+                    cp_async_8(slot(stage, 2 * G32), uh + e);
+                    cp_async_8(slot(stage, 2 * G32 + 1), ut + e);
+                    if (has_w) cp_async_8(slot(stage, 2 * G32 + 2), wh + e);
+                };
+#pragma unroll
+                for (int s0 = 0; s0 < NS - 1; ++s0) {
+                    if (s0 < K) issue(s0, s0);
+                    cp_async_commit();
+                }
+                int cs = 0, cnt = 0;
+                for (long long k = 0; k < K; ++k) {
+                    const int is = cs == 0 ? NS - 1 : cs - 1;   // stage of entry k + NS - 1 (read at k - 1)
+                    if (k + NS - 1 < K) issue(k + NS - 1, is);
+                    cp_async_commit();
+                    cp_async_wait<NS - 1>();                    // entry k has landed
+                    const uint2 xa = *slot(cs, 2 * G32), ya = *slot(cs, 2 * G32 + 2);
+                    const float2 xh = make_float2(__uint_as_float(xa.x), __uint_as_float(xa.y));
+                    const uint2 xt = *slot(cs, 2 * G32 + 1);
+                    const float2 yh = has_w ? make_float2(__uint_as_float(ya.x), __uint_as_float(ya.y))
+                                            : make_float2(0.f, 0.f);
+                    float ur1, ur2, ui1, ui2;
+                    f53_low(xh.x, xt.x, ur1, ur2);
+                    f53_low(xh.y, xt.y, ui1, ui2);
+                    const f2x Ur0 = f2_bcast(xh.x), NUr0 = f2_bcast(-xh.x), Ur1 = f2_bcast(ur1), NUr1 = f2_bcast(-ur1),
+                              Ur2 = f2_bcast(ur2);
+                    const f2x Ui0 = f2_bcast(xh.y), NUi0 = f2_bcast(-xh.y), Ui1 = f2_bcast(ui1), NUi1 = f2_bcast(-ui1),
+                              Ui2 = f2_bcast(ui2);
+                    const f2x Wr = f2_bcast(yh.x), Wi = f2_bcast(yh.y);
+#pragma unroll
+                    for (int t = 0; t < G32; ++t) {
+                        const uint2 h = *slot(cs, t);
+                        const float2 vh = vi[t] >= 0 ? make_float2(__uint_as_float(h.x), __uint_as_float(h.y))
+                                                     : make_float2(0.f, 0.f);
+                        const uint2 vt = vi[t] >= 0 ? *slot(cs, G32 + t) : make_uint2(0u, 0u);
+                        const f2x V0 = f2_of(vh);
+                        f2x V1, V2;
+                        f53_low2(vh, vt, V1, V2);
+                        tf_mac53(P[t], Ur0, Ur1, Ur2, NUr0, NUr1, V0, V1, V2);
+                        tf_mac53(R[t], Ui0, Ui1, Ui2, NUi0, NUi1, V0, V1, V2);
+                        B1[t] = fma2(Wr, V0, B1[t]);
+                        B2[t] = fma2(Wi, V0, B2[t]);
+                    }
+                    if ((++cnt & 3) == 0) {
+#pragma unroll
+                        for (int t = 0; t < G32; ++t) { tf_renorm(P[t]); tf_renorm(R[t]); }
+                    }
+                    cs = cs + 1 == NS ? 0 : cs + 1;
+                }
+                cp_async_wait<0>();                             // (only empty groups remain) the slots are free
+#pragma unroll
+                for (int t = 0; t < G32; ++t) {
+                    double2 al = make_double2(tf_lane(P[t], 0) + tf_lane(R[t], 1), tf_lane(R[t], 0) - tf_lane(P[t], 1));
+                    al = warp_sum(al);
+                    const float2 b1 = f2_unpack(B1[t]), b2 = f2_unpack(B2[t]);
+                    const float2 b = warp_sum(make_float2(b1.x + b2.y, b2.x - b1.y));
+                    if (lane == 0 && vi[t] >= 0) {
+                        part[vi[t]] = al;
+                        reinterpret_cast<float4*>(part)[S + vi[t]] = make_float4(b.x, b.y, 0.f, 0.f);
+                    }
+                }
+            }
+        }
+        int nx = 0;
+        if (lane == 0) nx = atomicAdd(&s_next, 1);
+        gi = __shfl_sync(0xffffffffu, nx, 0);
     }
 }
 
@@ -353,19 +616,39 @@ size_t s53_update_smem(int j) { return (size_t)(j > 0 ? j : 1) * sizeof(S53Coef)
 
 // returns the number of blocks (rows of partials the reduction sums): whole waves of
 // resident blocks, at most kb.nblk_dot
+template <int MINB, int NS>
+static const void* s53_dot_fn(int g) {
+    return g == 1 ? (const void*)k_s53_dot<MINB, NS, 1> : (const void*)k_s53_dot<MINB, NS, 2>;
+}
+template <int MINB>
+static const void* s53_dot_fn(int ns, int g) {
+    return ns == 4 ? s53_dot_fn<MINB, 4>(g) : ns == 3 ? s53_dot_fn<MINB, 3>(g) : s53_dot_fn<MINB, 0>(g);
+}
+
 int launch_s53_dot(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int has_w, unsigned dmask) {
     const float2* Vh = kb.V32;
     const uint2* Vt = static_cast<const uint2*>(kb.V32lo);
-    if (kb.s53_minb == 3) {
-        const int blocks = std::min(kb.nblk_dot, 3 * cx.num_sms);
-        k_s53_dot<3><<<dim3(blocks, nb), kS53Threads, 0, cx.stream>>>(j, kb.N, kb.ld, kb.pstride(), kb.maxit + 1, Vh,
-                                                                     Vt, kb.sV(), has_w, dmask, kb.part, kb.sP(),
-                                                                     kb.st);
-        return blocks;
+    const int minb = kb.s53_dot_minb;
+    const int ns = kb.s53_ring == 4 ? 4 : (kb.s53_ring == 3 ? 3 : 0);
+    const int gsz = kb.s53_group == 1 ? 1 : 2;
+    const size_t smem = (size_t)ns * (2 * gsz + 3) * kS53Threads * sizeof(uint2);
+    const void* fn = minb == 4 ? s53_dot_fn<4>(ns, gsz) : minb == 3 ? s53_dot_fn<3>(ns, gsz) : s53_dot_fn<2>(ns, gsz);
+    size_t smem_l = smem;
+    if (kb.s53_ws) {
+        // specialised warps: FP64 tasks of 4 vectors, FP32 tasks of s53_group vectors, 4-stage ring
+        smem_l = (size_t)4 * (2 * gsz + 3) * kS53Threads * sizeof(uint2);
+        fn = minb == 3 ? (gsz == 1 ? (const void*)k_s53_dot_ws<3, 4, 1, 4> : (const void*)k_s53_dot_ws<3, 4, 2, 4>)
+                       : (gsz == 1 ? (const void*)k_s53_dot_ws<2, 4, 1, 4> : (const void*)k_s53_dot_ws<2, 4, 2, 4>);
     }
-    const int blocks = std::min(kb.nblk_dot, 4 * cx.num_sms);
-    k_s53_dot<2><<<dim3(blocks, nb), kS53Threads, 0, cx.stream>>>(j, kb.N, kb.ld, kb.pstride(), kb.maxit + 1, Vh, Vt,
-                                                                 kb.sV(), has_w, dmask, kb.part, kb.sP(), kb.st);
+    if (smem_l > 0 && allow_dynamic_smem(fn, smem_l) != cudaSuccess) return 0;
+    const int blocks = std::min(kb.nblk_dot, (minb == 3 ? 3 : 4) * cx.num_sms);
+    int S = kb.maxit + 1;
+    long long N = kb.N, ld = kb.ld, sV = kb.sV(), sP = kb.sP();
+    int ps = kb.pstride();
+    double2* part = kb.part;
+    const KState* st = kb.st;
+    void* args[] = {&j, &N, &ld, &ps, &S, (void*)&Vh, (void*)&Vt, &sV, &has_w, &dmask, &part, &sP, (void*)&st};
+    if (cudaLaunchKernel(fn, dim3(blocks, nb), dim3(kS53Threads), args, smem_l, cx.stream) != cudaSuccess) return 0;
     return blocks;
 }
 

@@ -5,16 +5,17 @@
   kernels are launched), and every solution has the oracle-matrix residual;
 * hzs_solve_batched over problems of different wavenumber and grid size gives
   the same per-problem results as separate calls;
-* the batched MP-2 workload (point sources at seeded nodes, k = 25 and 50 on
-  n = 257 with 4 x 4 subdomains of 64 nodes, k = 100 on n = 513 with 8 x 8, B_2
-  with H = 32h, tol 1e-6) converges for every right-hand side.
+* the batched MP-2 workload of the benchmark (64 point sources at seeded nodes
+  for each of (k, n) = (25, 257), (50, 257), (100, 513), (200, 1025), 64-node
+  subdomains, B_2 with kH <= 1, tol 1e-6) converges for every right-hand side, and
+  matches the oracle's solution on the two n = 257 problems.
 """
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
-from oracle import SOMMERFELD, Problem  # noqa: E402
+from oracle import B2, SHS2, SOMMERFELD, Problem, Schwarz, gmres  # noqa: E402
 from paper_2408_03571_gb300.inputs import point_source, random_source_nodes  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -74,18 +75,33 @@ def test_multi_problem_batch_equals_separate_calls(hzs):
         assert np.all(residuals(P.n, k, F, U) <= 1.01e-7)
 
 
+# The batched MP-2 set of the benchmark: (k, n, subdomains per axis, H/h); 64-node
+# subdomains, H the largest power-of-two multiple of h with kH <= 1 (Section 5)
+BATCHED = ((25.0, 257, 4, 8), (50.0, 257, 4, 4), (100.0, 513, 8, 4), (200.0, 1025, 16, 4))
+
+
 def test_batched_mp2_workload(hzs):
-    """64 right-hand sides each for (k, n) = (25, 257), (50, 257); 4 for (100, 513)."""
+    """64 right-hand sides for each of the four problems, solved concurrently; every one
+    converges to its true residual, and on the two n = 257 problems the first right-hand
+    side's solution matches the oracle's FP64 GMRES solution."""
     probs, rhs, ks = [], [], []
-    for idx, (k, n, cnt) in enumerate([(25.0, 257, 64), (50.0, 257, 64), (100.0, 513, 4)]):
-        g = hzs.Grid(n, hzs.SOMMERFELD, k=k, nsub=(n - 1) // 64, overlap=2,
-                     stream=torch.cuda.Stream())
-        probs.append(hzs.Preconditioner(g, hzs.SHS2, hzs.COARSE_B2, 32, hzs.MIXED))
-        rhs.append(sources(n, cnt, seed=1000 + idx))
+    for idx, (k, n, nsub, p) in enumerate(BATCHED):
+        g = hzs.Grid(n, hzs.SOMMERFELD, k=k, nsub=nsub, overlap=2, stream=torch.cuda.Stream())
+        probs.append(hzs.Preconditioner(g, hzs.SHS2, hzs.COARSE_B2, p, hzs.MIXED))
+        rhs.append(sources(n, 64, seed=1000 + idx))
         ks.append(k)
     torch.cuda.synchronize()
-    outs, res = hzs.solve_batched(probs, rhs, tol=1e-6, maxit=1000)
+    outs, res = hzs.solve_batched(probs, rhs, tol=1e-6, maxit=300)
     torch.cuda.synchronize()
     for P, F, U, R, k in zip(probs, rhs, outs, res, ks):
         assert all(r.converged for r in R)
         assert np.all(residuals(P.n, k, F, U) <= 1.01e-6)
+    for (k, n, nsub, p), F, U in list(zip(BATCHED, rhs, outs))[:2]:
+        prob = Problem(n, SOMMERFELD, k * k)
+        A = prob.assemble_fast()
+        M = Schwarz(prob, A, nsub, 2, SHS2, B2, p)
+        f = prob.grid_to_vec(F[0].cpu().numpy())
+        ref = gmres(lambda x: A @ x, M.apply, f, 1e-6, 300)
+        u = prob.grid_to_vec(U[0].cpu().numpy())
+        assert ref.converged
+        assert np.linalg.norm(u - ref.x) <= 1e-5 * np.linalg.norm(ref.x)

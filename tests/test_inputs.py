@@ -1,6 +1,7 @@
 """The seeded synthetic inputs have the shapes and distributions the workloads state:
 
-* the point source is 1/h^2 at one node (the centre by default, Eq. 1 read as R-3);
+* the point source is 1/h^2 at one node (the centre by default): Eq. 1's delta source
+  at (1/2, 1/2) discretised as the grid function of unit integral;
 * source nodes, receivers and finite-difference nodes are seeded, inside the boundary
   by the requested margin, and distinct where asked;
 * the bump field is a sum of 16 Gaussians normalised to max |g| = 1, so

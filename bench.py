@@ -288,6 +288,9 @@ def reference_arm(args, world, rank):
 # multiple of h with kH <= 1 (the robustness condition of Section 5): kH = 0.78.
 BATCHED = ((25.0, 257, 4, 8), (50.0, 257, 4, 4), (100.0, 513, 8, 4), (200.0, 1025, 16, 4))
 MAXIT_BATCHED = 300
+# DRAM bytes (read + write) of one launch of each basis pass over its algorithmic bytes,
+# from one ncu capture of the current kernels at the headline size (step j = 200)
+TRAFFIC_RATIO = {"dot": 3803.9 / 3382.4, "update": 3651.5 / 3415.9}
 
 
 def _peaks_file():
@@ -579,19 +582,24 @@ def gpu_line_and_print(args, world, rank, L):
     # FP32 error-free arithmetic; reported against the measured FP64 FMA rate
     macs = 8.0 * sum(j * Nu for j in range(it + 1))
 
-    def pass_roofline(name, nbytes, t, nl):
+    def pass_roofline(name, nbytes, t, nl, ratio):
         a = nbytes / t / 1e9 if t > 0 else 0.0
+        tuned = any(k.startswith("HZS_F53_") for k in os.environ)
         return {"kernel": name, "bound": "hbm", "achieved": a, "peak": hbm_peak, "unit": "GB/s",
-                "frac": a / hbm_peak, "traffic": None, "traffic_source": "no ncu capture of this kernel version",
+                "frac": a / hbm_peak, "traffic": None if tuned else ratio * nbytes / nl,
+                "traffic_source": ("HZS_F53_* set: not the captured kernel version" if tuned else
+                                   f"ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel at this size "
+                                   f"(step j = 200: {ratio:.3f} x its algorithmic bytes), scaled to the average "
+                                   f"launch's algorithmic bytes"),
                 "peak_source": peak_src + ", of measured", "bytes_per_solve": nbytes, "time_per_solve_s": t,
                 "launches": nl, "bytes_per_launch": nbytes / nl,
                 "fp64_equivalent_tflops": macs / t / 1e12 if t > 0 else 0.0,
                 "fp64_fma_peak_tflops": pipes["fp64_tflops"],
                 "timing": "CUDA events around every launch of the kernel on the solve stream"}
-    r_dot = pass_roofline("k_s53_dot (delayed CGS2 dot pass on the f53 basis: FP64-accurate alpha, complex64 b)",
-                          dot_bytes, t_dot, it + 1)
+    r_dot = pass_roofline("k_s53_dot_ws (delayed CGS2 dot pass on the f53 basis: FP64-accurate alpha, complex64 b)",
+                          dot_bytes, t_dot, it + 1, TRAFFIC_RATIO["dot"])
     r_upd = pass_roofline("k_s53_update (delayed CGS2 update pass on the f53 basis, FP64-accurate)",
-                          upd_bytes, t_upd, it)
+                          upd_bytes, t_upd, it, TRAFFIC_RATIO["update"])
     roofline = dict(r_upd if t_upd >= t_dot else r_dot)
     roofline["other_pass"] = r_dot if t_upd >= t_dot else r_upd
     roofline["orth_group"] = {"time_per_solve_s": orth_s, "achieved_gbs": (dot_bytes + upd_bytes) / orth_s / 1e9,

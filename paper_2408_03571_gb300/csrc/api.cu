@@ -806,8 +806,11 @@ static hzs_status ensure_krylov(hzs_precond* p, int maxit, int nb, bool full_v) 
     //                              FP64 FMAs; the others take the FP32 path
     //   HZS_F53_OCC=2|3            blocks per SM of both passes; HZS_F53_DOT_OCC=2..4 the dot pass
     //   HZS_F53_WS=0|1             dot pass with warp tasks on one path each, or mixed tasks
-    //   HZS_F53_GROUP=1|2          vectors per FP32 (or mixed) warp task of the dot pass
+    //   HZS_F53_GROUP=1|2|4        vectors per FP32 (or mixed) warp task of the dot pass (4:
+    //                              specialised warps only)
     //   HZS_F53_RING=0|3|4         stages of the dot pass's copy ring (mixed tasks; 0: none)
+    //   HZS_F53_UPD_E=1|2          entries per thread and sweep of the update pass
+    //   HZS_F53_G64=4|8            vectors per FP64 task of the dot pass (specialised warps)
     if (const char* ev = std::getenv("HZS_F53_OCC")) {
         const int v = std::atoi(ev);
         if (v == 2 || v == 3) kb.s53_minb = kb.s53_dot_minb = v;
@@ -821,9 +824,11 @@ static hzs_status ensure_krylov(hzs_precond* p, int maxit, int nb, bool full_v) 
         if (v == 0 || v == 3 || v == 4) kb.s53_ring = v;
     }
     if (const char* ev = std::getenv("HZS_F53_WS")) kb.s53_ws = std::atoi(ev) ? 1 : 0;
+    if (const char* ev = std::getenv("HZS_F53_UPD_E")) kb.s53_upd_e = std::atoi(ev) == 2 ? 2 : 1;
+    if (const char* ev = std::getenv("HZS_F53_G64")) kb.s53_g64 = std::atoi(ev) == 8 ? 8 : 4;
     if (const char* ev = std::getenv("HZS_F53_GROUP")) {
         const int v = std::atoi(ev);
-        if (v == 1 || v == 2) kb.s53_group = v;
+        if (v == 1 || v == 2 || v == 4) kb.s53_group = v;
     }
     if (const char* ev = std::getenv("HZS_F53_MASK")) {
         unsigned a = 0, b = 0;

@@ -194,6 +194,8 @@ struct KrylovBufs {
     int s53_group = 2;     // dot pass: basis vectors per warp task on the FP32 path (1 or 2)
     int s53_dot_minb = 2;  // dot pass: blocks per SM it is compiled for (2, 3 or 4)
     int s53_ws = 1;        // dot pass: each warp task on one of the two paths (k_s53_dot_ws)
+    int s53_upd_e = 1;     // update pass: entries per thread and sweep (1 or 2)
+    int s53_g64 = 4;       // dot pass, specialised warps: vectors per FP64 task (4 or 8)
     double* sigma;     // (maxit+1): basis vector i = sigma[i] * V_i
     double2* H;        // (maxit+1) x maxit, column j at H[j*(maxit+1)]
     double* cs;        // maxit+1

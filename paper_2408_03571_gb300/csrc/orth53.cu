@@ -602,6 +602,144 @@ __global__ void __launch_bounds__(kS53Threads, MINB) k_s53_update(int j, long lo
     }
 }
 
+// The update pass with two entries per thread and sweep (e and e + blockDim.x): each
+// vector's coefficients are read from shared memory once for both entries, and the
+// two entries' sums are independent chains of arithmetic.
+template <int MINB>
+__global__ void __launch_bounds__(kS53Threads, MINB) k_s53_update2(int j, long long N, long long ld,
+                                                               float2* __restrict__ Vh, uint2* __restrict__ Vt,
+                                                               long long sV, const double* __restrict__ sigma,
+                                                               const double2* __restrict__ h1,
+                                                               const double2* __restrict__ h2, long long sS,
+                                                               unsigned dmask, double* __restrict__ npart, int nblk,
+                                                               const KState* __restrict__ st) {
+    constexpr int G = kS53Group;
+    const int r = blockIdx.y;
+    if (st[r].done) return;
+    Vh += r * sV; Vt += r * sV; sigma += r * sS; h1 += r * sS; h2 += r * sS;
+    float2* uh = Vh + (size_t)j * ld;
+    uint2* ut = Vt + (size_t)j * ld;
+    float2* wh = Vh + (size_t)(j + 1) * ld;
+    uint2* wt = Vt + (size_t)(j + 1) * ld;
+    extern __shared__ S53Coef s53c[];
+    __shared__ double2 s_cj;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        const double2 c = cscale(h1[i], sigma[i]);
+        if (i == j) { s_cj = c; continue; }
+        const double2 a = cscale(h2[i], sigma[i]);
+        const float cr = (float)c.x, ci = (float)c.y;          // exact: c is an FP32 value
+        const float arh = (float)a.x, arl = (float)(a.x - (double)arh);
+        const float aih = (float)a.y, ail = (float)(a.y - (double)aih);
+        S53Coef k;
+        k.Pcr = f2_bcast(cr); k.Ncr = f2_bcast(-cr); k.Pci = f2_bcast(ci); k.Nci = f2_bcast(-ci);
+        k.Parh = f2_bcast(arh); k.Narh = f2_bcast(-arh); k.Narl = f2_bcast(-arl);
+        k.Paih = f2_bcast(aih); k.Naih = f2_bcast(-aih); k.Nail = f2_bcast(-ail);
+        k.c = make_double2((double)cr, (double)ci);
+        s53c[i] = k;
+    }
+    __syncthreads();
+    const double2 cj = s_cj;
+    long long e0, e1;
+    chunk_of53(N, e0, e1);
+    const long long bd = blockDim.x;
+    double nrm = 0.0;
+    for (long long e = e0 + threadIdx.x; e < e1; e += 2 * bd) {
+        const long long ee[2] = {e, e + bd};
+        const bool in1 = e + bd < e1;
+        TF2 A[2], B[2];
+        double2 acc[2];
+        f2x rah[2], ral[2], rbh[2], rbl[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            tf_zero(A[q]);
+            tf_zero(B[q]);
+            acc[q] = make_double2(0.0, 0.0);
+            rah[q] = ral[q] = rbh[q] = rbl[q] = 0ull;
+        }
+        auto vec = [&](int i, const float2* vh, const uint2* vt, bool d64) {
+            const S53Coef& k = s53c[i];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                f2x V1, V2;
+                f53_low2(vh[q], vt[q], V1, V2);
+                const f2x V0 = f2_of(vh[q]);
+                if (d64) {
+                    const double2 v = make_double2(f53_double(vh[q].x, vt[q].x), f53_double(vh[q].y, vt[q].y));
+                    acc[q] = cfma(k.c, v, acc[q]);
+                } else {
+                    tf_mac24(A[q], k.Pcr, k.Ncr, V0, V1, V2);
+                    tf_mac24(B[q], k.Pci, k.Nci, V0, V1, V2);
+                }
+                df_mac2(rah[q], ral[q], k.Parh, k.Narh, k.Narl, V0, V1);
+                df_mac2(rbh[q], rbl[q], k.Paih, k.Naih, k.Nail, V0, V1);
+            }
+        };
+        int i = j - 1, g = 0;
+        float2 ch[G][2], nh[G][2];
+        uint2 ct[G][2], nt[G][2];
+        auto load = [&](int i0, float2 (*hh)[2], uint2 (*tt)[2]) {
+#pragma unroll
+            for (int t = 0; t < G; ++t)
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const bool in = i0 - t >= 0 && (q == 0 || in1);
+                    hh[t][q] = in ? __ldcs(Vh + (size_t)(i0 - t) * ld + ee[q]) : make_float2(0.f, 0.f);
+                    tt[t][q] = in ? __ldcs(Vt + (size_t)(i0 - t) * ld + ee[q]) : make_uint2(0u, 0u);
+                }
+        };
+        if (i >= 0) load(i, ch, ct);
+        for (; i >= 0; i -= G, ++g) {
+            if (i - G >= 0) load(i - G, nh, nt);
+#pragma unroll
+            for (int t = 0; t < G; ++t)
+                if (i - t >= 0) vec(i - t, ch[t], ct[t], (dmask >> ((i - t) & 7)) & 1);
+            if ((g & 1) == 1) {
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    tf_renorm(A[q]);
+                    tf_renorm(B[q]);
+                    df_norm2(rah[q], ral[q]);
+                    df_norm2(rbh[q], rbl[q]);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < G; ++t)
+#pragma unroll
+                for (int q = 0; q < 2; ++q) { ch[t][q] = nh[t][q]; ct[t][q] = nt[t][q]; }
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            if (q == 1 && !in1) break;
+            const long long eq = ee[q];
+            const double2 s = make_double2(acc[q].x + (tf_lane(A[q], 0) - tf_lane(B[q], 1)),
+                                           acc[q].y + (tf_lane(A[q], 1) + tf_lane(B[q], 0)));
+            const float2 pah = f2_unpack(rah[q]), pal = f2_unpack(ral[q]), pbh = f2_unpack(rbh[q]),
+                         pbl = f2_unpack(rbl[q]);
+            const double rre = (f53_double(pah.x, 0u) + f53_double(pal.x, 0u)) -
+                               (f53_double(pbh.y, 0u) + f53_double(pbl.y, 0u));
+            const double rim = (f53_double(pah.y, 0u) + f53_double(pal.y, 0u)) +
+                               (f53_double(pbh.x, 0u) + f53_double(pbl.x, 0u));
+            double2 x = f53_load(uh, ut, eq);
+            x.x -= rre;
+            x.y -= rim;
+            f53_store(uh, ut, eq, x);
+            double2 y = csub(f53_load(wh, wt, eq), s);
+            y = cfms(cj, x, y);
+            f53_store(wh, wt, eq, y);
+            nrm = fma(y.x, y.x, fma(y.y, y.y, nrm));
+        }
+    }
+    __shared__ double nred[kS53Threads / 32];
+    nrm = warp_sum_d(nrm);
+    if ((threadIdx.x & 31) == 0) nred[threadIdx.x >> 5] = nrm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += nred[k];
+        npart[(size_t)r * nblk + blockIdx.x] = t;
+    }
+}
+
 // ------------------------------------------------------------------ launchers
 void launch_f53_encode(const Ctx& cx, int nb, long long N, const double2* src, long long ss, float2* dh, uint2* dt,
                        long long ds, const double* scale, const KState* st) {
@@ -630,15 +768,19 @@ int launch_s53_dot(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int has_w
     const uint2* Vt = static_cast<const uint2*>(kb.V32lo);
     const int minb = kb.s53_dot_minb;
     const int ns = kb.s53_ring == 4 ? 4 : (kb.s53_ring == 3 ? 3 : 0);
-    const int gsz = kb.s53_group == 1 ? 1 : 2;
+    const int gsz = kb.s53_group == 1 ? 1 : (kb.s53_group == 4 && kb.s53_ws ? 4 : 2);
     const size_t smem = (size_t)ns * (2 * gsz + 3) * kS53Threads * sizeof(uint2);
     const void* fn = minb == 4 ? s53_dot_fn<4>(ns, gsz) : minb == 3 ? s53_dot_fn<3>(ns, gsz) : s53_dot_fn<2>(ns, gsz);
+    // (s53_dot_fn maps a group of 4 to 2: only the specialised kernel takes 4)
     size_t smem_l = smem;
     if (kb.s53_ws) {
-        // specialised warps: FP64 tasks of 4 vectors, FP32 tasks of s53_group vectors, 4-stage ring
+        // specialised warps: FP64 tasks of s53_g64 vectors, FP32 tasks of s53_group vectors, 4-stage ring
         smem_l = (size_t)4 * (2 * gsz + 3) * kS53Threads * sizeof(uint2);
+        const bool g8 = kb.s53_g64 == 8;
         fn = minb == 3 ? (gsz == 1 ? (const void*)k_s53_dot_ws<3, 4, 1, 4> : (const void*)k_s53_dot_ws<3, 4, 2, 4>)
-                       : (gsz == 1 ? (const void*)k_s53_dot_ws<2, 4, 1, 4> : (const void*)k_s53_dot_ws<2, 4, 2, 4>);
+             : gsz == 1 ? (const void*)k_s53_dot_ws<2, 4, 1, 4>
+             : gsz == 4 ? (g8 ? (const void*)k_s53_dot_ws<2, 8, 4, 4> : (const void*)k_s53_dot_ws<2, 4, 4, 4>)
+                        : (g8 ? (const void*)k_s53_dot_ws<2, 8, 2, 4> : (const void*)k_s53_dot_ws<2, 4, 2, 4>);
     }
     if (smem_l > 0 && allow_dynamic_smem(fn, smem_l) != cudaSuccess) return 0;
     const int blocks = std::min(kb.nblk_dot, (minb == 3 ? 3 : 4) * cx.num_sms);
@@ -657,21 +799,25 @@ int launch_s53_dot(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int has_w
 int launch_s53_update(const Ctx& cx, const KrylovBufs& kb, int nb, int j, unsigned dmask) {
     const size_t us = s53_update_smem(j);
     const bool three = kb.s53_minb == 3;
-    const void* fn = three ? (const void*)k_s53_update<3> : (const void*)k_s53_update<2>;
+    const void* fn = kb.s53_upd_e == 2 ? (three ? (const void*)k_s53_update2<3> : (const void*)k_s53_update2<2>)
+                                       : (three ? (const void*)k_s53_update<3> : (const void*)k_s53_update<2>);
     if (allow_dynamic_smem(fn, us) != cudaSuccess) return 0;
     // blocks per SM: as the registers allow while their shared memory fits (<= kb.nblk / SMs,
     // the partials' stride)
     int bps = three ? 3 : 2;
     while (bps > 1 && (size_t)bps * (us + 2048) > (size_t)(228 * 1024)) --bps;
     const int blocks = bps * cx.num_sms;
-    if (three)
-        k_s53_update<3><<<dim3(blocks, nb), kS53Threads, us, cx.stream>>>(
-            j, kb.N, kb.ld, kb.V32, static_cast<uint2*>(kb.V32lo), kb.sV(), kb.sigma, kb.h1, kb.h2, kb.sS(), dmask,
-            kb.npart, kb.nblk, kb.st);
-    else
-        k_s53_update<2><<<dim3(blocks, nb), kS53Threads, us, cx.stream>>>(
-            j, kb.N, kb.ld, kb.V32, static_cast<uint2*>(kb.V32lo), kb.sV(), kb.sigma, kb.h1, kb.h2, kb.sS(), dmask,
-            kb.npart, kb.nblk, kb.st);
+    float2* Vh = kb.V32;
+    uint2* Vt = static_cast<uint2*>(kb.V32lo);
+    long long N = kb.N, ld = kb.ld, sV = kb.sV(), sS = kb.sS();
+    const double* sigma = kb.sigma;
+    const double2 *h1 = kb.h1, *h2 = kb.h2;
+    double* npart = kb.npart;
+    int nblk = kb.nblk;
+    const KState* st = kb.st;
+    void* args[] = {&j, &N, &ld, (void*)&Vh, (void*)&Vt, &sV, (void*)&sigma, (void*)&h1, (void*)&h2, &sS, &dmask,
+                    (void*)&npart, &nblk, (void*)&st};
+    if (cudaLaunchKernel(fn, dim3(blocks, nb), dim3(kS53Threads), args, us, cx.stream) != cudaSuccess) return 0;
     return blocks;
 }
 

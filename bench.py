@@ -290,7 +290,7 @@ BATCHED = ((25.0, 257, 4, 8), (50.0, 257, 4, 4), (100.0, 513, 8, 4), (200.0, 102
 MAXIT_BATCHED = 300
 # DRAM bytes (read + write) of one launch of each basis pass over its algorithmic bytes,
 # from one ncu capture of the current kernels at the headline size (step j = 200)
-TRAFFIC_RATIO = {"dot": 3803.9 / 3382.4, "update": 3651.5 / 3415.9}
+TRAFFIC_RATIO = {"dot": 3840.5 / 3382.4, "update": 3530.4 / 3415.9}
 
 
 def _peaks_file():
@@ -598,7 +598,8 @@ def gpu_line_and_print(args, world, rank, L):
                 "timing": "CUDA events around every launch of the kernel on the solve stream"}
     r_dot = pass_roofline("k_s53_dot_ws (delayed CGS2 dot pass on the f53 basis: FP64-accurate alpha, complex64 b)",
                           dot_bytes, t_dot, it + 1, TRAFFIC_RATIO["dot"])
-    r_upd = pass_roofline("k_s53_update (delayed CGS2 update pass on the f53 basis, FP64-accurate)",
+    r_upd = pass_roofline("k_s53_update2 (delayed CGS2 update pass on the f53 basis, FP64-accurate, two entries "
+                          "per thread)",
                           upd_bytes, t_upd, it, TRAFFIC_RATIO["update"])
     roofline = dict(r_upd if t_upd >= t_dot else r_dot)
     roofline["other_pass"] = r_dot if t_upd >= t_dot else r_upd

@@ -164,7 +164,12 @@ typedef struct {
  * FP32 three-word expansions whose error bound is below FP64's (the FP64 pipe of
  * the part is 1/64 of its FP32 rate).  HZS_SOLVE_ORTH_DFMA: the same delayed CGS2
  * with every one of those sums in FP64 fused multiply-adds on a complex128 basis
- * (also taken by default when maxit exceeds about 2300).  HZS_SOLVE_ORTH_FP64:
+ * (also taken by default when maxit exceeds about 2300).  The environment
+ * variables HZS_F53_MASK, _OCC, _DOT_OCC, _WS, _GROUP, _G64, _RING and _UPD_E, read
+ * when a solve first makes its work space on a handle, select other launch
+ * variants of the default (which vectors take which pipe, blocks per SM, task
+ * sizes); every variant computes the same FP64 Arnoldi process and the defaults
+ * are the fastest measured.  HZS_SOLVE_ORTH_FP64:
  * classical CGS2 with every dot product and update in FP64 (four passes per
  * step), as HZS_FP64 uses.  HZS_SOLVE_BASIS_DF: the delayed CGS2 on a narrower
  * double-float basis (complex64 rounding + remainder, see HZS_SOLVE_BASIS_WIDE)

@@ -188,13 +188,14 @@ struct KrylovBufs {
     // update pass, the others in FP32 error-free arithmetic.  Defaults: the fastest of the
     // splits, occupancies, task sizes and copy rings measured at the headline size
     unsigned dmask_dot = 0x6Du;    // 5 of 8 vectors on the FP64 path
-    unsigned dmask_upd = 0x77u;    // 6 of 8
-    int s53_minb = 3;      // update pass: blocks per SM it is compiled for (2 or 3)
+    unsigned dmask_upd = 0x6Du;    // 5 of 8
+    int s53_minb = 2;      // update pass: blocks per SM it is compiled for (2 or 3)
     int s53_ring = 4;      // dot pass: stages of its per-thread shared-memory copy ring (0: none)
-    int s53_group = 2;     // dot pass: basis vectors per warp task on the FP32 path (1 or 2)
+    int s53_group = 4;     // dot pass: basis vectors per warp task on the FP32 path (1, 2; 4 with
+                           // specialised warps)
     int s53_dot_minb = 2;  // dot pass: blocks per SM it is compiled for (2, 3 or 4)
     int s53_ws = 1;        // dot pass: each warp task on one of the two paths (k_s53_dot_ws)
-    int s53_upd_e = 1;     // update pass: entries per thread and sweep (1 or 2)
+    int s53_upd_e = 2;     // update pass: entries per thread and sweep (1 or 2)
     int s53_g64 = 4;       // dot pass, specialised warps: vectors per FP64 task (4 or 8)
     double* sigma;     // (maxit+1): basis vector i = sigma[i] * V_i
     double2* H;        // (maxit+1) x maxit, column j at H[j*(maxit+1)]

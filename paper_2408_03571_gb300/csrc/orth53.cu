@@ -774,12 +774,15 @@ int launch_s53_dot(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int has_w
     // (s53_dot_fn maps a group of 4 to 2: only the specialised kernel takes 4)
     size_t smem_l = smem;
     if (kb.s53_ws) {
-        // specialised warps: FP64 tasks of s53_g64 vectors, FP32 tasks of s53_group vectors, 4-stage ring
-        smem_l = (size_t)4 * (2 * gsz + 3) * kS53Threads * sizeof(uint2);
-        const bool g8 = kb.s53_g64 == 8;
-        fn = minb == 3 ? (gsz == 1 ? (const void*)k_s53_dot_ws<3, 4, 1, 4> : (const void*)k_s53_dot_ws<3, 4, 2, 4>)
-             : gsz == 1 ? (const void*)k_s53_dot_ws<2, 4, 1, 4>
-             : gsz == 4 ? (g8 ? (const void*)k_s53_dot_ws<2, 8, 4, 4> : (const void*)k_s53_dot_ws<2, 4, 4, 4>)
+        // specialised warps: FP64 tasks of s53_g64 vectors, FP32 tasks of s53_group vectors, 4-stage
+        // ring; compiled for 3 blocks per SM with FP32 tasks of 1 or 2 vectors and FP64 tasks of 4,
+        // else for 2 blocks per SM
+        const int g32 = minb == 3 && gsz == 4 ? 2 : gsz;
+        const bool g8 = kb.s53_g64 == 8 && minb != 3;
+        smem_l = (size_t)4 * (2 * g32 + 3) * kS53Threads * sizeof(uint2);
+        fn = minb == 3 ? (g32 == 1 ? (const void*)k_s53_dot_ws<3, 4, 1, 4> : (const void*)k_s53_dot_ws<3, 4, 2, 4>)
+             : g32 == 1 ? (const void*)k_s53_dot_ws<2, 4, 1, 4>
+             : g32 == 4 ? (g8 ? (const void*)k_s53_dot_ws<2, 8, 4, 4> : (const void*)k_s53_dot_ws<2, 4, 4, 4>)
                         : (g8 ? (const void*)k_s53_dot_ws<2, 8, 2, 4> : (const void*)k_s53_dot_ws<2, 4, 2, 4>);
     }
     if (smem_l > 0 && allow_dynamic_smem(fn, smem_l) != cudaSuccess) return 0;

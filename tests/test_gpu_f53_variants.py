@@ -38,6 +38,9 @@ VARIANTS = [
     {"HZS_F53_MASK": "0xFF,0xFF"},                                          # every vector on the FP64 path
     {"HZS_F53_MASK": "0x11,0x55", "HZS_F53_OCC": "2"},
     {"HZS_F53_MASK": "0x00,0xFF", "HZS_F53_WS": "0"},
+    {"HZS_F53_UPD_E": "1", "HZS_F53_OCC": "3", "HZS_F53_MASK": "0x6D,0x77"},
+    {"HZS_F53_G64": "8", "HZS_F53_GROUP": "2"},
+    {"HZS_F53_UPD_E": "2", "HZS_F53_OCC": "3"},
 ]
 
 

@@ -216,9 +216,11 @@ def oracle_sample(prob, A, M, f, steps: int, iterations: int):
     """A bounded sample of the oracle on the full workload: ``steps`` Arnoldi steps of its
     GMRES (set-up done before), plus the measured cost of the preconditioner and operator
     and of one Gram-Schmidt projection on basis vectors that are not cache-resident.  The
-    per-solve time at ``iterations`` steps is extrapolated from those two costs (the
-    orthogonalisation grows linearly with the step) and corrected by the ratio of the
-    sample's measured run to the same model at ``steps`` steps."""
+    per-solve time at ``iterations`` steps is modelled from those two costs (the
+    orthogonalisation grows linearly with the step): it * t_pm + t_proj * it (it + 1) / 2.
+    The model is checked against one complete oracle solve of this workload (the GPU
+    arm's cpu_baseline: 355 steps in 232 s measured, 236 s modelled); the sample run's
+    own time is reported beside it."""
     import numpy as np
 
     from oracle import gmres
@@ -238,10 +240,9 @@ def oracle_sample(prob, A, M, f, steps: int, iterations: int):
     res = gmres(lambda x: A @ x, M.apply, f, TOL, steps)
     t_run = time.perf_counter() - t0
     model = lambda it: it * t_pm + t_proj * it * (it + 1) / 2
-    corr = t_run / model(res.iterations)
     return {"t_precond_plus_operator_s": t_pm, "t_projection_s": t_proj, "t_sample_run_s": t_run,
-            "sample_steps": res.iterations, "model_correction": corr, "iterations_assumed": iterations,
-            "t_solve_extrapolated_s": corr * model(iterations)}
+            "sample_steps": res.iterations, "sample_modelled_s": model(res.iterations),
+            "iterations_assumed": iterations, "t_solve_extrapolated_s": model(iterations)}
 
 
 def basis_dtype(bits: int, kind: int) -> str:
@@ -259,7 +260,7 @@ def reference_arm(args, world, rank):
     # one core, as stated in the line (the numerical libraries are loaded after this)
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[var] = "1"
-    iters_assumed = 373   # the mixed GPU solve's iteration count at this workload (measured)
+    iters_assumed = 355   # the oracle's own step count for this workload (its full solve, measured)
     prob, A, M, f, t_setup = _oracle_setup()
     for _ in range(min(args.warmup, 1)):
         A @ M.apply(f)
@@ -271,7 +272,8 @@ def reference_arm(args, world, rank):
     v = statistics.median(1.0 / s["t_solve_extrapolated_s"] for s in samples)
     sample = (f"per step: {args.cpu_steps} GMRES steps of the FP64 oracle (numpy/scipy, one core) at the full "
               f"workload plus its measured per-step preconditioner+operator and per-projection costs; "
-              f"value = one solve of {iters_assumed} steps extrapolated from them (set-up {t_setup:.1f} s, once)")
+              f"value = one solve of the oracle's {iters_assumed} steps modelled from them (set-up {t_setup:.1f} s, "
+              f"once; the model is within 2 % of a complete oracle solve timed on the same host)")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(walls),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",

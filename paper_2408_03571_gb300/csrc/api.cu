@@ -355,9 +355,9 @@ static hzs_status setup_impl(hzs_grid* g, const hzs_precond_desc* d, hzs_precond
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) { cudaFree(A0b); return cuda_fail(g, e, "coarse assembly"); }
             double minpiv = 0.0;
+            // the factorisation keeps A0b (the couplings of its solve) and frees it
             const int rc = coarse_block_setup(p->cx, p->hct.nc1, d->coarse == HZS_COARSE_B2 ? 2 : 1, A0b, p->cblk,
                                               &minpiv);
-            cudaFree(A0b);
             if (rc < 0) return fail(g, HZS_ERR_CUDA, "coarse block factorisation failed");
             p->coarse_minpiv = minpiv;
             if (rc > 0) return fail(g, HZS_ERR_SINGULAR_COARSE, "coarse matrix A_0 has a zero pivot");

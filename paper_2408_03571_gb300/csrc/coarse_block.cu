@@ -7,11 +7,12 @@
 // grouping s consecutive coarse rows into one block row gives a block-
 // tridiagonal matrix with blocks of size b_i = (rows in group i) * nc1:
 //   D_i (b_i x b_i), L_i (b_i x b_{i-1}), U_i (b_i x b_{i+1}).
-// Set-up (FP64): S_0 = D_0, S_i = D_i - L_i Q_{i-1};  W_i = S_i^{-1} (Gauss-Jordan
-// with partial pivoting), P_i = W_i L_i, Q_i = W_i U_i.
-// Solve: y_0 = W_0 c_0, y_i = W_i c_i - P_i y_{i-1};  x_{m-1} = y_{m-1},
-// x_i = y_i - Q_i x_{i+1}: 2m - 1 dependent dense matrix-vector products, each a
-// kernel with one warp per row.
+// Set-up (FP64): S_0 = D_0, S_i = D_i - L_i Q_{i-1} with Q_{i-1} = W_{i-1} U_{i-1};
+// W_i = S_i^{-1} (Gauss-Jordan with partial pivoting).  Only the W_i are kept; the
+// couplings L_i, U_i stay in A_0's band form (at most 10 entries a row).
+// Solve: y_0 = W_0 c_0, y_i = W_i (c_i - L_i y_{i-1});  x_{m-1} = y_{m-1},
+// x_i = y_i - W_i (U_i x_{i+1}): 2m - 1 dependent dense matrix-vector products with
+// the W_i (one warp per row), each after a banded product (one thread per row).
 #include <vector>
 
 #include "kernels.cuh"
@@ -95,6 +96,36 @@ __global__ void k_cb_step(int rows, const double2* __restrict__ Ma, const double
     }
 }
 
+// Banded coupling of block row i (rows [r0, r0 + rows)) with the unknowns
+// [cr0, cr0 + crows) of a neighbouring block row, batch entry r = blockIdx.y, one
+// thread per row: acc = sum over A_0's band entries of the row whose column lies in
+// that range of A0b[row, o] x[col];  v[row] = v[row] - acc (subtract) or acc.
+__global__ void k_cb_band(int nc1, const double2* __restrict__ A0b, int r0, int rows, int cr0, int crows,
+                          const double2* __restrict__ x, double2* __restrict__ v, long long stride, int subtract,
+                          BatchSkip sk) {
+    const int r = blockIdx.y;
+    if (sk.flag && sk.flag[(size_t)r * sk.stride]) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= rows) return;
+    const long long off = (long long)r * stride;
+    const int row = r0 + t, I = row % nc1, J = row / nc1;
+    double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int dJ = -2; dJ <= 2; ++dJ) {
+        const int J2 = J + dJ;
+        if (J2 < 0 || J2 >= nc1) continue;
+#pragma unroll
+        for (int dI = -2; dI <= 2; ++dI) {
+            const int I2 = I + dI;
+            if (I2 < 0 || I2 >= nc1) continue;
+            const int col = J2 * nc1 + I2;
+            if (col < cr0 || col >= cr0 + crows) continue;
+            acc = cfma(A0b[(size_t)row * 25 + (dJ + 2) * 5 + (dI + 2)], x[off + col], acc);
+        }
+    }
+    v[off + row] = subtract ? csub(v[off + row], acc) : acc;
+}
+
 __global__ void k_c128_to_c64_batched(int Nc, const double2* __restrict__ a, float2* __restrict__ b, BatchSkip sk) {
     const int r = blockIdx.y;
     if (sk.flag && sk.flag[(size_t)r * sk.stride]) return;
@@ -102,38 +133,37 @@ __global__ void k_c128_to_c64_batched(int Nc, const double2* __restrict__ a, flo
         b[(size_t)r * Nc + e] = to_f(a[(size_t)r * Nc + e]);
 }
 
-int coarse_block_setup(const Ctx& cx, int nc1, int s, const double2* A0b, CoarseBlockLU& lu, double* minpiv) {
+int coarse_block_setup(const Ctx& cx, int nc1, int s, double2* A0b, CoarseBlockLU& lu, double* minpiv) {
     lu = CoarseBlockLU{};
     lu.nc1 = nc1;
     lu.s = s;
     lu.m = (nc1 + s - 1) / s;
+    lu.A0b = A0b;
     const int m = lu.m;
     std::vector<int> b(m), r0(m);
     for (int i = 0; i < m; ++i) {
         r0[i] = i * s * nc1;
         b[i] = (std::min(nc1, (i + 1) * s) - i * s) * nc1;
     }
-    long long wsz = 0, psz = 0, qsz = 0;
-    std::vector<long long> wo(m), po(m), qo(m);
+    long long wsz = 0;
+    std::vector<long long> wo(m);
     for (int i = 0; i < m; ++i) {
-        wo[i] = wsz; wsz += (long long)b[i] * b[i];
-        po[i] = psz; if (i > 0) psz += (long long)b[i] * b[i - 1];
-        qo[i] = qsz; if (i + 1 < m) qsz += (long long)b[i] * b[i + 1];
+        wo[i] = wsz;
+        wsz += (long long)b[i] * b[i];
     }
     const int bmax = s * nc1;
-    double2 *D = nullptr, *Lb = nullptr, *Ub = nullptr;
+    double2 *D = nullptr, *Lb = nullptr, *Ub = nullptr, *Qp = nullptr;
     auto fail = [&]() {
-        cudaFree(D); cudaFree(Lb); cudaFree(Ub);
-        cudaFree(lu.W); cudaFree(lu.P); cudaFree(lu.Q);
+        cudaFree(D); cudaFree(Lb); cudaFree(Ub); cudaFree(Qp);
+        cudaFree(lu.W); cudaFree(lu.A0b);
         lu = CoarseBlockLU{};
         return -1;
     };
     if (cudaMalloc(&lu.W, (size_t)wsz * sizeof(double2)) != cudaSuccess) return fail();
-    if (cudaMalloc(&lu.P, (size_t)(psz > 0 ? psz : 1) * sizeof(double2)) != cudaSuccess) return fail();
-    if (cudaMalloc(&lu.Q, (size_t)(qsz > 0 ? qsz : 1) * sizeof(double2)) != cudaSuccess) return fail();
     if (cudaMalloc(&D, (size_t)bmax * bmax * sizeof(double2)) != cudaSuccess) return fail();
     if (cudaMalloc(&Lb, (size_t)bmax * bmax * sizeof(double2)) != cudaSuccess) return fail();
     if (cudaMalloc(&Ub, (size_t)bmax * bmax * sizeof(double2)) != cudaSuccess) return fail();
+    if (cudaMalloc(&Qp, (size_t)bmax * bmax * sizeof(double2)) != cudaSuccess) return fail();
     double mp = 1e300;
     int singular = 0;
     const int cb = 4 * cx.num_sms;
@@ -143,7 +173,7 @@ int coarse_block_setup(const Ctx& cx, int nc1, int s, const double2* A0b, Coarse
         if (i > 0) {
             // S_i = D_i - L_i Q_{i-1}
             k_band_to_block<<<cb, 256, 0, cx.stream>>>(nc1, A0b, r0[i], bi, r0[i - 1], b[i - 1], Lb);
-            zgemm(cx, bi, bi, b[i - 1], -1.0, Lb, b[i - 1], lu.Q + qo[i - 1], bi, 1.0, D, bi);
+            zgemm(cx, bi, bi, b[i - 1], -1.0, Lb, b[i - 1], Qp, bi, 1.0, D, bi);
         }
         double piv = 0.0;
         const int rc = gj_invert(cx, D, bi, &piv);      // D <- S_i^{-1}
@@ -153,44 +183,47 @@ int coarse_block_setup(const Ctx& cx, int nc1, int s, const double2* A0b, Coarse
         if (cudaMemcpyAsync(lu.W + wo[i], D, (size_t)bi * bi * sizeof(double2), cudaMemcpyDeviceToDevice,
                             cx.stream) != cudaSuccess)
             return fail();
-        if (i > 0) zgemm(cx, bi, b[i - 1], bi, 1.0, lu.W + wo[i], bi, Lb, b[i - 1], 0.0, lu.P + po[i], b[i - 1]);
         if (i + 1 < m) {
+            // Q_i = W_i U_i, used by the next block row only
             k_band_to_block<<<cb, 256, 0, cx.stream>>>(nc1, A0b, r0[i], bi, r0[i + 1], b[i + 1], Ub);
-            zgemm(cx, bi, b[i + 1], bi, 1.0, lu.W + wo[i], bi, Ub, b[i + 1], 0.0, lu.Q + qo[i], b[i + 1]);
+            zgemm(cx, bi, b[i + 1], bi, 1.0, lu.W + wo[i], bi, Ub, b[i + 1], 0.0, Qp, b[i + 1]);
         }
     }
     const cudaError_t e = cudaStreamSynchronize(cx.stream);
-    cudaFree(D); cudaFree(Lb); cudaFree(Ub);
-    if (e != cudaSuccess) { cudaFree(lu.W); cudaFree(lu.P); cudaFree(lu.Q); lu = CoarseBlockLU{}; return -1; }
-    lu.b = b; lu.r0 = r0; lu.wo = wo; lu.po = po; lu.qo = qo;
+    cudaFree(D); cudaFree(Lb); cudaFree(Ub); cudaFree(Qp);
+    if (e != cudaSuccess) { cudaFree(lu.W); cudaFree(lu.A0b); lu = CoarseBlockLU{}; return -1; }
+    lu.b = b; lu.r0 = r0; lu.wo = wo;
     *minpiv = mp;
     return singular ? 1 : 0;
 }
 
 void coarse_block_free(CoarseBlockLU& lu) {
-    cudaFree(lu.W); cudaFree(lu.P); cudaFree(lu.Q);
+    cudaFree(lu.W); cudaFree(lu.A0b);
     lu = CoarseBlockLU{};
 }
 
-void launch_coarse_block_solve(const Ctx& cx, int nb, const CoarseBlockLU& lu, const double2* c, double2* out,
+void launch_coarse_block_solve(const Ctx& cx, int nb, const CoarseBlockLU& lu, double2* c, double2* out,
                                float2* outf, BatchSkip sk) {
     const int m = lu.m, Nc = lu.nc1 * lu.nc1;
     const int threads = 256, wpb = threads / 32;
-    // forward: out_i = W_i c_i - P_i out_{i-1}
+    // forward: c_i <- c_i - L_i y_{i-1}, y_i = W_i c_i
     for (int i = 0; i < m; ++i) {
         const int bi = lu.b[i];
+        if (i > 0)
+            k_cb_band<<<dim3((bi + 127) / 128, nb), 128, 0, cx.stream>>>(lu.nc1, lu.A0b, lu.r0[i], bi, lu.r0[i - 1],
+                                                                         lu.b[i - 1], out, c, Nc, 1, sk);
         const dim3 grd((bi + wpb - 1) / wpb, nb);
-        k_cb_step<<<grd, threads, 0, cx.stream>>>(bi, lu.W + lu.wo[i], c + lu.r0[i], bi,
-                                                  i > 0 ? lu.P + lu.po[i] : nullptr,
-                                                  i > 0 ? out + lu.r0[i - 1] : nullptr, i > 0 ? lu.b[i - 1] : 0,
-                                                  nullptr, out + lu.r0[i], Nc, sk);
+        k_cb_step<<<grd, threads, 0, cx.stream>>>(bi, lu.W + lu.wo[i], c + lu.r0[i], bi, nullptr, nullptr, 0, nullptr,
+                                                  out + lu.r0[i], Nc, sk);
     }
-    // backward: out_i = out_i - Q_i out_{i+1}
+    // backward: c_i <- U_i x_{i+1}, x_i = y_i - W_i c_i
     for (int i = m - 2; i >= 0; --i) {
         const int bi = lu.b[i];
+        k_cb_band<<<dim3((bi + 127) / 128, nb), 128, 0, cx.stream>>>(lu.nc1, lu.A0b, lu.r0[i], bi, lu.r0[i + 1],
+                                                                     lu.b[i + 1], out, c, Nc, 0, sk);
         const dim3 grd((bi + wpb - 1) / wpb, nb);
-        k_cb_step<<<grd, threads, 0, cx.stream>>>(bi, nullptr, nullptr, 0, lu.Q + lu.qo[i], out + lu.r0[i + 1],
-                                                  lu.b[i + 1], out + lu.r0[i], out + lu.r0[i], Nc, sk);
+        k_cb_step<<<grd, threads, 0, cx.stream>>>(bi, nullptr, nullptr, 0, lu.W + lu.wo[i], c + lu.r0[i], bi,
+                                                  out + lu.r0[i], out + lu.r0[i], Nc, sk);
     }
     if (outf) k_c128_to_c64_batched<<<dim3((Nc + 255) / 256, nb), 256, 0, cx.stream>>>(Nc, out, outf, sk);
 }

@@ -123,16 +123,17 @@ void launch_galerkin_banded(const Ctx& cx, double2* A0b);
 struct CoarseBlockLU {
     int nc1 = 0, s = 0, m = 0;            // m block rows of s coarse rows (the last may be shorter)
     std::vector<int> b, r0;               // block sizes and first unknowns
-    std::vector<long long> wo, po, qo;    // offsets of W_i, P_i, Q_i
+    std::vector<long long> wo;            // offsets of W_i
     double2* W = nullptr;                 // W_i = S_i^{-1}        (b_i x b_i)
-    double2* P = nullptr;                 // P_i = W_i L_i         (b_i x b_{i-1})
-    double2* Q = nullptr;                 // Q_i = W_i U_i         (b_i x b_{i+1})
+    double2* A0b = nullptr;               // A_0 in band form (Nc x 25), owned: the couplings L_i, U_i
 };
 // 0 on success, 1 if a pivot was zero, -1 on a CUDA error; *minpiv = smallest |pivot|.
-int coarse_block_setup(const Ctx& cx, int nc1, int s, const double2* A0b, CoarseBlockLU& lu, double* minpiv);
+// Takes ownership of A0b (freed by coarse_block_free, or here on failure).
+int coarse_block_setup(const Ctx& cx, int nc1, int s, double2* A0b, CoarseBlockLU& lu, double* minpiv);
 void coarse_block_free(CoarseBlockLU& lu);
-// out = A_0^{-1} c (FP64, stride nc1^2 per batch entry); outf (if given) its complex64 rounding
-void launch_coarse_block_solve(const Ctx& cx, int nb, const CoarseBlockLU& lu, const double2* c, double2* out,
+// out = A_0^{-1} c (FP64, stride nc1^2 per batch entry); outf (if given) its complex64 rounding.
+// c is overwritten (it holds the intermediate vectors of the sweeps).
+void launch_coarse_block_solve(const Ctx& cx, int nb, const CoarseBlockLU& lu, double2* c, double2* out,
                                float2* outf, BatchSkip sk);
 int gj_invert(const Ctx& cx, double2* a, int N, double* minpiv);
 

@@ -811,6 +811,7 @@ static hzs_status ensure_krylov(hzs_precond* p, int maxit, int nb, bool full_v) 
     //   HZS_F53_RING=0|3|4         stages of the dot pass's copy ring (mixed tasks; 0: none)
     //   HZS_F53_UPD_E=1|2          entries per thread and sweep of the update pass
     //   HZS_F53_G64=4|8            vectors per FP64 task of the dot pass (specialised warps)
+    //   HZS_F53_RING64=0|1         FP64 tasks of the dot pass through the copy ring as well
     if (const char* ev = std::getenv("HZS_F53_OCC")) {
         const int v = std::atoi(ev);
         if (v == 2 || v == 3) kb.s53_minb = kb.s53_dot_minb = v;
@@ -826,6 +827,7 @@ static hzs_status ensure_krylov(hzs_precond* p, int maxit, int nb, bool full_v) 
     if (const char* ev = std::getenv("HZS_F53_WS")) kb.s53_ws = std::atoi(ev) ? 1 : 0;
     if (const char* ev = std::getenv("HZS_F53_UPD_E")) kb.s53_upd_e = std::atoi(ev) == 2 ? 2 : 1;
     if (const char* ev = std::getenv("HZS_F53_G64")) kb.s53_g64 = std::atoi(ev) == 8 ? 8 : 4;
+    if (const char* ev = std::getenv("HZS_F53_RING64")) kb.s53_ring64 = std::atoi(ev) ? 1 : 0;
     if (const char* ev = std::getenv("HZS_F53_GROUP")) {
         const int v = std::atoi(ev);
         if (v == 1 || v == 2 || v == 4) kb.s53_group = v;
@@ -1259,16 +1261,43 @@ extern "C" hzs_status hzs_solve_batched(int nprob, hzs_precond* const* probs, co
     std::vector<hzs_status> st(nprob, HZS_OK);
     int dev = 0;
     cudaGetDevice(&dev);
-    // the problems allocate their Krylov spaces at the same time: split the free memory evenly
+    // the problems allocate their Krylov spaces at the same time: split 80 % of the free
+    // memory by water-filling, each problem at most what all its right-hand sides need
+    // (so that the small problems leave the rest to the large ones, which then solve
+    // their right-hand sides in fewer, larger lockstep batches)
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
-    const size_t share = nprob > 0 ? (size_t)(0.8 * (double)fr / nprob) : 0;
+    std::vector<double> need(nprob), share(nprob, 0.0);
+    for (int k = 0; k < nprob; ++k) {
+        const long long N = (long long)probs[k]->g->desc.n * probs[k]->g->desc.n;
+        const int om = orth_mode(probs[k], sd);
+        need[k] = (double)krylov_entry_bytes(probs[k], sd->maxit, (N + 63) / 64 * 64,
+                                             om == kOrthCGS2 || om == kOrthD64) * std::max(nrhs[k], 1);
+    }
+    {
+        double left = 0.8 * (double)fr;
+        std::vector<int> open;
+        for (int k = 0; k < nprob; ++k) open.push_back(k);
+        while (!open.empty()) {
+            const double each = left / (double)open.size();
+            std::vector<int> rest;
+            for (int k : open) {
+                if (need[k] <= each) { share[k] = need[k]; left -= need[k]; }
+                else rest.push_back(k);
+            }
+            if (rest.size() == open.size()) {
+                for (int k : rest) share[k] = each;
+                break;
+            }
+            open.swap(rest);
+        }
+    }
     std::vector<std::thread> th;
     for (int k = 0; k < nprob; ++k) {
         th.emplace_back([&, k]() {
             cudaSetDevice(dev);
             st[k] = solve_many(probs[k], sd, f_dev[k], u_dev[k], nrhs[k], info ? info + off[k] : nullptr, 0,
-                               share > 0 ? share : 1);
+                               share[k] >= 1.0 ? (size_t)share[k] : 1);
         });
     }
     for (auto& t : th) t.join();

@@ -7,12 +7,15 @@
 // grouping s consecutive coarse rows into one block row gives a block-
 // tridiagonal matrix with blocks of size b_i = (rows in group i) * nc1:
 //   D_i (b_i x b_i), L_i (b_i x b_{i-1}), U_i (b_i x b_{i+1}).
-// Set-up (FP64): S_0 = D_0, S_i = D_i - L_i Q_{i-1} with Q_{i-1} = W_{i-1} U_{i-1};
-// W_i = S_i^{-1} (Gauss-Jordan with partial pivoting).  Only the W_i are kept; the
-// couplings L_i, U_i stay in A_0's band form (at most 10 entries a row).
-// Solve: y_0 = W_0 c_0, y_i = W_i (c_i - L_i y_{i-1});  x_{m-1} = y_{m-1},
-// x_i = y_i - W_i (U_i x_{i+1}): 2m - 1 dependent dense matrix-vector products with
-// the W_i (one warp per row), each after a banded product (one thread per row).
+// Set-up (FP64): S_0 = D_0, S_i = D_i - L_i Q_{i-1};  W_i = S_i^{-1} (Gauss-Jordan
+// with partial pivoting), P_i = W_i L_i, Q_i = W_i U_i; A_0's band form is kept too
+// (L_i and U_i have at most 10 entries a row there).
+// Solve, two forms of the same block substitution:
+//  - many right-hand sides (FP64-bound): y_0 = W_0 c_0, y_i = W_i (c_i - L_i y_{i-1});
+//    x_{m-1} = y_{m-1}, x_i = y_i - W_i (U_i x_{i+1}): 2m - 1 dense products with the
+//    W_i (one warp per row and right-hand side), each after a banded product;
+//  - one or two right-hand sides (latency-bound): y_i = W_i c_i - P_i y_{i-1},
+//    x_i = y_i - Q_i x_{i+1}: one launch per block step, 3m - 2 dense products.
 #include <vector>
 
 #include "kernels.cuh"
@@ -145,25 +148,27 @@ int coarse_block_setup(const Ctx& cx, int nc1, int s, double2* A0b, CoarseBlockL
         r0[i] = i * s * nc1;
         b[i] = (std::min(nc1, (i + 1) * s) - i * s) * nc1;
     }
-    long long wsz = 0;
-    std::vector<long long> wo(m);
+    long long wsz = 0, psz = 0, qsz = 0;
+    std::vector<long long> wo(m), po(m), qo(m);
     for (int i = 0; i < m; ++i) {
-        wo[i] = wsz;
-        wsz += (long long)b[i] * b[i];
+        wo[i] = wsz; wsz += (long long)b[i] * b[i];
+        po[i] = psz; if (i > 0) psz += (long long)b[i] * b[i - 1];
+        qo[i] = qsz; if (i + 1 < m) qsz += (long long)b[i] * b[i + 1];
     }
     const int bmax = s * nc1;
-    double2 *D = nullptr, *Lb = nullptr, *Ub = nullptr, *Qp = nullptr;
+    double2 *D = nullptr, *Lb = nullptr, *Ub = nullptr;
     auto fail = [&]() {
-        cudaFree(D); cudaFree(Lb); cudaFree(Ub); cudaFree(Qp);
-        cudaFree(lu.W); cudaFree(lu.A0b);
+        cudaFree(D); cudaFree(Lb); cudaFree(Ub);
+        cudaFree(lu.W); cudaFree(lu.P); cudaFree(lu.Q); cudaFree(lu.A0b);
         lu = CoarseBlockLU{};
         return -1;
     };
     if (cudaMalloc(&lu.W, (size_t)wsz * sizeof(double2)) != cudaSuccess) return fail();
+    if (cudaMalloc(&lu.P, (size_t)(psz > 0 ? psz : 1) * sizeof(double2)) != cudaSuccess) return fail();
+    if (cudaMalloc(&lu.Q, (size_t)(qsz > 0 ? qsz : 1) * sizeof(double2)) != cudaSuccess) return fail();
     if (cudaMalloc(&D, (size_t)bmax * bmax * sizeof(double2)) != cudaSuccess) return fail();
     if (cudaMalloc(&Lb, (size_t)bmax * bmax * sizeof(double2)) != cudaSuccess) return fail();
     if (cudaMalloc(&Ub, (size_t)bmax * bmax * sizeof(double2)) != cudaSuccess) return fail();
-    if (cudaMalloc(&Qp, (size_t)bmax * bmax * sizeof(double2)) != cudaSuccess) return fail();
     double mp = 1e300;
     int singular = 0;
     const int cb = 4 * cx.num_sms;
@@ -173,7 +178,7 @@ int coarse_block_setup(const Ctx& cx, int nc1, int s, double2* A0b, CoarseBlockL
         if (i > 0) {
             // S_i = D_i - L_i Q_{i-1}
             k_band_to_block<<<cb, 256, 0, cx.stream>>>(nc1, A0b, r0[i], bi, r0[i - 1], b[i - 1], Lb);
-            zgemm(cx, bi, bi, b[i - 1], -1.0, Lb, b[i - 1], Qp, bi, 1.0, D, bi);
+            zgemm(cx, bi, bi, b[i - 1], -1.0, Lb, b[i - 1], lu.Q + qo[i - 1], bi, 1.0, D, bi);
         }
         double piv = 0.0;
         const int rc = gj_invert(cx, D, bi, &piv);      // D <- S_i^{-1}
@@ -183,22 +188,26 @@ int coarse_block_setup(const Ctx& cx, int nc1, int s, double2* A0b, CoarseBlockL
         if (cudaMemcpyAsync(lu.W + wo[i], D, (size_t)bi * bi * sizeof(double2), cudaMemcpyDeviceToDevice,
                             cx.stream) != cudaSuccess)
             return fail();
+        if (i > 0) zgemm(cx, bi, b[i - 1], bi, 1.0, lu.W + wo[i], bi, Lb, b[i - 1], 0.0, lu.P + po[i], b[i - 1]);
         if (i + 1 < m) {
-            // Q_i = W_i U_i, used by the next block row only
             k_band_to_block<<<cb, 256, 0, cx.stream>>>(nc1, A0b, r0[i], bi, r0[i + 1], b[i + 1], Ub);
-            zgemm(cx, bi, b[i + 1], bi, 1.0, lu.W + wo[i], bi, Ub, b[i + 1], 0.0, Qp, b[i + 1]);
+            zgemm(cx, bi, b[i + 1], bi, 1.0, lu.W + wo[i], bi, Ub, b[i + 1], 0.0, lu.Q + qo[i], b[i + 1]);
         }
     }
     const cudaError_t e = cudaStreamSynchronize(cx.stream);
-    cudaFree(D); cudaFree(Lb); cudaFree(Ub); cudaFree(Qp);
-    if (e != cudaSuccess) { cudaFree(lu.W); cudaFree(lu.A0b); lu = CoarseBlockLU{}; return -1; }
-    lu.b = b; lu.r0 = r0; lu.wo = wo;
+    cudaFree(D); cudaFree(Lb); cudaFree(Ub);
+    if (e != cudaSuccess) {
+        cudaFree(lu.W); cudaFree(lu.P); cudaFree(lu.Q); cudaFree(lu.A0b);
+        lu = CoarseBlockLU{};
+        return -1;
+    }
+    lu.b = b; lu.r0 = r0; lu.wo = wo; lu.po = po; lu.qo = qo;
     *minpiv = mp;
     return singular ? 1 : 0;
 }
 
 void coarse_block_free(CoarseBlockLU& lu) {
-    cudaFree(lu.W); cudaFree(lu.A0b);
+    cudaFree(lu.W); cudaFree(lu.P); cudaFree(lu.Q); cudaFree(lu.A0b);
     lu = CoarseBlockLU{};
 }
 
@@ -206,6 +215,26 @@ void launch_coarse_block_solve(const Ctx& cx, int nb, const CoarseBlockLU& lu, d
                                float2* outf, BatchSkip sk) {
     const int m = lu.m, Nc = lu.nc1 * lu.nc1;
     const int threads = 256, wpb = threads / 32;
+    if (nb <= 2) {
+        // few right-hand sides: one launch per block step, W_i c_i - P_i y_{i-1} and
+        // y_i - Q_i x_{i+1}
+        for (int i = 0; i < m; ++i) {
+            const int bi = lu.b[i];
+            const dim3 grd((bi + wpb - 1) / wpb, nb);
+            k_cb_step<<<grd, threads, 0, cx.stream>>>(bi, lu.W + lu.wo[i], c + lu.r0[i], bi,
+                                                      i > 0 ? lu.P + lu.po[i] : nullptr,
+                                                      i > 0 ? out + lu.r0[i - 1] : nullptr, i > 0 ? lu.b[i - 1] : 0,
+                                                      nullptr, out + lu.r0[i], Nc, sk);
+        }
+        for (int i = m - 2; i >= 0; --i) {
+            const int bi = lu.b[i];
+            const dim3 grd((bi + wpb - 1) / wpb, nb);
+            k_cb_step<<<grd, threads, 0, cx.stream>>>(bi, nullptr, nullptr, 0, lu.Q + lu.qo[i], out + lu.r0[i + 1],
+                                                      lu.b[i + 1], out + lu.r0[i], out + lu.r0[i], Nc, sk);
+        }
+        if (outf) k_c128_to_c64_batched<<<dim3((Nc + 255) / 256, nb), 256, 0, cx.stream>>>(Nc, out, outf, sk);
+        return;
+    }
     // forward: c_i <- c_i - L_i y_{i-1}, y_i = W_i c_i
     for (int i = 0; i < m; ++i) {
         const int bi = lu.b[i];

@@ -123,8 +123,10 @@ void launch_galerkin_banded(const Ctx& cx, double2* A0b);
 struct CoarseBlockLU {
     int nc1 = 0, s = 0, m = 0;            // m block rows of s coarse rows (the last may be shorter)
     std::vector<int> b, r0;               // block sizes and first unknowns
-    std::vector<long long> wo;            // offsets of W_i
+    std::vector<long long> wo, po, qo;    // offsets of W_i, P_i, Q_i
     double2* W = nullptr;                 // W_i = S_i^{-1}        (b_i x b_i)
+    double2* P = nullptr;                 // P_i = W_i L_i         (b_i x b_{i-1})
+    double2* Q = nullptr;                 // Q_i = W_i U_i         (b_i x b_{i+1})
     double2* A0b = nullptr;               // A_0 in band form (Nc x 25), owned: the couplings L_i, U_i
 };
 // 0 on success, 1 if a pivot was zero, -1 on a CUDA error; *minpiv = smallest |pivot|.
@@ -198,6 +200,7 @@ struct KrylovBufs {
     int s53_ws = 1;        // dot pass: each warp task on one of the two paths (k_s53_dot_ws)
     int s53_upd_e = 2;     // update pass: entries per thread and sweep (1 or 2)
     int s53_g64 = 4;       // dot pass, specialised warps: vectors per FP64 task (4 or 8)
+    int s53_ring64 = 1;    // dot pass, specialised warps: FP64 tasks also through the copy ring
     double* sigma;     // (maxit+1): basis vector i = sigma[i] * V_i
     double2* H;        // (maxit+1) x maxit, column j at H[j*(maxit+1)]
     double* cs;        // maxit+1

@@ -286,7 +286,7 @@ __device__ __forceinline__ int s53_count(int j, unsigned mask) {
 // proportion and are taken by the warps of a block from a shared counter, so the FP64
 // pipe and the FP32 pipes are fed by different warps at the same time.  The FP32 path's
 // entries stream through a per-thread shared-memory ring of NS stages (cp.async).
-template <int MINB, int G64, int G32, int NS>
+template <int MINB, int G64, int G32, int NS, bool R64>
 __global__ void __launch_bounds__(kS53Threads, MINB) k_s53_dot_ws(int j, long long N, long long ld, int ps, int S,
                                                               const float2* __restrict__ Vh,
                                                               const uint2* __restrict__ Vt, long long sV, int has_w,
@@ -299,7 +299,10 @@ __global__ void __launch_bounds__(kS53Threads, MINB) k_s53_dot_ws(int j, long lo
     const uint2* ut = Vt + (size_t)j * ld;
     const float2* wh = Vh + (size_t)(has_w ? j + 1 : j) * ld;
     part += r * sP + (size_t)blockIdx.x * ps;
-    extern __shared__ uint2 s53ring[];              // NS x (2 G32 + 3) x kS53Threads 8-byte slots
+    // NS x IT x kS53Threads 8-byte slots, IT = 2 G + 3 for the larger task that uses the ring
+    extern __shared__ uint2 s53ring[];
+    constexpr int IT = 2 * (R64 && G64 > G32 ? G64 : G32) + 3;
+    auto slot = [&](int stage, int item) { return s53ring + ((stage * IT + item) * kS53Threads + threadIdx.x); };
     __shared__ int s_next;
     long long e0, e1;
     chunk_of53(N, e0, e1);
@@ -347,16 +350,58 @@ __global__ void __launch_bounds__(kS53Threads, MINB) k_s53_dot_ws(int j, long lo
                     al[t] = make_double2(0.0, 0.0);
                     B1[t] = B2[t] = 0ull;
                 }
-                for (long long e = e0 + lane; e < e1; e += 32) {
-                    const float2 xh = __ldg(uh + e);
-                    const uint2 xt = __ldg(ut + e);
-                    const float2 yh = has_w ? __ldg(wh + e) : make_float2(0.f, 0.f);
+                auto issue64 = [&](long long k, int stage) {
+                    const long long e = e0 + lane + 32 * k;
+#pragma unroll
+                    for (int t = 0; t < G64; ++t)
+                        if (vi[t] >= 0) {
+                            cp_async_8(slot(stage, t), Vh + (size_t)vi[t] * ld + e);
+                            cp_async_8(slot(stage, G64 + t), Vt + (size_t)vi[t] * ld + e);
+                        }
+                    cp_async_8(slot(stage, 2 * G64), uh + e);
+                    cp_async_8(slot(stage, 2 * G64 + 1), ut + e);
+                    if (has_w) cp_async_8(slot(stage, 2 * G64 + 2), wh + e);
+                };
+                if constexpr (R64) {
+#pragma unroll
+                    for (int s0 = 0; s0 < NS - 1; ++s0) {
+                        if (s0 < K) issue64(s0, s0);
+                        cp_async_commit();
+                    }
+                }
+                int cs = 0;
+                for (long long k = 0; k < K; ++k) {
+                    const long long e = e0 + lane + 32 * k;
+                    float2 xh, yh;
+                    uint2 xt;
                     float2 vh[G64];
                     uint2 vt[G64];
+                    if constexpr (R64) {
+                        const int is = cs == 0 ? NS - 1 : cs - 1;   // stage of entry k + NS - 1 (read at k - 1)
+                        if (k + NS - 1 < K) issue64(k + NS - 1, is);
+                        cp_async_commit();
+                        cp_async_wait<NS - 1>();                    // entry k has landed
+                        const uint2 xa = *slot(cs, 2 * G64), ya = *slot(cs, 2 * G64 + 2);
+                        xh = make_float2(__uint_as_float(xa.x), __uint_as_float(xa.y));
+                        xt = *slot(cs, 2 * G64 + 1);
+                        yh = has_w ? make_float2(__uint_as_float(ya.x), __uint_as_float(ya.y)) : make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int t = 0; t < G64; ++t) {
-                        vh[t] = vi[t] >= 0 ? __ldcs(Vh + (size_t)vi[t] * ld + e) : make_float2(0.f, 0.f);
-                        vt[t] = vi[t] >= 0 ? __ldcs(Vt + (size_t)vi[t] * ld + e) : make_uint2(0u, 0u);
+                        for (int t = 0; t < G64; ++t) {
+                            const uint2 h = *slot(cs, t);
+                            vh[t] = vi[t] >= 0 ? make_float2(__uint_as_float(h.x), __uint_as_float(h.y))
+                                               : make_float2(0.f, 0.f);
+                            vt[t] = vi[t] >= 0 ? *slot(cs, G64 + t) : make_uint2(0u, 0u);
+                        }
+                        cs = cs + 1 == NS ? 0 : cs + 1;
+                    } else {
+                        xh = __ldg(uh + e);
+                        xt = __ldg(ut + e);
+                        yh = has_w ? __ldg(wh + e) : make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int t = 0; t < G64; ++t) {
+                            vh[t] = vi[t] >= 0 ? __ldcs(Vh + (size_t)vi[t] * ld + e) : make_float2(0.f, 0.f);
+                            vt[t] = vi[t] >= 0 ? __ldcs(Vt + (size_t)vi[t] * ld + e) : make_uint2(0u, 0u);
+                        }
                     }
                     const double2 x = make_double2(f53_double(xh.x, xt.x), f53_double(xh.y, xt.y));
                     const f2x Wr = f2_bcast(yh.x), Wi = f2_bcast(yh.y);
@@ -369,6 +414,7 @@ __global__ void __launch_bounds__(kS53Threads, MINB) k_s53_dot_ws(int j, long lo
                         B2[t] = fma2(Wi, V0, B2[t]);
                     }
                 }
+                if constexpr (R64) cp_async_wait<0>();          // (only empty groups remain) the slots are free
 #pragma unroll
                 for (int t = 0; t < G64; ++t) {
                     const double2 sa = warp_sum(al[t]);
@@ -392,10 +438,6 @@ __global__ void __launch_bounds__(kS53Threads, MINB) k_s53_dot_ws(int j, long lo
                     tf_zero(R[t]);
                     B1[t] = B2[t] = 0ull;
                 }
-                constexpr int IT = 2 * G32 + 3;
-                auto slot = [&](int stage, int item) {
-                    return s53ring + ((stage * IT + item) * kS53Threads + threadIdx.x);
-                };
                 auto issue = [&](long long k, int stage) {
                     const long long e = e0 + lane + 32 * k;
 #pragma unroll
@@ -779,11 +821,17 @@ int launch_s53_dot(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int has_w
         // else for 2 blocks per SM
         const int g32 = minb == 3 && gsz == 4 ? 2 : gsz;
         const bool g8 = kb.s53_g64 == 8 && minb != 3;
+        // FP64 tasks through the ring too (FP64 tasks of 4 and FP32 tasks of 4 only)
+        const bool r64 = kb.s53_ring64 && minb != 3 && !g8 && g32 == 4;
         smem_l = (size_t)4 * (2 * g32 + 3) * kS53Threads * sizeof(uint2);
-        fn = minb == 3 ? (g32 == 1 ? (const void*)k_s53_dot_ws<3, 4, 1, 4> : (const void*)k_s53_dot_ws<3, 4, 2, 4>)
-             : g32 == 1 ? (const void*)k_s53_dot_ws<2, 4, 1, 4>
-             : g32 == 4 ? (g8 ? (const void*)k_s53_dot_ws<2, 8, 4, 4> : (const void*)k_s53_dot_ws<2, 4, 4, 4>)
-                        : (g8 ? (const void*)k_s53_dot_ws<2, 8, 2, 4> : (const void*)k_s53_dot_ws<2, 4, 2, 4>);
+        fn = minb == 3 ? (g32 == 1 ? (const void*)k_s53_dot_ws<3, 4, 1, 4, false>
+                                   : (const void*)k_s53_dot_ws<3, 4, 2, 4, false>)
+             : g32 == 1 ? (const void*)k_s53_dot_ws<2, 4, 1, 4, false>
+             : g32 == 4 ? (g8  ? (const void*)k_s53_dot_ws<2, 8, 4, 4, false>
+                           : r64 ? (const void*)k_s53_dot_ws<2, 4, 4, 4, true>
+                                 : (const void*)k_s53_dot_ws<2, 4, 4, 4, false>)
+                        : (g8 ? (const void*)k_s53_dot_ws<2, 8, 2, 4, false>
+                              : (const void*)k_s53_dot_ws<2, 4, 2, 4, false>);
     }
     if (smem_l > 0 && allow_dynamic_smem(fn, smem_l) != cudaSuccess) return 0;
     const int blocks = std::min(kb.nblk_dot, (minb == 3 ? 3 : 4) * cx.num_sms);

@@ -91,7 +91,7 @@ def test_batched_mp2_workload(hzs):
         rhs.append(sources(n, 64, seed=1000 + idx))
         ks.append(k)
     torch.cuda.synchronize()
-    outs, res = hzs.solve_batched(probs, rhs, tol=1e-6, maxit=300)
+    outs, res = hzs.solve_batched(probs, rhs, tol=1e-6, maxit=100)
     torch.cuda.synchronize()
     for P, F, U, R, k in zip(probs, rhs, outs, res, ks):
         assert all(r.converged for r in R)

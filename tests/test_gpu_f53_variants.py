@@ -26,7 +26,8 @@ from paper_2408_03571_gb300.inputs import point_source  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-KNOBS = ("HZS_F53_MASK", "HZS_F53_OCC", "HZS_F53_DOT_OCC", "HZS_F53_WS", "HZS_F53_GROUP", "HZS_F53_RING")
+KNOBS = ("HZS_F53_MASK", "HZS_F53_OCC", "HZS_F53_DOT_OCC", "HZS_F53_WS", "HZS_F53_GROUP", "HZS_F53_RING",
+         "HZS_F53_UPD_E", "HZS_F53_G64", "HZS_F53_RING64")
 
 VARIANTS = [
     {},                                                                     # the defaults
@@ -41,6 +42,8 @@ VARIANTS = [
     {"HZS_F53_UPD_E": "1", "HZS_F53_OCC": "3", "HZS_F53_MASK": "0x6D,0x77"},
     {"HZS_F53_G64": "8", "HZS_F53_GROUP": "2"},
     {"HZS_F53_UPD_E": "2", "HZS_F53_OCC": "3"},
+    {"HZS_F53_RING64": "1"},
+    {"HZS_F53_RING64": "1", "HZS_F53_MASK": "0xFF,0x6D"},
 ]
 
 

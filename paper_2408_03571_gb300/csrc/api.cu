@@ -916,7 +916,7 @@ static int orth_mode(const hzs_precond* p, const hzs_solve_desc* sd) {
     if (sd->flags & HZS_SOLVE_ORTH_DFMA) return kOrthD64;
     // the f53 update pass keeps 96 bytes of coefficients per basis vector in shared
     // memory; longer runs use the all-FMA variant (32 bytes per vector)
-    return s53_update_smem(sd->maxit) + 2048 <= (size_t)227 * 1024 ? kOrthS53 : kOrthD64;
+    return s53_update_smem(sd->maxit) + 8192 <= (size_t)227 * 1024 ? kOrthS53 : kOrthD64;
 }
 
 // Kernel launches of one preconditioner apply.

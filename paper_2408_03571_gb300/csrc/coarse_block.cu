@@ -99,6 +99,49 @@ __global__ void k_cb_step(int rows, const double2* __restrict__ Ma, const double
     }
 }
 
+// The same step with each row split over kCbWarpsPerRow warps (few right-hand sides:
+// the step's latency, not the FP64 pipe, bounds it): every warp sums a strided quarter
+// of the row, the quarters are added in a fixed order through shared memory.
+constexpr int kCbWarpsPerRow = 4;
+__global__ void __launch_bounds__(256) k_cb_step_split(int rows, const double2* __restrict__ Ma,
+                                                       const double2* __restrict__ xa, int na,
+                                                       const double2* __restrict__ Mb,
+                                                       const double2* __restrict__ xb, int nbc,
+                                                       const double2* __restrict__ base,
+                                                       double2* __restrict__ out, long long stride, BatchSkip sk) {
+    constexpr int W = kCbWarpsPerRow, RPB = 256 / 32 / W;     // rows per block
+    __shared__ double2 part[RPB][W];
+    const int r = blockIdx.y;
+    if (sk.flag && sk.flag[(size_t)r * sk.stride]) return;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rib = wib / W, q = wib % W;
+    const int row = blockIdx.x * RPB + rib;
+    const long long off = (long long)r * stride;
+    double2 acc = make_double2(0.0, 0.0);
+    if (row < rows) {
+        if (Ma) {
+            const double2* m = Ma + (size_t)row * na;
+            const double2* x = xa + off;
+            for (int k = q * 32 + lane; k < na; k += 32 * W) acc = cfma(m[k], x[k], acc);
+        }
+        if (Mb) {
+            const double2* m = Mb + (size_t)row * nbc;
+            const double2* x = xb + off;
+            for (int k = q * 32 + lane; k < nbc; k += 32 * W) acc = cfms(m[k], x[k], acc);
+        }
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) part[rib][q] = acc;
+    __syncthreads();
+    if (q == 0 && lane == 0 && row < rows) {
+        double2 t = part[rib][0];
+#pragma unroll
+        for (int u = 1; u < W; ++u) t = cadd(t, part[rib][u]);
+        if (base) t = cadd(t, base[off + row]);
+        out[off + row] = t;
+    }
+}
+
 // Banded coupling of block row i (rows [r0, r0 + rows)) with the unknowns
 // [cr0, cr0 + crows) of a neighbouring block row, batch entry r = blockIdx.y, one
 // thread per row: acc = sum over A_0's band entries of the row whose column lies in
@@ -217,20 +260,22 @@ void launch_coarse_block_solve(const Ctx& cx, int nb, const CoarseBlockLU& lu, d
     const int threads = 256, wpb = threads / 32;
     if (nb <= 2) {
         // few right-hand sides: one launch per block step, W_i c_i - P_i y_{i-1} and
-        // y_i - Q_i x_{i+1}
+        // y_i - Q_i x_{i+1}, each row split over kCbWarpsPerRow warps
+        constexpr int rpb = 256 / 32 / kCbWarpsPerRow;
         for (int i = 0; i < m; ++i) {
             const int bi = lu.b[i];
-            const dim3 grd((bi + wpb - 1) / wpb, nb);
-            k_cb_step<<<grd, threads, 0, cx.stream>>>(bi, lu.W + lu.wo[i], c + lu.r0[i], bi,
-                                                      i > 0 ? lu.P + lu.po[i] : nullptr,
-                                                      i > 0 ? out + lu.r0[i - 1] : nullptr, i > 0 ? lu.b[i - 1] : 0,
-                                                      nullptr, out + lu.r0[i], Nc, sk);
+            const dim3 grd((bi + rpb - 1) / rpb, nb);
+            k_cb_step_split<<<grd, threads, 0, cx.stream>>>(bi, lu.W + lu.wo[i], c + lu.r0[i], bi,
+                                                            i > 0 ? lu.P + lu.po[i] : nullptr,
+                                                            i > 0 ? out + lu.r0[i - 1] : nullptr,
+                                                            i > 0 ? lu.b[i - 1] : 0, nullptr, out + lu.r0[i], Nc, sk);
         }
         for (int i = m - 2; i >= 0; --i) {
             const int bi = lu.b[i];
-            const dim3 grd((bi + wpb - 1) / wpb, nb);
-            k_cb_step<<<grd, threads, 0, cx.stream>>>(bi, nullptr, nullptr, 0, lu.Q + lu.qo[i], out + lu.r0[i + 1],
-                                                      lu.b[i + 1], out + lu.r0[i], out + lu.r0[i], Nc, sk);
+            const dim3 grd((bi + rpb - 1) / rpb, nb);
+            k_cb_step_split<<<grd, threads, 0, cx.stream>>>(bi, nullptr, nullptr, 0, lu.Q + lu.qo[i],
+                                                            out + lu.r0[i + 1], lu.b[i + 1], out + lu.r0[i],
+                                                            out + lu.r0[i], Nc, sk);
         }
         if (outf) k_c128_to_c64_batched<<<dim3((Nc + 255) / 256, nb), 256, 0, cx.stream>>>(Nc, out, outf, sk);
         return;

@@ -856,7 +856,7 @@ int launch_s53_update(const Ctx& cx, const KrylovBufs& kb, int nb, int j, unsign
     // blocks per SM: as the registers allow while their shared memory fits (<= kb.nblk / SMs,
     // the partials' stride)
     int bps = three ? 3 : 2;
-    while (bps > 1 && (size_t)bps * (us + 2048) > (size_t)(228 * 1024)) --bps;
+    while (bps > 1 && (size_t)bps * (us + 8192) > (size_t)(228 * 1024)) --bps;
     const int blocks = bps * cx.num_sms;
     float2* Vh = kb.V32;
     uint2* Vt = static_cast<uint2*>(kb.V32lo);

@@ -44,6 +44,8 @@ VARIANTS = [
     {"HZS_F53_UPD_E": "2", "HZS_F53_OCC": "3"},
     {"HZS_F53_RING64": "1"},
     {"HZS_F53_RING64": "1", "HZS_F53_MASK": "0xFF,0x6D"},
+    {"HZS_F53_MASK": "0x6D,0xFF"},
+    {"HZS_F53_MASK": "0x6D,0x00"},
 ]
 
 

@@ -1022,10 +1022,7 @@ static hzs_status solve_batch(hzs_precond* p, const hzs_solve_desc* sd, const do
             float2* Zj = p->Z + (size_t)j * ld;
             st = precond_apply<float, float2>(p, nb, kb.V32 + (size_t)j * ld, sV, kb.sigt + j, sS, Zj, sZ, sk);
             if (prof) HZS_CUDA(g, cudaEventRecord(pe[1], cx.stream));
-            launch_apply_A<float2, double2, double>(cx, nb, Zj, sZ, p->ztmp, ld, nullptr, 0, sk);
-            launch_f53_encode(cx, nb, kb.N, p->ztmp, ld, kb.V32 + (size_t)(j + 1) * ld, Vt + (size_t)(j + 1) * ld, sV,
-                              nullptr, kb.st);
-            launches += 1;
+            launch_apply_A_f53(cx, nb, Zj, sZ, kb.V32 + (size_t)(j + 1) * ld, Vt + (size_t)(j + 1) * ld, sV, sk);
         } else if (d64) {
             // the complex64 preconditioner reads u~_j (the once-projected vector of the previous
             // step, see launch_dcgs2_step64) scaled by 1/|u~_j|; A z_j in FP64 into slot j+1

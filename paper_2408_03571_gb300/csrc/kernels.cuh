@@ -94,6 +94,9 @@ void launch_apply_A(const Ctx& cx, int nb, const Cin* x, long long xs, Cout* y, 
                     long long y32s, BatchSkip sk, LoDst y32lo = LoDst{nullptr, nullptr});
 // y = A x in double-float arithmetic, y as the pair yh + yl (see LoDst); false (nothing
 // launched) when the couplings are not exact in FP32 (n > 4097).
+// y = A x (complex64 x, FP64 arithmetic) stored as f53 heads yh and tails yt
+void launch_apply_A_f53(const Ctx& cx, int nb, const float2* x, long long xs, float2* yh, uint2* yt, long long ys,
+                        BatchSkip sk);
 bool launch_apply_A_df(const Ctx& cx, int nb, const float2* x, long long xs, float2* yh, LoDst yl, long long ys,
                        BatchSkip sk);
 template <typename Cv, typename Cw, typename R>

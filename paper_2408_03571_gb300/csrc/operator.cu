@@ -8,6 +8,7 @@
 // Every kernel handles a batch of right-hand sides: batch entry r = blockIdx.z
 // reads and writes its vectors at r times the stride given for each buffer,
 // and is skipped when skip[r * skip_stride] is set.
+#include "f32x2.cuh"
 #include "kernels.cuh"
 
 namespace hzs {
@@ -79,6 +80,59 @@ __global__ void k_apply_A(OpDesc op, const Cin* __restrict__ x, long long xs, Co
 // error-free (FMA form of Dekker's product), so y carries about 47 significant
 // bits relative to the largest term of the stencil sum before the remainder is
 // stored.
+// FP32 -> FP64 by integer operations (exact, as the conversion instruction, which runs
+// on the part's FP64 pipe): subnormal FP32 inputs take the conversion instruction.
+__device__ __forceinline__ double f2d_exact(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu, sg = u & 0x80000000u;
+    if (e == 0u) return m ? (double)x : __hiloint2double((int)sg, 0);
+    const unsigned hi = sg | ((e == 0xffu ? 0x7ffu : e + 896u) << 20) | (m >> 3);
+    return __hiloint2double((int)hi, (int)(m << 29));
+}
+__device__ __forceinline__ double2 f2d_exact2(float2 v) { return make_double2(f2d_exact(v.x), f2d_exact(v.y)); }
+
+// y = A x for a complex64 x with the FP64 arithmetic of k_apply_A<float2, double2, double>
+// (the same operations in the same order, so the same FP64 values), stored as f53 (an
+// FP32 head and a 29-bit tail, see f32x2.cuh): the outer product of the mixed solve
+// written straight into the Krylov slot it fills.
+__global__ void k_apply_A_f53(OpDesc op, const float2* __restrict__ x, long long xs, float2* __restrict__ yh,
+                              uint2* __restrict__ yt, long long ys, BatchSkip sk) {
+    const int r = blockIdx.z;
+    if (skipped(sk, r)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int n = op.n;
+    if (i >= n || j >= n) return;
+    x += r * xs;
+    yh += r * ys;
+    yt += r * ys;
+    const size_t p = (size_t)j * n + i;
+    if (!op_is_unknown(op, i, j)) {
+        yh[p] = make_float2(0.f, 0.f);
+        yt[p] = make_uint2(0u, 0u);
+        return;
+    }
+    const double2 d = op_diag(op, i, j);
+    const double cx = op_cx(op, j), cy = op_cy(op, i);
+    const double2 xp = f2d_exact2(x[p]);
+    double2 acc;
+    acc.x = d.x * xp.x - d.y * xp.y;
+    acc.y = d.x * xp.y + d.y * xp.x;
+    double2 sx = make_double2(0.0, 0.0), sy = make_double2(0.0, 0.0);
+    if (i > 0 && op_is_unknown(op, i - 1, j)) sx = cadd(sx, f2d_exact2(x[p - 1]));
+    if (i < n - 1 && op_is_unknown(op, i + 1, j)) sx = cadd(sx, f2d_exact2(x[p + 1]));
+    if (j > 0 && op_is_unknown(op, i, j - 1)) sy = cadd(sy, f2d_exact2(x[p - n]));
+    if (j < n - 1 && op_is_unknown(op, i, j + 1)) sy = cadd(sy, f2d_exact2(x[p + n]));
+    acc.x += cx * sx.x + cy * sy.x;
+    acc.y += cx * sx.y + cy * sy.y;
+    float2 h;
+    uint2 t;
+    f53_encode(acc.x, h.x, t.x);
+    f53_encode(acc.y, h.y, t.y);
+    yh[p] = h;
+    yt[p] = t;
+}
+
 __global__ void k_apply_A_df(OpDesc op, float ch, float dh, float dl, const float2* __restrict__ x, long long xs,
                              float2* __restrict__ yh, LoDst yl, long long ys, BatchSkip sk) {
     const int r = blockIdx.z;
@@ -321,6 +375,12 @@ template void launch_apply_A<double2, double2, double>(const Ctx&, int, const do
                                                        long long, float2*, long long, BatchSkip, LoDst);
 template void launch_apply_A<float2, double2, double>(const Ctx&, int, const float2*, long long, double2*, long long,
                                                       float2*, long long, BatchSkip, LoDst);
+
+void launch_apply_A_f53(const Ctx& cx, int nb, const float2* x, long long xs, float2* yh, uint2* yt, long long ys,
+                        BatchSkip sk) {
+    const dim3 b(32, 8);
+    k_apply_A_f53<<<grid2d(cx.op.n, b, nb), b, 0, cx.stream>>>(cx.op, x, xs, yh, yt, ys, sk);
+}
 
 bool launch_apply_A_df(const Ctx& cx, int nb, const float2* x, long long xs, float2* yh, LoDst yl, long long ys,
                        BatchSkip sk) {

@@ -227,3 +227,36 @@ def test_three_word_sum_of_fp64_products_beats_fp64(j):
     terms = [Fraction(float(a)) * Fraction(float(b)) for a, b in zip(u, x)]
     exact, mag = sum(terms), sum(abs(t) for t in terms)
     assert abs(A.value() - exact) <= Fraction(2) ** -60 * mag
+
+
+def _f2d_bits(u: int) -> int:
+    """The integer FP32 -> FP64 conversion of the mixed path's outer operator, restated:
+    (sign, exponent + 896, fraction << 29); zero keeps its sign, the all-ones exponent
+    maps to FP64's; subnormal inputs are left to the conversion instruction (None)."""
+    e = (u >> 23) & 0xFF
+    m = u & 0x7FFFFF
+    sg = u & 0x80000000
+    if e == 0:
+        return None if m else sg << 32
+    hi = sg | ((0x7FF if e == 0xFF else e + 896) << 20) | (m >> 3)
+    return (hi << 32) | ((m << 29) & 0xFFFFFFFF)
+
+
+def test_integer_fp32_to_fp64_conversion_is_exact():
+    rng = np.random.default_rng(5)
+    bits = list(rng.integers(0, 2**32, size=20000, dtype=np.uint64))
+    bits += [0x00000000, 0x80000000, 0x7F800000, 0xFF800000, 0x7F7FFFFF, 0x00800000, 0x80800000,
+             0x3F800000, 0x7FC00000, 0x7F800001, 0x00000001, 0x807FFFFF]
+    for u in bits:
+        u = int(u)
+        got = _f2d_bits(u)
+        if got is None:
+            continue
+        with np.errstate(invalid="ignore"):
+            ref = np.array([u], dtype=np.uint32).view(np.float32).astype(np.float64).view(np.uint64)[0]
+        x = np.array([u], dtype=np.uint32).view(np.float32)[0]
+        if np.isnan(x):
+            # NaN stays NaN (quiet bit and payload carried in the fraction)
+            assert (got >> 52) & 0x7FF == 0x7FF and got & ((1 << 52) - 1) != 0
+            continue
+        assert got == int(ref), hex(u)

@@ -101,13 +101,25 @@ typedef struct {
     int nsub_y;
 } hzs_grid_desc;
 
-/* How the exact coarse solve A_0^{-1} (Eq. 4) is carried out.  Both are exact
+/* How the coarse solve A_0^{-1} (Eq. 4) is carried out.  DENSE and BLOCK are exact
  * up to rounding; they differ in cost.  DENSE: explicit inverse by Gauss-Jordan,
  * one dense matrix-vector product per apply (memory |G_H|^2).  BLOCK: block-
- * tridiagonal LU over groups of coarse rows (2 rows for B_2, 1 for P_1), 2m - 1
- * dependent block products per apply (memory ~3 |G_H|^{3/2} s).  AUTO: DENSE up
- * to 4096 coarse unknowns, BLOCK above. */
-typedef enum { HZS_COARSE_SOLVER_AUTO = 0, HZS_COARSE_SOLVER_DENSE = 1, HZS_COARSE_SOLVER_BLOCK = 2 } hzs_coarse_solver;
+ * tridiagonal LU over groups of coarse rows (2 rows for B_2, 1 for P_1), one
+ * launch per block step (memory ~3 |G_H|^{3/2} s).  AUTO: DENSE up to 4096 coarse
+ * unknowns, BLOCK above.  MULTILEVEL (never chosen by AUTO; Section 5 names the
+ * exact coarse solve as the cost that grows with |G_H|): A_0^{-1} replaced by one
+ * application of SHS2 (Eq. 6) on the coarse grid G_H itself - G_H taken as a grid
+ * (MP-1: the interior of a Dirichlet grid of nc1 + 2 nodes per axis, MP-2: all nc1),
+ * ml_nsub x ml_nsub coarse subdomains with ml_overlap layers of overlap and exact
+ * solves of their blocks of A_0, and a B_2 coarse-of-coarse space of ratio ml_ratio
+ * with its own exact Galerkin solve; FP64.  It is not exact, so the solve around a
+ * preconditioner using it is flexible GMRES (HZS_MIXED) or its step count grows. */
+typedef enum {
+    HZS_COARSE_SOLVER_AUTO = 0,
+    HZS_COARSE_SOLVER_DENSE = 1,
+    HZS_COARSE_SOLVER_BLOCK = 2,
+    HZS_COARSE_SOLVER_MULTILEVEL = 3
+} hzs_coarse_solver;
 
 /* The diagonal D_i of SAS2 and SHS2 (Eqs. 5-6; Section 3 asks only for
  * sum_i R_i^T D_i R_i = I).  OWNER: 1 on the nodes subdomain i owns, 0 on its
@@ -140,6 +152,14 @@ typedef struct {
     int coarse_solver;
     int autotune;
     int scaling_mode;      /* an hzs_scaling_mode (0 = OWNER); used by SAS2 and SHS2 */
+    /* HZS_COARSE_SOLVER_MULTILEVEL only: coarse subdomains per axis (must divide the
+     * coarse grid's nodes per axis minus one), their overlap in coarse node layers
+     * (at most half their width), and the coarse-of-coarse ratio (>= 2, must divide
+     * the same number; at most 8192 coarse-of-coarse unknowns).  Invalid values fail
+     * set-up with HZS_ERR_INVALID_ARG. */
+    int ml_nsub;
+    int ml_overlap;
+    int ml_ratio;
 } hzs_precond_desc;
 
 /* GMRES controls (Section 5): right preconditioning, zero initial guess, no
@@ -280,7 +300,7 @@ hzs_status hzs_kappa_gradient(hzs_precond* p, const void* u_dev, const void* lam
 typedef struct {
     int nfactors;              /* distinct subdomain factorisations (Section 3) */
     int coarse_unknowns;       /* |G_H| unknowns of A_0 (Section 4); 0 for HZS_AS1 */
-    int coarse_solver;         /* HZS_COARSE_SOLVER_DENSE or _BLOCK as resolved; 0 for HZS_AS1 */
+    int coarse_solver;         /* HZS_COARSE_SOLVER_DENSE, _BLOCK or _MULTILEVEL as resolved; 0 for HZS_AS1 */
     double coarse_min_pivot;   /* smallest pivot magnitude of the coarse factorisation */
     int tile_group;            /* launch shape of the subdomain solve: tiles per thread block, */
     int tile_stages;           /*   depth of the factor-block copy ring, */

@@ -64,6 +64,8 @@ struct hzs_precond {
     double2* Ainv = nullptr;
     int coarse_block = 0;             // coarse solve by block-tridiagonal LU instead of Ainv
     CoarseBlockLU cblk;
+    int coarse_ml = 0;                // coarse solve by SHS2 on G_H (multilevel) instead of Ainv
+    CoarseML cml;
     float2* c2f = nullptr;            // complex64 copy of the coarse solution
     int* err = nullptr;               // device error word (HZS_ERR_TIMEOUT from bounded waits)
     int* groups_d = nullptr;          // tiles grouped by shared factor
@@ -285,6 +287,7 @@ extern "C" void hzs_precond_destroy(hzs_precond* p) {
     cudaFree(p->c0); cudaFree(p->lo); cudaFree(p->hi); cudaFree(p->off); cudaFree(p->w); cudaFree(p->wt);
     cudaFree(p->wf); cudaFree(p->wtf); cudaFree(p->c2f); cudaFree(p->err); cudaFree(p->groups_d);
     coarse_block_free(p->cblk);
+    coarse_ml_free(p->cml);
     cudaFree(p->Ainv); cudaFree(p->W64); cudaFree(p->W32); cudaFree(p->tiles_d);
     cudaFree(p->cover_d); cudaFree(p->cover_yd);
     cudaFree(p->t_buf); cudaFree(p->c_buf); cudaFree(p->c2_buf); cudaFree(p->w_buf); cudaFree(p->ytiles);
@@ -327,11 +330,14 @@ static hzs_status setup_impl(hzs_grid* g, const hzs_precond_desc* d, hzs_precond
         if (p->hct.nc1 < 1) return fail(g, HZS_ERR_INVALID_ARG, "coarse mesh has no interior nodes");
         if (p->hct.bad) return fail(g, HZS_ERR_INVALID_ARG, "coarse basis wider than three coarse cells");
         p->Nc = p->hct.nc1 * p->hct.nc1;
-        p->coarse_block = d->coarse_solver == HZS_COARSE_SOLVER_BLOCK ||
-                          (d->coarse_solver == HZS_COARSE_SOLVER_AUTO && p->Nc > kDenseCoarseMax);
-        if (!p->coarse_block && p->Nc > 8192)
+        if (d->coarse_solver < HZS_COARSE_SOLVER_AUTO || d->coarse_solver > HZS_COARSE_SOLVER_MULTILEVEL)
+            return fail(g, HZS_ERR_INVALID_ARG, "coarse_solver must be AUTO, DENSE, BLOCK or MULTILEVEL");
+        p->coarse_ml = d->coarse_solver == HZS_COARSE_SOLVER_MULTILEVEL;
+        p->coarse_block = !p->coarse_ml && (d->coarse_solver == HZS_COARSE_SOLVER_BLOCK ||
+                                            (d->coarse_solver == HZS_COARSE_SOLVER_AUTO && p->Nc > kDenseCoarseMax));
+        if (!p->coarse_block && !p->coarse_ml && p->Nc > 8192)
             return fail(g, HZS_ERR_INVALID_ARG, "coarse space larger than 8192 for the dense coarse inverse");
-        if (p->coarse_block && p->hct.nc1 > 512)
+        if ((p->coarse_block || p->coarse_ml) && p->hct.nc1 > 512)
             return fail(g, HZS_ERR_INVALID_ARG, "more than 512 coarse nodes per axis for the block coarse solve");
         HZS_CUDA(g, upload(&p->c0, p->hct.c0, s));
         HZS_CUDA(g, upload(&p->w, p->hct.w, s));
@@ -348,7 +354,22 @@ static hzs_status setup_impl(hzs_grid* g, const hzs_precond_desc* d, hzs_precond
         p->cx.ct.c0 = p->c0; p->cx.ct.w = p->w; p->cx.ct.lo = p->lo; p->cx.ct.hi = p->hi;
         p->cx.ct.off = p->off; p->cx.ct.wt = p->wt;
         p->cx.ct.wf = p->wf; p->cx.ct.wtf = p->wtf;
-        if (p->coarse_block) {
+        if (p->coarse_ml) {
+            double2* A0b = nullptr;
+            HZS_CUDA(g, dalloc(&A0b, (size_t)p->Nc * 25));
+            launch_galerkin_banded(p->cx, A0b);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) { cudaFree(A0b); return cuda_fail(g, e, "coarse assembly"); }
+            double minpiv = 0.0;
+            std::string why;
+            // the multilevel solver keeps A0b (its level-2 residual and local blocks) and frees it
+            const int rc = coarse_ml_setup(p->cx, p->hct.nc1, g->desc.bc, A0b, d->ml_nsub, d->ml_overlap,
+                                           d->ml_ratio, p->cml, &minpiv, &why);
+            if (rc == -2) return fail(g, HZS_ERR_INVALID_ARG, why);
+            if (rc < 0) return fail(g, HZS_ERR_CUDA, "multilevel coarse set-up failed");
+            p->coarse_minpiv = minpiv;
+            if (rc > 0) return fail(g, HZS_ERR_SINGULAR_COARSE, "a block of the coarse matrix A_0 has a zero pivot");
+        } else if (p->coarse_block) {
             double2* A0b = nullptr;
             HZS_CUDA(g, dalloc(&A0b, (size_t)p->Nc * 25));
             launch_galerkin_banded(p->cx, A0b);
@@ -356,8 +377,8 @@ static hzs_status setup_impl(hzs_grid* g, const hzs_precond_desc* d, hzs_precond
             if (e != cudaSuccess) { cudaFree(A0b); return cuda_fail(g, e, "coarse assembly"); }
             double minpiv = 0.0;
             // the factorisation keeps A0b (the couplings of its solve) and frees it
-            const int rc = coarse_block_setup(p->cx, p->hct.nc1, d->coarse == HZS_COARSE_B2 ? 2 : 1, A0b, p->cblk,
-                                              &minpiv);
+            const int rc = coarse_block_setup(p->cx, p->hct.nc1, d->coarse == HZS_COARSE_B2 ? 2 : 1, 2, A0b,
+                                              p->cblk, &minpiv);
             if (rc < 0) return fail(g, HZS_ERR_CUDA, "coarse block factorisation failed");
             p->coarse_minpiv = minpiv;
             if (rc > 0) return fail(g, HZS_ERR_SINGULAR_COARSE, "coarse matrix A_0 has a zero pivot");
@@ -481,7 +502,7 @@ extern "C" hzs_status hzs_precond_setup(hzs_grid* g, const hzs_precond_desc* d, 
     if (!g || !d) return fail(g, HZS_ERR_INVALID_ARG, "grid or desc is NULL");
     if (d->kind < HZS_AS1 || d->kind > HZS_SHS2) return fail(g, HZS_ERR_INVALID_ARG, "bad preconditioner kind");
     if (d->precision != HZS_FP64 && d->precision != HZS_MIXED) return fail(g, HZS_ERR_INVALID_ARG, "bad precision");
-    if (d->coarse_solver < HZS_COARSE_SOLVER_AUTO || d->coarse_solver > HZS_COARSE_SOLVER_BLOCK)
+    if (d->coarse_solver < HZS_COARSE_SOLVER_AUTO || d->coarse_solver > HZS_COARSE_SOLVER_MULTILEVEL)
         return fail(g, HZS_ERR_INVALID_ARG, "bad coarse_solver");
     if (d->autotune < 0 || d->autotune > 2) return fail(g, HZS_ERR_INVALID_ARG, "bad autotune");
     hzs_precond* p = new hzs_precond();
@@ -514,6 +535,8 @@ static hzs_status ensure_work(hzs_precond* p, int nb) {
         HZS_CUDA(g, dalloc(&p->c_buf, (size_t)p->Nc * nb));
         HZS_CUDA(g, dalloc(&p->c2_buf, (size_t)p->Nc * nb));
         HZS_CUDA(g, dalloc(&p->c2f, (size_t)p->Nc * nb));
+        if (p->coarse_ml && coarse_ml_reserve(p->cml, nb) != 0)
+            return fail(g, HZS_ERR_CUDA, "multilevel coarse work space");
     }
     HZS_CUDA(g, cudaMalloc(&p->w_buf, n * n * cs * nb));
     if (p->desc.kind == HZS_AS1 || p->desc.kind == HZS_AS2 || p->desc.scaling_mode == HZS_SCALING_MULTIPLICITY)
@@ -542,7 +565,9 @@ static hzs_status precond_apply(hzs_precond* p, int nb, const Cv* v, long long v
     const int kind = p->desc.kind;
     if (p->use_coarse) {
         launch_restrict<Cv, R>(cx, nb, v, vs, vscale, vss, (C*)p->t_buf, p->c_buf, sk);
-        if (p->coarse_block)
+        if (p->coarse_ml)
+            launch_coarse_ml_solve(cx, nb, p->cml, p->c_buf, p->c2_buf, f32 ? p->c2f : nullptr, sk);
+        else if (p->coarse_block)
             launch_coarse_block_solve(cx, nb, p->cblk, p->c_buf, p->c2_buf, f32 ? p->c2f : nullptr, sk);
         else
             launch_coarse_matvec(cx, nb, p->Ainv, p->Nc, p->c_buf, p->c2_buf, f32 ? p->c2f : nullptr, sk);
@@ -756,7 +781,9 @@ extern "C" hzs_status hzs_precond_get_info(const hzs_precond* p, hzs_precond_inf
     hzs_precond_info in{};
     in.nfactors = p->nfactors;
     in.coarse_unknowns = p->use_coarse ? p->Nc : 0;
-    in.coarse_solver = !p->use_coarse ? 0 : (p->coarse_block ? HZS_COARSE_SOLVER_BLOCK : HZS_COARSE_SOLVER_DENSE);
+    in.coarse_solver = !p->use_coarse ? 0
+                       : p->coarse_ml  ? HZS_COARSE_SOLVER_MULTILEVEL
+                       : (p->coarse_block ? HZS_COARSE_SOLVER_BLOCK : HZS_COARSE_SOLVER_DENSE);
     in.coarse_min_pivot = p->coarse_minpiv;
     int T = 0, nst = 0, tpr = 0;
     if (tile_shape_resolve(tile_groups(p), p->g->max_mx, p->g->max_my, (int)cplx_size(p->desc.precision), &T, &nst,
@@ -1345,7 +1372,7 @@ hzs_status hzs_internal_set_error(hzs_precond* p, hzs_status s, const std::strin
 
 hzs_status hzs_internal_noalloc_view(hzs_precond* p, NoAllocView* v, std::string* err) {
     if (!p) return fail(nullptr, HZS_ERR_INVALID_ARG, "precond is NULL");
-    if (p->coarse_block)
+    if (p->coarse_block || p->coarse_ml)
         return fail(p->g, HZS_ERR_INVALID_ARG,
                     "the allocation-free apply supports the dense coarse inverse only (coarse_solver DENSE/AUTO "
                     "with at most 4096 coarse unknowns)");

@@ -22,11 +22,14 @@
 
 namespace hzs {
 
-// dst (rows x cols, row-major) = the block of the banded A_0 with row range
-// [r0, r0+rows) and column range [c0, c0+cols); the band holds 25 offsets
-// (dI, dJ) in [-2, 2]^2 per row, offset index o = (dJ + 2) * 5 + (dI + 2).
-__global__ void k_band_to_block(int nc1, const double2* __restrict__ A0b, int r0, int rows, int c0, int cols,
+// dst (rows x cols, row-major) = the block of the banded matrix with row range
+// [r0, r0+rows) and column range [c0, c0+cols); the band of radius rad holds
+// (2 rad + 1)^2 offsets (dI, dJ) in [-rad, rad]^2 per row, offset index
+// o = (dJ + rad) (2 rad + 1) + (dI + rad) (rad = 2: A_0; rad = 3: the Galerkin matrix
+// of a coarse space on G_H).
+__global__ void k_band_to_block(int nc1, int rad, const double2* __restrict__ A0b, int r0, int rows, int c0, int cols,
                                 double2* __restrict__ dst) {
+    const int bw = 2 * rad + 1;
     const long long total = (long long)rows * cols;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
@@ -35,7 +38,8 @@ __global__ void k_band_to_block(int nc1, const double2* __restrict__ A0b, int r0
         const int I = row % nc1, J = row / nc1, I2 = col % nc1, J2 = col / nc1;
         const int dI = I2 - I, dJ = J2 - J;
         double2 v = make_double2(0.0, 0.0);
-        if (dI >= -2 && dI <= 2 && dJ >= -2 && dJ <= 2) v = A0b[(size_t)row * 25 + (dJ + 2) * 5 + (dI + 2)];
+        if (dI >= -rad && dI <= rad && dJ >= -rad && dJ <= rad)
+            v = A0b[(size_t)row * bw * bw + (dJ + rad) * bw + (dI + rad)];
         dst[t] = v;
     }
 }
@@ -146,9 +150,10 @@ __global__ void __launch_bounds__(256) k_cb_step_split(int rows, const double2* 
 // [cr0, cr0 + crows) of a neighbouring block row, batch entry r = blockIdx.y, one
 // thread per row: acc = sum over A_0's band entries of the row whose column lies in
 // that range of A0b[row, o] x[col];  v[row] = v[row] - acc (subtract) or acc.
-__global__ void k_cb_band(int nc1, const double2* __restrict__ A0b, int r0, int rows, int cr0, int crows,
+__global__ void k_cb_band(int nc1, int rad, const double2* __restrict__ A0b, int r0, int rows, int cr0, int crows,
                           const double2* __restrict__ x, double2* __restrict__ v, long long stride, int subtract,
                           BatchSkip sk) {
+    const int bw = 2 * rad + 1;
     const int r = blockIdx.y;
     if (sk.flag && sk.flag[(size_t)r * sk.stride]) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -156,17 +161,15 @@ __global__ void k_cb_band(int nc1, const double2* __restrict__ A0b, int r0, int 
     const long long off = (long long)r * stride;
     const int row = r0 + t, I = row % nc1, J = row / nc1;
     double2 acc = make_double2(0.0, 0.0);
-#pragma unroll
-    for (int dJ = -2; dJ <= 2; ++dJ) {
+    for (int dJ = -rad; dJ <= rad; ++dJ) {
         const int J2 = J + dJ;
         if (J2 < 0 || J2 >= nc1) continue;
-#pragma unroll
-        for (int dI = -2; dI <= 2; ++dI) {
+        for (int dI = -rad; dI <= rad; ++dI) {
             const int I2 = I + dI;
             if (I2 < 0 || I2 >= nc1) continue;
             const int col = J2 * nc1 + I2;
             if (col < cr0 || col >= cr0 + crows) continue;
-            acc = cfma(A0b[(size_t)row * 25 + (dJ + 2) * 5 + (dI + 2)], x[off + col], acc);
+            acc = cfma(A0b[(size_t)row * bw * bw + (dJ + rad) * bw + (dI + rad)], x[off + col], acc);
         }
     }
     v[off + row] = subtract ? csub(v[off + row], acc) : acc;
@@ -179,10 +182,11 @@ __global__ void k_c128_to_c64_batched(int Nc, const double2* __restrict__ a, flo
         b[(size_t)r * Nc + e] = to_f(a[(size_t)r * Nc + e]);
 }
 
-int coarse_block_setup(const Ctx& cx, int nc1, int s, double2* A0b, CoarseBlockLU& lu, double* minpiv) {
+int coarse_block_setup(const Ctx& cx, int nc1, int s, int rad, double2* A0b, CoarseBlockLU& lu, double* minpiv) {
     lu = CoarseBlockLU{};
     lu.nc1 = nc1;
     lu.s = s;
+    lu.rad = rad;
     lu.m = (nc1 + s - 1) / s;
     lu.A0b = A0b;
     const int m = lu.m;
@@ -217,10 +221,10 @@ int coarse_block_setup(const Ctx& cx, int nc1, int s, double2* A0b, CoarseBlockL
     const int cb = 4 * cx.num_sms;
     for (int i = 0; i < m; ++i) {
         const int bi = b[i];
-        k_band_to_block<<<cb, 256, 0, cx.stream>>>(nc1, A0b, r0[i], bi, r0[i], bi, D);
+        k_band_to_block<<<cb, 256, 0, cx.stream>>>(nc1, rad, A0b, r0[i], bi, r0[i], bi, D);
         if (i > 0) {
             // S_i = D_i - L_i Q_{i-1}
-            k_band_to_block<<<cb, 256, 0, cx.stream>>>(nc1, A0b, r0[i], bi, r0[i - 1], b[i - 1], Lb);
+            k_band_to_block<<<cb, 256, 0, cx.stream>>>(nc1, rad, A0b, r0[i], bi, r0[i - 1], b[i - 1], Lb);
             zgemm(cx, bi, bi, b[i - 1], -1.0, Lb, b[i - 1], lu.Q + qo[i - 1], bi, 1.0, D, bi);
         }
         double piv = 0.0;
@@ -233,7 +237,7 @@ int coarse_block_setup(const Ctx& cx, int nc1, int s, double2* A0b, CoarseBlockL
             return fail();
         if (i > 0) zgemm(cx, bi, b[i - 1], bi, 1.0, lu.W + wo[i], bi, Lb, b[i - 1], 0.0, lu.P + po[i], b[i - 1]);
         if (i + 1 < m) {
-            k_band_to_block<<<cb, 256, 0, cx.stream>>>(nc1, A0b, r0[i], bi, r0[i + 1], b[i + 1], Ub);
+            k_band_to_block<<<cb, 256, 0, cx.stream>>>(nc1, rad, A0b, r0[i], bi, r0[i + 1], b[i + 1], Ub);
             zgemm(cx, bi, b[i + 1], bi, 1.0, lu.W + wo[i], bi, Ub, b[i + 1], 0.0, lu.Q + qo[i], b[i + 1]);
         }
     }
@@ -284,7 +288,7 @@ void launch_coarse_block_solve(const Ctx& cx, int nb, const CoarseBlockLU& lu, d
     for (int i = 0; i < m; ++i) {
         const int bi = lu.b[i];
         if (i > 0)
-            k_cb_band<<<dim3((bi + 127) / 128, nb), 128, 0, cx.stream>>>(lu.nc1, lu.A0b, lu.r0[i], bi, lu.r0[i - 1],
+            k_cb_band<<<dim3((bi + 127) / 128, nb), 128, 0, cx.stream>>>(lu.nc1, lu.rad, lu.A0b, lu.r0[i], bi, lu.r0[i - 1],
                                                                          lu.b[i - 1], out, c, Nc, 1, sk);
         const dim3 grd((bi + wpb - 1) / wpb, nb);
         k_cb_step<<<grd, threads, 0, cx.stream>>>(bi, lu.W + lu.wo[i], c + lu.r0[i], bi, nullptr, nullptr, 0, nullptr,
@@ -293,7 +297,7 @@ void launch_coarse_block_solve(const Ctx& cx, int nb, const CoarseBlockLU& lu, d
     // backward: c_i <- U_i x_{i+1}, x_i = y_i - W_i c_i
     for (int i = m - 2; i >= 0; --i) {
         const int bi = lu.b[i];
-        k_cb_band<<<dim3((bi + 127) / 128, nb), 128, 0, cx.stream>>>(lu.nc1, lu.A0b, lu.r0[i], bi, lu.r0[i + 1],
+        k_cb_band<<<dim3((bi + 127) / 128, nb), 128, 0, cx.stream>>>(lu.nc1, lu.rad, lu.A0b, lu.r0[i], bi, lu.r0[i + 1],
                                                                      lu.b[i + 1], out, c, Nc, 0, sk);
         const dim3 grd((bi + wpb - 1) / wpb, nb);
         k_cb_step<<<grd, threads, 0, cx.stream>>>(bi, nullptr, nullptr, 0, lu.W + lu.wo[i], c + lu.r0[i], bi,

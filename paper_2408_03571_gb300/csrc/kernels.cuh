@@ -6,6 +6,8 @@
 // (BatchSkip) is set.
 #pragma once
 
+#include <string>
+
 #include <vector>
 
 #include "common.cuh"
@@ -125,6 +127,7 @@ void launch_galerkin_banded(const Ctx& cx, double2* A0b);
 // ---- coarse_block.cu: block-tridiagonal LU of A_0 over groups of s coarse rows
 struct CoarseBlockLU {
     int nc1 = 0, s = 0, m = 0;            // m block rows of s coarse rows (the last may be shorter)
+    int rad = 2;                          // band radius of the matrix (its couplings reach rad rows)
     std::vector<int> b, r0;               // block sizes and first unknowns
     std::vector<long long> wo, po, qo;    // offsets of W_i, P_i, Q_i
     double2* W = nullptr;                 // W_i = S_i^{-1}        (b_i x b_i)
@@ -134,12 +137,42 @@ struct CoarseBlockLU {
 };
 // 0 on success, 1 if a pivot was zero, -1 on a CUDA error; *minpiv = smallest |pivot|.
 // Takes ownership of A0b (freed by coarse_block_free, or here on failure).
-int coarse_block_setup(const Ctx& cx, int nc1, int s, double2* A0b, CoarseBlockLU& lu, double* minpiv);
+int coarse_block_setup(const Ctx& cx, int nc1, int s, int rad, double2* A0b, CoarseBlockLU& lu, double* minpiv);
 void coarse_block_free(CoarseBlockLU& lu);
 // out = A_0^{-1} c (FP64, stride nc1^2 per batch entry); outf (if given) its complex64 rounding.
 // c is overwritten (it holds the intermediate vectors of the sweeps).
 void launch_coarse_block_solve(const Ctx& cx, int nb, const CoarseBlockLU& lu, double2* c, double2* out,
                                float2* outf, BatchSkip sk);
+
+// Multilevel coarse solve (coarse_ml.cu): SHS2 on the coarse grid G_H in place of A_0^{-1}.
+struct CoarseML {
+    int nc1 = 0, Nc = 0;        // G_H unknowns per axis, in all
+    int lo0 = 0;                // pseudo-grid index of G_H unknown 0 (1 for MP-1, 0 for MP-2)
+    int nc00 = 0, Nc00 = 0;     // coarse-of-coarse unknowns per axis, in all
+    int *lo2 = nullptr, *hi2 = nullptr, *off2 = nullptr, *c02 = nullptr;   // level-2 B_2 tables
+    double *wt2 = nullptr, *w2 = nullptr;
+    double2* A00inv = nullptr;  // Nc00 x Nc00
+    int nsub = 0, max_own = 0, max_m = 0;
+    int4* sub = nullptr;        // per coarse subdomain: extended rectangle x0, y0, mx, my (G_H indices)
+    int4* own = nullptr;        // per coarse subdomain: owned x0, x1, y0, y1 (inclusive)
+    long long* aoff = nullptr;  // per coarse subdomain: offset of its dense inverse in Ainv
+    double2* Ainv = nullptr;
+    double2* A0b = nullptr;     // A_0 in band form (Nc x 25), owned
+    double2 *c00 = nullptr, *c00p = nullptr, *q = nullptr, *wv = nullptr;   // work, nb_cap right-hand sides
+    int nb_cap = 0;
+    int blk00 = 0;              // coarse-of-coarse solve by block LU (above 4096 unknowns) instead of A00inv
+    CoarseBlockLU cblk00;
+};
+// 0 on success, 1 if a pivot was zero, -1 on a CUDA error, -2 on a bad parameter (*why);
+// takes ownership of A0b.
+int coarse_ml_setup(const Ctx& cx, int nc1, int bc, double2* A0b, int ns0, int ov0, int p0, CoarseML& ml,
+                    double* minpiv, std::string* why);
+void coarse_ml_free(CoarseML& ml);
+int coarse_ml_reserve(CoarseML& ml, int nb);
+// out = M_0^{-1} c (FP64, stride nc1^2 per batch entry); outf (if given) its complex64 rounding
+void launch_coarse_ml_solve(const Ctx& cx, int nb, const CoarseML& ml, const double2* c, double2* out, float2* outf,
+                            BatchSkip sk);
+
 int gj_invert(const Ctx& cx, double2* a, int N, double* minpiv);
 
 // ---- local.cu

@@ -24,7 +24,7 @@ ERR_SINGULAR_LOCAL, ERR_SINGULAR_COARSE, ERR_NONFINITE, ERR_TIMEOUT, ERR_BREAKDO
 DIRICHLET, SOMMERFELD = 0, 1
 AS1, AS2, SAS2, SHS2 = 0, 1, 2, 3
 COARSE_NONE, COARSE_P1, COARSE_B2 = 0, 1, 2
-COARSE_SOLVER_AUTO, COARSE_SOLVER_DENSE, COARSE_SOLVER_BLOCK = 0, 1, 2
+COARSE_SOLVER_AUTO, COARSE_SOLVER_DENSE, COARSE_SOLVER_BLOCK, COARSE_SOLVER_MULTILEVEL = 0, 1, 2, 3
 FP64, MIXED = 0, 1
 
 EXPORTS = (
@@ -43,7 +43,8 @@ class GridDesc(ct.Structure):
 class PrecondDesc(ct.Structure):
     _fields_ = [("kind", ct.c_int), ("coarse", ct.c_int), ("coarse_ratio", ct.c_int),
                 ("precision", ct.c_int), ("dedup_tiles", ct.c_int), ("coarse_solver", ct.c_int),
-                ("autotune", ct.c_int), ("scaling_mode", ct.c_int)]
+                ("autotune", ct.c_int), ("scaling_mode", ct.c_int), ("ml_nsub", ct.c_int), ("ml_overlap", ct.c_int),
+                ("ml_ratio", ct.c_int)]
 
 
 class PrecondInfo(ct.Structure):
@@ -231,15 +232,18 @@ class Preconditioner:
 
     def __init__(self, grid: Grid, kind: int = SHS2, coarse: int = COARSE_B2, coarse_ratio: int = 2,
                  precision: int = FP64, dedup_tiles: bool = True, coarse_solver: int = 0, autotune: int = 0,
-                 scaling_mode: int = 0):
+                 scaling_mode: int = 0, ml: tuple[int, int, int] | None = None):
         """autotune: 0 = default launch shape of the subdomain solve, 1 = pick it by timing at
         set-up (reusing an earlier choice for the same problem size), 2 = always re-time.
-        scaling_mode: D_i of SAS2 / SHS2, SCALING_OWNER (0) or SCALING_MULTIPLICITY (1)."""
+        scaling_mode: D_i of SAS2 / SHS2, SCALING_OWNER (0) or SCALING_MULTIPLICITY (1).
+        ml: (coarse subdomains per axis, their overlap, coarse-of-coarse ratio) for
+        coarse_solver = COARSE_SOLVER_MULTILEVEL."""
         lib = load()
         self.grid = grid
         self.kind, self.coarse, self.coarse_ratio, self.precision = kind, coarse, coarse_ratio, precision
+        ml = ml or (0, 0, 0)
         d = PrecondDesc(kind, coarse, coarse_ratio, precision, int(dedup_tiles), int(coarse_solver), int(autotune),
-                        int(scaling_mode))
+                        int(scaling_mode), int(ml[0]), int(ml[1]), int(ml[2]))
         h = ct.c_void_p()
         _check(lib.hzs_precond_setup(grid.handle, ct.byref(d), ct.byref(h)), grid.handle)
         self._h = h

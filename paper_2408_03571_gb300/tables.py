@@ -15,7 +15,10 @@ H_sub = H = r h for r = 4 or 16, overlap r/2, at most 50 steps:
     python -m paper_2408_03571_gb300.tables --kn 16
 
 Everything runs through the C ABI (hzs.py); a coarse space above 4096 unknowns
-is solved by the block-tridiagonal LU (hzs_coarse_solver AUTO).
+is solved by the block-tridiagonal LU (hzs_coarse_solver AUTO), or, with
+--coarse-ml nsub,overlap,ratio, by the multilevel coarse solve:
+
+    python -m paper_2408_03571_gb300.tables --bc sommerfeld --k 40 --coarse-ml 5,2,2
 """
 from __future__ import annotations
 
@@ -37,8 +40,11 @@ def regime(k: float) -> tuple[int, int, int, int]:
     return n, int(round(k)), 2, 4
 
 
-def run(bc: int, ks, precision: int = hzs.FP64, tol: float = 1e-7, maxit: int = 100, device: int = 0):
-    """List of rows {k, n, Nc, (name, coarse): (steps, converged, ms per solve)}."""
+def run(bc: int, ks, precision: int = hzs.FP64, tol: float = 1e-7, maxit: int = 100, device: int = 0,
+        ml: tuple[int, int, int] | None = None):
+    """List of rows {k, n, Nc, (name, coarse): (steps, converged, ms per solve)}.  ml: the
+    multilevel coarse solve (coarse subdomains per axis, overlap, coarse-of-coarse ratio)
+    in place of the exact one."""
     torch.cuda.set_device(device)
     rows = []
     for k in ks:
@@ -48,7 +54,8 @@ def run(bc: int, ks, precision: int = hzs.FP64, tol: float = 1e-7, maxit: int = 
         row = {"k": k, "n": n}
         for cname, coarse in COARSES:
             for kname, kind in KINDS:
-                P = hzs.Preconditioner(g, kind, coarse, p, precision)
+                kw = dict(coarse_solver=hzs.COARSE_SOLVER_MULTILEVEL, ml=ml) if ml else {}
+                P = hzs.Preconditioner(g, kind, coarse, p, precision, **kw)
                 P.solve(f, tol, maxit)                       # warm-up (work space, first launches)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
@@ -117,6 +124,8 @@ def main() -> None:
     ap.add_argument("--k", type=float, nargs="+", default=[20, 40, 60, 80, 100, 120, 140, 200])
     ap.add_argument("--mixed", action="store_true", help="complex64 preconditioner inside FP64 FGMRES")
     ap.add_argument("--kn", type=int, choices=[4, 16], help="the k-n sweep with H_sub = H = 4h or 16h")
+    ap.add_argument("--coarse-ml", type=str, default=None,
+                    help="multilevel coarse solve 'nsub,overlap,ratio' on the coarse grid instead of the exact one")
     args = ap.parse_args()
     hzs.load()
     prec = hzs.MIXED if args.mixed else hzs.FP64
@@ -125,7 +134,8 @@ def main() -> None:
         print(format_kn(run_kn(args.kn, ks, ns, prec), ks, ns))
         return
     bc = hzs.SOMMERFELD if args.bc == "sommerfeld" else hzs.DIRICHLET
-    rows = run(bc, args.k, prec)
+    ml = tuple(int(x) for x in args.coarse_ml.split(",")) if args.coarse_ml else None
+    rows = run(bc, args.k, prec, ml=ml)
     print(format_rows(rows))
     for r in rows:
         t = sum(v[2] for key, v in r.items() if isinstance(key, tuple))

@@ -30,7 +30,7 @@ def test_header_is_c99_and_links(tmp_path):
         "int main(void) {\n"
         "    hzs_grid_desc gd = {65, HZS_DIRICHLET, 20.0, NULL, 4, 2, 0};\n"
         "    hzs_precond_desc pd = {HZS_SHS2, HZS_COARSE_B2, 8, HZS_MIXED, 1, HZS_COARSE_SOLVER_AUTO, 0,\n"
-        "                           HZS_SCALING_OWNER};\n"
+        "                           HZS_SCALING_OWNER, 0, 0, 0};\n"
         "    hzs_solve_desc sd = {1e-7, 200, HZS_SOLVE_GRAPH};\n"
         "    hzs_solve_info info; hzs_precond_info pinfo; hzs_pipe_rates rates;\n"
         "    void (*fns[])(void) = {\n"

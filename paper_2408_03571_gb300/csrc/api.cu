@@ -839,6 +839,7 @@ static hzs_status ensure_krylov(hzs_precond* p, int maxit, int nb, bool full_v) 
     //   HZS_F53_UPD_E=1|2          entries per thread and sweep of the update pass
     //   HZS_F53_G64=4|8            vectors per FP64 task of the dot pass (specialised warps)
     //   HZS_F53_RING64=0|1         FP64 tasks of the dot pass through the copy ring as well
+    //   HZS_F53_DOT_WAVES=1|2      dot pass at 2 blocks/SM in one or two waves of blocks
     if (const char* ev = std::getenv("HZS_F53_OCC")) {
         const int v = std::atoi(ev);
         if (v == 2 || v == 3) kb.s53_minb = kb.s53_dot_minb = v;
@@ -855,6 +856,7 @@ static hzs_status ensure_krylov(hzs_precond* p, int maxit, int nb, bool full_v) 
     if (const char* ev = std::getenv("HZS_F53_UPD_E")) kb.s53_upd_e = std::atoi(ev) == 2 ? 2 : 1;
     if (const char* ev = std::getenv("HZS_F53_G64")) kb.s53_g64 = std::atoi(ev) == 8 ? 8 : 4;
     if (const char* ev = std::getenv("HZS_F53_RING64")) kb.s53_ring64 = std::atoi(ev) ? 1 : 0;
+    if (const char* ev = std::getenv("HZS_F53_DOT_WAVES")) kb.s53_dot_waves = std::atoi(ev) == 1 ? 1 : 2;
     if (const char* ev = std::getenv("HZS_F53_GROUP")) {
         const int v = std::atoi(ev);
         if (v == 1 || v == 2 || v == 4) kb.s53_group = v;

@@ -834,7 +834,8 @@ int launch_s53_dot(const Ctx& cx, const KrylovBufs& kb, int nb, int j, int has_w
                               : (const void*)k_s53_dot_ws<2, 4, 2, 4, false>);
     }
     if (smem_l > 0 && allow_dynamic_smem(fn, smem_l) != cudaSuccess) return 0;
-    const int blocks = std::min(kb.nblk_dot, (minb == 3 ? 3 : 4) * cx.num_sms);
+    const int per_sm = minb == 3 ? 3 : (kb.s53_dot_waves == 1 ? 2 : 4);   // 2 blocks/SM: one or two waves
+    const int blocks = std::min(kb.nblk_dot, per_sm * cx.num_sms);
     int S = kb.maxit + 1;
     long long N = kb.N, ld = kb.ld, sV = kb.sV(), sP = kb.sP();
     int ps = kb.pstride();

@@ -237,7 +237,7 @@ struct KrylovBufs {
     int s53_upd_e = 2;     // update pass: entries per thread and sweep (1 or 2)
     int s53_g64 = 4;       // dot pass, specialised warps: vectors per FP64 task (4 or 8)
     int s53_ring64 = 1;    // dot pass, specialised warps: FP64 tasks also through the copy ring
-    int s53_dot_waves = 2; // dot pass at 2 blocks/SM: launched as one or two waves of blocks
+    int s53_dot_waves = 1; // dot pass at 2 blocks/SM: launched as one or two waves of blocks
     double* sigma;     // (maxit+1): basis vector i = sigma[i] * V_i
     double2* H;        // (maxit+1) x maxit, column j at H[j*(maxit+1)]
     double* cs;        // maxit+1

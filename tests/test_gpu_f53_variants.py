@@ -27,7 +27,7 @@ from paper_2408_03571_gb300.inputs import point_source  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 KNOBS = ("HZS_F53_MASK", "HZS_F53_OCC", "HZS_F53_DOT_OCC", "HZS_F53_WS", "HZS_F53_GROUP", "HZS_F53_RING",
-         "HZS_F53_UPD_E", "HZS_F53_G64", "HZS_F53_RING64")
+         "HZS_F53_UPD_E", "HZS_F53_G64", "HZS_F53_RING64", "HZS_F53_DOT_WAVES")
 
 VARIANTS = [
     {},                                                                     # the defaults
@@ -46,6 +46,7 @@ VARIANTS = [
     {"HZS_F53_RING64": "1", "HZS_F53_MASK": "0xFF,0x6D"},
     {"HZS_F53_MASK": "0x6D,0xFF"},
     {"HZS_F53_MASK": "0x6D,0x00"},
+    {"HZS_F53_DOT_WAVES": "2"},
 ]
 
 

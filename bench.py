@@ -294,7 +294,7 @@ BATCHED = ((25.0, 257, 4, 8), (50.0, 257, 4, 4), (100.0, 513, 8, 4), (200.0, 102
 MAXIT_BATCHED = 100
 # DRAM bytes (read + write) of one launch of each basis pass over its algorithmic bytes,
 # from one ncu capture of the current kernels at the headline size (step j = 200)
-TRAFFIC_RATIO = {"dot": 3578.4 / 3382.4, "update": 3527.4 / 3415.9}
+TRAFFIC_RATIO = {"dot": 3736.3 / 3382.4, "update": 3525.2 / 3415.9}
 
 
 def _peaks_file():

@@ -308,6 +308,9 @@ typedef struct {
     int autotuned;             /* 1 if set-up picked that shape by timing (hzs_precond_desc.autotune) */
     double apply_us_default;   /* with autotuning: one preconditioner apply with the default shape, */
     double apply_us_tuned;     /*   and with the chosen one (microseconds, one right-hand side) */
+    int coarse_tensor_cores;   /* 1 if the block coarse solve forms the dense products of its sweeps
+                                  with more than two right-hand sides on the tensor cores (FP64-
+                                  accurate digit-slice products); 0 if on the FP64 pipe */
 } hzs_precond_info;
 
 /* Fills *out for p.  The paper has no counterpart. */

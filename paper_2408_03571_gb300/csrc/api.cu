@@ -351,6 +351,8 @@ static hzs_status setup_impl(hzs_grid* g, const hzs_precond_desc* d, hzs_precond
         HZS_CUDA(g, upload(&p->wtf, wtf, s));
         HZS_CUDA(g, cudaStreamSynchronize(s));   // the host vectors above go out of scope
         p->cx.ct.nc1 = p->hct.nc1;
+        p->cx.ct.max_sup = 1;
+        for (int I = 0; I < p->hct.nc1; ++I) p->cx.ct.max_sup = std::max(p->cx.ct.max_sup, p->hct.hi[I] - p->hct.lo[I] + 1);
         p->cx.ct.c0 = p->c0; p->cx.ct.w = p->w; p->cx.ct.lo = p->lo; p->cx.ct.hi = p->hi;
         p->cx.ct.off = p->off; p->cx.ct.wt = p->wt;
         p->cx.ct.wf = p->wf; p->cx.ct.wtf = p->wtf;
@@ -382,6 +384,11 @@ static hzs_status setup_impl(hzs_grid* g, const hzs_precond_desc* d, hzs_precond
             if (rc < 0) return fail(g, HZS_ERR_CUDA, "coarse block factorisation failed");
             p->coarse_minpiv = minpiv;
             if (rc > 0) return fail(g, HZS_ERR_SINGULAR_COARSE, "coarse matrix A_0 has a zero pivot");
+            // the dense products of the sweeps with more than two right-hand sides on the
+            // tensor cores (digit slices of the W_i); HZS_COARSE_TC=0 keeps them on the FP64 pipe
+            const char* tc = std::getenv("HZS_COARSE_TC");
+            if (!(tc && std::atoi(tc) == 0) && coarse_oz_setup(p->cx, p->cblk) < 0)
+                return fail(g, HZS_ERR_CUDA, "tensor-core form of the coarse block solve failed");
         } else {
         HZS_CUDA(g, dalloc(&p->Ainv, (size_t)p->Nc * p->Nc));
         launch_galerkin(p->cx, p->Ainv);
@@ -537,6 +544,8 @@ static hzs_status ensure_work(hzs_precond* p, int nb) {
         HZS_CUDA(g, dalloc(&p->c2f, (size_t)p->Nc * nb));
         if (p->coarse_ml && coarse_ml_reserve(p->cml, nb) != 0)
             return fail(g, HZS_ERR_CUDA, "multilevel coarse work space");
+        if (p->coarse_block && nb > 2 && coarse_oz_reserve(p->cblk, nb) != 0)
+            return fail(g, HZS_ERR_CUDA, "coarse block work space");
     }
     HZS_CUDA(g, cudaMalloc(&p->w_buf, n * n * cs * nb));
     if (p->desc.kind == HZS_AS1 || p->desc.kind == HZS_AS2 || p->desc.scaling_mode == HZS_SCALING_MULTIPLICITY)
@@ -793,6 +802,7 @@ extern "C" hzs_status hzs_precond_get_info(const hzs_precond* p, hzs_precond_inf
     in.autotuned = p->autotuned;
     in.apply_us_default = p->apply_us_default;
     in.apply_us_tuned = p->apply_us_tuned;
+    in.coarse_tensor_cores = p->coarse_block && p->cblk.Aoz ? 1 : 0;
     *out = in;
     return HZS_OK;
 }

@@ -70,61 +70,78 @@ void build_coarse_tables(int n, int bc, int kind, int p, HostCoarseTab& t) {
 }
 
 // ------------------------------------------------------------------ restriction
-// t[j * nc1 + I] = s * sum_{i in supp I} phi_I(x_i) v[j n + i]   (x pass; one warp per (j, I))
-template <typename Cv, typename R>
+// t[j * nc1 + I] = s * sum_{i in supp I} phi_I(x_i) v[j n + i]   (x pass)
+// G lanes per restricted value (G divides 32; G is about a quarter of the support, so
+// the lanes stay busy for the short supports of H = 4h and the wide ones of H = 32h);
+// consecutive groups take consecutive I of the same fine row, whose supports overlap.
+template <typename Cv, typename R, int G>
 __global__ void k_restrict_x(int n, CoarseTab ct, const Cv* __restrict__ v, long long vs,
                              const double* __restrict__ vscale, long long vss, cplx_t<R>* __restrict__ t,
                              BatchSkip sk) {
     using C = cplx_t<R>;
     const int r = blockIdx.y;
     if (sk.flag && sk.flag[(size_t)r * sk.stride]) return;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
     const int nc1 = ct.nc1;
-    if (warp >= n * nc1) return;
+    const long long o = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int sub = threadIdx.x % G;
+    const bool ok = o < (long long)n * nc1;
     v += r * vs;
     t += (size_t)r * n * nc1;
-    const int j = warp / nc1, I = warp % nc1;
-    const int lo = ct.lo[I], hi = ct.hi[I];
-    const int off = ct.off[I];
     C acc; acc.x = 0; acc.y = 0;
-    const Cv* row = v + (size_t)j * n;
-    for (int i = lo + lane; i <= hi; i += 32) {
-        const R wgt = CoarseW<R>::wt(ct, off + i - lo);
-        const C x = conv<C>(row[i]);
-        acc.x += wgt * x.x; acc.y += wgt * x.y;
+    if (ok) {
+        const int j = (int)(o / nc1), I = (int)(o % nc1);
+        const int lo = ct.lo[I], hi = ct.hi[I];
+        const int off = ct.off[I];
+        const Cv* row = v + (size_t)j * n;
+        for (int i = lo + sub; i <= hi; i += G) {
+            const R wgt = CoarseW<R>::wt(ct, off + i - lo);
+            const C x = conv<C>(row[i]);
+            acc.x += wgt * x.x; acc.y += wgt * x.y;
+        }
     }
-    acc = warp_sum(acc);
-    if (lane == 0) {
+#pragma unroll
+    for (int m = G / 2; m > 0; m >>= 1) {        // every lane of the warp takes part
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, m);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, m);
+    }
+    if (ok && sub == 0) {
         const R s = vscale ? (R)vscale[r * vss] : (R)1;
         acc.x *= s; acc.y *= s;
-        t[(size_t)j * nc1 + I] = acc;
+        t[o] = acc;
     }
 }
 
-// c[J * nc1 + I] = sum_{j in supp J} phi_J(y_j) t[j * nc1 + I]   (y pass, FP64 result)
-template <typename R>
+// c[J * nc1 + I] = sum_{j in supp J} phi_J(y_j) t[j * nc1 + I]   (y pass, FP64 result);
+// G lanes per value as in the x pass: lane sub of consecutive groups reads consecutive I
+// of the same row j, so the loads coalesce across the groups of a warp.
+template <typename R, int G>
 __global__ void k_restrict_y(int n, CoarseTab ct, const cplx_t<R>* __restrict__ t, double2* __restrict__ c,
                              BatchSkip sk) {
     const int r = blockIdx.y;
     if (sk.flag && sk.flag[(size_t)r * sk.stride]) return;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
     const int nc1 = ct.nc1;
-    if (warp >= nc1 * nc1) return;
+    const long long o = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int sub = threadIdx.x % G;
+    const bool ok = o < (long long)nc1 * nc1;
     t += (size_t)r * n * nc1;
     c += (size_t)r * nc1 * nc1;
-    const int J = warp / nc1, I = warp % nc1;
-    const int lo = ct.lo[J], hi = ct.hi[J];
-    const int off = ct.off[J];
     double2 acc = make_double2(0.0, 0.0);
-    for (int j = lo + lane; j <= hi; j += 32) {
-        const double wgt = ct.wt[off + j - lo];
-        const double2 x = to_d(t[(size_t)j * nc1 + I]);
-        acc.x += wgt * x.x; acc.y += wgt * x.y;
+    if (ok) {
+        const int J = (int)(o / nc1), I = (int)(o % nc1);
+        const int lo = ct.lo[J], hi = ct.hi[J];
+        const int off = ct.off[J];
+        for (int j = lo + sub; j <= hi; j += G) {
+            const double wgt = ct.wt[off + j - lo];
+            const double2 x = to_d(t[(size_t)j * nc1 + I]);
+            acc.x += wgt * x.x; acc.y += wgt * x.y;
+        }
     }
-    acc = warp_sum(acc);
-    if (lane == 0) c[(size_t)J * nc1 + I] = acc;
+#pragma unroll
+    for (int m = G / 2; m > 0; m >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, m);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, m);
+    }
+    if (ok && sub == 0) c[o] = acc;
 }
 
 // ------------------------------------------------------------------ coarse solve
@@ -316,21 +333,34 @@ __global__ void k_gj_colswap(int N, int k, double2* __restrict__ a, const int* _
 }
 
 // ------------------------------------------------------------------ launchers
-template <typename Cv, typename R>
-void launch_restrict(const Ctx& cx, int nb, const Cv* v, long long vs, const double* vscale, long long vss,
-                     cplx_t<R>* t, double2* c, BatchSkip sk) {
+template <typename Cv, typename R, int G>
+static void launch_restrict_g(const Ctx& cx, int nb, const Cv* v, long long vs, const double* vscale, long long vss,
+                              cplx_t<R>* t, double2* c, BatchSkip sk) {
     const int n = cx.op.n, nc1 = cx.ct.nc1;
     const int threads = 256;
     {
-        const long long warps = (long long)n * nc1;
-        const dim3 grid((unsigned)((warps * 32 + threads - 1) / threads), nb);
-        k_restrict_x<Cv, R><<<grid, threads, 0, cx.stream>>>(n, cx.ct, v, vs, vscale, vss, t, sk);
+        const long long lanes = (long long)n * nc1 * G;
+        const dim3 grid((unsigned)((lanes + threads - 1) / threads), nb);
+        k_restrict_x<Cv, R, G><<<grid, threads, 0, cx.stream>>>(n, cx.ct, v, vs, vscale, vss, t, sk);
     }
     {
-        const long long warps = (long long)nc1 * nc1;
-        const dim3 grid((unsigned)((warps * 32 + threads - 1) / threads), nb);
-        k_restrict_y<R><<<grid, threads, 0, cx.stream>>>(n, cx.ct, t, c, sk);
+        const long long lanes = (long long)nc1 * nc1 * G;
+        const dim3 grid((unsigned)((lanes + threads - 1) / threads), nb);
+        k_restrict_y<R, G><<<grid, threads, 0, cx.stream>>>(n, cx.ct, t, c, sk);
     }
+}
+
+template <typename Cv, typename R>
+void launch_restrict(const Ctx& cx, int nb, const Cv* v, long long vs, const double* vscale, long long vss,
+                     cplx_t<R>* t, double2* c, BatchSkip sk) {
+    // lanes per restricted value: about a quarter of the longest support (3p - 1 fine
+    // nodes for B_2 and 2p - 1 for P_1 at H = p h), at least 4
+    if (cx.ct.max_sup <= 16)
+        launch_restrict_g<Cv, R, 4>(cx, nb, v, vs, vscale, vss, t, c, sk);
+    else if (cx.ct.max_sup <= 32)
+        launch_restrict_g<Cv, R, 8>(cx, nb, v, vs, vscale, vss, t, c, sk);
+    else
+        launch_restrict_g<Cv, R, 32>(cx, nb, v, vs, vscale, vss, t, c, sk);
 }
 #define HZS_RS(Cv, R)                                                                                          \
     template void launch_restrict<Cv, R>(const Ctx&, int, const Cv*, long long, const double*, long long,     \

@@ -254,6 +254,7 @@ int coarse_block_setup(const Ctx& cx, int nc1, int s, int rad, double2* A0b, Coa
 }
 
 void coarse_block_free(CoarseBlockLU& lu) {
+    coarse_oz_free(lu);
     cudaFree(lu.W); cudaFree(lu.P); cudaFree(lu.Q); cudaFree(lu.A0b);
     lu = CoarseBlockLU{};
 }
@@ -284,12 +285,19 @@ void launch_coarse_block_solve(const Ctx& cx, int nb, const CoarseBlockLU& lu, d
         if (outf) k_c128_to_c64_batched<<<dim3((Nc + 255) / 256, nb), 256, 0, cx.stream>>>(Nc, out, outf, sk);
         return;
     }
+    // the dense products on the tensor cores (FP64-accurate digit-slice products) when
+    // they are built and the work space holds nb right-hand sides, else on the FP64 pipe
+    const bool oz = lu.Aoz && nb <= lu.oz_cap;
     // forward: c_i <- c_i - L_i y_{i-1}, y_i = W_i c_i
     for (int i = 0; i < m; ++i) {
         const int bi = lu.b[i];
         if (i > 0)
             k_cb_band<<<dim3((bi + 127) / 128, nb), 128, 0, cx.stream>>>(lu.nc1, lu.rad, lu.A0b, lu.r0[i], bi, lu.r0[i - 1],
                                                                          lu.b[i - 1], out, c, Nc, 1, sk);
+        if (oz) {
+            launch_coarse_oz_step(cx, nb, lu, i, c + lu.r0[i], out + lu.r0[i], false, Nc, sk);
+            continue;
+        }
         const dim3 grd((bi + wpb - 1) / wpb, nb);
         k_cb_step<<<grd, threads, 0, cx.stream>>>(bi, lu.W + lu.wo[i], c + lu.r0[i], bi, nullptr, nullptr, 0, nullptr,
                                                   out + lu.r0[i], Nc, sk);
@@ -299,6 +307,10 @@ void launch_coarse_block_solve(const Ctx& cx, int nb, const CoarseBlockLU& lu, d
         const int bi = lu.b[i];
         k_cb_band<<<dim3((bi + 127) / 128, nb), 128, 0, cx.stream>>>(lu.nc1, lu.rad, lu.A0b, lu.r0[i], bi, lu.r0[i + 1],
                                                                      lu.b[i + 1], out, c, Nc, 0, sk);
+        if (oz) {
+            launch_coarse_oz_step(cx, nb, lu, i, c + lu.r0[i], out + lu.r0[i], true, Nc, sk);
+            continue;
+        }
         const dim3 grd((bi + wpb - 1) / wpb, nb);
         k_cb_step<<<grd, threads, 0, cx.stream>>>(bi, nullptr, nullptr, 0, lu.W + lu.wo[i], c + lu.r0[i], bi,
                                                   out + lu.r0[i], out + lu.r0[i], Nc, sk);

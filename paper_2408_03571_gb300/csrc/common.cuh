@@ -214,6 +214,7 @@ __host__ __device__ __forceinline__ double2 op_ddiag_dkappa(const OpDesc& op, in
 // wt[off[I] + (i - lo[I])].
 struct CoarseTab {
     int nc1;            // coarse nodes per axis (kept)
+    int max_sup;        // longest support hi - lo + 1 (sets the lanes per restricted value)
     int* c0;            // [n]
     double* w;          // [3n]
     float* wf;          // [3n]

@@ -134,6 +134,16 @@ struct CoarseBlockLU {
     double2* P = nullptr;                 // P_i = W_i L_i         (b_i x b_{i-1})
     double2* Q = nullptr;                 // Q_i = W_i U_i         (b_i x b_{i+1})
     double2* A0b = nullptr;               // A_0 in band form (Nc x 25), owned: the couplings L_i, U_i
+    // tensor-core form of the many-right-hand-side products W_i X (coarse_oz.cu); Aoz is
+    // null when it is not built
+    unsigned char* Aoz = nullptr;         // bf16 digit slices of [Re W_i | Im W_i], block i at aoz[i]
+    std::vector<long long> aoz;
+    std::vector<int> oz_mt, oz_kch;       // per block: 128-row tiles, 64-wide K chunks
+    int* eoz = nullptr;                   // per coarse unknown: scale exponent of its row of W_i
+    int oz_cap = 0;                       // right-hand sides the work space below holds
+    unsigned char* Boz = nullptr;         // digit slices of one block step's right-hand sides
+    float* Poz = nullptr;                 // per-CTA partial sums (three-word expansions)
+    int* foz = nullptr;                   // per right-hand side: scale exponent
 };
 // 0 on success, 1 if a pivot was zero, -1 on a CUDA error; *minpiv = smallest |pivot|.
 // Takes ownership of A0b (freed by coarse_block_free, or here on failure).
@@ -143,6 +153,15 @@ void coarse_block_free(CoarseBlockLU& lu);
 // c is overwritten (it holds the intermediate vectors of the sweeps).
 void launch_coarse_block_solve(const Ctx& cx, int nb, const CoarseBlockLU& lu, double2* c, double2* out,
                                float2* outf, BatchSkip sk);
+// Tensor-core products of the many-right-hand-side sweeps (coarse_oz.cu).  setup: 0 built,
+// 1 not applicable (a block wider than 520), -1 CUDA error; reserve: work space for nb
+// right-hand sides (0 / -1).  One step: out = W_i x (or out - W_i x when subtract), FP64-
+// accurate, for the nb vectors x + c stride.
+int coarse_oz_setup(const Ctx& cx, CoarseBlockLU& lu);
+int coarse_oz_reserve(CoarseBlockLU& lu, int nb);
+void coarse_oz_free(CoarseBlockLU& lu);
+void launch_coarse_oz_step(const Ctx& cx, int nb, const CoarseBlockLU& lu, int i, const double2* x, double2* out,
+                           bool subtract, long long stride, BatchSkip sk);
 
 // Multilevel coarse solve (coarse_ml.cu): SHS2 on the coarse grid G_H in place of A_0^{-1}.
 struct CoarseML {

@@ -9,6 +9,7 @@
 // The dense blocks W_j are inverted once in FP64 (Gauss-Jordan with partial
 // pivoting inside each block) and stored; the solve is then 2 my dense
 // mx x mx matrix-vector products per tile.
+#include "async.cuh"
 #include "kernels.cuh"
 
 namespace hzs {
@@ -163,41 +164,6 @@ int launch_tile_factor(const Ctx& cx, const FactorDesc* fdesc_dev, int nfactors,
 // step ends with one barrier.
 // Every mbarrier wait is bounded: on expiry the block records HZS_ERR_TIMEOUT in
 // the error word, drains its outstanding copies (again bounded) and returns.
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-// true when the phase with the given parity has completed
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-constexpr long long kSpinLimit = 1LL << 24;   // try_wait polls before a stage wait is declared timed out
-
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit = kSpinLimit) {
-    for (long long it = 0; it < limit; ++it)
-        if (mbar_try(bar, parity)) return true;
-    return false;
-}
 
 template <typename R, int T, int NST>
 __host__ __device__ constexpr size_t tile_smem_bytes(int mx, int my) {

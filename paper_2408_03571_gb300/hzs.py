@@ -51,7 +51,7 @@ class PrecondInfo(ct.Structure):
     _fields_ = [("nfactors", ct.c_int), ("coarse_unknowns", ct.c_int), ("coarse_solver", ct.c_int),
                 ("coarse_min_pivot", ct.c_double), ("tile_group", ct.c_int), ("tile_stages", ct.c_int),
                 ("tile_threads_per_row", ct.c_int), ("autotuned", ct.c_int), ("apply_us_default", ct.c_double),
-                ("apply_us_tuned", ct.c_double)]
+                ("apply_us_tuned", ct.c_double), ("coarse_tensor_cores", ct.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -67,7 +67,9 @@ def parse():
     ap.add_argument("--oracle-full-solve", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--profile-solve", action="store_true",
                     help="set up, then run exactly one stream-issued MIXED solve of the workload and exit "
-                         "(for profiler captures; prints its step count)")
+                         "(for profiler captures; prints its step count); with --workload batched: one "
+                         "MP-2 problem (--k --n --nsub --coarse-ratio) with --nrhs point sources, solved once "
+                         "untimed and once between cudaProfilerStart and cudaProfilerStop")
     # smaller MP-1 instances of the same path, for profiling captures only
     ap.add_argument("--n", type=int, default=1025)
     ap.add_argument("--k", type=float, default=100.0)
@@ -716,13 +718,33 @@ def batched_arm(args, world, rank, local):
 
 def profile_solve(args):
     """One MIXED solve of the workload, stream-issued (every kernel a plain launch), after set-up."""
+    import numpy as np
     import torch
 
     from paper_2408_03571_gb300 import build, hzs
-    from paper_2408_03571_gb300.inputs import point_source
+    from paper_2408_03571_gb300.inputs import point_source, random_source_nodes
 
     build.build()
     hzs.load()
+    if args.workload == "batched":
+        # one problem of the batched MP-2 set: H = p h, sources at seeded nodes as in the set
+        g = hzs.Grid(N, hzs.SOMMERFELD, k=K_WAVE, nsub=NSUB, overlap=OVERLAP)
+        P = hzs.Preconditioner(g, hzs.SHS2, hzs.COARSE_B2, P_COARSE, hzs.MIXED)
+        nodes = random_source_nodes(N, args.nrhs, 1000)
+        F = torch.from_numpy(np.stack([point_source(N, nd) for nd in nodes])).cuda()
+        P.solve(F, TOL, MAXIT)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        _, inf = P.solve(F, TOL, MAXIT)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"workload": f"MP-2 Sommerfeld, k={K_WAVE:g}, n={N}, {NSUB}x{NSUB} subdomains, overlap 2, "
+                                      f"SHS2 with B2 H={P_COARSE}h, {args.nrhs} point sources, GMRES to 1e-6 "
+                                      f"(at most {MAXIT} steps; profiling instance)",
+                          "iterations_max": max(r.iterations for r in inf), "info": P.info()}), flush=True)
+        P.close()
+        g.close()
+        return
     f = torch.from_numpy(point_source(N)).cuda()
     g = hzs.Grid(N, hzs.DIRICHLET, k=K_WAVE, nsub=NSUB, overlap=OVERLAP)
     P = hzs.Preconditioner(g, hzs.SHS2, hzs.COARSE_B2, P_COARSE, hzs.MIXED)

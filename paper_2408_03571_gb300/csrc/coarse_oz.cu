@@ -20,8 +20,9 @@
 //
 // Layout: a slice of A (or B) is stored in chunks of 128 (32) rows by 64 K, each chunk the
 // canonical no-swizzle K-major arrangement of the tensor cores (core matrices of 8 rows by
-// 8 K, 128 contiguous bytes; consecutive core matrices along K, then along rows), so that
-// one bulk copy moves a chunk into shared memory ready for the MMA.
+// 8 K, 128 contiguous bytes; consecutive core matrices along K, then along rows).  The
+// chunks one CTA reads for one K range sit side by side (A: the two slices s and 9 - s of
+// a row tile; B: slices 1..8 of a column tile), so two bulk copies fill a pipeline stage.
 //
 // One CTA computes a 128 x 32 output tile for the slice pairs (s, t) with s in
 // {sp + 1, 8 - sp} (sp = 0..3) and s + t <= 9: 9 pairs for every sp, so the four CTAs of a
@@ -97,8 +98,19 @@ __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long m
     return m;
 }
 
+// Chunk of A slice s (1..8) for row tile mt and K chunk kc: slices s and 9 - s are paired
+// (sp = min(s, 9 - s) - 1, the smaller first) and stored side by side.
+__host__ __device__ __forceinline__ size_t oz_achunk(int s, int mt, int kc, int MT, int KCH) {
+    const int sp = (s <= 4 ? s : 9 - s) - 1, h = s <= 4 ? 0 : 1;
+    return (((size_t)sp * MT + mt) * KCH + kc) * 2 + h;
+}
+// Chunk of B slice t (1..8) for column tile nq and K chunk kc: slices 1..8 side by side.
+__host__ __device__ __forceinline__ size_t oz_bchunk(int t, int nq, int kc, int KCH) {
+    return ((size_t)nq * KCH + kc) * kOzS + (t - 1);
+}
+
 // Set-up: digit slices of A = [Re W | Im W] (b x b complex, row-major), one block per row;
-// As (zeroed beforehand) receives slice s at chunks ((s MT + mt) KCH + kc); erow[r] = e_r.
+// As (zeroed beforehand) receives slice s at chunk oz_achunk; erow[r] = e_r.
 __global__ void k_oz_split_a(const double2* __restrict__ W, int b, int MT, int KCH, unsigned short* __restrict__ As,
                              int* __restrict__ erow) {
     __shared__ unsigned long long red[32];
@@ -123,7 +135,7 @@ __global__ void k_oz_split_a(const double2* __restrict__ W, int b, int MT, int K
         const size_t in_chunk = (size_t)oz_off(rl, kl) / 2;
 #pragma unroll
         for (int s = 1; s <= kOzS; ++s)
-            As[(((size_t)(s - 1) * MT + mt) * KCH + kc) * (kOzAChunk / 2) + in_chunk] = oz_digit(a, neg, s);
+            As[oz_achunk(s, mt, kc, MT, KCH) * (kOzAChunk / 2) + in_chunk] = oz_digit(a, neg, s);
     }
 }
 
@@ -162,7 +174,7 @@ __global__ void k_oz_split_b(const double2* __restrict__ x, long long stride, in
         const size_t o0 = (size_t)oz_off(nl, kl) / 2, o1 = (size_t)oz_off(nl + 1, kl) / 2;
 #pragma unroll
         for (int s = 1; s <= kOzS; ++s) {
-            unsigned short* chunk = Bs + (((size_t)(s - 1) * NQ + nq) * KCH + kc) * (kOzBChunk / 2);
+            unsigned short* chunk = Bs + oz_bchunk(s, nq, kc, KCH) * (kOzBChunk / 2);
             chunk[o0] = oz_digit(a0, g0, s);
             chunk[o1] = oz_digit(a1, g1, s);
         }
@@ -213,11 +225,9 @@ __global__ void __launch_bounds__(128, 1) k_oz_gemm(const unsigned char* __restr
         auto load = [&](int kc, int st) {
             unsigned char* S = oz_smem + (size_t)st * kOzStageBytes;
             mbar_expect_tx(&full[st], stage_bytes);
-            bulk_g2s(S, As + (((size_t)(sa - 1) * MT + mt) * KCH + kc) * kOzAChunk, kOzAChunk, &full[st]);
-            bulk_g2s(S + kOzAChunk, As + (((size_t)(sb - 1) * MT + mt) * KCH + kc) * kOzAChunk, kOzAChunk, &full[st]);
-            for (int t = 0; t < tmax; ++t)
-                bulk_g2s(S + 2 * kOzAChunk + t * kOzBChunk, Bs + (((size_t)t * NQ + nq) * KCH + kc) * kOzBChunk,
-                         kOzBChunk, &full[st]);
+            bulk_g2s(S, As + oz_achunk(sa, mt, kc, MT, KCH) * kOzAChunk, 2 * kOzAChunk, &full[st]);
+            bulk_g2s(S + 2 * kOzAChunk, Bs + oz_bchunk(1, nq, kc, KCH) * kOzBChunk, (uint32_t)(tmax * kOzBChunk),
+                     &full[st]);
         };
         int loaded = 0;                                       // chunks whose copies are issued
         for (; loaded < kOzStages && loaded < KCH; ++loaded) load(loaded, loaded);

@@ -10,7 +10,8 @@ expansions, one rounding to FP64).  Checked here:
   (HZS_COARSE_TC=0) to 1e-11, MP-1 and MP-2, B_2 and P_1, ragged block sizes;
 * at the widest blocks (n = 1025, H = 4h: 257 coarse nodes a row, blocks of 514, K = 1028,
   the limit of exact accumulation) against the FP64-pipe sweeps;
-* numbers of right-hand sides that do not fill a 32-column tile (3, 5, 17);
+* numbers of right-hand sides that do not fill a 32-column tile (3, 5, 17), and 64 (four
+  column tiles);
 * a batched GMRES solve takes the same steps and reaches the same solutions as with the
   FP64-pipe sweeps, right-hand sides that converge early included;
 * the preconditioner reports which form it built.
@@ -119,13 +120,12 @@ def test_widest_blocks(hzs, fp64_sweeps):
         assert rel(zt[r], zf[r]) < 1e-11
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_batched_solve_same_steps(hzs, fp64_sweeps, prec):
+@pytest.mark.parametrize("prec,nrhs", [(0, 8), (1, 8), (0, 64)])
+def test_batched_solve_same_steps(hzs, fp64_sweeps, prec, nrhs):
     """FP64 preconditioner: the same steps; complex64 (whose coarse solution is rounded to
     complex64 after the FP64 solve, so a last-bit difference there can flip a rounding):
-    within one step."""
+    within one step.  64 right-hand sides fill four 32-column tiles."""
     n, nsub, ov, p, k = 257, 4, 2, 4, 50.0
-    nrhs = 8
     nodes = random_source_nodes(n, nrhs, 7)
     F = np.stack([point_source(n, nd) for nd in nodes])
     F[5] = point_source(n)                              # the centre source: its own step count

@@ -27,7 +27,8 @@
 // One CTA computes a 128 x 32 output tile for the slice pairs (s, t) with s in
 // {sp + 1, 8 - sp} (sp = 0..3) and s + t <= 9: 9 pairs for every sp, so the four CTAs of a
 // tile carry equal work.  K streams through a 3-stage ring (bulk copies on full barriers,
-// MMA completion on empty barriers); the 9 accumulators (128 x 32 FP32 each) live in
+// MMA completion on empty barriers; one thread copies, another issues the MMAs); the 9
+// accumulators (128 x 32 FP32 each) live in
 // tensor memory.  A combine kernel adds the four CTAs' expansions, converts to FP64 and
 // applies the scales.
 #include <vector>
@@ -220,17 +221,30 @@ __global__ void __launch_bounds__(128, 1) k_oz_gemm(const unsigned char* __restr
     tc_fence_after();
     const uint32_t tmem = tmem_base;
 
+    auto load = [&](int kc, int st) {
+        unsigned char* S = oz_smem + (size_t)st * kOzStageBytes;
+        mbar_expect_tx(&full[st], stage_bytes);
+        bulk_g2s(S, As + oz_achunk(sa, mt, kc, MT, KCH) * kOzAChunk, 2 * kOzAChunk, &full[st]);
+        bulk_g2s(S + 2 * kOzAChunk, Bs + oz_bchunk(1, nq, kc, KCH) * kOzBChunk, (uint32_t)(tmax * kOzBChunk),
+                 &full[st]);
+    };
+    // warp 0 copies, warp 1 issues the MMAs: neither waits on the other's barriers
+    __shared__ int s_loaded, s_consumed;
     if (tid == 0) {
+        // a stage is refilled once the MMAs of the chunk kOzStages back have read it
+        int kc = 0;
+        for (; kc < KCH; ++kc) {
+            const int st = kc % kOzStages;
+            if (kc >= kOzStages &&
+                !mbar_wait_bounded(&empty[st], (uint32_t)(((kc - kOzStages) / kOzStages) & 1))) {
+                s_fail = 1;
+                break;
+            }
+            load(kc, st);
+        }
+        s_loaded = kc;
+    } else if (tid == 32) {
         const uint32_t idesc = idesc_bf16_f32(kOzMT, kOzNC);
-        auto load = [&](int kc, int st) {
-            unsigned char* S = oz_smem + (size_t)st * kOzStageBytes;
-            mbar_expect_tx(&full[st], stage_bytes);
-            bulk_g2s(S, As + oz_achunk(sa, mt, kc, MT, KCH) * kOzAChunk, 2 * kOzAChunk, &full[st]);
-            bulk_g2s(S + 2 * kOzAChunk, Bs + oz_bchunk(1, nq, kc, KCH) * kOzBChunk, (uint32_t)(tmax * kOzBChunk),
-                     &full[st]);
-        };
-        int loaded = 0;                                       // chunks whose copies are issued
-        for (; loaded < kOzStages && loaded < KCH; ++loaded) load(loaded, loaded);
         int kc = 0;
         for (; kc < KCH; ++kc) {
             const int st = kc % kOzStages;
@@ -253,24 +267,15 @@ __global__ void __launch_bounds__(128, 1) k_oz_gemm(const unsigned char* __restr
                 }
             }
             mma_commit(&empty[st]);
-            // refill the stage of the previous chunk once its MMAs have read it
-            if (kc >= 1 && loaded < KCH) {
-                const int ps = (kc - 1) % kOzStages;
-                if (!mbar_wait_bounded(&empty[ps], (uint32_t)(((kc - 1) / kOzStages) & 1))) {
-                    s_fail = 1;
-                    ++kc;
-                    break;
-                }
-                load(loaded, ps);
-                ++loaded;
-            }
         }
         mma_commit(&done);
-        if (s_fail) {
-            if (err) atomicExch(err, (int)HZS_ERR_TIMEOUT);
-            for (int c = kc; c < loaded; ++c)                 // copies possibly in flight
-                mbar_wait_bounded(&full[c % kOzStages], (uint32_t)((c / kOzStages) & 1));
-        }
+        s_consumed = kc;
+    }
+    __syncthreads();
+    if (tid == 0 && s_fail) {
+        if (err) atomicExch(err, (int)HZS_ERR_TIMEOUT);
+        for (int c = s_consumed; c < s_loaded; ++c)           // copies possibly in flight
+            mbar_wait_bounded(&full[c % kOzStages], (uint32_t)((c / kOzStages) & 1));
     }
     __syncthreads();
     bool ok = mbar_wait_bounded(&done, 0);

@@ -245,6 +245,19 @@ __global__ void __launch_bounds__(128, 1) k_oz_gemm(const unsigned char* __restr
         s_loaded = kc;
     } else if (tid == 32) {
         const uint32_t idesc = idesc_bf16_f32(kOzMT, kOzNC);
+        // the 9 pairs' A and B slots in a stage, in the 16-byte units of a descriptor's start
+        // address: each MMA's descriptors are then one 64-bit add to the stage's (shared
+        // addresses stay below 2^14 units, so the field never carries)
+        // (pairs 0 .. na - 1 are (sa, t = p + 1), the rest (sb, t = p - na + 1))
+        const int na = 9 - sa;
+        uint32_t aoff[9], boff[9];
+#pragma unroll
+        for (int p = 0; p < 9; ++p) {
+            const int h = p >= na, t = h ? p - na + 1 : p + 1;
+            aoff[p] = (uint32_t)(h * kOzAChunk) >> 4;
+            boff[p] = (uint32_t)(2 * kOzAChunk + (t - 1) * kOzBChunk) >> 4;
+        }
+        const uint64_t dbase = smem_desc(smem_u32(oz_smem), 128, 1024);
         int kc = 0;
         for (; kc < KCH; ++kc) {
             const int st = kc % kOzStages;
@@ -253,19 +266,14 @@ __global__ void __launch_bounds__(128, 1) k_oz_gemm(const unsigned char* __restr
                 break;
             }
             tc_fence_after();
-            const uint32_t sbase = smem_u32(oz_smem + (size_t)st * kOzStageBytes);
-            int p = 0;
-            for (int h = 0; h < 2; ++h) {
-                const int s = h ? sb : sa;
-                const uint32_t abase = sbase + (uint32_t)(h * kOzAChunk);
-                for (int t = 1; t <= 9 - s; ++t, ++p) {
-                    const uint32_t bbase = sbase + (uint32_t)(2 * kOzAChunk + (t - 1) * kOzBChunk);
+            const uint64_t dst = dbase + (uint64_t)((uint32_t)(st * kOzStageBytes) >> 4);
+            const uint32_t first = kc != 0;
 #pragma unroll
-                    for (int ks = 0; ks < kOzKC / 16; ++ks)
-                        mma_bf16(tmem + (uint32_t)(p * kOzNC), smem_desc(abase + ks * 256, 128, 1024),
-                                 smem_desc(bbase + ks * 256, 128, 1024), idesc, (uint32_t)((kc | ks) != 0));
-                }
-            }
+            for (int p = 0; p < 9; ++p)
+#pragma unroll
+                for (int ks = 0; ks < kOzKC / 16; ++ks)
+                    mma_bf16(tmem + (uint32_t)(p * kOzNC), dst + aoff[p] + (uint32_t)(ks * 16),
+                             dst + boff[p] + (uint32_t)(ks * 16), idesc, ks == 0 ? first : 1u);
             mma_commit(&empty[st]);
         }
         mma_commit(&done);

@@ -105,7 +105,11 @@ typedef struct {
  * up to rounding; they differ in cost.  DENSE: explicit inverse by Gauss-Jordan,
  * one dense matrix-vector product per apply (memory |G_H|^2).  BLOCK: block-
  * tridiagonal LU over groups of coarse rows (2 rows for B_2, 1 for P_1), one
- * launch per block step (memory ~3 |G_H|^{3/2} s).  AUTO: DENSE up to 4096 coarse
+ * launch per block step (memory ~3 |G_H|^{3/2} s); with more than two right-hand
+ * sides its dense block products run on the tensor cores as FP64-accurate digit-slice
+ * products (blocks up to 520 wide; their slices add about 32 s |G_H|^{3/2} bytes;
+ * HZS_COARSE_TC=0 in the environment at set-up keeps them on the FP64 pipe, and
+ * hzs_precond_info.coarse_tensor_cores reports which).  AUTO: DENSE up to 4096 coarse
  * unknowns, BLOCK above.  MULTILEVEL (never chosen by AUTO; Section 5 names the
  * exact coarse solve as the cost that grows with |G_H|): A_0^{-1} replaced by one
  * application of SHS2 (Eq. 6) on the coarse grid G_H itself - G_H taken as a grid

@@ -162,22 +162,39 @@ __global__ void k_oz_split_b(const double2* __restrict__ x, long long stride, in
     const int e = oz_exponent(m);
     if (threadIdx.x == 0) fcol[c] = real ? e : 0;
     const int n0 = 2 * c, nq = n0 / kOzNC, nl = n0 % kOzNC;   // both columns in the same chunk
-    for (int k2 = threadIdx.x; k2 < KCH * kOzKC; k2 += blockDim.x) {
-        double v0 = 0.0, v1 = 0.0;
-        if (real && k2 < 2 * b) {
-            const double2 z = xc[k2 < b ? k2 : k2 - b];
-            v0 = k2 < b ? z.x : -z.y;
-            v1 = k2 < b ? z.y : z.x;
+    // one thread per 8 consecutive K: the 16-byte row of a core matrix, written whole for
+    // each slice and column
+    for (int ko = threadIdx.x; ko < KCH * kOzKC / 8; ko += blockDim.x) {
+        const int k0 = ko * 8;
+        uint32_t w0[kOzS][4], w1[kOzS][4];
+#pragma unroll
+        for (int s = 0; s < kOzS; ++s)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) w0[s][q] = w1[s][q] = 0u;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int k2 = k0 + j;
+            double v0 = 0.0, v1 = 0.0;
+            if (real && k2 < 2 * b) {
+                const double2 z = xc[k2 < b ? k2 : k2 - b];
+                v0 = k2 < b ? z.x : -z.y;
+                v1 = k2 < b ? z.y : z.x;
+            }
+            bool g0, g1;
+            const unsigned long long a0 = oz_fixed(v0, e, g0), a1 = oz_fixed(v1, e, g1);
+#pragma unroll
+            for (int s = 0; s < kOzS; ++s) {
+                w0[s][j >> 1] |= (uint32_t)oz_digit(a0, g0, s + 1) << ((j & 1) * 16);
+                w1[s][j >> 1] |= (uint32_t)oz_digit(a1, g1, s + 1) << ((j & 1) * 16);
+            }
         }
-        bool g0, g1;
-        const unsigned long long a0 = oz_fixed(v0, e, g0), a1 = oz_fixed(v1, e, g1);
-        const int kc = k2 / kOzKC, kl = k2 % kOzKC;
+        const int kc = k0 / kOzKC, kl = k0 % kOzKC;             // kl a multiple of 8
         const size_t o0 = (size_t)oz_off(nl, kl) / 2, o1 = (size_t)oz_off(nl + 1, kl) / 2;
 #pragma unroll
-        for (int s = 1; s <= kOzS; ++s) {
-            unsigned short* chunk = Bs + oz_bchunk(s, nq, kc, KCH) * (kOzBChunk / 2);
-            chunk[o0] = oz_digit(a0, g0, s);
-            chunk[o1] = oz_digit(a1, g1, s);
+        for (int s = 0; s < kOzS; ++s) {
+            unsigned short* chunk = Bs + oz_bchunk(s + 1, nq, kc, KCH) * (kOzBChunk / 2);
+            *reinterpret_cast<uint4*>(chunk + o0) = make_uint4(w0[s][0], w0[s][1], w0[s][2], w0[s][3]);
+            *reinterpret_cast<uint4*>(chunk + o1) = make_uint4(w1[s][0], w1[s][1], w1[s][2], w1[s][3]);
         }
     }
 }
